@@ -1,0 +1,253 @@
+"""FP64 CPU oracle for the batched Levenberg-Marquardt kinematic optimiser.
+
+TEST INFRASTRUCTURE ONLY.  The test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The library product
+(``paper_2505_03728_gb300``) never imports this package, and this package
+never imports the product: the two share only the seeded input generators.
+
+The arithmetic lives in plain C (``pk_oracle.c``, ``trajopt_oracle.c``,
+``mlp_oracle.c``), compiled with gcc into ``oracle/_build/libpk_oracle.so``;
+this module is the ctypes marshalling around it.  Each C function cites the
+paper passage it follows (Sec. III-A solver, Sec. III-B variables, Sec. III-C
+costs and Eq. 1).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libpk_oracle.so")
+_SOURCES = ["pk_oracle.c", "trajopt_oracle.c", "mlp_oracle.c"]
+_lock = threading.Lock()
+_lib = None
+
+JOINT_FIXED, JOINT_REVOLUTE, JOINT_PRISMATIC = 0, 1, 2
+TARGET_POSE, TARGET_POSITION = 0, 1
+P_CONVERGED, P_MAX_ITERS, P_NONFINITE = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no FMA contraction, no -march)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES if os.path.exists(os.path.join(_HERE, s))]
+    newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "pk_oracle.h")])
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp] + srcs + [
+        "-lpthread", "-lm"]
+    subprocess.run(cmd, check=True, cwd=_HERE)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_i32p = C.POINTER(C.c_int32)
+_f64p = C.POINTER(C.c_double)
+
+
+class _Robot(C.Structure):
+    _fields_ = [("n_joints", C.c_int32), ("parent", _i32p), ("type", _i32p), ("axis", _f64p),
+                ("origin", _f64p), ("lower", _f64p), ("upper", _f64p)]
+
+
+class _IkParams(C.Structure):
+    _fields_ = [("w_pos", C.c_double), ("w_rot", C.c_double), ("w_limit", C.c_double),
+                ("w_rest", C.c_double), ("lambda0", C.c_double), ("lambda_min", C.c_double),
+                ("lambda_max", C.c_double), ("nu", C.c_double), ("tol_pos", C.c_double),
+                ("tol_rot", C.c_double), ("max_iters", C.c_int32), ("early_exit", C.c_int32)]
+
+
+class _TargetSpec(C.Structure):
+    _fields_ = [("n_targets", C.c_int32), ("links", _i32p), ("kinds", _i32p)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB_PATH)
+            L.or_n_dof.restype = C.c_int32
+            L.or_n_residuals.restype = C.c_int32
+            L.or_cholesky_solve.restype = C.c_int32
+            L.or_ik_solve.restype = C.c_int32
+            for name in ("or_trajopt_solve", "or_mlp_forward", "or_mlp_loss_grad"):
+                if hasattr(L, name):
+                    getattr(L, name).restype = C.c_int32
+            _lib = L
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _p(a):
+    if a is None:
+        return None
+    if a.dtype == np.float64:
+        return a.ctypes.data_as(_f64p)
+    if a.dtype == np.int32:
+        return a.ctypes.data_as(_i32p)
+    raise TypeError(a.dtype)
+
+
+class Robot:
+    """A kinematic tree: parent[j] < j, joint types 0/1/2, axes, origins, limits."""
+
+    def __init__(self, parent, type, axis, origin, lower, upper):
+        self.parent = _i32(parent)
+        self.type = _i32(type)
+        self.axis = _f64(axis).reshape(-1, 3)
+        self.origin = _f64(origin).reshape(-1, 12)
+        self.lower = _f64(lower)
+        self.upper = _f64(upper)
+        self.n_joints = int(self.parent.shape[0])
+        self._c = _Robot(self.n_joints, _p(self.parent), _p(self.type), _p(self.axis),
+                         _p(self.origin), _p(self.lower), _p(self.upper))
+        self.n_dof = int(lib().or_n_dof(C.byref(self._c)))
+
+    @classmethod
+    def from_dict(cls, d):
+        return cls(d["parent"], d["type"], d["axis"], d["origin"], d["lower"], d["upper"])
+
+    @property
+    def dof_lower(self):
+        return self.lower[self.type != JOINT_FIXED]
+
+    @property
+    def dof_upper(self):
+        return self.upper[self.type != JOINT_FIXED]
+
+
+class IkParams:
+    def __init__(self, w_pos=1.0, w_rot=0.5, w_limit=10.0, w_rest=1e-3, lambda0=1e-2,
+                 lambda_min=1e-10, lambda_max=1e10, nu=2.0, tol_pos=1e-3,
+                 tol_rot=np.deg2rad(0.5), max_iters=30, early_exit=0):
+        self._c = _IkParams(w_pos, w_rot, w_limit, w_rest, lambda0, lambda_min, lambda_max, nu,
+                            tol_pos, tol_rot, max_iters, early_exit)
+
+    def __getattr__(self, k):
+        return getattr(self.__dict__["_c"], k)
+
+
+class Targets:
+    def __init__(self, links, kinds=None):
+        self.links = _i32(links)
+        self.kinds = None if kinds is None else _i32(kinds)
+        self._c = _TargetSpec(int(self.links.shape[0]), _p(self.links), _p(self.kinds))
+        self.k = int(self.links.shape[0])
+
+
+def fk(robot: Robot, q) -> np.ndarray:
+    """All joint frames: [..., n_joints, 12] (3x4 row-major)."""
+    q = _f64(q)
+    flat = q.reshape(-1, robot.n_dof)
+    out = np.empty((flat.shape[0], robot.n_joints, 12))
+    for i in range(flat.shape[0]):
+        row = np.ascontiguousarray(flat[i])
+        lib().or_fk(C.byref(robot._c), _p(row), out[i].ctypes.data_as(_f64p))
+    return out.reshape(q.shape[:-1] + (robot.n_joints, 12))
+
+
+def se3_log(T):
+    T = _f64(T)
+    out = np.empty(6)
+    lib().or_se3_log(_p(T), _p(out))
+    return out
+
+
+def se3_exp(xi):
+    xi = _f64(xi)
+    out = np.empty(12)
+    lib().or_se3_exp(_p(xi), _p(out))
+    return out
+
+
+def se3_jl(xi):
+    xi = _f64(xi)
+    out = np.empty((6, 6))
+    lib().or_se3_jl(_p(xi), out.ctypes.data_as(_f64p))
+    return out
+
+
+def se3_jlinv(xi):
+    xi = _f64(xi)
+    out = np.empty((6, 6))
+    lib().or_se3_jlinv(_p(xi), out.ctypes.data_as(_f64p))
+    return out
+
+
+def n_residuals(robot: Robot, tg: Targets) -> int:
+    return int(lib().or_n_residuals(C.byref(robot._c), C.byref(tg._c)))
+
+
+def ik_residual(robot: Robot, params: IkParams, tg: Targets, targets, q, jacobian=True):
+    targets = _f64(targets).reshape(tg.k, 12)
+    q = _f64(q)
+    m = n_residuals(robot, tg)
+    r = np.empty(m)
+    J = np.empty((m, robot.n_dof)) if jacobian else None
+    lib().or_ik_residual(C.byref(robot._c), C.byref(params._c), C.byref(tg._c), _p(targets),
+                         _p(q), _p(r), None if J is None else J.ctypes.data_as(_f64p))
+    return (r, J) if jacobian else r
+
+
+def ik_errors(robot: Robot, tg: Targets, targets, q):
+    targets = _f64(targets).reshape(tg.k, 12)
+    q = _f64(q)
+    pe, re = C.c_double(), C.c_double()
+    lib().or_ik_errors(C.byref(robot._c), C.byref(tg._c), _p(targets), _p(q), C.byref(pe),
+                       C.byref(re))
+    return pe.value, re.value
+
+
+def cholesky_solve(A, b):
+    A = _f64(A)
+    b = _f64(b)
+    n = b.shape[0]
+    x = np.empty(n)
+    rc = lib().or_cholesky_solve(n, A.ctypes.data_as(_f64p), _p(b), _p(x))
+    return x if rc == 0 else None
+
+
+def ik_solve(robot: Robot, params: IkParams, tg: Targets, targets, seeds, n_trace=0,
+             per_problem=False, n_threads=0):
+    """Multi-start LM.  targets [B][k][12], seeds [B][S][n_dof].
+
+    Returns a dict with q [B][n], err [B][2], iters [B], status [B], threads, and
+    (optionally) per_problem [B*S][n+5], trace [B*S][n_trace][n], margin [B*S].
+    """
+    targets = _f64(targets).reshape(-1, tg.k, 12)
+    B = targets.shape[0]
+    seeds = _f64(seeds).reshape(B, -1, robot.n_dof)
+    S = seeds.shape[1]
+    n = robot.n_dof
+    q = np.zeros((B, n))
+    err = np.zeros((B, 2))
+    iters = np.zeros(B, np.int32)
+    status = np.zeros(B, np.int32)
+    pp = np.zeros((B * S, n + 5)) if per_problem else None
+    tr = np.zeros((B * S, n_trace, n)) if n_trace > 0 else None
+    mg = np.zeros(B * S) if n_trace > 0 else None
+    threads = lib().or_ik_solve(
+        C.byref(robot._c), C.byref(params._c), C.byref(tg._c), B, S, _p(targets), _p(seeds),
+        _p(q), _p(err), _p(iters), _p(status), None if pp is None else pp.ctypes.data_as(_f64p),
+        int(n_trace), None if tr is None else tr.ctypes.data_as(_f64p), _p(mg), int(n_threads))
+    out = dict(q=q, err=err, iters=iters, status=status, threads=int(threads))
+    if pp is not None:
+        out["per_problem"] = pp
+    if tr is not None:
+        out["trace"] = tr
+        out["margin"] = mg
+    return out

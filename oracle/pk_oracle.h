@@ -1,0 +1,102 @@
+/*
+ * pk_oracle.h -- FP64 CPU oracle for the batched Levenberg-Marquardt kinematic
+ * optimiser of "PyRoki: A Modular Toolkit for Robot Kinematic Optimization"
+ * (arXiv 2505.03728).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the parity authority for the CUDA
+ * path; only the test-suite, the smoke check and the benchmark's CPU-baseline
+ * leg may load it.  It shares no code, header, constant or helper with the
+ * CUDA library: every formula here is written out again from the paper
+ * (Sec. III-A solver, Sec. III-B variables, Sec. III-C costs, Eq. 1) and from
+ * textbook Lie-group identities.
+ *
+ * Conventions
+ *   - A rigid transform is 12 doubles, 3x4 row-major [R | t].
+ *   - A twist is [rho; omega] (translation part first).
+ *   - Joint types: 0 fixed, 1 revolute, 2 prismatic.  Joint j's parent is
+ *     parent[j] < j (or -1 for the base).  Movable joints own one variable
+ *     each, numbered in joint order ("dof index").
+ *   - Target kinds: 0 full pose (6 residual rows), 1 position only (3 rows).
+ */
+#ifndef PK_ORACLE_H
+#define PK_ORACLE_H
+#include <stdint.h>
+
+#define OR_JOINT_FIXED 0
+#define OR_JOINT_REVOLUTE 1
+#define OR_JOINT_PRISMATIC 2
+#define OR_TARGET_POSE 0
+#define OR_TARGET_POSITION 1
+
+/* per-problem status codes */
+#define OR_P_CONVERGED 0
+#define OR_P_MAX_ITERS 1
+#define OR_P_NONFINITE 2
+
+typedef struct {
+  int32_t n_joints;
+  const int32_t* parent; /* [n_joints] */
+  const int32_t* type;   /* [n_joints] */
+  const double* axis;    /* [n_joints][3] unit vector, joint frame */
+  const double* origin;  /* [n_joints][12] parent frame -> joint frame */
+  const double* lower;   /* [n_joints] (ignored for fixed joints) */
+  const double* upper;   /* [n_joints] */
+} or_robot;
+
+typedef struct {
+  double w_pos, w_rot;     /* pose residual weights (translation / rotation rows) */
+  double w_limit, w_rest;  /* joint-limit hinge weight, rest-pose weight */
+  double lambda0, lambda_min, lambda_max, nu;
+  double tol_pos, tol_rot; /* success thresholds: metres, radians */
+  int32_t max_iters;
+  int32_t early_exit;      /* 1: stop once the tolerances are met */
+} or_ik_params;
+
+typedef struct {
+  int32_t n_targets;       /* k */
+  const int32_t* links;    /* [k] joint frame each target constrains */
+  const int32_t* kinds;    /* [k] OR_TARGET_* (NULL = all pose) */
+} or_target_spec;
+
+int32_t or_n_dof(const or_robot* rb);
+int32_t or_n_residuals(const or_robot* rb, const or_target_spec* ts);
+
+/* FK of every joint frame: T_out[n_joints][12] (base <- joint j after motion). */
+void or_fk(const or_robot* rb, const double* q, double* T_out);
+
+/* SE(3) / SO(3) helpers (exported for the pins). */
+void or_se3_log(const double* T, double* xi);
+void or_se3_exp(const double* xi, double* T);
+void or_se3_jl(const double* xi, double* J);     /* 6x6 row-major left Jacobian */
+void or_se3_jlinv(const double* xi, double* J);  /* 6x6 row-major inverse */
+
+/* IK residual r[m] and analytic Jacobian J[m][n_dof] (J may be NULL). */
+void or_ik_residual(const or_robot* rb, const or_ik_params* p, const or_target_spec* ts,
+                    const double* targets, const double* q, double* r, double* J);
+
+/* pose errors: max over targets of |p - p*| and of the rotation angle */
+void or_ik_errors(const or_robot* rb, const or_target_spec* ts, const double* targets,
+                  const double* q, double* pos_err, double* rot_err);
+
+/* Cholesky solve of the SPD system A x = b (n x n row-major). Returns 0 on success. */
+int32_t or_cholesky_solve(int32_t n, const double* A, const double* b, double* x);
+
+/*
+ * Multi-start LM over batch targets x n_seeds seeds.
+ *   targets [batch][k][12], seeds [batch][n_seeds][n_dof]
+ *   q_out [batch][n_dof] best seed (converged first, then lowest cost, then lowest index)
+ *   err_out [batch][2], iters_out [batch], status_out [batch]
+ *   per_problem (optional, [batch*n_seeds][n_dof + 5]): q, cost, pos_err, rot_err,
+ *       iters, status of every seed.
+ *   trace (optional, [batch*n_seeds][n_trace][n_dof]): q after iteration 1..n_trace.
+ *   margin (optional, [batch*n_seeds]): min over the first n_trace iterations of
+ *       |f_trial - f| / f, used to flag accept/reject near-ties.
+ * n_threads <= 0 uses every online core.  Returns the number of threads used.
+ */
+int32_t or_ik_solve(const or_robot* rb, const or_ik_params* p, const or_target_spec* ts,
+                    int32_t batch, int32_t n_seeds, const double* targets, const double* seeds,
+                    double* q_out, double* err_out, int32_t* iters_out, int32_t* status_out,
+                    double* per_problem, int32_t n_trace, double* trace, double* margin,
+                    int32_t n_threads);
+
+#endif

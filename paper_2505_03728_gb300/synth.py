@@ -1,0 +1,185 @@
+"""Seeded synthetic inputs shared by the CUDA path, the tests and the benchmark.
+
+This module draws random numbers and lays them out; it holds none of the
+optimiser's arithmetic (no kinematics, no residuals, no solves).  Target poses
+are *not* produced here: callers turn the drawn target configurations into
+poses with their own forward kinematics (the CUDA path with ``pk_fk``, the
+tests with the CPU oracle).
+
+Generator: NumPy's PCG64 (``numpy.random.default_rng(seed)``).
+
+Robots (Sec. III-B variables; workload shapes of the throughput IK, uneven
+batch, learned-seed and trajectory workloads):
+  * serial chains: joint axes are normalised Gaussian 3-vectors, each origin is
+    a pure translation whose direction is uniform on the sphere and whose
+    length is uniform in [0.05, 0.4] m, limits +-2.8 rad, and a fixed tool
+    frame appended after the last joint (drawn like a link origin);
+  * a 24-DoF hand-like tree (3-joint wrist, fingers of 5, 4, 4, 4, 4 joints,
+    one fixed fingertip frame per finger);
+  * a 30-joint humanoid-like tree (3-joint torso, two 7-joint arms, two 6-joint
+    legs, a 1-joint head, fixed end frames on hands, feet and head).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+JOINT_FIXED, JOINT_REVOLUTE, JOINT_PRISMATIC = 0, 1, 2
+TARGET_POSE, TARGET_POSITION = 0, 1
+
+EYE12 = np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], dtype=np.float64)
+
+
+def _unit(rng, n):
+    v = rng.standard_normal((n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def _translation_origin(rng, lo=0.05, hi=0.4):
+    o = EYE12.copy()
+    d = _unit(rng, 1)[0] * rng.uniform(lo, hi)
+    o[3], o[7], o[11] = d
+    return o
+
+
+class RobotSpec(dict):
+    """parent, type, axis [n][3], origin [n][12], lower, upper, plus a name."""
+
+    @property
+    def n_joints(self):
+        return len(self["parent"])
+
+    @property
+    def n_dof(self):
+        return int(np.sum(np.asarray(self["type"]) != JOINT_FIXED))
+
+    @property
+    def dof_lower(self):
+        t = np.asarray(self["type"])
+        return np.asarray(self["lower"])[t != JOINT_FIXED]
+
+    @property
+    def dof_upper(self):
+        t = np.asarray(self["type"])
+        return np.asarray(self["upper"])[t != JOINT_FIXED]
+
+
+def _finish(name, parent, types, axis, origin, lower, upper):
+    return RobotSpec(name=name, parent=np.asarray(parent, np.int32), type=np.asarray(types, np.int32),
+                     axis=np.asarray(axis, np.float64).reshape(-1, 3),
+                     origin=np.asarray(origin, np.float64).reshape(-1, 12),
+                     lower=np.asarray(lower, np.float64), upper=np.asarray(upper, np.float64))
+
+
+def chain_robot(seed: int = 100, n_dof: int = 7, limit: float = 2.8, tool: bool = True,
+                prismatic: tuple = ()) -> RobotSpec:
+    """Serial chain of ``n_dof`` joints (revolute unless listed in ``prismatic``)."""
+    rng = np.random.default_rng(seed)
+    n = n_dof + (1 if tool else 0)
+    parent = np.arange(n) - 1
+    types, axis, origin, lower, upper = [], [], [], [], []
+    ax = _unit(rng, n_dof)
+    for j in range(n_dof):
+        pri = j in prismatic
+        types.append(JOINT_PRISMATIC if pri else JOINT_REVOLUTE)
+        axis.append(ax[j])
+        origin.append(_translation_origin(rng))
+        lim = 0.5 if pri else limit
+        lower.append(-lim)
+        upper.append(lim)
+    if tool:
+        types.append(JOINT_FIXED)
+        axis.append([0.0, 0.0, 1.0])
+        origin.append(_translation_origin(rng))
+        lower.append(0.0)
+        upper.append(0.0)
+    return _finish(f"chain{n_dof}", parent, types, axis, origin, lower, upper)
+
+
+def _add_branch(rng, parent_of_first, n_joints, parent, types, axis, origin, lower, upper,
+                limit, tip=True):
+    prev = parent_of_first
+    ax = _unit(rng, n_joints)
+    for j in range(n_joints):
+        parent.append(prev)
+        types.append(JOINT_REVOLUTE)
+        axis.append(ax[j])
+        origin.append(_translation_origin(rng, 0.02, 0.12) if limit < 2 else _translation_origin(rng))
+        lower.append(-limit)
+        upper.append(limit)
+        prev = len(parent) - 1
+    if tip:
+        parent.append(prev)
+        types.append(JOINT_FIXED)
+        axis.append([0.0, 0.0, 1.0])
+        origin.append(_translation_origin(rng, 0.02, 0.05) if limit < 2 else _translation_origin(rng))
+        lower.append(0.0)
+        upper.append(0.0)
+        return len(parent) - 1
+    return prev
+
+
+def hand_robot(seed: int = 102) -> tuple[RobotSpec, np.ndarray]:
+    """24-DoF hand-like tree; returns (robot, fingertip frame indices [5])."""
+    rng = np.random.default_rng(seed)
+    parent, types, axis, origin, lower, upper = [], [], [], [], [], []
+    wrist = _add_branch(rng, -1, 3, parent, types, axis, origin, lower, upper, 1.5, tip=False)
+    tips = []
+    for nf in (5, 4, 4, 4, 4):
+        tips.append(_add_branch(rng, wrist, nf, parent, types, axis, origin, lower, upper, 1.5))
+    return _finish("hand24", parent, types, axis, origin, lower, upper), np.asarray(tips, np.int32)
+
+
+def humanoid_robot(seed: int = 103) -> tuple[RobotSpec, np.ndarray]:
+    """30-joint humanoid-like tree; returns (robot, end frames [6]:
+    left hand, right hand, left foot, right foot, head, torso)."""
+    rng = np.random.default_rng(seed)
+    parent, types, axis, origin, lower, upper = [], [], [], [], [], []
+    torso = _add_branch(rng, -1, 3, parent, types, axis, origin, lower, upper, 1.0, tip=False)
+    ends = []
+    for n in (7, 7):
+        ends.append(_add_branch(rng, torso, n, parent, types, axis, origin, lower, upper, 2.5))
+    for n in (6, 6):
+        ends.append(_add_branch(rng, -1, n, parent, types, axis, origin, lower, upper, 2.0))
+    ends.append(_add_branch(rng, torso, 1, parent, types, axis, origin, lower, upper, 1.0))
+    ends.append(torso)
+    return _finish("humanoid30", parent, types, axis, origin, lower, upper), np.asarray(ends, np.int32)
+
+
+def uniform_q(seed: int, shape, lower, upper) -> np.ndarray:
+    """Joint configurations uniform in [lower, upper]: shape + (n_dof,)."""
+    rng = np.random.default_rng(seed)
+    lower = np.asarray(lower, np.float64)
+    upper = np.asarray(upper, np.float64)
+    if isinstance(shape, int):
+        shape = (shape,)
+    u = rng.random(tuple(shape) + (lower.shape[0],))
+    return lower + (upper - lower) * u
+
+
+def batch_sizes(seed: int, count: int, lo: int = 1, hi: int = 4096) -> np.ndarray:
+    """Per-robot batch sizes drawn uniformly from {lo..hi}."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(lo, hi + 1, size=count)
+
+
+def sphere_obstacles(seed: int, count: int, reach: float, r_lo=0.05, r_hi=0.2) -> np.ndarray:
+    """Obstacle spheres [count][4] (x, y, z, radius), centres uniform in a ball of
+    radius ``reach`` above the ground plane z = -0.15."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((count, 4))
+    i = 0
+    while i < count:
+        c = rng.uniform(-reach, reach, 3)
+        if np.linalg.norm(c) > reach or c[2] < 0.0:
+            continue
+        out[i, :3] = c
+        out[i, 3] = rng.uniform(r_lo, r_hi)
+        i += 1
+    return out
+
+
+def link_spheres(seed: int, n_dof: int, per_link: int = 4, r_lo=0.03, r_hi=0.08) -> np.ndarray:
+    """Sphere radii [n_dof][per_link]; centres are placed by the callers along
+    each link's child-origin vector."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(r_lo, r_hi, size=(n_dof, per_link))
