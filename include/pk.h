@@ -1,0 +1,198 @@
+/*
+ * pk.h -- C ABI of libpk, the GB300 (sm_103a) batched kinematic optimiser.
+ *
+ * The library solves many independent robot-kinematics least-squares problems
+ * with Levenberg-Marquardt (LM), following "PyRoki: A Modular Toolkit for
+ * Robot Kinematic Optimization" (arXiv 2505.03728):
+ *   - variables: one joint configuration q per problem, forward kinematics
+ *     T_base<-i = FK(q)_i over fixed, revolute and prismatic joints (Sec. III-B);
+ *   - costs, each weighted (Sec. III-C): joint pose cost
+ *     log(T_target^-1 T_base<-i) in R^6 ordered [rho; omega], joint limit cost
+ *     max(0, q - q_upper) + max(0, q_lower - q), joint regularisation
+ *     q - q_rest with q_rest the middle of the limits;
+ *   - solver: LM on the sum of squared residuals with analytic Jacobians
+ *     (Sec. III-A and Sec. V-C): (J^T J + lambda I) dq = -J^T r, a trial step is
+ *     kept iff it strictly lowers the cost; lambda /= nu on acceptance and
+ *     lambda *= nu on rejection, clamped to [lambda_min, lambda_max].
+ *
+ * Conventions shared by every entry point
+ *   - Transforms are 12 floats, 3x4 row-major [R | t]; lengths in metres,
+ *     angles in radians.
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; all other
+ *     pointers are host pointers, read during the call only.
+ *   - Every call that takes a stream only enqueues work on it (cudaStream_t,
+ *     NULL = the legacy default stream) and returns without synchronising.
+ *     Argument errors are detected on the host and returned synchronously,
+ *     with nothing enqueued.  Per-problem numerical trouble is reported in the
+ *     per-problem status output, never by a trap.
+ *   - No C++ exception crosses this interface.  pk_last_error() returns a
+ *     thread-local description of the last non-PK_OK status.
+ *   - Robot handles are immutable after creation and may be used from several
+ *     threads and streams at once.
+ */
+#ifndef PK_H
+#define PK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PK_OK = 0,
+  PK_ERR_INVALID_ARG = 1,
+  PK_ERR_CUDA = 2,
+  PK_ERR_OOM = 3,
+  PK_ERR_TIMEOUT = 4,
+  PK_ERR_UNSUPPORTED = 5
+} pk_status;
+
+typedef enum { PK_JOINT_FIXED = 0, PK_JOINT_REVOLUTE = 1, PK_JOINT_PRISMATIC = 2 } pk_joint_type;
+
+/* Pose targets give 6 residual rows, position targets 3 (world-frame
+ * difference of the frame origin), Sec. III-C joint pose cost. */
+typedef enum { PK_TARGET_POSE = 0, PK_TARGET_POSITION = 1 } pk_target_kind;
+
+/* Per-problem status codes written by the solvers. */
+enum {
+  PK_P_CONVERGED = 0, /* final pose within tol_pos / tol_rot for every target */
+  PK_P_MAX_ITERS = 1, /* iteration cap reached without meeting the tolerances */
+  PK_P_NONFINITE = 2, /* the cost at the seed was not finite (e.g. NaN target) */
+  PK_P_CANCELLED = 3  /* stopped because a sibling seed of the same target converged */
+};
+
+typedef struct pk_robot pk_robot;
+
+/* LM settings.  Weights multiply residuals (the cost is 1/2 sum r^2). */
+typedef struct {
+  float w_pos;           /* translation rows of the pose residual (default 1)   */
+  float w_rot;           /* rotation rows of the pose residual (default 0.5)    */
+  float w_limit;         /* joint-limit hinge (default 10)                      */
+  float w_rest;          /* rest-pose regularisation (default 1e-3)             */
+  float lambda0;         /* initial damping (default 1e-2)                      */
+  float lambda_min;      /* default 1e-10                                       */
+  float lambda_max;      /* default 1e10                                        */
+  float nu;              /* damping factor, > 1 (default 2)                     */
+  float tol_pos;         /* success threshold, metres (default 1e-3)            */
+  float tol_rot;         /* success threshold, radians (default 0.5 deg)        */
+  int32_t max_iters;     /* LM iterations per seed; a rejected step counts      */
+  int32_t early_exit;    /* 1: a seed stops as soon as it meets the tolerances  */
+  int32_t cancel_siblings; /* 1: all seeds of a target stop once one converged  */
+  int32_t reserved;      /* must be 0                                           */
+} pk_ik_params;
+
+/* Fills *p with the defaults listed above (max_iters 50, early_exit 1,
+ * cancel_siblings 0). */
+void pk_ik_params_default(pk_ik_params* p);
+
+/*
+ * pk_robot_create -- kinematic tree (Sec. III-B: fixed, revolute and prismatic
+ * joints; T_j = T_parent(j) * origin_j * X_j(q_j)).
+ *   n_joints  1..64
+ *   parent    [n_joints], parent[j] in [-1, j-1]; -1 = attached to the base
+ *   type      [n_joints], pk_joint_type
+ *   axis      [n_joints][3], joint axis in the joint frame (normalised here;
+ *             must be non-zero for movable joints)
+ *   origin    [n_joints][12], parent frame -> joint frame before motion
+ *             (rotation part must be orthonormal to 1e-4)
+ *   lower, upper [n_joints], limits of movable joints (lower <= upper);
+ *             ignored for fixed joints
+ *   tool      [12] or NULL: when given, appended as one more fixed joint
+ *             whose parent is joint n_joints-1
+ * Movable joints own one variable each, numbered in joint order.
+ * All pointers are host pointers, copied.  Returns PK_ERR_INVALID_ARG on a
+ * malformed tree, PK_ERR_CUDA / PK_ERR_OOM if the device copy fails.
+ */
+pk_status pk_robot_create(int32_t n_joints, const int32_t* parent, const int32_t* type,
+                          const float* axis, const float* origin, const float* lower,
+                          const float* upper, const float* tool, pk_robot** out);
+void pk_robot_destroy(pk_robot* robot);
+int32_t pk_robot_n_joints(const pk_robot* robot);
+int32_t pk_robot_n_dof(const pk_robot* robot);
+
+/*
+ * pk_fk -- forward kinematics of every joint frame (Sec. III-B).
+ *   d_q      [batch][n_dof]
+ *   d_T_out  [batch][n_joints][12]
+ */
+pk_status pk_fk(const pk_robot* robot, int32_t batch, const float* d_q, float* d_T_out,
+                void* stream);
+
+/*
+ * pk_ik_residual -- weighted residual vector and analytic Jacobian at given
+ * configurations (Sec. III-C costs; the Jacobian of the pose rows is
+ * Jl^-1(r) Ad(T_target^-1) xi_j for every movable ancestor j).
+ * Supported: serial chains with one target on the last frame (k = 1), n_dof <= 8.
+ *   d_targets [batch][k][12], d_q [batch][n_dof]
+ *   d_r_out   [batch][m], m = 6 (or 3) + 2 n_dof, rows: pose, limit, rest
+ *   d_J_out   [batch][m][n_dof] row-major, or NULL
+ */
+pk_status pk_ik_residual(const pk_robot* robot, const pk_ik_params* params, int32_t k,
+                         const int32_t* target_links, const int32_t* target_kinds, int32_t batch,
+                         const float* d_targets, const float* d_q, float* d_r_out, float* d_J_out,
+                         void* stream);
+
+/*
+ * Scratch that pk_ik_solve needs for (batch, n_seeds): a work-queue head, one
+ * cancellation flag per target and one result record per seed.
+ */
+size_t pk_ik_workspace_bytes(const pk_robot* robot, int32_t batch, int32_t n_seeds);
+
+/*
+ * pk_ik_solve -- multi-start LM inverse kinematics (Sec. III-A, Sec. IV-A).
+ * Each target is solved from n_seeds seeds independently; the returned seed is
+ * the best one: converged first, then lowest cost, then lowest seed index.
+ *   k, target_links, target_kinds  host [k]; kinds may be NULL (all pose)
+ *   d_targets  [batch][k][12]
+ *   d_seeds    [batch][n_seeds][n_dof]
+ *   d_q_out    [batch][n_dof]     best seed's final configuration
+ *   d_err_out  [batch][2]         its position error (m) and rotation error (rad),
+ *                                 max over targets
+ *   d_iters_out [batch]           its LM iteration count
+ *   d_status_out [batch]          its PK_P_* status
+ *   d_workspace, workspace_bytes  caller scratch of at least
+ *                                 pk_ik_workspace_bytes() bytes, 256-byte aligned;
+ *                                 NULL makes the call allocate it stream-ordered
+ *                                 (cudaMallocAsync / cudaFreeAsync).
+ * batch == 0 is a no-op.  The workspace must not be shared by calls that can
+ * overlap on the GPU.
+ * Supported: serial chains with one target on the last frame, n_dof <= 8
+ * (PK_ERR_UNSUPPORTED otherwise).
+ */
+pk_status pk_ik_solve(const pk_robot* robot, const pk_ik_params* params, int32_t k,
+                      const int32_t* target_links, const int32_t* target_kinds, int32_t batch,
+                      int32_t n_seeds, const float* d_targets, const float* d_seeds,
+                      float* d_q_out, float* d_err_out, int32_t* d_iters_out,
+                      int32_t* d_status_out, void* d_workspace, size_t workspace_bytes,
+                      void* stream);
+
+/*
+ * Work counters of the last pk_ik_solve that ran with this caller workspace
+ * (read back with a synchronous copy, so call it after the solve has been
+ * enqueued; it waits for the device).  stats_out (host, [4]):
+ *   [0] candidate evaluations (FK + residuals + cost, seeds included)
+ *   [1] normal-equation builds (Jacobian, J^T J, J^T r)
+ *   [2] damped solves (Cholesky + triangular solves)
+ *   [3] problems finished
+ */
+pk_status pk_ik_workspace_stats(const void* d_workspace, int64_t* stats_out);
+
+/*
+ * Kernel timing trace.  While enabled, every solver kernel launch is bracketed
+ * by CUDA events recorded on its own stream.  pk_trace_enable() clears the
+ * trace.  pk_trace_summary() waits for the recorded events and returns the
+ * summed duration (ms) and the count of traced launches of one kernel family:
+ * "ik_lm" (fused LM kernel), "ik_reduce" (best-seed reduction).
+ */
+pk_status pk_trace_enable(int32_t enable);
+pk_status pk_trace_summary(const char* kernel, double* total_ms, int64_t* launches);
+
+/* Thread-local message for the last failing call on this thread ("" if none). */
+const char* pk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PK_H */

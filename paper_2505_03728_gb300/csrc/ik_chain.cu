@@ -1,0 +1,565 @@
+// ik_chain.cu -- fused Levenberg-Marquardt IK for serial chains, one thread per
+// (target, seed) problem, persistent grid with a lane-refilling work queue.
+//
+// One LM iteration of one problem (Sec. III-A solver, Sec. III-C costs):
+//   FK of the candidate q_c expressed in the target frame (T_target^-1 * FK),
+//   pose residual log(E) (Sec. III-C joint pose cost), joint-limit hinge and
+//   rest-pose rows, cost 1/2 sum r^2;  accept iff the cost strictly drops
+//   (lambda /= nu) else reject (lambda *= nu);  on acceptance the analytic
+//   Jacobian Jl^-1(log E) Ad(T_target^-1) xi_j and the packed normal matrix
+//   J^T J and gradient J^T r are rebuilt;  (J^T J + lambda I) dq = -J^T r is
+//   solved by a register-resident Cholesky and q_c = q + dq.
+// A rejected step keeps J^T J and J^T r, so only the damping changes and no
+// kinematics is redone.  Each lane owns one problem; when it finishes (tolerance
+// met with early exit, iteration cap, or a converged sibling seed) it writes a
+// result record and claims the next problem index from a warp-aggregated
+// atomic queue, so early exits do not leave lanes idle.  A second kernel picks
+// the best seed of every target.
+#include "pk_internal.h"
+#include "pk_math.cuh"
+
+namespace pk {
+
+constexpr int kLmThreads = 128;
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int N>
+struct ChainC {
+  float o_r[N][9];
+  float o_t[N][3];
+  float a[N][3];
+  float tool_r[9], tool_t[3];
+  float lo[N], hi[N], mid[N];
+  uint32_t prism, orot, toolrot;
+};
+
+template <int N>
+static ChainC<N> chain_const(const ChainHost& h) {
+  ChainC<N> c;
+  for (int j = 0; j < N; ++j) {
+    for (int i = 0; i < 9; ++i) c.o_r[j][i] = h.o_r[j][i];
+    for (int i = 0; i < 3; ++i) {
+      c.o_t[j][i] = h.o_t[j][i];
+      c.a[j][i] = h.a[j][i];
+    }
+    c.lo[j] = h.lo[j];
+    c.hi[j] = h.hi[j];
+    c.mid[j] = 0.5f * (h.lo[j] + h.hi[j]);
+  }
+  for (int i = 0; i < 9; ++i) c.tool_r[i] = h.tool_r[i];
+  for (int i = 0; i < 3; ++i) c.tool_t[i] = h.tool_t[i];
+  c.prism = h.prism;
+  c.orot = h.orot;
+  c.toolrot = h.toolrot;
+  return c;
+}
+
+template <int N>
+struct Frames {
+  float u[N][3];  // joint axis, target frame
+  float p[N][3];  // joint origin, target frame
+};
+
+// FK of q expressed in the frame Ti (= T_target^-1, or a pure translation by
+// -p_target for position targets), the target-frame residual xi (unweighted:
+// log(E) for pose targets, E.t for position targets), the errors and the cost.
+template <int N>
+__device__ __forceinline__ void chain_eval(const ChainC<N>& rc, const LmParams& lp, const Rt& Ti,
+                                           const float* q, Frames<N>& fr, float* xi, float& th,
+                                           float& pe, float& f) {
+  Rt T = Ti;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if (rc.orot & (1u << j)) {
+      Rt O;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) O.r[i] = rc.o_r[j][i];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) O.t[i] = rc.o_t[j][i];
+      rt_mul(T, O, T);
+    } else {
+      rt_translate(T, rc.o_t[j]);
+    }
+    mat_vec(T.r, rc.a[j], fr.u[j]);
+    fr.p[j][0] = T.t[0];
+    fr.p[j][1] = T.t[1];
+    fr.p[j][2] = T.t[2];
+    if (rc.prism & (1u << j)) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) T.t[i] = fmaf(fr.u[j][i], q[j], T.t[i]);
+    } else {
+      float s, c;
+      sincos_rad(q[j], &s, &c);
+      rot_joint(T.r, fr.u[j], rc.a[j], s, c);
+    }
+  }
+  if (rc.toolrot) {
+    Rt O;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) O.r[i] = rc.tool_r[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) O.t[i] = rc.tool_t[i];
+    rt_mul(T, O, T);
+  } else {
+    rt_translate(T, rc.tool_t);
+  }
+  pe = sqrtf(fmaf(T.t[0], T.t[0], fmaf(T.t[1], T.t[1], T.t[2] * T.t[2])));
+  float acc;
+  if (!lp.pos_only) {
+    th = se3_log(T, xi);
+    const float a = lp.w_pos * lp.w_pos, b = lp.w_rot * lp.w_rot;
+    acc = a * (xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]) +
+          b * (xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5]);
+  } else {
+    th = 0.f;
+    xi[0] = T.t[0]; xi[1] = T.t[1]; xi[2] = T.t[2];
+    xi[3] = xi[4] = xi[5] = 0.f;
+    acc = lp.w_pos * lp.w_pos * (pe * pe);
+  }
+  const float wl2 = lp.w_limit * lp.w_limit, wr2 = lp.w_rest * lp.w_rest;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const float h = fmaxf(0.f, q[j] - rc.hi[j]) + fmaxf(0.f, rc.lo[j] - q[j]);
+    const float d = q[j] - rc.mid[j];
+    acc = fmaf(wl2, h * h, fmaf(wr2, d * d, acc));
+  }
+  f = 0.5f * acc;
+}
+
+// Weighted pose (or position) rows of the Jacobian, J[6][N], and the weighted
+// residual rw[6] (zero rows 3..5 for position targets).
+template <int N>
+__device__ __forceinline__ void chain_pose_jac(const ChainC<N>& rc, const LmParams& lp,
+                                               const Frames<N>& fr, const float* xi, float th,
+                                               float (&J)[6][N], float* rw) {
+  if (!lp.pos_only) {
+    float A[9], B[9];
+    se3_jlinv_blocks(xi, xi + 3, th, A, B);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      float top[3], bot[3];
+      if (rc.prism & (1u << j)) {
+        mat_vec(A, fr.u[j], top);
+        bot[0] = bot[1] = bot[2] = 0.f;
+      } else {
+        float v[3], t1[3], t2[3];
+        cross3(fr.p[j], fr.u[j], v);  // revolute twist [p x w; w]
+        mat_vec(A, v, t1);
+        mat_vec(B, fr.u[j], t2);
+        mat_vec(A, fr.u[j], bot);
+        top[0] = t1[0] + t2[0];
+        top[1] = t1[1] + t2[1];
+        top[2] = t1[2] + t2[2];
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        J[i][j] = lp.w_pos * top[i];
+        J[3 + i][j] = lp.w_rot * bot[i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      rw[i] = lp.w_pos * xi[i];
+      rw[3 + i] = lp.w_rot * xi[3 + i];
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      float col[3];
+      if (rc.prism & (1u << j)) {
+        col[0] = fr.u[j][0]; col[1] = fr.u[j][1]; col[2] = fr.u[j][2];
+      } else {
+        float d[3] = {xi[0] - fr.p[j][0], xi[1] - fr.p[j][1], xi[2] - fr.p[j][2]};
+        cross3(fr.u[j], d, col);
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        J[i][j] = lp.w_pos * col[i];
+        J[3 + i][j] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      rw[i] = lp.w_pos * xi[i];
+      rw[3 + i] = 0.f;
+    }
+  }
+}
+
+// Packed J^T J (lower) and J^T r including the limit and rest rows.
+template <int N>
+__device__ __forceinline__ void chain_normal(const ChainC<N>& rc, const LmParams& lp,
+                                             const Frames<N>& fr, const float* xi, float th,
+                                             const float* q, float* A, float* g) {
+  float J[6][N], rw[6];
+  chain_pose_jac<N>(rc, lp, fr, xi, th, J, rw);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < 6; ++r) s = fmaf(J[r][i], J[r][j], s);
+      A[tri(i, j)] = s;
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) s = fmaf(J[r][i], rw[r], s);
+    g[i] = s;
+  }
+  const float wl2 = lp.w_limit * lp.w_limit, wr2 = lp.w_rest * lp.w_rest;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    float h = 0.f, d = 0.f;
+    if (q[j] > rc.hi[j]) { h = q[j] - rc.hi[j]; d = 1.f; }
+    if (q[j] < rc.lo[j]) { h = rc.lo[j] - q[j]; d = -1.f; }
+    A[tri(j, j)] += wl2 * d * d + wr2;
+    g[j] = fmaf(wl2 * d, h, fmaf(wr2, q[j] - rc.mid[j], g[j]));
+  }
+}
+
+__device__ __forceinline__ void load_target_frame(const float* __restrict__ tp, bool pos_only,
+                                                  Rt& Ti) {
+  const float4* p4 = reinterpret_cast<const float4*>(tp);
+  const float4 a = __ldg(p4), b = __ldg(p4 + 1), c = __ldg(p4 + 2);
+  Rt Tt;
+  Tt.r[0] = a.x; Tt.r[1] = a.y; Tt.r[2] = a.z; Tt.t[0] = a.w;
+  Tt.r[3] = b.x; Tt.r[4] = b.y; Tt.r[5] = b.z; Tt.t[1] = b.w;
+  Tt.r[6] = c.x; Tt.r[7] = c.y; Tt.r[8] = c.z; Tt.t[2] = c.w;
+  if (pos_only) {
+    rt_identity(Ti);
+    Ti.t[0] = -Tt.t[0]; Ti.t[1] = -Tt.t[1]; Ti.t[2] = -Tt.t[2];
+  } else {
+    rt_inv(Tt, Ti);
+  }
+}
+
+int ik_rec_stride(int n_dof) { return ((n_dof + 3) & ~3) + 4; }
+
+template <int N>
+__global__ void __launch_bounds__(kLmThreads) chain_lm_kernel(
+    const __grid_constant__ ChainC<N> rc, const __grid_constant__ LmParams lp,
+    const float* __restrict__ targets, const float* __restrict__ seeds, int n_seeds, int P,
+    IkWorkspace ws) {
+  constexpr int NT = N * (N + 1) / 2;
+  constexpr int NP = ((N + 3) & ~3);
+  constexpr int STRIDE = NP + 4;
+  const int lane = threadIdx.x & 31;
+  int prob = -1;
+  bool need = true, exhausted = false, fresh = false;
+  Rt Ti;
+  float q[N], qc[N], A0[NT], g[N];
+  float f = 0.f, lam = 0.f, pe_a = 0.f, re_a = 0.f;
+  int it = 0;
+  unsigned n_eval = 0, n_build = 0, n_solve = 0, n_done = 0;  // work counters
+#pragma unroll
+  for (int j = 0; j < N; ++j) { q[j] = qc[j] = g[j] = 0.f; }
+#pragma unroll
+  for (int j = 0; j < NT; ++j) A0[j] = 0.f;
+
+  for (;;) {
+    // --- claim problems for the lanes that need one (warp-aggregated)
+    const bool want = need && !exhausted;
+    const unsigned nm = __ballot_sync(kFull, want);
+    if (nm) {
+      const int leader = __ffs(nm) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(ws.head, __popc(nm));
+      base = __shfl_sync(kFull, base, leader);
+      if (want) {
+        prob = base + __popc(nm & ((1u << lane) - 1u));
+        if (prob >= P) {
+          exhausted = true;
+        } else {
+          load_target_frame(targets + (size_t)(prob / n_seeds) * 12, lp.pos_only != 0, Ti);
+          const float* sp = seeds + (size_t)prob * N;
+#pragma unroll
+          for (int j = 0; j < N; ++j) qc[j] = __ldg(sp + j);
+          fresh = true;
+          it = 0;
+          lam = lp.lambda0;
+        }
+      }
+    }
+    need = false;
+    const bool active = !exhausted;
+    if (!__any_sync(kFull, active)) break;
+    if (!active) continue;
+
+    const int tgt = prob / n_seeds;
+    int cancelled = 0;
+    if (lp.cancel) cancelled = __ldcg(ws.flags + tgt);
+
+    // --- evaluate the candidate
+    Frames<N> fr;
+    float xi[6], th, pe, fc;
+    chain_eval<N>(rc, lp, Ti, qc, fr, xi, th, pe, fc);
+    ++n_eval;
+
+    bool acc, done = false;
+    int status = PK_P_MAX_ITERS;
+    if (fresh) {
+      acc = true;
+      if (!isfinite(fc)) { done = true; status = PK_P_NONFINITE; }
+    } else {
+      acc = fc < f;
+      ++it;
+    }
+    if (acc) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) q[j] = qc[j];
+      f = fc;
+      pe_a = pe;
+      re_a = th;
+      if (!fresh) lam = fmaxf(lam / lp.nu, lp.lambda_min);
+    } else {
+      lam = fminf(lam * lp.nu, lp.lambda_max);
+    }
+    const bool conv = pe_a <= lp.tol_pos && re_a <= lp.tol_rot;
+    if (!done) {
+      if (lp.early_exit && conv) { done = true; status = PK_P_CONVERGED; }
+      else if (it >= lp.max_iters) { done = true; status = conv ? PK_P_CONVERGED : PK_P_MAX_ITERS; }
+      else if (cancelled) { done = true; status = PK_P_CANCELLED; }
+    }
+    fresh = false;
+
+    if (!done) {
+      // --- damped normal equations and the next candidate
+      if (acc) {
+        chain_normal<N>(rc, lp, fr, xi, th, q, A0, g);
+        ++n_build;
+      }
+      ++n_solve;
+      float L[NT], d[N];
+#pragma unroll
+      for (int j = 0; j < NT; ++j) L[j] = A0[j];
+#pragma unroll
+      for (int j = 0; j < N; ++j) { L[tri(j, j)] += lam; d[j] = -g[j]; }
+      const bool ok = chol_packed<N>(L);
+      chol_solve_packed<N>(L, d);
+#pragma unroll
+      for (int j = 0; j < N; ++j) qc[j] = ok ? q[j] + d[j] : q[j];
+    } else {
+      float* r = ws.rec + (size_t)prob * STRIDE;
+#pragma unroll
+      for (int j = 0; j < N; ++j) r[j] = q[j];
+      r[NP + 0] = f;
+      r[NP + 1] = pe_a;
+      r[NP + 2] = re_a;
+      r[NP + 3] = __int_as_float((status << 24) | it);
+      if (lp.cancel && status == PK_P_CONVERGED) __stcg(ws.flags + tgt, 1);
+      ++n_done;
+      need = true;
+    }
+  }
+  // one atomic per warp and counter
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n_eval += __shfl_xor_sync(kFull, n_eval, o);
+    n_build += __shfl_xor_sync(kFull, n_build, o);
+    n_solve += __shfl_xor_sync(kFull, n_solve, o);
+    n_done += __shfl_xor_sync(kFull, n_done, o);
+  }
+  if (lane == 0) {
+    atomicAdd(ws.stats + 0, (unsigned long long)n_eval);
+    atomicAdd(ws.stats + 1, (unsigned long long)n_build);
+    atomicAdd(ws.stats + 2, (unsigned long long)n_solve);
+    atomicAdd(ws.stats + 3, (unsigned long long)n_done);
+  }
+}
+
+// Best seed per target: converged first, then lowest cost, then lowest index.
+__global__ void ik_reduce_kernel(const float* __restrict__ rec, int n, int stride, int batch,
+                                 int n_seeds, float* __restrict__ q_out, float* __restrict__ err_out,
+                                 int32_t* __restrict__ iters_out, int32_t* __restrict__ status_out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  const int np = stride - 4;
+  int best = 0, best_c = -1;
+  float best_f = 0.f;
+  for (int s = 0; s < n_seeds; ++s) {
+    const float* r = rec + ((size_t)b * n_seeds + s) * stride;
+    const int meta = __float_as_int(r[np + 3]);
+    const int c = ((meta >> 24) == PK_P_CONVERGED) ? 1 : 0;
+    float fv = r[np];
+    if (!isfinite(fv)) fv = INFINITY;
+    if (best_c < 0 || c > best_c || (c == best_c && fv < best_f)) {
+      best = s;
+      best_c = c;
+      best_f = fv;
+    }
+  }
+  const float* r = rec + ((size_t)b * n_seeds + best) * stride;
+  for (int j = 0; j < n; ++j) q_out[(size_t)b * n + j] = r[j];
+  err_out[2 * (size_t)b] = r[np + 1];
+  err_out[2 * (size_t)b + 1] = r[np + 2];
+  const int meta = __float_as_int(r[np + 3]);
+  iters_out[b] = meta & 0xffffff;
+  status_out[b] = meta >> 24;
+}
+
+template <int N>
+__global__ void chain_residual_kernel(const __grid_constant__ ChainC<N> rc,
+                                      const __grid_constant__ LmParams lp,
+                                      const float* __restrict__ targets,
+                                      const float* __restrict__ qs, int batch,
+                                      float* __restrict__ r_out, float* __restrict__ J_out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  Rt Ti;
+  load_target_frame(targets + (size_t)b * 12, lp.pos_only != 0, Ti);
+  float q[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) q[j] = qs[(size_t)b * N + j];
+  Frames<N> fr;
+  float xi[6], th, pe, f;
+  chain_eval<N>(rc, lp, Ti, q, fr, xi, th, pe, f);
+  float J[6][N], rw[6];
+  chain_pose_jac<N>(rc, lp, fr, xi, th, J, rw);
+  const int rows = lp.pos_only ? 3 : 6;
+  const int m = rows + 2 * N;
+  float* r = r_out + (size_t)b * m;
+  for (int i = 0; i < rows; ++i) r[i] = rw[i];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const float h = fmaxf(0.f, q[j] - rc.hi[j]) + fmaxf(0.f, rc.lo[j] - q[j]);
+    r[rows + j] = lp.w_limit * h;
+    r[rows + N + j] = lp.w_rest * (q[j] - rc.mid[j]);
+  }
+  if (!J_out) return;
+  float* Jo = J_out + (size_t)b * m * N;
+  for (int i = 0; i < m * N; ++i) Jo[i] = 0.f;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    if (i < rows)
+#pragma unroll
+      for (int j = 0; j < N; ++j) Jo[i * N + j] = J[i][j];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    float d = 0.f;
+    if (q[j] > rc.hi[j]) d = 1.f;
+    if (q[j] < rc.lo[j]) d = -1.f;
+    Jo[(rows + j) * N + j] = lp.w_limit * d;
+    Jo[(rows + N + j) * N + j] = lp.w_rest;
+  }
+}
+
+// Generic tree FK, one thread per configuration; parents' frames are re-read
+// from the output rows this thread already wrote.
+__global__ void fk_kernel(const RobotDev* __restrict__ rb, int nj, int nd, int batch,
+                          const float* __restrict__ qs, float* __restrict__ T_out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  float* out = T_out + (size_t)b * nj * 12;
+  for (int j = 0; j < nj; ++j) {
+    Rt O, X, L;
+    rt_load(rb->origin[j], O);
+    rt_identity(X);
+    const int t = rb->type[j];
+    if (t != PK_JOINT_FIXED) {
+      const float qv = qs[(size_t)b * nd + rb->var[j]];
+      const float* a = rb->axis[j];
+      if (t == PK_JOINT_REVOLUTE) {
+        float u[3] = {a[0], a[1], a[2]}, s, c;
+        sincos_rad(qv, &s, &c);
+        rot_joint(X.r, u, a, s, c);
+      } else {
+        X.t[0] = a[0] * qv; X.t[1] = a[1] * qv; X.t[2] = a[2] * qv;
+      }
+    }
+    rt_mul(O, X, L);
+    const int p = rb->parent[j];
+    if (p >= 0) {
+      Rt Tp;
+      rt_load(out + p * 12, Tp);
+      rt_mul(Tp, L, L);
+    }
+    rt_store(out + j * 12, L);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+
+static int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+template <int N>
+static cudaError_t chain_lm_launch(const ChainHost& ch, const LmParams& lp, const float* d_targets,
+                                   const float* d_seeds, int batch, int n_seeds, IkWorkspace ws,
+                                   float* d_q, float* d_err, int32_t* d_iters, int32_t* d_status,
+                                   cudaStream_t stream) {
+  static int blocks_per_sm = 0;
+  if (blocks_per_sm == 0) {
+    int b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, chain_lm_kernel<N>, kLmThreads, 0);
+    if (e != cudaSuccess) return e;
+    blocks_per_sm = b > 0 ? b : 1;
+  }
+  const long P = (long)batch * n_seeds;
+  long grid = (long)blocks_per_sm * sm_count();
+  const long need = (P + kLmThreads - 1) / kLmThreads;
+  if (grid > need) grid = need;
+  const ChainC<N> rc = chain_const<N>(ch);
+  {
+    TraceScope tr("ik_lm", stream);
+    chain_lm_kernel<N><<<(unsigned)grid, kLmThreads, 0, stream>>>(rc, lp, d_targets, d_seeds, n_seeds,
+                                                                  (int)P, ws);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  {
+    TraceScope tr("ik_reduce", stream);
+    ik_reduce_kernel<<<(batch + 127) / 128, 128, 0, stream>>>(ws.rec, N, ik_rec_stride(N), batch,
+                                                              n_seeds, d_q, d_err, d_iters, d_status);
+  }
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t chain_res_launch(const ChainHost& ch, const LmParams& lp, const float* d_targets,
+                                    const float* d_q, int batch, float* d_r, float* d_J,
+                                    cudaStream_t stream) {
+  const ChainC<N> rc = chain_const<N>(ch);
+  chain_residual_kernel<N><<<(batch + 127) / 128, 128, 0, stream>>>(rc, lp, d_targets, d_q, batch, d_r, d_J);
+  return cudaGetLastError();
+}
+
+#define PK_CHAIN_DISPATCH(FN, ...)         \
+  switch (ch.n) {                          \
+    case 1: return FN<1>(__VA_ARGS__);     \
+    case 2: return FN<2>(__VA_ARGS__);     \
+    case 3: return FN<3>(__VA_ARGS__);     \
+    case 4: return FN<4>(__VA_ARGS__);     \
+    case 5: return FN<5>(__VA_ARGS__);     \
+    case 6: return FN<6>(__VA_ARGS__);     \
+    case 7: return FN<7>(__VA_ARGS__);     \
+    case 8: return FN<8>(__VA_ARGS__);     \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t launch_chain_lm(const ChainHost& ch, const LmParams& lp, const float* d_targets,
+                            const float* d_seeds, int batch, int n_seeds, IkWorkspace ws,
+                            float* d_q, float* d_err, int32_t* d_iters, int32_t* d_status,
+                            cudaStream_t stream) {
+  PK_CHAIN_DISPATCH(chain_lm_launch, ch, lp, d_targets, d_seeds, batch, n_seeds, ws, d_q, d_err,
+                    d_iters, d_status, stream)
+}
+
+cudaError_t launch_chain_residual(const ChainHost& ch, const LmParams& lp, const float* d_targets,
+                                  const float* d_q, int batch, float* d_r, float* d_J,
+                                  cudaStream_t stream) {
+  PK_CHAIN_DISPATCH(chain_res_launch, ch, lp, d_targets, d_q, batch, d_r, d_J, stream)
+}
+
+cudaError_t launch_fk(const RobotDev* d_robot, int n_joints, int n_dof, int batch, const float* d_q,
+                      float* d_T, cudaStream_t stream) {
+  fk_kernel<<<(batch + 127) / 128, 128, 0, stream>>>(d_robot, n_joints, n_dof, batch, d_q, d_T);
+  return cudaGetLastError();
+}
+
+}  // namespace pk

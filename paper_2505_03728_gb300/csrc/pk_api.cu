@@ -1,0 +1,472 @@
+// pk_api.cu -- the C ABI of libpk: argument checking, robot handles, scratch
+// layout and kernel dispatch.  No C++ exception leaves this file.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+
+#include "pk_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+pk_status fail(pk_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+pk_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? PK_ERR_OOM : PK_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+bool finite_all(const float* p, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!isfinite(p[i])) return false;
+  return true;
+}
+
+bool rotation_ok(const float* T) {
+  // T is 3x4 row-major; check R^T R = I to 1e-4
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double s = 0;
+      for (int i = 0; i < 3; ++i) s += (double)T[i * 4 + a] * T[i * 4 + b];
+      if (fabs(s - (a == b ? 1.0 : 0.0)) > 1e-4) return false;
+    }
+  return true;
+}
+
+bool is_identity_rot(const float* r9) {
+  for (int i = 0; i < 9; ++i)
+    if (r9[i] != ((i % 4 == 0) ? 1.f : 0.f)) return false;
+  return true;
+}
+
+// 3x4 row-major compose: C = A * B (double accumulation for the host folds).
+void compose(const float* A, const float* B, float* C) {
+  float o[12];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += (double)A[i * 4 + k] * B[k * 4 + j];
+      o[i * 4 + j] = (float)s;
+    }
+    double t = A[i * 4 + 3];
+    for (int k = 0; k < 3; ++k) t += (double)A[i * 4 + k] * B[k * 4 + 3];
+    o[i * 4 + 3] = (float)t;
+  }
+  memcpy(C, o, sizeof o);
+}
+
+pk_status check_params(const pk_ik_params* p) {
+  if (!p) return fail(PK_ERR_INVALID_ARG, "params is NULL");
+  if (!(p->nu > 1.f) || !isfinite(p->nu)) return fail(PK_ERR_INVALID_ARG, "nu must be > 1");
+  if (!(p->lambda0 > 0.f) || !(p->lambda_min > 0.f) || !(p->lambda_max >= p->lambda_min))
+    return fail(PK_ERR_INVALID_ARG, "lambda0, lambda_min must be > 0 and lambda_max >= lambda_min");
+  if (p->max_iters < 0) return fail(PK_ERR_INVALID_ARG, "max_iters must be >= 0");
+  if (!(p->w_pos >= 0.f) || !(p->w_rot >= 0.f) || !(p->w_limit >= 0.f) || !(p->w_rest >= 0.f))
+    return fail(PK_ERR_INVALID_ARG, "weights must be >= 0");
+  if (!(p->tol_pos >= 0.f) || !(p->tol_rot >= 0.f))
+    return fail(PK_ERR_INVALID_ARG, "tolerances must be >= 0");
+  if (p->reserved != 0) return fail(PK_ERR_INVALID_ARG, "reserved must be 0");
+  return PK_OK;
+}
+
+pk::LmParams lm_params(const pk_ik_params* p, bool pos_only) {
+  pk::LmParams l;
+  l.w_pos = p->w_pos; l.w_rot = p->w_rot; l.w_limit = p->w_limit; l.w_rest = p->w_rest;
+  l.lambda0 = p->lambda0; l.lambda_min = p->lambda_min; l.lambda_max = p->lambda_max; l.nu = p->nu;
+  l.tol_pos = p->tol_pos; l.tol_rot = pos_only ? INFINITY : p->tol_rot;
+  l.max_iters = p->max_iters; l.early_exit = p->early_exit != 0; l.cancel = p->cancel_siblings != 0;
+  l.pos_only = pos_only;
+  return l;
+}
+
+// Fold a serial chain ending at frame `link` into the kernel's canonical form.
+pk_status fold_chain(const pk_robot* rb, int link, pk::ChainHost* ch) {
+  for (int j = 0; j < rb->n_joints; ++j)
+    if (rb->parent[j] != j - 1)
+      return fail(PK_ERR_UNSUPPORTED, "the fused IK kernel needs a serial chain (parent[j] == j-1)");
+  for (int j = link + 1; j < rb->n_joints; ++j)
+    if (rb->type[j] != PK_JOINT_FIXED)
+      return fail(PK_ERR_UNSUPPORTED, "the target must be on or after the last movable joint");
+  if (rb->n_dof < 1 || rb->n_dof > pk::kMaxChainDof)
+    return fail(PK_ERR_UNSUPPORTED, "serial-chain IK supports 1..%d movable joints (got %d)",
+                pk::kMaxChainDof, rb->n_dof);
+  memset(ch, 0, sizeof *ch);
+  float pend[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+  int v = 0;
+  for (int j = 0; j <= link; ++j) {
+    float o[12];
+    compose(pend, &rb->origin[12 * j], o);
+    if (rb->type[j] == PK_JOINT_FIXED) {
+      memcpy(pend, o, sizeof o);
+      continue;
+    }
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 3; ++c) ch->o_r[v][r * 3 + c] = o[r * 4 + c];
+      ch->o_t[v][r] = o[r * 4 + 3];
+      ch->a[v][r] = rb->axis[3 * j + r];
+    }
+    if (!is_identity_rot(ch->o_r[v])) ch->orot |= 1u << v;
+    if (rb->type[j] == PK_JOINT_PRISMATIC) ch->prism |= 1u << v;
+    ch->lo[v] = rb->lower[j];
+    ch->hi[v] = rb->upper[j];
+    ++v;
+    const float I[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+    memcpy(pend, I, sizeof I);
+  }
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) ch->tool_r[r * 3 + c] = pend[r * 4 + c];
+    ch->tool_t[r] = pend[r * 4 + 3];
+  }
+  ch->toolrot = is_identity_rot(ch->tool_r) ? 0u : 1u;
+  ch->n = v;
+  return PK_OK;
+}
+
+pk_status check_targets(const pk_robot* rb, int32_t k, const int32_t* links, const int32_t* kinds,
+                        bool* pos_only) {
+  if (k < 1) return fail(PK_ERR_INVALID_ARG, "k must be >= 1");
+  if (!links) return fail(PK_ERR_INVALID_ARG, "target_links is NULL");
+  for (int i = 0; i < k; ++i) {
+    if (links[i] < 0 || links[i] >= rb->n_joints)
+      return fail(PK_ERR_INVALID_ARG, "target_links[%d] = %d out of range", i, links[i]);
+    if (kinds && kinds[i] != PK_TARGET_POSE && kinds[i] != PK_TARGET_POSITION)
+      return fail(PK_ERR_INVALID_ARG, "target_kinds[%d] = %d invalid", i, kinds[i]);
+  }
+  if (k != 1) return fail(PK_ERR_UNSUPPORTED, "serial-chain IK takes one target (k = 1)");
+  *pos_only = kinds && kinds[0] == PK_TARGET_POSITION;
+  return PK_OK;
+}
+
+}  // namespace
+
+namespace pk {
+
+size_t ik_workspace_bytes(int n_dof, long batch, long n_seeds) {
+  const size_t head = 256;
+  const size_t flags = (((size_t)batch * 4) + 255) & ~(size_t)255;
+  const size_t rec = (size_t)batch * n_seeds * ik_rec_stride(n_dof) * sizeof(float);
+  return head + flags + ((rec + 255) & ~(size_t)255);
+}
+
+void ik_workspace_carve(void* base, int n_dof, long batch, long n_seeds, IkWorkspace* ws,
+                        size_t* zero_bytes) {
+  char* p = (char*)base;
+  const size_t flags = (((size_t)batch * 4) + 255) & ~(size_t)255;
+  ws->stats = (unsigned long long*)p;
+  ws->head = (int32_t*)(p + 64);
+  ws->flags = (int32_t*)(p + 256);
+  ws->rec = (float*)(p + 256 + flags);
+  *zero_bytes = 256 + flags;
+  (void)n_dof;
+  (void)n_seeds;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel timing trace: a pool of event pairs, one per traced launch.
+
+namespace {
+struct TraceRec {
+  std::string name;
+  cudaEvent_t start, stop;
+};
+std::mutex g_trace_mu;
+bool g_trace_on = false;
+std::vector<TraceRec*> g_trace;  // recorded launches
+std::vector<TraceRec*> g_trace_free;
+}  // namespace
+
+TraceScope::TraceScope(const char* name, cudaStream_t s) : slot(nullptr), stream(s) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  if (!g_trace_on) return;
+  TraceRec* r = nullptr;
+  if (!g_trace_free.empty()) {
+    r = g_trace_free.back();
+    g_trace_free.pop_back();
+  } else {
+    r = new (std::nothrow) TraceRec;
+    if (!r) return;
+    if (cudaEventCreate(&r->start) != cudaSuccess || cudaEventCreate(&r->stop) != cudaSuccess) {
+      delete r;
+      return;
+    }
+  }
+  r->name = name;
+  cudaEventRecord(r->start, s);
+  slot = r;
+}
+
+TraceScope::~TraceScope() {
+  if (!slot) return;
+  TraceRec* r = (TraceRec*)slot;
+  cudaEventRecord(r->stop, stream);
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  g_trace.push_back(r);
+}
+
+}  // namespace pk
+
+extern "C" {
+
+pk_status pk_trace_enable(int32_t enable) {
+  std::lock_guard<std::mutex> lk(pk::g_trace_mu);
+  for (auto* r : pk::g_trace) pk::g_trace_free.push_back(r);
+  pk::g_trace.clear();
+  pk::g_trace_on = enable != 0;
+  return PK_OK;
+}
+
+pk_status pk_trace_summary(const char* kernel, double* total_ms, int64_t* launches) {
+  if (!kernel || !total_ms || !launches) return fail(PK_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(pk::g_trace_mu);
+  double ms = 0;
+  int64_t n = 0;
+  for (auto* r : pk::g_trace) {
+    if (r->name != kernel) continue;
+    cudaError_t e = cudaEventSynchronize(r->stop);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r->start, r->stop);
+    if (e != cudaSuccess) return cuda_fail(e, "pk_trace_summary");
+    ms += t;
+    ++n;
+  }
+  *total_ms = ms;
+  *launches = n;
+  return PK_OK;
+}
+
+pk_status pk_ik_workspace_stats(const void* d_workspace, int64_t* stats_out) {
+  if (!d_workspace || !stats_out) return fail(PK_ERR_INVALID_ARG, "NULL argument");
+  unsigned long long h[4];
+  cudaError_t e = cudaMemcpy(h, d_workspace, sizeof h, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "pk_ik_workspace_stats");
+  for (int i = 0; i < 4; ++i) stats_out[i] = (int64_t)h[i];
+  return PK_OK;
+}
+
+
+void pk_ik_params_default(pk_ik_params* p) {
+  if (!p) return;
+  p->w_pos = 1.f;
+  p->w_rot = 0.5f;
+  p->w_limit = 10.f;
+  p->w_rest = 1e-3f;
+  p->lambda0 = 1e-2f;
+  p->lambda_min = 1e-10f;
+  p->lambda_max = 1e10f;
+  p->nu = 2.f;
+  p->tol_pos = 1e-3f;
+  p->tol_rot = 0.5f * 3.14159265358979f / 180.f;
+  p->max_iters = 50;
+  p->early_exit = 1;
+  p->cancel_siblings = 0;
+  p->reserved = 0;
+}
+
+const char* pk_last_error(void) { return g_last_error.c_str(); }
+
+pk_status pk_robot_create(int32_t n_joints, const int32_t* parent, const int32_t* type,
+                          const float* axis, const float* origin, const float* lower,
+                          const float* upper, const float* tool, pk_robot** out) {
+  if (!out) return fail(PK_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  const int total = n_joints + (tool ? 1 : 0);
+  if (n_joints < 1 || total > pk::kMaxJoints)
+    return fail(PK_ERR_INVALID_ARG, "n_joints must be in 1..%d (including the tool)", pk::kMaxJoints);
+  if (!parent || !type || !axis || !origin || !lower || !upper)
+    return fail(PK_ERR_INVALID_ARG, "NULL robot array");
+  pk_robot* rb = new (std::nothrow) pk_robot;
+  if (!rb) return fail(PK_ERR_OOM, "host allocation failed");
+  rb->n_joints = total;
+  rb->parent.resize(total);
+  rb->type.resize(total);
+  rb->var.resize(total);
+  rb->axis.resize(3 * total);
+  rb->origin.resize(12 * total);
+  rb->lower.resize(total);
+  rb->upper.resize(total);
+  int nd = 0;
+  for (int j = 0; j < total; ++j) {
+    const bool is_tool = j == n_joints;
+    const int32_t pj = is_tool ? n_joints - 1 : parent[j];
+    const int32_t tj = is_tool ? PK_JOINT_FIXED : type[j];
+    const float* o = is_tool ? tool : origin + 12 * j;
+    if (pj < -1 || pj >= j) {
+      delete rb;
+      return fail(PK_ERR_INVALID_ARG, "parent[%d] = %d must be in [-1, %d]", j, pj, j - 1);
+    }
+    if (tj != PK_JOINT_FIXED && tj != PK_JOINT_REVOLUTE && tj != PK_JOINT_PRISMATIC) {
+      delete rb;
+      return fail(PK_ERR_INVALID_ARG, "type[%d] = %d invalid", j, tj);
+    }
+    if (!finite_all(o, 12) || !rotation_ok(o)) {
+      delete rb;
+      return fail(PK_ERR_INVALID_ARG, "origin of joint %d is not a finite rigid transform", j);
+    }
+    rb->parent[j] = pj;
+    rb->type[j] = tj;
+    memcpy(&rb->origin[12 * j], o, 12 * sizeof(float));
+    float a[3] = {0.f, 0.f, 1.f};
+    float lo = 0.f, hi = 0.f;
+    if (tj != PK_JOINT_FIXED) {
+      if (!finite_all(axis + 3 * j, 3)) {
+        delete rb;
+        return fail(PK_ERR_INVALID_ARG, "axis of joint %d is not finite", j);
+      }
+      const double n = sqrt((double)axis[3 * j] * axis[3 * j] + (double)axis[3 * j + 1] * axis[3 * j + 1] +
+                            (double)axis[3 * j + 2] * axis[3 * j + 2]);
+      if (!(n > 1e-9)) {
+        delete rb;
+        return fail(PK_ERR_INVALID_ARG, "axis of movable joint %d is zero", j);
+      }
+      for (int i = 0; i < 3; ++i) a[i] = (float)(axis[3 * j + i] / n);
+      lo = lower[j];
+      hi = upper[j];
+      if (!(lo <= hi) || !isfinite(lo) || !isfinite(hi)) {
+        delete rb;
+        return fail(PK_ERR_INVALID_ARG, "limits of joint %d invalid (need finite lower <= upper)", j);
+      }
+      rb->var[j] = nd++;
+    } else {
+      rb->var[j] = -1;
+    }
+    memcpy(&rb->axis[3 * j], a, sizeof a);
+    rb->lower[j] = lo;
+    rb->upper[j] = hi;
+  }
+  rb->n_dof = nd;
+
+  pk::RobotDev h;
+  memset(&h, 0, sizeof h);
+  h.n_joints = total;
+  h.n_dof = nd;
+  for (int j = 0; j < total; ++j) {
+    h.parent[j] = rb->parent[j];
+    h.type[j] = rb->type[j];
+    h.var[j] = rb->var[j];
+    memcpy(h.axis[j], &rb->axis[3 * j], 3 * sizeof(float));
+    memcpy(h.origin[j], &rb->origin[12 * j], 12 * sizeof(float));
+    h.lower[j] = rb->lower[j];
+    h.upper[j] = rb->upper[j];
+  }
+  cudaGetDevice(&rb->device);
+  cudaError_t e = cudaMalloc(&rb->d_blob, sizeof h);
+  if (e != cudaSuccess) {
+    delete rb;
+    return cuda_fail(e, "cudaMalloc(robot)");
+  }
+  e = cudaMemcpy(rb->d_blob, &h, sizeof h, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(rb->d_blob);
+    delete rb;
+    return cuda_fail(e, "cudaMemcpy(robot)");
+  }
+  *out = rb;
+  return PK_OK;
+}
+
+void pk_robot_destroy(pk_robot* rb) {
+  if (!rb) return;
+  if (rb->d_blob) cudaFree(rb->d_blob);
+  delete rb;
+}
+
+int32_t pk_robot_n_joints(const pk_robot* rb) { return rb ? rb->n_joints : -1; }
+int32_t pk_robot_n_dof(const pk_robot* rb) { return rb ? rb->n_dof : -1; }
+
+pk_status pk_fk(const pk_robot* rb, int32_t batch, const float* d_q, float* d_T_out, void* stream) {
+  if (!rb) return fail(PK_ERR_INVALID_ARG, "robot is NULL");
+  if (batch < 0) return fail(PK_ERR_INVALID_ARG, "batch must be >= 0");
+  if (batch == 0) return PK_OK;
+  if (!d_q || !d_T_out) return fail(PK_ERR_INVALID_ARG, "NULL device buffer");
+  cudaError_t e = pk::launch_fk((const pk::RobotDev*)rb->d_blob, rb->n_joints, rb->n_dof, batch, d_q,
+                                d_T_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? PK_OK : cuda_fail(e, "pk_fk launch");
+}
+
+pk_status pk_ik_residual(const pk_robot* rb, const pk_ik_params* params, int32_t k,
+                         const int32_t* target_links, const int32_t* target_kinds, int32_t batch,
+                         const float* d_targets, const float* d_q, float* d_r_out, float* d_J_out,
+                         void* stream) {
+  if (!rb) return fail(PK_ERR_INVALID_ARG, "robot is NULL");
+  pk_status s = check_params(params);
+  if (s != PK_OK) return s;
+  bool pos_only = false;
+  if ((s = check_targets(rb, k, target_links, target_kinds, &pos_only)) != PK_OK) return s;
+  if (batch < 0) return fail(PK_ERR_INVALID_ARG, "batch must be >= 0");
+  pk::ChainHost ch;
+  if ((s = fold_chain(rb, target_links[0], &ch)) != PK_OK) return s;
+  if (batch == 0) return PK_OK;
+  if (!d_targets || !d_q || !d_r_out) return fail(PK_ERR_INVALID_ARG, "NULL device buffer");
+  if (((uintptr_t)d_targets & 15) != 0) return fail(PK_ERR_INVALID_ARG, "d_targets must be 16-byte aligned");
+  cudaError_t e = pk::launch_chain_residual(ch, lm_params(params, pos_only), d_targets, d_q, batch,
+                                            d_r_out, d_J_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? PK_OK : cuda_fail(e, "pk_ik_residual launch");
+}
+
+size_t pk_ik_workspace_bytes(const pk_robot* rb, int32_t batch, int32_t n_seeds) {
+  if (!rb || batch < 0 || n_seeds < 1) return 0;
+  return pk::ik_workspace_bytes(rb->n_dof, batch, n_seeds);
+}
+
+pk_status pk_ik_solve(const pk_robot* rb, const pk_ik_params* params, int32_t k,
+                      const int32_t* target_links, const int32_t* target_kinds, int32_t batch,
+                      int32_t n_seeds, const float* d_targets, const float* d_seeds,
+                      float* d_q_out, float* d_err_out, int32_t* d_iters_out,
+                      int32_t* d_status_out, void* d_workspace, size_t workspace_bytes,
+                      void* stream) {
+  if (!rb) return fail(PK_ERR_INVALID_ARG, "robot is NULL");
+  pk_status s = check_params(params);
+  if (s != PK_OK) return s;
+  bool pos_only = false;
+  if ((s = check_targets(rb, k, target_links, target_kinds, &pos_only)) != PK_OK) return s;
+  if (batch < 0) return fail(PK_ERR_INVALID_ARG, "batch must be >= 0");
+  if (n_seeds < 1) return fail(PK_ERR_INVALID_ARG, "n_seeds must be >= 1");
+  if ((long long)batch * n_seeds > 0x7fffff00LL)
+    return fail(PK_ERR_INVALID_ARG, "batch * n_seeds exceeds 2^31");
+  pk::ChainHost ch;
+  if ((s = fold_chain(rb, target_links[0], &ch)) != PK_OK) return s;
+  if (batch == 0) return PK_OK;
+  if (!d_targets || !d_seeds || !d_q_out || !d_err_out || !d_iters_out || !d_status_out)
+    return fail(PK_ERR_INVALID_ARG, "NULL device buffer");
+  if (((uintptr_t)d_targets & 15) != 0) return fail(PK_ERR_INVALID_ARG, "d_targets must be 16-byte aligned");
+  const size_t need = pk::ik_workspace_bytes(rb->n_dof, batch, n_seeds);
+  cudaStream_t st = (cudaStream_t)stream;
+  void* ws_base = d_workspace;
+  bool owned = false;
+  if (ws_base) {
+    if (workspace_bytes < need)
+      return fail(PK_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
+    if (((uintptr_t)ws_base & 255) != 0) return fail(PK_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  } else {
+    cudaError_t e = cudaMallocAsync(&ws_base, need, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(workspace)");
+    owned = true;
+  }
+  pk::IkWorkspace ws;
+  size_t zero_bytes = 0;
+  pk::ik_workspace_carve(ws_base, rb->n_dof, batch, n_seeds, &ws, &zero_bytes);
+  cudaError_t e = cudaMemsetAsync(ws_base, 0, zero_bytes, st);
+  if (e == cudaSuccess)
+    e = pk::launch_chain_lm(ch, lm_params(params, pos_only), d_targets, d_seeds, batch, n_seeds, ws,
+                            d_q_out, d_err_out, d_iters_out, d_status_out, st);
+  if (owned) {
+    cudaError_t e2 = cudaFreeAsync(ws_base, st);
+    if (e == cudaSuccess) e = e2;
+  }
+  return e == cudaSuccess ? PK_OK : cuda_fail(e, "pk_ik_solve launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// pk_internal.h -- host-side types shared by the libpk translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pk.h"
+
+struct pk_robot {
+  int32_t n_joints = 0, n_dof = 0;
+  std::vector<int32_t> parent, type, var;  // var[j]: variable index or -1
+  std::vector<float> axis, origin, lower, upper;
+  // Device copy for the generic (tree) kernels, see RobotDev.
+  void* d_blob = nullptr;
+  int device = 0;
+};
+
+namespace pk {
+
+constexpr int kMaxJoints = 64;
+constexpr int kMaxChainDof = 8;
+
+// Device-side robot layout (one contiguous allocation per robot handle).
+struct RobotDev {
+  int32_t n_joints, n_dof;
+  int32_t parent[kMaxJoints];
+  int32_t type[kMaxJoints];
+  int32_t var[kMaxJoints];
+  float axis[kMaxJoints][3];
+  float origin[kMaxJoints][12];
+  float lower[kMaxJoints], upper[kMaxJoints];
+};
+
+// Serial chain folded so that every fixed joint is merged into the next
+// movable joint's origin and the fixed joints after the last movable joint
+// form the tool transform.
+struct ChainHost {
+  int n;                      // movable joints
+  float o_r[kMaxChainDof][9];  // origin rotations
+  float o_t[kMaxChainDof][3];  // origin translations
+  float a[kMaxChainDof][3];    // axes (unit)
+  float tool_r[9], tool_t[3];
+  float lo[kMaxChainDof], hi[kMaxChainDof];
+  uint32_t prism, orot, toolrot;
+};
+
+// Device-ready LM settings.
+struct LmParams {
+  float w_pos, w_rot, w_limit, w_rest;
+  float lambda0, lambda_min, lambda_max, nu;
+  float tol_pos, tol_rot;
+  int32_t max_iters, early_exit, cancel, pos_only;
+};
+
+// Scratch layout of the IK solve.
+struct IkWorkspace {
+  unsigned long long* stats;  // [4] work counters (zeroed per call)
+  int32_t* head;   // work-queue head (1 int, zeroed per call)
+  int32_t* flags;  // [batch] converged-sibling flags (zeroed per call)
+  float* rec;      // [batch * n_seeds][rec_stride] per-seed results
+};
+
+size_t ik_workspace_bytes(int n_dof, long batch, long n_seeds);
+void ik_workspace_carve(void* base, int n_dof, long batch, long n_seeds, IkWorkspace* ws,
+                        size_t* zero_bytes);
+int ik_rec_stride(int n_dof);
+
+// Launchers (ik_chain.cu).  Return a cudaError_t from the launch.
+cudaError_t launch_chain_lm(const ChainHost& ch, const LmParams& lp, const float* d_targets,
+                            const float* d_seeds, int batch, int n_seeds, IkWorkspace ws,
+                            float* d_q, float* d_err, int32_t* d_iters, int32_t* d_status,
+                            cudaStream_t stream);
+cudaError_t launch_chain_residual(const ChainHost& ch, const LmParams& lp, const float* d_targets,
+                                  const float* d_q, int batch, float* d_r, float* d_J,
+                                  cudaStream_t stream);
+cudaError_t launch_fk(const RobotDev* d_robot, int n_joints, int n_dof, int batch, const float* d_q,
+                      float* d_T, cudaStream_t stream);
+
+// Kernel timing trace (pk_api.cu): brackets a launch with events when enabled.
+struct TraceScope {
+  TraceScope(const char* name, cudaStream_t s);
+  ~TraceScope();
+  void* slot;
+  cudaStream_t stream;
+};
+
+}  // namespace pk

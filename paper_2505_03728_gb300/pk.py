@@ -1,0 +1,246 @@
+"""Python binding of libpk (include/pk.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: it checks tensor devices, dtypes and shapes, passes
+``data_ptr()`` values and the current CUDA stream, and turns a non-PK_OK
+status into :class:`PkError`.  Device memory comes from PyTorch tensors.
+
+The CUDA library must have been built (``__graft_entry__.build()`` or
+``python -m paper_2505_03728_gb300.build``); importing a function that needs it
+raises immediately if ``libpk.so`` is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpk.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "pk.h")
+
+PK_OK, PK_ERR_INVALID_ARG, PK_ERR_CUDA, PK_ERR_OOM, PK_ERR_TIMEOUT, PK_ERR_UNSUPPORTED = range(6)
+PK_JOINT_FIXED, PK_JOINT_REVOLUTE, PK_JOINT_PRISMATIC = 0, 1, 2
+PK_TARGET_POSE, PK_TARGET_POSITION = 0, 1
+PK_P_CONVERGED, PK_P_MAX_ITERS, PK_P_NONFINITE, PK_P_CANCELLED = 0, 1, 2, 3
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PkError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"libpk status {status}: {message}")
+        self.status = status
+
+
+class pk_ik_params(C.Structure):
+    _fields_ = [("w_pos", C.c_float), ("w_rot", C.c_float), ("w_limit", C.c_float),
+                ("w_rest", C.c_float), ("lambda0", C.c_float), ("lambda_min", C.c_float),
+                ("lambda_max", C.c_float), ("nu", C.c_float), ("tol_pos", C.c_float),
+                ("tol_rot", C.c_float), ("max_iters", C.c_int32), ("early_exit", C.c_int32),
+                ("cancel_siblings", C.c_int32), ("reserved", C.c_int32)]
+
+
+_vp = C.c_void_p
+_i32 = C.c_int32
+_i32p = C.POINTER(C.c_int32)
+_f32p = C.POINTER(C.c_float)
+
+_SIGNATURES = {
+    "pk_ik_params_default": (None, [C.POINTER(pk_ik_params)]),
+    "pk_last_error": (C.c_char_p, []),
+    "pk_robot_create": (_i32, [_i32, _i32p, _i32p, _f32p, _f32p, _f32p, _f32p, _f32p, C.POINTER(_vp)]),
+    "pk_robot_destroy": (None, [_vp]),
+    "pk_robot_n_joints": (_i32, [_vp]),
+    "pk_robot_n_dof": (_i32, [_vp]),
+    "pk_fk": (_i32, [_vp, _i32, _vp, _vp, _vp]),
+    "pk_ik_residual": (_i32, [_vp, C.POINTER(pk_ik_params), _i32, _i32p, _i32p, _i32, _vp, _vp, _vp,
+                              _vp, _vp]),
+    "pk_ik_workspace_bytes": (C.c_size_t, [_vp, _i32, _i32]),
+    "pk_ik_solve": (_i32, [_vp, C.POINTER(pk_ik_params), _i32, _i32p, _i32p, _i32, _i32, _vp, _vp,
+                           _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "pk_ik_workspace_stats": (_i32, [_vp, C.POINTER(C.c_int64)]),
+    "pk_trace_enable": (_i32, [_i32]),
+    "pk_trace_summary": (_i32, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+}
+
+
+def lib():
+    """The loaded libpk.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                                   "(python -m paper_2505_03728_gb300.build)")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGNATURES.items():
+                if hasattr(L, name):
+                    fn = getattr(L, name)
+                    fn.restype = res
+                    fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of every function declared in include/pk.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pk_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(status):
+    if status != PK_OK:
+        raise PkError(status, pk_last_error())
+
+
+def pk_last_error() -> str:
+    return lib().pk_last_error().decode()
+
+
+def pk_ik_params_default(**overrides) -> pk_ik_params:
+    p = pk_ik_params()
+    lib().pk_ik_params_default(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype=torch.float32, name="tensor"):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+class Robot:
+    """Owns a pk_robot handle (pk_robot_create / pk_robot_destroy)."""
+
+    def __init__(self, parent, type, axis, origin, lower, upper, tool=None):
+        parent = np.ascontiguousarray(parent, np.int32)
+        type = np.ascontiguousarray(type, np.int32)
+        axis = np.ascontiguousarray(axis, np.float32).reshape(-1)
+        origin = np.ascontiguousarray(origin, np.float32).reshape(-1)
+        lower = np.ascontiguousarray(lower, np.float32)
+        upper = np.ascontiguousarray(upper, np.float32)
+        tool_p = None
+        if tool is not None:
+            tool = np.ascontiguousarray(tool, np.float32)
+            tool_p = tool.ctypes.data_as(_f32p)
+        h = C.c_void_p()
+        _check(lib().pk_robot_create(len(parent), parent.ctypes.data_as(_i32p),
+                                     type.ctypes.data_as(_i32p), axis.ctypes.data_as(_f32p),
+                                     origin.ctypes.data_as(_f32p), lower.ctypes.data_as(_f32p),
+                                     upper.ctypes.data_as(_f32p), tool_p, C.byref(h)))
+        self.handle = h
+        self.n_joints = lib().pk_robot_n_joints(h)
+        self.n_dof = lib().pk_robot_n_dof(h)
+
+    @classmethod
+    def from_spec(cls, spec):
+        return cls(spec["parent"], spec["type"], spec["axis"], spec["origin"], spec["lower"],
+                   spec["upper"])
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.pk_robot_destroy(h)
+            self.handle = None
+
+
+def _links(links, kinds):
+    links = np.ascontiguousarray(links, np.int32).reshape(-1)
+    kinds_a = None if kinds is None else np.ascontiguousarray(kinds, np.int32).reshape(-1)
+    return links, kinds_a, (None if kinds_a is None else kinds_a.ctypes.data_as(_i32p))
+
+
+def pk_fk(robot: Robot, q: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """All joint frames [B][n_joints][12] for configurations q [B][n_dof]."""
+    B = q.shape[0]
+    if q.shape != (B, robot.n_dof):
+        raise ValueError("q must be [batch][n_dof]")
+    if out is None:
+        out = torch.empty(B, robot.n_joints, 12, device=q.device, dtype=torch.float32)
+    _check(lib().pk_fk(robot.handle, B, _dev(q, name="q"), _dev(out, name="out"), _stream(stream)))
+    return out
+
+
+def pk_ik_residual(robot: Robot, params: pk_ik_params, links, kinds, targets: torch.Tensor,
+                   q: torch.Tensor, jacobian=True, stream=None):
+    """Weighted residuals [B][m] and Jacobian [B][m][n_dof] at q [B][n_dof]."""
+    links, kinds_a, kinds_p = _links(links, kinds)
+    B = q.shape[0]
+    rows = 3 if (kinds_a is not None and kinds_a[0] == PK_TARGET_POSITION) else 6
+    m = rows * len(links) + 2 * robot.n_dof
+    r = torch.empty(B, m, device=q.device, dtype=torch.float32)
+    J = torch.empty(B, m, robot.n_dof, device=q.device, dtype=torch.float32) if jacobian else None
+    _check(lib().pk_ik_residual(robot.handle, C.byref(params), len(links), links.ctypes.data_as(_i32p),
+                                kinds_p, B, _dev(targets, name="targets"), _dev(q, name="q"),
+                                _dev(r, name="r"), None if J is None else _dev(J, name="J"),
+                                _stream(stream)))
+    return (r, J) if jacobian else r
+
+
+def pk_ik_workspace_bytes(robot: Robot, batch: int, n_seeds: int) -> int:
+    return int(lib().pk_ik_workspace_bytes(robot.handle, batch, n_seeds))
+
+
+def pk_ik_solve(robot: Robot, params: pk_ik_params, links, kinds, targets: torch.Tensor,
+                seeds: torch.Tensor, workspace: torch.Tensor | None = None, out=None, stream=None):
+    """Multi-start LM IK.  targets [B][k][12], seeds [B][S][n_dof].
+
+    Returns (q [B][n_dof], err [B][2], iters [B], status [B]) as CUDA tensors.
+    """
+    links, kinds_a, kinds_p = _links(links, kinds)
+    B, S = seeds.shape[0], seeds.shape[1]
+    if seeds.shape != (B, S, robot.n_dof):
+        raise ValueError("seeds must be [batch][n_seeds][n_dof]")
+    if targets.shape != (B, len(links), 12):
+        raise ValueError("targets must be [batch][k][12]")
+    dev = seeds.device
+    if out is None:
+        out = (torch.empty(B, robot.n_dof, device=dev), torch.empty(B, 2, device=dev),
+               torch.empty(B, device=dev, dtype=torch.int32), torch.empty(B, device=dev, dtype=torch.int32))
+    q, err, iters, status = out
+    ws_p, ws_n = None, 0
+    if workspace is not None:
+        ws_p, ws_n = _dev(workspace, torch.uint8, "workspace"), workspace.numel()
+    _check(lib().pk_ik_solve(robot.handle, C.byref(params), len(links), links.ctypes.data_as(_i32p),
+                             kinds_p, B, S, _dev(targets, name="targets"), _dev(seeds, name="seeds"),
+                             _dev(q, name="q"), _dev(err, name="err"),
+                             _dev(iters, torch.int32, "iters"), _dev(status, torch.int32, "status"),
+                             ws_p, ws_n, _stream(stream)))
+    return q, err, iters, status
+
+
+def pk_ik_workspace_stats(workspace: torch.Tensor) -> dict:
+    """Work counters of the last solve that used ``workspace`` (synchronises)."""
+    out = (C.c_int64 * 4)()
+    _check(lib().pk_ik_workspace_stats(_dev(workspace, torch.uint8, "workspace"), out))
+    return dict(evals=out[0], builds=out[1], solves=out[2], problems=out[3])
+
+
+def pk_trace_enable(enable: bool = True):
+    _check(lib().pk_trace_enable(1 if enable else 0))
+
+
+def pk_trace_summary(kernel: str):
+    """(total ms, launches) of the traced launches of one kernel family."""
+    ms, n = C.c_double(), C.c_int64()
+    _check(lib().pk_trace_summary(kernel.encode(), C.byref(ms), C.byref(n)))
+    return ms.value, n.value

@@ -183,3 +183,22 @@ def link_spheres(seed: int, n_dof: int, per_link: int = 4, r_lo=0.03, r_hi=0.08)
     each link's child-origin vector."""
     rng = np.random.default_rng(seed)
     return rng.uniform(r_lo, r_hi, size=(n_dof, per_link))
+
+
+# Workload definitions (sizes and generator seeds) of the IK configurations.
+IK_PARITY = dict(name="ik7_parity_256x1", robot_seed=100, n_dof=7, batch=256, n_seeds=1,
+                 target_seed=200, seed_seed=300, max_iters=30, early_exit=0)
+IK_THROUGHPUT = dict(name="ik7_throughput_65536x8", robot_seed=100, n_dof=7, batch=65536, n_seeds=8,
+                     target_seed=201, seed_seed=301, max_iters=50, early_exit=1)
+
+
+def ik_workload(cfg: dict, batch: int | None = None):
+    """(robot spec, target configurations [B][n], seeds [B][S][n]) of an IK workload.
+    ``batch`` takes the first rows of the full workload."""
+    spec = chain_robot(cfg["robot_seed"], cfg["n_dof"])
+    B = cfg["batch"]
+    qt = uniform_q(cfg["target_seed"], B, spec.dof_lower, spec.dof_upper)
+    sd = uniform_q(cfg["seed_seed"], (B, cfg["n_seeds"]), spec.dof_lower, spec.dof_upper)
+    if batch is not None:
+        qt, sd = qt[:batch], sd[:batch]
+    return spec, qt, sd

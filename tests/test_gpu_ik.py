@@ -1,0 +1,273 @@
+"""GPU parity of the CUDA IK path (through the C ABI) against the FP64 oracle.
+
+Tolerances (FP32 GPU vs FP64 oracle):
+  * forward kinematics, residuals: 1e-5 (metres / radians);
+  * Jacobian: 2e-5 * max(1, |J|);
+  * LM iterates 1..5: max_j |dq_j| <= 1e-4 * max(1, |q_j|), excluding problems
+    whose accept/reject test is a near-tie (|f_trial - f| <= 1e-5 f in one of
+    the first five iterations), where FP32 may legitimately decide the other way;
+  * converged solutions: every GPU solution reported converged is re-checked in
+    FP64 by the oracle against the success thresholds.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2505_03728_gb300 import build, pk, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_POS, TOL_ROT = 1e-3, np.deg2rad(0.5)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    pk.lib()
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda").contiguous()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def pair(spec):
+    return pk.Robot.from_spec(spec), oracle.Robot.from_dict(spec)
+
+
+def oracle_params(p: pk.pk_ik_params):
+    return oracle.IkParams(w_pos=p.w_pos, w_rot=p.w_rot, w_limit=p.w_limit, w_rest=p.w_rest,
+                           lambda0=p.lambda0, lambda_min=p.lambda_min, lambda_max=p.lambda_max,
+                           nu=p.nu, tol_pos=p.tol_pos, tol_rot=p.tol_rot, max_iters=p.max_iters,
+                           early_exit=p.early_exit)
+
+
+def robots():
+    hand, _ = synth.hand_robot(102)
+    hum, _ = synth.humanoid_robot(103)
+    return [("chain7", synth.chain_robot(100, 7)), ("prismatic6", synth.chain_robot(9, 6, prismatic=(0, 3))),
+            ("hand24", hand), ("humanoid30", hum)]
+
+
+@pytest.mark.parametrize("name,spec", robots(), ids=[r[0] for r in robots()])
+def test_fk_parity(name, spec):
+    g, o = pair(spec)
+    q = synth.uniform_q(40, 333, o.dof_lower, o.dof_upper)
+    T = host(pk.pk_fk(g, dev(q)))
+    Tref = oracle.fk(o, q)
+    assert np.abs(T - Tref).max() <= 1e-5
+
+
+def _res_case(kind):
+    spec = synth.chain_robot(9, 6, prismatic=(0, 3)) if kind == "prismatic" else synth.chain_robot(100, 7)
+    kinds = [oracle.TARGET_POSITION] if kind == "position" else None
+    return spec, kinds
+
+
+@pytest.mark.parametrize("kind", ["pose", "prismatic", "position"])
+@pytest.mark.parametrize("regime", ["random", "near_solution"])
+def test_residual_and_jacobian_parity(kind, regime):
+    spec, kinds = _res_case(kind)
+    g, o = pair(spec)
+    ee = o.n_joints - 1
+    B = 301
+    qt = synth.uniform_q(41, B, o.dof_lower, o.dof_upper)
+    if regime == "random":
+        q = synth.uniform_q(42, B, o.dof_lower - 0.2, o.dof_upper + 0.2)  # some past the limits
+    else:
+        q = qt + np.random.default_rng(43).normal(0, 1e-3, qt.shape)
+    targets = oracle.fk(o, qt)[:, [ee]]
+    p = pk.pk_ik_params_default()
+    r, J = pk.pk_ik_residual(g, p, [ee], kinds, dev(targets), dev(q))
+    r, J = host(r), host(J)
+    op = oracle_params(p)
+    tg = oracle.Targets([ee], kinds)
+    for b in range(B):
+        rr, JJ = oracle.ik_residual(o, op, tg, targets[b], q[b])
+        assert np.abs(r[b] - rr).max() <= 1e-5, b
+        assert (np.abs(J[b] - JJ) / np.maximum(1.0, np.abs(JJ))).max() <= 2e-5, b
+
+
+def _solve(g, p, ee, targets, seeds, kinds=None, workspace=None):
+    return [host(x) for x in pk.pk_ik_solve(g, p, [ee], kinds, dev(targets), dev(seeds), workspace)]
+
+
+def _parity_setup(batch=None):
+    cfg = synth.IK_PARITY
+    spec, qt, sd = synth.ik_workload(cfg, batch)
+    g, o = pair(spec)
+    ee = o.n_joints - 1
+    targets = oracle.fk(o, qt)[:, [ee]]
+    return g, o, ee, targets, sd
+
+
+def test_first_five_iterates_match_oracle():
+    g, o, ee, targets, sd = _parity_setup()
+    B = targets.shape[0]
+    p = pk.pk_ik_params_default(max_iters=30, early_exit=0)
+    ref = oracle.ik_solve(o, oracle_params(p), oracle.Targets([ee]), targets, sd, n_trace=5)
+    tie = ref["margin"] <= 1e-5
+    worst = 0.0
+    for k in range(1, 6):
+        pk_ = pk.pk_ik_params_default(max_iters=k, early_exit=0)
+        q, err, iters, status = _solve(g, pk_, ee, targets, sd)
+        assert np.all(iters == k)
+        qr = ref["trace"][:, k - 1]
+        rel = (np.abs(q - qr) / np.maximum(1.0, np.abs(qr))).max(axis=1)
+        worst = max(worst, rel[~tie].max())
+        assert np.all(rel[~tie] <= 1e-4), (k, np.argsort(-rel)[:5], np.sort(rel)[-5:])
+    assert tie.sum() <= 0.05 * B
+    print(f"iterate parity: worst rel {worst:.2e}, near-ties excluded {int(tie.sum())}/{B}")
+
+
+def test_thirty_iterations_final_errors():
+    g, o, ee, targets, sd = _parity_setup()
+    p = pk.pk_ik_params_default(max_iters=30, early_exit=0)
+    q, err, iters, status = _solve(g, p, ee, targets, sd)
+    ref = oracle.ik_solve(o, oracle_params(p), oracle.Targets([ee]), targets, sd)
+    agree = (status == ref["status"]).mean()
+    assert agree >= 0.9
+    conv = status == pk.PK_P_CONVERGED
+    for b in np.nonzero(conv)[0]:
+        pe, re = oracle.ik_errors(o, oracle.Targets([ee]), targets[b], q[b])
+        assert pe <= TOL_POS * (1 + 1e-3) and re <= TOL_ROT * (1 + 1e-3)
+    # reported errors are the FP32 errors of the returned q
+    both = conv & (ref["status"] == 0)
+    print(f"status agreement {agree:.3f}; GPU converged {conv.mean():.3f}, oracle {np.mean(ref['status'] == 0):.3f}; "
+          f"median pos err GPU {np.median(err[both, 0]):.2e} oracle {np.median(ref['err'][both, 0]):.2e}")
+
+
+@pytest.mark.parametrize("cancel", [0, 1])
+def test_multistart_early_exit_against_oracle(cancel):
+    cfg = synth.IK_THROUGHPUT
+    spec, qt, sd = synth.ik_workload(cfg, 1000)
+    g, o = pair(spec)
+    ee = o.n_joints - 1
+    targets = oracle.fk(o, qt)[:, [ee]]
+    p = pk.pk_ik_params_default(max_iters=50, early_exit=1, cancel_siblings=cancel)
+    q, err, iters, status = _solve(g, p, ee, targets, sd)
+    ref = oracle.ik_solve(o, oracle_params(p), oracle.Targets([ee]), targets, sd)
+    ok, ok_ref = status == 0, ref["status"] == 0
+    assert abs(ok.mean() - ok_ref.mean()) <= 0.03
+    assert (ok == ok_ref).mean() >= 0.95
+    tg = oracle.Targets([ee])
+    for b in np.nonzero(ok)[0]:
+        pe, re = oracle.ik_errors(o, tg, targets[b], q[b])
+        assert pe <= TOL_POS * (1 + 1e-3) and re <= TOL_ROT * (1 + 1e-3)
+        assert abs(pe - err[b, 0]) <= 1e-5 and abs(re - err[b, 1]) <= 1e-5
+
+
+def test_cancellation_keeps_the_solved_set():
+    spec, qt, sd = synth.ik_workload(synth.IK_THROUGHPUT, 4000)
+    g, o = pair(spec)
+    ee = o.n_joints - 1
+    targets = host(pk.pk_fk(g, dev(qt)))[:, [ee]]
+    a = _solve(g, pk.pk_ik_params_default(cancel_siblings=0), ee, targets, sd)
+    b = _solve(g, pk.pk_ik_params_default(cancel_siblings=1), ee, targets, sd)
+    np.testing.assert_array_equal(a[3] == 0, b[3] == 0)
+
+
+def test_edge_cases():
+    g, o, ee, targets, sd = _parity_setup(40)
+    p = pk.pk_ik_params_default()
+    # batch 0 is a no-op
+    z = torch.empty(0, 1, 12, device="cuda")
+    out = pk.pk_ik_solve(g, p, [ee], None, z, torch.empty(0, 1, 7, device="cuda"))
+    assert out[0].shape == (0, 7)
+    # ragged batches, caller workspace == internal workspace
+    for B in (1, 31, 33):
+        ws = torch.empty(pk.pk_ik_workspace_bytes(g, B, 1), dtype=torch.uint8, device="cuda")
+        a = _solve(g, p, ee, targets[:B], sd[:B])
+        b = _solve(g, p, ee, targets[:B], sd[:B], workspace=ws)
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
+    # too-small workspace is rejected on the host
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(pk.PkError) as e:
+        _solve(g, p, ee, targets[:4], sd[:4], workspace=ws)
+    assert e.value.status == pk.PK_ERR_INVALID_ARG
+    # NaN target
+    t2 = targets[:3].copy()
+    t2[1, 0, 3] = np.nan
+    q, err, iters, status = _solve(g, p, ee, t2, sd[:3])
+    assert status[1] == pk.PK_P_NONFINITE and status[0] != pk.PK_P_NONFINITE
+    # zero iterations return the best seed
+    p0 = pk.pk_ik_params_default(max_iters=0)
+    seeds8 = synth.uniform_q(5, (8, 8), o.dof_lower, o.dof_upper)
+    q, err, iters, status = _solve(g, p0, ee, targets[:8], seeds8)
+    assert np.all(iters == 0)
+    for b in range(8):
+        assert any(np.allclose(q[b], seeds8[b, s], atol=0) for s in range(8))
+    # trees are not served by the chain kernel
+    hand, tips = synth.hand_robot(102)
+    gh = pk.Robot.from_spec(hand)
+    with pytest.raises(pk.PkError) as e:
+        pk.pk_ik_solve(gh, p, [int(tips[0])], None, dev(np.zeros((2, 1, 12))),
+                       dev(np.zeros((2, 1, gh.n_dof))))
+    assert e.value.status == pk.PK_ERR_UNSUPPORTED
+
+
+def test_small_chains_and_position_targets():
+    # 2-link planar arm with a position target converges to a closed-form branch
+    l1, l2 = 0.7, 0.4
+    o2 = synth.EYE12.copy(); o2[3] = l1
+    ot = synth.EYE12.copy(); ot[3] = l2
+    spec = dict(parent=[-1, 0, 1], type=[1, 1, 0], axis=[(0, 0, 1)] * 3, origin=[synth.EYE12, o2, ot],
+                lower=[-10, -10, 0], upper=[10, 10, 0])
+    g, o = pair(spec)
+    rng = np.random.default_rng(8)
+    B = 64
+    r = rng.uniform(0.4, 1.0, B)
+    phi = rng.uniform(-np.pi, np.pi, B)
+    targets = np.tile(synth.EYE12, (B, 1, 1))
+    targets[:, 0, 3], targets[:, 0, 7] = r * np.cos(phi), r * np.sin(phi)
+    seeds = rng.uniform(-2, 2, (B, 4, 2))
+    p = pk.pk_ik_params_default(w_rest=0.0, max_iters=100, tol_pos=1e-5)
+    q, err, iters, status = _solve(g, p, 2, targets, seeds, kinds=[pk.PK_TARGET_POSITION])
+    assert np.all(status == 0)
+    x = l1 * np.cos(q[:, 0]) + l2 * np.cos(q[:, 0] + q[:, 1])
+    y = l1 * np.sin(q[:, 0]) + l2 * np.sin(q[:, 0] + q[:, 1])
+    assert np.abs(np.hypot(x - targets[:, 0, 3], y - targets[:, 0, 7])).max() <= 1e-5
+    # 1-DoF: the best of 9 seeds finds the grid-search global minimum
+    L = 0.8
+    tool = synth.EYE12.copy(); tool[3] = L
+    spec1 = dict(parent=[-1, 0], type=[1, 0], axis=[(0, 0, 1)] * 2, origin=[synth.EYE12, tool],
+                 lower=[-2.8, 0], upper=[2.8, 0])
+    g1, _ = pair(spec1)
+    tgt = synth.EYE12.copy(); tgt[3], tgt[7], tgt[11] = -0.3, 0.5, 0.2
+    p1 = pk.pk_ik_params_default(w_rest=0.05, max_iters=200, tol_pos=0.0, tol_rot=0.0, early_exit=0)
+    seeds1 = np.linspace(-2.7, 2.7, 9)[None, :, None]
+    q1 = _solve(g1, p1, 1, tgt[None, None], seeds1, kinds=[pk.PK_TARGET_POSITION])[0]
+    grid = np.linspace(-3.4, 3.4, 2_000_001)
+    hinge = np.maximum(0, grid - 2.8) + np.maximum(0, -2.8 - grid)
+    cost = 0.5 * ((L * np.cos(grid) + 0.3) ** 2 + (L * np.sin(grid) - 0.5) ** 2 + 0.04) \
+        + 0.5 * (10 * hinge) ** 2 + 0.5 * (0.05 * grid) ** 2
+    assert abs(q1[0, 0] - grid[np.argmin(cost)]) < 1e-3
+
+
+def test_full_size_sampled_against_oracle():
+    """The throughput workload at full size (65,536 targets x 8 seeds) in the
+    benchmark's launch configuration; 64 sampled targets re-solved by the oracle."""
+    cfg = synth.IK_THROUGHPUT
+    spec, qt, sd = synth.ik_workload(cfg)
+    g, o = pair(spec)
+    ee = o.n_joints - 1
+    targets_d = pk.pk_fk(g, dev(qt))[:, ee:ee + 1].contiguous()
+    p = pk.pk_ik_params_default(max_iters=50, early_exit=1, cancel_siblings=1)
+    q, err, iters, status = [host(x) for x in pk.pk_ik_solve(g, p, [ee], None, targets_d, dev(sd))]
+    targets = host(targets_d)
+    ok = status == 0
+    assert ok.mean() >= 0.8
+    idx = np.random.default_rng(9).choice(cfg["batch"], 64, replace=False)
+    ref = oracle.ik_solve(o, oracle_params(p), oracle.Targets([ee]), targets[idx], sd[idx])
+    assert (ok[idx] == (ref["status"] == 0)).mean() >= 0.9
+    tg = oracle.Targets([ee])
+    for b in np.nonzero(ok)[0][:2000]:
+        pe, re = oracle.ik_errors(o, tg, targets[b], q[b])
+        assert pe <= TOL_POS * (1 + 1e-3) and re <= TOL_ROT * (1 + 1e-3)
