@@ -35,9 +35,9 @@ UNIT = "solves/s"
 # FP32 operations (add, mul = 1; fma = 2) per unit of work of the fused LM
 # kernel for the 7-DoF chain, from ncu's per-thread executed FADD/FMUL/FFMA
 # counts over launches with known work counters (see profiles/).
-FLOPS_PER_EVAL = 1100.0
-FLOPS_PER_BUILD = 1360.0
-FLOPS_PER_SOLVE = 370.0
+FLOPS_PER_EVAL = 1207.4
+FLOPS_PER_BUILD = 1362.0
+FLOPS_PER_SOLVE = 172.4
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
 
 

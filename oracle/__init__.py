@@ -251,3 +251,45 @@ def ik_solve(robot: Robot, params: IkParams, tg: Targets, targets, seeds, n_trac
         out["trace"] = tr
         out["margin"] = mg
     return out
+
+
+# ---------------------------------------------------------------- seed network
+def mlp_n_params(dims):
+    return int(sum(dims[l + 1] * dims[l] + dims[l + 1] for l in range(len(dims) - 1)))
+
+
+def mlp_forward(dims, params, x):
+    """Pre-head outputs [M][dims[-1]] of the SiLU MLP (FP64)."""
+    dims_a = _i32(dims)
+    params = _f64(params)
+    x = _f64(x).reshape(-1, dims[0])
+    y = np.empty((x.shape[0], dims[-1]))
+    lib().or_mlp_forward(len(dims) - 1, _p(dims_a), _p(params), x.shape[0], _p(x), _p(y))
+    return y
+
+
+def mlp_loss_grad(dims, params, x, q_star, K, lo, hi, mu=0.01):
+    """(mean loss, gradient [n_params], proposals [M][K][n]) of the min-over-K loss."""
+    dims_a = _i32(dims)
+    params = _f64(params)
+    x = _f64(x).reshape(-1, dims[0])
+    M = x.shape[0]
+    q_star = _f64(q_star).reshape(M, -1)
+    n = q_star.shape[1]
+    grad = np.empty(mlp_n_params(dims))
+    q = np.empty((M, K, n))
+    loss = C.c_double()
+    rc = lib().or_mlp_loss_grad(len(dims) - 1, _p(dims_a), _p(params), M, _p(x), _p(q_star), K, n,
+                                _p(_f64(lo)), _p(_f64(hi)), C.c_double(mu), _p(grad), _p(q),
+                                C.byref(loss))
+    if rc != 0:
+        raise ValueError("last layer width must be K * n")
+    return loss.value, grad, q
+
+
+def adamw(p, g, m, v, lr, beta1, beta2, eps, wd, step):
+    """One AdamW step in place on FP64 arrays p, m, v."""
+    for a in (p, g, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().or_adamw(C.c_int64(p.size), _p(p), _p(g), _p(m), _p(v), C.c_double(lr), C.c_double(beta1),
+                   C.c_double(beta2), C.c_double(eps), C.c_double(wd), C.c_int64(step))
