@@ -169,6 +169,32 @@ pk_status pk_ik_solve(const pk_robot* robot, const pk_ik_params* params, int32_t
                       void* stream);
 
 /*
+ * pk_ik_solve_noalloc -- pk_ik_solve for callers that cannot allocate device
+ * memory while they run: real-time control loops that must not allocate on
+ * their hot path (cudaMalloc can block for an unbounded time) and plugin hosts
+ * whose device memory belongs to another allocator.  The paper has no
+ * counterpart; this entry point only changes where the solver's scratch lives.
+ *   Arguments, outputs and results are those of pk_ik_solve, without the
+ *   workspace.  The scratch is a 32 MiB array in the library's own device
+ *   memory (held on every GPU that loads the library until the process
+ *   exits); a (batch, n_seeds) whose pk_ik_workspace_bytes() exceeds it is
+ *   rejected with PK_ERR_INVALID_ARG and nothing is enqueued (about 690,000
+ *   seeds in total for a 7-DoF chain).
+ *   No cudaMalloc, cudaFree or other allocating call is made.  The first call
+ *   on each device looks up the array's device address (set-up), so make that
+ *   first call before any stream capture.
+ *   All calls on a device share the one array, and it keeps the last call's
+ *   contents; each call clears what must start at zero.  Calls that can
+ *   overlap on the GPU (different streams, or threads) race on the array and
+ *   must be serialised by the caller.
+ */
+pk_status pk_ik_solve_noalloc(const pk_robot* robot, const pk_ik_params* params, int32_t k,
+                              const int32_t* target_links, const int32_t* target_kinds,
+                              int32_t batch, int32_t n_seeds, const float* d_targets,
+                              const float* d_seeds, float* d_q_out, float* d_err_out,
+                              int32_t* d_iters_out, int32_t* d_status_out, void* stream);
+
+/*
  * Work counters of the last pk_ik_solve that ran with this caller workspace
  * (read back with a synchronous copy, so call it after the solve has been
  * enqueued; it waits for the device).  stats_out (host, [4]):

@@ -154,6 +154,8 @@ pk_status check_targets(const pk_robot* rb, int32_t k, const int32_t* links, con
 
 namespace pk {
 
+pk_status set_error(pk_status s, const char* msg) { return fail(s, "%s", msg); }
+
 size_t ik_workspace_bytes(int n_dof, long batch, long n_seeds) {
   const size_t head = 256;
   const size_t flags = (((size_t)batch * 4) + 255) & ~(size_t)255;

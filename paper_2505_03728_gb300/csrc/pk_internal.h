@@ -20,6 +20,7 @@ struct pk_robot {
 namespace pk {
 
 constexpr int kMaxJoints = 64;
+constexpr int kMaxDevices = 64;
 constexpr int kMaxChainDof = 8;
 
 // Device-side robot layout (one contiguous allocation per robot handle).
@@ -77,6 +78,9 @@ cudaError_t launch_chain_residual(const ChainHost& ch, const LmParams& lp, const
                                   cudaStream_t stream);
 cudaError_t launch_fk(const RobotDev* d_robot, int n_joints, int n_dof, int batch, const float* d_q,
                       float* d_T, cudaStream_t stream);
+
+// Records a thread-local error message (pk_last_error) and returns s.
+pk_status set_error(pk_status s, const char* msg);
 
 // Kernel timing trace (pk_api.cu): brackets a launch with events when enabled.
 struct TraceScope {

@@ -64,6 +64,8 @@ _SIGNATURES = {
     "pk_ik_workspace_bytes": (C.c_size_t, [_vp, _i32, _i32]),
     "pk_ik_solve": (_i32, [_vp, C.POINTER(pk_ik_params), _i32, _i32p, _i32p, _i32, _i32, _vp, _vp,
                            _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "pk_ik_solve_noalloc": (_i32, [_vp, C.POINTER(pk_ik_params), _i32, _i32p, _i32p, _i32, _i32, _vp,
+                                   _vp, _vp, _vp, _vp, _vp, _vp]),
     "pk_ik_workspace_stats": (_i32, [_vp, C.POINTER(C.c_int64)]),
     "pk_trace_enable": (_i32, [_i32]),
     "pk_trace_summary": (_i32, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -244,3 +246,27 @@ def pk_trace_summary(kernel: str):
     ms, n = C.c_double(), C.c_int64()
     _check(lib().pk_trace_summary(kernel.encode(), C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def pk_ik_solve_noalloc(robot: Robot, params: pk_ik_params, links, kinds, targets: torch.Tensor,
+                        seeds: torch.Tensor, out=None, stream=None):
+    """pk_ik_solve with the library's static device scratch (no allocation in
+    the call).  Same outputs as :func:`pk_ik_solve`."""
+    links, kinds_a, kinds_p = _links(links, kinds)
+    B, S = seeds.shape[0], seeds.shape[1]
+    if seeds.shape != (B, S, robot.n_dof):
+        raise ValueError("seeds must be [batch][n_seeds][n_dof]")
+    if targets.shape != (B, len(links), 12):
+        raise ValueError("targets must be [batch][k][12]")
+    dev = seeds.device
+    if out is None:
+        out = (torch.empty(B, robot.n_dof, device=dev), torch.empty(B, 2, device=dev),
+               torch.empty(B, device=dev, dtype=torch.int32), torch.empty(B, device=dev, dtype=torch.int32))
+    q, err, iters, status = out
+    _check(lib().pk_ik_solve_noalloc(robot.handle, C.byref(params), len(links),
+                                     links.ctypes.data_as(_i32p), kinds_p, B, S,
+                                     _dev(targets, name="targets"), _dev(seeds, name="seeds"),
+                                     _dev(q, name="q"), _dev(err, name="err"),
+                                     _dev(iters, torch.int32, "iters"),
+                                     _dev(status, torch.int32, "status"), _stream(stream)))
+    return q, err, iters, status
