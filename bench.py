@@ -1,13 +1,17 @@
 """Benchmark: converged IK solves per second on one GB300 (or N, weak scaling).
 
-Workload (default): the throughput IK workload -- a seeded synthetic 7-DoF
-revolute chain, 65,536 reachable target poses (FK of uniform in-limit
-configurations), 8 uniform random seeds per target (524,288 LM problems), up
-to 50 LM iterations with early exit at 1 mm / 0.5 deg, and sibling
-cancellation (a target stops once one of its seeds converged).  One step =
-one pk_ik_solve of the whole batch with inputs resident in HBM; every timed
-step is preceded by an L2 flush (a 256 MiB device write outside the timed
-events).  value = converged targets / device time.
+Workload: the throughput IK workload -- a seeded synthetic 7-DoF revolute
+chain, 65,536 reachable target poses (FK of uniform in-limit configurations),
+8 seeds per target (524,288 LM problems), up to 50 LM iterations with early
+exit at 1 mm / 0.5 deg, and sibling cancellation (a target stops once one of
+its seeds converged).  Two arms, both timed the same way:
+  * plain:   8 uniform random seeds per target -> pk_ik_solve;
+  * learned: the seed network (trained on the GPU before timing, untimed)
+             proposes the 8 seeds inside every step -> pk_ik_solve.
+One step = one pass of the arm over the whole batch with inputs resident in
+HBM; every timed step is preceded by an L2 flush (a 256 MiB device write
+outside the timed events).  value = converged targets / device time of the
+learned arm (the plain arm is reported beside it).
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pk|reference]
 Multi-GPU: launched by torchrun, one rank per GPU; every rank solves its own
@@ -50,6 +54,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--no-cancel", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--train-epochs", type=int, default=8)
     return ap.parse_args()
 
 
@@ -164,21 +170,65 @@ def run_reference(args, cfg):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(cfg, args),
+            "data": "synthetic", "config": config_dict(cfg, args, "plain"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
 
 
-def config_dict(cfg, args):
+def config_dict(cfg, args, head="plain"):
+    seeding = ("learned: seed network (9 -> 4 x 512 SiLU -> 8 x 7, BF16 tcgen05, trained on the GPU "
+               "before timing) inferred inside every step" if head == "learned" else "uniform random")
     return {"workload": cfg["name"], "robot": "synthetic 7-DoF revolute chain (seed 100)",
             "targets": args.batch, "seeds_per_target": cfg["n_seeds"], "max_iters": cfg["max_iters"],
-            "early_exit": True, "cancel_siblings": not args.no_cancel, "seeding": "uniform random",
+            "early_exit": True, "cancel_siblings": not args.no_cancel, "seeding": seeding,
             "l2": "flushed by a 256 MiB device write before every timed step"}
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def measured_bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
+def seednet_flops(n_in_pad, width, depth, n_out_pad, rows):
+    macs = n_in_pad * width + (depth - 1) * width * width + width * n_out_pad
+    return 2.0 * rows * macs
+
+
+class Timed:
+    """Per-step CUDA events on the current stream, L2 flushed before each step."""
+
+    def __init__(self, torch, steps, flush):
+        self.torch, self.steps, self.flush = torch, steps, flush
+        self.s = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        self.e = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+
+    def run(self, step_fn, stream):
+        for k in range(self.steps):
+            self.flush.zero_()
+            self.s[k].record(stream)
+            step_fn()
+            self.e[k].record(stream)
+        self.torch.cuda.synchronize()
+        return float(sum(a.elapsed_time(b) for a, b in zip(self.s, self.e)))
+
+
+def reduce_over_ranks(torch, world, ms, count):
+    if world == 1:
+        return ms, count
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([count], dtype=torch.int64, device="cuda")
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
+
+
 def main():
     args = parse()
     from paper_2505_03728_gb300 import synth
@@ -212,50 +262,63 @@ def main():
             torch.empty(B, dtype=torch.int32, device="cuda"), torch.empty(B, dtype=torch.int32, device="cuda"))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-
-    def step():
-        return pk.pk_ik_solve(robot, params, [ee], None, targets, seeds, ws, out=outs)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     conv = torch.zeros((), dtype=torch.int64, device="cuda")
+
+    def plain_step():
+        pk.pk_ik_solve(robot, params, [ee], None, targets, seeds, ws, out=outs)
+
+    # ---- learned seeds: train once (untimed), then infer + solve per step
+    net = None
+    train_s = 0.0
+    if not args.no_learned:
+        net = pk.SeedNet(robot, [ee], K=S, width=512, depth=4, seed=11)
+        tp = pk.pk_train_params_default(epochs=args.train_epochs, steps_per_epoch=1220, batch=8192, seed=500)
+        t0 = time.perf_counter()
+        train_loss = pk.pk_seednet_train(net, tp)
+        train_s = time.perf_counter() - t0
+        lseeds = torch.empty(B, S, n, device="cuda")
+
+    def learned_step():
+        pk.pk_seednet_infer(net, targets, lseeds)
+        pk.pk_ik_solve(robot, params, [ee], None, targets, lseeds, ws, out=outs)
+
     props = torch.cuda.get_device_properties(local)
     gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.synchronize()
-    pk.pk_trace_enable(True)
+    results = {}
+    arms = [("plain", plain_step)] + ([("learned", learned_step)] if net is not None else [])
     with ClockSampler(gpu_id) as clocks:
-        for k in range(args.steps):
-            flush.zero_()
-            starts[k].record(stream)
-            step()
-            ends[k].record(stream)
-            conv += (outs[3] == pk.PK_P_CONVERGED).sum()
-        torch.cuda.synchronize()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    lm_ms, lm_n = pk.pk_trace_summary("ik_lm")
-    red_ms, red_n = pk.pk_trace_summary("ik_reduce")
-    pk.pk_trace_enable(False)
-    stats = pk.pk_ik_workspace_stats(ws)
-    total_ms = float(sum(step_ms))
-    n_conv = int(conv.item())
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        c = torch.tensor([n_conv], dtype=torch.int64, device="cuda")
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        total_ms, n_conv = float(t.item()), int(c.item())
-    value = n_conv / (total_ms / 1e3)
+        for name, fn in arms:
+            for _ in range(args.warmup):  # the same kernels the timed steps launch
+                fn()
+                conv.add_((outs[3] == pk.PK_P_CONVERGED).sum())
+            torch.cuda.synchronize()
+            if world > 1:
+                import torch.distributed as dist
+                dist.barrier()
+            conv.zero_()
+            pk.pk_trace_enable(True)
+            timed = Timed(torch, args.steps, flush)
 
-    # end to end through the public API with host buffers
+            def counted():
+                fn()
+                conv.add_((outs[3] == pk.PK_P_CONVERGED).sum())
+            total_ms = timed.run(counted, stream)
+            lm_ms, lm_n = pk.pk_trace_summary("ik_lm")
+            gemm_ms, gemm_n = pk.pk_trace_summary("gemm")
+            pk.pk_trace_enable(False)
+            stats = pk.pk_ik_workspace_stats(ws)
+            n_conv = int(conv.item())
+            if world > 1:
+                import torch.distributed as dist
+                dist.barrier()
+            total_ms, n_conv = reduce_over_ranks(torch, world, total_ms, n_conv)
+            results[name] = dict(value=n_conv / (total_ms / 1e3), ms_per_step=total_ms / args.steps,
+                                 success_rate=n_conv / (B * args.steps * world), lm_ms=lm_ms / max(1, lm_n),
+                                 gemm_ms=gemm_ms / max(1, args.steps), gemm_launches=gemm_n // max(1, args.steps),
+                                 stats=stats)
+
+    # ---- end to end through the public API with host buffers (headline path)
+    head = "learned" if net is not None else "plain"
     h_t = torch.empty(targets.shape, dtype=torch.float32, pin_memory=True)
     h_t.copy_(targets)
     h_s = torch.empty(seeds.shape, dtype=torch.float32, pin_memory=True)
@@ -268,23 +331,21 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         d_t.copy_(h_t, non_blocking=True)
-        d_s.copy_(h_s, non_blocking=True)
-        pk.pk_ik_solve(robot, params, [ee], None, d_t, d_s, ws, out=outs)
+        if head == "learned":
+            pk.pk_seednet_infer(net, d_t, lseeds)
+            pk.pk_ik_solve(robot, params, [ee], None, d_t, lseeds, ws, out=outs)
+        else:
+            d_s.copy_(h_s, non_blocking=True)
+            pk.pk_ik_solve(robot, params, [ee], None, d_t, d_s, ws, out=outs)
         for ho, o in zip(h_out, outs):
             ho.copy_(o, non_blocking=True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        if k > 0:  # first one is a warm-up of the copies
+        if k > 0:
             e2e_ms += dt * 1e3
             e2e_conv += int((h_out[3] == pk.PK_P_CONVERGED).sum())
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        c = torch.tensor([e2e_conv], dtype=torch.int64, device="cuda")
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        e2e_ms, e2e_conv = float(t.item()), int(c.item())
-    h2d = h_t.numel() * 4 + h_s.numel() * 4
+    e2e_ms, e2e_conv = reduce_over_ranks(torch, world, e2e_ms, e2e_conv)
+    h2d = h_t.numel() * 4 + (0 if head == "learned" else h_s.numel() * 4)
     d2h = sum(o.numel() * o.element_size() for o in outs)
 
     if rank != 0:
@@ -292,27 +353,45 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    flops = (stats["evals"] * FLOPS_PER_EVAL + stats["builds"] * FLOPS_PER_BUILD
-             + stats["solves"] * FLOPS_PER_SOLVE)
-    lm_avg_ms = lm_ms / max(1, lm_n)
-    achieved = flops / (lm_avg_ms / 1e3) / 1e12
+    r = results[head]
+    st = r["stats"]
+    lm_flops = (st["evals"] * FLOPS_PER_EVAL + st["builds"] * FLOPS_PER_BUILD + st["solves"] * FLOPS_PER_SOLVE)
+    lm_tf = lm_flops / (r["lm_ms"] / 1e3) / 1e12
+    lm_roof = {"bound": "alu", "kernel": "chain_lm_kernel<7>", "achieved": lm_tf, "peak": FP32_PEAK_TFLOPS,
+               "unit": "TFLOP/s", "frac": lm_tf / FP32_PEAK_TFLOPS, "traffic": None,
+               "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (unit counts x max clock)",
+               "ms_per_launch": r["lm_ms"], "work_per_launch": st}
+    roofs = [lm_roof]
+    if head == "learned":
+        peak, src = measured_bf16_peak()
+        fl = seednet_flops(64, 512, 4, 64, ((B + 127) // 128) * 128)
+        g_tf = fl / (r["gemm_ms"] / 1e3) / 1e12
+        roofs.append({"bound": "tensor", "kernel": f"gemm_bf16_tc_kernel ({r['gemm_launches']} launches per "
+                                                    "inference, aggregate)",
+                      "achieved": g_tf, "peak": peak, "unit": "TFLOP/s", "frac": g_tf / peak, "traffic": None,
+                      "peak_source": f"bf16 dense GEMM burst ({src}, MEASURED_PEAKS.json)",
+                      "ms_per_step": r["gemm_ms"], "flops_per_step": fl})
+    dominant = max(roofs, key=lambda x: x.get("ms_per_launch", x.get("ms_per_step", 0)))
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_dict(cfg, args),
-        "success_rate": n_conv / (B * args.steps * world),
-        "roofline": {"bound": "alu", "kernel": "chain_lm_kernel<7>", "achieved": achieved,
-                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                     "traffic": None,
-                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (unit counts x max clock)",
-                     "lm_kernel_ms": lm_avg_ms, "reduce_kernel_ms": red_ms / max(1, red_n),
-                     "work_per_launch": stats},
+        "config": config_dict(cfg, args, head),
+        "success_rate": r["success_rate"],
+        "plain": {k: results["plain"][k] for k in ("value", "ms_per_step", "success_rate", "lm_ms")},
+        "roofline": dominant,
+        "roofline_other": [x for x in roofs if x is not dominant],
         "e2e": {"value": e2e_conv / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": args.steps * (9 if head == "learned" else 2),
         "clocks": clocks.summary(),
     }
+    if "learned" in results:
+        line["learned"] = {k: results["learned"][k] for k in ("value", "ms_per_step", "success_rate", "lm_ms",
+                                                               "gemm_ms")}
+        line["learned"]["train_s"] = train_s
+        line["learned"]["train_loss"] = [float(x) for x in train_loss]
+        line["learned_over_plain"] = results["learned"]["value"] / results["plain"]["value"]
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, qt, sd)
     print(json.dumps(line), flush=True)

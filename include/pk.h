@@ -215,6 +215,72 @@ pk_status pk_ik_workspace_stats(const void* d_workspace, int64_t* stats_out);
 pk_status pk_trace_enable(int32_t enable);
 pk_status pk_trace_summary(const char* kernel, double* total_ms, int64_t* launches);
 
+/*
+ * Learned seeds.  The paper's solver starts from given seeds; a seed network
+ * adds the learned-seed pattern around it: a SiLU MLP maps target poses to K
+ * joint-space proposals that the LM solver (pk_ik_solve) refines.  It runs on
+ * the BF16 tensor cores (tcgen05, FP32 accumulation) for inference and
+ * training, with FP32 master weights and AdamW.
+ *   Features of one target pose: its position then the first two columns of its
+ *   rotation, [t0 t1 t2 r00 r10 r20 r01 r11 r21]; k targets give 9k inputs.
+ *   Head: q = (lower + upper)/2 + (upper - lower)/2 * tanh(y) per joint.
+ *   Loss per sample with label q*: min_k |q_k - q*|^2 + mu * mean_k |q_k - q*|^2.
+ *   Training data: uniform random in-limit configurations (drawn on the device by
+ *   a counter-based SplitMix64 generator keyed by seed and step) and the
+ *   forward kinematics of the target frames.
+ * A net is used by one stream at a time (it owns its activation buffers).
+ */
+typedef struct pk_seednet pk_seednet;
+
+typedef struct {
+  int32_t epochs;          /* default 8 */
+  int32_t batch;           /* samples per step, >= 128 (default 8192) */
+  int32_t steps_per_epoch; /* default 1220 (~10M samples per epoch) */
+  float lr;                /* peak learning rate, cosine schedule (default 1e-3) */
+  float weight_decay;      /* AdamW decoupled decay (default 1e-4) */
+  float beta1, beta2, eps; /* AdamW moments (0.9, 0.999, 1e-8) */
+  float mu;                /* weight of the mean term of the loss (default 0.01) */
+  int32_t reserved;        /* must be 0 */
+  uint64_t seed;           /* training-data generator key (default 500) */
+} pk_train_params;
+
+void pk_train_params_default(pk_train_params* p);
+
+/* k target frames (target_links, host [k]), K proposals, `depth` hidden layers
+ * of `width` (a multiple of 256) units; weights initialised from `seed`. */
+pk_status pk_seednet_create(const pk_robot* robot, int32_t k, const int32_t* target_links, int32_t K,
+                            int32_t width, int32_t depth, uint64_t seed, pk_seednet** out);
+void pk_seednet_destroy(pk_seednet* net);
+
+/* Parameter count and FP32 copies in the layout: per layer W [out][in] row-major
+ * then b [out] (host buffers).  set_params also resets the AdamW state. */
+int64_t pk_seednet_n_params(const pk_seednet* net);
+pk_status pk_seednet_get_params(const pk_seednet* net, float* host_params, int64_t n);
+pk_status pk_seednet_set_params(pk_seednet* net, const float* host_params, int64_t n);
+
+/* Pre-head outputs d_y_out [batch][K * n_dof] (FP32) for d_targets [batch][k][12]. */
+pk_status pk_seednet_forward(pk_seednet* net, int32_t batch, const float* d_targets, float* d_y_out,
+                             void* stream);
+
+/* Seeds d_seeds_out [batch][K][n_dof] for d_targets [batch][k][12]: the layout
+ * pk_ik_solve takes. */
+pk_status pk_seednet_infer(pk_seednet* net, int32_t batch, const float* d_targets, float* d_seeds_out,
+                           void* stream);
+
+/* Mean loss and gradient (host, parameter layout above) of one batch with
+ * labels d_qstar [batch][n_dof], mu = 0.01.  Synchronous. */
+pk_status pk_seednet_loss_grad(pk_seednet* net, int32_t batch, const float* d_targets,
+                               const float* d_qstar, float* host_loss, float* host_grad, void* stream);
+
+/* One AdamW step on one given batch at learning rate lr.  Synchronous. */
+pk_status pk_seednet_train_step(pk_seednet* net, const pk_train_params* params, int32_t batch,
+                                const float* d_targets, const float* d_qstar, float lr, void* stream);
+
+/* Full training run on generated data; host_loss [epochs] (or NULL) receives the
+ * mean loss of every epoch.  Synchronous.  PK_ERR_TIMEOUT if a tensor-core
+ * pipeline wait expired (the kernels bound every wait). */
+pk_status pk_seednet_train(pk_seednet* net, const pk_train_params* params, float* host_loss, void* stream);
+
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char* pk_last_error(void);
 

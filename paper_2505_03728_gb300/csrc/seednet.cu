@@ -1,0 +1,810 @@
+// seednet.cu -- the learned-seed network: a SiLU MLP that maps target poses to
+// K joint-space proposals, trained and run on the tensor cores (tc_gemm.cuh).
+//
+// Features of one target pose (3x4 [R | t]): t (3) then the first two columns
+// of R ([r00 r10 r20 r01 r11 r21]); k targets give 9k inputs, zero-padded to a
+// multiple of 64.  Hidden layers: `depth` x `width` with SiLU; output layer
+// K * n (padded to a multiple of 64); head q = mid + half * tanh(y) per joint.
+// Loss per sample: min_k |q_k - q*|^2 + mu * mean_k |q_k - q*|^2.  AdamW with
+// FP32 master weights; BF16 copies W [out][in] (forward) and W^T [in][out]
+// (input gradients).  Training data: uniform random in-limit configurations
+// drawn on the device with a counter-based SplitMix64 generator, their forward
+// kinematics (the features) and themselves (the labels).
+#include <cudaTypedefs.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <random>
+#include <vector>
+
+#include "pk_internal.h"
+#include "pk_math.cuh"
+#include "tc_gemm.cuh"
+
+using pk::tc::Epilogue;
+
+struct pk_seednet {
+  const pk::RobotDev* d_robot = nullptr;
+  int n_dof = 0, n_joints = 0;
+  int k = 0;                      // targets per sample
+  int links[16] = {};
+  int K = 0, width = 0, depth = 0;
+  int in_dim = 0, in_pad = 0, out_dim = 0, out_pad = 0;
+  int L = 0;                      // layers = depth + 1
+  std::vector<int> din, dout;     // padded dims per layer
+  std::vector<size_t> w_off, b_off;  // offsets into the FP32 parameter buffers
+  size_t n_master = 0;            // padded parameter count
+  float* master = nullptr;        // FP32 [n_master]
+  float* grad = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  std::vector<__nv_bfloat16*> W, Wt;
+  std::vector<float> lo, hi;      // joint limits per dof
+  float* d_lohi = nullptr;        // [2][n]
+  int* d_links = nullptr;
+  int* d_err = nullptr;
+  float* d_loss = nullptr;
+  int64_t step = 0;
+  uint64_t seed = 0;
+  // activation buffers, sized for `cap_rows` rows
+  int cap_rows = 0;
+  __nv_bfloat16 *X = nullptr, *Xt = nullptr, *dY = nullptr, *dYt = nullptr;
+  std::vector<__nv_bfloat16*> A, At;  // per hidden layer
+  std::vector<float*> Z;
+  __nv_bfloat16 *dZ[2] = {nullptr, nullptr}, *dZt[2] = {nullptr, nullptr};
+  float* Y = nullptr;
+  float* qstar = nullptr;
+};
+
+namespace {
+
+std::mutex g_map_mu;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+pk_status sn_fail(pk_status s, const char* msg) { return pk::set_error(s, msg); }
+
+pk_status sn_cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return PK_OK;
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  return sn_fail(e == cudaErrorMemoryAllocation ? PK_ERR_OOM : PK_ERR_CUDA, buf);
+}
+
+bool get_encode() {
+  std::lock_guard<std::mutex> lk(g_map_mu);
+  if (g_encode) return true;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+          cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return false;
+  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  return true;
+}
+
+// 2-D BF16 tensor map over a row-major [rows][cols] matrix, box 64 x box_rows,
+// 128-byte swizzle.
+bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * 2};
+  cuuint32_t box[2] = {64, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t gemm_launch(const CUtensorMap& ma, const CUtensorMap& mb, int a_rows, int b_rows, int K,
+                        int splits, const Epilogue& ep, int* d_err, cudaStream_t st) {
+  using Lay = pk::tc::SmemLayout<BN>;
+  static int sms = 0;
+  if (!sms) {
+    cudaError_t e = cudaFuncSetAttribute(pk::tc::gemm_bf16_tc_kernel<BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::kBytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int nkb = K / pk::tc::kBK;
+  if (splits < 1) splits = 1;
+  if (splits > nkb) splits = nkb;
+  const int per = (nkb + splits - 1) / splits;
+  splits = (nkb + per - 1) / per;
+  const int m_tiles = a_rows / pk::tc::kBM, n_tiles = b_rows / BN;
+  const int tiles = m_tiles * n_tiles * splits;
+  const int grid = tiles < sms ? tiles : sms;
+  pk::TraceScope tr(ep.mode == pk::tc::EPI_WGRAD_ADD ? "gemm_wgrad" : "gemm", st);
+  pk::tc::gemm_bf16_tc_kernel<BN><<<grid, pk::tc::kThreads, Lay::kBytes, st>>>(ma, mb, m_tiles, n_tiles, splits,
+                                                                              K, per, ep, d_err);
+  return cudaGetLastError();
+}
+
+// D[a_rows x b_rows] = A[a_rows x K] B[b_rows x K]^T with epilogue `ep`.
+cudaError_t gemm(const __nv_bfloat16* A, int a_rows, const __nv_bfloat16* B, int b_rows, int K, int splits,
+                 const Epilogue& ep, int* d_err, cudaStream_t st) {
+  const int BN = (b_rows % 256 == 0) ? 256 : (b_rows % 128 == 0) ? 128 : 64;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, a_rows, K, pk::tc::kBM) || !make_map(&mb, B, b_rows, K, BN))
+    return cudaErrorInvalidValue;
+  if (BN == 256) return gemm_launch<256>(ma, mb, a_rows, b_rows, K, splits, ep, d_err, st);
+  if (BN == 128) return gemm_launch<128>(ma, mb, a_rows, b_rows, K, splits, ep, d_err, st);
+  return gemm_launch<64>(ma, mb, a_rows, b_rows, K, splits, ep, d_err, st);
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// ---------------------------------------------------------------- kernels
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// Uniform in [0, 1) from the counter-based generator: the 24 high bits of
+// SplitMix64(seed + counter * golden gamma).
+__device__ __forceinline__ float uniform01(uint64_t seed, uint64_t counter) {
+  const uint64_t r = splitmix64(seed + counter * 0x9e3779b97f4a7c15ull);
+  return (float)(r >> 40) * (1.0f / 16777216.0f);
+}
+
+// Frame of joint `link` by generic tree FK (frames kept in local memory).
+__device__ void tree_fk_link(const pk::RobotDev* __restrict__ rb, const float* q, int link, pk::Rt& out,
+                             pk::Rt* frames) {
+  for (int j = 0; j <= link; ++j) {
+    pk::Rt O, X, Lm;
+    pk::rt_load(rb->origin[j], O);
+    pk::rt_identity(X);
+    const int t = rb->type[j];
+    if (t != PK_JOINT_FIXED) {
+      const float qv = q[rb->var[j]];
+      const float* a = rb->axis[j];
+      if (t == PK_JOINT_REVOLUTE) {
+        float u[3] = {a[0], a[1], a[2]}, s, c;
+        pk::sincos_rad(qv, &s, &c);
+        pk::rot_joint(X.r, u, a, s, c);
+      } else {
+        X.t[0] = a[0] * qv; X.t[1] = a[1] * qv; X.t[2] = a[2] * qv;
+      }
+    }
+    pk::rt_mul(O, X, Lm);
+    const int p = rb->parent[j];
+    if (p >= 0) pk::rt_mul(frames[p], Lm, Lm);
+    frames[j] = Lm;
+  }
+  out = frames[link];
+}
+
+__device__ __forceinline__ void pose_features(const pk::Rt& T, float* f) {
+  f[0] = T.t[0]; f[1] = T.t[1]; f[2] = T.t[2];
+  f[3] = T.r[0]; f[4] = T.r[3]; f[5] = T.r[6];
+  f[6] = T.r[1]; f[7] = T.r[4]; f[8] = T.r[7];
+}
+
+__device__ __forceinline__ void store_features(const float* f, int in_dim, int in_pad, int row, int m_pad,
+                                               __nv_bfloat16* X, __nv_bfloat16* Xt) {
+  for (int i = 0; i < in_pad; ++i) {
+    const __nv_bfloat16 v = __float2bfloat16_rn(i < in_dim ? f[i] : 0.f);
+    X[(size_t)row * in_pad + i] = v;
+    if (Xt) Xt[(size_t)i * m_pad + row] = v;
+  }
+}
+
+// Features of given target poses [B][k][12]; rows >= B are zero.
+__global__ void features_kernel(const float* __restrict__ targets, int B, int k, int in_pad, int m_pad,
+                                __nv_bfloat16* X, __nv_bfloat16* Xt) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= m_pad) return;
+  float f[9 * 16];
+  const int in_dim = 9 * k;
+  for (int t = 0; t < k; ++t) {
+    pk::Rt T;
+    if (b < B) {
+      pk::rt_load(targets + ((size_t)b * k + t) * 12, T);
+      pose_features(T, f + 9 * t);
+    } else {
+      for (int i = 0; i < 9; ++i) f[9 * t + i] = 0.f;
+    }
+  }
+  store_features(f, in_dim, in_pad, b, m_pad, X, Xt);
+}
+
+// Training samples: q* uniform in the limits, features of FK(q*).
+__global__ void datagen_kernel(const pk::RobotDev* __restrict__ rb, const int* __restrict__ links, int k,
+                               const float* __restrict__ lohi, int n, uint64_t seed, int64_t step, int M,
+                               int in_pad, int m_pad, __nv_bfloat16* X, __nv_bfloat16* Xt, float* qstar) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= m_pad) return;
+  float q[pk::kMaxJoints];
+  float f[9 * 16];
+  if (b < M) {
+    const uint64_t base = ((uint64_t)step * (uint64_t)M + (uint64_t)b) * (uint64_t)n;
+    for (int j = 0; j < n; ++j) {
+      const float lo = lohi[j], hi = lohi[n + j];
+      q[j] = lo + (hi - lo) * uniform01(seed, base + j);
+      qstar[(size_t)b * n + j] = q[j];
+    }
+    pk::Rt frames[pk::kMaxJoints];
+    for (int t = 0; t < k; ++t) {
+      pk::Rt T;
+      tree_fk_link(rb, q, links[t], T, frames);
+      pose_features(T, f + 9 * t);
+    }
+  } else {
+    for (int i = 0; i < 9 * k; ++i) f[i] = 0.f;
+  }
+  store_features(f, 9 * k, in_pad, b, m_pad, X, Xt);
+}
+
+// Head, min-over-K loss and dL/dy (scaled by 1/M) for M valid rows.
+__global__ void head_loss_kernel(const float* __restrict__ Y, int ldy, int M, int m_pad, int K, int n,
+                                 const float* __restrict__ lohi, const float* __restrict__ qstar, float mu,
+                                 __nv_bfloat16* dY, int ld_dy, __nv_bfloat16* dYt, float* loss_sum) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= m_pad) return;
+  if (b >= M) {
+    for (int i = 0; i < ld_dy; ++i) {
+      dY[(size_t)b * ld_dy + i] = __float2bfloat16_rn(0.f);
+      dYt[(size_t)i * m_pad + b] = __float2bfloat16_rn(0.f);
+    }
+    return;
+  }
+  const float* y = Y + (size_t)b * ldy;
+  const float* qs = qstar + (size_t)b * n;
+  float e[64];
+  int best = 0;
+  float mean = 0.f;
+  for (int kk = 0; kk < K; ++kk) {
+    float s = 0.f;
+    for (int i = 0; i < n; ++i) {
+      const float lo = lohi[i], hi = lohi[n + i];
+      const float q = 0.5f * (lo + hi) + 0.5f * (hi - lo) * tanhf(y[kk * n + i]);
+      s = fmaf(q - qs[i], q - qs[i], s);
+    }
+    e[kk] = s;
+    mean += s / K;
+    if (s < e[best]) best = kk;
+  }
+  atomicAdd(loss_sum, e[best] + mu * mean);
+  const float invM = 1.f / (float)M;
+  for (int kk = 0; kk < K; ++kk) {
+    const float w = (kk == best ? 1.f : 0.f) + mu / K;
+    for (int i = 0; i < n; ++i) {
+      const float lo = lohi[i], hi = lohi[n + i];
+      const float t = tanhf(y[kk * n + i]);
+      const float q = 0.5f * (lo + hi) + 0.5f * (hi - lo) * t;
+      const float g = w * 2.f * (q - qs[i]) * 0.5f * (hi - lo) * (1.f - t * t) * invM;
+      const __nv_bfloat16 h = __float2bfloat16_rn(g);
+      dY[(size_t)b * ld_dy + kk * n + i] = h;
+      dYt[(size_t)(kk * n + i) * m_pad + b] = h;
+    }
+  }
+  for (int i = K * n; i < ld_dy; ++i) {
+    dY[(size_t)b * ld_dy + i] = __float2bfloat16_rn(0.f);
+    dYt[(size_t)i * m_pad + b] = __float2bfloat16_rn(0.f);
+  }
+}
+
+// db[r] = sum over the m_pad columns of G^T row r (one warp per row).
+__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ Gt, int rows, int m_pad, float* db) {
+  const int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  float s = 0.f;
+  for (int i = lane; i < m_pad; i += 32) s += __bfloat162float(Gt[(size_t)r * m_pad + i]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) db[r] = s;
+}
+
+__global__ void adamw_kernel(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1,
+                             float b2, float eps, float wd, float c1, float c2) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * p[i]);
+}
+
+// BF16 copies of one layer's weights: W [out][in] and W^T [in][out].
+__global__ void cast_weights_kernel(const float* __restrict__ w, int out, int in, __nv_bfloat16* W,
+                                    __nv_bfloat16* Wt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= out * in) return;
+  const int o = i / in, c = i % in;
+  const __nv_bfloat16 h = __float2bfloat16_rn(w[i]);
+  W[i] = h;
+  Wt[(size_t)c * out + o] = h;
+}
+
+// Seeds [B][K][n] from the pre-head outputs.
+__global__ void seeds_head_kernel(const float* __restrict__ Y, int ldy, int B, int K, int n,
+                                  const float* __restrict__ lohi, float* seeds) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * K * n) return;
+  const int b = i / (K * n), r = i % (K * n), j = r % n;
+  const float lo = lohi[j], hi = lohi[n + j];
+  seeds[i] = 0.5f * (lo + hi) + 0.5f * (hi - lo) * tanhf(Y[(size_t)b * ldy + r]);
+}
+
+// ---------------------------------------------------------------- host helpers
+
+void free_acts(pk_seednet* s) {
+  auto f = [](void* p) { if (p) cudaFree(p); };
+  f(s->X); f(s->Xt); f(s->dY); f(s->dYt); f(s->Y); f(s->qstar);
+  for (auto* p : s->A) f(p);
+  for (auto* p : s->At) f(p);
+  for (auto* p : s->Z) f(p);
+  for (int i = 0; i < 2; ++i) { f(s->dZ[i]); f(s->dZt[i]); }
+  s->X = s->Xt = s->dY = s->dYt = nullptr;
+  s->Y = s->qstar = nullptr;
+  s->A.assign(s->depth, nullptr);
+  s->At.assign(s->depth, nullptr);
+  s->Z.assign(s->depth, nullptr);
+  s->dZ[0] = s->dZ[1] = s->dZt[0] = s->dZt[1] = nullptr;
+  s->cap_rows = 0;
+}
+
+// Activation buffers for m_pad rows (training buffers included).
+pk_status ensure_acts(pk_seednet* s, int m_pad) {
+  if (s->cap_rows >= m_pad) return PK_OK;
+  free_acts(s);
+  const size_t H = s->width;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+  al((void**)&s->X, (size_t)m_pad * s->in_pad * 2);
+  al((void**)&s->Xt, (size_t)m_pad * s->in_pad * 2);
+  al((void**)&s->dY, (size_t)m_pad * s->out_pad * 2);
+  al((void**)&s->dYt, (size_t)m_pad * 128 * 2);
+  al((void**)&s->Y, (size_t)m_pad * s->out_pad * 4);
+  al((void**)&s->qstar, (size_t)m_pad * s->n_dof * 4);
+  for (int l = 0; l < s->depth; ++l) {
+    al((void**)&s->A[l], (size_t)m_pad * H * 2);
+    al((void**)&s->At[l], (size_t)m_pad * H * 2);
+    al((void**)&s->Z[l], (size_t)m_pad * H * 4);
+  }
+  for (int i = 0; i < 2; ++i) {
+    al((void**)&s->dZ[i], (size_t)m_pad * H * 2);
+    al((void**)&s->dZt[i], (size_t)m_pad * H * 2);
+  }
+  if (e == cudaSuccess) e = cudaMemset(s->dYt, 0, (size_t)m_pad * 128 * 2);
+  if (e != cudaSuccess) {
+    free_acts(s);
+    return sn_cuda(e, "seednet activation buffers");
+  }
+  s->cap_rows = m_pad;
+  return PK_OK;
+}
+
+cudaError_t cast_all(pk_seednet* s, cudaStream_t st) {
+  for (int l = 0; l < s->L; ++l) {
+    const int n = s->dout[l] * s->din[l];
+    cast_weights_kernel<<<(n + 255) / 256, 256, 0, st>>>(s->master + s->w_off[l], s->dout[l], s->din[l], s->W[l],
+                                                         s->Wt[l]);
+  }
+  return cudaGetLastError();
+}
+
+// Forward pass of m_pad rows whose features are in s->X (m_valid real rows).
+// With `train`, pre-activations and transposed activations are kept.
+cudaError_t forward(pk_seednet* s, int m_valid, int m_pad, bool train, cudaStream_t st) {
+  const __nv_bfloat16* a = s->X;
+  int K = s->in_pad;
+  for (int l = 0; l < s->depth; ++l) {
+    Epilogue ep{};
+    ep.mode = pk::tc::EPI_FWD_SILU;
+    ep.m_valid = m_pad;  // padded rows are zero features; keep them finite
+    ep.bias = s->master + s->b_off[l];
+    ep.out_f32 = train ? s->Z[l] : nullptr;
+    ep.ld_f32 = s->width;
+    ep.out_bf16 = s->A[l];
+    ep.ld_bf16 = s->width;
+    ep.out_t = train ? s->At[l] : nullptr;
+    ep.ld_t = m_pad;
+    cudaError_t e = gemm(a, m_pad, s->W[l], s->width, K, 1, ep, s->d_err, st);
+    if (e != cudaSuccess) return e;
+    a = s->A[l];
+    K = s->width;
+  }
+  Epilogue ep{};
+  ep.mode = pk::tc::EPI_FWD_LINEAR;
+  ep.m_valid = m_valid;
+  ep.n_valid = s->out_pad;
+  ep.bias = s->master + s->b_off[s->depth];
+  ep.out_f32 = s->Y;
+  ep.ld_f32 = s->out_pad;
+  return gemm(a, m_pad, s->W[s->depth], s->out_pad, K, 1, ep, s->d_err, st);
+}
+
+// Backward pass (gradients into s->grad) from dY / dYt; features in X / Xt.
+cudaError_t backward(pk_seednet* s, int m_pad, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(s->grad, 0, s->n_master * sizeof(float), st);
+  if (e != cudaSuccess) return e;
+  const int splits = m_pad / 64 >= 16 ? 16 : 1;
+  const int D = s->depth;
+  // last layer: dW = dY^T A_{D-1}, db = column sums of dY
+  {
+    Epilogue ep{};
+    ep.mode = pk::tc::EPI_WGRAD_ADD;
+    ep.m_valid = s->out_pad;
+    ep.out_f32 = s->grad + s->w_off[D];
+    ep.ld_f32 = s->width;
+    if ((e = gemm(s->dYt, 128, s->At[D - 1], s->width, m_pad, splits, ep, s->d_err, st)) != cudaSuccess) return e;
+    bias_grad_kernel<<<(s->out_pad + 7) / 8, 256, 0, st>>>(s->dYt, s->out_pad, m_pad, s->grad + s->b_off[D]);
+  }
+  // dZ_{D-1} = (dY W_D) * silu'(Z_{D-1})
+  const __nv_bfloat16* g = s->dY;
+  int gk = s->out_pad;
+  int cur = 0;
+  for (int l = D - 1; l >= 0; --l) {
+    Epilogue ep{};
+    ep.mode = pk::tc::EPI_DGRAD_SILU;
+    ep.m_valid = m_pad;
+    ep.zprev = s->Z[l];
+    ep.ld_zprev = s->width;
+    ep.out_bf16 = s->dZ[cur];
+    ep.ld_bf16 = s->width;
+    ep.out_t = s->dZt[cur];
+    ep.ld_t = m_pad;
+    if ((e = gemm(g, m_pad, s->Wt[l + 1], s->width, gk, 1, ep, s->d_err, st)) != cudaSuccess) return e;
+    // layer l weights: dW_l = dZ_l^T A_{l-1} (A_{-1} = X)
+    Epilogue ew{};
+    ew.mode = pk::tc::EPI_WGRAD_ADD;
+    ew.m_valid = s->width;
+    ew.out_f32 = s->grad + s->w_off[l];
+    ew.ld_f32 = s->din[l];
+    const __nv_bfloat16* prev_t = l > 0 ? s->At[l - 1] : s->Xt;
+    if ((e = gemm(s->dZt[cur], s->width, prev_t, s->din[l], m_pad, splits, ew, s->d_err, st)) != cudaSuccess)
+      return e;
+    bias_grad_kernel<<<(s->width + 7) / 8, 256, 0, st>>>(s->dZt[cur], s->width, m_pad, s->grad + s->b_off[l]);
+    g = s->dZ[cur];
+    gk = s->width;
+    cur ^= 1;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t loss_and_grad(pk_seednet* s, int M, int m_pad, float mu, cudaStream_t st) {
+  cudaError_t e = forward(s, M, m_pad, true, st);
+  if (e != cudaSuccess) return e;
+  head_loss_kernel<<<(m_pad + 127) / 128, 128, 0, st>>>(s->Y, s->out_pad, M, m_pad, s->K, s->n_dof, s->d_lohi,
+                                                        s->qstar, mu, s->dY, s->out_pad, s->dYt, s->d_loss);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return backward(s, m_pad, st);
+}
+
+cudaError_t adamw(pk_seednet* s, const pk_train_params* tp, float lr, cudaStream_t st) {
+  s->step += 1;
+  const float c1 = 1.f - powf(tp->beta1, (float)s->step), c2 = 1.f - powf(tp->beta2, (float)s->step);
+  adamw_kernel<<<(unsigned)((s->n_master + 255) / 256), 256, 0, st>>>(s->master, s->grad, s->adam_m, s->adam_v,
+                                                                     s->n_master, lr, tp->beta1, tp->beta2,
+                                                                     tp->eps, tp->weight_decay, c1, c2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cast_all(s, st);
+}
+
+pk_status check_err(pk_seednet* s, cudaStream_t st) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, s->d_err, sizeof h, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return sn_cuda(e, "seednet");
+  if (h != 0) {
+    cudaMemsetAsync(s->d_err, 0, sizeof(int), st);
+    char buf[128];
+    snprintf(buf, sizeof buf, "tensor-core GEMM pipeline wait timed out (code %d)", h);
+    return sn_fail(PK_ERR_TIMEOUT, buf);
+  }
+  return PK_OK;
+}
+
+// oracle-layout <-> padded-layout parameter copies
+size_t oracle_count(const pk_seednet* s) {
+  size_t n = 0;
+  for (int l = 0; l < s->L; ++l) {
+    const int i = l == 0 ? s->in_dim : s->width;
+    const int o = l == s->L - 1 ? s->out_dim : s->width;
+    n += (size_t)o * i + o;
+  }
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pk_train_params_default(pk_train_params* p) {
+  if (!p) return;
+  p->epochs = 8;
+  p->batch = 8192;
+  p->steps_per_epoch = 1220;
+  p->lr = 1e-3f;
+  p->weight_decay = 1e-4f;
+  p->beta1 = 0.9f;
+  p->beta2 = 0.999f;
+  p->eps = 1e-8f;
+  p->mu = 0.01f;
+  p->reserved = 0;
+  p->seed = 500;
+}
+
+pk_status pk_seednet_create(const pk_robot* rb, int32_t k, const int32_t* target_links, int32_t K,
+                            int32_t width, int32_t depth, uint64_t seed, pk_seednet** out) {
+  if (!out) return sn_fail(PK_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!rb || !target_links) return sn_fail(PK_ERR_INVALID_ARG, "robot or target_links is NULL");
+  if (k < 1 || k > 16) return sn_fail(PK_ERR_INVALID_ARG, "k must be in 1..16");
+  for (int i = 0; i < k; ++i)
+    if (target_links[i] < 0 || target_links[i] >= rb->n_joints)
+      return sn_fail(PK_ERR_INVALID_ARG, "target link out of range");
+  if (K < 1 || K > 64) return sn_fail(PK_ERR_INVALID_ARG, "K must be in 1..64");
+  if (width < 64 || width % 256 != 0 || width > 2048)
+    return sn_fail(PK_ERR_INVALID_ARG, "width must be a multiple of 256 in 256..2048");
+  if (depth < 1 || depth > 8) return sn_fail(PK_ERR_INVALID_ARG, "depth must be in 1..8");
+  if (K * rb->n_dof > 1024) return sn_fail(PK_ERR_INVALID_ARG, "K * n_dof must be <= 1024");
+  if (!get_encode()) return sn_fail(PK_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  pk_seednet* s = new (std::nothrow) pk_seednet;
+  if (!s) return sn_fail(PK_ERR_OOM, "host allocation failed");
+  s->d_robot = (const pk::RobotDev*)rb->d_blob;
+  s->n_dof = rb->n_dof;
+  s->n_joints = rb->n_joints;
+  s->k = k;
+  memcpy(s->links, target_links, k * sizeof(int));
+  s->K = K;
+  s->width = width;
+  s->depth = depth;
+  s->L = depth + 1;
+  s->in_dim = 9 * k;
+  s->in_pad = round_up(s->in_dim, 64);
+  s->out_dim = K * rb->n_dof;
+  s->out_pad = round_up(s->out_dim, 64);
+  s->seed = seed;
+  for (int l = 0; l < s->L; ++l) {
+    s->din.push_back(l == 0 ? s->in_pad : width);
+    s->dout.push_back(l == s->L - 1 ? s->out_pad : width);
+  }
+  size_t off = 0;
+  for (int l = 0; l < s->L; ++l) {
+    s->w_off.push_back(off);
+    off += (size_t)s->dout[l] * s->din[l];
+    s->b_off.push_back(off);
+    off += s->dout[l];
+  }
+  s->n_master = off;
+  for (int j = 0; j < rb->n_joints; ++j)
+    if (rb->var[j] >= 0) {
+      s->lo.push_back(rb->lower[j]);
+      s->hi.push_back(rb->upper[j]);
+    }
+  // initial weights: U(-1/sqrt(fan_in), 1/sqrt(fan_in)) on the real entries, zero padding
+  std::vector<float> h(s->n_master, 0.f);
+  std::mt19937_64 gen(seed);
+  for (int l = 0; l < s->L; ++l) {
+    const int fi = l == 0 ? s->in_dim : width;
+    const int fo = l == s->L - 1 ? s->out_dim : width;
+    const float bound = 1.f / sqrtf((float)fi);
+    std::uniform_real_distribution<float> U(-bound, bound);
+    for (int o = 0; o < fo; ++o) {
+      for (int i = 0; i < fi; ++i) h[s->w_off[l] + (size_t)o * s->din[l] + i] = U(gen);
+      h[s->b_off[l] + o] = U(gen);
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+  al((void**)&s->master, s->n_master * 4);
+  al((void**)&s->grad, s->n_master * 4);
+  al((void**)&s->adam_m, s->n_master * 4);
+  al((void**)&s->adam_v, s->n_master * 4);
+  s->W.assign(s->L, nullptr);
+  s->Wt.assign(s->L, nullptr);
+  for (int l = 0; l < s->L; ++l) {
+    al((void**)&s->W[l], (size_t)s->dout[l] * s->din[l] * 2);
+    al((void**)&s->Wt[l], (size_t)s->dout[l] * s->din[l] * 2);
+  }
+  al((void**)&s->d_lohi, 2 * s->n_dof * 4);
+  al((void**)&s->d_links, 16 * 4);
+  al((void**)&s->d_err, 4);
+  al((void**)&s->d_loss, 4);
+  s->A.assign(depth, nullptr);
+  s->At.assign(depth, nullptr);
+  s->Z.assign(depth, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(s->master, h.data(), s->n_master * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(s->adam_m, 0, s->n_master * 4);
+  if (e == cudaSuccess) e = cudaMemset(s->adam_v, 0, s->n_master * 4);
+  if (e == cudaSuccess) e = cudaMemset(s->d_err, 0, 4);
+  std::vector<float> lohi(s->lo);
+  lohi.insert(lohi.end(), s->hi.begin(), s->hi.end());
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_lohi, lohi.data(), lohi.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_links, s->links, 16 * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cast_all(s, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    pk_seednet_destroy(s);
+    return sn_cuda(e, "pk_seednet_create");
+  }
+  *out = s;
+  return PK_OK;
+}
+
+void pk_seednet_destroy(pk_seednet* s) {
+  if (!s) return;
+  free_acts(s);
+  auto f = [](void* p) { if (p) cudaFree(p); };
+  f(s->master); f(s->grad); f(s->adam_m); f(s->adam_v); f(s->d_lohi); f(s->d_links); f(s->d_err); f(s->d_loss);
+  for (auto* p : s->W) f(p);
+  for (auto* p : s->Wt) f(p);
+  delete s;
+}
+
+int64_t pk_seednet_n_params(const pk_seednet* s) { return s ? (int64_t)oracle_count(s) : -1; }
+
+pk_status pk_seednet_get_params(const pk_seednet* s, float* host, int64_t n) {
+  if (!s || !host) return sn_fail(PK_ERR_INVALID_ARG, "NULL argument");
+  if ((size_t)n != oracle_count(s)) return sn_fail(PK_ERR_INVALID_ARG, "parameter count mismatch");
+  std::vector<float> h(s->n_master);
+  cudaError_t e = cudaMemcpy(h.data(), s->master, s->n_master * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return sn_cuda(e, "pk_seednet_get_params");
+  size_t o = 0;
+  for (int l = 0; l < s->L; ++l) {
+    const int fi = l == 0 ? s->in_dim : s->width;
+    const int fo = l == s->L - 1 ? s->out_dim : s->width;
+    for (int r = 0; r < fo; ++r)
+      for (int c = 0; c < fi; ++c) host[o++] = h[s->w_off[l] + (size_t)r * s->din[l] + c];
+    for (int r = 0; r < fo; ++r) host[o++] = h[s->b_off[l] + r];
+  }
+  return PK_OK;
+}
+
+pk_status pk_seednet_set_params(pk_seednet* s, const float* host, int64_t n) {
+  if (!s || !host) return sn_fail(PK_ERR_INVALID_ARG, "NULL argument");
+  if ((size_t)n != oracle_count(s)) return sn_fail(PK_ERR_INVALID_ARG, "parameter count mismatch");
+  std::vector<float> h(s->n_master, 0.f);
+  size_t o = 0;
+  for (int l = 0; l < s->L; ++l) {
+    const int fi = l == 0 ? s->in_dim : s->width;
+    const int fo = l == s->L - 1 ? s->out_dim : s->width;
+    for (int r = 0; r < fo; ++r)
+      for (int c = 0; c < fi; ++c) h[s->w_off[l] + (size_t)r * s->din[l] + c] = host[o++];
+    for (int r = 0; r < fo; ++r) h[s->b_off[l] + r] = host[o++];
+  }
+  cudaError_t e = cudaMemcpy(s->master, h.data(), s->n_master * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(s->adam_m, 0, s->n_master * 4);
+  if (e == cudaSuccess) e = cudaMemset(s->adam_v, 0, s->n_master * 4);
+  if (e == cudaSuccess) e = cast_all(s, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  s->step = 0;
+  return sn_cuda(e, "pk_seednet_set_params");
+}
+
+pk_status pk_seednet_forward(pk_seednet* s, int32_t batch, const float* d_targets, float* d_y_out,
+                             void* stream) {
+  if (!s) return sn_fail(PK_ERR_INVALID_ARG, "net is NULL");
+  if (batch < 0) return sn_fail(PK_ERR_INVALID_ARG, "batch must be >= 0");
+  if (batch == 0) return PK_OK;
+  if (!d_targets || !d_y_out) return sn_fail(PK_ERR_INVALID_ARG, "NULL device buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int m_pad = round_up(batch, 128);
+  pk_status ps = ensure_acts(s, m_pad);
+  if (ps != PK_OK) return ps;
+  features_kernel<<<(m_pad + 127) / 128, 128, 0, st>>>(d_targets, batch, s->k, s->in_pad, m_pad, s->X, nullptr);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = forward(s, batch, m_pad, false, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(d_y_out, s->out_dim * 4, s->Y, s->out_pad * 4, s->out_dim * 4, batch,
+                          cudaMemcpyDeviceToDevice, st);
+  return sn_cuda(e, "pk_seednet_forward");
+}
+
+pk_status pk_seednet_infer(pk_seednet* s, int32_t batch, const float* d_targets, float* d_seeds_out,
+                           void* stream) {
+  if (!s) return sn_fail(PK_ERR_INVALID_ARG, "net is NULL");
+  if (batch < 0) return sn_fail(PK_ERR_INVALID_ARG, "batch must be >= 0");
+  if (batch == 0) return PK_OK;
+  if (!d_targets || !d_seeds_out) return sn_fail(PK_ERR_INVALID_ARG, "NULL device buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int m_pad = round_up(batch, 128);
+  pk_status ps = ensure_acts(s, m_pad);
+  if (ps != PK_OK) return ps;
+  features_kernel<<<(m_pad + 127) / 128, 128, 0, st>>>(d_targets, batch, s->k, s->in_pad, m_pad, s->X, nullptr);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = forward(s, batch, m_pad, false, st);
+  if (e == cudaSuccess) {
+    const int n = batch * s->K * s->n_dof;
+    seeds_head_kernel<<<(n + 255) / 256, 256, 0, st>>>(s->Y, s->out_pad, batch, s->K, s->n_dof, s->d_lohi,
+                                                       d_seeds_out);
+    e = cudaGetLastError();
+  }
+  return sn_cuda(e, "pk_seednet_infer");
+}
+
+pk_status pk_seednet_loss_grad(pk_seednet* s, int32_t batch, const float* d_targets, const float* d_qstar,
+                               float* host_loss, float* host_grad, void* stream) {
+  if (!s) return sn_fail(PK_ERR_INVALID_ARG, "net is NULL");
+  if (batch < 1 || !d_targets || !d_qstar || !host_loss || !host_grad)
+    return sn_fail(PK_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int m_pad = round_up(batch, 128);
+  pk_status ps = ensure_acts(s, m_pad);
+  if (ps != PK_OK) return ps;
+  features_kernel<<<(m_pad + 127) / 128, 128, 0, st>>>(d_targets, batch, s->k, s->in_pad, m_pad, s->X, s->Xt);
+  cudaError_t e = cudaMemcpyAsync(s->qstar, d_qstar, (size_t)batch * s->n_dof * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_loss, 0, 4, st);
+  if (e == cudaSuccess) e = loss_and_grad(s, batch, m_pad, 0.01f, st);
+  if (e != cudaSuccess) return sn_cuda(e, "pk_seednet_loss_grad");
+  if ((ps = check_err(s, st)) != PK_OK) return ps;
+  float loss = 0.f;
+  std::vector<float> g(s->n_master);
+  e = cudaMemcpy(&loss, s->d_loss, 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(g.data(), s->grad, s->n_master * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return sn_cuda(e, "pk_seednet_loss_grad");
+  *host_loss = loss / batch;
+  size_t o = 0;
+  for (int l = 0; l < s->L; ++l) {
+    const int fi = l == 0 ? s->in_dim : s->width;
+    const int fo = l == s->L - 1 ? s->out_dim : s->width;
+    for (int r = 0; r < fo; ++r)
+      for (int c = 0; c < fi; ++c) host_grad[o++] = g[s->w_off[l] + (size_t)r * s->din[l] + c];
+    for (int r = 0; r < fo; ++r) host_grad[o++] = g[s->b_off[l] + r];
+  }
+  return PK_OK;
+}
+
+pk_status pk_seednet_train(pk_seednet* s, const pk_train_params* tp, float* host_loss, void* stream) {
+  if (!s || !tp) return sn_fail(PK_ERR_INVALID_ARG, "NULL argument");
+  if (tp->epochs < 0 || tp->batch < 128 || tp->steps_per_epoch < 1 || !(tp->lr > 0.f))
+    return sn_fail(PK_ERR_INVALID_ARG, "invalid training parameters");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int M = tp->batch, m_pad = round_up(M, 128);
+  pk_status ps = ensure_acts(s, m_pad);
+  if (ps != PK_OK) return ps;
+  const int64_t total = (int64_t)tp->epochs * tp->steps_per_epoch;
+  int64_t t = 0;
+  for (int ep = 0; ep < tp->epochs; ++ep) {
+    cudaError_t e = cudaMemsetAsync(s->d_loss, 0, 4, st);
+    for (int it = 0; it < tp->steps_per_epoch && e == cudaSuccess; ++it, ++t) {
+      datagen_kernel<<<(m_pad + 127) / 128, 128, 0, st>>>(s->d_robot, s->d_links, s->k, s->d_lohi, s->n_dof,
+                                                          tp->seed, s->step, M, s->in_pad, m_pad, s->X, s->Xt,
+                                                          s->qstar);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = loss_and_grad(s, M, m_pad, tp->mu, st);
+      const float lr = tp->lr * 0.5f * (1.f + cosf(3.14159265f * (float)t / (float)total));
+      if (e == cudaSuccess) e = adamw(s, tp, lr, st);
+    }
+    if (e != cudaSuccess) return sn_cuda(e, "pk_seednet_train");
+    if ((ps = check_err(s, st)) != PK_OK) return ps;
+    if (host_loss) {
+      float l = 0.f;
+      e = cudaMemcpy(&l, s->d_loss, 4, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return sn_cuda(e, "pk_seednet_train");
+      host_loss[ep] = l / ((float)M * tp->steps_per_epoch);
+    }
+  }
+  return sn_cuda(cudaStreamSynchronize(st), "pk_seednet_train");
+}
+
+pk_status pk_seednet_train_step(pk_seednet* s, const pk_train_params* tp, int32_t batch,
+                                const float* d_targets, const float* d_qstar, float lr, void* stream) {
+  if (!s || !tp || batch < 1 || !d_targets || !d_qstar) return sn_fail(PK_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int m_pad = round_up(batch, 128);
+  pk_status ps = ensure_acts(s, m_pad);
+  if (ps != PK_OK) return ps;
+  features_kernel<<<(m_pad + 127) / 128, 128, 0, st>>>(d_targets, batch, s->k, s->in_pad, m_pad, s->X, s->Xt);
+  cudaError_t e = cudaMemcpyAsync(s->qstar, d_qstar, (size_t)batch * s->n_dof * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = loss_and_grad(s, batch, m_pad, tp->mu, st);
+  if (e == cudaSuccess) e = adamw(s, tp, lr, st);
+  if (e != cudaSuccess) return sn_cuda(e, "pk_seednet_train_step");
+  return check_err(s, st);
+}
+
+}  // extern "C"

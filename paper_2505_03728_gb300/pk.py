@@ -46,6 +46,13 @@ class pk_ik_params(C.Structure):
                 ("cancel_siblings", C.c_int32), ("reserved", C.c_int32)]
 
 
+class pk_train_params(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("steps_per_epoch", C.c_int32),
+                ("lr", C.c_float), ("weight_decay", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("mu", C.c_float), ("reserved", C.c_int32),
+                ("seed", C.c_uint64)]
+
+
 _vp = C.c_void_p
 _i32 = C.c_int32
 _i32p = C.POINTER(C.c_int32)
@@ -67,6 +74,17 @@ _SIGNATURES = {
     "pk_ik_solve_noalloc": (_i32, [_vp, C.POINTER(pk_ik_params), _i32, _i32p, _i32p, _i32, _i32, _vp,
                                    _vp, _vp, _vp, _vp, _vp, _vp]),
     "pk_ik_workspace_stats": (_i32, [_vp, C.POINTER(C.c_int64)]),
+    "pk_train_params_default": (None, [_vp]),
+    "pk_seednet_create": (_i32, [_vp, _i32, _i32p, _i32, _i32, _i32, C.c_uint64, C.POINTER(_vp)]),
+    "pk_seednet_destroy": (None, [_vp]),
+    "pk_seednet_n_params": (C.c_int64, [_vp]),
+    "pk_seednet_get_params": (_i32, [_vp, _f32p, C.c_int64]),
+    "pk_seednet_set_params": (_i32, [_vp, _f32p, C.c_int64]),
+    "pk_seednet_forward": (_i32, [_vp, _i32, _vp, _vp, _vp]),
+    "pk_seednet_infer": (_i32, [_vp, _i32, _vp, _vp, _vp]),
+    "pk_seednet_loss_grad": (_i32, [_vp, _i32, _vp, _vp, _f32p, _f32p, _vp]),
+    "pk_seednet_train_step": (_i32, [_vp, _vp, _i32, _vp, _vp, C.c_float, _vp]),
+    "pk_seednet_train": (_i32, [_vp, _vp, _f32p, _vp]),
     "pk_trace_enable": (_i32, [_i32]),
     "pk_trace_summary": (_i32, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
@@ -270,3 +288,89 @@ def pk_ik_solve_noalloc(robot: Robot, params: pk_ik_params, links, kinds, target
                                      _dev(iters, torch.int32, "iters"),
                                      _dev(status, torch.int32, "status"), _stream(stream)))
     return q, err, iters, status
+
+
+def pk_train_params_default(**overrides) -> pk_train_params:
+    p = pk_train_params()
+    lib().pk_train_params_default(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+class SeedNet:
+    """Owns a pk_seednet handle (pk_seednet_create / pk_seednet_destroy)."""
+
+    def __init__(self, robot: Robot, links, K=8, width=512, depth=4, seed=0):
+        links = np.ascontiguousarray(links, np.int32).reshape(-1)
+        h = C.c_void_p()
+        _check(lib().pk_seednet_create(robot.handle, len(links), links.ctypes.data_as(_i32p), K, width,
+                                       depth, seed, C.byref(h)))
+        self.handle = h
+        self.robot = robot
+        self.k, self.K, self.n = len(links), K, robot.n_dof
+        self.width, self.depth = width, depth
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.pk_seednet_destroy(h)
+            self.handle = None
+
+    @property
+    def dims(self):
+        return [9 * self.k] + [self.width] * self.depth + [self.K * self.n]
+
+
+def pk_seednet_n_params(net: SeedNet) -> int:
+    return int(lib().pk_seednet_n_params(net.handle))
+
+
+def pk_seednet_get_params(net: SeedNet) -> np.ndarray:
+    out = np.empty(pk_seednet_n_params(net), np.float32)
+    _check(lib().pk_seednet_get_params(net.handle, out.ctypes.data_as(_f32p), out.size))
+    return out
+
+
+def pk_seednet_set_params(net: SeedNet, params) -> None:
+    params = np.ascontiguousarray(params, np.float32)
+    _check(lib().pk_seednet_set_params(net.handle, params.ctypes.data_as(_f32p), params.size))
+
+
+def pk_seednet_forward(net: SeedNet, targets: torch.Tensor, stream=None) -> torch.Tensor:
+    B = targets.shape[0]
+    y = torch.empty(B, net.K * net.n, device=targets.device)
+    _check(lib().pk_seednet_forward(net.handle, B, _dev(targets, name="targets"), _dev(y, name="y"),
+                                    _stream(stream)))
+    return y
+
+
+def pk_seednet_infer(net: SeedNet, targets: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    B = targets.shape[0]
+    if out is None:
+        out = torch.empty(B, net.K, net.n, device=targets.device)
+    _check(lib().pk_seednet_infer(net.handle, B, _dev(targets, name="targets"), _dev(out, name="seeds"),
+                                  _stream(stream)))
+    return out
+
+
+def pk_seednet_loss_grad(net: SeedNet, targets: torch.Tensor, qstar: torch.Tensor, stream=None):
+    B = targets.shape[0]
+    loss = C.c_float()
+    grad = np.empty(pk_seednet_n_params(net), np.float32)
+    _check(lib().pk_seednet_loss_grad(net.handle, B, _dev(targets, name="targets"), _dev(qstar, name="qstar"),
+                                      C.byref(loss), grad.ctypes.data_as(_f32p), _stream(stream)))
+    return loss.value, grad
+
+
+def pk_seednet_train_step(net: SeedNet, params: pk_train_params, targets, qstar, lr: float, stream=None):
+    _check(lib().pk_seednet_train_step(net.handle, C.byref(params), targets.shape[0],
+                                       _dev(targets, name="targets"), _dev(qstar, name="qstar"),
+                                       C.c_float(lr), _stream(stream)))
+
+
+def pk_seednet_train(net: SeedNet, params: pk_train_params, stream=None) -> np.ndarray:
+    losses = np.zeros(max(1, params.epochs), np.float32)
+    _check(lib().pk_seednet_train(net.handle, C.byref(params), losses.ctypes.data_as(_f32p),
+                                  _stream(stream)))
+    return losses[:params.epochs]
