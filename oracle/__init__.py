@@ -77,9 +77,12 @@ def lib():
             L.or_n_residuals.restype = C.c_int32
             L.or_cholesky_solve.restype = C.c_int32
             L.or_ik_solve.restype = C.c_int32
-            for name in ("or_trajopt_solve", "or_mlp_forward", "or_mlp_loss_grad"):
+            for name in ("or_traj_solve", "or_mlp_forward", "or_mlp_loss_grad", "or_traj_n_residuals",
+                         "or_banded_cholesky", "or_host_cores"):
                 if hasattr(L, name):
                     getattr(L, name).restype = C.c_int32
+            for name in ("or_coll_activation", "or_traj_normal"):
+                getattr(L, name).restype = C.c_double
             _lib = L
     return _lib
 
@@ -293,3 +296,94 @@ def adamw(p, g, m, v, lr, beta1, beta2, eps, wd, step):
         assert a.dtype == np.float64 and a.flags.c_contiguous
     lib().or_adamw(C.c_int64(p.size), _p(p), _p(g), _p(m), _p(v), C.c_double(lr), C.c_double(beta1),
                    C.c_double(beta2), C.c_double(eps), C.c_double(wd), C.c_int64(step))
+
+
+# ---------------------------------------------------------------- trajectory optimisation
+class _TrajParams(C.Structure):
+    _fields_ = [("w_start", C.c_double), ("w_goal_pos", C.c_double), ("w_goal_rot", C.c_double),
+                ("w_vel", C.c_double), ("w_acc", C.c_double), ("w_limit", C.c_double),
+                ("w_coll", C.c_double), ("eta", C.c_double), ("lambda0", C.c_double),
+                ("lambda_min", C.c_double), ("lambda_max", C.c_double), ("nu", C.c_double),
+                ("iters", C.c_int32), ("banded", C.c_int32)]
+
+
+class _TrajScene(C.Structure):
+    _fields_ = [("S", C.c_int32), ("radii", _f64p), ("n_obs", C.c_int32), ("obs", _f64p),
+                ("plane", _f64p)]
+
+
+class TrajParams:
+    def __init__(self, w_start=100.0, w_goal_pos=1.0, w_goal_rot=0.5, w_vel=1.0, w_acc=1.0, w_limit=10.0,
+                 w_coll=10.0, eta=0.02, lambda0=1e-2, lambda_min=1e-10, lambda_max=1e10, nu=2.0, iters=50,
+                 banded=1):
+        self._c = _TrajParams(w_start, w_goal_pos, w_goal_rot, w_vel, w_acc, w_limit, w_coll, eta, lambda0,
+                              lambda_min, lambda_max, nu, iters, banded)
+
+    def __getattr__(self, k):
+        return getattr(self.__dict__["_c"], k)
+
+
+class Scene:
+    """Link spheres (radii [n_dof][S]), obstacles [n_obs][4] and a plane [4]."""
+
+    def __init__(self, radii, obstacles, plane):
+        self.radii = _f64(radii)
+        self.obs = _f64(obstacles).reshape(-1, 4)
+        self.plane = _f64(plane)
+        self._c = _TrajScene(int(self.radii.shape[1]), _p(self.radii), int(self.obs.shape[0]),
+                             _p(self.obs) if self.obs.size else None, _p(self.plane))
+
+
+def coll_activation(d, eta):
+    df = C.c_double()
+    f = lib().or_coll_activation(C.c_double(d), C.c_double(eta), C.byref(df))
+    return f, df.value
+
+
+def traj_n_residuals(robot, scene, T):
+    return int(lib().or_traj_n_residuals(C.byref(robot._c), C.byref(scene._c), T))
+
+
+def traj_residual(robot, params, scene, x, q_start, goal, jacobian=True):
+    x = _f64(x)
+    T = x.shape[0]
+    m = traj_n_residuals(robot, scene, T)
+    r = np.empty(m)
+    J = np.empty((m, x.size)) if jacobian else None
+    lib().or_traj_residual(C.byref(robot._c), C.byref(params._c), C.byref(scene._c), T, _p(x),
+                           _p(_f64(q_start)), _p(_f64(goal)), _p(r), None if J is None else J.ctypes.data_as(_f64p))
+    return (r, J) if jacobian else r
+
+
+def traj_normal(robot, params, scene, x, q_start, goal):
+    x = _f64(x)
+    N = x.size
+    A = np.empty((N, N))
+    g = np.empty(N)
+    f = lib().or_traj_normal(C.byref(robot._c), C.byref(params._c), C.byref(scene._c), x.shape[0], _p(x),
+                             _p(_f64(q_start)), _p(_f64(goal)), A.ctypes.data_as(_f64p), _p(g))
+    return f, A, g
+
+
+def banded_cholesky(A, T, n):
+    A = _f64(A)
+    L = np.empty_like(A)
+    rc = lib().or_banded_cholesky(T, n, A.ctypes.data_as(_f64p), L.ctypes.data_as(_f64p))
+    return L if rc == 0 else None
+
+
+def traj_solve(robot, params, scene, x0, q_start, goals, n_trace=False, n_threads=0):
+    """Batched LM; x0 [B][T][n].  Returns dict(x, cost, threads[, trace, margin])."""
+    x = _f64(x0).copy()
+    B, T, n = x.shape
+    cost = np.empty(B)
+    tr = np.empty((B, params.iters, T, n)) if n_trace else None
+    mg = np.empty(B) if n_trace else None
+    thr = lib().or_traj_solve(C.byref(robot._c), C.byref(params._c), C.byref(scene._c), B, T, _p(x),
+                              _p(_f64(q_start)), _p(_f64(goals)), _p(cost),
+                              None if tr is None else tr.ctypes.data_as(_f64p), _p(mg), int(n_threads))
+    out = dict(x=x, cost=cost, threads=int(thr))
+    if tr is not None:
+        out["trace"] = tr
+        out["margin"] = mg
+    return out

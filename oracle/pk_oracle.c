@@ -576,7 +576,7 @@ static void* pool_worker(void* arg) {
   return NULL;
 }
 
-static int host_cores(void) {
+int32_t or_host_cores(void) {
   cpu_set_t set;
   if (sched_getaffinity(0, sizeof set, &set) == 0) {
     int n = CPU_COUNT(&set);
@@ -593,7 +593,7 @@ int32_t or_ik_solve(const or_robot* rb, const or_ik_params* p, const or_target_s
                     int32_t n_threads) {
   const int nd = or_n_dof(rb);
   const long P = (long)batch * n_seeds;
-  if (n_threads <= 0) n_threads = host_cores();
+  if (n_threads <= 0) n_threads = or_host_cores();
   if (n_threads > P) n_threads = (int)(P > 0 ? P : 1);
   pool_ctx c = {rb, p, ts, batch, n_seeds, nd, trace ? n_trace : 0, targets, seeds,
                 (double*)malloc(sizeof(double) * (P > 0 ? P : 1) * nd),

@@ -99,4 +99,7 @@ int32_t or_ik_solve(const or_robot* rb, const or_ik_params* p, const or_target_s
                     double* per_problem, int32_t n_trace, double* trace, double* margin,
                     int32_t n_threads);
 
+/* Host cores available to this process (affinity mask, else online CPUs). */
+int32_t or_host_cores(void);
+
 #endif

@@ -1,0 +1,381 @@
+/*
+ * trajopt_oracle.c -- FP64 oracle of collision-aware trajectory optimisation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Variables: T joint configurations q_0..q_{T-1}
+ * (Sec. III-B "q_t").  Residuals, each weighted (Sec. III-C):
+ *   start      w_s (q_0 - q_start)                                  7 rows
+ *   goal pose  [w_gp rho; w_gr omega] = log(T_goal^-1 FK(q_{T-1}))   6 rows
+ *   velocity   w_v (q_t - q_{t-1}),           t = 1..T-1  (smoothness cost)
+ *   accel.     w_a (q_{t+1} - 2 q_t + q_{t-1}), t = 1..T-2 (finite-difference
+ *              acceleration, the 3-point stencil)
+ *   limits     w_l hinge(q_t)                 every t
+ *   collision  w_c f(d, eta) per (link sphere, obstacle) and (sphere, plane),
+ *              f the activation of Eq. 1 (d <= 0 takes the linear branch)
+ * Link j carries S spheres with centres p_j + (s + 1/2)/S (p_{j+1} - p_j)
+ * (p_j the origin of joint frame j, p_n the tool frame) and given radii; the
+ * first link's spheres are not tested against the plane.  The solver is LM on
+ * the sum of squared residuals (Sec. III-A) with the same rules as the IK
+ * oracle, a fixed iteration count, and either a dense Cholesky of the full
+ * normal matrix or a block-banded one (the normal matrix is block
+ * pentadiagonal in t).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "pk_oracle.h"
+
+typedef struct {
+  double w_start, w_goal_pos, w_goal_rot, w_vel, w_acc, w_limit, w_coll, eta;
+  double lambda0, lambda_min, lambda_max, nu;
+  int32_t iters;
+  int32_t banded; /* 1: block-banded Cholesky, 0: dense */
+} or_traj_params;
+
+typedef struct {
+  int32_t S;             /* spheres per link */
+  const double* radii;   /* [n_dof][S] */
+  int32_t n_obs;
+  const double* obs;     /* [n_obs][4] centre, radius */
+  const double* plane;   /* [4] unit normal, offset h: signed distance n.c - h */
+} or_traj_scene;
+
+/* Eq. 1 activation and its derivative. */
+double or_coll_activation(double d, double eta, double* df) {
+  if (d <= 0) {
+    if (df) *df = -1.0;
+    return -d + 0.5 * eta;
+  }
+  if (d < eta) {
+    if (df) *df = -(eta - d) / eta;
+    return 0.5 / eta * (eta - d) * (eta - d);
+  }
+  if (df) *df = 0.0;
+  return 0.0;
+}
+
+int32_t or_traj_n_residuals(const or_robot* rb, const or_traj_scene* sc, int32_t T) {
+  const int n = or_n_dof(rb);
+  return n + 6 + n * (T - 1) + n * (T - 2 > 0 ? T - 2 : 0) + n * T + T * n * sc->S * (sc->n_obs + 1);
+}
+
+/* All residual rows and (optionally) the dense Jacobian [m][T*n] (row-major).
+ * Row order: start, goal, velocity (t = 1..), acceleration (t = 1..T-2),
+ * limits (t-major), collisions (t, link, sphere, [obstacles..., plane]). */
+void or_traj_residual(const or_robot* rb, const or_traj_params* p, const or_traj_scene* sc, int32_t T,
+                      const double* x, const double* q_start, const double* goal, double* r, double* J) {
+  const int n = or_n_dof(rb), N = T * n, nj = rb->n_joints;
+  const int m = or_traj_n_residuals(rb, sc, T);
+  if (J) memset(J, 0, sizeof(double) * (size_t)m * N);
+  int row = 0;
+  /* start */
+  for (int i = 0; i < n; ++i, ++row) {
+    r[row] = p->w_start * (x[i] - q_start[i]);
+    if (J) J[(size_t)row * N + i] = p->w_start;
+  }
+  /* goal pose at t = T-1, through the IK residual of one pose target on the last frame */
+  {
+    or_ik_params ip;
+    memset(&ip, 0, sizeof ip);
+    ip.w_pos = p->w_goal_pos;
+    ip.w_rot = p->w_goal_rot;
+    int32_t link = nj - 1;
+    or_target_spec ts = {1, &link, NULL};
+    const int mi = or_n_residuals(rb, &ts);
+    double* ri = (double*)malloc(sizeof(double) * mi);
+    double* Ji = (double*)malloc(sizeof(double) * mi * n);
+    or_ik_residual(rb, &ip, &ts, goal, x + (size_t)(T - 1) * n, ri, Ji);
+    for (int i = 0; i < 6; ++i, ++row) {
+      r[row] = ri[i];
+      if (J)
+        for (int a = 0; a < n; ++a) J[(size_t)row * N + (T - 1) * n + a] = Ji[i * n + a];
+    }
+    free(ri);
+    free(Ji);
+  }
+  /* velocity */
+  for (int t = 1; t < T; ++t)
+    for (int i = 0; i < n; ++i, ++row) {
+      r[row] = p->w_vel * (x[t * n + i] - x[(t - 1) * n + i]);
+      if (J) {
+        J[(size_t)row * N + t * n + i] = p->w_vel;
+        J[(size_t)row * N + (t - 1) * n + i] = -p->w_vel;
+      }
+    }
+  /* acceleration */
+  for (int t = 1; t + 1 < T; ++t)
+    for (int i = 0; i < n; ++i, ++row) {
+      r[row] = p->w_acc * (x[(t + 1) * n + i] - 2 * x[t * n + i] + x[(t - 1) * n + i]);
+      if (J) {
+        J[(size_t)row * N + (t + 1) * n + i] = p->w_acc;
+        J[(size_t)row * N + t * n + i] = -2 * p->w_acc;
+        J[(size_t)row * N + (t - 1) * n + i] = p->w_acc;
+      }
+    }
+  /* limits */
+  {
+    int v = 0;
+    for (int t = 0; t < T; ++t) {
+      v = 0;
+      for (int j = 0; j < nj; ++j) {
+        if (rb->type[j] == OR_JOINT_FIXED) continue;
+        const double q = x[t * n + v], lo = rb->lower[j], hi = rb->upper[j];
+        double h = 0, dh = 0;
+        if (q > hi) { h = q - hi; dh = 1; }
+        if (q < lo) { h = lo - q; dh = -1; }
+        r[row + v] = p->w_limit * h;
+        if (J) J[(size_t)(row + v) * N + t * n + v] = p->w_limit * dh;
+        ++v;
+      }
+      row += n;
+    }
+  }
+  /* collisions: frames of the movable joints and the tool (serial chain) */
+  double* Tf = (double*)malloc(sizeof(double) * 12 * nj);
+  int* jidx = (int*)malloc(sizeof(int) * (n + 1));
+  {
+    int v = 0;
+    for (int j = 0; j < nj; ++j)
+      if (rb->type[j] != OR_JOINT_FIXED) jidx[v++] = j;
+    jidx[n] = nj - 1; /* tool frame closes the last link */
+  }
+  for (int t = 0; t < T; ++t) {
+    or_fk(rb, x + (size_t)t * n, Tf);
+    for (int l = 0; l < n; ++l) {
+      const double* pa = Tf + 12 * jidx[l];
+      const double* pb = Tf + 12 * jidx[l + 1];
+      for (int s = 0; s < sc->S; ++s) {
+        const double al = (s + 0.5) / sc->S;
+        double c[3] = {pa[3] + al * (pb[3] - pa[3]), pa[7] + al * (pb[7] - pa[7]),
+                       pa[11] + al * (pb[11] - pa[11])};
+        const double rad = sc->radii[l * sc->S + s];
+        for (int o = 0; o <= sc->n_obs; ++o, ++row) {
+          double d, nrm[3];
+          if (o < sc->n_obs) {
+            const double* ob = sc->obs + 4 * o;
+            double v3[3] = {c[0] - ob[0], c[1] - ob[1], c[2] - ob[2]};
+            double len = sqrt(v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2]);
+            d = len - rad - ob[3];
+            nrm[0] = v3[0] / len; nrm[1] = v3[1] / len; nrm[2] = v3[2] / len;
+          } else {
+            if (l == 0) { r[row] = 0; continue; } /* first link not tested against the plane */
+            nrm[0] = sc->plane[0]; nrm[1] = sc->plane[1]; nrm[2] = sc->plane[2];
+            d = nrm[0] * c[0] + nrm[1] * c[1] + nrm[2] * c[2] - sc->plane[3] - rad;
+          }
+          double df;
+          r[row] = p->w_coll * or_coll_activation(d, p->eta, &df);
+          if (J && df != 0.0) {
+            /* d(c)/d(q_i) = w_i x (c - p_i) for the joints of links 0..l */
+            for (int i = 0; i <= l; ++i) {
+              const double* Ti = Tf + 12 * jidx[i];
+              double Ri[9] = {Ti[0], Ti[1], Ti[2], Ti[4], Ti[5], Ti[6], Ti[8], Ti[9], Ti[10]};
+              const double* a = rb->axis + 3 * jidx[i];
+              double w[3] = {Ri[0] * a[0] + Ri[1] * a[1] + Ri[2] * a[2], Ri[3] * a[0] + Ri[4] * a[1] + Ri[5] * a[2],
+                             Ri[6] * a[0] + Ri[7] * a[1] + Ri[8] * a[2]};
+              double dc[3];
+              if (rb->type[jidx[i]] == OR_JOINT_REVOLUTE) {
+                double e[3] = {c[0] - Ti[3], c[1] - Ti[7], c[2] - Ti[11]};
+                dc[0] = w[1] * e[2] - w[2] * e[1];
+                dc[1] = w[2] * e[0] - w[0] * e[2];
+                dc[2] = w[0] * e[1] - w[1] * e[0];
+              } else {
+                /* a prismatic joint translates both ends of the link */
+                dc[0] = w[0]; dc[1] = w[1]; dc[2] = w[2];
+              }
+              J[(size_t)row * N + t * n + i] = p->w_coll * df * (nrm[0] * dc[0] + nrm[1] * dc[1] + nrm[2] * dc[2]);
+            }
+          }
+        }
+      }
+    }
+  }
+  free(Tf);
+  free(jidx);
+  (void)m;
+}
+
+/* Normal equations (J^T J [N][N] dense, J^T r [N]) and cost 1/2 |r|^2, formed
+ * row by row from the dense Jacobian of or_traj_residual. */
+static double traj_normal(const or_robot* rb, const or_traj_params* p, const or_traj_scene* sc, int32_t T,
+                          const double* x, const double* qs, const double* goal, double* A, double* g) {
+  const int n = or_n_dof(rb), N = T * n, m = or_traj_n_residuals(rb, sc, T);
+  double* r = (double*)malloc(sizeof(double) * m);
+  double* J = A ? (double*)malloc(sizeof(double) * (size_t)m * N) : NULL;
+  or_traj_residual(rb, p, sc, T, x, qs, goal, r, J);
+  double f = 0;
+  for (int i = 0; i < m; ++i) f += r[i] * r[i];
+  if (A) {
+    memset(A, 0, sizeof(double) * (size_t)N * N);
+    memset(g, 0, sizeof(double) * N);
+    int* nz = (int*)malloc(sizeof(int) * N);
+    for (int i = 0; i < m; ++i) {
+      int k = 0;
+      for (int a = 0; a < N; ++a)
+        if (J[(size_t)i * N + a] != 0.0) nz[k++] = a;
+      for (int u = 0; u < k; ++u) {
+        const double ja = J[(size_t)i * N + nz[u]];
+        g[nz[u]] += ja * r[i];
+        for (int v = 0; v < k; ++v) A[(size_t)nz[u] * N + nz[v]] += ja * J[(size_t)i * N + nz[v]];
+      }
+    }
+    free(nz);
+    free(J);
+  }
+  free(r);
+  return 0.5 * f;
+}
+
+/* Block-banded Cholesky of an SPD matrix with blocks (t, t'), |t - t'| <= 2,
+ * of size n: the three block diagonals are factored step by step in t.
+ * L is written into a dense [N][N] array (zero outside the band).  Returns 0
+ * on success. */
+int32_t or_banded_cholesky(int32_t T, int32_t n, const double* A, double* L) {
+  const int N = T * n;
+  memset(L, 0, sizeof(double) * (size_t)N * N);
+  for (int t = 0; t < T; ++t) {
+    const int c0 = (t >= 2 ? t - 2 : 0) * n; /* first column of the band in block row t */
+    for (int i = t * n; i < (t + 1) * n; ++i) {
+      for (int j = c0; j <= i; ++j) {
+        double s = A[(size_t)i * N + j];
+        /* L[i][k] and L[j][k] are both inside the band only from column k0 on */
+        const int cj = (j / n >= 2 ? j / n - 2 : 0) * n;
+        const int k0 = cj > c0 ? cj : c0;
+        for (int k = k0; k < j; ++k) s -= L[(size_t)i * N + k] * L[(size_t)j * N + k];
+        if (i == j) {
+          if (!(s > 0) || !isfinite(s)) return 1;
+          L[(size_t)i * N + i] = sqrt(s);
+        } else {
+          L[(size_t)i * N + j] = s / L[(size_t)j * N + j];
+        }
+      }
+    }
+  }
+  return 0;
+}
+
+static int dense_cholesky(int N, const double* A, double* L) {
+  memset(L, 0, sizeof(double) * (size_t)N * N);
+  for (int j = 0; j < N; ++j) {
+    double d = A[(size_t)j * N + j];
+    for (int k = 0; k < j; ++k) d -= L[(size_t)j * N + k] * L[(size_t)j * N + k];
+    if (!(d > 0) || !isfinite(d)) return 1;
+    L[(size_t)j * N + j] = sqrt(d);
+    for (int i = j + 1; i < N; ++i) {
+      double s = A[(size_t)i * N + j];
+      for (int k = 0; k < j; ++k) s -= L[(size_t)i * N + k] * L[(size_t)j * N + k];
+      L[(size_t)i * N + j] = s / L[(size_t)j * N + j];
+    }
+  }
+  return 0;
+}
+
+static void chol_solve(int N, const double* L, const double* b, double* x) {
+  double* y = (double*)malloc(sizeof(double) * N);
+  for (int i = 0; i < N; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= L[(size_t)i * N + k] * y[k];
+    y[i] = s / L[(size_t)i * N + i];
+  }
+  for (int i = N - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < N; ++k) s -= L[(size_t)k * N + i] * x[k];
+    x[i] = s / L[(size_t)i * N + i];
+  }
+  free(y);
+}
+
+/* Exported for the pins: normal matrix, gradient and cost at x. */
+double or_traj_normal(const or_robot* rb, const or_traj_params* p, const or_traj_scene* sc, int32_t T,
+                      const double* x, const double* qs, const double* goal, double* A, double* g) {
+  return traj_normal(rb, p, sc, T, x, qs, goal, A, g);
+}
+
+/* LM on one trajectory: x [T][n] in/out; trace (optional) [iters][T][n]. */
+static double traj_lm(const or_robot* rb, const or_traj_params* p, const or_traj_scene* sc, int32_t T,
+                      double* x, const double* qs, const double* goal, double* trace, double* margin) {
+  const int n = or_n_dof(rb), N = T * n;
+  double* A = (double*)malloc(sizeof(double) * (size_t)N * N);
+  double* Al = (double*)malloc(sizeof(double) * (size_t)N * N);
+  double* L = (double*)malloc(sizeof(double) * (size_t)N * N);
+  double* g = (double*)malloc(sizeof(double) * N);
+  double* ng = (double*)malloc(sizeof(double) * N);
+  double* dx = (double*)malloc(sizeof(double) * N);
+  double* xt = (double*)malloc(sizeof(double) * N);
+  double lambda = p->lambda0;
+  double f = traj_normal(rb, p, sc, T, x, qs, goal, A, g);
+  if (margin) *margin = INFINITY;
+  for (int it = 0; it < p->iters; ++it) {
+    memcpy(Al, A, sizeof(double) * (size_t)N * N);
+    for (int i = 0; i < N; ++i) {
+      Al[(size_t)i * N + i] += lambda;
+      ng[i] = -g[i];
+    }
+    const int rc = p->banded ? or_banded_cholesky(T, n, Al, L) : dense_cholesky(N, Al, L);
+    int accepted = 0;
+    if (rc == 0) {
+      chol_solve(N, L, ng, dx);
+      for (int i = 0; i < N; ++i) xt[i] = x[i] + dx[i];
+      const double ft = traj_normal(rb, p, sc, T, xt, qs, goal, NULL, NULL);
+      if (margin && it < 5 && f > 0 && fabs(ft - f) / f < *margin) *margin = fabs(ft - f) / f;
+      if (ft < f) {
+        accepted = 1;
+        memcpy(x, xt, sizeof(double) * N);
+        f = traj_normal(rb, p, sc, T, x, qs, goal, A, g);
+      }
+    }
+    if (accepted) {
+      lambda /= p->nu;
+      if (lambda < p->lambda_min) lambda = p->lambda_min;
+    } else {
+      lambda *= p->nu;
+      if (lambda > p->lambda_max) lambda = p->lambda_max;
+    }
+    if (trace) memcpy(trace + (size_t)it * N, x, sizeof(double) * N);
+  }
+  free(A); free(Al); free(L); free(g); free(ng); free(dx); free(xt);
+  return f;
+}
+
+typedef struct {
+  const or_robot* rb;
+  const or_traj_params* p;
+  const or_traj_scene* sc;
+  int32_t batch, T, n;
+  double* x;
+  const double* qs;
+  const double* goals;
+  double* cost;
+  double* trace;
+  double* margin;
+  long next;
+} traj_pool;
+
+static void* traj_worker(void* arg) {
+  traj_pool* c = (traj_pool*)arg;
+  for (;;) {
+    long b = __atomic_fetch_add(&c->next, 1, __ATOMIC_RELAXED);
+    if (b >= c->batch) break;
+    const size_t N = (size_t)c->T * c->n;
+    c->cost[b] = traj_lm(c->rb, c->p, c->sc, c->T, c->x + b * N, c->qs + b * c->n, c->goals + b * 12,
+                         c->trace ? c->trace + b * (size_t)c->p->iters * N : NULL,
+                         c->margin ? c->margin + b : NULL);
+  }
+  return NULL;
+}
+
+/* Batched LM over trajectories (x [batch][T][n] in/out, q_start [batch][n],
+ * goals [batch][12]); returns the number of threads used. */
+int32_t or_traj_solve(const or_robot* rb, const or_traj_params* p, const or_traj_scene* sc, int32_t batch,
+                      int32_t T, double* x, const double* q_start, const double* goals, double* cost,
+                      double* trace, double* margin, int32_t n_threads) {
+  if (n_threads <= 0) n_threads = or_host_cores();
+  if (n_threads > batch) n_threads = batch > 0 ? batch : 1;
+  traj_pool c = {rb, p, sc, batch, T, or_n_dof(rb), x, q_start, goals, cost, trace, margin, 0};
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * n_threads);
+  for (int i = 0; i < n_threads; ++i) pthread_create(&th[i], NULL, traj_worker, &c);
+  for (int i = 0; i < n_threads; ++i) pthread_join(th[i], NULL);
+  free(th);
+  return n_threads;
+}

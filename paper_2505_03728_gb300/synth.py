@@ -202,3 +202,27 @@ def ik_workload(cfg: dict, batch: int | None = None):
     if batch is not None:
         qt, sd = qt[:batch], sd[:batch]
     return spec, qt, sd
+
+
+TRAJOPT = dict(name="trajopt7_1024xT64", robot_seed=100, n_dof=7, batch=1024, T=64, start_seed=600,
+               goal_seed=603, obstacle_seed=601, n_obstacles=32, sphere_seed=602, spheres_per_link=4,
+               plane=(0.0, 0.0, 1.0, -0.15), reach=1.0, iters=50)
+
+
+def trajopt_workload(cfg: dict, batch: int | None = None):
+    """(robot spec, start configs [B][n], goal configs [B][n], link sphere radii [n][S],
+    obstacles [n_obs][4], plane [4]).  Goal poses are FK of the goal configurations
+    (computed by the callers)."""
+    spec = chain_robot(cfg["robot_seed"], cfg["n_dof"])
+    B = cfg["batch"] if batch is None else batch
+    qs = uniform_q(cfg["start_seed"], cfg["batch"], spec.dof_lower, spec.dof_upper)[:B]
+    qg = uniform_q(cfg["goal_seed"], cfg["batch"], spec.dof_lower, spec.dof_upper)[:B]
+    radii = link_spheres(cfg["sphere_seed"], cfg["n_dof"], cfg["spheres_per_link"])
+    obs = sphere_obstacles(cfg["obstacle_seed"], cfg["n_obstacles"], cfg["reach"])
+    return spec, qs, qg, radii, obs, np.asarray(cfg["plane"], np.float64)
+
+
+def linear_interpolation(q0, q1, T):
+    """[B][T][n] straight line from q0 [B][n] to q1 [B][n] in joint space."""
+    s = np.linspace(0.0, 1.0, T)[None, :, None]
+    return (1.0 - s) * np.asarray(q0)[:, None, :] + s * np.asarray(q1)[:, None, :]
