@@ -216,6 +216,68 @@ pk_status pk_trace_enable(int32_t enable);
 pk_status pk_trace_summary(const char* kernel, double* total_ms, int64_t* launches);
 
 /*
+ * Collision-aware trajectory optimisation (Sec. IV-A, Sec. III-C costs): the
+ * variables are T configurations q_0 .. q_{T-1} of a serial chain; the
+ * residuals, each weighted, are the start configuration, the goal pose
+ * log(T_goal^-1 FK(q_{T-1})) on the last frame, velocity q_t - q_{t-1} and
+ * acceleration q_{t+1} - 2 q_t + q_{t-1} (smoothness), joint-limit hinges, and
+ * the world collision cost w_c f(d, eta) of Eq. 1 for every (link sphere,
+ * obstacle sphere) and (link sphere, plane) pair, d the signed distance
+ * (d <= 0 takes the linear branch).  Link j carries S spheres centred at
+ * p_j + (s + 1/2)/S (p_{j+1} - p_j), p_j the origin of joint frame j and p_n
+ * the tool frame; the first link's spheres are not tested against the plane.
+ * LM with the rules of pk_ik_solve for a fixed number of iterations; the
+ * block-pentadiagonal normal matrix is factored by a block-banded Cholesky.
+ */
+enum { PK_T_OK = 0, PK_T_GOAL_MISSED = 1, PK_T_COLLISION = 2 }; /* status bits */
+
+typedef struct {
+  float w_start;      /* default 100 */
+  float w_goal_pos;   /* default 1 */
+  float w_goal_rot;   /* default 0.5 */
+  float w_vel;        /* default 1 */
+  float w_acc;        /* default 1 */
+  float w_limit;      /* default 10 */
+  float w_coll;       /* default 10 */
+  float eta;          /* collision margin, metres (default 0.02) */
+  float lambda0, lambda_min, lambda_max, nu; /* as pk_ik_params */
+  float tol_pos, tol_rot; /* goal success thresholds (1 mm, 0.5 deg) */
+  int32_t iters;      /* LM iterations (default 50) */
+  int32_t reserved;   /* must be 0 */
+} pk_trajopt_params;
+
+void pk_trajopt_params_default(pk_trajopt_params* p);
+
+/*
+ * pk_trajopt_solve -- batch of trajectories of one serial chain (6 or 7 movable
+ * joints, the goal on the last frame).
+ *   T                  3..64 timesteps
+ *   d_q_start [batch][n], d_goal [batch][12], d_q_init [batch][T][n]
+ *   spheres_per_link   1..4;  d_radii [n][spheres_per_link]
+ *   n_obs 0..64;  d_obs [n_obs][4] centre, radius (shared by the batch)
+ *   plane              host [4]: unit normal and offset h (distance n.c - h)
+ *   d_q_out [batch][T][n], d_cost_out [batch] (1/2 sum r^2),
+ *   d_status_out [batch]: PK_T_* bits (goal missed, any sphere penetrating)
+ */
+pk_status pk_trajopt_solve(const pk_robot* robot, const pk_trajopt_params* params, int32_t batch, int32_t T,
+                           const float* d_q_start, const float* d_goal, const float* d_q_init,
+                           int32_t spheres_per_link, const float* d_radii, int32_t n_obs, const float* d_obs,
+                           const float* plane, float* d_q_out, float* d_cost_out, int32_t* d_status_out,
+                           void* stream);
+
+/*
+ * pk_trajopt_normal -- the normal equations of the same problem at given
+ * trajectories d_q [batch][T][n]: full diagonal blocks of J^T J
+ * d_D_out [batch][T][n][n] (smoothness included), J^T r d_g_out [batch][T][n]
+ * and the cost d_cost_out [batch].  The off-diagonal blocks are the
+ * smoothness terms alone: -(w_vel^2 + 2 w_acc^2 ...) I and w_acc^2 I.
+ */
+pk_status pk_trajopt_normal(const pk_robot* robot, const pk_trajopt_params* params, int32_t batch, int32_t T,
+                            const float* d_q_start, const float* d_goal, const float* d_q,
+                            int32_t spheres_per_link, const float* d_radii, int32_t n_obs, const float* d_obs,
+                            const float* plane, float* d_D_out, float* d_g_out, float* d_cost_out, void* stream);
+
+/*
  * Learned seeds.  The paper's solver starts from given seeds; a seed network
  * adds the learned-seed pattern around it: a SiLU MLP maps target poses to K
  * joint-space proposals that the LM solver (pk_ik_solve) refines.  It runs on

@@ -61,19 +61,35 @@ int32_t or_traj_n_residuals(const or_robot* rb, const or_traj_scene* sc, int32_t
   return n + 6 + n * (T - 1) + n * (T - 2 > 0 ? T - 2 : 0) + n * T + T * n * sc->S * (sc->n_obs + 1);
 }
 
-/* All residual rows and (optionally) the dense Jacobian [m][T*n] (row-major).
+/* Row-sparse Jacobian: every row has at most n nonzeros; row i keeps its
+ * column indices in Jc[i][0..n) (-1 = unused) and values in Jv[i][0..n). */
+#define SETJ(row_, col_, val_)                                     \
+  do {                                                             \
+    if (Jc) {                                                      \
+      int* c_ = Jc + (size_t)(row_) * n;                           \
+      double* v_ = Jv + (size_t)(row_) * n;                        \
+      int k_ = 0;                                                  \
+      while (k_ < n && c_[k_] >= 0 && c_[k_] != (col_)) ++k_;      \
+      c_[k_] = (col_);                                             \
+      v_[k_] = (val_);                                             \
+    }                                                              \
+  } while (0)
+
+/* All residual rows and (optionally) the row-sparse Jacobian.
  * Row order: start, goal, velocity (t = 1..), acceleration (t = 1..T-2),
  * limits (t-major), collisions (t, link, sphere, [obstacles..., plane]). */
-void or_traj_residual(const or_robot* rb, const or_traj_params* p, const or_traj_scene* sc, int32_t T,
-                      const double* x, const double* q_start, const double* goal, double* r, double* J) {
-  const int n = or_n_dof(rb), N = T * n, nj = rb->n_joints;
+void or_traj_residual_sparse(const or_robot* rb, const or_traj_params* p, const or_traj_scene* sc, int32_t T,
+                             const double* x, const double* q_start, const double* goal, double* r, int* Jc,
+                             double* Jv) {
+  const int n = or_n_dof(rb), nj = rb->n_joints;
   const int m = or_traj_n_residuals(rb, sc, T);
-  if (J) memset(J, 0, sizeof(double) * (size_t)m * N);
+  if (Jc)
+    for (size_t i = 0; i < (size_t)m * n; ++i) Jc[i] = -1;
   int row = 0;
   /* start */
   for (int i = 0; i < n; ++i, ++row) {
     r[row] = p->w_start * (x[i] - q_start[i]);
-    if (J) J[(size_t)row * N + i] = p->w_start;
+    SETJ(row, i, p->w_start);
   }
   /* goal pose at t = T-1, through the IK residual of one pose target on the last frame */
   {
@@ -89,8 +105,7 @@ void or_traj_residual(const or_robot* rb, const or_traj_params* p, const or_traj
     or_ik_residual(rb, &ip, &ts, goal, x + (size_t)(T - 1) * n, ri, Ji);
     for (int i = 0; i < 6; ++i, ++row) {
       r[row] = ri[i];
-      if (J)
-        for (int a = 0; a < n; ++a) J[(size_t)row * N + (T - 1) * n + a] = Ji[i * n + a];
+      for (int a = 0; a < n; ++a) SETJ(row, (T - 1) * n + a, Ji[i * n + a]);
     }
     free(ri);
     free(Ji);
@@ -99,20 +114,16 @@ void or_traj_residual(const or_robot* rb, const or_traj_params* p, const or_traj
   for (int t = 1; t < T; ++t)
     for (int i = 0; i < n; ++i, ++row) {
       r[row] = p->w_vel * (x[t * n + i] - x[(t - 1) * n + i]);
-      if (J) {
-        J[(size_t)row * N + t * n + i] = p->w_vel;
-        J[(size_t)row * N + (t - 1) * n + i] = -p->w_vel;
-      }
+      SETJ(row, t * n + i, p->w_vel);
+      SETJ(row, (t - 1) * n + i, -p->w_vel);
     }
   /* acceleration */
   for (int t = 1; t + 1 < T; ++t)
     for (int i = 0; i < n; ++i, ++row) {
       r[row] = p->w_acc * (x[(t + 1) * n + i] - 2 * x[t * n + i] + x[(t - 1) * n + i]);
-      if (J) {
-        J[(size_t)row * N + (t + 1) * n + i] = p->w_acc;
-        J[(size_t)row * N + t * n + i] = -2 * p->w_acc;
-        J[(size_t)row * N + (t - 1) * n + i] = p->w_acc;
-      }
+      SETJ(row, (t + 1) * n + i, p->w_acc);
+      SETJ(row, t * n + i, -2 * p->w_acc);
+      SETJ(row, (t - 1) * n + i, p->w_acc);
     }
   /* limits */
   {
@@ -126,7 +137,7 @@ void or_traj_residual(const or_robot* rb, const or_traj_params* p, const or_traj
         if (q > hi) { h = q - hi; dh = 1; }
         if (q < lo) { h = lo - q; dh = -1; }
         r[row + v] = p->w_limit * h;
-        if (J) J[(size_t)(row + v) * N + t * n + v] = p->w_limit * dh;
+        SETJ(row + v, t * n + v, p->w_limit * dh);
         ++v;
       }
       row += n;
@@ -166,7 +177,7 @@ void or_traj_residual(const or_robot* rb, const or_traj_params* p, const or_traj
           }
           double df;
           r[row] = p->w_coll * or_coll_activation(d, p->eta, &df);
-          if (J && df != 0.0) {
+          if (Jc && df != 0.0) {
             /* d(c)/d(q_i) = w_i x (c - p_i) for the joints of links 0..l */
             for (int i = 0; i <= l; ++i) {
               const double* Ti = Tf + 12 * jidx[i];
@@ -184,7 +195,7 @@ void or_traj_residual(const or_robot* rb, const or_traj_params* p, const or_traj
                 /* a prismatic joint translates both ends of the link */
                 dc[0] = w[0]; dc[1] = w[1]; dc[2] = w[2];
               }
-              J[(size_t)row * N + t * n + i] = p->w_coll * df * (nrm[0] * dc[0] + nrm[1] * dc[1] + nrm[2] * dc[2]);
+              SETJ(row, t * n + i, p->w_coll * df * (nrm[0] * dc[0] + nrm[1] * dc[1] + nrm[2] * dc[2]));
             }
           }
         }
@@ -193,7 +204,22 @@ void or_traj_residual(const or_robot* rb, const or_traj_params* p, const or_traj
   }
   free(Tf);
   free(jidx);
-  (void)m;
+}
+
+/* Dense form of the same residual (small problems; J [m][T*n] row-major). */
+void or_traj_residual(const or_robot* rb, const or_traj_params* p, const or_traj_scene* sc, int32_t T,
+                      const double* x, const double* q_start, const double* goal, double* r, double* J) {
+  const int n = or_n_dof(rb), N = T * n, m = or_traj_n_residuals(rb, sc, T);
+  int* Jc = J ? (int*)malloc(sizeof(int) * (size_t)m * n) : NULL;
+  double* Jv = J ? (double*)malloc(sizeof(double) * (size_t)m * n) : NULL;
+  or_traj_residual_sparse(rb, p, sc, T, x, q_start, goal, r, Jc, Jv);
+  if (J) {
+    memset(J, 0, sizeof(double) * (size_t)m * N);
+    for (int i = 0; i < m; ++i)
+      for (int k = 0; k < n && Jc[(size_t)i * n + k] >= 0; ++k) J[(size_t)i * N + Jc[(size_t)i * n + k]] = Jv[(size_t)i * n + k];
+  }
+  free(Jc);
+  free(Jv);
 }
 
 /* Normal equations (J^T J [N][N] dense, J^T r [N]) and cost 1/2 |r|^2, formed
@@ -202,26 +228,25 @@ static double traj_normal(const or_robot* rb, const or_traj_params* p, const or_
                           const double* x, const double* qs, const double* goal, double* A, double* g) {
   const int n = or_n_dof(rb), N = T * n, m = or_traj_n_residuals(rb, sc, T);
   double* r = (double*)malloc(sizeof(double) * m);
-  double* J = A ? (double*)malloc(sizeof(double) * (size_t)m * N) : NULL;
-  or_traj_residual(rb, p, sc, T, x, qs, goal, r, J);
+  int* Jc = A ? (int*)malloc(sizeof(int) * (size_t)m * n) : NULL;
+  double* Jv = A ? (double*)malloc(sizeof(double) * (size_t)m * n) : NULL;
+  or_traj_residual_sparse(rb, p, sc, T, x, qs, goal, r, Jc, Jv);
   double f = 0;
   for (int i = 0; i < m; ++i) f += r[i] * r[i];
   if (A) {
+    /* J^T J and J^T r, one row's outer product at a time */
     memset(A, 0, sizeof(double) * (size_t)N * N);
     memset(g, 0, sizeof(double) * N);
-    int* nz = (int*)malloc(sizeof(int) * N);
     for (int i = 0; i < m; ++i) {
-      int k = 0;
-      for (int a = 0; a < N; ++a)
-        if (J[(size_t)i * N + a] != 0.0) nz[k++] = a;
-      for (int u = 0; u < k; ++u) {
-        const double ja = J[(size_t)i * N + nz[u]];
-        g[nz[u]] += ja * r[i];
-        for (int v = 0; v < k; ++v) A[(size_t)nz[u] * N + nz[v]] += ja * J[(size_t)i * N + nz[v]];
+      const int* c = Jc + (size_t)i * n;
+      const double* v = Jv + (size_t)i * n;
+      for (int u = 0; u < n && c[u] >= 0; ++u) {
+        g[c[u]] += v[u] * r[i];
+        for (int w = 0; w < n && c[w] >= 0; ++w) A[(size_t)c[u] * N + c[w]] += v[u] * v[w];
       }
     }
-    free(nz);
-    free(J);
+    free(Jc);
+    free(Jv);
   }
   free(r);
   return 0.5 * f;

@@ -249,6 +249,78 @@ pk_status pk_trace_summary(const char* kernel, double* total_ms, int64_t* launch
   return PK_OK;
 }
 
+void pk_trajopt_params_default(pk_trajopt_params* p) {
+  if (!p) return;
+  p->w_start = 100.f;
+  p->w_goal_pos = 1.f;
+  p->w_goal_rot = 0.5f;
+  p->w_vel = 1.f;
+  p->w_acc = 1.f;
+  p->w_limit = 10.f;
+  p->w_coll = 10.f;
+  p->eta = 0.02f;
+  p->lambda0 = 1e-2f;
+  p->lambda_min = 1e-10f;
+  p->lambda_max = 1e10f;
+  p->nu = 2.f;
+  p->tol_pos = 1e-3f;
+  p->tol_rot = 0.5f * 3.14159265358979f / 180.f;
+  p->iters = 50;
+  p->reserved = 0;
+}
+
+static pk_status trajopt_common(const pk_robot* rb, const pk_trajopt_params* p, int32_t batch, int32_t T,
+                                const float* d_q_start, const float* d_goal, const float* d_q,
+                                int32_t S, const float* d_radii, int32_t n_obs, const float* d_obs,
+                                const float* plane, float* d_q_out, float* d_cost_out, int32_t* d_status_out,
+                                float* d_D_out, float* d_g_out, void* stream) {
+  if (!rb || !p) return fail(PK_ERR_INVALID_ARG, "robot or params is NULL");
+  if (!(p->nu > 1.f) || !(p->lambda0 > 0.f) || !(p->lambda_min > 0.f) || !(p->lambda_max >= p->lambda_min))
+    return fail(PK_ERR_INVALID_ARG, "invalid damping parameters");
+  if (p->iters < 0 || p->reserved != 0) return fail(PK_ERR_INVALID_ARG, "iters must be >= 0, reserved 0");
+  if (!(p->eta > 0.f)) return fail(PK_ERR_INVALID_ARG, "eta must be > 0");
+  if (T < 3 || T > pk::kTrajMaxT) return fail(PK_ERR_INVALID_ARG, "T must be in 3..%d", pk::kTrajMaxT);
+  if (S < 1 || S > pk::kTrajMaxS) return fail(PK_ERR_INVALID_ARG, "spheres_per_link must be in 1..%d", pk::kTrajMaxS);
+  if (n_obs < 0 || n_obs > pk::kTrajMaxObs) return fail(PK_ERR_INVALID_ARG, "n_obs must be in 0..%d", pk::kTrajMaxObs);
+  if (!plane || !finite_all(plane, 4)) return fail(PK_ERR_INVALID_ARG, "plane must be 4 finite floats");
+  if (batch < 0) return fail(PK_ERR_INVALID_ARG, "batch must be >= 0");
+  pk::ChainHost ch;
+  pk_status s = fold_chain(rb, rb->n_joints - 1, &ch);
+  if (s != PK_OK) return s;
+  if (ch.n != 6 && ch.n != 7) return fail(PK_ERR_UNSUPPORTED, "trajectory optimisation supports 6 or 7 movable joints");
+  if (batch == 0) return PK_OK;
+  if (!d_q_start || !d_goal || !d_q || !d_radii || (n_obs > 0 && !d_obs) || !d_cost_out)
+    return fail(PK_ERR_INVALID_ARG, "NULL device buffer");
+  pk::TrajParamsDev tp;
+  tp.w_start = p->w_start; tp.w_goal_pos = p->w_goal_pos; tp.w_goal_rot = p->w_goal_rot;
+  tp.w_vel = p->w_vel; tp.w_acc = p->w_acc; tp.w_limit = p->w_limit; tp.w_coll = p->w_coll; tp.eta = p->eta;
+  tp.lambda0 = p->lambda0; tp.lambda_min = p->lambda_min; tp.lambda_max = p->lambda_max; tp.nu = p->nu;
+  tp.tol_pos = p->tol_pos; tp.tol_rot = p->tol_rot;
+  tp.iters = p->iters; tp.T = T; tp.S = S; tp.n_obs = n_obs;
+  for (int i = 0; i < 4; ++i) tp.plane[i] = plane[i];
+  cudaError_t e = pk::launch_trajopt(ch, tp, batch, d_q_start, d_goal, d_q, d_radii, d_obs, d_q_out, d_cost_out,
+                                     d_status_out, d_D_out, d_g_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? PK_OK : cuda_fail(e, "trajectory optimisation launch");
+}
+
+pk_status pk_trajopt_solve(const pk_robot* rb, const pk_trajopt_params* p, int32_t batch, int32_t T,
+                           const float* d_q_start, const float* d_goal, const float* d_q_init, int32_t S,
+                           const float* d_radii, int32_t n_obs, const float* d_obs, const float* plane,
+                           float* d_q_out, float* d_cost_out, int32_t* d_status_out, void* stream) {
+  if (batch > 0 && (!d_q_out || !d_status_out)) return fail(PK_ERR_INVALID_ARG, "NULL device buffer");
+  return trajopt_common(rb, p, batch, T, d_q_start, d_goal, d_q_init, S, d_radii, n_obs, d_obs, plane, d_q_out,
+                        d_cost_out, d_status_out, nullptr, nullptr, stream);
+}
+
+pk_status pk_trajopt_normal(const pk_robot* rb, const pk_trajopt_params* p, int32_t batch, int32_t T,
+                            const float* d_q_start, const float* d_goal, const float* d_q, int32_t S,
+                            const float* d_radii, int32_t n_obs, const float* d_obs, const float* plane,
+                            float* d_D_out, float* d_g_out, float* d_cost_out, void* stream) {
+  if (batch > 0 && (!d_D_out || !d_g_out)) return fail(PK_ERR_INVALID_ARG, "NULL device buffer");
+  return trajopt_common(rb, p, batch, T, d_q_start, d_goal, d_q, S, d_radii, n_obs, d_obs, plane, nullptr,
+                        d_cost_out, nullptr, d_D_out, d_g_out, stream);
+}
+
 pk_status pk_ik_workspace_stats(const void* d_workspace, int64_t* stats_out) {
   if (!d_workspace || !stats_out) return fail(PK_ERR_INVALID_ARG, "NULL argument");
   unsigned long long h[4];

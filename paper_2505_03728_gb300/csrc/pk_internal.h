@@ -79,6 +79,23 @@ cudaError_t launch_chain_residual(const ChainHost& ch, const LmParams& lp, const
 cudaError_t launch_fk(const RobotDev* d_robot, int n_joints, int n_dof, int batch, const float* d_q,
                       float* d_T, cudaStream_t stream);
 
+// Trajectory optimisation (trajopt.cu).
+constexpr int kTrajMaxT = 64;
+constexpr int kTrajMaxObs = 64;
+constexpr int kTrajMaxS = 4;
+
+struct TrajParamsDev {
+  float w_start, w_goal_pos, w_goal_rot, w_vel, w_acc, w_limit, w_coll, eta;
+  float lambda0, lambda_min, lambda_max, nu, tol_pos, tol_rot;
+  int32_t iters, T, S, n_obs;
+  float plane[4];
+};
+
+cudaError_t launch_trajopt(const ChainHost& ch, const TrajParamsDev& tp, int batch, const float* q_start,
+                           const float* goals, const float* q_init, const float* radii, const float* obs,
+                           float* q_out, float* cost_out, int32_t* status_out, float* D_out, float* g_out,
+                           cudaStream_t st);
+
 // Records a thread-local error message (pk_last_error) and returns s.
 pk_status set_error(pk_status s, const char* msg);
 

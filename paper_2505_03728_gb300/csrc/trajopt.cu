@@ -1,0 +1,594 @@
+// trajopt.cu -- collision-aware trajectory optimisation, one CTA per trajectory.
+//
+// Variables q_0 .. q_{T-1} of a serial chain (Sec. III-B).  Residuals (each
+// weighted, Sec. III-C): start configuration, goal pose log(T_goal^-1
+// FK(q_{T-1})), velocity q_t - q_{t-1} and acceleration q_{t+1} - 2 q_t + q_{t-1}
+// (smoothness, finite differences), joint-limit hinges, and the world
+// collision cost: for every link sphere and every obstacle sphere (and the
+// ground plane), w_c f(d, eta) with f the activation of Eq. 1.  Link j carries
+// S spheres centred at p_j + (s + 1/2)/S (p_{j+1} - p_j).  LM (Sec. III-A) with
+// a fixed iteration count.
+//
+// The normal matrix is block pentadiagonal in t: collision, limit, start and
+// goal rows touch one timestep (full N x N diagonal blocks D_t), while the
+// smoothness rows add s_t I on the diagonal and the scalar multiples b_t I and
+// c_t I on the first and second sub-diagonals.  Per LM iteration:
+//   1. timestep threads run FK, limits, smoothness, start and goal terms;
+//      warps then take timesteps and their lanes take link spheres, test them
+//      against every obstacle and the plane, and reduce the active rows' rank-1
+//      updates into D_t and J^T r;
+//   2. accept/reject and the lambda update;
+//   3. block-banded Cholesky, serial in t, each step a handful of N x N block
+//      products spread over N*N threads (the inverse of each diagonal factor is
+//      kept so that the off-diagonal factors are plain products);
+//   4. block forward and backward substitution, then the next candidate.
+#include "pk_chain.cuh"
+#include "pk_internal.h"
+#include "pk_math.cuh"
+
+namespace pk {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+template <int N>
+struct TrajSmem {
+  static constexpr int NT = N * (N + 1) / 2;
+  float x[2][kTrajMaxT][8];    // current / candidate trajectories
+  float D[2][kTrajMaxT][NT];   // diagonal blocks of J^T J without smoothness
+  float g[2][kTrajMaxT][8];    // J^T r
+  float f[2], mind[2], gpe[2], gre[2];
+  float p[kTrajMaxT][N + 1][3];  // joint origins and tool point (world), candidate
+  float w[kTrajMaxT][N][3];      // joint axes (world), candidate
+  float Linv[kTrajMaxT][NT];     // inverse of the diagonal Cholesky factor (lower)
+  float L1[kTrajMaxT][N][N];     // factor block (t, t-1)
+  float L2[kTrajMaxT][N][N];     // factor block (t, t-2)
+  float M[N][N];
+  float Sch[NT];
+  float tmp[8];
+  float y[kTrajMaxT][8];
+  alignas(16) float obs[kTrajMaxObs][4];
+  float rad[N][kTrajMaxS];
+  float qs[8];
+  float Tgi[12];
+  float red_f[kWarps], red_d[kWarps];
+  int chol_fail;
+};
+
+struct Acc {
+  float f, mind;
+};
+
+__device__ __forceinline__ float coll_act(float d, float eta, float* df) {
+  if (d <= 0.f) {
+    *df = -1.f;
+    return -d + 0.5f * eta;
+  }
+  if (d < eta) {
+    const float e = eta - d;
+    *df = -e / eta;
+    return 0.5f / eta * e * e;
+  }
+  *df = 0.f;
+  return 0.f;
+}
+
+// Smoothness scalars of the normal matrix: diagonal s_t, first sub-diagonal
+// b_t (block (t, t-1)), second sub-diagonal c_t (block (t, t-2)).
+__device__ __forceinline__ void smooth_scalars(const TrajParamsDev& tp, int t, float* s, float* b, float* c) {
+  const int T = tp.T;
+  const float v2 = tp.w_vel * tp.w_vel, a2 = tp.w_acc * tp.w_acc;
+  auto in = [&](int u) { return (u >= 1 && u <= T - 2) ? 1.f : 0.f; };  // acceleration residual u exists
+  *s = v2 * ((t >= 1 ? 1.f : 0.f) + (t <= T - 2 ? 1.f : 0.f)) + a2 * (in(t + 1) + 4.f * in(t) + in(t - 1));
+  *b = -v2 * (t >= 1 ? 1.f : 0.f) - 2.f * a2 * (in(t) + in(t - 1));
+  *c = a2 * in(t - 1) * (t >= 2 ? 1.f : 0.f);
+}
+
+// Per-timestep terms (thread t): FK, limits, smoothness, start and goal.
+template <int N>
+__device__ void eval_timestep(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N>& S, int buf, int t,
+                              float& fpart) {
+  constexpr int NT = N * (N + 1) / 2;
+  const int T = tp.T;
+  float q[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) q[j] = S.x[buf][t][j];
+  float D[NT], g[N];
+#pragma unroll
+  for (int i = 0; i < NT; ++i) D[i] = 0.f;
+#pragma unroll
+  for (int j = 0; j < N; ++j) g[j] = 0.f;
+  float acc = 0.f;
+  // FK in the world frame
+  Rt Tw;
+  rt_identity(Tw);
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if (rc.orot & (1u << j)) {
+      Rt O;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) O.r[i] = rc.o_r[j][i];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) O.t[i] = rc.o_t[j][i];
+      rt_mul(Tw, O, Tw);
+    } else {
+      rt_translate(Tw, rc.o_t[j]);
+    }
+    float u[3];
+    mat_vec(Tw.r, rc.a[j], u);
+    if (rc.prism & (1u << j)) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Tw.t[i] = fmaf(u[i], q[j], Tw.t[i]);
+    } else {
+      float s, c;
+      sincos_rad(q[j], &s, &c);
+      rot_joint(Tw.r, u, rc.a[j], s, c);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      S.w[t][j][i] = u[i];
+      S.p[t][j][i] = Tw.t[i];
+    }
+  }
+  if (rc.toolrot) {
+    Rt O;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) O.r[i] = rc.tool_r[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) O.t[i] = rc.tool_t[i];
+    rt_mul(Tw, O, Tw);
+  } else {
+    rt_translate(Tw, rc.tool_t);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) S.p[t][N][i] = Tw.t[i];
+  // joint limits
+  const float wl2 = tp.w_limit * tp.w_limit;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    float h = 0.f, d = 0.f;
+    if (q[j] > rc.hi[j]) { h = q[j] - rc.hi[j]; d = 1.f; }
+    if (q[j] < rc.lo[j]) { h = rc.lo[j] - q[j]; d = -1.f; }
+    acc = fmaf(wl2, h * h, acc);
+    D[tri(j, j)] += wl2 * d * d;
+    g[j] = fmaf(wl2 * d, h, g[j]);
+  }
+  // smoothness (residuals owned by this t; gradient from every residual touching t)
+  const float v2 = tp.w_vel * tp.w_vel, a2 = tp.w_acc * tp.w_acc;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const float xm = t >= 1 ? S.x[buf][t - 1][j] : 0.f;
+    const float xp = t + 1 < T ? S.x[buf][t + 1][j] : 0.f;
+    const float xm2 = t >= 2 ? S.x[buf][t - 2][j] : 0.f;
+    const float xp2 = t + 2 < T ? S.x[buf][t + 2][j] : 0.f;
+    const float x0 = q[j];
+    float gj = 0.f;
+    if (t >= 1) {
+      const float v = x0 - xm;
+      acc = fmaf(v2, v * v, acc);
+      gj = fmaf(v2, v, gj);
+    }
+    if (t + 1 < T) gj = fmaf(-v2, xp - x0, gj);
+    if (t >= 1 && t <= T - 2) {
+      const float a = xp - 2.f * x0 + xm;
+      acc = fmaf(a2, a * a, acc);
+      gj = fmaf(-2.f * a2, a, gj);
+    }
+    if (t - 1 >= 1 && t - 1 <= T - 2) gj = fmaf(a2, x0 - 2.f * xm + xm2, gj);
+    if (t + 1 >= 1 && t + 1 <= T - 2) gj = fmaf(a2, xp2 - 2.f * xp + x0, gj);
+    g[j] += gj;
+  }
+  // start configuration
+  if (t == 0) {
+    const float s2 = tp.w_start * tp.w_start;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const float r = q[j] - S.qs[j];
+      acc = fmaf(s2, r * r, acc);
+      D[tri(j, j)] += s2;
+      g[j] = fmaf(s2, r, g[j]);
+    }
+  }
+  // goal pose on the last timestep: r = w (.) log(T_goal^-1 T_ee)
+  if (t == T - 1) {
+    Rt Gi, E;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) Gi.r[i * 3 + k] = S.Tgi[i * 4 + k];
+      Gi.t[i] = S.Tgi[i * 4 + 3];
+    }
+    rt_mul(Gi, Tw, E);
+    float xi[6];
+    const float th = se3_log(E, xi);
+    S.gpe[buf] = sqrtf(E.t[0] * E.t[0] + E.t[1] * E.t[1] + E.t[2] * E.t[2]);
+    S.gre[buf] = th;
+    const float wv[6] = {tp.w_goal_pos, tp.w_goal_pos, tp.w_goal_pos, tp.w_goal_rot, tp.w_goal_rot, tp.w_goal_rot};
+    float A[9], B[9];
+    se3_jlinv_blocks(xi, xi + 3, th, A, B);
+    float J[6][N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      // world twist of joint j expressed in the goal frame
+      float pw[3] = {S.p[t][j][0], S.p[t][j][1], S.p[t][j][2]};
+      float ww[3] = {S.w[t][j][0], S.w[t][j][1], S.w[t][j][2]};
+      float pg[3], wg[3];
+      mat_vec(Gi.r, pw, pg);
+      pg[0] += Gi.t[0]; pg[1] += Gi.t[1]; pg[2] += Gi.t[2];
+      mat_vec(Gi.r, ww, wg);
+      float top[3], bot[3];
+      if (rc.prism & (1u << j)) {
+        mat_vec(A, wg, top);
+        bot[0] = bot[1] = bot[2] = 0.f;
+      } else {
+        float v[3], t1[3], t2[3];
+        cross3(pg, wg, v);
+        mat_vec(A, v, t1);
+        mat_vec(B, wg, t2);
+        mat_vec(A, wg, bot);
+        top[0] = t1[0] + t2[0]; top[1] = t1[1] + t2[1]; top[2] = t1[2] + t2[2];
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        J[i][j] = wv[i] * top[i];
+        J[3 + i][j] = wv[3 + i] * bot[i];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      const float rr = wv[r] * xi[r];
+      acc = fmaf(rr, rr, acc);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        g[i] = fmaf(J[r][i], rr, g[i]);
+#pragma unroll
+        for (int k = 0; k <= i; ++k) D[tri(i, k)] = fmaf(J[r][i], J[r][k], D[tri(i, k)]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NT; ++i) S.D[buf][t][i] = D[i];
+#pragma unroll
+  for (int j = 0; j < N; ++j) S.g[buf][t][j] = g[j];
+  fpart += acc;
+}
+
+// Collision terms of timestep t, one link sphere per lane (lanes >= N*S idle).
+template <int N>
+__device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N>& S, int buf, int t,
+                                int lane, float& fpart, float& mind) {
+  constexpr int NT = N * (N + 1) / 2;
+  const int nsph = N * tp.S;
+  float Dl[NT], gl[N];
+#pragma unroll
+  for (int i = 0; i < NT; ++i) Dl[i] = 0.f;
+#pragma unroll
+  for (int j = 0; j < N; ++j) gl[j] = 0.f;
+  bool any = false;
+  if (lane < nsph) {
+    const int l = lane / tp.S, s = lane % tp.S;
+    const float al = (s + 0.5f) / (float)tp.S;
+    float c[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c[i] = fmaf(al, S.p[t][l + 1][i] - S.p[t][l][i], S.p[t][l][i]);
+    const float rad = S.rad[l][s];
+    const float wc = tp.w_coll;
+    for (int o = 0; o <= tp.n_obs; ++o) {
+      float d, nrm[3];
+      if (o < tp.n_obs) {
+        const float4 ob = *reinterpret_cast<const float4*>(S.obs[o]);
+        const float v0 = c[0] - ob.x, v1 = c[1] - ob.y, v2 = c[2] - ob.z;
+        const float len = sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
+        d = len - rad - ob.w;
+        const float inv = 1.f / len;
+        nrm[0] = v0 * inv; nrm[1] = v1 * inv; nrm[2] = v2 * inv;
+      } else {
+        if (l == 0) continue;  // the first link is not tested against the plane
+        nrm[0] = tp.plane[0]; nrm[1] = tp.plane[1]; nrm[2] = tp.plane[2];
+        d = nrm[0] * c[0] + nrm[1] * c[1] + nrm[2] * c[2] - tp.plane[3] - rad;
+      }
+      mind = fminf(mind, d);
+      float df;
+      const float fa = coll_act(d, tp.eta, &df);
+      if (df == 0.f) continue;
+      any = true;
+      const float r = wc * fa;
+      fpart = fmaf(r, r, fpart);
+      float jr[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float dc;
+        if (i > l) {
+          dc = 0.f;
+        } else if (rc.prism & (1u << i)) {
+          dc = S.w[t][i][0] * nrm[0] + S.w[t][i][1] * nrm[1] + S.w[t][i][2] * nrm[2];
+        } else {
+          // n . (w_i x (c - p_i)) = w_i . ((c - p_i) x n)
+          const float e0 = c[0] - S.p[t][i][0], e1 = c[1] - S.p[t][i][1], e2 = c[2] - S.p[t][i][2];
+          const float x0 = e1 * nrm[2] - e2 * nrm[1], x1 = e2 * nrm[0] - e0 * nrm[2], x2 = e0 * nrm[1] - e1 * nrm[0];
+          dc = S.w[t][i][0] * x0 + S.w[t][i][1] * x1 + S.w[t][i][2] * x2;
+        }
+        jr[i] = wc * df * dc;
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        gl[i] = fmaf(jr[i], r, gl[i]);
+#pragma unroll
+        for (int k = 0; k <= i; ++k) Dl[tri(i, k)] = fmaf(jr[i], jr[k], Dl[tri(i, k)]);
+      }
+    }
+  }
+  if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+    for (int i = 0; i < NT; ++i)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) Dl[i] += __shfl_xor_sync(0xffffffffu, Dl[i], o);
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) gl[j] += __shfl_xor_sync(0xffffffffu, gl[j], o);
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < NT; ++i) S.D[buf][t][i] += Dl[i];
+#pragma unroll
+      for (int j = 0; j < N; ++j) S.g[buf][t][j] += gl[j];
+    }
+  }
+}
+
+// Cost, J^T J diagonal blocks and J^T r of trajectory buffer `buf`.
+template <int N>
+__device__ void evaluate(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N>& S, int buf) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float fpart = 0.f, mind = INFINITY;
+  for (int t = tid; t < tp.T; t += kThreads) eval_timestep<N>(rc, tp, S, buf, t, fpart);
+  __syncthreads();
+  for (int t = warp; t < tp.T; t += kWarps) eval_collisions<N>(rc, tp, S, buf, t, lane, fpart, mind);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fpart += __shfl_xor_sync(0xffffffffu, fpart, o);
+    mind = fminf(mind, __shfl_xor_sync(0xffffffffu, mind, o));
+  }
+  if (lane == 0) {
+    S.red_f[warp] = fpart;
+    S.red_d[warp] = mind;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float f = 0.f, m = INFINITY;
+    for (int w = 0; w < kWarps; ++w) {
+      f += S.red_f[w];
+      m = fminf(m, S.red_d[w]);
+    }
+    S.f[buf] = 0.5f * f;
+    S.mind[buf] = m;
+  }
+  __syncthreads();
+}
+
+// Block-banded Cholesky of D[buf] + smoothness + lambda I, then the two block
+// substitutions for dq = -(A)^-1 g; the step lands in S.y.  Returns false if a
+// diagonal block was not positive definite.
+template <int N>
+__device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N>& S, int buf, float lam) {
+  constexpr int NT = N * (N + 1) / 2;
+  const int tid = threadIdx.x, T = tp.T;
+  if (tid == 0) S.chol_fail = 0;
+  for (int t = 0; t < T; ++t) {
+    float sd, bd, cd;
+    smooth_scalars(tp, t, &sd, &bd, &cd);
+    // (1) L2_t = c_t Linv_{t-2}^T and M = b_t I - L2_t L1_{t-1}^T
+    if (tid < N * N && t >= 1) {
+      const int i = tid / N, j = tid % N;
+      float m = (i == j) ? bd : 0.f;
+      if (t >= 2) {
+        S.L2[t][i][j] = (j >= i) ? cd * S.Linv[t - 2][tri(j, i)] : 0.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          if (k >= i) m = fmaf(-cd * S.Linv[t - 2][tri(k, i)], S.L1[t - 1][j][k], m);
+      }
+      S.M[i][j] = m;
+    }
+    __syncthreads();
+    // (2) L1_t = M Linv_{t-1}^T
+    if (tid < N * N && t >= 1) {
+      const int i = tid / N, j = tid % N;
+      float v = 0.f;
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        if (k <= j) v = fmaf(S.M[i][k], S.Linv[t - 1][tri(j, k)], v);
+      S.L1[t][i][j] = v;
+    }
+    __syncthreads();
+    // (3) Schur complement S = D_t + (s_t + lambda) I - L1 L1^T - L2 L2^T (lower)
+    if (tid < NT) {
+      int i = 0;
+      while ((i + 1) * (i + 2) / 2 <= tid) ++i;
+      const int j = tid - i * (i + 1) / 2;
+      float v = S.D[buf][t][tid] + ((i == j) ? sd + lam : 0.f);
+      if (t >= 1)
+#pragma unroll
+        for (int k = 0; k < N; ++k) v = fmaf(-S.L1[t][i][k], S.L1[t][j][k], v);
+      if (t >= 2)
+#pragma unroll
+        for (int k = 0; k < N; ++k) v = fmaf(-S.L2[t][i][k], S.L2[t][j][k], v);
+      S.Sch[tid] = v;
+    }
+    __syncthreads();
+    // (4) dense Cholesky of the Schur complement (lane 0), then its inverse
+    //     (lane j computes column j)
+    if (tid == 0) {
+      float L[NT];
+#pragma unroll
+      for (int i = 0; i < NT; ++i) L[i] = S.Sch[i];
+      const bool ok = chol_packed<N>(L);  // diagonal slots hold 1 / L_ii
+      if (!ok) S.chol_fail = 1;
+#pragma unroll
+      for (int i = 0; i < NT; ++i) S.Sch[i] = L[i];
+    }
+    __syncwarp();
+    if (tid < N) {
+      const int j = tid;
+      float col[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float v = (i == j) ? 1.f : 0.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          if (k >= j && k < i) v = fmaf(-S.Sch[tri(i, k)], col[k], v);
+        col[i] = (i >= j) ? v * S.Sch[tri(i, i)] : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i >= j) S.Linv[t][tri(i, j)] = col[i];
+    }
+    __syncthreads();
+  }
+  const bool ok = S.chol_fail == 0;
+  // forward substitution: y_t = Linv_t (-g_t - L1_t y_{t-1} - L2_t y_{t-2})
+  for (int t = 0; t < T; ++t) {
+    if (tid < N) {
+      float v = -S.g[buf][t][tid];
+      if (t >= 1)
+#pragma unroll
+        for (int k = 0; k < N; ++k) v = fmaf(-S.L1[t][tid][k], S.y[t - 1][k], v);
+      if (t >= 2)
+#pragma unroll
+        for (int k = 0; k < N; ++k) v = fmaf(-S.L2[t][tid][k], S.y[t - 2][k], v);
+      S.tmp[tid] = v;
+    }
+    __syncthreads();
+    if (tid < N) {
+      float v = 0.f;
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        if (k <= tid) v = fmaf(S.Linv[t][tri(tid, k)], S.tmp[k], v);
+      S.y[t][tid] = v;
+    }
+    __syncthreads();
+  }
+  // backward substitution: dq_t = Linv_t^T (y_t - L1_{t+1}^T dq_{t+1} - L2_{t+2}^T dq_{t+2})
+  for (int t = T - 1; t >= 0; --t) {
+    if (tid < N) {
+      float v = S.y[t][tid];
+      if (t + 1 < T)
+#pragma unroll
+        for (int k = 0; k < N; ++k) v = fmaf(-S.L1[t + 1][k][tid], S.y[t + 1][k], v);
+      if (t + 2 < T)
+#pragma unroll
+        for (int k = 0; k < N; ++k) v = fmaf(-S.L2[t + 2][k][tid], S.y[t + 2][k], v);
+      S.tmp[tid] = v;
+    }
+    __syncthreads();
+    if (tid < N) {
+      float v = 0.f;
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        if (k >= tid) v = fmaf(S.Linv[t][tri(k, tid)], S.tmp[k], v);
+      S.y[t][tid] = v;
+    }
+    __syncthreads();
+  }
+  return ok;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) trajopt_kernel(
+    const __grid_constant__ ChainC<N> rc, const __grid_constant__ TrajParamsDev tp, const float* __restrict__ q_start,
+    const float* __restrict__ goals, const float* __restrict__ q_init, const float* __restrict__ radii,
+    const float* __restrict__ obs, float* __restrict__ q_out, float* __restrict__ cost_out,
+    int32_t* __restrict__ status_out, float* __restrict__ D_out, float* __restrict__ g_out) {
+  extern __shared__ float4 smem_f4[];
+  TrajSmem<N>& S = *reinterpret_cast<TrajSmem<N>*>(smem_f4);
+  const int b = blockIdx.x, tid = threadIdx.x, T = tp.T;
+  // inputs
+  for (int i = tid; i < T * N; i += kThreads) S.x[0][i / N][i % N] = q_init[(size_t)b * T * N + i];
+  for (int i = tid; i < tp.n_obs * 4; i += kThreads) S.obs[i / 4][i % 4] = obs[i];
+  for (int i = tid; i < N * tp.S; i += kThreads) S.rad[i / tp.S][i % tp.S] = radii[i];
+  if (tid < N) S.qs[tid] = q_start[(size_t)b * N + tid];
+  if (tid == 0) {
+    Rt G, Gi;
+    rt_load(goals + (size_t)b * 12, G);
+    rt_inv(G, Gi);
+    rt_store(S.Tgi, Gi);
+  }
+  __syncthreads();
+  evaluate<N>(rc, tp, S, 0);
+  if (D_out) {
+    // normal equations only: full diagonal blocks (smoothness included) and J^T r
+    for (int i = tid; i < T * N * N; i += kThreads) {
+      const int t = i / (N * N), r = (i / N) % N, c = i % N;
+      float sd, bd, cd;
+      smooth_scalars(tp, t, &sd, &bd, &cd);
+      const float v = (r >= c) ? S.D[0][t][tri(r, c)] : S.D[0][t][tri(c, r)];
+      D_out[(size_t)b * T * N * N + i] = v + ((r == c) ? sd : 0.f);
+    }
+    for (int i = tid; i < T * N; i += kThreads) g_out[(size_t)b * T * N + i] = S.g[0][i / N][i % N];
+    if (tid == 0) cost_out[b] = S.f[0];
+    return;
+  }
+  int u = 0;  // buffer of the accepted trajectory
+  float lam = tp.lambda0;
+  for (int it = 0; it < tp.iters; ++it) {
+    const bool ok = banded_solve<N>(tp, S, u, lam);
+    if (ok) {
+      const int c = u ^ 1;
+      for (int i = tid; i < T * N; i += kThreads) S.x[c][i / N][i % N] = S.x[u][i / N][i % N] + S.y[i / N][i % N];
+      __syncthreads();
+      evaluate<N>(rc, tp, S, c);
+      if (S.f[c] < S.f[u]) {
+        u = c;
+        lam = fmaxf(lam / tp.nu, tp.lambda_min);
+      } else {
+        lam = fminf(lam * tp.nu, tp.lambda_max);
+      }
+    } else {
+      lam = fminf(lam * tp.nu, tp.lambda_max);
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < T * N; i += kThreads) q_out[(size_t)b * T * N + i] = S.x[u][i / N][i % N];
+  if (tid == 0) {
+    cost_out[b] = S.f[u];
+    int st = 0;
+    if (!(S.gpe[u] <= tp.tol_pos && S.gre[u] <= tp.tol_rot)) st |= PK_T_GOAL_MISSED;
+    if (!(S.mind[u] >= 0.f)) st |= PK_T_COLLISION;
+    status_out[b] = st;
+  }
+}
+
+template <int N>
+cudaError_t trajopt_launch(const ChainHost& ch, const TrajParamsDev& tp, int batch, const float* q_start,
+                           const float* goals, const float* q_init, const float* radii, const float* obs,
+                           float* q_out, float* cost_out, int32_t* status_out, float* D_out, float* g_out,
+                           cudaStream_t st) {
+  const size_t smem = sizeof(TrajSmem<N>);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(trajopt_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const ChainC<N> rc = chain_const<N>(ch);
+  TraceScope tr("trajopt", st);
+  trajopt_kernel<N><<<batch, kThreads, smem, st>>>(rc, tp, q_start, goals, q_init, radii, obs, q_out, cost_out,
+                                                   status_out, D_out, g_out);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_trajopt(const ChainHost& ch, const TrajParamsDev& tp, int batch, const float* q_start,
+                           const float* goals, const float* q_init, const float* radii, const float* obs,
+                           float* q_out, float* cost_out, int32_t* status_out, float* D_out, float* g_out,
+                           cudaStream_t st) {
+  switch (ch.n) {
+    case 6: return trajopt_launch<6>(ch, tp, batch, q_start, goals, q_init, radii, obs, q_out, cost_out, status_out, D_out, g_out, st);
+    case 7: return trajopt_launch<7>(ch, tp, batch, q_start, goals, q_init, radii, obs, q_out, cost_out, status_out, D_out, g_out, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace pk

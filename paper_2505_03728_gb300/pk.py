@@ -46,6 +46,14 @@ class pk_ik_params(C.Structure):
                 ("cancel_siblings", C.c_int32), ("reserved", C.c_int32)]
 
 
+class pk_trajopt_params(C.Structure):
+    _fields_ = [("w_start", C.c_float), ("w_goal_pos", C.c_float), ("w_goal_rot", C.c_float),
+                ("w_vel", C.c_float), ("w_acc", C.c_float), ("w_limit", C.c_float), ("w_coll", C.c_float),
+                ("eta", C.c_float), ("lambda0", C.c_float), ("lambda_min", C.c_float),
+                ("lambda_max", C.c_float), ("nu", C.c_float), ("tol_pos", C.c_float), ("tol_rot", C.c_float),
+                ("iters", C.c_int32), ("reserved", C.c_int32)]
+
+
 class pk_train_params(C.Structure):
     _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("steps_per_epoch", C.c_int32),
                 ("lr", C.c_float), ("weight_decay", C.c_float), ("beta1", C.c_float),
@@ -75,6 +83,11 @@ _SIGNATURES = {
                                    _vp, _vp, _vp, _vp, _vp, _vp]),
     "pk_ik_workspace_stats": (_i32, [_vp, C.POINTER(C.c_int64)]),
     "pk_train_params_default": (None, [_vp]),
+    "pk_trajopt_params_default": (None, [_vp]),
+    "pk_trajopt_solve": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _i32, _vp, _f32p, _vp, _vp,
+                                _vp, _vp]),
+    "pk_trajopt_normal": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _i32, _vp, _f32p, _vp, _vp,
+                                 _vp, _vp]),
     "pk_seednet_create": (_i32, [_vp, _i32, _i32p, _i32, _i32, _i32, C.c_uint64, C.POINTER(_vp)]),
     "pk_seednet_destroy": (None, [_vp]),
     "pk_seednet_n_params": (C.c_int64, [_vp]),
@@ -374,3 +387,54 @@ def pk_seednet_train(net: SeedNet, params: pk_train_params, stream=None) -> np.n
     _check(lib().pk_seednet_train(net.handle, C.byref(params), losses.ctypes.data_as(_f32p),
                                   _stream(stream)))
     return losses[:params.epochs]
+
+
+PK_T_OK, PK_T_GOAL_MISSED, PK_T_COLLISION = 0, 1, 2
+
+
+def pk_trajopt_params_default(**overrides) -> pk_trajopt_params:
+    p = pk_trajopt_params()
+    lib().pk_trajopt_params_default(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def _scene_args(radii, obstacles, plane):
+    S = radii.shape[1]
+    n_obs = obstacles.shape[0]
+    pl = np.ascontiguousarray(plane, np.float32)
+    return S, n_obs, pl
+
+
+def pk_trajopt_solve(robot: Robot, params: pk_trajopt_params, q_start, goals, q_init, radii, obstacles, plane,
+                     stream=None):
+    """Trajectories [B][T][n], costs [B], status bits [B]."""
+    B, T, n = q_init.shape
+    S, n_obs, pl = _scene_args(radii, obstacles, plane)
+    q_out = torch.empty_like(q_init)
+    cost = torch.empty(B, device=q_init.device)
+    status = torch.empty(B, dtype=torch.int32, device=q_init.device)
+    _check(lib().pk_trajopt_solve(robot.handle, C.byref(params), B, T, _dev(q_start, name="q_start"),
+                                  _dev(goals, name="goals"), _dev(q_init, name="q_init"), S,
+                                  _dev(radii, name="radii"), n_obs,
+                                  _dev(obstacles, name="obstacles") if n_obs else None,
+                                  pl.ctypes.data_as(_f32p), _dev(q_out, name="q_out"), _dev(cost, name="cost"),
+                                  _dev(status, torch.int32, "status"), _stream(stream)))
+    return q_out, cost, status
+
+
+def pk_trajopt_normal(robot: Robot, params: pk_trajopt_params, q_start, goals, q, radii, obstacles, plane,
+                      stream=None):
+    """Diagonal blocks [B][T][n][n], J^T r [B][T][n] and costs [B] at trajectories q."""
+    B, T, n = q.shape
+    S, n_obs, pl = _scene_args(radii, obstacles, plane)
+    D = torch.empty(B, T, n, n, device=q.device)
+    g = torch.empty(B, T, n, device=q.device)
+    cost = torch.empty(B, device=q.device)
+    _check(lib().pk_trajopt_normal(robot.handle, C.byref(params), B, T, _dev(q_start, name="q_start"),
+                                   _dev(goals, name="goals"), _dev(q, name="q"), S, _dev(radii, name="radii"),
+                                   n_obs, _dev(obstacles, name="obstacles") if n_obs else None,
+                                   pl.ctypes.data_as(_f32p), _dev(D, name="D"), _dev(g, name="g"),
+                                   _dev(cost, name="cost"), _stream(stream)))
+    return D, g, cost

