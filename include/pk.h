@@ -158,8 +158,10 @@ size_t pk_ik_workspace_bytes(const pk_robot* robot, int32_t batch, int32_t n_see
  *                                 (cudaMallocAsync / cudaFreeAsync).
  * batch == 0 is a no-op.  The workspace must not be shared by calls that can
  * overlap on the GPU.
- * Supported: serial chains with one target on the last frame, n_dof <= 8
- * (PK_ERR_UNSUPPORTED otherwise).
+ * Kernels: a serial chain (n_dof <= 8) with one target on a frame after its
+ * last movable joint runs one problem per thread; any other tree with up to 32
+ * movable joints, 64 joints and 8 targets runs one problem per warp
+ * (PK_ERR_UNSUPPORTED beyond that).
  */
 pk_status pk_ik_solve(const pk_robot* robot, const pk_ik_params* params, int32_t k,
                       const int32_t* target_links, const int32_t* target_kinds, int32_t batch,
@@ -193,6 +195,56 @@ pk_status pk_ik_solve_noalloc(const pk_robot* robot, const pk_ik_params* params,
                               int32_t batch, int32_t n_seeds, const float* d_targets,
                               const float* d_seeds, float* d_q_out, float* d_err_out,
                               int32_t* d_iters_out, int32_t* d_status_out, void* stream);
+
+/*
+ * Uneven batches (plans).  Several problem sets -- each its own robot, target
+ * set, batch size and seeds -- are solved by ONE persistent kernel launch:
+ * every warp drains the sets in turn, serial chains of 6 or 7 movable joints
+ * one problem per thread and other trees one problem per warp, so warps that
+ * finish the expensive sets fall through to the cheap ones.  A plan fixes its
+ * buffers at creation; its first run captures the whole solve (workspace reset,
+ * the persistent kernel, one best-seed reduction per set) into a CUDA graph
+ * and every run launches that graph.  The LM rules and outputs are those of
+ * pk_ik_solve, per set.
+ */
+typedef struct pk_ik_plan pk_ik_plan;
+
+typedef struct {
+  const pk_robot* robot;
+  int32_t k;                   /* targets, 1..8 */
+  const int32_t* target_links; /* host [k] */
+  const int32_t* target_kinds; /* host [k] or NULL (all pose) */
+  int32_t batch, n_seeds;
+  const float* d_targets;      /* [batch][k][12], 16-byte aligned */
+  const float* d_seeds;        /* [batch][n_seeds][n_dof] */
+  float* d_q_out;              /* [batch][n_dof] */
+  float* d_err_out;            /* [batch][2] */
+  int32_t* d_iters_out;        /* [batch] */
+  int32_t* d_status_out;       /* [batch] */
+} pk_ik_problem_set;
+
+/* 1..8 sets; allocates the plan's workspace (cudaMalloc).  A schedule tuned
+ * earlier in this process for the same device and plan signature (robots,
+ * target counts, power-of-two batch buckets, seeds) is reused. */
+pk_status pk_ik_plan_create(const pk_ik_params* params, int32_t n_sets, const pk_ik_problem_set* sets,
+                            pk_ik_plan** out);
+void pk_ik_plan_destroy(pk_ik_plan* plan);
+/* Enqueue one solve as a CUDA-graph launch on `stream`. */
+pk_status pk_ik_plan_run(pk_ik_plan* plan, void* stream);
+/* The same work launched kernel by kernel (no graph). */
+pk_status pk_ik_plan_run_eager(pk_ik_plan* plan, void* stream);
+/* Autotuner: times every candidate schedule (block size 64/128/256, chain sets
+ * on the thread or the warp path, largest-work-first or given set order) with
+ * `reps` timed runs each after a warm-up, keeps the fastest (returned in
+ * *best_ms, milliseconds per solve) and caches it.  Synchronous; it runs the
+ * plan's solve many times, overwriting its outputs. */
+pk_status pk_ik_plan_autotune(pk_ik_plan* plan, int32_t reps, void* stream, float* best_ms);
+/* Read or force the schedule. */
+pk_status pk_ik_plan_schedule(const pk_ik_plan* plan, int32_t* block, int32_t* grid, int32_t* chains_as_trees,
+                              int32_t* given_order);
+pk_status pk_ik_plan_set_schedule(pk_ik_plan* plan, int32_t block, int32_t chains_as_trees, int32_t given_order);
+/* Work counters of the last run (as pk_ik_workspace_stats; synchronous). */
+pk_status pk_ik_plan_stats(const pk_ik_plan* plan, int64_t* stats_out);
 
 /*
  * Work counters of the last pk_ik_solve that ran with this caller workspace
@@ -233,8 +285,8 @@ enum { PK_T_OK = 0, PK_T_GOAL_MISSED = 1, PK_T_COLLISION = 2 }; /* status bits *
 
 typedef struct {
   float w_start;      /* default 100 */
-  float w_goal_pos;   /* default 1 */
-  float w_goal_rot;   /* default 0.5 */
+  float w_goal_pos;   /* default 100 (the goal is held like the start) */
+  float w_goal_rot;   /* default 50 */
   float w_vel;        /* default 1 */
   float w_acc;        /* default 1 */
   float w_limit;      /* default 10 */

@@ -313,7 +313,7 @@ class _TrajScene(C.Structure):
 
 
 class TrajParams:
-    def __init__(self, w_start=100.0, w_goal_pos=1.0, w_goal_rot=0.5, w_vel=1.0, w_acc=1.0, w_limit=10.0,
+    def __init__(self, w_start=100.0, w_goal_pos=100.0, w_goal_rot=50.0, w_vel=1.0, w_acc=1.0, w_limit=10.0,
                  w_coll=10.0, eta=0.02, lambda0=1e-2, lambda_min=1e-10, lambda_max=1e10, nu=2.0, iters=50,
                  banded=1):
         self._c = _TrajParams(w_start, w_goal_pos, w_goal_rot, w_vel, w_acc, w_limit, w_coll, eta, lambda0,

@@ -18,6 +18,7 @@
 #include "pk_internal.h"
 #include "pk_math.cuh"
 #include "pk_chain.cuh"
+#include "ik_tree.cuh"
 
 namespace pk {
 
@@ -206,11 +207,13 @@ __device__ __forceinline__ void load_target_frame(const float* __restrict__ tp, 
 
 int ik_rec_stride(int n_dof) { return ((n_dof + 3) & ~3) + 4; }
 
+// The lane-refilling LM loop over the P problems of one batch; problems are
+// claimed from *head, results go to rec, converged flags to flags.
 template <int N>
-__global__ void __launch_bounds__(kLmThreads) chain_lm_kernel(
-    const __grid_constant__ ChainC<N> rc, const __grid_constant__ LmParams lp,
-    const float* __restrict__ targets, const float* __restrict__ seeds, int n_seeds, int P,
-    IkWorkspace ws) {
+__device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams& lp,
+                                             const float* __restrict__ targets, const float* __restrict__ seeds,
+                                             int n_seeds, int P, int32_t* head, int32_t* flags, float* rec,
+                                             WorkCount& wc) {
   constexpr int NT = N * (N + 1) / 2;
   constexpr int NP = ((N + 3) & ~3);
   constexpr int STRIDE = NP + 4;
@@ -221,7 +224,6 @@ __global__ void __launch_bounds__(kLmThreads) chain_lm_kernel(
   float q[N], qc[N], A0[NT], g[N];
   float f = 0.f, lam = 0.f, pe_a = 0.f, re_a = 0.f;
   int it = 0;
-  unsigned n_eval = 0, n_build = 0, n_solve = 0, n_done = 0;  // work counters
 #pragma unroll
   for (int j = 0; j < N; ++j) { q[j] = qc[j] = g[j] = 0.f; }
 #pragma unroll
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(kLmThreads) chain_lm_kernel(
     if (nm) {
       const int leader = __ffs(nm) - 1;
       int base = 0;
-      if (lane == leader) base = atomicAdd(ws.head, __popc(nm));
+      if (lane == leader) base = atomicAdd(head, __popc(nm));
       base = __shfl_sync(kFull, base, leader);
       if (want) {
         prob = base + __popc(nm & ((1u << lane) - 1u));
@@ -258,13 +260,13 @@ __global__ void __launch_bounds__(kLmThreads) chain_lm_kernel(
 
     const int tgt = prob / n_seeds;
     int cancelled = 0;
-    if (lp.cancel) cancelled = __ldcg(ws.flags + tgt);
+    if (lp.cancel) cancelled = __ldcg(flags + tgt);
 
     // --- evaluate the candidate
     Frames<N> fr;
     float xi[6], th, pe, fc;
     chain_eval<N>(rc, lp, Ti, qc, fr, xi, th, pe, fc);
-    ++n_eval;
+    ++wc.eval;
 
     bool acc, done = false;
     int status = PK_P_MAX_ITERS;
@@ -297,9 +299,9 @@ __global__ void __launch_bounds__(kLmThreads) chain_lm_kernel(
       // --- damped normal equations and the next candidate
       if (acc) {
         chain_normal<N>(rc, lp, fr, xi, th, q, A0, g);
-        ++n_build;
+        ++wc.build;
       }
-      ++n_solve;
+      ++wc.solve;
       float L[NT], d[N];
 #pragma unroll
       for (int j = 0; j < NT; ++j) L[j] = A0[j];
@@ -310,32 +312,45 @@ __global__ void __launch_bounds__(kLmThreads) chain_lm_kernel(
 #pragma unroll
       for (int j = 0; j < N; ++j) qc[j] = ok ? q[j] + d[j] : q[j];
     } else {
-      float* r = ws.rec + (size_t)prob * STRIDE;
+      float* r = rec + (size_t)prob * STRIDE;
 #pragma unroll
       for (int j = 0; j < N; ++j) r[j] = q[j];
       r[NP + 0] = f;
       r[NP + 1] = pe_a;
       r[NP + 2] = re_a;
       r[NP + 3] = __int_as_float((status << 24) | it);
-      if (lp.cancel && status == PK_P_CONVERGED) __stcg(ws.flags + tgt, 1);
-      ++n_done;
+      if (lp.cancel && status == PK_P_CONVERGED) __stcg(flags + tgt, 1);
+      ++wc.done;
       need = true;
     }
   }
-  // one atomic per warp and counter
+}
+
+// Per-lane work counters summed over the warp, one atomic per counter.
+__device__ __forceinline__ void flush_counts(WorkCount wc, unsigned long long* stats) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    n_eval += __shfl_xor_sync(kFull, n_eval, o);
-    n_build += __shfl_xor_sync(kFull, n_build, o);
-    n_solve += __shfl_xor_sync(kFull, n_solve, o);
-    n_done += __shfl_xor_sync(kFull, n_done, o);
+    wc.eval += __shfl_xor_sync(kFull, wc.eval, o);
+    wc.build += __shfl_xor_sync(kFull, wc.build, o);
+    wc.solve += __shfl_xor_sync(kFull, wc.solve, o);
+    wc.done += __shfl_xor_sync(kFull, wc.done, o);
   }
-  if (lane == 0) {
-    atomicAdd(ws.stats + 0, (unsigned long long)n_eval);
-    atomicAdd(ws.stats + 1, (unsigned long long)n_build);
-    atomicAdd(ws.stats + 2, (unsigned long long)n_solve);
-    atomicAdd(ws.stats + 3, (unsigned long long)n_done);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(stats + 0, (unsigned long long)wc.eval);
+    atomicAdd(stats + 1, (unsigned long long)wc.build);
+    atomicAdd(stats + 2, (unsigned long long)wc.solve);
+    atomicAdd(stats + 3, (unsigned long long)wc.done);
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kLmThreads) chain_lm_kernel(
+    const __grid_constant__ ChainC<N> rc, const __grid_constant__ LmParams lp,
+    const float* __restrict__ targets, const float* __restrict__ seeds, int n_seeds, int P,
+    IkWorkspace ws) {
+  WorkCount wc;
+  chain_lm_run<N>(rc, lp, targets, seeds, n_seeds, P, ws.head, ws.flags, ws.rec, wc);
+  flush_counts(wc, ws.stats);
 }
 
 // Best seed per target: converged first, then lowest cost, then lowest index.
@@ -482,12 +497,7 @@ static cudaError_t chain_lm_launch(const ChainHost& ch, const LmParams& lp, cons
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  {
-    TraceScope tr("ik_reduce", stream);
-    ik_reduce_kernel<<<(batch + 127) / 128, 128, 0, stream>>>(ws.rec, N, ik_rec_stride(N), batch,
-                                                              n_seeds, d_q, d_err, d_iters, d_status);
-  }
-  return cudaGetLastError();
+  return launch_ik_reduce(ws.rec, N, batch, n_seeds, d_q, d_err, d_iters, d_status, stream);
 }
 
 template <int N>
@@ -512,6 +522,14 @@ static cudaError_t chain_res_launch(const ChainHost& ch, const LmParams& lp, con
     default: return cudaErrorInvalidValue; \
   }
 
+cudaError_t launch_ik_reduce(const float* rec, int n_dof, int batch, int n_seeds, float* d_q, float* d_err,
+                             int32_t* d_iters, int32_t* d_status, cudaStream_t stream) {
+  TraceScope tr("ik_reduce", stream);
+  ik_reduce_kernel<<<(batch + 127) / 128, 128, 0, stream>>>(rec, n_dof, ik_rec_stride(n_dof), batch, n_seeds, d_q,
+                                                            d_err, d_iters, d_status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_chain_lm(const ChainHost& ch, const LmParams& lp, const float* d_targets,
                             const float* d_seeds, int batch, int n_seeds, IkWorkspace ws,
                             float* d_q, float* d_err, int32_t* d_iters, int32_t* d_status,
@@ -529,6 +547,88 @@ cudaError_t launch_chain_residual(const ChainHost& ch, const LmParams& lp, const
 cudaError_t launch_fk(const RobotDev* d_robot, int n_joints, int n_dof, int batch, const float* d_q,
                       float* d_T, cudaStream_t stream) {
   fk_kernel<<<(batch + 127) / 128, 128, 0, stream>>>(d_robot, n_joints, n_dof, batch, d_q, d_T);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Uneven batches: one persistent launch over several (robot, target set,
+// seeds) segments.  Every warp walks the segments in the plan's order and
+// drains each one (chains: lanes claim problems one by one; trees: the warp
+// claims one problem at a time) before moving on, so warps that finish the
+// expensive segments fall through to the cheap ones and the launch ends when
+// the last problem of the last segment is done.
+
+struct MultiParams {
+  int32_t n_segs;
+  LmParams lp;
+  unsigned long long* stats;
+  MultiSeg seg[kMaxSegs];
+  ChainC<6> c6[kMaxSegs];
+  ChainC<7> c7[kMaxSegs];
+  TreeInfo tree[kMaxSegs];
+};
+
+__global__ void __launch_bounds__(256) ik_multi_kernel(const __grid_constant__ MultiParams mp) {
+  extern __shared__ TreeWarpSmem tsm[];
+  TreeWarpSmem& sm = tsm[threadIdx.x >> 5];
+  WorkCount wc;
+  for (int s = 0; s < mp.n_segs; ++s) {
+    const MultiSeg& g = mp.seg[s];
+    if (g.kind == 0) {
+      LmParams lp = mp.lp;
+      lp.pos_only = g.pos_only;
+      if (g.pos_only) lp.tol_rot = INFINITY;
+      if (g.n == 6)
+        chain_lm_run<6>(mp.c6[g.slot], lp, g.targets, g.seeds, g.n_seeds, g.P, g.head, g.flags, g.rec, wc);
+      else
+        chain_lm_run<7>(mp.c7[g.slot], lp, g.targets, g.seeds, g.n_seeds, g.P, g.head, g.flags, g.rec, wc);
+    } else {
+      tree_lm_run<kTreeMaxDof>(g.rb, mp.tree[g.slot], mp.lp, g.targets, g.seeds, g.n_seeds, g.P, g.head, g.flags,
+                               g.rec, sm, wc);
+    }
+  }
+  flush_counts(wc, mp.stats);
+}
+
+size_t ik_multi_params_size() { return sizeof(MultiParams); }
+void* ik_multi_params_new() { return new MultiParams(); }
+void ik_multi_params_free(void* p) { delete (MultiParams*)p; }
+
+bool ik_multi_set_chain(void* p, int slot, const ChainHost& ch) {
+  MultiParams* mp = (MultiParams*)p;
+  if (ch.n == 6) mp->c6[slot] = chain_const<6>(ch);
+  else if (ch.n == 7) mp->c7[slot] = chain_const<7>(ch);
+  else return false;
+  return true;
+}
+void ik_multi_set_tree(void* p, int slot, const TreeInfo& ti) { ((MultiParams*)p)->tree[slot] = ti; }
+void ik_multi_set_seg(void* p, int s, const MultiSeg& seg) { ((MultiParams*)p)->seg[s] = seg; }
+void ik_multi_set_common(void* p, int n_segs, const LmParams& lp, unsigned long long* stats) {
+  MultiParams* mp = (MultiParams*)p;
+  mp->n_segs = n_segs;
+  mp->lp = lp;
+  mp->stats = stats;
+}
+
+int ik_multi_max_blocks_per_sm(int block) {
+  int b = 0;
+  const size_t smem = (size_t)(block / 32) * sizeof(TreeWarpSmem);
+  cudaFuncSetAttribute(ik_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ik_multi_kernel, block, smem) != cudaSuccess) return 1;
+  return b > 0 ? b : 1;
+}
+
+cudaError_t launch_ik_multi(const void* host_params, int n_segs, int block, int grid, cudaStream_t st) {
+  (void)n_segs;
+  const size_t smem = (size_t)(block / 32) * sizeof(TreeWarpSmem);
+  static int attr_block = 0;
+  if (attr_block < block) {
+    cudaError_t e = cudaFuncSetAttribute(ik_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_block = block;
+  }
+  TraceScope tr("ik_multi", st);
+  ik_multi_kernel<<<grid, block, smem, st>>>(*(const MultiParams*)host_params);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,396 @@
+// ik_tree.cuh -- Levenberg-Marquardt IK for kinematic trees with several
+// targets: one warp per (target set, seed) problem, lane i owning variable i.
+//
+// Per iteration (Sec. III-A, Sec. III-C): level-parallel FK over the tree
+// (lanes take the joints of one depth level), per-target residuals on the
+// target lanes (pose: log(T_target^-1 T_link) with the inverse left-Jacobian
+// blocks; position: world-frame difference), joint-limit and rest rows on the
+// variable lanes, warp-reduced cost and errors; accept/reject; on acceptance
+// the Jacobian is formed one target at a time (lane i writes column i of the
+// target's rows into shared memory) and lane i accumulates row i of J^T J and
+// entry i of J^T r in registers; the damped system is factored by a
+// warp-shuffle Cholesky (lane i holds row i) and solved by forward and
+// backward substitution with broadcasts and warp reductions.
+#pragma once
+#include "pk_internal.h"
+#include "pk_math.cuh"
+
+namespace pk {
+
+constexpr int kTreeMaxDof = 32;
+constexpr int kTreeMaxTargets = 8;
+constexpr unsigned kTreeFull = 0xffffffffu;
+
+// Per-robot, per-target-set constants (global memory, built on the host).
+struct TreeInfo {
+  int32_t n_joints, n_dof, k;
+  int32_t n_levels;
+  int32_t level_start[kMaxJoints + 1];  // joints of depth level l: order[level_start[l] .. level_start[l+1])
+  int32_t order[kMaxJoints];
+  int32_t dof_joint[kTreeMaxDof];   // joint index of variable i
+  uint32_t dof_targets[kTreeMaxDof];  // bit t: variable i moves target t's frame
+  int32_t links[kTreeMaxTargets];
+  int32_t kinds[kTreeMaxTargets];
+  float lo[kTreeMaxDof], hi[kTreeMaxDof];
+};
+
+// Shared memory of one warp.
+struct TreeWarpSmem {
+  float frames[kMaxJoints][12];
+  float Jk[6][kTreeMaxDof];       // rows of the current target
+  float Ti[kTreeMaxTargets][12];  // target inverses (pose) or -p (position)
+  float xi[kTreeMaxTargets][6];   // unweighted residuals of the candidate
+  float th[kTreeMaxTargets];
+  float q[kTreeMaxDof];           // configuration being evaluated
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kTreeFull, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kTreeFull, v, o));
+  return v;
+}
+
+// FK of sm.q into sm.frames, level by level.
+__device__ __forceinline__ void tree_fk(const RobotDev* __restrict__ rb, const TreeInfo& ti, TreeWarpSmem& sm,
+                                        int lane) {
+  for (int l = 0; l < ti.n_levels; ++l) {
+    for (int idx = ti.level_start[l] + lane; idx < ti.level_start[l + 1]; idx += 32) {
+      const int j = ti.order[idx];
+      Rt O, X, Lm;
+      rt_load(rb->origin[j], O);
+      rt_identity(X);
+      const int t = rb->type[j];
+      if (t != PK_JOINT_FIXED) {
+        const float qv = sm.q[rb->var[j]];
+        const float* a = rb->axis[j];
+        if (t == PK_JOINT_REVOLUTE) {
+          float u[3] = {a[0], a[1], a[2]}, s, c;
+          sincos_rad(qv, &s, &c);
+          rot_joint(X.r, u, a, s, c);
+        } else {
+          X.t[0] = a[0] * qv; X.t[1] = a[1] * qv; X.t[2] = a[2] * qv;
+        }
+      }
+      rt_mul(O, X, Lm);
+      const int p = rb->parent[j];
+      if (p >= 0) {
+        Rt Tp;
+        rt_load(sm.frames[p], Tp);
+        rt_mul(Tp, Lm, Lm);
+      }
+      rt_store(sm.frames[j], Lm);
+    }
+    __syncwarp();
+  }
+}
+
+// Evaluate sm.q: residual data into sm.xi / sm.th, returns the cost; the
+// largest position and rotation errors over targets come back in pe / re.
+__device__ __forceinline__ float tree_eval(const RobotDev* __restrict__ rb, const TreeInfo& ti,
+                                           const LmParams& lp, TreeWarpSmem& sm, int lane, float& pe, float& re) {
+  tree_fk(rb, ti, sm, lane);
+  float acc = 0.f, mpe = 0.f, mre = 0.f;
+  if (lane < ti.k) {
+    Rt Tl, Ti, E;
+    rt_load(sm.frames[ti.links[lane]], Tl);
+    rt_load(sm.Ti[lane], Ti);
+    rt_mul(Ti, Tl, E);
+    mpe = sqrtf(E.t[0] * E.t[0] + E.t[1] * E.t[1] + E.t[2] * E.t[2]);
+    if (ti.kinds[lane] == PK_TARGET_POSE) {
+      float xi[6];
+      const float th = se3_log(E, xi);
+      mre = th;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) sm.xi[lane][i] = xi[i];
+      sm.th[lane] = th;
+      acc = lp.w_pos * lp.w_pos * (xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]) +
+            lp.w_rot * lp.w_rot * (xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        sm.xi[lane][i] = E.t[i];
+        sm.xi[lane][3 + i] = 0.f;
+      }
+      sm.th[lane] = 0.f;
+      acc = lp.w_pos * lp.w_pos * mpe * mpe;
+    }
+  }
+  if (lane < ti.n_dof) {
+    const float q = sm.q[lane];
+    const float h = fmaxf(0.f, q - ti.hi[lane]) + fmaxf(0.f, ti.lo[lane] - q);
+    const float d = q - 0.5f * (ti.lo[lane] + ti.hi[lane]);
+    acc = fmaf(lp.w_limit * lp.w_limit, h * h, fmaf(lp.w_rest * lp.w_rest, d * d, acc));
+  }
+  pe = warp_max(mpe);
+  re = warp_max(mre);
+  __syncwarp();
+  return 0.5f * warp_sum(acc);
+}
+
+// Row `lane` of J^T J (in Arow[0..N)) and entry g of J^T r at the configuration
+// whose frames and residuals sm holds.
+template <int N>
+__device__ __forceinline__ void tree_normal(const RobotDev* __restrict__ rb, const TreeInfo& ti,
+                                            const LmParams& lp, TreeWarpSmem& sm, int lane, float (&Arow)[N],
+                                            float& g) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) Arow[j] = 0.f;
+  g = 0.f;
+  const bool mine = lane < ti.n_dof;
+  int jj = 0;
+  float pj[3] = {0.f, 0.f, 0.f}, wj[3] = {0.f, 0.f, 0.f};
+  bool prism = false;
+  if (mine) {
+    jj = ti.dof_joint[lane];
+    Rt Tj;
+    rt_load(sm.frames[jj], Tj);
+    mat_vec(Tj.r, rb->axis[jj], wj);
+    pj[0] = Tj.t[0]; pj[1] = Tj.t[1]; pj[2] = Tj.t[2];
+    prism = rb->type[jj] == PK_JOINT_PRISMATIC;
+  }
+  for (int k = 0; k < ti.k; ++k) {
+    const bool pose = ti.kinds[k] == PK_TARGET_POSE;
+    float col[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (mine && (ti.dof_targets[lane] >> k & 1u)) {
+      Rt Ti;
+      rt_load(sm.Ti[k], Ti);
+      // joint axis and origin in the target frame
+      float u[3], p[3];
+      mat_vec(Ti.r, wj, u);
+      mat_vec(Ti.r, pj, p);
+      p[0] += Ti.t[0]; p[1] += Ti.t[1]; p[2] += Ti.t[2];
+      if (pose) {
+        float A[9], B[9];
+        se3_jlinv_blocks(sm.xi[k], sm.xi[k] + 3, sm.th[k], A, B);
+        float top[3], bot[3];
+        if (prism) {
+          mat_vec(A, u, top);
+          bot[0] = bot[1] = bot[2] = 0.f;
+        } else {
+          float v[3], t1[3], t2[3];
+          cross3(p, u, v);
+          mat_vec(A, v, t1);
+          mat_vec(B, u, t2);
+          mat_vec(A, u, bot);
+          top[0] = t1[0] + t2[0]; top[1] = t1[1] + t2[1]; top[2] = t1[2] + t2[2];
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          col[i] = lp.w_pos * top[i];
+          col[3 + i] = lp.w_rot * bot[i];
+        }
+      } else {
+        float c[3];
+        if (prism) {
+          c[0] = u[0]; c[1] = u[1]; c[2] = u[2];
+        } else {
+          float d[3] = {sm.xi[k][0] - p[0], sm.xi[k][1] - p[1], sm.xi[k][2] - p[2]};
+          cross3(u, d, c);
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) col[i] = lp.w_pos * c[i];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) sm.Jk[r][lane] = col[r];
+    __syncwarp();
+    const int rows = pose ? 6 : 3;
+    for (int r = 0; r < rows; ++r) {
+      const float wr = (r < 3 ? lp.w_pos : lp.w_rot) * sm.xi[k][r];
+      g = fmaf(col[r], wr, g);
+#pragma unroll
+      for (int j = 0; j < N; ++j) Arow[j] = fmaf(col[r], sm.Jk[r][j], Arow[j]);
+    }
+    __syncwarp();
+  }
+  if (mine) {
+    const float q = sm.q[lane];
+    float h = 0.f, d = 0.f;
+    if (q > ti.hi[lane]) { h = q - ti.hi[lane]; d = 1.f; }
+    if (q < ti.lo[lane]) { h = ti.lo[lane] - q; d = -1.f; }
+    const float wl2 = lp.w_limit * lp.w_limit, wr2 = lp.w_rest * lp.w_rest;
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      if (j == lane) Arow[j] += wl2 * d * d + wr2;
+    g = fmaf(wl2 * d, h, fmaf(wr2, q - 0.5f * (ti.lo[lane] + ti.hi[lane]), g));
+  }
+}
+
+// Solve (A + lam I) x = -g for the n x n system held row-per-lane; returns
+// false on a non-positive pivot.  x comes back on lane i.
+template <int N>
+__device__ __forceinline__ bool tree_solve(const float (&Arow)[N], float g, float lam, int n, int lane,
+                                           float& x) {
+  float L[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) L[j] = Arow[j] + ((j == lane) ? lam : 0.f);
+  bool ok = true;
+  // right-looking: step k finalises column k
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    if (k < n) {
+      const float d = __shfl_sync(kTreeFull, L[k], k);
+      ok = ok && (d > 0.f) && (d < INFINITY);
+      const float inv = rsqrtf(d);
+      float lik = 0.f;
+      if (lane > k && lane < n) {
+        lik = L[k] * inv;
+        L[k] = lik;
+      }
+      if (lane == k) L[k] = d * inv;
+#pragma unroll
+      for (int j = k + 1; j < N; ++j) {
+        if (j < n) {
+          const float ljk = __shfl_sync(kTreeFull, lik, j);
+          if (lane >= j && lane < n) L[j] = fmaf(-lik, ljk, L[j]);
+        }
+      }
+    }
+  }
+  // forward: L y = -g
+  float b = -g, y = 0.f;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    if (k < n) {
+      float diag = 0.f, lk = 0.f;
+#pragma unroll
+      for (int j = 0; j < N; ++j)
+        if (j == k) { diag = L[j]; lk = L[j]; }
+      const float yk = __shfl_sync(kTreeFull, b / diag, k);
+      if (lane == k) y = yk;
+      if (lane > k && lane < n) b = fmaf(-lk, yk, b);
+    }
+  }
+  // backward: L^T x = y
+  float xv = 0.f;
+  for (int k = n - 1; k >= 0; --k) {
+    float lik = 0.f;
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      if (j == k) lik = L[j];
+    const float part = (lane > k && lane < n) ? lik * xv : 0.f;
+    const float s = warp_sum(part);
+    float diag = 0.f;
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      if (j == k) diag = L[j];
+    const float xk = __shfl_sync(kTreeFull, (y - s) / diag, k);
+    if (lane == k) xv = xk;
+  }
+  x = xv;
+  return ok;
+}
+
+}  // namespace pk
+
+namespace pk {
+
+// Work counters kept per lane and flushed once per warp.
+struct WorkCount {
+  unsigned eval = 0, build = 0, solve = 0, done = 0;
+};
+
+// LM on problems of one (robot, target set, seeds) batch, one problem per warp
+// at a time, problems claimed from *head until P are done.  Records as in the
+// chain kernel: q[0..n), cost, pos_err, rot_err, (status << 24) | iters.
+template <int N>
+__device__ void tree_lm_run(const RobotDev* __restrict__ rb, const TreeInfo& ti, const LmParams& lp,
+                            const float* __restrict__ targets, const float* __restrict__ seeds, int n_seeds, int P,
+                            int32_t* head, int32_t* flags, float* rec, TreeWarpSmem& sm, WorkCount& wc) {
+  const int lane = threadIdx.x & 31;
+  const int n = ti.n_dof, k = ti.k;
+  const int np = (n + 3) & ~3, stride = np + 4;
+  for (;;) {
+    int prob = 0;
+    if (lane == 0) prob = atomicAdd(head, 1);
+    prob = __shfl_sync(kTreeFull, prob, 0);
+    if (prob >= P) break;
+    const int tgt = prob / n_seeds;
+    if (lane < k) {
+      Rt T, Ti;
+      rt_load(targets + ((size_t)tgt * k + lane) * 12, T);
+      if (ti.kinds[lane] == PK_TARGET_POSE) {
+        rt_inv(T, Ti);
+      } else {
+        rt_identity(Ti);
+        Ti.t[0] = -T.t[0]; Ti.t[1] = -T.t[1]; Ti.t[2] = -T.t[2];
+      }
+      rt_store(sm.Ti[lane], Ti);
+    }
+    float q = lane < n ? __ldg(seeds + (size_t)prob * n + lane) : 0.f;
+    sm.q[lane] = q;
+    __syncwarp();
+    float pe, re;
+    float f = tree_eval(rb, ti, lp, sm, lane, pe, re);
+    const unsigned one = lane == 0 ? 1u : 0u;  // warp-level work counted once
+    wc.eval += one;
+    float Arow[N], g = 0.f;
+    float lam = lp.lambda0;
+    int it = 0, status = PK_P_MAX_ITERS;
+    bool conv = pe <= lp.tol_pos && re <= lp.tol_rot;
+    bool done = false;
+    if (!isfinite(f)) { done = true; status = PK_P_NONFINITE; }
+    else if (lp.early_exit && conv) { done = true; status = PK_P_CONVERGED; }
+    else if (lp.max_iters <= 0) { done = true; status = conv ? PK_P_CONVERGED : PK_P_MAX_ITERS; }
+    else { tree_normal<N>(rb, ti, lp, sm, lane, Arow, g); wc.build += one; }
+    while (!done) {
+      ++it;
+      float dx;
+      const bool ok = tree_solve<N>(Arow, g, lam, n, lane, dx);
+      wc.solve += one;
+      const float qc = (ok && lane < n) ? q + dx : q;
+      sm.q[lane] = qc;
+      __syncwarp();
+      float pe_c, re_c;
+      const float fc = tree_eval(rb, ti, lp, sm, lane, pe_c, re_c);
+      wc.eval += one;
+      if (fc < f) {
+        q = qc;
+        f = fc;
+        pe = pe_c;
+        re = re_c;
+        lam = fmaxf(lam / lp.nu, lp.lambda_min);
+        conv = pe <= lp.tol_pos && re <= lp.tol_rot;
+        if (lp.early_exit && conv) {
+          done = true;
+          status = PK_P_CONVERGED;
+        } else if (it < lp.max_iters) {
+          tree_normal<N>(rb, ti, lp, sm, lane, Arow, g);
+          wc.build += one;
+        }
+      } else {
+        lam = fminf(lam * lp.nu, lp.lambda_max);
+      }
+      if (!done && it >= lp.max_iters) {
+        done = true;
+        status = conv ? PK_P_CONVERGED : PK_P_MAX_ITERS;
+      }
+      if (!done && lp.cancel) {
+        int c = 0;
+        if (lane == 0) c = __ldcg(flags + tgt);
+        if (__shfl_sync(kTreeFull, c, 0)) {
+          done = true;
+          status = PK_P_CANCELLED;
+        }
+      }
+    }
+    float* r = rec + (size_t)prob * stride;
+    if (lane < n) r[lane] = q;
+    if (lane == 0) {
+      r[np + 0] = f;
+      r[np + 1] = pe;
+      r[np + 2] = re;
+      r[np + 3] = __int_as_float((status << 24) | it);
+      if (lp.cancel && status == PK_P_CONVERGED) __stcg(flags + tgt, 1);
+      ++wc.done;
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace pk

@@ -9,6 +9,7 @@
 #include <new>
 
 #include "pk_internal.h"
+#include "ik_tree.cuh"
 
 namespace {
 
@@ -145,9 +146,18 @@ pk_status check_targets(const pk_robot* rb, int32_t k, const int32_t* links, con
     if (kinds && kinds[i] != PK_TARGET_POSE && kinds[i] != PK_TARGET_POSITION)
       return fail(PK_ERR_INVALID_ARG, "target_kinds[%d] = %d invalid", i, kinds[i]);
   }
-  if (k != 1) return fail(PK_ERR_UNSUPPORTED, "serial-chain IK takes one target (k = 1)");
   *pos_only = kinds && kinds[0] == PK_TARGET_POSITION;
   return PK_OK;
+}
+
+// True when the thread-per-problem chain kernel serves this (robot, target).
+bool chain_eligible(const pk_robot* rb, int32_t k, const int32_t* links) {
+  if (k != 1 || rb->n_dof < 1 || rb->n_dof > pk::kMaxChainDof) return false;
+  for (int j = 0; j < rb->n_joints; ++j)
+    if (rb->parent[j] != j - 1) return false;
+  for (int j = links[0] + 1; j < rb->n_joints; ++j)
+    if (rb->type[j] != PK_JOINT_FIXED) return false;
+  return true;
 }
 
 }  // namespace
@@ -155,6 +165,13 @@ pk_status check_targets(const pk_robot* rb, int32_t k, const int32_t* links, con
 namespace pk {
 
 pk_status set_error(pk_status s, const char* msg) { return fail(s, "%s", msg); }
+
+bool fold_chain_quiet(const pk_robot* rb, int link, ChainHost* ch) {
+  const std::string keep = g_last_error;
+  const bool ok = fold_chain(rb, link, ch) == PK_OK;
+  g_last_error = keep;
+  return ok;
+}
 
 size_t ik_workspace_bytes(int n_dof, long batch, long n_seeds) {
   const size_t head = 256;
@@ -252,8 +269,8 @@ pk_status pk_trace_summary(const char* kernel, double* total_ms, int64_t* launch
 void pk_trajopt_params_default(pk_trajopt_params* p) {
   if (!p) return;
   p->w_start = 100.f;
-  p->w_goal_pos = 1.f;
-  p->w_goal_rot = 0.5f;
+  p->w_goal_pos = 100.f;
+  p->w_goal_rot = 50.f;
   p->w_vel = 1.f;
   p->w_acc = 1.f;
   p->w_limit = 10.f;
@@ -480,6 +497,7 @@ pk_status pk_ik_residual(const pk_robot* rb, const pk_ik_params* params, int32_t
   bool pos_only = false;
   if ((s = check_targets(rb, k, target_links, target_kinds, &pos_only)) != PK_OK) return s;
   if (batch < 0) return fail(PK_ERR_INVALID_ARG, "batch must be >= 0");
+  if (k != 1) return fail(PK_ERR_UNSUPPORTED, "pk_ik_residual takes one target (k = 1)");
   pk::ChainHost ch;
   if ((s = fold_chain(rb, target_links[0], &ch)) != PK_OK) return s;
   if (batch == 0) return PK_OK;
@@ -510,8 +528,15 @@ pk_status pk_ik_solve(const pk_robot* rb, const pk_ik_params* params, int32_t k,
   if (n_seeds < 1) return fail(PK_ERR_INVALID_ARG, "n_seeds must be >= 1");
   if ((long long)batch * n_seeds > 0x7fffff00LL)
     return fail(PK_ERR_INVALID_ARG, "batch * n_seeds exceeds 2^31");
+  const bool chain = chain_eligible(rb, k, target_links);
   pk::ChainHost ch;
-  if ((s = fold_chain(rb, target_links[0], &ch)) != PK_OK) return s;
+  pk::TreeInfo ti;
+  if (chain) {
+    if ((s = fold_chain(rb, target_links[0], &ch)) != PK_OK) return s;
+  } else if (!pk::build_tree_info(rb, k, target_links, target_kinds, &ti)) {
+    return fail(PK_ERR_UNSUPPORTED, "IK supports up to %d movable joints, %d targets and %d joints",
+                pk::kTreeMaxDof, pk::kTreeMaxTargets, pk::kMaxJoints);
+  }
   if (batch == 0) return PK_OK;
   if (!d_targets || !d_seeds || !d_q_out || !d_err_out || !d_iters_out || !d_status_out)
     return fail(PK_ERR_INVALID_ARG, "NULL device buffer");
@@ -533,9 +558,17 @@ pk_status pk_ik_solve(const pk_robot* rb, const pk_ik_params* params, int32_t k,
   size_t zero_bytes = 0;
   pk::ik_workspace_carve(ws_base, rb->n_dof, batch, n_seeds, &ws, &zero_bytes);
   cudaError_t e = cudaMemsetAsync(ws_base, 0, zero_bytes, st);
-  if (e == cudaSuccess)
-    e = pk::launch_chain_lm(ch, lm_params(params, pos_only), d_targets, d_seeds, batch, n_seeds, ws,
-                            d_q_out, d_err_out, d_iters_out, d_status_out, st);
+  if (e == cudaSuccess) {
+    if (chain) {
+      e = pk::launch_chain_lm(ch, lm_params(params, pos_only), d_targets, d_seeds, batch, n_seeds, ws, d_q_out,
+                              d_err_out, d_iters_out, d_status_out, st);
+    } else {
+      pk::LmParams lp = lm_params(params, false);
+      lp.tol_rot = params->tol_rot;  // position targets report 0 rotation error
+      e = pk::launch_tree_lm(rb, ti, lp, d_targets, d_seeds, batch, n_seeds, ws, d_q_out, d_err_out, d_iters_out,
+                             d_status_out, st);
+    }
+  }
   if (owned) {
     cudaError_t e2 = cudaFreeAsync(ws_base, st);
     if (e == cudaSuccess) e = e2;

@@ -73,11 +73,46 @@ cudaError_t launch_chain_lm(const ChainHost& ch, const LmParams& lp, const float
                             const float* d_seeds, int batch, int n_seeds, IkWorkspace ws,
                             float* d_q, float* d_err, int32_t* d_iters, int32_t* d_status,
                             cudaStream_t stream);
+cudaError_t launch_ik_reduce(const float* rec, int n_dof, int batch, int n_seeds, float* d_q, float* d_err,
+                             int32_t* d_iters, int32_t* d_status, cudaStream_t stream);
+struct TreeInfo;
+bool build_tree_info(const pk_robot* rb, int k, const int32_t* links, const int32_t* kinds, TreeInfo* ti);
+cudaError_t launch_tree_lm(const pk_robot* rb, const TreeInfo& ti, const LmParams& lp, const float* d_targets,
+                           const float* d_seeds, int batch, int n_seeds, IkWorkspace ws, float* d_q, float* d_err,
+                           int32_t* d_iters, int32_t* d_status, cudaStream_t stream);
 cudaError_t launch_chain_residual(const ChainHost& ch, const LmParams& lp, const float* d_targets,
                                   const float* d_q, int batch, float* d_r, float* d_J,
                                   cudaStream_t stream);
 cudaError_t launch_fk(const RobotDev* d_robot, int n_joints, int n_dof, int batch, const float* d_q,
                       float* d_T, cudaStream_t stream);
+
+// Uneven multi-robot batches in one persistent launch (ik_chain.cu, ik_plan.cu).
+constexpr int kMaxSegs = 8;
+
+struct MultiSeg {
+  int32_t kind;     // 0: chain (thread per problem), 1: tree (warp per problem)
+  int32_t n;        // movable joints
+  int32_t slot;     // constants slot (chain n-specific array or tree array)
+  int32_t pos_only;
+  int32_t batch, n_seeds, P;
+  const float* targets;
+  const float* seeds;
+  int32_t* head;
+  int32_t* flags;
+  float* rec;
+  const RobotDev* rb;
+};
+
+cudaError_t launch_ik_multi(const void* host_params, int n_segs, int block, int grid, cudaStream_t st);
+size_t ik_multi_params_size();
+void* ik_multi_params_new();
+void ik_multi_params_free(void* p);
+// Fill slot `slot` of the chain (n = 6, 7) or tree constants and segment `s`.
+bool ik_multi_set_chain(void* p, int slot, const ChainHost& ch);
+void ik_multi_set_tree(void* p, int slot, const struct TreeInfo& ti);
+void ik_multi_set_seg(void* p, int s, const MultiSeg& seg);
+void ik_multi_set_common(void* p, int n_segs, const LmParams& lp, unsigned long long* stats);
+int ik_multi_max_blocks_per_sm(int block);
 
 // Trajectory optimisation (trajopt.cu).
 constexpr int kTrajMaxT = 64;
@@ -95,6 +130,9 @@ cudaError_t launch_trajopt(const ChainHost& ch, const TrajParamsDev& tp, int bat
                            const float* goals, const float* q_init, const float* radii, const float* obs,
                            float* q_out, float* cost_out, int32_t* status_out, float* D_out, float* g_out,
                            cudaStream_t st);
+
+// Folds a serial chain ending at frame `link` (false if it is not one).
+bool fold_chain_quiet(const pk_robot* rb, int link, ChainHost* ch);
 
 // Records a thread-local error message (pk_last_error) and returns s.
 pk_status set_error(pk_status s, const char* msg);

@@ -46,6 +46,13 @@ class pk_ik_params(C.Structure):
                 ("cancel_siblings", C.c_int32), ("reserved", C.c_int32)]
 
 
+class pk_ik_problem_set(C.Structure):
+    _fields_ = [("robot", C.c_void_p), ("k", C.c_int32), ("target_links", C.POINTER(C.c_int32)),
+                ("target_kinds", C.POINTER(C.c_int32)), ("batch", C.c_int32), ("n_seeds", C.c_int32),
+                ("d_targets", C.c_void_p), ("d_seeds", C.c_void_p), ("d_q_out", C.c_void_p),
+                ("d_err_out", C.c_void_p), ("d_iters_out", C.c_void_p), ("d_status_out", C.c_void_p)]
+
+
 class pk_trajopt_params(C.Structure):
     _fields_ = [("w_start", C.c_float), ("w_goal_pos", C.c_float), ("w_goal_rot", C.c_float),
                 ("w_vel", C.c_float), ("w_acc", C.c_float), ("w_limit", C.c_float), ("w_coll", C.c_float),
@@ -83,6 +90,14 @@ _SIGNATURES = {
                                    _vp, _vp, _vp, _vp, _vp, _vp]),
     "pk_ik_workspace_stats": (_i32, [_vp, C.POINTER(C.c_int64)]),
     "pk_train_params_default": (None, [_vp]),
+    "pk_ik_plan_create": (_i32, [C.POINTER(pk_ik_params), _i32, _vp, C.POINTER(_vp)]),
+    "pk_ik_plan_destroy": (None, [_vp]),
+    "pk_ik_plan_run": (_i32, [_vp, _vp]),
+    "pk_ik_plan_run_eager": (_i32, [_vp, _vp]),
+    "pk_ik_plan_autotune": (_i32, [_vp, _i32, _vp, C.POINTER(C.c_float)]),
+    "pk_ik_plan_schedule": (_i32, [_vp, _i32p, _i32p, _i32p, _i32p]),
+    "pk_ik_plan_set_schedule": (_i32, [_vp, _i32, _i32, _i32]),
+    "pk_ik_plan_stats": (_i32, [_vp, C.POINTER(C.c_int64)]),
     "pk_trajopt_params_default": (None, [_vp]),
     "pk_trajopt_solve": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _i32, _vp, _f32p, _vp, _vp,
                                 _vp, _vp]),
@@ -438,3 +453,56 @@ def pk_trajopt_normal(robot: Robot, params: pk_trajopt_params, q_start, goals, q
                                    pl.ctypes.data_as(_f32p), _dev(D, name="D"), _dev(g, name="g"),
                                    _dev(cost, name="cost"), _stream(stream)))
     return D, g, cost
+
+
+class IkPlan:
+    """A pk_ik_plan over several (robot, links, kinds, targets, seeds) sets; keeps
+    the tensors it was built on alive and owns the per-set outputs."""
+
+    def __init__(self, params: pk_ik_params, sets):
+        self.keep, self.outs = [], []
+        arr = (pk_ik_problem_set * len(sets))()
+        for i, (robot, links, kinds, targets, seeds) in enumerate(sets):
+            links_a, kinds_a, kinds_p = _links(links, kinds)
+            B, S = seeds.shape[0], seeds.shape[1]
+            dev = seeds.device
+            out = (torch.empty(B, robot.n_dof, device=dev), torch.empty(B, 2, device=dev),
+                   torch.empty(B, device=dev, dtype=torch.int32), torch.empty(B, device=dev, dtype=torch.int32))
+            self.outs.append(out)
+            self.keep += [robot, links_a, kinds_a, targets, seeds]
+            arr[i] = pk_ik_problem_set(robot.handle.value, len(links_a), links_a.ctypes.data_as(_i32p), kinds_p,
+                                       B, S, targets.data_ptr(), seeds.data_ptr(), out[0].data_ptr(),
+                                       out[1].data_ptr(), out[2].data_ptr(), out[3].data_ptr())
+        self.params = params
+        h = C.c_void_p()
+        _check(lib().pk_ik_plan_create(C.byref(params), len(sets), C.cast(arr, C.c_void_p), C.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.pk_ik_plan_destroy(h)
+            self.handle = None
+
+    def run(self, stream=None, graph=True):
+        fn = lib().pk_ik_plan_run if graph else lib().pk_ik_plan_run_eager
+        _check(fn(self.handle, _stream(stream)))
+        return self.outs
+
+    def autotune(self, reps=3, stream=None) -> float:
+        ms = C.c_float()
+        _check(lib().pk_ik_plan_autotune(self.handle, reps, _stream(stream), C.byref(ms)))
+        return ms.value
+
+    def schedule(self) -> dict:
+        v = [C.c_int32() for _ in range(4)]
+        _check(lib().pk_ik_plan_schedule(self.handle, *[C.byref(x) for x in v]))
+        return dict(block=v[0].value, grid=v[1].value, chains_as_trees=v[2].value, given_order=v[3].value)
+
+    def set_schedule(self, block=128, chains_as_trees=0, given_order=0):
+        _check(lib().pk_ik_plan_set_schedule(self.handle, block, chains_as_trees, given_order))
+
+    def stats(self) -> dict:
+        out = (C.c_int64 * 4)()
+        _check(lib().pk_ik_plan_stats(self.handle, out))
+        return dict(evals=out[0], builds=out[1], solves=out[2], problems=out[3])

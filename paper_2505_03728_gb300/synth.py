@@ -206,23 +206,69 @@ def ik_workload(cfg: dict, batch: int | None = None):
 
 TRAJOPT = dict(name="trajopt7_1024xT64", robot_seed=100, n_dof=7, batch=1024, T=64, start_seed=600,
                goal_seed=603, obstacle_seed=601, n_obstacles=32, sphere_seed=602, spheres_per_link=4,
-               plane=(0.0, 0.0, 1.0, -0.15), reach=1.0, iters=50)
+               plane=(0.0, 0.0, 1.0, -0.15), reach=(0.5, 1.6), iters=50, candidates=16)
+
+
+def sphere_obstacles_shell(seed: int, count: int, r_in: float, r_out: float, z_min: float,
+                           r_lo=0.05, r_hi=0.2) -> np.ndarray:
+    """Obstacle spheres [count][4]: centres uniform in the shell r_in <= |c| <= r_out
+    above z_min, radii uniform in [r_lo, r_hi]."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((count, 4))
+    i = 0
+    while i < count:
+        c = rng.uniform(-r_out, r_out, 3)
+        if not (r_in <= np.linalg.norm(c) <= r_out) or c[2] < z_min:
+            continue
+        out[i, :3] = c
+        out[i, 3] = rng.uniform(r_lo, r_hi)
+        i += 1
+    return out
 
 
 def trajopt_workload(cfg: dict, batch: int | None = None):
-    """(robot spec, start configs [B][n], goal configs [B][n], link sphere radii [n][S],
-    obstacles [n_obs][4], plane [4]).  Goal poses are FK of the goal configurations
-    (computed by the callers)."""
+    """(robot spec, candidate start configs [C*B][n], candidate goal configs [C*B][n],
+    link sphere radii [n][S], obstacles [n_obs][4], plane [4]) with C = cfg['candidates'].
+    Callers keep the first B candidates that clear the scene (by their own forward
+    kinematics) and take goal poses as FK of the goal configurations."""
     spec = chain_robot(cfg["robot_seed"], cfg["n_dof"])
     B = cfg["batch"] if batch is None else batch
-    qs = uniform_q(cfg["start_seed"], cfg["batch"], spec.dof_lower, spec.dof_upper)[:B]
-    qg = uniform_q(cfg["goal_seed"], cfg["batch"], spec.dof_lower, spec.dof_upper)[:B]
+    C = cfg["candidates"] * cfg["batch"]
+    qs = uniform_q(cfg["start_seed"], C, spec.dof_lower, spec.dof_upper)
+    qg = uniform_q(cfg["goal_seed"], C, spec.dof_lower, spec.dof_upper)
     radii = link_spheres(cfg["sphere_seed"], cfg["n_dof"], cfg["spheres_per_link"])
-    obs = sphere_obstacles(cfg["obstacle_seed"], cfg["n_obstacles"], cfg["reach"])
-    return spec, qs, qg, radii, obs, np.asarray(cfg["plane"], np.float64)
+    plane = np.asarray(cfg["plane"], np.float64)
+    obs = sphere_obstacles_shell(cfg["obstacle_seed"], cfg["n_obstacles"], cfg["reach"][0], cfg["reach"][1],
+                                 plane[3])
+    return spec, qs, qg, radii, obs, plane
 
 
 def linear_interpolation(q0, q1, T):
     """[B][T][n] straight line from q0 [B][n] to q1 [B][n] in joint space."""
     s = np.linspace(0.0, 1.0, T)[None, :, None]
     return (1.0 - s) * np.asarray(q0)[:, None, :] + s * np.asarray(q1)[:, None, :]
+
+
+UNEVEN = dict(name="uneven_6_7_24_30", batch_seed=400, batch_lo=1, batch_hi=4096, n_seeds=8, target_seed=410,
+              seed_seed=420, max_iters=50)
+
+
+def uneven_workload(cfg: dict = UNEVEN, scale: float = 1.0):
+    """The four robots of the uneven batch with their target frames, target kinds,
+    per-robot batch sizes (uniform in [batch_lo, batch_hi], times `scale`), target
+    configurations and seeds: [(name, spec, links, kinds, q_targets [B][n], seeds [B][S][n])]."""
+    sizes = batch_sizes(cfg["batch_seed"], 4, cfg["batch_lo"], cfg["batch_hi"])
+    hand, tips = hand_robot(102)
+    hum, ends = humanoid_robot(103)
+    c6, c7 = chain_robot(101, 6), chain_robot(100, 7)
+    robots = [("chain6", c6, [len(c6["parent"]) - 1], None),
+              ("chain7", c7, [len(c7["parent"]) - 1], None),
+              ("hand24", hand, list(tips), [TARGET_POSITION] * len(tips)),
+              ("humanoid30", hum, list(ends), None)]
+    out = []
+    for i, (name, spec, links, kinds) in enumerate(robots):
+        B = max(1, int(round(sizes[i] * scale)))
+        qt = uniform_q(cfg["target_seed"] + i, B, spec.dof_lower, spec.dof_upper)
+        sd = uniform_q(cfg["seed_seed"] + i, (B, cfg["n_seeds"]), spec.dof_lower, spec.dof_upper)
+        out.append((name, spec, links, kinds, qt, sd))
+    return out
