@@ -233,16 +233,19 @@ void pk_ik_plan_destroy(pk_ik_plan* plan);
 pk_status pk_ik_plan_run(pk_ik_plan* plan, void* stream);
 /* The same work launched kernel by kernel (no graph). */
 pk_status pk_ik_plan_run_eager(pk_ik_plan* plan, void* stream);
-/* Autotuner: times every candidate schedule (block size 64/128/256, chain sets
- * on the thread or the warp path, largest-work-first or given set order) with
+/* Autotuner: times every candidate schedule (kernel variant -- registers
+ * unconstrained, or capped for three 128-thread blocks per SM --, block size
+ * 64/128/256, chain sets on the thread or the warp path, largest-work-first or
+ * given set order) with
  * `reps` timed runs each after a warm-up, keeps the fastest (returned in
  * *best_ms, milliseconds per solve) and caches it.  Synchronous; it runs the
  * plan's solve many times, overwriting its outputs. */
 pk_status pk_ik_plan_autotune(pk_ik_plan* plan, int32_t reps, void* stream, float* best_ms);
 /* Read or force the schedule. */
 pk_status pk_ik_plan_schedule(const pk_ik_plan* plan, int32_t* block, int32_t* grid, int32_t* chains_as_trees,
-                              int32_t* given_order);
-pk_status pk_ik_plan_set_schedule(pk_ik_plan* plan, int32_t block, int32_t chains_as_trees, int32_t given_order);
+                              int32_t* given_order, int32_t* variant);
+pk_status pk_ik_plan_set_schedule(pk_ik_plan* plan, int32_t block, int32_t chains_as_trees, int32_t given_order,
+                                  int32_t variant);
 /* Work counters of the last run (as pk_ik_workspace_stats; synchronous). */
 pk_status pk_ik_plan_stats(const pk_ik_plan* plan, int64_t* stats_out);
 

@@ -568,7 +568,10 @@ struct MultiParams {
   TreeInfo tree[kMaxSegs];
 };
 
-__global__ void __launch_bounds__(256) ik_multi_kernel(const __grid_constant__ MultiParams mp) {
+// MINB = 1 lets the compiler keep every path in registers; MINB = 3 caps the
+// registers for three 128-thread blocks per SM (the autotuner picks).
+template <int MINB>
+__global__ void __launch_bounds__(MINB == 1 ? 256 : 128, MINB) ik_multi_kernel(const __grid_constant__ MultiParams mp) {
   extern __shared__ TreeWarpSmem tsm[];
   TreeWarpSmem& sm = tsm[threadIdx.x >> 5];
   WorkCount wc;
@@ -610,25 +613,27 @@ void ik_multi_set_common(void* p, int n_segs, const LmParams& lp, unsigned long 
   mp->stats = stats;
 }
 
-int ik_multi_max_blocks_per_sm(int block) {
+int ik_multi_max_blocks_per_sm(int block, int variant) {
   int b = 0;
   const size_t smem = (size_t)(block / 32) * sizeof(TreeWarpSmem);
-  cudaFuncSetAttribute(ik_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ik_multi_kernel, block, smem) != cudaSuccess) return 1;
+  if (variant == 1) {
+    if (block > 128) return 0;
+    cudaFuncSetAttribute(ik_multi_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ik_multi_kernel<3>, block, smem) != cudaSuccess) return 1;
+  } else {
+    cudaFuncSetAttribute(ik_multi_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ik_multi_kernel<1>, block, smem) != cudaSuccess) return 1;
+  }
   return b > 0 ? b : 1;
 }
 
-cudaError_t launch_ik_multi(const void* host_params, int n_segs, int block, int grid, cudaStream_t st) {
-  (void)n_segs;
+cudaError_t launch_ik_multi(const void* host_params, int variant, int block, int grid, cudaStream_t st) {
   const size_t smem = (size_t)(block / 32) * sizeof(TreeWarpSmem);
-  static int attr_block = 0;
-  if (attr_block < block) {
-    cudaError_t e = cudaFuncSetAttribute(ik_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_block = block;
-  }
   TraceScope tr("ik_multi", st);
-  ik_multi_kernel<<<grid, block, smem, st>>>(*(const MultiParams*)host_params);
+  if (variant == 1)
+    ik_multi_kernel<3><<<grid, block, smem, st>>>(*(const MultiParams*)host_params);
+  else
+    ik_multi_kernel<1><<<grid, block, smem, st>>>(*(const MultiParams*)host_params);
   return cudaGetLastError();
 }
 

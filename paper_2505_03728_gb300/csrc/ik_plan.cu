@@ -45,6 +45,7 @@ struct PlanConfig {
   int block = 128;
   int chains_as_trees = 0;
   int given_order = 0;
+  int variant = 0;  // 0: unconstrained registers, 1: capped for 3 blocks per SM
 };
 
 struct pk_ik_plan {
@@ -134,7 +135,7 @@ void configure(pk_ik_plan* pl, const PlanConfig& cfg) {
   pk::ik_multi_set_common(pl->mp, n, plan_lm(&pl->params), (unsigned long long*)ws);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device);
-  pl->grid = pk::ik_multi_max_blocks_per_sm(cfg.block) * (sms > 0 ? sms : 1);
+  pl->grid = pk::ik_multi_max_blocks_per_sm(cfg.block, cfg.variant) * (sms > 0 ? sms : 1);
   if (pl->exec) {
     cudaGraphExecDestroy(pl->exec);
     pl->exec = nullptr;
@@ -148,7 +149,7 @@ void configure(pk_ik_plan* pl, const PlanConfig& cfg) {
 cudaError_t enqueue(pk_ik_plan* pl, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(pl->d_ws, 0, pl->zero_bytes, st);
   if (e != cudaSuccess) return e;
-  e = pk::launch_ik_multi(pl->mp, (int)pl->sets.size(), pl->cfg.block, pl->grid, st);
+  e = pk::launch_ik_multi(pl->mp, pl->cfg.variant, pl->cfg.block, pl->grid, st);
   if (e != cudaSuccess) return e;
   for (const PlanSet& ps : pl->sets) {
     if (ps.batch == 0) continue;
@@ -292,9 +293,12 @@ pk_status pk_ik_plan_autotune(pk_ik_plan* pl, int32_t reps, void* stream, float*
   std::vector<PlanConfig> cands;
   bool any_chain = false;
   for (const PlanSet& ps : pl->sets) any_chain = any_chain || ps.chain_ok;
-  for (int block : {64, 128, 256})
-    for (int cat = 0; cat <= (any_chain ? 1 : 0); ++cat)
-      for (int go = 0; go <= 1; ++go) cands.push_back(PlanConfig{block, cat, go});
+  for (int variant = 0; variant <= 1; ++variant)
+    for (int block : {64, 128, 256}) {
+      if (variant == 1 && block > 128) continue;
+      for (int cat = 0; cat <= (any_chain ? 1 : 0); ++cat)
+        for (int go = 0; go <= 1; ++go) cands.push_back(PlanConfig{block, cat, go, variant});
+    }
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -332,8 +336,9 @@ pk_status pk_ik_plan_autotune(pk_ik_plan* pl, int32_t reps, void* stream, float*
 }
 
 pk_status pk_ik_plan_schedule(const pk_ik_plan* pl, int32_t* block, int32_t* grid, int32_t* chains_as_trees,
-                              int32_t* given_order) {
+                              int32_t* given_order, int32_t* variant) {
   if (!pl) return pfail(PK_ERR_INVALID_ARG, "plan is NULL");
+  if (variant) *variant = pl->cfg.variant;
   if (block) *block = pl->cfg.block;
   if (grid) *grid = pl->grid;
   if (chains_as_trees) *chains_as_trees = pl->cfg.chains_as_trees;
@@ -341,10 +346,13 @@ pk_status pk_ik_plan_schedule(const pk_ik_plan* pl, int32_t* block, int32_t* gri
   return PK_OK;
 }
 
-pk_status pk_ik_plan_set_schedule(pk_ik_plan* pl, int32_t block, int32_t chains_as_trees, int32_t given_order) {
+pk_status pk_ik_plan_set_schedule(pk_ik_plan* pl, int32_t block, int32_t chains_as_trees, int32_t given_order,
+                                  int32_t variant) {
   if (!pl) return pfail(PK_ERR_INVALID_ARG, "plan is NULL");
   if (block != 64 && block != 128 && block != 256) return pfail(PK_ERR_INVALID_ARG, "block must be 64, 128 or 256");
-  configure(pl, PlanConfig{block, chains_as_trees ? 1 : 0, given_order ? 1 : 0});
+  if (variant != 0 && variant != 1) return pfail(PK_ERR_INVALID_ARG, "variant must be 0 or 1");
+  if (variant == 1 && block > 128) return pfail(PK_ERR_INVALID_ARG, "variant 1 takes blocks of at most 128");
+  configure(pl, PlanConfig{block, chains_as_trees ? 1 : 0, given_order ? 1 : 0, variant});
   return PK_OK;
 }
 

@@ -42,6 +42,8 @@ struct TreeWarpSmem {
   float xi[kTreeMaxTargets][6];   // unweighted residuals of the candidate
   float th[kTreeMaxTargets];
   float q[kTreeMaxDof];           // configuration being evaluated
+  float L[kTreeMaxDof][kTreeMaxDof + 1];  // Cholesky factor, row i by lane i (padded rows)
+  float dinv[kTreeMaxDof];        // reciprocal diagonal of L
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -221,68 +223,57 @@ __device__ __forceinline__ void tree_normal(const RobotDev* __restrict__ rb, con
   }
 }
 
-// Solve (A + lam I) x = -g for the n x n system held row-per-lane; returns
-// false on a non-positive pivot.  x comes back on lane i.
+// Solve (A + lam I) x = -g for the n x n system held row-per-lane (Arow on
+// lane i is row i); returns false on a non-positive pivot.  The factor lives
+// in shared memory so that every loop below stays rolled (small code): step k
+// of the right-looking Cholesky scales column k and lane i updates its row
+// with column k broadcast from shared memory; the substitutions broadcast one
+// unknown per step.  x comes back on lane i.
 template <int N>
-__device__ __forceinline__ bool tree_solve(const float (&Arow)[N], float g, float lam, int n, int lane,
-                                           float& x) {
-  float L[N];
+__device__ __forceinline__ bool tree_solve(const float (&Arow)[N], float g, float lam, int n, int lane, float& x,
+                                           TreeWarpSmem& sm) {
 #pragma unroll
-  for (int j = 0; j < N; ++j) L[j] = Arow[j] + ((j == lane) ? lam : 0.f);
+  for (int j = 0; j < N; ++j) sm.L[lane][j] = Arow[j] + ((j == lane) ? lam : 0.f);
+  __syncwarp();
   bool ok = true;
-  // right-looking: step k finalises column k
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    if (k < n) {
-      const float d = __shfl_sync(kTreeFull, L[k], k);
-      ok = ok && (d > 0.f) && (d < INFINITY);
-      const float inv = rsqrtf(d);
-      float lik = 0.f;
-      if (lane > k && lane < n) {
-        lik = L[k] * inv;
-        L[k] = lik;
-      }
-      if (lane == k) L[k] = d * inv;
-#pragma unroll
-      for (int j = k + 1; j < N; ++j) {
-        if (j < n) {
-          const float ljk = __shfl_sync(kTreeFull, lik, j);
-          if (lane >= j && lane < n) L[j] = fmaf(-lik, ljk, L[j]);
-        }
-      }
+#pragma unroll 1
+  for (int k = 0; k < n; ++k) {
+    const float d = sm.L[k][k];
+    ok = ok && (d > 0.f) && (d < INFINITY);
+    const float inv = rsqrtf(d);
+    __syncwarp();
+    if (lane == k) {
+      sm.L[k][k] = d * inv;
+      sm.dinv[k] = inv;
+    } else if (lane > k && lane < n) {
+      sm.L[lane][k] *= inv;
     }
+    __syncwarp();
+    if (lane > k && lane < n) {
+      const float lik = sm.L[lane][k];
+#pragma unroll 1
+      for (int j = k + 1; j <= lane; ++j) sm.L[lane][j] = fmaf(-lik, sm.L[j][k], sm.L[lane][j]);
+    }
+    __syncwarp();
   }
   // forward: L y = -g
   float b = -g, y = 0.f;
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    if (k < n) {
-      float diag = 0.f, lk = 0.f;
-#pragma unroll
-      for (int j = 0; j < N; ++j)
-        if (j == k) { diag = L[j]; lk = L[j]; }
-      const float yk = __shfl_sync(kTreeFull, b / diag, k);
-      if (lane == k) y = yk;
-      if (lane > k && lane < n) b = fmaf(-lk, yk, b);
-    }
+#pragma unroll 1
+  for (int k = 0; k < n; ++k) {
+    const float yk = __shfl_sync(kTreeFull, b * sm.dinv[k], k);
+    if (lane == k) y = yk;
+    if (lane > k && lane < n) b = fmaf(-sm.L[lane][k], yk, b);
   }
-  // backward: L^T x = y
-  float xv = 0.f;
+  // backward: L^T x = y (row k of L, read by column, holds L[k][i] for lane i)
+  float yr = y, xv = 0.f;
+#pragma unroll 1
   for (int k = n - 1; k >= 0; --k) {
-    float lik = 0.f;
-#pragma unroll
-    for (int j = 0; j < N; ++j)
-      if (j == k) lik = L[j];
-    const float part = (lane > k && lane < n) ? lik * xv : 0.f;
-    const float s = warp_sum(part);
-    float diag = 0.f;
-#pragma unroll
-    for (int j = 0; j < N; ++j)
-      if (j == k) diag = L[j];
-    const float xk = __shfl_sync(kTreeFull, (y - s) / diag, k);
+    const float xk = __shfl_sync(kTreeFull, yr * sm.dinv[k], k);
     if (lane == k) xv = xk;
+    if (lane < k) yr = fmaf(-sm.L[k][lane], xk, yr);
   }
   x = xv;
+  __syncwarp();
   return ok;
 }
 
@@ -341,7 +332,7 @@ __device__ void tree_lm_run(const RobotDev* __restrict__ rb, const TreeInfo& ti,
     while (!done) {
       ++it;
       float dx;
-      const bool ok = tree_solve<N>(Arow, g, lam, n, lane, dx);
+      const bool ok = tree_solve<N>(Arow, g, lam, n, lane, dx, sm);
       wc.solve += one;
       const float qc = (ok && lane < n) ? q + dx : q;
       sm.q[lane] = qc;

@@ -95,8 +95,8 @@ _SIGNATURES = {
     "pk_ik_plan_run": (_i32, [_vp, _vp]),
     "pk_ik_plan_run_eager": (_i32, [_vp, _vp]),
     "pk_ik_plan_autotune": (_i32, [_vp, _i32, _vp, C.POINTER(C.c_float)]),
-    "pk_ik_plan_schedule": (_i32, [_vp, _i32p, _i32p, _i32p, _i32p]),
-    "pk_ik_plan_set_schedule": (_i32, [_vp, _i32, _i32, _i32]),
+    "pk_ik_plan_schedule": (_i32, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p]),
+    "pk_ik_plan_set_schedule": (_i32, [_vp, _i32, _i32, _i32, _i32]),
     "pk_ik_plan_stats": (_i32, [_vp, C.POINTER(C.c_int64)]),
     "pk_trajopt_params_default": (None, [_vp]),
     "pk_trajopt_solve": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _i32, _vp, _f32p, _vp, _vp,
@@ -495,12 +495,13 @@ class IkPlan:
         return ms.value
 
     def schedule(self) -> dict:
-        v = [C.c_int32() for _ in range(4)]
+        v = [C.c_int32() for _ in range(5)]
         _check(lib().pk_ik_plan_schedule(self.handle, *[C.byref(x) for x in v]))
-        return dict(block=v[0].value, grid=v[1].value, chains_as_trees=v[2].value, given_order=v[3].value)
+        return dict(block=v[0].value, grid=v[1].value, chains_as_trees=v[2].value, given_order=v[3].value,
+                    variant=v[4].value)
 
-    def set_schedule(self, block=128, chains_as_trees=0, given_order=0):
-        _check(lib().pk_ik_plan_set_schedule(self.handle, block, chains_as_trees, given_order))
+    def set_schedule(self, block=128, chains_as_trees=0, given_order=0, variant=0):
+        _check(lib().pk_ik_plan_set_schedule(self.handle, block, chains_as_trees, given_order, variant))
 
     def stats(self) -> dict:
         out = (C.c_int64 * 4)()
