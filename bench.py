@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--train-epochs", type=int, default=8)
+    ap.add_argument("--no-extra", action="store_true", help="skip the uneven-batch and trajectory lines")
     return ap.parse_args()
 
 
@@ -229,6 +230,71 @@ def reduce_over_ranks(torch, world, ms, count):
     return float(t.item()), int(c.item())
 
 
+def extra_workloads(torch, pk, synth, args, flush, stream):
+    """Secondary lines: the uneven multi-robot batch (one persistent launch,
+    CUDA graph, autotuned) and collision-aware trajectory optimisation."""
+    from paper_2505_03728_gb300 import scenes
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    out = {}
+    # uneven batch: 6-DoF chain, 7-DoF chain, 24-DoF hand, 30-joint humanoid
+    sets, names = [], []
+    for name, spec, links, kinds, qt, sd in synth.uneven_workload():
+        g = pk.Robot.from_spec(spec)
+        T = pk.pk_fk(g, dev(qt))[:, links].contiguous()
+        sets.append((g, links, kinds, T, dev(sd)))
+        names.append((name, int(qt.shape[0])))
+    prm = pk.pk_ik_params_default(max_iters=50, early_exit=1, cancel_siblings=1)
+    plan = pk.IkPlan(prm, sets)
+    tuned_ms = plan.autotune(reps=2)
+    steps = max(3, args.steps // 2)
+    for _ in range(args.warmup):
+        plan.run()
+    timed = Timed(torch, steps, flush)
+    conv = torch.zeros((), dtype=torch.int64, device="cuda")
+
+    def run():
+        outs = plan.run()
+        for o in outs:
+            conv.add_((o[3] == pk.PK_P_CONVERGED).sum())
+    ms = timed.run(run, stream)
+    out["uneven"] = {"workload": synth.UNEVEN["name"], "robots": dict(names), "seeds": synth.UNEVEN["n_seeds"],
+                     "value": int(conv.item()) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+                     "success_rate": int(conv.item()) / (steps * sum(b for _, b in names)),
+                     "launch": "one persistent kernel per step, CUDA graph replay",
+                     "schedule": plan.schedule(), "autotuned_ms": tuned_ms, "work_per_launch": plan.stats()}
+    # trajectory optimisation: 1024 trajectories x T = 64, 32 obstacles + plane, 50 LM iterations
+    cfg = synth.TRAJOPT
+    spec, qs_c, qg_c, radii, obs, plane = synth.trajopt_workload(cfg)
+    g = pk.Robot.from_spec(spec)
+    pts = lambda q: pk.pk_fk(g, dev(q)).cpu().numpy()[:, :, [3, 7, 11]].astype(np.float64)
+    qs = scenes.pick_clear(qs_c, pts(qs_c), radii, obs, plane, 0.02, cfg["batch"])
+    qg = scenes.pick_clear(qg_c, pts(qg_c), radii, obs, plane, 0.02, cfg["batch"])
+    goals = pk.pk_fk(g, dev(qg))[:, -1].contiguous()
+    x0 = dev(synth.linear_interpolation(qs, qg, cfg["T"]))
+    tp = pk.pk_trajopt_params_default(iters=cfg["iters"])
+    targs = (dev(qs), goals, x0, dev(radii), dev(obs), plane)
+    for _ in range(2):
+        res = pk.pk_trajopt_solve(g, tp, *targs)
+    tsteps = 3
+    timed = Timed(torch, tsteps, flush)
+    holder = {}
+
+    def trun():
+        holder["r"] = pk.pk_trajopt_solve(g, tp, *targs)
+    pk.pk_trace_enable(True)
+    tms = timed.run(trun, stream)
+    t_ms, t_n = pk.pk_trace_summary("trajopt")
+    pk.pk_trace_enable(False)
+    st = holder["r"][2].cpu().numpy()
+    out["trajopt"] = {"workload": cfg["name"], "value": cfg["batch"] * tsteps / (tms / 1e3), "unit": "trajectories/s",
+                      "ms_per_step": tms / tsteps, "kernel_ms": t_ms / max(1, t_n),
+                      "goal_reached": float(np.mean((st & pk.PK_T_GOAL_MISSED) == 0)),
+                      "collision_free": float(np.mean((st & pk.PK_T_COLLISION) == 0)),
+                      "config": {"T": cfg["T"], "iters": cfg["iters"], "obstacles": cfg["n_obstacles"],
+                                 "spheres_per_link": cfg["spheres_per_link"]}}
+    return out
+
+
 def main():
     args = parse()
     from paper_2505_03728_gb300 import synth
@@ -302,7 +368,9 @@ def main():
             def counted():
                 fn()
                 conv.add_((outs[3] == pk.PK_P_CONVERGED).sum())
+            torch.cuda.nvtx.range_push(f"timed_{name}")
             total_ms = timed.run(counted, stream)
+            torch.cuda.nvtx.range_pop()
             lm_ms, lm_n = pk.pk_trace_summary("ik_lm")
             gemm_ms, gemm_n = pk.pk_trace_summary("gemm")
             pk.pk_trace_enable(False)
@@ -348,6 +416,8 @@ def main():
     h2d = h_t.numel() * 4 + (0 if head == "learned" else h_s.numel() * 4)
     d2h = sum(o.numel() * o.element_size() for o in outs)
 
+    extra = {} if args.no_extra else extra_workloads(torch, pk, synth, args, flush, stream)
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -392,6 +462,7 @@ def main():
         line["learned"]["train_s"] = train_s
         line["learned"]["train_loss"] = [float(x) for x in train_loss]
         line["learned_over_plain"] = results["learned"]["value"] / results["plain"]["value"]
+    line.update(extra)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, qt, sd)
     print(json.dumps(line), flush=True)
