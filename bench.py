@@ -237,6 +237,9 @@ def extra_workloads(torch, pk, synth, args, flush, stream):
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
     out = {}
     # uneven batch: 6-DoF chain, 7-DoF chain, 24-DoF hand, 30-joint humanoid
+    UNEVEN_LAUNCH = ["one persistent kernel over all robots", "one persistent kernel over all robots (capped "
+                     "registers)", "one specialised kernel per robot, serial", "one specialised kernel per robot, "
+                     "forked streams"]
     sets, names = [], []
     for name, spec, links, kinds, qt, sd in synth.uneven_workload():
         g = pk.Robot.from_spec(spec)
@@ -260,7 +263,7 @@ def extra_workloads(torch, pk, synth, args, flush, stream):
     out["uneven"] = {"workload": synth.UNEVEN["name"], "robots": dict(names), "seeds": synth.UNEVEN["n_seeds"],
                      "value": int(conv.item()) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
                      "success_rate": int(conv.item()) / (steps * sum(b for _, b in names)),
-                     "launch": "one persistent kernel per step, CUDA graph replay",
+                     "launch": UNEVEN_LAUNCH[plan.schedule()["variant"]] + ", CUDA graph replay",
                      "schedule": plan.schedule(), "autotuned_ms": tuned_ms, "work_per_launch": plan.stats()}
     # trajectory optimisation: 1024 trajectories x T = 64, 32 obstacles + plane, 50 LM iterations
     cfg = synth.TRAJOPT

@@ -198,14 +198,17 @@ pk_status pk_ik_solve_noalloc(const pk_robot* robot, const pk_ik_params* params,
 
 /*
  * Uneven batches (plans).  Several problem sets -- each its own robot, target
- * set, batch size and seeds -- are solved by ONE persistent kernel launch:
- * every warp drains the sets in turn, serial chains of 6 or 7 movable joints
- * one problem per thread and other trees one problem per warp, so warps that
- * finish the expensive sets fall through to the cheap ones.  A plan fixes its
- * buffers at creation; its first run captures the whole solve (workspace reset,
- * the persistent kernel, one best-seed reduction per set) into a CUDA graph
- * and every run launches that graph.  The LM rules and outputs are those of
- * pk_ik_solve, per set.
+ * set, batch size and seeds -- are solved together.  Schedule variants 0 and 1
+ * run ONE persistent kernel launch: every warp drains the sets in turn, serial
+ * chains of 6 or 7 movable joints one problem per thread and other trees one
+ * problem per warp, so warps that finish the expensive sets fall through to
+ * the cheap ones (variant 1 caps registers for three 128-thread blocks per SM).
+ * Variants 2 and 3 run each set's own specialised kernel (the pk_ik_solve
+ * kernels), one after another (2) or on forked streams so that their tails
+ * overlap (3).  A plan fixes its buffers at creation; its first run captures
+ * the whole solve (workspace reset, the LM kernels, one best-seed reduction
+ * per set) into a CUDA graph and every run launches that graph.  The LM rules
+ * and outputs are those of pk_ik_solve, per set.
  */
 typedef struct pk_ik_plan pk_ik_plan;
 
@@ -233,15 +236,15 @@ void pk_ik_plan_destroy(pk_ik_plan* plan);
 pk_status pk_ik_plan_run(pk_ik_plan* plan, void* stream);
 /* The same work launched kernel by kernel (no graph). */
 pk_status pk_ik_plan_run_eager(pk_ik_plan* plan, void* stream);
-/* Autotuner: times every candidate schedule (kernel variant -- registers
- * unconstrained, or capped for three 128-thread blocks per SM --, block size
- * 64/128/256, chain sets on the thread or the warp path, largest-work-first or
- * given set order) with
+/* Autotuner: times every candidate schedule (variant 0..3 as above, block
+ * size 64/128/256 for the persistent variants, chain sets on the thread or the
+ * warp path, largest-work-first or given set order) with
  * `reps` timed runs each after a warm-up, keeps the fastest (returned in
  * *best_ms, milliseconds per solve) and caches it.  Synchronous; it runs the
  * plan's solve many times, overwriting its outputs. */
 pk_status pk_ik_plan_autotune(pk_ik_plan* plan, int32_t reps, void* stream, float* best_ms);
-/* Read or force the schedule. */
+/* Read or force the schedule (block 64, 128 or 256; variant 0..3; variant 1
+ * takes blocks of at most 128; grid is 0 for variants 2 and 3). */
 pk_status pk_ik_plan_schedule(const pk_ik_plan* plan, int32_t* block, int32_t* grid, int32_t* chains_as_trees,
                               int32_t* given_order, int32_t* variant);
 pk_status pk_ik_plan_set_schedule(pk_ik_plan* plan, int32_t block, int32_t chains_as_trees, int32_t given_order,

@@ -207,18 +207,19 @@ __device__ __forceinline__ void load_target_frame(const float* __restrict__ tp, 
 
 int ik_rec_stride(int n_dof) { return ((n_dof + 3) & ~3) + 4; }
 
+
+
 // The lane-refilling LM loop over the P problems of one batch; problems are
 // claimed from *head, results go to rec, converged flags to flags.
 template <int N>
 __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams& lp,
                                              const float* __restrict__ targets, const float* __restrict__ seeds,
                                              int n_seeds, int P, int32_t* head, int32_t* flags, float* rec,
-                                             WorkCount& wc) {
+                                             WorkCount& wc, ChainQueue<N>& qq) {
   constexpr int NT = N * (N + 1) / 2;
   constexpr int NP = ((N + 3) & ~3);
   constexpr int STRIDE = NP + 4;
   const int lane = threadIdx.x & 31;
-  int prob = -1;
   bool need = true, exhausted = false, fresh = false;
   Rt Ti;
   float q[N], qc[N], A0[NT], g[N];
@@ -229,36 +230,74 @@ __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams
 #pragma unroll
   for (int j = 0; j < NT; ++j) A0[j] = 0.f;
 
+  // Problems come from the warp's double-buffered queue (claim order: see
+  // claim_order); a seed whose target is already solved is skipped.
+  const int batch = P / n_seeds;
+  const bool cancel = lp.cancel != 0;
+  int tgt = 0, pid = 0;  // target and record index of the lane's problem
+  int qcur = 0, qpos = 0;
+  chain_chunk_claim<N>(qq, 0, head, P, batch, n_seeds, cancel, targets, seeds, flags, lane);
+  chain_chunk_claim<N>(qq, 1, head, P, batch, n_seeds, cancel, targets, seeds, flags, lane);
+  cp_async_wait_one_pending();
+  __syncwarp();
   for (;;) {
-    // --- claim problems for the lanes that need one (warp-aggregated)
-    const bool want = need && !exhausted;
-    const unsigned nm = __ballot_sync(kFull, want);
-    if (nm) {
-      const int leader = __ffs(nm) - 1;
-      int base = 0;
-      if (lane == leader) base = atomicAdd(head, __popc(nm));
-      base = __shfl_sync(kFull, base, leader);
-      if (want) {
-        prob = base + __popc(nm & ((1u << lane) - 1u));
-        if (prob >= P) {
+    // --- hand queued problems to the lanes that need one
+    for (;;) {
+      const bool want = need && !exhausted;
+      const unsigned nm = __ballot_sync(kFull, want);
+      if (!nm) break;
+      if (qpos == kQ) {  // current chunk used up: switch and refill the other buffer
+        cp_async_wait_all();
+        __syncwarp();
+        qcur ^= 1;
+        qpos = 0;
+        chain_chunk_claim<N>(qq, qcur ^ 1, head, P, batch, n_seeds, cancel, targets, seeds, flags, lane);
+      }
+      const int rank = __popc(nm & ((1u << lane) - 1u));
+      const int avail = kQ - qpos;
+      if (want && rank < avail) {
+        const int e = qpos + rank;
+        const int pe = qq.pid[qcur][e];
+        if (pe < 0) {
           exhausted = true;
         } else {
-          load_target_frame(targets + (size_t)(prob / n_seeds) * 12, lp.pos_only != 0, Ti);
-          const float* sp = seeds + (size_t)prob * N;
+          pid = pe;
+          tgt = qq.tid[qcur][e];
+          if (cancel && qq.flag[qcur][e]) {
+            float* r = rec + (size_t)pid * STRIDE;
+            r[NP + 0] = INFINITY;
+            r[NP + 3] = __int_as_float(PK_P_CANCELLED << 24);
+            ++wc.done;
+          } else {
+            Rt Tt;
 #pragma unroll
-          for (int j = 0; j < N; ++j) qc[j] = __ldg(sp + j);
-          fresh = true;
-          it = 0;
-          lam = lp.lambda0;
+            for (int i = 0; i < 3; ++i) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) Tt.r[i * 3 + c] = qq.tgt[qcur][e][i * 4 + c];
+              Tt.t[i] = qq.tgt[qcur][e][i * 4 + 3];
+            }
+            if (lp.pos_only) {
+              rt_identity(Ti);
+              Ti.t[0] = -Tt.t[0]; Ti.t[1] = -Tt.t[1]; Ti.t[2] = -Tt.t[2];
+            } else {
+              rt_inv(Tt, Ti);
+            }
+#pragma unroll
+            for (int j = 0; j < N; ++j) qc[j] = qq.seed[qcur][e][j];
+            fresh = true;
+            it = 0;
+            lam = lp.lambda0;
+            need = false;
+          }
         }
       }
+      qpos += min(__popc(nm), avail);
     }
     need = false;
     const bool active = !exhausted;
     if (!__any_sync(kFull, active)) break;
     if (!active) continue;
 
-    const int tgt = prob / n_seeds;
     int cancelled = 0;
     if (lp.cancel) cancelled = __ldcg(flags + tgt);
 
@@ -312,7 +351,7 @@ __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams
 #pragma unroll
       for (int j = 0; j < N; ++j) qc[j] = ok ? q[j] + d[j] : q[j];
     } else {
-      float* r = rec + (size_t)prob * STRIDE;
+      float* r = rec + (size_t)pid * STRIDE;
 #pragma unroll
       for (int j = 0; j < N; ++j) r[j] = q[j];
       r[NP + 0] = f;
@@ -324,6 +363,8 @@ __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams
       need = true;
     }
   }
+  cp_async_wait_all();
+  __syncwarp();
 }
 
 // Per-lane work counters summed over the warp, one atomic per counter.
@@ -348,8 +389,9 @@ __global__ void __launch_bounds__(kLmThreads) chain_lm_kernel(
     const __grid_constant__ ChainC<N> rc, const __grid_constant__ LmParams lp,
     const float* __restrict__ targets, const float* __restrict__ seeds, int n_seeds, int P,
     IkWorkspace ws) {
+  __shared__ ChainQueue<N> qq[kLmThreads / 32];
   WorkCount wc;
-  chain_lm_run<N>(rc, lp, targets, seeds, n_seeds, P, ws.head, ws.flags, ws.rec, wc);
+  chain_lm_run<N>(rc, lp, targets, seeds, n_seeds, P, ws.head, ws.flags, ws.rec, wc, qq[threadIdx.x >> 5]);
   flush_counts(wc, ws.stats);
 }
 
@@ -570,6 +612,9 @@ struct MultiParams {
 
 // MINB = 1 lets the compiler keep every path in registers; MINB = 3 caps the
 // registers for three 128-thread blocks per SM (the autotuner picks).
+static_assert(sizeof(ChainQueue<7>) <= sizeof(TreeWarpSmem), "chain queue must fit the per-warp scratch");
+static_assert(sizeof(TreeWarpSmem) % 16 == 0, "per-warp scratch must keep 16-byte alignment");
+
 template <int MINB>
 __global__ void __launch_bounds__(MINB == 1 ? 256 : 128, MINB) ik_multi_kernel(const __grid_constant__ MultiParams mp) {
   extern __shared__ TreeWarpSmem tsm[];
@@ -581,10 +626,14 @@ __global__ void __launch_bounds__(MINB == 1 ? 256 : 128, MINB) ik_multi_kernel(c
       LmParams lp = mp.lp;
       lp.pos_only = g.pos_only;
       if (g.pos_only) lp.tol_rot = INFINITY;
+      // the chain path's queue lives in this warp's tree scratch (one path at a time)
       if (g.n == 6)
-        chain_lm_run<6>(mp.c6[g.slot], lp, g.targets, g.seeds, g.n_seeds, g.P, g.head, g.flags, g.rec, wc);
+        chain_lm_run<6>(mp.c6[g.slot], lp, g.targets, g.seeds, g.n_seeds, g.P, g.head, g.flags, g.rec, wc,
+                        *reinterpret_cast<ChainQueue<6>*>(&sm));
       else
-        chain_lm_run<7>(mp.c7[g.slot], lp, g.targets, g.seeds, g.n_seeds, g.P, g.head, g.flags, g.rec, wc);
+        chain_lm_run<7>(mp.c7[g.slot], lp, g.targets, g.seeds, g.n_seeds, g.P, g.head, g.flags, g.rec, wc,
+                        *reinterpret_cast<ChainQueue<7>*>(&sm));
+      __syncwarp();
     } else {
       tree_lm_run<kTreeMaxDof>(g.rb, mp.tree[g.slot], mp.lp, g.targets, g.seeds, g.n_seeds, g.P, g.head, g.flags,
                                g.rec, sm, wc);

@@ -1,12 +1,14 @@
 // ik_plan.cu -- plans for uneven batches: several (robot, target set, seeds)
-// problem sets solved by one persistent launch (ik_multi_kernel), replayed as a
-// CUDA graph, with a schedule picked by an autotuner.
+// problem sets solved either by one persistent launch (ik_multi_kernel) or by
+// one specialised launch per set (serial, or on forked streams so that their
+// tails overlap), replayed as a CUDA graph, with a schedule picked by an
+// autotuner.
 //
 // A plan fixes its buffers at creation, so the whole solve (workspace reset,
-// the persistent LM kernel, one best-seed reduction per set) is captured once
-// into a graph and every pk_ik_plan_run is a single cudaGraphLaunch.  The
-// autotuner times the candidate schedules -- block size, chain sets on the
-// thread-per-problem or the warp-per-problem path, and the segment order
+// the LM kernels, one best-seed reduction per set) is captured once into a
+// graph and every pk_ik_plan_run is a single cudaGraphLaunch.  The autotuner
+// times the candidate schedules -- kernel variant, block size, chain sets on
+// the thread-per-problem or the warp-per-problem path, and the set order
 // (largest estimated work first, or as given) -- with CUDA events and keeps the
 // fastest; results are cached per device and plan signature.
 #include <math.h>
@@ -45,8 +47,12 @@ struct PlanConfig {
   int block = 128;
   int chains_as_trees = 0;
   int given_order = 0;
-  int variant = 0;  // 0: unconstrained registers, 1: capped for 3 blocks per SM
+  // 0: one persistent launch, registers unconstrained; 1: the same, capped for
+  // 3 blocks per SM; 2: one specialised launch per set, serial; 3: the same on
+  // forked streams.
+  int variant = 0;
 };
+constexpr int kPlanVariants = 4;
 
 struct pk_ik_plan {
   pk_ik_params params;
@@ -59,6 +65,8 @@ struct pk_ik_plan {
   std::vector<int> order;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  cudaStream_t side[pk::kMaxSegs] = {};  // forked streams of variant 3
+  cudaEvent_t fork = nullptr, join[pk::kMaxSegs] = {};
   int device = 0;
   std::string signature;
   float tuned_ms = -1.f;
@@ -135,7 +143,7 @@ void configure(pk_ik_plan* pl, const PlanConfig& cfg) {
   pk::ik_multi_set_common(pl->mp, n, plan_lm(&pl->params), (unsigned long long*)ws);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device);
-  pl->grid = pk::ik_multi_max_blocks_per_sm(cfg.block, cfg.variant) * (sms > 0 ? sms : 1);
+  pl->grid = cfg.variant < 2 ? pk::ik_multi_max_blocks_per_sm(cfg.block, cfg.variant) * (sms > 0 ? sms : 1) : 0;
   if (pl->exec) {
     cudaGraphExecDestroy(pl->exec);
     pl->exec = nullptr;
@@ -146,10 +154,60 @@ void configure(pk_ik_plan* pl, const PlanConfig& cfg) {
   }
 }
 
+// One specialised launch (LM kernel + best-seed reduction) for set i.
+cudaError_t launch_set(pk_ik_plan* pl, int i, cudaStream_t st) {
+  const PlanSet& ps = pl->sets[i];
+  if (ps.batch == 0) return cudaSuccess;
+  char* ws = (char*)pl->d_ws;
+  pk::IkWorkspace w;
+  w.stats = (unsigned long long*)ws;
+  w.head = (int32_t*)(ws + 64 + 4 * i);
+  w.flags = (int32_t*)(ws + ps.flags_off);
+  w.rec = (float*)(ws + ps.rec_off);
+  pk::LmParams lp = plan_lm(&pl->params);
+  if (ps.chain_ok && !pl->cfg.chains_as_trees) {
+    lp.pos_only = ps.pos_only;
+    if (ps.pos_only) lp.tol_rot = INFINITY;
+    return pk::launch_chain_lm(ps.ch, lp, ps.targets, ps.seeds, ps.batch, ps.n_seeds, w, ps.q_out, ps.err_out,
+                               ps.iters_out, ps.status_out, st);
+  }
+  return pk::launch_tree_lm(ps.robot, ps.ti, lp, ps.targets, ps.seeds, ps.batch, ps.n_seeds, w, ps.q_out,
+                            ps.err_out, ps.iters_out, ps.status_out, st);
+}
+
+cudaError_t ensure_side_streams(pk_ik_plan* pl) {
+  if (pl->fork) return cudaSuccess;
+  cudaError_t e = cudaEventCreateWithFlags(&pl->fork, cudaEventDisableTiming);
+  for (size_t i = 0; i < pl->sets.size() && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&pl->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->join[i], cudaEventDisableTiming);
+  }
+  return e;
+}
+
 cudaError_t enqueue(pk_ik_plan* pl, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(pl->d_ws, 0, pl->zero_bytes, st);
   if (e != cudaSuccess) return e;
-  e = pk::launch_ik_multi(pl->mp, pl->cfg.variant, pl->cfg.block, pl->grid, st);
+  const int v = pl->cfg.variant;
+  if (v == 2) {
+    for (int i : pl->order)
+      if ((e = launch_set(pl, i, st)) != cudaSuccess) return e;
+    return cudaSuccess;
+  }
+  if (v == 3) {
+    if ((e = ensure_side_streams(pl)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(pl->fork, st)) != cudaSuccess) return e;
+    for (size_t s = 0; s < pl->order.size(); ++s) {
+      cudaStream_t ss = pl->side[s];
+      if ((e = cudaStreamWaitEvent(ss, pl->fork, 0)) != cudaSuccess) return e;
+      if ((e = launch_set(pl, pl->order[s], ss)) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(pl->join[s], ss)) != cudaSuccess) return e;
+    }
+    for (size_t s = 0; s < pl->order.size(); ++s)
+      if ((e = cudaStreamWaitEvent(st, pl->join[s], 0)) != cudaSuccess) return e;
+    return cudaSuccess;
+  }
+  e = pk::launch_ik_multi(pl->mp, v, pl->cfg.block, pl->grid, st);
   if (e != cudaSuccess) return e;
   for (const PlanSet& ps : pl->sets) {
     if (ps.batch == 0) continue;
@@ -258,6 +316,11 @@ void pk_ik_plan_destroy(pk_ik_plan* pl) {
   if (pl->graph) cudaGraphDestroy(pl->graph);
   if (pl->d_ws) cudaFree(pl->d_ws);
   if (pl->mp) pk::ik_multi_params_free(pl->mp);
+  for (int i = 0; i < pk::kMaxSegs; ++i) {
+    if (pl->side[i]) cudaStreamDestroy(pl->side[i]);
+    if (pl->join[i]) cudaEventDestroy(pl->join[i]);
+  }
+  if (pl->fork) cudaEventDestroy(pl->fork);
   delete pl;
 }
 
@@ -293,9 +356,10 @@ pk_status pk_ik_plan_autotune(pk_ik_plan* pl, int32_t reps, void* stream, float*
   std::vector<PlanConfig> cands;
   bool any_chain = false;
   for (const PlanSet& ps : pl->sets) any_chain = any_chain || ps.chain_ok;
-  for (int variant = 0; variant <= 1; ++variant)
+  for (int variant = 0; variant < kPlanVariants; ++variant)
     for (int block : {64, 128, 256}) {
       if (variant == 1 && block > 128) continue;
+      if (variant >= 2 && block != 128) continue;  // the specialised kernels fix their own blocks
       for (int cat = 0; cat <= (any_chain ? 1 : 0); ++cat)
         for (int go = 0; go <= 1; ++go) cands.push_back(PlanConfig{block, cat, go, variant});
     }
@@ -350,7 +414,7 @@ pk_status pk_ik_plan_set_schedule(pk_ik_plan* pl, int32_t block, int32_t chains_
                                   int32_t variant) {
   if (!pl) return pfail(PK_ERR_INVALID_ARG, "plan is NULL");
   if (block != 64 && block != 128 && block != 256) return pfail(PK_ERR_INVALID_ARG, "block must be 64, 128 or 256");
-  if (variant != 0 && variant != 1) return pfail(PK_ERR_INVALID_ARG, "variant must be 0 or 1");
+  if (variant < 0 || variant >= kPlanVariants) return pfail(PK_ERR_INVALID_ARG, "variant must be in 0..3");
   if (variant == 1 && block > 128) return pfail(PK_ERR_INVALID_ARG, "variant 1 takes blocks of at most 128");
   configure(pl, PlanConfig{block, chains_as_trees ? 1 : 0, given_order ? 1 : 0, variant});
   return PK_OK;

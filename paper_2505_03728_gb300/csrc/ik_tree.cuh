@@ -281,6 +281,22 @@ __device__ __forceinline__ bool tree_solve(const float (&Arow)[N], float g, floa
 
 namespace pk {
 
+#ifndef PK_CLAIM_ORDER
+#define PK_CLAIM_ORDER 1
+#endif
+// Problem index -> (target, seed).  Without cancellation: target-major.  With
+// it: seeds are claimed in waves (PK_CLAIM_ORDER 1: one seed per wave, i.e.
+// seed-major; 2: waves of four seeds, target-major inside a wave; 0:
+// target-major throughout).
+__device__ __forceinline__ void claim_order(int prob, int batch, int n_seeds, bool cancel, int* tgt, int* sd) {
+  const int W = (!cancel || PK_CLAIM_ORDER == 0) ? n_seeds : (PK_CLAIM_ORDER == 1 ? 1 : 4);
+  const int wave_size = batch * W;
+  const int wave = prob / wave_size, r = prob - wave * wave_size;
+  const int w_here = min(W, n_seeds - wave * W);  // the last wave may be narrower
+  *tgt = r / w_here;
+  *sd = wave * W + r % w_here;
+}
+
 // Work counters kept per lane and flushed once per warp.
 struct WorkCount {
   unsigned eval = 0, build = 0, solve = 0, done = 0;
@@ -296,12 +312,29 @@ __device__ void tree_lm_run(const RobotDev* __restrict__ rb, const TreeInfo& ti,
   const int lane = threadIdx.x & 31;
   const int n = ti.n_dof, k = ti.k;
   const int np = (n + 3) & ~3, stride = np + 4;
+  const int batch = P / n_seeds;
   for (;;) {
     int prob = 0;
     if (lane == 0) prob = atomicAdd(head, 1);
     prob = __shfl_sync(kTreeFull, prob, 0);
     if (prob >= P) break;
-    const int tgt = prob / n_seeds;
+    // seed-major order and claim-time skipping under sibling cancellation
+    int sd, tgt;
+    claim_order(prob, batch, n_seeds, lp.cancel != 0, &tgt, &sd);
+    const int pid = tgt * n_seeds + sd;
+    if (lp.cancel) {
+      int c = 0;
+      if (lane == 0) c = __ldcg(flags + tgt);
+      if (__shfl_sync(kTreeFull, c, 0)) {
+        if (lane == 0) {
+          float* r = rec + (size_t)pid * stride;
+          r[np + 0] = INFINITY;
+          r[np + 3] = __int_as_float(PK_P_CANCELLED << 24);
+          ++wc.done;
+        }
+        continue;
+      }
+    }
     if (lane < k) {
       Rt T, Ti;
       rt_load(targets + ((size_t)tgt * k + lane) * 12, T);
@@ -313,7 +346,7 @@ __device__ void tree_lm_run(const RobotDev* __restrict__ rb, const TreeInfo& ti,
       }
       rt_store(sm.Ti[lane], Ti);
     }
-    float q = lane < n ? __ldg(seeds + (size_t)prob * n + lane) : 0.f;
+    float q = lane < n ? __ldg(seeds + (size_t)pid * n + lane) : 0.f;
     sm.q[lane] = q;
     __syncwarp();
     float pe, re;
@@ -370,7 +403,7 @@ __device__ void tree_lm_run(const RobotDev* __restrict__ rb, const TreeInfo& ti,
         }
       }
     }
-    float* r = rec + (size_t)prob * stride;
+    float* r = rec + (size_t)pid * stride;
     if (lane < n) r[lane] = q;
     if (lane == 0) {
       r[np + 0] = f;
@@ -382,6 +415,80 @@ __device__ void tree_lm_run(const RobotDev* __restrict__ rb, const TreeInfo& ti,
     }
     __syncwarp();
   }
+}
+
+}  // namespace pk
+
+namespace pk {
+
+// ---------------------------------------------------------------------------
+// Per-warp problem queue for the thread-per-problem chain kernel.  The warp
+// claims problems 32 at a time (one atomic) and copies their target poses,
+// seeds and cancellation flags into shared memory with cp.async while it keeps
+// iterating, double-buffered, so a lane that finishes a problem refills from
+// shared memory instead of waiting on global memory.  The prefetched flag may
+// be stale; it only lets a solved target's seed be skipped early, the loop's
+// own flag poll is authoritative.
+constexpr int kQ = 32;
+
+template <int N>
+struct ChainQueue {
+  alignas(16) float tgt[2][kQ][12];
+  float seed[2][kQ][N];
+  int32_t flag[2][kQ];
+  int32_t pid[2][kQ];  // record index, or -1 past the end
+  int32_t tid[2][kQ];  // target index
+};
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one_pending() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Claim the next 32 problems into buffer `buf` and start copying their inputs.
+template <int N>
+__device__ __forceinline__ void chain_chunk_claim(ChainQueue<N>& q, int buf, int32_t* head, int P, int batch,
+                                                  int n_seeds, bool cancel, const float* __restrict__ targets,
+                                                  const float* __restrict__ seeds, const int32_t* flags, int lane) {
+  int base = 0;
+  if (lane == 0) base = atomicAdd(head, kQ);
+  base = __shfl_sync(kTreeFull, base, 0);
+  const int p = base + lane;
+  if (p < P) {
+    int tgt, sd;
+    claim_order(p, batch, n_seeds, cancel, &tgt, &sd);
+    const int pid = tgt * n_seeds + sd;
+    q.pid[buf][lane] = pid;
+    q.tid[buf][lane] = tgt;
+    const float* tp = targets + (size_t)tgt * 12;
+    if ((reinterpret_cast<uintptr_t>(targets) & 15) == 0) {
+      cp_async16(&q.tgt[buf][lane][0], tp);
+      cp_async16(&q.tgt[buf][lane][4], tp + 4);
+      cp_async16(&q.tgt[buf][lane][8], tp + 8);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 12; ++j) cp_async4(&q.tgt[buf][lane][j], tp + j);
+    }
+    const float* sp = seeds + (size_t)pid * N;
+#pragma unroll
+    for (int j = 0; j < N; ++j) cp_async4(&q.seed[buf][lane][j], sp + j);
+    if (cancel)
+      cp_async4(&q.flag[buf][lane], flags + tgt);
+    else
+      q.flag[buf][lane] = 0;
+  } else {
+    q.pid[buf][lane] = -1;
+  }
+  cp_async_commit();
 }
 
 }  // namespace pk

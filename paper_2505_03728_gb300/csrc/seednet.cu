@@ -189,13 +189,24 @@ __device__ __forceinline__ void pose_features(const pk::Rt& T, float* f) {
   f[6] = T.r[1]; f[7] = T.r[4]; f[8] = T.r[7];
 }
 
+// One row of features: 16-byte stores into X (8 BF16 at a time), scalar
+// stores into the transposed copy used by the weight gradient.
 __device__ __forceinline__ void store_features(const float* f, int in_dim, int in_pad, int row, int m_pad,
                                                __nv_bfloat16* X, __nv_bfloat16* Xt) {
-  for (int i = 0; i < in_pad; ++i) {
-    const __nv_bfloat16 v = __float2bfloat16_rn(i < in_dim ? f[i] : 0.f);
-    X[(size_t)row * in_pad + i] = v;
-    if (Xt) Xt[(size_t)i * m_pad + row] = v;
+  uint4* xr = reinterpret_cast<uint4*>(X + (size_t)row * in_pad);
+  for (int c = 0; c < in_pad; c += 8) {
+    uint4 pk4;
+    uint32_t* w = reinterpret_cast<uint32_t*>(&pk4);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int a = c + 2 * i;
+      __nv_bfloat162 h = __floats2bfloat162_rn(a < in_dim ? f[a] : 0.f, a + 1 < in_dim ? f[a + 1] : 0.f);
+      w[i] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    xr[c / 8] = pk4;
   }
+  if (Xt)
+    for (int i = 0; i < in_pad; ++i) Xt[(size_t)i * m_pad + row] = __float2bfloat16_rn(i < in_dim ? f[i] : 0.f);
 }
 
 // Features of given target poses [B][k][12]; rows >= B are zero.
@@ -327,16 +338,6 @@ __global__ void cast_weights_kernel(const float* __restrict__ w, int out, int in
   Wt[(size_t)c * out + o] = h;
 }
 
-// Seeds [B][K][n] from the pre-head outputs.
-__global__ void seeds_head_kernel(const float* __restrict__ Y, int ldy, int B, int K, int n,
-                                  const float* __restrict__ lohi, float* seeds) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= B * K * n) return;
-  const int b = i / (K * n), r = i % (K * n), j = r % n;
-  const float lo = lohi[j], hi = lohi[n + j];
-  seeds[i] = 0.5f * (lo + hi) + 0.5f * (hi - lo) * tanhf(Y[(size_t)b * ldy + r]);
-}
-
 // ---------------------------------------------------------------- host helpers
 
 void free_acts(pk_seednet* s) {
@@ -397,7 +398,8 @@ cudaError_t cast_all(pk_seednet* s, cudaStream_t st) {
 
 // Forward pass of m_pad rows whose features are in s->X (m_valid real rows).
 // With `train`, pre-activations and transposed activations are kept.
-cudaError_t forward(pk_seednet* s, int m_valid, int m_pad, bool train, cudaStream_t st) {
+cudaError_t forward(pk_seednet* s, int m_valid, int m_pad, bool train, cudaStream_t st,
+                    float* seeds_out = nullptr) {
   const __nv_bfloat16* a = s->X;
   int K = s->in_pad;
   for (int l = 0; l < s->depth; ++l) {
@@ -417,12 +419,14 @@ cudaError_t forward(pk_seednet* s, int m_valid, int m_pad, bool train, cudaStrea
     K = s->width;
   }
   Epilogue ep{};
-  ep.mode = pk::tc::EPI_FWD_LINEAR;
+  ep.mode = seeds_out ? pk::tc::EPI_SEEDS : pk::tc::EPI_FWD_LINEAR;
   ep.m_valid = m_valid;
-  ep.n_valid = s->out_pad;
+  ep.n_valid = seeds_out ? s->out_dim : s->out_pad;
   ep.bias = s->master + s->b_off[s->depth];
-  ep.out_f32 = s->Y;
-  ep.ld_f32 = s->out_pad;
+  ep.out_f32 = seeds_out ? seeds_out : s->Y;
+  ep.ld_f32 = seeds_out ? s->out_dim : s->out_pad;
+  ep.lohi = s->d_lohi;
+  ep.n_dof = s->n_dof;
   return gemm(a, m_pad, s->W[s->depth], s->out_pad, K, 1, ep, s->d_err, st);
 }
 
@@ -717,13 +721,8 @@ pk_status pk_seednet_infer(pk_seednet* s, int32_t batch, const float* d_targets,
   if (ps != PK_OK) return ps;
   features_kernel<<<(m_pad + 127) / 128, 128, 0, st>>>(d_targets, batch, s->k, s->in_pad, m_pad, s->X, nullptr);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = forward(s, batch, m_pad, false, st);
-  if (e == cudaSuccess) {
-    const int n = batch * s->K * s->n_dof;
-    seeds_head_kernel<<<(n + 255) / 256, 256, 0, st>>>(s->Y, s->out_pad, batch, s->K, s->n_dof, s->d_lohi,
-                                                       d_seeds_out);
-    e = cudaGetLastError();
-  }
+  // the head q = mid + half tanh(y) runs in the output layer's epilogue
+  if (e == cudaSuccess) e = forward(s, batch, m_pad, false, st, d_seeds_out);
   return sn_cuda(e, "pk_seednet_infer");
 }
 

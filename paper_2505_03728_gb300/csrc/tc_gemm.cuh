@@ -33,6 +33,7 @@ enum EpiMode : int {
   EPI_FWD_LINEAR = 1,  // y = acc + b -> f32 [M][n_valid]
   EPI_DGRAD_SILU = 2,  // d = acc * silu'(Zprev) -> bf16 row-major + transposed
   EPI_WGRAD_ADD = 3,   // atomically add acc into f32 [M][N] (split-K partial sums)
+  EPI_SEEDS = 4,       // q = mid + half tanh(acc + b) -> f32 [M][n_valid] (seed-network head)
 };
 
 struct Epilogue {
@@ -48,6 +49,8 @@ struct Epilogue {
   int ld_t;
   const float* zprev;       // DGRAD_SILU: pre-activation [M][ld_zprev]
   int ld_zprev;
+  const float* lohi;        // SEEDS: joint limits [2][n_dof]
+  int n_dof;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -183,6 +186,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 __device__ __forceinline__ float silu_f(float z) { return z / (1.f + __expf(-z)); }
+// SiLU through one MUFU tanh: z sigmoid(z) = z (1 + tanh(z / 2)) / 2.  The
+// hardware tanh approximation (relative error ~2^-11) is below the BF16
+// rounding the output receives.
+__device__ __forceinline__ float silu_fast(float z) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
+  return 0.5f * z * (1.f + t);
+}
 __device__ __forceinline__ float dsilu_f(float z) {
   const float s = 1.f / (1.f + __expf(-z));
   return s * (1.f + z * (1.f - s));
@@ -220,7 +231,13 @@ struct SmemLayout {
   static constexpr uint32_t kTmemCols = 2 * BN;           // two accumulator buffers
 };
 
-constexpr int kThreads = 192;  // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
+#ifndef PK_EPI_WARPS
+#define PK_EPI_WARPS 8
+#endif
+// Epilogue warps: two per TMEM lane quarter, each taking half of the columns
+// (or one per quarter with 4).
+constexpr int kEpiWarps = PK_EPI_WARPS;
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // warp 0: TMA, warp 1: MMA, then the epilogue warps
 
 // Epilogue of 32 columns [col0, col0 + 32) of one accumulator row.
 __device__ __forceinline__ void epilogue32(const Epilogue& ep, int row, bool row_ok, int col0, float* v) {
@@ -241,6 +258,21 @@ __device__ __forceinline__ void epilogue32(const Epilogue& ep, int row, bool row
     }
     return;
   }
+  if (ep.mode == EPI_SEEDS) {
+    if (row_ok) {
+      float* o = ep.out_f32 + (size_t)row * ep.ld_f32;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int c = col0 + i;
+        if (c < ep.n_valid) {
+          const int j = c % ep.n_dof;
+          const float lo = __ldg(ep.lohi + j), hi = __ldg(ep.lohi + ep.n_dof + j);
+          o[c] = 0.5f * (lo + hi) + 0.5f * (hi - lo) * tanhf(v[i] + __ldg(ep.bias + c));
+        }
+      }
+    }
+    return;
+  }
   float a[32];
   if (ep.mode == EPI_FWD_SILU) {
     const float4* b4 = (const float4*)(ep.bias + col0);
@@ -250,7 +282,7 @@ __device__ __forceinline__ void epilogue32(const Epilogue& ep, int row, bool row
       v[4 * i + 0] += b.x; v[4 * i + 1] += b.y; v[4 * i + 2] += b.z; v[4 * i + 3] += b.w;
     }
 #pragma unroll
-    for (int i = 0; i < 32; ++i) a[i] = __fdividef(v[i], 1.f + __expf(-v[i]));
+    for (int i = 0; i < 32; ++i) a[i] = silu_fast(v[i]);
     if (ep.out_f32 && row_ok) {
       float4* o = (float4*)(ep.out_f32 + (size_t)row * ep.ld_f32 + col0);
 #pragma unroll
@@ -315,7 +347,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 4);
+      mbar_init(&tempty[a], kEpiWarps);
     }
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -391,8 +423,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncwarp();
   } else {
-    // ---- epilogue warps: warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31
+    // ---- epilogue warps: warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31,
+    //      columns [h BN / H, (h + 1) BN / H) with h = (w - 2) / 4, H = kEpiWarps / 4
     const int q = warp & 3;
+    constexpr int H = kEpiWarps / 4;
+    const int h = (warp - 2) / 4;
     uint32_t tc = 0;
     for (int t = blockIdx.x; t < n_tiles_total; t += gridDim.x, ++tc) {
       const int r = t % (m_tiles * n_tiles);
@@ -408,7 +443,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool row_ok = row < ep.m_valid;
       const uint32_t base = tmem + acc * BN + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = h * (BN / H); c0 < (h + 1) * (BN / H); c0 += 32) {
         float v[32];
         tmem_ld32(base + (uint32_t)c0, v);
         epilogue32(ep, row, row_ok, n0 + c0, v);

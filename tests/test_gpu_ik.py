@@ -204,12 +204,11 @@ def test_edge_cases():
     assert np.all(iters == 0)
     for b in range(8):
         assert any(np.allclose(q[b], seeds8[b, s], atol=0) for s in range(8))
-    # trees are not served by the chain kernel
-    hand, tips = synth.hand_robot(102)
-    gh = pk.Robot.from_spec(hand)
+    # more movable joints than a warp has lanes are refused on the host
+    big = synth.chain_robot(7, 33)
+    gb = pk.Robot.from_spec(big)
     with pytest.raises(pk.PkError) as e:
-        pk.pk_ik_solve(gh, p, [int(tips[0])], None, dev(np.zeros((2, 1, 12))),
-                       dev(np.zeros((2, 1, gh.n_dof))))
+        pk.pk_ik_solve(gb, p, [gb.n_joints - 1], None, dev(np.zeros((2, 1, 12))), dev(np.zeros((2, 1, 33))))
     assert e.value.status == pk.PK_ERR_UNSUPPORTED
 
 

@@ -77,11 +77,12 @@ def test_autotuned_schedule_keeps_results_valid():
         for i in np.nonzero(b[3] == 0)[0]:
             pe, re = oracle.ik_errors(o, tg, Th[i], b[0][i])
             assert pe <= 1e-3 * (1 + 1e-3) and re <= np.deg2rad(0.5) * (1 + 1e-3), name
-    # every schedule is valid: force the other chain path and the given order
-    plan.set_schedule(block=64, chains_as_trees=1 - sched["chains_as_trees"], given_order=1,
-                      variant=1 - sched["variant"])
-    other = host(plan.run())
-    for a, b in zip(base, other):
-        assert (a[3] == b[3]).mean() >= 0.97
+    # every schedule is valid: each variant, the other chain path, the given order
+    for variant in range(4):
+        plan.set_schedule(block=64, chains_as_trees=1 - sched["chains_as_trees"], given_order=1,
+                          variant=variant)
+        other = host(plan.run())
+        for a, b in zip(base, other):
+            assert (a[3] == b[3]).mean() >= 0.97, variant
     st = plan.stats()
     assert st["problems"] > 0
