@@ -43,6 +43,15 @@ FLOPS_PER_EVAL = 1207.4
 FLOPS_PER_BUILD = 1362.0
 FLOPS_PER_SOLVE = 172.4
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
+# DRAM bytes (read + write) per target of the LM kernel: ncu capture of the
+# 16,384-target learned-seed launch (4.594 MB), inputs read once (see profiles/).
+LM_DRAM_BYTES_PER_TARGET = 4593920 / 16384
+# FP32 operations per trajectory-iteration of the trajectory kernel (ncu count
+# over 64 trajectories x 50 iterations, see profiles/).
+TRAJ_FLOPS_PER_ITER = 1.995e6
+
+
+CASES = ("lm", "lm-learned", "seednet", "tree", "trajopt")
 
 
 def parse():
@@ -57,6 +66,9 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--train-epochs", type=int, default=8)
     ap.add_argument("--no-extra", action="store_true", help="skip the uneven-batch and trajectory lines")
+    ap.add_argument("--case", choices=CASES, default=None,
+                    help="profiling case: run one small kernel workload (a few launches, --batch sized) and exit; "
+                         "prints one status line, no JSON")
     return ap.parse_args()
 
 
@@ -210,10 +222,11 @@ class Timed:
         self.e = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
 
     def run(self, step_fn, stream):
+        """step_fn(k) enqueues timed step k."""
         for k in range(self.steps):
             self.flush.zero_()
             self.s[k].record(stream)
-            step_fn()
+            step_fn(k)
             self.e[k].record(stream)
         self.torch.cuda.synchronize()
         return float(sum(a.elapsed_time(b) for a, b in zip(self.s, self.e)))
@@ -255,7 +268,7 @@ def extra_workloads(torch, pk, synth, args, flush, stream):
     timed = Timed(torch, steps, flush)
     conv = torch.zeros((), dtype=torch.int64, device="cuda")
 
-    def run():
+    def run(k):
         outs = plan.run()
         for o in outs:
             conv.add_((o[3] == pk.PK_P_CONVERGED).sum())
@@ -282,15 +295,19 @@ def extra_workloads(torch, pk, synth, args, flush, stream):
     timed = Timed(torch, tsteps, flush)
     holder = {}
 
-    def trun():
+    def trun(k):
         holder["r"] = pk.pk_trajopt_solve(g, tp, *targs)
     pk.pk_trace_enable(True)
     tms = timed.run(trun, stream)
     t_ms, t_n = pk.pk_trace_summary("trajopt")
     pk.pk_trace_enable(False)
     st = holder["r"][2].cpu().numpy()
+    k_ms = t_ms / max(1, t_n)
+    t_tf = cfg["batch"] * cfg["iters"] * TRAJ_FLOPS_PER_ITER / (k_ms / 1e3) / 1e12
     out["trajopt"] = {"workload": cfg["name"], "value": cfg["batch"] * tsteps / (tms / 1e3), "unit": "trajectories/s",
-                      "ms_per_step": tms / tsteps, "kernel_ms": t_ms / max(1, t_n),
+                      "ms_per_step": tms / tsteps, "kernel_ms": k_ms,
+                      "roofline": {"bound": "alu", "kernel": "trajopt_kernel<7>", "achieved": t_tf,
+                                   "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": t_tf / FP32_PEAK_TFLOPS},
                       "goal_reached": float(np.mean((st & pk.PK_T_GOAL_MISSED) == 0)),
                       "collision_free": float(np.mean((st & pk.PK_T_COLLISION) == 0)),
                       "config": {"T": cfg["T"], "iters": cfg["iters"], "obstacles": cfg["n_obstacles"],
@@ -298,8 +315,74 @@ def extra_workloads(torch, pk, synth, args, flush, stream):
     return out
 
 
+def run_case(args):
+    """Small single-kernel workloads for ncu captures (the commands in profiles/):
+    lm          pk_ik_solve, 7-DoF chain, uniform seeds, --batch targets x 8, 2 solves
+    lm-learned  the same with seeds from a briefly trained seed network
+    seednet     pk_seednet_infer of an untrained network over --batch targets, 3 calls
+    tree        pk_ik_solve on the 30-joint humanoid (6 pose targets), --batch targets x 8, 2 solves
+    trajopt     pk_trajopt_solve, --batch trajectories of the trajectory workload, 2 solves"""
+    import torch
+    from paper_2505_03728_gb300 import build, pk, scenes, synth
+    build.build()
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    B = args.batch
+    if args.case in ("lm", "lm-learned", "seednet"):
+        spec, qt, sd = synth.ik_workload(synth.IK_THROUGHPUT, B)
+        g = pk.Robot.from_spec(spec)
+        ee = g.n_joints - 1
+        T = pk.pk_fk(g, dev(qt))[:, ee:ee + 1].contiguous()
+        seeds = dev(sd)
+        if args.case != "lm":
+            net = pk.SeedNet(g, [ee], K=8, width=512, depth=4, seed=11)
+            if args.case == "seednet":
+                for _ in range(3):
+                    seeds = pk.pk_seednet_infer(net, T)
+                torch.cuda.synchronize()
+                print("ok seednet", B, float(seeds.abs().mean()))
+                return
+            pk.pk_seednet_train(net, pk.pk_train_params_default(epochs=2, steps_per_epoch=600))
+            seeds = pk.pk_seednet_infer(net, T)
+        p = pk.pk_ik_params_default(cancel_siblings=1)
+        ws = torch.empty(pk.pk_ik_workspace_bytes(g, B, 8), dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            out = pk.pk_ik_solve(g, p, [ee], None, T, seeds, ws)
+        torch.cuda.synchronize()
+        print("ok", args.case, B, pk.pk_ik_workspace_stats(ws), float((out[3] == 0).float().mean()))
+    elif args.case == "tree":
+        spec, ends = synth.humanoid_robot(103)
+        g = pk.Robot.from_spec(spec)
+        links = list(ends)
+        qt = synth.uniform_q(203, B, spec.dof_lower, spec.dof_upper)
+        sd = dev(synth.uniform_q(303, (B, 8), spec.dof_lower, spec.dof_upper))
+        T = pk.pk_fk(g, dev(qt))[:, links].contiguous()
+        p = pk.pk_ik_params_default(max_iters=50, early_exit=1, cancel_siblings=1)
+        ws = torch.empty(pk.pk_ik_workspace_bytes(g, B, 8), dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            out = pk.pk_ik_solve(g, p, links, None, T, sd, ws)
+        torch.cuda.synchronize()
+        print("ok tree", B, pk.pk_ik_workspace_stats(ws), float((out[3] == 0).float().mean()))
+    elif args.case == "trajopt":
+        cfg = synth.TRAJOPT
+        spec, qs_c, qg_c, radii, obs, plane = synth.trajopt_workload(cfg)
+        g = pk.Robot.from_spec(spec)
+        pts = lambda q: pk.pk_fk(g, dev(q)).cpu().numpy()[:, :, [3, 7, 11]].astype(np.float64)
+        qs = scenes.pick_clear(qs_c, pts(qs_c), radii, obs, plane, 0.02, B)
+        qg = scenes.pick_clear(qg_c, pts(qg_c), radii, obs, plane, 0.02, B)
+        goals = pk.pk_fk(g, dev(qg))[:, -1].contiguous()
+        x0 = dev(synth.linear_interpolation(qs, qg, cfg["T"]))
+        tp = pk.pk_trajopt_params_default(iters=cfg["iters"])
+        for _ in range(2):
+            out = pk.pk_trajopt_solve(g, tp, dev(qs), goals, x0, dev(radii), dev(obs), plane)
+        torch.cuda.synchronize()
+        print("ok trajopt", B, float(out[1].mean()))
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args)
+        return
     from paper_2505_03728_gb300 import synth
     cfg = dict(synth.IK_THROUGHPUT)
     cfg["batch"] = args.batch
@@ -331,10 +414,13 @@ def main():
             torch.empty(B, dtype=torch.int32, device="cuda"), torch.empty(B, dtype=torch.int32, device="cuda"))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    conv = torch.zeros((), dtype=torch.int64, device="cuda")
 
-    def plain_step():
-        pk.pk_ik_solve(robot, params, [ee], None, targets, seeds, ws, out=outs)
+    # each timed step writes its own status row; converged targets are counted
+    # after the timed region
+    status_steps = torch.empty(max(args.steps, 1), B, dtype=torch.int32, device="cuda")
+
+    def plain_step(status):
+        pk.pk_ik_solve(robot, params, [ee], None, targets, seeds, ws, out=outs[:3] + (status,))
 
     # ---- learned seeds: train once (untimed), then infer + solve per step
     net = None
@@ -347,9 +433,9 @@ def main():
         train_s = time.perf_counter() - t0
         lseeds = torch.empty(B, S, n, device="cuda")
 
-    def learned_step():
+    def learned_step(status):
         pk.pk_seednet_infer(net, targets, lseeds)
-        pk.pk_ik_solve(robot, params, [ee], None, targets, lseeds, ws, out=outs)
+        pk.pk_ik_solve(robot, params, [ee], None, targets, lseeds, ws, out=outs[:3] + (status,))
 
     props = torch.cuda.get_device_properties(local)
     gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
@@ -358,27 +444,22 @@ def main():
     with ClockSampler(gpu_id) as clocks:
         for name, fn in arms:
             for _ in range(args.warmup):  # the same kernels the timed steps launch
-                fn()
-                conv.add_((outs[3] == pk.PK_P_CONVERGED).sum())
+                fn(outs[3])
             torch.cuda.synchronize()
             if world > 1:
                 import torch.distributed as dist
                 dist.barrier()
-            conv.zero_()
             pk.pk_trace_enable(True)
             timed = Timed(torch, args.steps, flush)
-
-            def counted():
-                fn()
-                conv.add_((outs[3] == pk.PK_P_CONVERGED).sum())
             torch.cuda.nvtx.range_push(f"timed_{name}")
-            total_ms = timed.run(counted, stream)
+            total_ms = timed.run(lambda k: fn(status_steps[k]), stream)
             torch.cuda.nvtx.range_pop()
             lm_ms, lm_n = pk.pk_trace_summary("ik_lm")
             gemm_ms, gemm_n = pk.pk_trace_summary("gemm")
+            launches = lm_n + gemm_n + sum(pk.pk_trace_summary(k)[1] for k in ("ik_reduce", "features"))
             pk.pk_trace_enable(False)
             stats = pk.pk_ik_workspace_stats(ws)
-            n_conv = int(conv.item())
+            n_conv = int((status_steps[:args.steps] == pk.PK_P_CONVERGED).sum().item())
             if world > 1:
                 import torch.distributed as dist
                 dist.barrier()
@@ -386,7 +467,7 @@ def main():
             results[name] = dict(value=n_conv / (total_ms / 1e3), ms_per_step=total_ms / args.steps,
                                  success_rate=n_conv / (B * args.steps * world), lm_ms=lm_ms / max(1, lm_n),
                                  gemm_ms=gemm_ms / max(1, args.steps), gemm_launches=gemm_n // max(1, args.steps),
-                                 stats=stats)
+                                 launches=launches, stats=stats)
 
     # ---- end to end through the public API with host buffers (headline path)
     head = "learned" if net is not None else "plain"
@@ -426,15 +507,17 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return
+    def lm_roofline(r):
+        st = r["stats"]
+        fl = st["evals"] * FLOPS_PER_EVAL + st["builds"] * FLOPS_PER_BUILD + st["solves"] * FLOPS_PER_SOLVE
+        tf = fl / (r["lm_ms"] / 1e3) / 1e12
+        return {"bound": "alu", "kernel": "chain_lm_kernel<7>", "achieved": tf, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": tf / FP32_PEAK_TFLOPS, "traffic": LM_DRAM_BYTES_PER_TARGET * B,
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (unit counts x max clock)",
+                "ms_per_launch": r["lm_ms"], "work_per_launch": st}
+
     r = results[head]
-    st = r["stats"]
-    lm_flops = (st["evals"] * FLOPS_PER_EVAL + st["builds"] * FLOPS_PER_BUILD + st["solves"] * FLOPS_PER_SOLVE)
-    lm_tf = lm_flops / (r["lm_ms"] / 1e3) / 1e12
-    lm_roof = {"bound": "alu", "kernel": "chain_lm_kernel<7>", "achieved": lm_tf, "peak": FP32_PEAK_TFLOPS,
-               "unit": "TFLOP/s", "frac": lm_tf / FP32_PEAK_TFLOPS, "traffic": None,
-               "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (unit counts x max clock)",
-               "ms_per_launch": r["lm_ms"], "work_per_launch": st}
-    roofs = [lm_roof]
+    roofs = [lm_roofline(r)]
     if head == "learned":
         peak, src = measured_bf16_peak()
         fl = seednet_flops(64, 512, 4, 64, ((B + 127) // 128) * 128)
@@ -451,12 +534,13 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_dict(cfg, args, head),
         "success_rate": r["success_rate"],
-        "plain": {k: results["plain"][k] for k in ("value", "ms_per_step", "success_rate", "lm_ms")},
+        "plain": dict({k: results["plain"][k] for k in ("value", "ms_per_step", "success_rate", "lm_ms")},
+                      roofline=lm_roofline(results["plain"])),
         "roofline": dominant,
         "roofline_other": [x for x in roofs if x is not dominant],
         "e2e": {"value": e2e_conv / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * (9 if head == "learned" else 2),
+        "gpu_launches": r["launches"],
         "clocks": clocks.summary(),
     }
     if "learned" in results:

@@ -9,8 +9,8 @@
 // the Jacobian is formed one target at a time (lane i writes column i of the
 // target's rows into shared memory) and lane i accumulates row i of J^T J and
 // entry i of J^T r in registers; the damped system is factored by a
-// warp-shuffle Cholesky (lane i holds row i) and solved by forward and
-// backward substitution with broadcasts and warp reductions.
+// right-looking Cholesky with the factor in shared memory (lane i updates row
+// i) and solved by forward and backward substitution.
 #pragma once
 #include "pk_internal.h"
 #include "pk_math.cuh"

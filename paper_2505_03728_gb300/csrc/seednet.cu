@@ -719,7 +719,10 @@ pk_status pk_seednet_infer(pk_seednet* s, int32_t batch, const float* d_targets,
   const int m_pad = round_up(batch, 128);
   pk_status ps = ensure_acts(s, m_pad);
   if (ps != PK_OK) return ps;
-  features_kernel<<<(m_pad + 127) / 128, 128, 0, st>>>(d_targets, batch, s->k, s->in_pad, m_pad, s->X, nullptr);
+  {
+    pk::TraceScope tr("features", st);
+    features_kernel<<<(m_pad + 127) / 128, 128, 0, st>>>(d_targets, batch, s->k, s->in_pad, m_pad, s->X, nullptr);
+  }
   cudaError_t e = cudaGetLastError();
   // the head q = mid + half tanh(y) runs in the output layer's epilogue
   if (e == cudaSuccess) e = forward(s, batch, m_pad, false, st, d_seeds_out);

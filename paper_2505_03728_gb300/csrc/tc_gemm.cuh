@@ -4,12 +4,15 @@
 //
 //   D[M x N] (FP32, in TMEM) = A[M x K] * B[N x K]^T      A, B: BF16, K-major
 //
-// One CTA (128 threads, 4 warps) computes one 128 x BN tile (BN = 64, 128 or
-// 256), optionally over a slice of K (split-K, grid.z).  Warp 0 / lane 0 issues
-// the TMA loads of a 4-stage ring (128B-swizzled 64-wide K blocks), warp 1 /
-// lane 0 issues tcgen05.mma (M = 128, N = BN, K = 16, four per K block) and
-// commits each stage back to the producer; then all four warps read their 32
-// accumulator rows out of TMEM (tcgen05.ld 32x32b) and run the epilogue.
+// Persistent kernel, one CTA per SM striding over the (m, n, k-split) output
+// tiles of 128 x BN (BN = 64, 128 or 256; split-K over grid tiles for the
+// weight gradients).  Warp 0 / lane 0 issues the TMA loads of a 4-stage ring
+// (128B-swizzled 64-wide K blocks), warp 1 / lane 0 issues tcgen05.mma (M = 128,
+// N = BN, K = 16, four per K block) into one of two TMEM accumulators and
+// commits each stage back to the producer; eight epilogue warps (two per TMEM
+// lane quarter, each taking half of the columns) read the other accumulator
+// with tcgen05.ld 32x32b and run the fused epilogue, so the epilogue of one
+// tile overlaps the MMAs of the next.
 //
 // Every mbarrier wait is bounded (1 s of %globaltimer); on timeout the kernel
 // records an error code in *err, skips the rest of its work, frees its TMEM
@@ -321,7 +324,7 @@ __device__ __forceinline__ void epilogue32(const Epilogue& ep, int row, bool row
 }
 
 // Persistent GEMM: CTAs stride over the (m, n, k-split) tiles; the MMA warp
-// fills one TMEM accumulator while the four epilogue warps drain the other.
+// fills one TMEM accumulator while the epilogue warps drain the other.
 template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
