@@ -78,7 +78,7 @@ def lib():
             L.or_cholesky_solve.restype = C.c_int32
             L.or_ik_solve.restype = C.c_int32
             for name in ("or_traj_solve", "or_mlp_forward", "or_mlp_loss_grad", "or_traj_n_residuals",
-                         "or_banded_cholesky", "or_host_cores"):
+                         "or_banded_cholesky", "or_host_cores", "or_ik_beam"):
                 if hasattr(L, name):
                     getattr(L, name).restype = C.c_int32
             for name in ("or_coll_activation", "or_traj_normal"):
@@ -254,6 +254,29 @@ def ik_solve(robot: Robot, params: IkParams, tg: Targets, targets, seeds, n_trac
         out["trace"] = tr
         out["margin"] = mg
     return out
+
+
+def ik_beam(robot: Robot, params: IkParams, tg: Targets, targets, seeds, steps1=6, keep=4, steps2=10,
+            n_threads=0):
+    """IK-Beam (Sec. V-C).  targets [B][k][12], seeds [B][S][n_dof]; steps1 LM
+    iterations on all S seeds, the `keep` lowest-cost seeds continue for steps2.
+
+    Returns a dict with q [B][n], err [B][2], iters [B], status [B], kept [B][keep]
+    (selected seed indices, in selection order) and threads."""
+    targets = _f64(targets).reshape(-1, tg.k, 12)
+    B = targets.shape[0]
+    seeds = _f64(seeds).reshape(B, -1, robot.n_dof)
+    S = seeds.shape[1]
+    n = robot.n_dof
+    q = np.zeros((B, n))
+    err = np.zeros((B, 2))
+    iters = np.zeros(B, np.int32)
+    status = np.zeros(B, np.int32)
+    kept = np.zeros((B, keep), np.int32)
+    threads = lib().or_ik_beam(C.byref(robot._c), C.byref(params._c), C.byref(tg._c), B, S, int(steps1),
+                               int(keep), int(steps2), _p(targets), _p(seeds), _p(q), _p(err), _p(iters),
+                               _p(status), _p(kept), int(n_threads))
+    return dict(q=q, err=err, iters=iters, status=status, kept=kept, threads=int(threads))
 
 
 # ---------------------------------------------------------------- seed network

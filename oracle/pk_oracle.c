@@ -467,9 +467,12 @@ static int converged(const or_ik_params* p, double pe, double re) {
   return pe <= p->tol_pos && re <= p->tol_rot;
 }
 
+/* One LM run (Sec. III-A) from `seed` with damping lambda_init (the LM state
+ * of an earlier run, or p->lambda0 when negative); the damping after the last
+ * iteration goes to *lambda_out when given. */
 static void lm_problem(const or_robot* rb, const or_ik_params* p, const or_target_spec* ts,
                        const double* targets, const double* seed, double* q, lm_result* res,
-                       int n_trace, double* trace) {
+                       int n_trace, double* trace, double lambda_init, double* lambda_out) {
   const int nd = or_n_dof(rb), m = or_n_residuals(rb, ts);
   double* r = (double*)malloc(sizeof(double) * m);
   double* rt = (double*)malloc(sizeof(double) * m);
@@ -491,7 +494,7 @@ static void lm_problem(const or_robot* rb, const or_ik_params* p, const or_targe
     goto done;
   }
   or_ik_errors(rb, ts, targets, q, &pe, &re);
-  double lambda = p->lambda0;
+  double lambda = lambda_init >= 0 ? lambda_init : p->lambda0;
   int conv = converged(p, pe, re);
   if (!(p->early_exit && conv)) {
     while (it < p->max_iters) {
@@ -541,6 +544,7 @@ static void lm_problem(const or_robot* rb, const or_ik_params* p, const or_targe
   or_ik_errors(rb, ts, targets, q, &pe, &re);
   res->cost = f; res->pos_err = pe; res->rot_err = re; res->iters = it;
   res->status = converged(p, pe, re) ? OR_P_CONVERGED : OR_P_MAX_ITERS;
+  if (lambda_out) *lambda_out = lambda;
 done:
   free(r); free(rt); free(J); free(A); free(g); free(ng); free(dq); free(qt);
 }
@@ -571,7 +575,7 @@ static void* pool_worker(void* arg) {
     long b = i / c->n_seeds;
     lm_problem(c->rb, c->p, c->ts, c->targets + b * 12 * k, c->seeds + i * c->nd,
                c->q_all + i * c->nd, &c->res[i], c->n_trace,
-               c->trace ? c->trace + i * (long)c->n_trace * c->nd : NULL);
+               c->trace ? c->trace + i * (long)c->n_trace * c->nd : NULL, -1.0, NULL);
   }
   return NULL;
 }
@@ -631,5 +635,104 @@ int32_t or_ik_solve(const or_robot* rb, const or_ik_params* p, const or_target_s
   }
   free(c.q_all);
   free(c.res);
+  return n_threads;
+}
+
+/* ------------------------------------------------------------------ */
+/* IK-Beam (Sec. V-C): every target starts from n_seeds seeds; all of them
+ * take steps1 LM iterations; the `keep` seeds with the lowest cost (ties: the
+ * lower seed index; a non-finite cost ranks last) continue from their LM state
+ * (configuration and damping) for steps2 more iterations; the result is the
+ * best of those (converged first, then lowest cost, then lowest seed index). */
+
+typedef struct {
+  const or_robot* rb;
+  const or_ik_params* p;
+  const or_target_spec* ts;
+  int32_t batch, n_seeds, steps1, keep, steps2, nd;
+  const double* targets;
+  const double* seeds;
+  double* q_out;
+  double* err_out;
+  int32_t* iters_out;
+  int32_t* status_out;
+  int32_t* kept_out;
+  long next;
+} beam_ctx;
+
+static double rank_cost(double f) { return isfinite(f) ? f : INFINITY; }
+
+static void beam_target(beam_ctx* c, long b) {
+  const int nd = c->nd, S = c->n_seeds, k = c->ts->n_targets;
+  const double* tg = c->targets + b * 12 * k;
+  or_ik_params p1 = *c->p, p2 = *c->p;
+  p1.max_iters = c->steps1;
+  p2.max_iters = c->steps2;
+  double* q1 = (double*)malloc(sizeof(double) * S * nd);
+  double* lam1 = (double*)malloc(sizeof(double) * S);
+  lm_result* r1 = (lm_result*)malloc(sizeof(lm_result) * S);
+  int* taken = (int*)calloc(S, sizeof(int));
+  double* q2 = (double*)malloc(sizeof(double) * nd);
+  /* phase 1: every seed */
+  for (int s = 0; s < S; ++s)
+    lm_problem(c->rb, &p1, c->ts, tg, c->seeds + (b * S + s) * nd, q1 + s * nd, &r1[s], 0, NULL, -1.0, &lam1[s]);
+  /* selection and phase 2 */
+  int best_s = -1, best_conv = 0, best_it = 0, best_status = 0;
+  double best_f = INFINITY, best_pe = NAN, best_re = NAN;
+  double* best_q = (double*)malloc(sizeof(double) * nd);
+  for (int r = 0; r < c->keep && r < S; ++r) {
+    int sel = -1;
+    for (int s = 0; s < S; ++s) {
+      if (taken[s]) continue;
+      if (sel < 0 || rank_cost(r1[s].cost) < rank_cost(r1[sel].cost)) sel = s;
+    }
+    taken[sel] = 1;
+    if (c->kept_out) c->kept_out[b * c->keep + r] = sel;
+    lm_result r2;
+    if (r1[sel].status == OR_P_NONFINITE) {
+      memcpy(q2, q1 + sel * nd, sizeof(double) * nd);
+      r2 = r1[sel];
+      r2.iters = 0;
+    } else {
+      lm_problem(c->rb, &p2, c->ts, tg, q1 + sel * nd, q2, &r2, 0, NULL, lam1[sel], NULL);
+    }
+    const int conv = r2.status == OR_P_CONVERGED;
+    const double f = rank_cost(r2.cost);
+    if (best_s < 0 || conv > best_conv || (conv == best_conv && (f < best_f || (f == best_f && sel < best_s)))) {
+      best_s = sel; best_conv = conv; best_f = f; best_pe = r2.pos_err; best_re = r2.rot_err;
+      best_it = r1[sel].iters + r2.iters; best_status = r2.status;
+      memcpy(best_q, q2, sizeof(double) * nd);
+    }
+  }
+  memcpy(c->q_out + b * nd, best_q, sizeof(double) * nd);
+  c->err_out[2 * b] = best_pe;
+  c->err_out[2 * b + 1] = best_re;
+  c->iters_out[b] = best_it;
+  c->status_out[b] = best_status;
+  free(q1); free(lam1); free(r1); free(taken); free(q2); free(best_q);
+}
+
+static void* beam_worker(void* arg) {
+  beam_ctx* c = (beam_ctx*)arg;
+  for (;;) {
+    long b = __atomic_fetch_add(&c->next, 1, __ATOMIC_RELAXED);
+    if (b >= c->batch) break;
+    beam_target(c, b);
+  }
+  return NULL;
+}
+
+int32_t or_ik_beam(const or_robot* rb, const or_ik_params* p, const or_target_spec* ts, int32_t batch,
+                   int32_t n_seeds, int32_t steps1, int32_t keep, int32_t steps2, const double* targets,
+                   const double* seeds, double* q_out, double* err_out, int32_t* iters_out,
+                   int32_t* status_out, int32_t* kept_out, int32_t n_threads) {
+  if (n_threads <= 0) n_threads = or_host_cores();
+  if (n_threads > batch) n_threads = batch > 0 ? batch : 1;
+  beam_ctx c = {rb, p, ts, batch, n_seeds, steps1, keep, steps2, or_n_dof(rb), targets, seeds,
+                q_out, err_out, iters_out, status_out, kept_out, 0};
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * n_threads);
+  for (int t = 0; t < n_threads; ++t) pthread_create(&th[t], NULL, beam_worker, &c);
+  for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+  free(th);
   return n_threads;
 }

@@ -99,6 +99,21 @@ int32_t or_ik_solve(const or_robot* rb, const or_ik_params* p, const or_target_s
                     double* per_problem, int32_t n_trace, double* trace, double* margin,
                     int32_t n_threads);
 
+/*
+ * IK-Beam (Sec. V-C) over batch targets with n_seeds seeds each: steps1 LM
+ * iterations on every seed, then the `keep` lowest-cost seeds (ties: lower
+ * seed index; non-finite costs last) continue from their configuration and
+ * damping for steps2 iterations; the best of those (converged first, then
+ * lowest cost, then lowest seed index) is returned.  p->max_iters is ignored;
+ * p->early_exit applies to both phases.  iters_out = phase-1 + phase-2
+ * iterations of the returned seed; kept_out (optional, [batch][keep]) the
+ * kept seed indices in selection order.
+ */
+int32_t or_ik_beam(const or_robot* rb, const or_ik_params* p, const or_target_spec* ts, int32_t batch,
+                   int32_t n_seeds, int32_t steps1, int32_t keep, int32_t steps2, const double* targets,
+                   const double* seeds, double* q_out, double* err_out, int32_t* iters_out,
+                   int32_t* status_out, int32_t* kept_out, int32_t n_threads);
+
 /* Host cores available to this process (affinity mask, else online CPUs). */
 int32_t or_host_cores(void);
 
