@@ -221,13 +221,16 @@ class Timed:
         self.s = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         self.e = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
 
-    def run(self, step_fn, stream):
-        """step_fn(k) enqueues timed step k."""
+    def run(self, step_fn, stream, after=None):
+        """step_fn(k) enqueues timed step k; after(k), if given, enqueues
+        untimed work (result counting) behind step k's end event."""
         for k in range(self.steps):
             self.flush.zero_()
             self.s[k].record(stream)
             step_fn(k)
             self.e[k].record(stream)
+            if after is not None:
+                after(k)
         self.torch.cuda.synchronize()
         return float(sum(a.elapsed_time(b) for a, b in zip(self.s, self.e)))
 
@@ -263,21 +266,51 @@ def extra_workloads(torch, pk, synth, args, flush, stream):
     plan = pk.IkPlan(prm, sets)
     tuned_ms = plan.autotune(reps=2)
     steps = max(3, args.steps // 2)
-    for _ in range(args.warmup):
-        plan.run()
-    timed = Timed(torch, steps, flush)
     conv = torch.zeros((), dtype=torch.int64, device="cuda")
 
-    def run(k):
-        outs = plan.run()
-        for o in outs:
+    def count(k):
+        for o in plan.outs:
             conv.add_((o[3] == pk.PK_P_CONVERGED).sum())
-    ms = timed.run(run, stream)
+    for _ in range(args.warmup):  # also loads the counting kernels before timing
+        plan.run()
+        count(0)
+    torch.cuda.synchronize()
+    conv.zero_()
+    timed = Timed(torch, steps, flush)
+    ms = timed.run(lambda k: plan.run(), stream, after=count)
     out["uneven"] = {"workload": synth.UNEVEN["name"], "robots": dict(names), "seeds": synth.UNEVEN["n_seeds"],
                      "value": int(conv.item()) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
                      "success_rate": int(conv.item()) / (steps * sum(b for _, b in names)),
                      "launch": UNEVEN_LAUNCH[plan.schedule()["variant"]] + ", CUDA graph replay",
                      "schedule": plan.schedule(), "autotuned_ms": tuned_ms, "work_per_launch": plan.stats()}
+    # IK-Beam (Sec. V-C): 64 seeds, 6 iterations, keep 4, 10 iterations, at the paper's batch sizes
+    spec = synth.chain_robot(100, 7)
+    g = pk.Robot.from_spec(spec)
+    ee = g.n_joints - 1
+    bp = pk.pk_ik_beam_params_default()
+    prm = pk.pk_ik_params_default(early_exit=0)
+    rows = {}
+    for Bb in (1, 10, 100, 1000, 2000):
+        qt = synth.uniform_q(700, Bb, spec.dof_lower, spec.dof_upper)
+        T = pk.pk_fk(g, dev(qt))[:, ee:ee + 1].contiguous()
+        sdb = dev(synth.uniform_q(701, (Bb, bp.n_seeds), spec.dof_lower, spec.dof_upper))
+        ws = torch.empty(pk.pk_ik_beam_workspace_bytes(g, Bb, bp), dtype=torch.uint8, device="cuda")
+        bouts = (torch.empty(Bb, 7, device="cuda"), torch.empty(Bb, 2, device="cuda"),
+                 torch.empty(Bb, dtype=torch.int32, device="cuda"), torch.empty(Bb, dtype=torch.int32, device="cuda"))
+        for _ in range(3):
+            pk.pk_ik_beam_solve(g, prm, bp, [ee], None, T, sdb, ws, out=bouts)
+        reps = 10
+        bms = Timed(torch, reps, flush).run(lambda k: pk.pk_ik_beam_solve(g, prm, bp, [ee], None, T, sdb, ws,
+                                                                          out=bouts), stream)
+        st = bouts[3].cpu().numpy()
+        err = bouts[1].cpu().numpy()
+        ok = st == pk.PK_P_CONVERGED
+        rows[str(Bb)] = {"ms": bms / reps, "success": float(ok.mean()),
+                         "p98_pos_m": float(np.percentile(err[:, 0], 98)),
+                         "p98_rot_rad": float(np.percentile(err[:, 1], 98))}
+    out["ik_beam"] = {"workload": "ik_beam7 (64 seeds, 6 steps, keep 4, 10 steps; synthetic 7-DoF chain)",
+                      "unit": "ms per batch", "batches": rows,
+                      "launch": "2 memsets + 4 kernels per solve (LM, select, LM, final)"}
     # trajectory optimisation: 1024 trajectories x T = 64, 32 obstacles + plane, 50 LM iterations
     cfg = synth.TRAJOPT
     spec, qs_c, qg_c, radii, obs, plane = synth.trajopt_workload(cfg)

@@ -197,6 +197,51 @@ pk_status pk_ik_solve_noalloc(const pk_robot* robot, const pk_ik_params* params,
                               int32_t* d_iters_out, int32_t* d_status_out, void* stream);
 
 /*
+ * IK-Beam (Sec. V-C) -- the paper's benchmark IK schedule: every target starts
+ * from n_seeds seeds, all of which take steps1 LM iterations; the `keep` seeds
+ * with the lowest cost (ties: lower seed index; a non-finite cost ranks last)
+ * continue from their LM state -- configuration and damping -- for steps2
+ * more iterations, and the best of those is returned (converged first, then
+ * lowest cost, then lowest seed index).  The paper's schedule is 64 seeds,
+ * 6 iterations, keep 4, 10 iterations (pk_ik_beam_params_default).
+ */
+typedef struct {
+  int32_t n_seeds;  /* seeds per target, keep..1024 */
+  int32_t steps1;   /* LM iterations on every seed, >= 0 */
+  int32_t keep;     /* seeds that continue, 1..32 */
+  int32_t steps2;   /* LM iterations on the kept seeds, >= 0 */
+} pk_ik_beam_params;
+
+void pk_ik_beam_params_default(pk_ik_beam_params* beam);
+/* Scratch bytes of pk_ik_beam_solve for `batch` targets (0 on bad arguments). */
+size_t pk_ik_beam_workspace_bytes(const pk_robot* robot, int32_t batch, const pk_ik_beam_params* beam);
+/*
+ *   params     LM weights, damping rules and tolerances as pk_ik_solve;
+ *              max_iters and cancel_siblings are ignored (the beam fixes the
+ *              iteration counts and runs every seed of the first round);
+ *              early_exit applies to both rounds.
+ *   k, target_links, target_kinds  one target on a frame after the last
+ *              movable joint of a serial chain with 1..8 movable joints
+ *              (PK_ERR_UNSUPPORTED otherwise)
+ *   d_targets  [batch][1][12], 16-byte aligned
+ *   d_seeds    [batch][n_seeds][n_dof]
+ *   d_q_out [batch][n_dof], d_err_out [batch][2], d_status_out [batch]: as
+ *              pk_ik_solve; d_iters_out [batch]: first-round + second-round
+ *              iterations of the returned seed
+ *   d_kept_out [batch][keep] or NULL: the kept seed indices, lowest cost first
+ *   d_workspace, workspace_bytes  caller scratch of at least
+ *              pk_ik_beam_workspace_bytes() bytes, 256-byte aligned, or NULL
+ *              (stream-ordered allocation); pk_ik_workspace_stats() on it
+ *              reports the work of both rounds.
+ * Enqueues two memsets and four kernels on `stream`; batch == 0 is a no-op.
+ */
+pk_status pk_ik_beam_solve(const pk_robot* robot, const pk_ik_params* params, const pk_ik_beam_params* beam,
+                           int32_t k, const int32_t* target_links, const int32_t* target_kinds, int32_t batch,
+                           const float* d_targets, const float* d_seeds, float* d_q_out, float* d_err_out,
+                           int32_t* d_iters_out, int32_t* d_status_out, int32_t* d_kept_out, void* d_workspace,
+                           size_t workspace_bytes, void* stream);
+
+/*
  * Uneven batches (plans).  Several problem sets -- each its own robot, target
  * set, batch size and seeds -- are solved together.  Schedule variants 0 and 1
  * run ONE persistent kernel launch: every warp drains the sets in turn, serial

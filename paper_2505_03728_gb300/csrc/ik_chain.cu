@@ -236,8 +236,8 @@ __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams
   const bool cancel = lp.cancel != 0;
   int tgt = 0, pid = 0;  // target and record index of the lane's problem
   int qcur = 0, qpos = 0;
-  chain_chunk_claim<N>(qq, 0, head, P, batch, n_seeds, cancel, targets, seeds, flags, lane);
-  chain_chunk_claim<N>(qq, 1, head, P, batch, n_seeds, cancel, targets, seeds, flags, lane);
+  chain_chunk_claim<N>(qq, 0, head, P, batch, n_seeds, cancel, targets, seeds, flags, lp, lane);
+  chain_chunk_claim<N>(qq, 1, head, P, batch, n_seeds, cancel, targets, seeds, flags, lp, lane);
   cp_async_wait_one_pending();
   __syncwarp();
   for (;;) {
@@ -251,7 +251,7 @@ __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams
         __syncwarp();
         qcur ^= 1;
         qpos = 0;
-        chain_chunk_claim<N>(qq, qcur ^ 1, head, P, batch, n_seeds, cancel, targets, seeds, flags, lane);
+        chain_chunk_claim<N>(qq, qcur ^ 1, head, P, batch, n_seeds, cancel, targets, seeds, flags, lp, lane);
       }
       const int rank = __popc(nm & ((1u << lane) - 1u));
       const int avail = kQ - qpos;
@@ -286,7 +286,7 @@ __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams
             for (int j = 0; j < N; ++j) qc[j] = qq.seed[qcur][e][j];
             fresh = true;
             it = 0;
-            lam = lp.lambda0;
+            lam = qq.lam[qcur][e];
             need = false;
           }
         }
@@ -358,6 +358,7 @@ __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams
       r[NP + 1] = pe_a;
       r[NP + 2] = re_a;
       r[NP + 3] = __int_as_float((status << 24) | it);
+      if (lp.lam_out) lp.lam_out[pid] = lam;
       if (lp.cancel && status == PK_P_CONVERGED) __stcg(flags + tgt, 1);
       ++wc.done;
       need = true;
@@ -538,7 +539,7 @@ static cudaError_t chain_lm_launch(const ChainHost& ch, const LmParams& lp, cons
                                                                   (int)P, ws);
   }
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || !d_q) return e;
   return launch_ik_reduce(ws.rec, N, batch, n_seeds, d_q, d_err, d_iters, d_status, stream);
 }
 

@@ -436,6 +436,7 @@ struct ChainQueue {
   alignas(16) float tgt[2][kQ][12];
   float seed[2][kQ][N];
   int32_t flag[2][kQ];
+  float lam[2][kQ];    // initial damping
   int32_t pid[2][kQ];  // record index, or -1 past the end
   int32_t tid[2][kQ];  // target index
 };
@@ -458,7 +459,8 @@ __device__ __forceinline__ void cp_async_wait_one_pending() { asm volatile("cp.a
 template <int N>
 __device__ __forceinline__ void chain_chunk_claim(ChainQueue<N>& q, int buf, int32_t* head, int P, int batch,
                                                   int n_seeds, bool cancel, const float* __restrict__ targets,
-                                                  const float* __restrict__ seeds, const int32_t* flags, int lane) {
+                                                  const float* __restrict__ seeds, const int32_t* flags,
+                                                  const LmParams& lp, int lane) {
   int base = 0;
   if (lane == 0) base = atomicAdd(head, kQ);
   base = __shfl_sync(kTreeFull, base, 0);
@@ -485,6 +487,10 @@ __device__ __forceinline__ void chain_chunk_claim(ChainQueue<N>& q, int buf, int
       cp_async4(&q.flag[buf][lane], flags + tgt);
     else
       q.flag[buf][lane] = 0;
+    if (lp.lam_in)
+      cp_async4(&q.lam[buf][lane], lp.lam_in + pid);
+    else
+      q.lam[buf][lane] = lp.lambda0;
   } else {
     q.pid[buf][lane] = -1;
   }

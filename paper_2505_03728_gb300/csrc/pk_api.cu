@@ -576,4 +576,72 @@ pk_status pk_ik_solve(const pk_robot* rb, const pk_ik_params* params, int32_t k,
   return e == cudaSuccess ? PK_OK : cuda_fail(e, "pk_ik_solve launch");
 }
 
+void pk_ik_beam_params_default(pk_ik_beam_params* b) {
+  if (!b) return;
+  b->n_seeds = 64;
+  b->steps1 = 6;
+  b->keep = 4;
+  b->steps2 = 10;
+}
+
+static bool beam_ok(const pk_ik_beam_params* b) {
+  return b && b->keep >= 1 && b->keep <= 32 && b->n_seeds >= b->keep && b->n_seeds <= 1024 && b->steps1 >= 0 &&
+         b->steps2 >= 0;
+}
+
+size_t pk_ik_beam_workspace_bytes(const pk_robot* rb, int32_t batch, const pk_ik_beam_params* beam) {
+  if (!rb || batch < 0 || !beam_ok(beam)) return 0;
+  pk::BeamWorkspace w;
+  pk::beam_layout(rb->n_dof, batch, beam->n_seeds, beam->keep, &w, nullptr);
+  return w.total;
+}
+
+pk_status pk_ik_beam_solve(const pk_robot* rb, const pk_ik_params* params, const pk_ik_beam_params* beam,
+                           int32_t k, const int32_t* target_links, const int32_t* target_kinds, int32_t batch,
+                           const float* d_targets, const float* d_seeds, float* d_q_out, float* d_err_out,
+                           int32_t* d_iters_out, int32_t* d_status_out, int32_t* d_kept_out, void* d_workspace,
+                           size_t workspace_bytes, void* stream) {
+  if (!rb) return fail(PK_ERR_INVALID_ARG, "robot is NULL");
+  pk_status s = check_params(params);
+  if (s != PK_OK) return s;
+  if (!beam_ok(beam))
+    return fail(PK_ERR_INVALID_ARG, "beam: need 1 <= keep <= 32, keep <= n_seeds <= 1024, steps >= 0");
+  bool pos_only = false;
+  if ((s = check_targets(rb, k, target_links, target_kinds, &pos_only)) != PK_OK) return s;
+  if (!chain_eligible(rb, k, target_links))
+    return fail(PK_ERR_UNSUPPORTED, "IK-Beam runs on serial chains with one target");
+  pk::ChainHost ch;
+  if ((s = fold_chain(rb, target_links[0], &ch)) != PK_OK) return s;
+  if (batch < 0) return fail(PK_ERR_INVALID_ARG, "batch must be >= 0");
+  if ((long long)batch * beam->n_seeds > 0x7fffff00LL)
+    return fail(PK_ERR_INVALID_ARG, "batch * n_seeds exceeds 2^31");
+  if (batch == 0) return PK_OK;
+  if (!d_targets || !d_seeds || !d_q_out || !d_err_out || !d_iters_out || !d_status_out)
+    return fail(PK_ERR_INVALID_ARG, "NULL device buffer");
+  if (((uintptr_t)d_targets & 15) != 0) return fail(PK_ERR_INVALID_ARG, "d_targets must be 16-byte aligned");
+  pk::BeamWorkspace w;
+  pk::beam_layout(rb->n_dof, batch, beam->n_seeds, beam->keep, &w, nullptr);
+  cudaStream_t st = (cudaStream_t)stream;
+  void* ws_base = d_workspace;
+  bool owned = false;
+  if (ws_base) {
+    if (workspace_bytes < w.total)
+      return fail(PK_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", workspace_bytes, w.total);
+    if (((uintptr_t)ws_base & 255) != 0) return fail(PK_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  } else {
+    cudaError_t e = cudaMallocAsync(&ws_base, w.total, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(workspace)");
+    owned = true;
+  }
+  w.base = (char*)ws_base;
+  cudaError_t e = pk::launch_beam(ch, lm_params(params, pos_only), beam->steps1, beam->steps2, d_targets, d_seeds,
+                                  batch, beam->n_seeds, beam->keep, w, d_kept_out, d_q_out, d_err_out, d_iters_out,
+                                  d_status_out, st);
+  if (owned) {
+    cudaError_t e2 = cudaFreeAsync(ws_base, st);
+    if (e == cudaSuccess) e = e2;
+  }
+  return e == cudaSuccess ? PK_OK : cuda_fail(e, "pk_ik_beam_solve launch");
+}
+
 }  // extern "C"

@@ -53,6 +53,11 @@ struct LmParams {
   float lambda0, lambda_min, lambda_max, nu;
   float tol_pos, tol_rot;
   int32_t max_iters, early_exit, cancel, pos_only;
+  // Chain path only: per-problem initial damping (NULL: lambda0) and the
+  // damping after the last iteration (NULL: not written), indexed like the
+  // records; used to continue an LM run in a later launch (IK-Beam).
+  const float* lam_in = nullptr;
+  float* lam_out = nullptr;
 };
 
 // Scratch layout of the IK solve.
@@ -69,6 +74,7 @@ void ik_workspace_carve(void* base, int n_dof, long batch, long n_seeds, IkWorks
 int ik_rec_stride(int n_dof);
 
 // Launchers (ik_chain.cu).  Return a cudaError_t from the launch.
+// d_q == NULL: records only, no best-seed reduction.
 cudaError_t launch_chain_lm(const ChainHost& ch, const LmParams& lp, const float* d_targets,
                             const float* d_seeds, int batch, int n_seeds, IkWorkspace ws,
                             float* d_q, float* d_err, int32_t* d_iters, int32_t* d_status,
@@ -85,6 +91,17 @@ cudaError_t launch_chain_residual(const ChainHost& ch, const LmParams& lp, const
                                   cudaStream_t stream);
 cudaError_t launch_fk(const RobotDev* d_robot, int n_joints, int n_dof, int batch, const float* d_q,
                       float* d_T, cudaStream_t stream);
+
+// IK-Beam (ik_beam.cu): byte offsets of the two rounds' scratch in one buffer.
+struct BeamWorkspace {
+  size_t bytes1, ws1_off, lam1_off, ws2_off, seeds2_off, lam2_off, it1_off, kept_off, total;
+  char* base;
+};
+void beam_layout(int n_dof, long batch, int S1, int keep, BeamWorkspace* w, char* base);
+cudaError_t launch_beam(const ChainHost& ch, const LmParams& lp, int steps1, int steps2, const float* d_targets,
+                        const float* d_seeds, int batch, int S1, int keep, const BeamWorkspace& w,
+                        int32_t* d_kept_out, float* d_q, float* d_err, int32_t* d_iters, int32_t* d_status,
+                        cudaStream_t st);
 
 // Uneven multi-robot batches in one persistent launch (ik_chain.cu, ik_plan.cu).
 constexpr int kMaxSegs = 8;

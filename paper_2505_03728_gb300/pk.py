@@ -46,6 +46,10 @@ class pk_ik_params(C.Structure):
                 ("cancel_siblings", C.c_int32), ("reserved", C.c_int32)]
 
 
+class pk_ik_beam_params(C.Structure):
+    _fields_ = [("n_seeds", C.c_int32), ("steps1", C.c_int32), ("keep", C.c_int32), ("steps2", C.c_int32)]
+
+
 class pk_ik_problem_set(C.Structure):
     _fields_ = [("robot", C.c_void_p), ("k", C.c_int32), ("target_links", C.POINTER(C.c_int32)),
                 ("target_kinds", C.POINTER(C.c_int32)), ("batch", C.c_int32), ("n_seeds", C.c_int32),
@@ -84,6 +88,10 @@ _SIGNATURES = {
     "pk_ik_residual": (_i32, [_vp, C.POINTER(pk_ik_params), _i32, _i32p, _i32p, _i32, _vp, _vp, _vp,
                               _vp, _vp]),
     "pk_ik_workspace_bytes": (C.c_size_t, [_vp, _i32, _i32]),
+    "pk_ik_beam_params_default": (None, [C.POINTER(pk_ik_beam_params)]),
+    "pk_ik_beam_workspace_bytes": (C.c_size_t, [_vp, _i32, C.POINTER(pk_ik_beam_params)]),
+    "pk_ik_beam_solve": (_i32, [_vp, C.POINTER(pk_ik_params), C.POINTER(pk_ik_beam_params), _i32, _i32p, _i32p,
+                                _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "pk_ik_solve": (_i32, [_vp, C.POINTER(pk_ik_params), _i32, _i32p, _i32p, _i32, _i32, _vp, _vp,
                            _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "pk_ik_solve_noalloc": (_i32, [_vp, C.POINTER(pk_ik_params), _i32, _i32p, _i32p, _i32, _i32, _vp,
@@ -273,6 +281,49 @@ def pk_ik_solve(robot: Robot, params: pk_ik_params, links, kinds, targets: torch
                              _dev(q, name="q"), _dev(err, name="err"),
                              _dev(iters, torch.int32, "iters"), _dev(status, torch.int32, "status"),
                              ws_p, ws_n, _stream(stream)))
+    return q, err, iters, status
+
+
+def pk_ik_beam_params_default(**overrides) -> pk_ik_beam_params:
+    b = pk_ik_beam_params()
+    lib().pk_ik_beam_params_default(C.byref(b))
+    for k, v in overrides.items():
+        setattr(b, k, v)
+    return b
+
+
+def pk_ik_beam_workspace_bytes(robot: Robot, batch: int, beam: pk_ik_beam_params) -> int:
+    return int(lib().pk_ik_beam_workspace_bytes(robot.handle, batch, C.byref(beam)))
+
+
+def pk_ik_beam_solve(robot: Robot, params: pk_ik_params, beam: pk_ik_beam_params, links, kinds,
+                     targets: torch.Tensor, seeds: torch.Tensor, workspace: torch.Tensor | None = None,
+                     out=None, kept: torch.Tensor | None = None, stream=None):
+    """IK-Beam.  targets [B][1][12], seeds [B][beam.n_seeds][n_dof].
+
+    Returns (q [B][n_dof], err [B][2], iters [B], status [B]) as CUDA tensors;
+    ``kept`` ([B][beam.keep] int32), when given, receives the kept seed indices.
+    """
+    links, kinds_a, kinds_p = _links(links, kinds)
+    B = seeds.shape[0]
+    if seeds.shape != (B, beam.n_seeds, robot.n_dof):
+        raise ValueError("seeds must be [batch][beam.n_seeds][n_dof]")
+    if targets.shape != (B, len(links), 12):
+        raise ValueError("targets must be [batch][k][12]")
+    dev = seeds.device
+    if out is None:
+        out = (torch.empty(B, robot.n_dof, device=dev), torch.empty(B, 2, device=dev),
+               torch.empty(B, device=dev, dtype=torch.int32), torch.empty(B, device=dev, dtype=torch.int32))
+    q, err, iters, status = out
+    ws_p, ws_n = None, 0
+    if workspace is not None:
+        ws_p, ws_n = _dev(workspace, torch.uint8, "workspace"), workspace.numel()
+    kept_p = None if kept is None else _dev(kept, torch.int32, "kept")
+    _check(lib().pk_ik_beam_solve(robot.handle, C.byref(params), C.byref(beam), len(links),
+                                  links.ctypes.data_as(_i32p), kinds_p, B, _dev(targets, name="targets"),
+                                  _dev(seeds, name="seeds"), _dev(q, name="q"), _dev(err, name="err"),
+                                  _dev(iters, torch.int32, "iters"), _dev(status, torch.int32, "status"),
+                                  kept_p, ws_p, ws_n, _stream(stream)))
     return q, err, iters, status
 
 
