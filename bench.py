@@ -192,7 +192,8 @@ def run_reference(args, cfg):
 
 def config_dict(cfg, args, head="plain"):
     seeding = ("learned: seed network (9 -> 4 x 512 SiLU -> 8 x 7, BF16 tcgen05, trained on the GPU "
-               "before timing) inferred inside every step" if head == "learned" else "uniform random")
+               "before timing, LM-refined labels every 2 epochs) inferred inside every step"
+               if head == "learned" else "uniform random")
     return {"workload": cfg["name"], "robot": "synthetic 7-DoF revolute chain (seed 100)",
             "targets": args.batch, "seeds_per_target": cfg["n_seeds"], "max_iters": cfg["max_iters"],
             "early_exit": True, "cancel_siblings": not args.no_cancel, "seeding": seeding,
@@ -283,6 +284,33 @@ def extra_workloads(torch, pk, synth, args, flush, stream):
                      "success_rate": int(conv.item()) / (steps * sum(b for _, b in names)),
                      "launch": UNEVEN_LAUNCH[plan.schedule()["variant"]] + ", CUDA graph replay",
                      "schedule": plan.schedule(), "autotuned_ms": tuned_ms, "work_per_launch": plan.stats()}
+    # learned vs random seeds on the 30-joint humanoid (six pose targets), 65,536 held-out targets x 8
+    spec, ends = synth.humanoid_robot(103)
+    links = list(ends)
+    g = pk.Robot.from_spec(spec)
+    net = pk.SeedNet(g, links, K=8, width=512, depth=4, seed=11)
+    t0 = time.perf_counter()
+    pk.pk_seednet_train(net, pk.pk_train_params_default(epochs=8, steps_per_epoch=1220, batch=8192, seed=520,
+                                                         refine_every=2))
+    h_train = time.perf_counter() - t0
+    Bh = 65536
+    T = pk.pk_fk(g, dev(synth.uniform_q(521, Bh, spec.dof_lower, spec.dof_upper)))[:, links].contiguous()
+    rs = dev(synth.uniform_q(522, (Bh, 8), spec.dof_lower, spec.dof_upper))
+    ls = torch.empty(Bh, 8, g.n_dof, device="cuda")
+    hp = pk.pk_ik_params_default(max_iters=50, early_exit=1, cancel_siblings=1)
+    hws = torch.empty(pk.pk_ik_workspace_bytes(g, Bh, 8), dtype=torch.uint8, device="cuda")
+    hout = (torch.empty(Bh, g.n_dof, device="cuda"), torch.empty(Bh, 2, device="cuda"),
+            torch.empty(Bh, dtype=torch.int32, device="cuda"), torch.empty(Bh, dtype=torch.int32, device="cuda"))
+    hst = torch.empty(3, Bh, dtype=torch.int32, device="cuda")
+    hum = {"workload": "humanoid30_65536x8 (6 pose targets)", "unit": UNIT, "train_s": h_train}
+    for name, fn in (("learned", lambda st: (pk.pk_seednet_infer(net, T, ls),
+                                             pk.pk_ik_solve(g, hp, links, None, T, ls, hws, out=hout[:3] + (st,)))),
+                     ("random", lambda st: pk.pk_ik_solve(g, hp, links, None, T, rs, hws, out=hout[:3] + (st,)))):
+        fn(hout[3])
+        hms = Timed(torch, 3, flush).run(lambda k: fn(hst[k]), stream)
+        nconv = int((hst == pk.PK_P_CONVERGED).sum().item())
+        hum[name] = {"value": nconv / (hms / 1e3), "ms_per_step": hms / 3, "success_rate": nconv / (3 * Bh)}
+    out["learned_humanoid"] = hum
     # IK-Beam (Sec. V-C): 64 seeds, 6 iterations, keep 4, 10 iterations, at the paper's batch sizes
     spec = synth.chain_robot(100, 7)
     g = pk.Robot.from_spec(spec)
@@ -299,9 +327,15 @@ def extra_workloads(torch, pk, synth, args, flush, stream):
                  torch.empty(Bb, dtype=torch.int32, device="cuda"), torch.empty(Bb, dtype=torch.int32, device="cuda"))
         for _ in range(3):
             pk.pk_ik_beam_solve(g, prm, bp, [ee], None, T, sdb, ws, out=bouts)
+        # the call allocates nothing with a caller workspace, so it is captured
+        # into a CUDA graph and replayed (one launch per solve)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            pk.pk_ik_beam_solve(g, prm, bp, [ee], None, T, sdb, ws, out=bouts)
+        for _ in range(3):
+            graph.replay()
         reps = 10
-        bms = Timed(torch, reps, flush).run(lambda k: pk.pk_ik_beam_solve(g, prm, bp, [ee], None, T, sdb, ws,
-                                                                          out=bouts), stream)
+        bms = Timed(torch, reps, flush).run(lambda k: graph.replay(), stream)
         st = bouts[3].cpu().numpy()
         err = bouts[1].cpu().numpy()
         ok = st == pk.PK_P_CONVERGED
@@ -310,7 +344,7 @@ def extra_workloads(torch, pk, synth, args, flush, stream):
                          "p98_rot_rad": float(np.percentile(err[:, 1], 98))}
     out["ik_beam"] = {"workload": "ik_beam7 (64 seeds, 6 steps, keep 4, 10 steps; synthetic 7-DoF chain)",
                       "unit": "ms per batch", "batches": rows,
-                      "launch": "2 memsets + 4 kernels per solve (LM, select, LM, final)"}
+                      "launch": "one CUDA graph replay per solve (2 memsets + 4 kernels: LM, select, LM, final)"}
     # trajectory optimisation: 1024 trajectories x T = 64, 32 obstacles + plane, 50 LM iterations
     cfg = synth.TRAJOPT
     spec, qs_c, qg_c, radii, obs, plane = synth.trajopt_workload(cfg)
@@ -460,7 +494,8 @@ def main():
     train_s = 0.0
     if not args.no_learned:
         net = pk.SeedNet(robot, [ee], K=S, width=512, depth=4, seed=11)
-        tp = pk.pk_train_params_default(epochs=args.train_epochs, steps_per_epoch=1220, batch=8192, seed=500)
+        tp = pk.pk_train_params_default(epochs=args.train_epochs, steps_per_epoch=1220, batch=8192, seed=500,
+                                        refine_every=2)
         t0 = time.perf_counter()
         train_loss = pk.pk_seednet_train(net, tp)
         train_s = time.perf_counter() - t0

@@ -405,8 +405,14 @@ typedef struct {
   float weight_decay;      /* AdamW decoupled decay (default 1e-4) */
   float beta1, beta2, eps; /* AdamW moments (0.9, 0.999, 1e-8) */
   float mu;                /* weight of the mean term of the loss (default 0.01) */
-  int32_t reserved;        /* must be 0 */
+  int32_t refine_every;    /* LM-refined labels: a pk_seednet_refine round after every
+                              refine_every epochs but the last (0: off, default) */
   uint64_t seed;           /* training-data generator key (default 500) */
+  int32_t refine_n;        /* targets per refinement round (default 65536) */
+  int32_t refine_iters;    /* LM iterations of a round (default 20) */
+  float pool_frac;         /* share of every batch drawn from the label pool once it
+                              holds a round (0..1, default 0.5) */
+  int32_t reserved;        /* must be 0 */
 } pk_train_params;
 
 void pk_train_params_default(pk_train_params* p);
@@ -445,6 +451,24 @@ pk_status pk_seednet_train_step(pk_seednet* net, const pk_train_params* params, 
  * mean loss of every epoch.  Synchronous.  PK_ERR_TIMEOUT if a tensor-core
  * pipeline wait expired (the kernels bound every wait). */
 pk_status pk_seednet_train(pk_seednet* net, const pk_train_params* params, float* host_loss, void* stream);
+
+/*
+ * One LM refinement round of the label pool: n fresh targets (forward
+ * kinematics of uniform in-limit configurations, a generator keyed by `seed`
+ * and the round), K proposals each from the network, pk_ik_solve from them
+ * (max_iters, early exit, sibling cancellation), and the pool becomes those n
+ * targets with the LM solution as label where it converged, the drawn
+ * configuration elsewhere.  Training then draws pool_frac of every batch from
+ * the pool.  The robot handle given to pk_seednet_create must still exist.
+ * Synchronous; *n_converged (optional) receives the converged count.
+ */
+pk_status pk_seednet_refine(pk_seednet* net, int32_t n, int32_t max_iters, uint64_t seed, int32_t* n_converged,
+                            void* stream);
+/* Copy the pool: d_targets_out [n][k][12], d_labels_out [n][n_dof], with n (host)
+ * = its size (0 before the first round; nothing is copied then).  Both buffers
+ * NULL: only the size is returned. */
+pk_status pk_seednet_pool(const pk_seednet* net, float* d_targets_out, float* d_labels_out, int32_t* n_out,
+                          void* stream);
 
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char* pk_last_error(void);

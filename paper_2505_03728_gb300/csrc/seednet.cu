@@ -57,6 +57,13 @@ struct pk_seednet {
   __nv_bfloat16 *dZ[2] = {nullptr, nullptr}, *dZt[2] = {nullptr, nullptr};
   float* Y = nullptr;
   float* qstar = nullptr;
+  // LM-refined label pool: (target poses [pool_n][k][12], labels [pool_n][n])
+  const pk_robot* robot = nullptr;
+  float* pool_T = nullptr;
+  float* pool_q = nullptr;
+  int pool_n = 0, pool_cap = 0;
+  int64_t refine_round = 0;
+  int* d_count = nullptr;
 };
 
 namespace {
@@ -253,6 +260,61 @@ __global__ void datagen_kernel(const pk::RobotDev* __restrict__ rb, const int* _
     for (int i = 0; i < 9 * k; ++i) f[i] = 0.f;
   }
   store_features(f, 9 * k, in_pad, b, m_pad, X, Xt);
+}
+
+// Fresh refinement targets: q uniform in the limits (generator keyed by the
+// training seed and the refinement round, disjoint from the training draws)
+// and the poses of the target frames, [M][k][12].
+__global__ void refine_targets_kernel(const pk::RobotDev* __restrict__ rb, const int* __restrict__ links, int k,
+                                      const float* __restrict__ lohi, int n, uint64_t key, int M, float* T_out,
+                                      float* q_out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= M) return;
+  float q[pk::kMaxJoints];
+  for (int j = 0; j < n; ++j) {
+    const float lo = lohi[j], hi = lohi[n + j];
+    q[j] = lo + (hi - lo) * uniform01(key, (uint64_t)b * n + j);
+    q_out[(size_t)b * n + j] = q[j];
+  }
+  pk::Rt frames[pk::kMaxJoints];
+  for (int t = 0; t < k; ++t) {
+    pk::Rt T;
+    tree_fk_link(rb, q, links[t], T, frames);
+    float* o = T_out + ((size_t)b * k + t) * 12;
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 3; ++c) o[r * 4 + c] = T.r[r * 3 + c];
+      o[r * 4 + 3] = T.t[r];
+    }
+  }
+}
+
+// Pool labels: the LM solution where the refinement converged (it becomes the
+// label), else the drawn configuration (already in pool_q).
+__global__ void refine_label_kernel(int M, int n, const int32_t* __restrict__ status, const float* __restrict__ q_lm,
+                                    float* pool_q, int* count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= M || status[b] != PK_P_CONVERGED) return;
+  for (int j = 0; j < n; ++j) pool_q[(size_t)b * n + j] = q_lm[(size_t)b * n + j];
+  atomicAdd(count, 1);
+}
+
+// Rows [0, r0) of a training batch drawn from the label pool (row b takes pool
+// entry hash(key, step, b) mod pool_n); datagen_kernel fills the others.
+__global__ void pool_rows_kernel(const float* __restrict__ pool_T, const float* __restrict__ pool_q, int pool_n,
+                                 int k, int n, uint64_t key, int64_t step, int r0, int in_pad, int m_pad,
+                                 __nv_bfloat16* X, __nv_bfloat16* Xt, float* qstar) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= r0) return;
+  const uint64_t h = splitmix64(key + ((uint64_t)step * (uint64_t)r0 + (uint64_t)b) * 0x9e3779b97f4a7c15ull);
+  const int idx = (int)(h % (uint64_t)pool_n);
+  float f[9 * 16];
+  for (int t = 0; t < k; ++t) {
+    pk::Rt T;
+    pk::rt_load(pool_T + ((size_t)idx * k + t) * 12, T);
+    pose_features(T, f + 9 * t);
+  }
+  store_features(f, 9 * k, in_pad, b, m_pad, X, Xt);
+  for (int j = 0; j < n; ++j) qstar[(size_t)b * n + j] = pool_q[(size_t)idx * n + j];
 }
 
 // Head, min-over-K loss and dL/dy (scaled by 1/M) for M valid rows.
@@ -538,8 +600,12 @@ void pk_train_params_default(pk_train_params* p) {
   p->beta2 = 0.999f;
   p->eps = 1e-8f;
   p->mu = 0.01f;
-  p->reserved = 0;
+  p->refine_every = 0;
   p->seed = 500;
+  p->refine_n = 65536;
+  p->refine_iters = 20;
+  p->pool_frac = 0.5f;
+  p->reserved = 0;
 }
 
 pk_status pk_seednet_create(const pk_robot* rb, int32_t k, const int32_t* target_links, int32_t K,
@@ -560,6 +626,7 @@ pk_status pk_seednet_create(const pk_robot* rb, int32_t k, const int32_t* target
   pk_seednet* s = new (std::nothrow) pk_seednet;
   if (!s) return sn_fail(PK_ERR_OOM, "host allocation failed");
   s->d_robot = (const pk::RobotDev*)rb->d_blob;
+  s->robot = rb;
   s->n_dof = rb->n_dof;
   s->n_joints = rb->n_joints;
   s->k = k;
@@ -619,6 +686,7 @@ pk_status pk_seednet_create(const pk_robot* rb, int32_t k, const int32_t* target
   al((void**)&s->d_links, 16 * 4);
   al((void**)&s->d_err, 4);
   al((void**)&s->d_loss, 4);
+  al((void**)&s->d_count, 4);
   s->A.assign(depth, nullptr);
   s->At.assign(depth, nullptr);
   s->Z.assign(depth, nullptr);
@@ -645,6 +713,7 @@ void pk_seednet_destroy(pk_seednet* s) {
   free_acts(s);
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(s->master); f(s->grad); f(s->adam_m); f(s->adam_v); f(s->d_lohi); f(s->d_links); f(s->d_err); f(s->d_loss);
+  f(s->d_count); f(s->pool_T); f(s->pool_q);
   for (auto* p : s->W) f(p);
   for (auto* p : s->Wt) f(p);
   delete s;
@@ -761,10 +830,86 @@ pk_status pk_seednet_loss_grad(pk_seednet* s, int32_t batch, const float* d_targ
   return PK_OK;
 }
 
+pk_status pk_seednet_refine(pk_seednet* s, int32_t n, int32_t max_iters, uint64_t seed, int32_t* n_converged,
+                            void* stream) {
+  if (!s) return sn_fail(PK_ERR_INVALID_ARG, "net is NULL");
+  if (n < 1 || max_iters < 0) return sn_fail(PK_ERR_INVALID_ARG, "need n >= 1 and max_iters >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (n > s->pool_cap) {
+    if (s->pool_T) cudaFree(s->pool_T);
+    if (s->pool_q) cudaFree(s->pool_q);
+    s->pool_T = s->pool_q = nullptr;
+    s->pool_cap = s->pool_n = 0;
+    e = cudaMalloc(&s->pool_T, (size_t)n * s->k * 12 * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->pool_q, (size_t)n * s->n_dof * 4);
+    if (e != cudaSuccess) return sn_cuda(e, "pk_seednet_refine (pool)");
+    s->pool_cap = n;
+  }
+  s->pool_n = 0;  // invalid until this round completes
+  const int nd = s->n_dof, K = s->K;
+  float *seeds = nullptr, *q_lm = nullptr, *err = nullptr;
+  int32_t *iters = nullptr, *status = nullptr;
+  e = cudaMallocAsync(&seeds, (size_t)n * K * nd * 4, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&q_lm, (size_t)n * nd * 4, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&err, (size_t)n * 8, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&iters, (size_t)n * 4, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&status, (size_t)n * 4, st);
+  const uint64_t key = seed ^ (0x7265666eull + 0x9e3779b97f4a7c15ull * (uint64_t)(++s->refine_round));
+  if (e == cudaSuccess) {
+    refine_targets_kernel<<<(n + 127) / 128, 128, 0, st>>>(s->d_robot, s->d_links, s->k, s->d_lohi, nd, key, n,
+                                                           s->pool_T, s->pool_q);
+    e = cudaGetLastError();
+  }
+  pk_status ps = PK_OK;
+  if (e == cudaSuccess) ps = pk_seednet_infer(s, n, s->pool_T, seeds, stream);
+  if (e == cudaSuccess && ps == PK_OK) {
+    pk_ik_params p;
+    pk_ik_params_default(&p);
+    p.max_iters = max_iters;
+    p.early_exit = 1;
+    p.cancel_siblings = 1;
+    ps = pk_ik_solve(s->robot, &p, s->k, s->links, nullptr, n, K, s->pool_T, seeds, q_lm, err, iters, status,
+                     nullptr, 0, stream);
+  }
+  if (e == cudaSuccess && ps == PK_OK) e = cudaMemsetAsync(s->d_count, 0, 4, st);
+  if (e == cudaSuccess && ps == PK_OK) {
+    refine_label_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, nd, status, q_lm, s->pool_q, s->d_count);
+    e = cudaGetLastError();
+  }
+  int count = 0;
+  if (e == cudaSuccess && ps == PK_OK) e = cudaMemcpyAsync(&count, s->d_count, 4, cudaMemcpyDeviceToHost, st);
+  for (void* p : {(void*)seeds, (void*)q_lm, (void*)err, (void*)iters, (void*)status})
+    if (p) cudaFreeAsync(p, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (ps != PK_OK) return ps;
+  if (e != cudaSuccess) return sn_cuda(e, "pk_seednet_refine");
+  s->pool_n = n;
+  if (n_converged) *n_converged = count;
+  return PK_OK;
+}
+
+pk_status pk_seednet_pool(const pk_seednet* s, float* d_targets_out, float* d_labels_out, int32_t* n_out,
+                          void* stream) {
+  if (!s || !n_out) return sn_fail(PK_ERR_INVALID_ARG, "NULL argument");
+  *n_out = s->pool_n;
+  if (s->pool_n == 0 || (!d_targets_out && !d_labels_out)) return PK_OK;  // size query
+  if (!d_targets_out || !d_labels_out) return sn_fail(PK_ERR_INVALID_ARG, "NULL device buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(d_targets_out, s->pool_T, (size_t)s->pool_n * s->k * 48, cudaMemcpyDeviceToDevice,
+                                  st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_labels_out, s->pool_q, (size_t)s->pool_n * s->n_dof * 4, cudaMemcpyDeviceToDevice, st);
+  return sn_cuda(e, "pk_seednet_pool");
+}
+
 pk_status pk_seednet_train(pk_seednet* s, const pk_train_params* tp, float* host_loss, void* stream) {
   if (!s || !tp) return sn_fail(PK_ERR_INVALID_ARG, "NULL argument");
   if (tp->epochs < 0 || tp->batch < 128 || tp->steps_per_epoch < 1 || !(tp->lr > 0.f))
     return sn_fail(PK_ERR_INVALID_ARG, "invalid training parameters");
+  if (tp->refine_every < 0 || (tp->refine_every > 0 && (tp->refine_n < 1 || tp->refine_iters < 0)) ||
+      !(tp->pool_frac >= 0.f && tp->pool_frac <= 1.f) || tp->reserved != 0)
+    return sn_fail(PK_ERR_INVALID_ARG, "invalid refinement parameters");
   cudaStream_t st = (cudaStream_t)stream;
   const int M = tp->batch, m_pad = round_up(M, 128);
   pk_status ps = ensure_acts(s, m_pad);
@@ -777,6 +922,11 @@ pk_status pk_seednet_train(pk_seednet* s, const pk_train_params* tp, float* host
       datagen_kernel<<<(m_pad + 127) / 128, 128, 0, st>>>(s->d_robot, s->d_links, s->k, s->d_lohi, s->n_dof,
                                                           tp->seed, s->step, M, s->in_pad, m_pad, s->X, s->Xt,
                                                           s->qstar);
+      const int r0 = s->pool_n > 0 ? (int)(tp->pool_frac * (float)M) : 0;
+      if (r0 > 0)
+        pool_rows_kernel<<<(r0 + 127) / 128, 128, 0, st>>>(s->pool_T, s->pool_q, s->pool_n, s->k, s->n_dof,
+                                                           tp->seed ^ 0x706f6f6cull, s->step, r0, s->in_pad, m_pad,
+                                                           s->X, s->Xt, s->qstar);
       e = cudaGetLastError();
       if (e == cudaSuccess) e = loss_and_grad(s, M, m_pad, tp->mu, st);
       const float lr = tp->lr * 0.5f * (1.f + cosf(3.14159265f * (float)t / (float)total));
@@ -789,6 +939,10 @@ pk_status pk_seednet_train(pk_seednet* s, const pk_train_params* tp, float* host
       e = cudaMemcpy(&l, s->d_loss, 4, cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) return sn_cuda(e, "pk_seednet_train");
       host_loss[ep] = l / ((float)M * tp->steps_per_epoch);
+    }
+    if (tp->refine_every > 0 && (ep + 1) % tp->refine_every == 0 && ep + 1 < tp->epochs) {
+      ps = pk_seednet_refine(s, tp->refine_n, tp->refine_iters, tp->seed, nullptr, stream);
+      if (ps != PK_OK) return ps;
     }
   }
   return sn_cuda(cudaStreamSynchronize(st), "pk_seednet_train");

@@ -68,8 +68,9 @@ class pk_trajopt_params(C.Structure):
 class pk_train_params(C.Structure):
     _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("steps_per_epoch", C.c_int32),
                 ("lr", C.c_float), ("weight_decay", C.c_float), ("beta1", C.c_float),
-                ("beta2", C.c_float), ("eps", C.c_float), ("mu", C.c_float), ("reserved", C.c_int32),
-                ("seed", C.c_uint64)]
+                ("beta2", C.c_float), ("eps", C.c_float), ("mu", C.c_float), ("refine_every", C.c_int32),
+                ("seed", C.c_uint64), ("refine_n", C.c_int32), ("refine_iters", C.c_int32),
+                ("pool_frac", C.c_float), ("reserved", C.c_int32)]
 
 
 _vp = C.c_void_p
@@ -121,6 +122,8 @@ _SIGNATURES = {
     "pk_seednet_loss_grad": (_i32, [_vp, _i32, _vp, _vp, _f32p, _f32p, _vp]),
     "pk_seednet_train_step": (_i32, [_vp, _vp, _i32, _vp, _vp, C.c_float, _vp]),
     "pk_seednet_train": (_i32, [_vp, _vp, _f32p, _vp]),
+    "pk_seednet_refine": (_i32, [_vp, _i32, _i32, C.c_uint64, _i32p, _vp]),
+    "pk_seednet_pool": (_i32, [_vp, _vp, _vp, _i32p, _vp]),
     "pk_trace_enable": (_i32, [_i32]),
     "pk_trace_summary": (_i32, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
@@ -453,6 +456,25 @@ def pk_seednet_train(net: SeedNet, params: pk_train_params, stream=None) -> np.n
     _check(lib().pk_seednet_train(net.handle, C.byref(params), losses.ctypes.data_as(_f32p),
                                   _stream(stream)))
     return losses[:params.epochs]
+
+
+def pk_seednet_refine(net: SeedNet, n: int, max_iters: int = 20, seed: int = 500, stream=None) -> int:
+    """One LM refinement round of the label pool; returns the converged count."""
+    c = C.c_int32()
+    _check(lib().pk_seednet_refine(net.handle, n, max_iters, seed, C.byref(c), _stream(stream)))
+    return c.value
+
+
+def pk_seednet_pool(net: SeedNet, stream=None):
+    """(targets [n][k][12], labels [n][n_dof]) of the label pool (CUDA tensors)."""
+    cnt = C.c_int32()
+    _check(lib().pk_seednet_pool(net.handle, None, None, C.byref(cnt), _stream(stream)))
+    T = torch.empty(cnt.value, net.k, 12, device="cuda")
+    q = torch.empty(cnt.value, net.n, device="cuda")
+    if cnt.value:
+        _check(lib().pk_seednet_pool(net.handle, _dev(T, name="targets"), _dev(q, name="labels"), C.byref(cnt),
+                                     _stream(stream)))
+    return T, q
 
 
 PK_T_OK, PK_T_GOAL_MISSED, PK_T_COLLISION = 0, 1, 2

@@ -52,3 +52,51 @@ def test_learned_seeds_beat_random_seeds(trained):
     for b in np.nonzero(ok_l)[0][:500]:
         pe, re = oracle.ik_errors(o, tg, T[b], ql[b])
         assert pe <= 1e-3 * (1 + 1e-3) and re <= np.deg2rad(0.5) * (1 + 1e-3)
+
+
+def test_refined_pool_labels_are_ik_solutions(trained):
+    """An LM refinement round: every pool label reaches its pool target in FP64
+    (LM solutions within the success thresholds, the rest exact preimages)."""
+    spec, g, ee, net, losses = trained
+    n = 4096
+    conv = pk.pk_seednet_refine(net, n, max_iters=20, seed=777)
+    T, q = pk.pk_seednet_pool(net)
+    assert T.shape == (n, 1, 12) and q.shape == (n, 7)
+    assert conv >= 0.9 * n
+    o = oracle.Robot.from_dict(spec)
+    tg = oracle.Targets([ee])
+    Th, qh = T.cpu().numpy().astype(np.float64), q.cpu().numpy().astype(np.float64)
+    for b in range(0, n, 4):
+        pe, re = oracle.ik_errors(o, tg, Th[b], qh[b])
+        assert pe <= 1e-3 * (1 + 1e-3) and re <= np.deg2rad(0.5) * (1 + 1e-3)
+
+
+def test_humanoid_learned_seeds_beat_random_seeds():
+    """The 30-joint humanoid with six pose targets (54 input features, 8 x 30
+    outputs): learned proposals against uniform random seeds, same LM."""
+    spec, ends = synth.humanoid_robot(103)
+    links = list(ends)
+    g = pk.Robot.from_spec(spec)
+    net = pk.SeedNet(g, links, K=8, width=512, depth=4, seed=5)
+    tp = pk.pk_train_params_default(epochs=4, steps_per_epoch=600, batch=8192, seed=510, refine_every=2,
+                                    refine_n=16384)
+    losses = pk.pk_seednet_train(net, tp)
+    assert losses[-1] < losses[0]
+    B = 2048
+    qt = synth.uniform_q(511, B, spec.dof_lower, spec.dof_upper)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    targets = pk.pk_fk(g, dev(qt))[:, links].contiguous()
+    p = pk.pk_ik_params_default(max_iters=50, early_exit=1, cancel_siblings=0)
+    learned = pk.pk_seednet_infer(net, targets)
+    rand = dev(synth.uniform_q(512, (B, 8), spec.dof_lower, spec.dof_upper))
+    ql, _, il, sl = [x.cpu().numpy() for x in pk.pk_ik_solve(g, p, links, None, targets, learned)]
+    _, _, ir, sr = [x.cpu().numpy() for x in pk.pk_ik_solve(g, p, links, None, targets, rand)]
+    ok_l, ok_r = sl == 0, sr == 0
+    print(f"humanoid success learned {ok_l.mean():.4f} random {ok_r.mean():.4f}")
+    assert ok_l.mean() >= 0.5 and ok_l.mean() >= 3 * ok_r.mean()
+    o = oracle.Robot.from_dict(spec)
+    tg = oracle.Targets(links)
+    T = targets.cpu().numpy()
+    for b in np.nonzero(ok_l)[0][:200]:
+        pe, re = oracle.ik_errors(o, tg, T[b], ql[b])
+        assert pe <= 1e-3 * (1 + 1e-3) and re <= np.deg2rad(0.5) * (1 + 1e-3)
