@@ -224,13 +224,107 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Split form of the 32-column TMEM load: issue, then wait with the registers
+// bound to the wait so that no use can be scheduled before the data arrives.
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+
+// Packed FP32 pairs (two lanes of work per instruction on sm_100-class SMs).
+__device__ __forceinline__ uint64_t f32x2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 f32x2_split(uint64_t r) {
+  float2 o;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+  return o;
+}
+__device__ __forceinline__ uint64_t fma_f32x2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t add_f32x2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ float tanh_fast(float x) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(x));
+  return t;
+}
+
+// SiLU epilogue of 32 accumulator columns with the half-bias hb (shared
+// memory): h = acc/2 + b/2 = z/2, silu(z) = h + h tanh(h), in packed pairs;
+// z = 2h goes to Z when kept (training); BF16 row-major output.
+__device__ __forceinline__ void epilogue_silu32(const Epilogue& ep, int row, bool row_ok, int col0,
+                                                const uint32_t (&r)[32], const float* __restrict__ hb) {
+  const uint64_t half2 = f32x2(0.5f, 0.5f);
+  uint32_t packed[16];
+  float z[32];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const float2 b = *reinterpret_cast<const float2*>(hb + col0 + 2 * i);
+    const uint64_t h2 = fma_f32x2(f32x2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1])), half2,
+                                  f32x2(b.x, b.y));
+    const float2 h = f32x2_split(h2);
+    const uint64_t s2 = fma_f32x2(h2, f32x2(tanh_fast(h.x), tanh_fast(h.y)), h2);
+    const float2 sv = f32x2_split(s2);
+    __nv_bfloat162 o = __floats2bfloat162_rn(sv.x, sv.y);
+    packed[i] = *reinterpret_cast<uint32_t*>(&o);
+    z[2 * i] = h.x + h.x;
+    z[2 * i + 1] = h.y + h.y;
+  }
+  if (ep.out_t) {  // transposed copy for the weight gradients; padded rows stay zero
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const uint32_t w = row_ok ? packed[i] : 0u;
+      ep.out_t[(size_t)(col0 + 2 * i) * ep.ld_t + row] = __ushort_as_bfloat16((unsigned short)(w & 0xffffu));
+      ep.out_t[(size_t)(col0 + 2 * i + 1) * ep.ld_t + row] = __ushort_as_bfloat16((unsigned short)(w >> 16));
+    }
+  }
+  if (!row_ok) return;
+  if (ep.out_f32) {
+    float4* o = (float4*)(ep.out_f32 + (size_t)row * ep.ld_f32 + col0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) o[i] = make_float4(z[4 * i], z[4 * i + 1], z[4 * i + 2], z[4 * i + 3]);
+  }
+  uint4* o = (uint4*)(ep.out_bf16 + (size_t)row * ep.ld_bf16 + col0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) o[i] = make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2], packed[4 * i + 3]);
+}
+
 template <int BN>
 struct SmemLayout {
   static constexpr int kABytes = kBM * kBK * 2;
   static constexpr int kBBytes = BN * kBK * 2;
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kBarOffset = kStages * kStageBytes;
-  static constexpr int kBytes = kBarOffset + 256 + 1024;  // barriers + TMEM slot + alignment slack
+  static constexpr int kBiasOffset = kBarOffset + 256;     // half-bias of the SiLU epilogue
+  static constexpr int kMaxBias = 2048;
+  static constexpr int kBytes = kBiasOffset + kMaxBias * 4 + 1024;  // + alignment slack
   static constexpr uint32_t kTmemCols = 2 * BN;           // two accumulator buffers
 };
 
@@ -356,6 +450,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
+  float* hbias = (float*)(smem + L::kBiasOffset);
+  const bool silu_fwd = ep.mode == EPI_FWD_SILU && n_tiles * BN <= L::kMaxBias;
+  if (silu_fwd)
+    for (int i = threadIdx.x; i < n_tiles * BN; i += blockDim.x) hbias[i] = 0.5f * ep.bias[i];
   if (warp == 0) tmem_alloc(tmem_slot, L::kTmemCols);
   tc_fence_before();
   __syncthreads();
@@ -445,11 +543,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int row = m0 + q * 32 + lane;
       const bool row_ok = row < ep.m_valid;
       const uint32_t base = tmem + acc * BN + ((uint32_t)(q * 32) << 16);
+      const int cbeg = h * (BN / H), cend = (h + 1) * (BN / H);
+      if (silu_fwd) {
+        // TMEM loads one chunk ahead of the arithmetic
+        uint32_t ra[32], rb[32];
+        tmem_ld32_issue(base + (uint32_t)cbeg, ra);
+        tmem_ld_wait(ra);
 #pragma unroll 1
-      for (int c0 = h * (BN / H); c0 < (h + 1) * (BN / H); c0 += 32) {
-        float v[32];
-        tmem_ld32(base + (uint32_t)c0, v);
-        epilogue32(ep, row, row_ok, n0 + c0, v);
+        for (int c0 = cbeg; c0 < cend; c0 += 64) {
+          const bool more = c0 + 32 < cend;
+          if (more) tmem_ld32_issue(base + (uint32_t)(c0 + 32), rb);
+          epilogue_silu32(ep, row, row_ok, n0 + c0, ra, hbias);
+          if (!more) break;
+          tmem_ld_wait(rb);
+          const bool more2 = c0 + 64 < cend;
+          if (more2) tmem_ld32_issue(base + (uint32_t)(c0 + 64), ra);
+          epilogue_silu32(ep, row, row_ok, n0 + c0 + 32, rb, hbias);
+          if (more2) tmem_ld_wait(ra);
+        }
+      } else {
+#pragma unroll 1
+        for (int c0 = cbeg; c0 < cend; c0 += 32) {
+          float v[32];
+          tmem_ld32(base + (uint32_t)c0, v);
+          epilogue32(ep, row, row_ok, n0 + c0, v);
+        }
       }
       tc_fence_before();
       __syncwarp();
