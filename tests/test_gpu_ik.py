@@ -270,3 +270,46 @@ def test_full_size_sampled_against_oracle():
     for b in np.nonzero(ok)[0][:2000]:
         pe, re = oracle.ik_errors(o, tg, targets[b], q[b])
         assert pe <= TOL_POS * (1 + 1e-3) and re <= TOL_ROT * (1 + 1e-3)
+
+
+@pytest.mark.parametrize("name,spec,kind", [
+    ("chain7", synth.chain_robot(100, 7), pk.PK_TARGET_POSE),
+    ("prismatic6", synth.chain_robot(9, 6, prismatic=(0, 3)), pk.PK_TARGET_POSE),
+    ("chain7_position", synth.chain_robot(100, 7), pk.PK_TARGET_POSITION),
+    ("chain3", synth.chain_robot(5, 3), pk.PK_TARGET_POSITION),
+], ids=["chain7", "prismatic6", "chain7_position", "chain3"])
+def test_tiny_launches_iterates_match_oracle(name, spec, kind):
+    """Calls of four problems (one partly filled warp, most lanes idle from the
+    start) against the oracle's iterates and against the same problems solved
+    in one full launch."""
+    g, o = pair(spec)
+    ee = o.n_joints - 1
+    qt = synth.uniform_q(61, 48, o.dof_lower, o.dof_upper)
+    sd = synth.uniform_q(62, (48, 1), o.dof_lower, o.dof_upper)
+    targets = oracle.fk(o, qt)[:, [ee]]
+    kinds = [kind]
+    tg = oracle.Targets([ee], kinds)
+    p = pk.pk_ik_params_default(max_iters=30, early_exit=0)
+    ref = oracle.ik_solve(o, oracle_params(p), tg, targets, sd, n_trace=5)
+    tie = ref["margin"] <= 1e-5
+    for k in (1, 3, 5):
+        pk_ = pk.pk_ik_params_default(max_iters=k, early_exit=0)
+        q = np.concatenate([_solve(g, pk_, ee, targets[i:i + 4], sd[i:i + 4], kinds=kinds)[0]
+                            for i in range(0, 48, 4)])
+        # the same problems in one launch (full warps)
+        q1 = _solve(g, pk_, ee, targets, sd, kinds=kinds)[0]
+        qr = ref["trace"][:, k - 1]
+        rel = (np.abs(q - qr) / np.maximum(1.0, np.abs(qr))).max(axis=1)
+        rel1 = (np.abs(q1 - qr) / np.maximum(1.0, np.abs(qr))).max(axis=1)
+        print(f"{name} k={k}: worst rel vs oracle {rel[~tie].max():.2e}")
+        assert np.all(rel[~tie] <= 1e-4), (k, np.sort(rel)[-5:])
+        np.testing.assert_array_equal(q, q1)  # a problem's arithmetic does not depend on its launch
+    # whole solves with early exit, ragged batches
+    p = pk.pk_ik_params_default(max_iters=50, early_exit=1)
+    for B in (3, 40):
+        q, err, iters, status = _solve(g, p, ee, targets[:B], sd[:B], kinds=kinds)
+        r = oracle.ik_solve(o, oracle_params(p), tg, targets[:B], sd[:B])
+        assert (status == r["status"]).mean() >= 0.9
+        for b in np.nonzero(status == 0)[0]:
+            pe, re = oracle.ik_errors(o, tg, targets[b], q[b])
+            assert pe <= TOL_POS * (1 + 1e-3) and re <= TOL_ROT * (1 + 1e-3)
