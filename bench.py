@@ -311,6 +311,35 @@ def extra_workloads(torch, pk, synth, args, flush, stream):
         nconv = int((hst == pk.PK_P_CONVERGED).sum().item())
         hum[name] = {"value": nconv / (hms / 1e3), "ms_per_step": hms / 3, "success_rate": nconv / (3 * Bh)}
     out["learned_humanoid"] = hum
+    # mobile-base IK (Sec. IV-D): shifted reachable poses, fixed vs SE(2)-base arm, 5 mm / 0.05 rad
+    mcfg = synth.MOBILE
+    arm, mob, qt, shift, sdm = synth.mobile_workload(mcfg)
+    ga, gm = pk.Robot.from_spec(arm), pk.Robot.from_spec(mob)
+    ee = ga.n_joints - 1
+    Tm = pk.pk_fk(ga, dev(qt))[:, ee:ee + 1].clone()
+    Tm[:, 0, 3] += dev(shift[:, 0])
+    Tm[:, 0, 7] += dev(shift[:, 1])
+    Tm = Tm.contiguous()
+    seeds_fixed = dev(sdm)
+    seeds_mobile = torch.cat([torch.zeros(sdm.shape[0], sdm.shape[1], 3, device="cuda"), seeds_fixed], dim=2)
+    mp = pk.pk_ik_params_default(max_iters=mcfg["max_iters"], early_exit=1, cancel_siblings=1,
+                                 tol_pos=mcfg["tol_pos"], tol_rot=mcfg["tol_rot"])
+    mob_line = {"workload": mcfg["name"], "unit": UNIT, "tolerance": "5 mm / 0.05 rad",
+                "targets": "reachable poses of the fixed-base arm shifted by U([-1, 1]^2) m in the plane"}
+    for name, gg, link, S in (("fixed_base", ga, ee, seeds_fixed), ("mobile_base", gm, ee + 3, seeds_mobile)):
+        Bm = S.shape[0]
+        mws = torch.empty(pk.pk_ik_workspace_bytes(gg, Bm, S.shape[1]), dtype=torch.uint8, device="cuda")
+        mst = torch.empty(3, Bm, dtype=torch.int32, device="cuda")
+        mq = (torch.empty(Bm, gg.n_dof, device="cuda"), torch.empty(Bm, 2, device="cuda"),
+              torch.empty(Bm, dtype=torch.int32, device="cuda"))
+        pk.pk_ik_solve(gg, mp, [link], None, Tm, S, mws, out=mq + (mst[0],))
+        mms = Timed(torch, 3, flush).run(
+            lambda k: pk.pk_ik_solve(gg, mp, [link], None, Tm, S, mws, out=mq + (mst[k],)), stream)
+        nconv = int((mst == pk.PK_P_CONVERGED).sum().item())
+        ok = (mst[2] == pk.PK_P_CONVERGED)
+        mob_line[name] = {"value": nconv / (mms / 1e3), "ms_per_step": mms / 3, "success_rate": nconv / (3 * Bm),
+                          "mean_pos_err_m": float(mq[1][ok, 0].mean().item()) if bool(ok.any()) else None}
+    out["mobile_base"] = mob_line
     # IK-Beam (Sec. V-C): 64 seeds, 6 iterations, keep 4, 10 iterations, at the paper's batch sizes
     spec = synth.chain_robot(100, 7)
     g = pk.Robot.from_spec(spec)

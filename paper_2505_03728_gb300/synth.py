@@ -118,6 +118,23 @@ def _add_branch(rng, parent_of_first, n_joints, parent, types, axis, origin, low
     return prev
 
 
+def mobile_base_robot(arm: RobotSpec, extent: float = 10.0) -> RobotSpec:
+    """The arm on an SE(2) mobile base: prismatic x, prismatic y and a revolute
+    z joint (all at the world origin) ahead of the arm's joints, so that every
+    frame is T_world<-base(x, y, theta) T_base<-i.  Base limits +-extent m and
+    +-2 pi rad keep the limit hinge inactive in practice."""
+    n0 = len(arm["parent"])
+    parent = [-1, 0, 1] + [p + 3 if p >= 0 else 2 for p in arm["parent"]]
+    types = [JOINT_PRISMATIC, JOINT_PRISMATIC, JOINT_REVOLUTE] + list(arm["type"])
+    axis = [[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]] + [list(a) for a in arm["axis"]]
+    eye = [1.0, 0, 0, 0, 0, 1.0, 0, 0, 0, 0, 1.0, 0]
+    origin = [eye, eye, eye] + [list(o) for o in arm["origin"]]
+    lower = [-extent, -extent, -2 * np.pi] + list(arm["lower"])
+    upper = [extent, extent, 2 * np.pi] + list(arm["upper"])
+    assert len(parent) == n0 + 3
+    return _finish("mobile_" + arm["name"], parent, types, axis, origin, lower, upper)
+
+
 def hand_robot(seed: int = 102) -> tuple[RobotSpec, np.ndarray]:
     """24-DoF hand-like tree; returns (robot, fingertip frame indices [5])."""
     rng = np.random.default_rng(seed)
@@ -224,6 +241,26 @@ def sphere_obstacles_shell(seed: int, count: int, r_in: float, r_out: float, z_m
         out[i, 3] = rng.uniform(r_lo, r_hi)
         i += 1
     return out
+
+
+# Mobile-base IK: reachable poses of the 7-DoF chain from the fixed base,
+# shifted by a planar translation uniform in [-shift, shift]^2 (z unchanged).
+MOBILE = dict(name="mobile_ik7_16384x8", robot_seed=100, n_dof=7, batch=16384, n_seeds=8, target_seed=800,
+              shift_seed=801, seed_seed=802, shift=1.0, max_iters=50, tol_pos=5e-3, tol_rot=0.05)
+
+
+def mobile_workload(cfg: dict = MOBILE, batch: int | None = None):
+    """(arm spec, mobile spec, arm configurations of the reachable poses [B][n],
+    planar shifts [B][2], arm seeds [B][S][n]).  Targets are the arm's FK of
+    the configurations with the shift added to the translation; base seeds
+    start at the origin (x = y = theta = 0)."""
+    arm = chain_robot(cfg["robot_seed"], cfg["n_dof"])
+    B = cfg["batch"] if batch is None else batch
+    qt = uniform_q(cfg["target_seed"], B, arm.dof_lower, arm.dof_upper)
+    rng = np.random.default_rng(cfg["shift_seed"])
+    shift = rng.uniform(-cfg["shift"], cfg["shift"], size=(B, 2))
+    sd = uniform_q(cfg["seed_seed"], (B, cfg["n_seeds"]), arm.dof_lower, arm.dof_upper)
+    return arm, mobile_base_robot(arm), qt, shift, sd
 
 
 def trajopt_workload(cfg: dict, batch: int | None = None):
