@@ -386,7 +386,12 @@ __device__ __forceinline__ void flush_counts(WorkCount wc, unsigned long long* s
 }
 
 template <int N>
-__global__ void __launch_bounds__(kLmThreads) chain_lm_kernel(
+// Three 128-thread blocks per SM (the register budget that avoids spills);
+// stating it lets the compiler schedule for that occupancy.
+#ifndef PK_LM_MINB
+#define PK_LM_MINB 3
+#endif
+__global__ void __launch_bounds__(kLmThreads, PK_LM_MINB) chain_lm_kernel(
     const __grid_constant__ ChainC<N> rc, const __grid_constant__ LmParams lp,
     const float* __restrict__ targets, const float* __restrict__ seeds, int n_seeds, int P,
     IkWorkspace ws) {
