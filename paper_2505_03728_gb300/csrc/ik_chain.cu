@@ -34,14 +34,22 @@ struct Frames {
 // FK of q expressed in the frame Ti (= T_target^-1, or a pure translation by
 // -p_target for position targets), the target-frame residual xi (unweighted:
 // log(E) for pose targets, E.t for position targets), the errors and the cost.
-template <int N>
+// F = kChainFast: all joints revolute, origins pure translations, a pure
+// translation as tool, pose target -- the runtime feature tests compile away
+// (smaller and denser code for the common arm); F = 0: general chain.
+constexpr int kChainFast = 1;
+#ifndef PK_CHAIN_FAST
+#define PK_CHAIN_FAST 1
+#endif
+
+template <int N, int F = 0>
 __device__ __forceinline__ void chain_eval(const ChainC<N>& rc, const LmParams& lp, const Rt& Ti,
                                            const float* q, Frames<N>& fr, float* xi, float& th,
                                            float& pe, float& f) {
   Rt T = Ti;
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    if (rc.orot & (1u << j)) {
+    if (F != kChainFast && (rc.orot & (1u << j))) {
       Rt O;
 #pragma unroll
       for (int i = 0; i < 9; ++i) O.r[i] = rc.o_r[j][i];
@@ -55,7 +63,7 @@ __device__ __forceinline__ void chain_eval(const ChainC<N>& rc, const LmParams& 
     fr.p[j][0] = T.t[0];
     fr.p[j][1] = T.t[1];
     fr.p[j][2] = T.t[2];
-    if (rc.prism & (1u << j)) {
+    if (F != kChainFast && (rc.prism & (1u << j))) {
 #pragma unroll
       for (int i = 0; i < 3; ++i) T.t[i] = fmaf(fr.u[j][i], q[j], T.t[i]);
     } else {
@@ -64,7 +72,7 @@ __device__ __forceinline__ void chain_eval(const ChainC<N>& rc, const LmParams& 
       rot_joint(T.r, fr.u[j], rc.a[j], s, c);
     }
   }
-  if (rc.toolrot) {
+  if (F != kChainFast && rc.toolrot) {
     Rt O;
 #pragma unroll
     for (int i = 0; i < 9; ++i) O.r[i] = rc.tool_r[i];
@@ -76,7 +84,7 @@ __device__ __forceinline__ void chain_eval(const ChainC<N>& rc, const LmParams& 
   }
   pe = sqrtf(fmaf(T.t[0], T.t[0], fmaf(T.t[1], T.t[1], T.t[2] * T.t[2])));
   float acc;
-  if (!lp.pos_only) {
+  if (F == kChainFast || !lp.pos_only) {
     th = se3_log(T, xi);
     const float a = lp.w_pos * lp.w_pos, b = lp.w_rot * lp.w_rot;
     acc = a * (xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]) +
@@ -99,17 +107,17 @@ __device__ __forceinline__ void chain_eval(const ChainC<N>& rc, const LmParams& 
 
 // Weighted pose (or position) rows of the Jacobian, J[6][N], and the weighted
 // residual rw[6] (zero rows 3..5 for position targets).
-template <int N>
+template <int N, int F = 0>
 __device__ __forceinline__ void chain_pose_jac(const ChainC<N>& rc, const LmParams& lp,
                                                const Frames<N>& fr, const float* xi, float th,
                                                float (&J)[6][N], float* rw) {
-  if (!lp.pos_only) {
+  if (F == kChainFast || !lp.pos_only) {
     float A[9], B[9];
     se3_jlinv_blocks(xi, xi + 3, th, A, B);
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       float top[3], bot[3];
-      if (rc.prism & (1u << j)) {
+      if (F != kChainFast && (rc.prism & (1u << j))) {
         mat_vec(A, fr.u[j], top);
         bot[0] = bot[1] = bot[2] = 0.f;
       } else {
@@ -158,12 +166,12 @@ __device__ __forceinline__ void chain_pose_jac(const ChainC<N>& rc, const LmPara
 }
 
 // Packed J^T J (lower) and J^T r including the limit and rest rows.
-template <int N>
+template <int N, int F = 0>
 __device__ __forceinline__ void chain_normal(const ChainC<N>& rc, const LmParams& lp,
                                              const Frames<N>& fr, const float* xi, float th,
                                              const float* q, float* A, float* g) {
   float J[6][N], rw[6];
-  chain_pose_jac<N>(rc, lp, fr, xi, th, J, rw);
+  chain_pose_jac<N, F>(rc, lp, fr, xi, th, J, rw);
 #pragma unroll
   for (int i = 0; i < N; ++i) {
 #pragma unroll
@@ -211,7 +219,7 @@ int ik_rec_stride(int n_dof) { return ((n_dof + 3) & ~3) + 4; }
 
 // The lane-refilling LM loop over the P problems of one batch; problems are
 // claimed from *head, results go to rec, converged flags to flags.
-template <int N>
+template <int N, int F = 0>
 __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams& lp,
                                              const float* __restrict__ targets, const float* __restrict__ seeds,
                                              int n_seeds, int P, int32_t* head, int32_t* flags, float* rec,
@@ -276,7 +284,7 @@ __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams
               for (int c = 0; c < 3; ++c) Tt.r[i * 3 + c] = qq.tgt[qcur][e][i * 4 + c];
               Tt.t[i] = qq.tgt[qcur][e][i * 4 + 3];
             }
-            if (lp.pos_only) {
+            if (F != kChainFast && lp.pos_only) {
               rt_identity(Ti);
               Ti.t[0] = -Tt.t[0]; Ti.t[1] = -Tt.t[1]; Ti.t[2] = -Tt.t[2];
             } else {
@@ -304,7 +312,7 @@ __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams
     // --- evaluate the candidate
     Frames<N> fr;
     float xi[6], th, pe, fc;
-    chain_eval<N>(rc, lp, Ti, qc, fr, xi, th, pe, fc);
+    chain_eval<N, F>(rc, lp, Ti, qc, fr, xi, th, pe, fc);
     ++wc.eval;
 
     bool acc, done = false;
@@ -337,7 +345,7 @@ __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams
     if (!done) {
       // --- damped normal equations and the next candidate
       if (acc) {
-        chain_normal<N>(rc, lp, fr, xi, th, q, A0, g);
+        chain_normal<N, F>(rc, lp, fr, xi, th, q, A0, g);
         ++wc.build;
       }
       ++wc.solve;
@@ -385,19 +393,19 @@ __device__ __forceinline__ void flush_counts(WorkCount wc, unsigned long long* s
   }
 }
 
-template <int N>
 // Three 128-thread blocks per SM (the register budget that avoids spills);
 // stating it lets the compiler schedule for that occupancy.
 #ifndef PK_LM_MINB
 #define PK_LM_MINB 3
 #endif
+template <int N, int F>
 __global__ void __launch_bounds__(kLmThreads, PK_LM_MINB) chain_lm_kernel(
     const __grid_constant__ ChainC<N> rc, const __grid_constant__ LmParams lp,
     const float* __restrict__ targets, const float* __restrict__ seeds, int n_seeds, int P,
     IkWorkspace ws) {
   __shared__ ChainQueue<N> qq[kLmThreads / 32];
   WorkCount wc;
-  chain_lm_run<N>(rc, lp, targets, seeds, n_seeds, P, ws.head, ws.flags, ws.rec, wc, qq[threadIdx.x >> 5]);
+  chain_lm_run<N, F>(rc, lp, targets, seeds, n_seeds, P, ws.head, ws.flags, ws.rec, wc, qq[threadIdx.x >> 5]);
   flush_counts(wc, ws.stats);
 }
 
@@ -526,22 +534,31 @@ static cudaError_t chain_lm_launch(const ChainHost& ch, const LmParams& lp, cons
                                    const float* d_seeds, int batch, int n_seeds, IkWorkspace ws,
                                    float* d_q, float* d_err, int32_t* d_iters, int32_t* d_status,
                                    cudaStream_t stream) {
-  static int blocks_per_sm = 0;
-  if (blocks_per_sm == 0) {
+  // the fast variant when the chain has only revolute joints, translation-only
+  // origins and tool, and a pose target (the common arm)
+  const bool fast = PK_CHAIN_FAST && ch.prism == 0 && ch.orot == 0 && !ch.toolrot && !lp.pos_only;
+  static int blocks_per_sm[2] = {0, 0};
+  if (blocks_per_sm[fast] == 0) {
     int b = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, chain_lm_kernel<N>, kLmThreads, 0);
+    cudaError_t e = fast ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, chain_lm_kernel<N, kChainFast>,
+                                                                        kLmThreads, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, chain_lm_kernel<N, 0>, kLmThreads, 0);
     if (e != cudaSuccess) return e;
-    blocks_per_sm = b > 0 ? b : 1;
+    blocks_per_sm[fast] = b > 0 ? b : 1;
   }
   const long P = (long)batch * n_seeds;
-  long grid = (long)blocks_per_sm * sm_count();
+  long grid = (long)blocks_per_sm[fast] * sm_count();
   const long need = (P + kLmThreads - 1) / kLmThreads;
   if (grid > need) grid = need;
   const ChainC<N> rc = chain_const<N>(ch);
   {
     TraceScope tr("ik_lm", stream);
-    chain_lm_kernel<N><<<(unsigned)grid, kLmThreads, 0, stream>>>(rc, lp, d_targets, d_seeds, n_seeds,
-                                                                  (int)P, ws);
+    if (fast)
+      chain_lm_kernel<N, kChainFast><<<(unsigned)grid, kLmThreads, 0, stream>>>(rc, lp, d_targets, d_seeds,
+                                                                                n_seeds, (int)P, ws);
+    else
+      chain_lm_kernel<N, 0><<<(unsigned)grid, kLmThreads, 0, stream>>>(rc, lp, d_targets, d_seeds, n_seeds,
+                                                                       (int)P, ws);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !d_q) return e;
