@@ -44,8 +44,8 @@ FLOPS_PER_BUILD = 1362.0
 FLOPS_PER_SOLVE = 172.4
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
 # DRAM bytes (read + write) per target of the LM kernel: ncu capture of the
-# 16,384-target learned-seed launch (4.594 MB), inputs read once (see profiles/).
-LM_DRAM_BYTES_PER_TARGET = 4593920 / 16384
+# 16,384-target learned-seed launch (4.586 MB), inputs read once (see profiles/).
+LM_DRAM_BYTES_PER_TARGET = 4586240 / 16384
 # FP32 operations per trajectory-iteration of the trajectory kernel (ncu count
 # over 64 trajectories x 50 iterations, see profiles/).
 TRAJ_FLOPS_PER_ITER = 1.995e6

@@ -93,6 +93,10 @@ bool get_encode() {
   return true;
 }
 
+#ifndef PK_TMA_STORE
+#define PK_TMA_STORE 1
+#endif
+
 // 2-D BF16 tensor map over a row-major [rows][cols] matrix, box 64 x box_rows,
 // 128-byte swizzle.
 bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
@@ -105,9 +109,21 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols, ui
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Output map of the SiLU epilogue: BF16 [rows][cols] row-major, 32 x 32 boxes,
+// no swizzle (the epilogue writes plain row-major tiles).
+bool make_store_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols) {
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * 2};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int BN>
-cudaError_t gemm_launch(const CUtensorMap& ma, const CUtensorMap& mb, int a_rows, int b_rows, int K,
-                        int splits, const Epilogue& ep, int* d_err, cudaStream_t st) {
+cudaError_t gemm_launch(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mc, int a_rows, int b_rows,
+                        int K, int splits, const Epilogue& ep, int* d_err, cudaStream_t st) {
   using Lay = pk::tc::SmemLayout<BN>;
   static int sms = 0;
   if (!sms) {
@@ -128,8 +144,8 @@ cudaError_t gemm_launch(const CUtensorMap& ma, const CUtensorMap& mb, int a_rows
   const int tiles = m_tiles * n_tiles * splits;
   const int grid = tiles < sms ? tiles : sms;
   pk::TraceScope tr(ep.mode == pk::tc::EPI_WGRAD_ADD ? "gemm_wgrad" : "gemm", st);
-  pk::tc::gemm_bf16_tc_kernel<BN><<<grid, pk::tc::kThreads, Lay::kBytes, st>>>(ma, mb, m_tiles, n_tiles, splits,
-                                                                              K, per, ep, d_err);
+  pk::tc::gemm_bf16_tc_kernel<BN><<<grid, pk::tc::kThreads, Lay::kBytes, st>>>(ma, mb, mc, m_tiles, n_tiles,
+                                                                              splits, K, per, ep, d_err);
   return cudaGetLastError();
 }
 
@@ -137,12 +153,20 @@ cudaError_t gemm_launch(const CUtensorMap& ma, const CUtensorMap& mb, int a_rows
 cudaError_t gemm(const __nv_bfloat16* A, int a_rows, const __nv_bfloat16* B, int b_rows, int K, int splits,
                  const Epilogue& ep, int* d_err, cudaStream_t st) {
   const int BN = (b_rows % 256 == 0) ? 256 : (b_rows % 128 == 0) ? 128 : 64;
-  CUtensorMap ma, mb;
+  CUtensorMap ma, mb, mc;
   if (!make_map(&ma, A, a_rows, K, pk::tc::kBM) || !make_map(&mb, B, b_rows, K, BN))
     return cudaErrorInvalidValue;
-  if (BN == 256) return gemm_launch<256>(ma, mb, a_rows, b_rows, K, splits, ep, d_err, st);
-  if (BN == 128) return gemm_launch<128>(ma, mb, a_rows, b_rows, K, splits, ep, d_err, st);
-  return gemm_launch<64>(ma, mb, a_rows, b_rows, K, splits, ep, d_err, st);
+  Epilogue e2 = ep;
+  e2.tma_store = 0;
+  mc = ma;  // unused unless the SiLU epilogue stores through it
+  if (ep.mode == pk::tc::EPI_FWD_SILU && PK_TMA_STORE && ep.out_bf16 && ep.ld_bf16 == b_rows &&
+      ep.m_valid == a_rows && (((uintptr_t)ep.out_bf16) & 15) == 0) {
+    if (!make_store_map(&mc, ep.out_bf16, a_rows, b_rows)) return cudaErrorInvalidValue;
+    e2.tma_store = 1;
+  }
+  if (BN == 256) return gemm_launch<256>(ma, mb, mc, a_rows, b_rows, K, splits, e2, d_err, st);
+  if (BN == 128) return gemm_launch<128>(ma, mb, mc, a_rows, b_rows, K, splits, e2, d_err, st);
+  return gemm_launch<64>(ma, mb, mc, a_rows, b_rows, K, splits, e2, d_err, st);
 }
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }

@@ -54,6 +54,7 @@ struct Epilogue {
   int ld_zprev;
   const float* lohi;        // SEEDS: joint limits [2][n_dof]
   int n_dof;
+  int tma_store;            // FWD_SILU: out_bf16 is written through the output tensor map
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -119,6 +120,21 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
           smem_u32(dst)),
       "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
+}
+
+// Bulk tensor store shared -> global (one bulk group per call site's commit).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"((uint64_t)map),
+               "r"(smem_u32(src)), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most one group still reading shared memory
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// generic-proxy shared-memory writes become visible to the bulk-copy engine
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
@@ -276,19 +292,23 @@ __device__ __forceinline__ float tanh_fast(float x) {
   return t;
 }
 
-// SiLU epilogue of 32 accumulator columns with the half-bias hb (shared
-// memory): h = acc/2 + b/2 = z/2, silu(z) = h + h tanh(h), in packed pairs;
-// z = 2h goes to Z when kept (training); BF16 row-major output.
+// SiLU epilogue of 32 accumulator columns: h = acc/2 + b/2 = z/2,
+// silu(z) = h + h tanh(h), in packed pairs; z = 2h goes to Z when kept
+// (training), the BF16 transposed copy too.  The BF16 row-major output goes
+// either straight to global memory or, with `stage` set, into this lane's
+// 64-byte row of a 32 x 32 shared-memory tile (16-byte chunks written in a
+// lane-rotated order: conflict-free) for a bulk tensor store.
 __device__ __forceinline__ void epilogue_silu32(const Epilogue& ep, int row, bool row_ok, int col0,
-                                                const uint32_t (&r)[32], const float* __restrict__ hb) {
+                                                const uint32_t (&r)[32], uint8_t* stage, int lane) {
   const uint64_t half2 = f32x2(0.5f, 0.5f);
   uint32_t packed[16];
   float z[32];
+  const float2* b2 = reinterpret_cast<const float2*>(ep.bias + col0);
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
-    const float2 b = *reinterpret_cast<const float2*>(hb + col0 + 2 * i);
-    const uint64_t h2 = fma_f32x2(f32x2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1])), half2,
-                                  f32x2(b.x, b.y));
+    const float2 b = __ldg(b2 + i);
+    const uint64_t hb = fma_f32x2(f32x2(b.x, b.y), half2, f32x2(0.f, 0.f));
+    const uint64_t h2 = fma_f32x2(f32x2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1])), half2, hb);
     const float2 h = f32x2_split(h2);
     const uint64_t s2 = fma_f32x2(h2, f32x2(tanh_fast(h.x), tanh_fast(h.y)), h2);
     const float2 sv = f32x2_split(s2);
@@ -305,28 +325,31 @@ __device__ __forceinline__ void epilogue_silu32(const Epilogue& ep, int row, boo
       ep.out_t[(size_t)(col0 + 2 * i + 1) * ep.ld_t + row] = __ushort_as_bfloat16((unsigned short)(w >> 16));
     }
   }
-  if (!row_ok) return;
-  if (ep.out_f32) {
+  if (row_ok && ep.out_f32) {
     float4* o = (float4*)(ep.out_f32 + (size_t)row * ep.ld_f32 + col0);
 #pragma unroll
     for (int i = 0; i < 8; ++i) o[i] = make_float4(z[4 * i], z[4 * i + 1], z[4 * i + 2], z[4 * i + 3]);
   }
+  if (stage) {
+    uint4* rowp = reinterpret_cast<uint4*>(stage + lane * 64);
+    const int rot = (lane >> 1) & 3;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = (i + rot) & 3;
+      uint4 w;
+      w.x = k == 0 ? packed[0] : k == 1 ? packed[4] : k == 2 ? packed[8] : packed[12];
+      w.y = k == 0 ? packed[1] : k == 1 ? packed[5] : k == 2 ? packed[9] : packed[13];
+      w.z = k == 0 ? packed[2] : k == 1 ? packed[6] : k == 2 ? packed[10] : packed[14];
+      w.w = k == 0 ? packed[3] : k == 1 ? packed[7] : k == 2 ? packed[11] : packed[15];
+      rowp[k] = w;
+    }
+    return;
+  }
+  if (!row_ok) return;
   uint4* o = (uint4*)(ep.out_bf16 + (size_t)row * ep.ld_bf16 + col0);
 #pragma unroll
   for (int i = 0; i < 4; ++i) o[i] = make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2], packed[4 * i + 3]);
 }
-
-template <int BN>
-struct SmemLayout {
-  static constexpr int kABytes = kBM * kBK * 2;
-  static constexpr int kBBytes = BN * kBK * 2;
-  static constexpr int kStageBytes = kABytes + kBBytes;
-  static constexpr int kBarOffset = kStages * kStageBytes;
-  static constexpr int kBiasOffset = kBarOffset + 256;     // half-bias of the SiLU epilogue
-  static constexpr int kMaxBias = 2048;
-  static constexpr int kBytes = kBiasOffset + kMaxBias * 4 + 1024;  // + alignment slack
-  static constexpr uint32_t kTmemCols = 2 * BN;           // two accumulator buffers
-};
 
 #ifndef PK_EPI_WARPS
 #define PK_EPI_WARPS 8
@@ -335,6 +358,20 @@ struct SmemLayout {
 // (or one per quarter with 4).
 constexpr int kEpiWarps = PK_EPI_WARPS;
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // warp 0: TMA, warp 1: MMA, then the epilogue warps
+
+template <int BN>
+struct SmemLayout {
+  static constexpr int kABytes = kBM * kBK * 2;
+  static constexpr int kBBytes = BN * kBK * 2;
+  static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kBarOffset = kStages * kStageBytes;
+  // output staging of the SiLU epilogue: two 32 x 32 BF16 tiles per epilogue warp
+  static constexpr int kStoreOffset = (kBarOffset + 256 + 1023) & ~1023;
+  static constexpr int kStoreTile = 32 * 32 * 2;
+  static constexpr int kBytes = kStoreOffset + kEpiWarps * 2 * kStoreTile + 1024;  // + alignment slack
+  static constexpr uint32_t kTmemCols = 2 * BN;           // two accumulator buffers
+};
+
 
 // Epilogue of 32 columns [col0, col0 + 32) of one accumulator row.
 __device__ __forceinline__ void epilogue32(const Epilogue& ep, int row, bool row_ok, int col0, float* v) {
@@ -422,7 +459,8 @@ __device__ __forceinline__ void epilogue32(const Epilogue& ep, int row, bool row
 template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                        int m_tiles, int n_tiles, int splits, int K, int kb_per_split, Epilogue ep, int* err) {
+                        const __grid_constant__ CUtensorMap tmC, int m_tiles, int n_tiles, int splits, int K,
+                        int kb_per_split, Epilogue ep, int* err) {
   using L = SmemLayout<BN>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -450,10 +488,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  float* hbias = (float*)(smem + L::kBiasOffset);
-  const bool silu_fwd = ep.mode == EPI_FWD_SILU && n_tiles * BN <= L::kMaxBias;
-  if (silu_fwd)
-    for (int i = threadIdx.x; i < n_tiles * BN; i += blockDim.x) hbias[i] = 0.5f * ep.bias[i];
+  const bool silu_fwd = ep.mode == EPI_FWD_SILU;
   if (warp == 0) tmem_alloc(tmem_slot, L::kTmemCols);
   tc_fence_before();
   __syncthreads();
@@ -529,6 +564,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;
     constexpr int H = kEpiWarps / 4;
     const int h = (warp - 2) / 4;
+    uint8_t* stage_base = smem + L::kStoreOffset + (warp - 2) * 2 * L::kStoreTile;
+    int sbuf = 0;
     uint32_t tc = 0;
     for (int t = blockIdx.x; t < n_tiles_total; t += gridDim.x, ++tc) {
       const int r = t % (m_tiles * n_tiles);
@@ -545,20 +582,42 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t base = tmem + acc * BN + ((uint32_t)(q * 32) << 16);
       const int cbeg = h * (BN / H), cend = (h + 1) * (BN / H);
       if (silu_fwd) {
-        // TMEM loads one chunk ahead of the arithmetic
+        // TMEM loads one chunk ahead of the arithmetic; with the tensor-map
+        // store, each 32 x 32 output block goes through a double-buffered
+        // shared-memory tile (the store issued two blocks earlier must have
+        // finished reading a buffer before it is rewritten)
         uint32_t ra[32], rb[32];
+        const int y0 = m0 + q * 32;
+        auto chunk = [&](int c, const uint32_t(&rr)[32]) {
+          uint8_t* buf = nullptr;
+          if (ep.tma_store) {
+            buf = stage_base + sbuf * L::kStoreTile;
+            if (lane == 0) bulk_wait_read_1();
+            __syncwarp();
+          }
+          epilogue_silu32(ep, row, row_ok, n0 + c, rr, buf, lane);
+          if (ep.tma_store) {
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+              tma_store_2d(&tmC, buf, n0 + c, y0);
+              bulk_commit();
+            }
+            sbuf ^= 1;
+          }
+        };
         tmem_ld32_issue(base + (uint32_t)cbeg, ra);
         tmem_ld_wait(ra);
 #pragma unroll 1
         for (int c0 = cbeg; c0 < cend; c0 += 64) {
           const bool more = c0 + 32 < cend;
           if (more) tmem_ld32_issue(base + (uint32_t)(c0 + 32), rb);
-          epilogue_silu32(ep, row, row_ok, n0 + c0, ra, hbias);
+          chunk(c0, ra);
           if (!more) break;
           tmem_ld_wait(rb);
           const bool more2 = c0 + 64 < cend;
           if (more2) tmem_ld32_issue(base + (uint32_t)(c0 + 64), ra);
-          epilogue_silu32(ep, row, row_ok, n0 + c0 + 32, rb, hbias);
+          chunk(c0 + 32, rb);
           if (more2) tmem_ld_wait(ra);
         }
       } else {
@@ -573,6 +632,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
     }
+    if (lane == 0) bulk_wait_all();  // the output stores are complete before the CTA exits
+    __syncwarp();
   }
   tc_fence_before();
   __syncthreads();
