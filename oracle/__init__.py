@@ -53,7 +53,8 @@ _f64p = C.POINTER(C.c_double)
 
 class _Robot(C.Structure):
     _fields_ = [("n_joints", C.c_int32), ("parent", _i32p), ("type", _i32p), ("axis", _f64p),
-                ("origin", _f64p), ("lower", _f64p), ("upper", _f64p)]
+                ("origin", _f64p), ("lower", _f64p), ("upper", _f64p), ("mimic", _i32p),
+                ("mimic_mult", _f64p), ("mimic_off", _f64p)]
 
 
 class _IkParams(C.Structure):
@@ -108,7 +109,7 @@ def _p(a):
 class Robot:
     """A kinematic tree: parent[j] < j, joint types 0/1/2, axes, origins, limits."""
 
-    def __init__(self, parent, type, axis, origin, lower, upper):
+    def __init__(self, parent, type, axis, origin, lower, upper, mimic=None, mimic_mult=None, mimic_off=None):
         self.parent = _i32(parent)
         self.type = _i32(type)
         self.axis = _f64(axis).reshape(-1, 3)
@@ -116,21 +117,32 @@ class Robot:
         self.lower = _f64(lower)
         self.upper = _f64(upper)
         self.n_joints = int(self.parent.shape[0])
+        self.mimic = None if mimic is None else _i32(mimic)
+        self.mimic_mult = None if mimic is None else _f64(mimic_mult)
+        self.mimic_off = None if mimic is None else _f64(mimic_off)
         self._c = _Robot(self.n_joints, _p(self.parent), _p(self.type), _p(self.axis),
-                         _p(self.origin), _p(self.lower), _p(self.upper))
+                         _p(self.origin), _p(self.lower), _p(self.upper), _p(self.mimic), _p(self.mimic_mult),
+                         _p(self.mimic_off))
         self.n_dof = int(lib().or_n_dof(C.byref(self._c)))
 
     @classmethod
     def from_dict(cls, d):
-        return cls(d["parent"], d["type"], d["axis"], d["origin"], d["lower"], d["upper"])
+        return cls(d["parent"], d["type"], d["axis"], d["origin"], d["lower"], d["upper"], d.get("mimic"),
+                   d.get("mimic_mult"), d.get("mimic_off"))
+
+    def _own_var(self):
+        own = self.type != JOINT_FIXED
+        if self.mimic is not None:
+            own &= self.mimic < 0
+        return own
 
     @property
     def dof_lower(self):
-        return self.lower[self.type != JOINT_FIXED]
+        return self.lower[self._own_var()]
 
     @property
     def dof_upper(self):
-        return self.upper[self.type != JOINT_FIXED]
+        return self.upper[self._own_var()]
 
 
 class IkParams:

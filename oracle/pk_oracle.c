@@ -105,10 +105,29 @@ static void rodrigues(const double* a, double th, double* R) {
 /* ------------------------------------------------------------------ */
 /* Robot model (Sec. III-B)                                             */
 
+static int is_mimic(const or_robot* rb, int j) { return rb->mimic && rb->mimic[j] >= 0; }
+
 int32_t or_n_dof(const or_robot* rb) {
   int32_t n = 0;
-  for (int j = 0; j < rb->n_joints; ++j) n += rb->type[j] != OR_JOINT_FIXED;
+  for (int j = 0; j < rb->n_joints; ++j) n += rb->type[j] != OR_JOINT_FIXED && !is_mimic(rb, j);
   return n;
+}
+
+/* Variable driving joint j (-1 for fixed joints), with the joint value
+ * mult * q[var] + off. */
+static int joint_var(const or_robot* rb, int j, double* mult, double* off) {
+  *mult = 1.0;
+  *off = 0.0;
+  if (rb->type[j] == OR_JOINT_FIXED) return -1;
+  int src = j;
+  if (is_mimic(rb, j)) {
+    src = rb->mimic[j];
+    *mult = rb->mimic_mult[j];
+    *off = rb->mimic_off[j];
+  }
+  int v = 0;
+  for (int i = 0; i < src; ++i) v += rb->type[i] != OR_JOINT_FIXED && !is_mimic(rb, i);
+  return v;
 }
 
 int32_t or_n_residuals(const or_robot* rb, const or_target_spec* ts) {
@@ -120,16 +139,17 @@ int32_t or_n_residuals(const or_robot* rb, const or_target_spec* ts) {
 
 /* T_j = T_parent(j) * origin_j * X_j(q_j) for j in index order. */
 void or_fk(const or_robot* rb, const double* q, double* T_out) {
-  int v = 0;
   for (int j = 0; j < rb->n_joints; ++j) {
     double X[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
     const double* a = rb->axis + 3 * j;
+    double mult, off;
+    const int v = joint_var(rb, j, &mult, &off);
     if (rb->type[j] == OR_JOINT_REVOLUTE) {
       double R[9], z[3] = {0, 0, 0};
-      rodrigues(a, q[v++], R);
+      rodrigues(a, mult * q[v] + off, R);
       tf_make(R, z, X);
     } else if (rb->type[j] == OR_JOINT_PRISMATIC) {
-      double d = q[v++];
+      double d = mult * q[v] + off;
       X[3] = a[0] * d; X[7] = a[1] * d; X[11] = a[2] * d;
     }
     double L[12];
@@ -303,8 +323,12 @@ void or_ik_residual(const or_robot* rb, const or_ik_params* p, const or_target_s
   const int n = rb->n_joints, nd = or_n_dof(rb), m = or_n_residuals(rb, ts);
   double* T = (double*)malloc(sizeof(double) * 12 * n);
   int* var = (int*)malloc(sizeof(int) * n);
+  double* mult = (double*)malloc(sizeof(double) * n);
   or_fk(rb, q, T);
-  for (int j = 0, v = 0; j < n; ++j) var[j] = rb->type[j] == OR_JOINT_FIXED ? -1 : v++;
+  for (int j = 0; j < n; ++j) {
+    double off;
+    var[j] = joint_var(rb, j, &mult[j], &off);
+  }
   if (J) memset(J, 0, sizeof(double) * m * nd);
   int row = 0;
   for (int k = 0; k < ts->n_targets; ++k) {
@@ -338,7 +362,7 @@ void or_ik_residual(const or_robot* rb, const or_ik_params* p, const or_target_s
           for (int i = 0; i < 6; ++i) {
             double s = 0;
             for (int l = 0; l < 6; ++l) s += Jli[i * 6 + l] * eta[l];
-            J[(row + i) * nd + var[j]] = w[i] * s;
+            J[(row + i) * nd + var[j]] += mult[j] * w[i] * s;  /* a mimic joint adds to its source's column */
           }
         }
       }
@@ -360,15 +384,16 @@ void or_ik_residual(const or_robot* rb, const or_ik_params* p, const or_target_s
           } else {
             col[0] = ax[0]; col[1] = ax[1]; col[2] = ax[2];
           }
-          for (int i = 0; i < 3; ++i) J[(row + i) * nd + var[j]] = p->w_pos * col[i];
+          for (int i = 0; i < 3; ++i) J[(row + i) * nd + var[j]] += mult[j] * p->w_pos * col[i];
         }
       }
       row += 3;
     }
   }
-  /* joint limit hinge and rest pose (middle of the limits) */
+  /* joint limit hinge and rest pose (middle of the limits) of every variable,
+   * with its own joint's limits (a mimic joint's limits are not enforced) */
   for (int j = 0; j < n; ++j) {
-    if (var[j] < 0) continue;
+    if (var[j] < 0 || is_mimic(rb, j)) continue;
     const int v = var[j];
     const double lo = rb->lower[j], hi = rb->upper[j], qv = q[v];
     double h = 0, dh = 0;
@@ -383,6 +408,7 @@ void or_ik_residual(const or_robot* rb, const or_ik_params* p, const or_target_s
   }
   free(T);
   free(var);
+  free(mult);
 }
 
 void or_ik_errors(const or_robot* rb, const or_target_spec* ts, const double* targets,

@@ -15,7 +15,8 @@
  *   - A twist is [rho; omega] (translation part first).
  *   - Joint types: 0 fixed, 1 revolute, 2 prismatic.  Joint j's parent is
  *     parent[j] < j (or -1 for the base).  Movable joints own one variable
- *     each, numbered in joint order ("dof index").
+ *     each, numbered in joint order ("dof index"), except mimic joints, which
+ *     follow another joint's variable.
  *   - Target kinds: 0 full pose (6 residual rows), 1 position only (3 rows).
  */
 #ifndef PK_ORACLE_H
@@ -41,6 +42,12 @@ typedef struct {
   const double* origin;  /* [n_joints][12] parent frame -> joint frame */
   const double* lower;   /* [n_joints] (ignored for fixed joints) */
   const double* upper;   /* [n_joints] */
+  /* Mimic joints (Sec. III-B): joint j with mimic[j] = s >= 0 has no variable
+   * of its own; its value is mimic_mult[j] * q(s) + mimic_off[j].  NULL = no
+   * mimic joints. */
+  const int32_t* mimic;      /* [n_joints] source joint or -1 */
+  const double* mimic_mult;  /* [n_joints] */
+  const double* mimic_off;   /* [n_joints] */
 } or_robot;
 
 typedef struct {

@@ -48,19 +48,23 @@ class RobotSpec(dict):
     def n_joints(self):
         return len(self["parent"])
 
+    def _own_var(self):
+        own = np.asarray(self["type"]) != JOINT_FIXED
+        if self.get("mimic") is not None:
+            own &= np.asarray(self["mimic"]) < 0
+        return own
+
     @property
     def n_dof(self):
-        return int(np.sum(np.asarray(self["type"]) != JOINT_FIXED))
+        return int(np.sum(self._own_var()))
 
     @property
     def dof_lower(self):
-        t = np.asarray(self["type"])
-        return np.asarray(self["lower"])[t != JOINT_FIXED]
+        return np.asarray(self["lower"])[self._own_var()]
 
     @property
     def dof_upper(self):
-        t = np.asarray(self["type"])
-        return np.asarray(self["upper"])[t != JOINT_FIXED]
+        return np.asarray(self["upper"])[self._own_var()]
 
 
 def _finish(name, parent, types, axis, origin, lower, upper):
@@ -144,6 +148,24 @@ def hand_robot(seed: int = 102) -> tuple[RobotSpec, np.ndarray]:
     for nf in (5, 4, 4, 4, 4):
         tips.append(_add_branch(rng, wrist, nf, parent, types, axis, origin, lower, upper, 1.5))
     return _finish("hand24", parent, types, axis, origin, lower, upper), np.asarray(tips, np.int32)
+
+
+def hand_mimic_robot(seed: int = 102, mult: float = 0.8, off: float = 0.05) -> tuple[RobotSpec, np.ndarray]:
+    """The 24-joint hand with the distal joint of every finger coupled to the
+    joint before it (value = mult * q_prev + off), as hands' mimic joints are:
+    19 variables.  Returns (robot, fingertip frame indices [5])."""
+    spec, tips = hand_robot(seed)
+    n = len(spec["parent"])
+    mimic = -np.ones(n, np.int32)
+    for tip in tips:
+        distal = int(spec["parent"][tip])
+        mimic[distal] = int(spec["parent"][distal])
+    spec = RobotSpec(spec)
+    spec["name"] = "hand24_mimic"
+    spec["mimic"] = mimic
+    spec["mimic_mult"] = np.where(mimic >= 0, mult, 1.0)
+    spec["mimic_off"] = np.where(mimic >= 0, off, 0.0)
+    return spec, tips
 
 
 def humanoid_robot(seed: int = 103) -> tuple[RobotSpec, np.ndarray]:
