@@ -109,6 +109,20 @@ pk_status pk_robot_create(int32_t n_joints, const int32_t* parent, const int32_t
                           const float* axis, const float* origin, const float* lower,
                           const float* upper, const float* tool, pk_robot** out);
 void pk_robot_destroy(pk_robot* robot);
+/*
+ * Mimic joints (Sec. III-B, the coupled joints of robot hands): movable joint
+ * `joint` gives up its own variable and follows movable joint `source`'s:
+ * value = multiplier * q_source + offset.  Variables are renumbered (the
+ * movable joints that are not mimics, in joint order), so pk_robot_n_dof()
+ * drops by one; the mimic joint's own limits are not enforced (its source's
+ * are).  A source may not itself be a mimic, a mimic may not be a source, and
+ * a joint is made a mimic once.
+ * Robots with mimic joints run on the warp-per-problem path (up to 4 mimics
+ * per variable); the serial-chain kernels and trajectory optimisation refuse
+ * them (PK_ERR_UNSUPPORTED).  Synchronous (updates the device copy); call it
+ * before any solve that uses the robot.
+ */
+pk_status pk_robot_set_mimic(pk_robot* robot, int32_t joint, int32_t source, float multiplier, float offset);
 int32_t pk_robot_n_joints(const pk_robot* robot);
 int32_t pk_robot_n_dof(const pk_robot* robot);
 

@@ -498,7 +498,7 @@ __global__ void fk_kernel(const RobotDev* __restrict__ rb, int nj, int nd, int b
     rt_identity(X);
     const int t = rb->type[j];
     if (t != PK_JOINT_FIXED) {
-      const float qv = qs[(size_t)b * nd + rb->var[j]];
+      const float qv = fmaf(rb->mult[j], qs[(size_t)b * nd + rb->var[j]], rb->offs[j]);
       const float* a = rb->axis[j];
       if (t == PK_JOINT_REVOLUTE) {
         float u[3] = {a[0], a[1], a[2]}, s, c;

@@ -86,7 +86,7 @@ pk_status pcuda(cudaError_t e, const char* what) {
 }
 
 bool chain_like(const pk_robot* rb, int k, const int32_t* links) {
-  if (k != 1 || (rb->n_dof != 6 && rb->n_dof != 7)) return false;
+  if (k != 1 || (rb->n_dof != 6 && rb->n_dof != 7) || rb->has_mimic) return false;
   for (int j = 0; j < rb->n_joints; ++j)
     if (rb->parent[j] != j - 1) return false;
   for (int j = links[0] + 1; j < rb->n_joints; ++j)

@@ -46,17 +46,33 @@ bool build_tree_info(const pk_robot* rb, int k, const int32_t* links, const int3
       if (depth[j] == l) ti->order[pos++] = j;
   }
   ti->level_start[max_depth + 1] = pos;
-  for (int j = 0; j < rb->n_joints; ++j)
-    if (rb->var[j] >= 0) {
-      ti->dof_joint[rb->var[j]] = j;
-      ti->lo[rb->var[j]] = rb->lower[j];
-      ti->hi[rb->var[j]] = rb->upper[j];
+  std::vector<int> slot(rb->n_joints, -1);  // a mimic joint's index in its variable's list
+  for (int j = 0; j < rb->n_joints; ++j) {
+    const int v = rb->var[j];
+    if (v < 0) continue;
+    if (rb->mimic[j] < 0) {
+      ti->dof_joint[v] = j;
+      ti->lo[v] = rb->lower[j];
+      ti->hi[v] = rb->upper[j];
+    } else {
+      if (ti->n_mim[v] >= kTreeMaxMimic) return false;
+      slot[j] = ti->n_mim[v]++;
+      ti->mim_joint[v][slot[j]] = j;
+      ti->mim_mult[v][slot[j]] = rb->mult[j];
     }
+  }
   for (int t = 0; t < k; ++t) {
     ti->links[t] = links[t];
     ti->kinds[t] = kinds ? kinds[t] : PK_TARGET_POSE;
-    for (int j = links[t]; j >= 0; j = rb->parent[j])
-      if (rb->var[j] >= 0) ti->dof_targets[rb->var[j]] |= 1u << t;
+    for (int j = links[t]; j >= 0; j = rb->parent[j]) {
+      const int v = rb->var[j];
+      if (v < 0) continue;
+      ti->dof_targets[v] |= 1u << t;
+      if (rb->mimic[j] < 0)
+        ti->own_targets[v] |= 1u << t;
+      else
+        ti->mim_targets[v][slot[j]] |= 1u << t;
+    }
   }
   return true;
 }

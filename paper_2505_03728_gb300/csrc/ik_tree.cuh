@@ -19,6 +19,7 @@ namespace pk {
 
 constexpr int kTreeMaxDof = 32;
 constexpr int kTreeMaxTargets = 8;
+constexpr int kTreeMaxMimic = 4;  // mimic joints per variable
 constexpr unsigned kTreeFull = 0xffffffffu;
 
 // Per-robot, per-target-set constants (global memory, built on the host).
@@ -28,7 +29,13 @@ struct TreeInfo {
   int32_t level_start[kMaxJoints + 1];  // joints of depth level l: order[level_start[l] .. level_start[l+1])
   int32_t order[kMaxJoints];
   int32_t dof_joint[kTreeMaxDof];   // joint index of variable i
-  uint32_t dof_targets[kTreeMaxDof];  // bit t: variable i moves target t's frame
+  uint32_t dof_targets[kTreeMaxDof];  // bit t: variable i moves target t's frame (any of its joints)
+  uint32_t own_targets[kTreeMaxDof];  // bit t: variable i's own joint moves target t
+  // mimic joints following variable i (Sec. III-B): joint, multiplier, targets moved
+  int32_t n_mim[kTreeMaxDof];
+  int32_t mim_joint[kTreeMaxDof][kTreeMaxMimic];
+  float mim_mult[kTreeMaxDof][kTreeMaxMimic];
+  uint32_t mim_targets[kTreeMaxDof][kTreeMaxMimic];
   int32_t links[kTreeMaxTargets];
   int32_t kinds[kTreeMaxTargets];
   float lo[kTreeMaxDof], hi[kTreeMaxDof];
@@ -68,7 +75,7 @@ __device__ __forceinline__ void tree_fk(const RobotDev* __restrict__ rb, const T
       rt_identity(X);
       const int t = rb->type[j];
       if (t != PK_JOINT_FIXED) {
-        const float qv = sm.q[rb->var[j]];
+        const float qv = fmaf(rb->mult[j], sm.q[rb->var[j]], rb->offs[j]);
         const float* a = rb->axis[j];
         if (t == PK_JOINT_REVOLUTE) {
           float u[3] = {a[0], a[1], a[2]}, s, c;
@@ -134,6 +141,54 @@ __device__ __forceinline__ float tree_eval(const RobotDev* __restrict__ rb, cons
   return 0.5f * warp_sum(acc);
 }
 
+// Adds scale x the weighted Jacobian column of joint jj for target k (pose:
+// Jl^-1 Ad(T_target^-1) xi_j; position: w x (p - p_j)) to col[6].
+__device__ __forceinline__ void tree_joint_col(const RobotDev* __restrict__ rb, const TreeWarpSmem& sm, int k,
+                                               bool pose, const LmParams& lp, int jj, float scale, float* col) {
+  Rt Tj, Ti;
+  rt_load(sm.frames[jj], Tj);
+  rt_load(sm.Ti[k], Ti);
+  float wj[3], pj[3] = {Tj.t[0], Tj.t[1], Tj.t[2]};
+  mat_vec(Tj.r, rb->axis[jj], wj);
+  const bool prism = rb->type[jj] == PK_JOINT_PRISMATIC;
+  // joint axis and origin in the target frame
+  float u[3], p[3];
+  mat_vec(Ti.r, wj, u);
+  mat_vec(Ti.r, pj, p);
+  p[0] += Ti.t[0]; p[1] += Ti.t[1]; p[2] += Ti.t[2];
+  if (pose) {
+    float A[9], B[9];
+    se3_jlinv_blocks(sm.xi[k], sm.xi[k] + 3, sm.th[k], A, B);
+    float top[3], bot[3];
+    if (prism) {
+      mat_vec(A, u, top);
+      bot[0] = bot[1] = bot[2] = 0.f;
+    } else {
+      float v[3], t1[3], t2[3];
+      cross3(p, u, v);
+      mat_vec(A, v, t1);
+      mat_vec(B, u, t2);
+      mat_vec(A, u, bot);
+      top[0] = t1[0] + t2[0]; top[1] = t1[1] + t2[1]; top[2] = t1[2] + t2[2];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      col[i] = fmaf(scale, lp.w_pos * top[i], col[i]);
+      col[3 + i] = fmaf(scale, lp.w_rot * bot[i], col[3 + i]);
+    }
+  } else {
+    float c[3];
+    if (prism) {
+      c[0] = u[0]; c[1] = u[1]; c[2] = u[2];
+    } else {
+      float d[3] = {sm.xi[k][0] - p[0], sm.xi[k][1] - p[1], sm.xi[k][2] - p[2]};
+      cross3(u, d, c);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) col[i] = fmaf(scale, lp.w_pos * c[i], col[i]);
+  }
+}
+
 // Row `lane` of J^T J (in Arow[0..N)) and entry g of J^T r at the configuration
 // whose frames and residuals sm holds.
 template <int N>
@@ -144,59 +199,14 @@ __device__ __forceinline__ void tree_normal(const RobotDev* __restrict__ rb, con
   for (int j = 0; j < N; ++j) Arow[j] = 0.f;
   g = 0.f;
   const bool mine = lane < ti.n_dof;
-  int jj = 0;
-  float pj[3] = {0.f, 0.f, 0.f}, wj[3] = {0.f, 0.f, 0.f};
-  bool prism = false;
-  if (mine) {
-    jj = ti.dof_joint[lane];
-    Rt Tj;
-    rt_load(sm.frames[jj], Tj);
-    mat_vec(Tj.r, rb->axis[jj], wj);
-    pj[0] = Tj.t[0]; pj[1] = Tj.t[1]; pj[2] = Tj.t[2];
-    prism = rb->type[jj] == PK_JOINT_PRISMATIC;
-  }
   for (int k = 0; k < ti.k; ++k) {
     const bool pose = ti.kinds[k] == PK_TARGET_POSE;
     float col[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (mine && (ti.dof_targets[lane] >> k & 1u)) {
-      Rt Ti;
-      rt_load(sm.Ti[k], Ti);
-      // joint axis and origin in the target frame
-      float u[3], p[3];
-      mat_vec(Ti.r, wj, u);
-      mat_vec(Ti.r, pj, p);
-      p[0] += Ti.t[0]; p[1] += Ti.t[1]; p[2] += Ti.t[2];
-      if (pose) {
-        float A[9], B[9];
-        se3_jlinv_blocks(sm.xi[k], sm.xi[k] + 3, sm.th[k], A, B);
-        float top[3], bot[3];
-        if (prism) {
-          mat_vec(A, u, top);
-          bot[0] = bot[1] = bot[2] = 0.f;
-        } else {
-          float v[3], t1[3], t2[3];
-          cross3(p, u, v);
-          mat_vec(A, v, t1);
-          mat_vec(B, u, t2);
-          mat_vec(A, u, bot);
-          top[0] = t1[0] + t2[0]; top[1] = t1[1] + t2[1]; top[2] = t1[2] + t2[2];
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          col[i] = lp.w_pos * top[i];
-          col[3 + i] = lp.w_rot * bot[i];
-        }
-      } else {
-        float c[3];
-        if (prism) {
-          c[0] = u[0]; c[1] = u[1]; c[2] = u[2];
-        } else {
-          float d[3] = {sm.xi[k][0] - p[0], sm.xi[k][1] - p[1], sm.xi[k][2] - p[2]};
-          cross3(u, d, c);
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) col[i] = lp.w_pos * c[i];
-      }
+      if (ti.own_targets[lane] >> k & 1u) tree_joint_col(rb, sm, k, pose, lp, ti.dof_joint[lane], 1.f, col);
+      for (int m = 0; m < ti.n_mim[lane]; ++m)  // a mimic joint adds to its source's column
+        if (ti.mim_targets[lane][m] >> k & 1u)
+          tree_joint_col(rb, sm, k, pose, lp, ti.mim_joint[lane][m], ti.mim_mult[lane][m], col);
     }
 #pragma unroll
     for (int r = 0; r < 6; ++r) sm.Jk[r][lane] = col[r];

@@ -95,6 +95,7 @@ pk::LmParams lm_params(const pk_ik_params* p, bool pos_only) {
 
 // Fold a serial chain ending at frame `link` into the kernel's canonical form.
 pk_status fold_chain(const pk_robot* rb, int link, pk::ChainHost* ch) {
+  if (rb->has_mimic) return fail(PK_ERR_UNSUPPORTED, "chains with mimic joints run on the tree path");
   for (int j = 0; j < rb->n_joints; ++j)
     if (rb->parent[j] != j - 1)
       return fail(PK_ERR_UNSUPPORTED, "the fused IK kernel needs a serial chain (parent[j] == j-1)");
@@ -152,7 +153,7 @@ pk_status check_targets(const pk_robot* rb, int32_t k, const int32_t* links, con
 
 // True when the thread-per-problem chain kernel serves this (robot, target).
 bool chain_eligible(const pk_robot* rb, int32_t k, const int32_t* links) {
-  if (k != 1 || rb->n_dof < 1 || rb->n_dof > pk::kMaxChainDof) return false;
+  if (k != 1 || rb->n_dof < 1 || rb->n_dof > pk::kMaxChainDof || rb->has_mimic) return false;
   for (int j = 0; j < rb->n_joints; ++j)
     if (rb->parent[j] != j - 1) return false;
   for (int j = links[0] + 1; j < rb->n_joints; ++j)
@@ -368,6 +369,27 @@ void pk_ik_params_default(pk_ik_params* p) {
 
 const char* pk_last_error(void) { return g_last_error.c_str(); }
 
+// Device copy of the robot (RobotDev) from the host description.
+static cudaError_t upload_robot(const pk_robot* rb) {
+  pk::RobotDev h;
+  memset(&h, 0, sizeof h);
+  h.n_joints = rb->n_joints;
+  h.n_dof = rb->n_dof;
+  for (int j = 0; j < rb->n_joints; ++j) {
+    h.parent[j] = rb->parent[j];
+    h.type[j] = rb->type[j];
+    h.var[j] = rb->var[j];
+    memcpy(h.axis[j], &rb->axis[3 * j], 3 * sizeof(float));
+    memcpy(h.origin[j], &rb->origin[12 * j], 12 * sizeof(float));
+    h.lower[j] = rb->lower[j];
+    h.upper[j] = rb->upper[j];
+    h.mult[j] = rb->mult[j];
+    h.offs[j] = rb->offs[j];
+    h.own[j] = rb->type[j] != PK_JOINT_FIXED && rb->mimic[j] < 0;
+  }
+  return cudaMemcpy(rb->d_blob, &h, sizeof h, cudaMemcpyHostToDevice);
+}
+
 pk_status pk_robot_create(int32_t n_joints, const int32_t* parent, const int32_t* type,
                           const float* axis, const float* origin, const float* lower,
                           const float* upper, const float* tool, pk_robot** out) {
@@ -438,27 +460,16 @@ pk_status pk_robot_create(int32_t n_joints, const int32_t* parent, const int32_t
     rb->upper[j] = hi;
   }
   rb->n_dof = nd;
-
-  pk::RobotDev h;
-  memset(&h, 0, sizeof h);
-  h.n_joints = total;
-  h.n_dof = nd;
-  for (int j = 0; j < total; ++j) {
-    h.parent[j] = rb->parent[j];
-    h.type[j] = rb->type[j];
-    h.var[j] = rb->var[j];
-    memcpy(h.axis[j], &rb->axis[3 * j], 3 * sizeof(float));
-    memcpy(h.origin[j], &rb->origin[12 * j], 12 * sizeof(float));
-    h.lower[j] = rb->lower[j];
-    h.upper[j] = rb->upper[j];
-  }
+  rb->mimic.assign(total, -1);
+  rb->mult.assign(total, 1.f);
+  rb->offs.assign(total, 0.f);
   cudaGetDevice(&rb->device);
-  cudaError_t e = cudaMalloc(&rb->d_blob, sizeof h);
+  cudaError_t e = cudaMalloc(&rb->d_blob, sizeof(pk::RobotDev));
   if (e != cudaSuccess) {
     delete rb;
     return cuda_fail(e, "cudaMalloc(robot)");
   }
-  e = cudaMemcpy(rb->d_blob, &h, sizeof h, cudaMemcpyHostToDevice);
+  e = upload_robot(rb);
   if (e != cudaSuccess) {
     cudaFree(rb->d_blob);
     delete rb;
@@ -466,6 +477,33 @@ pk_status pk_robot_create(int32_t n_joints, const int32_t* parent, const int32_t
   }
   *out = rb;
   return PK_OK;
+}
+
+pk_status pk_robot_set_mimic(pk_robot* rb, int32_t joint, int32_t source, float multiplier, float offset) {
+  if (!rb) return fail(PK_ERR_INVALID_ARG, "robot is NULL");
+  if (joint < 0 || joint >= rb->n_joints || source < 0 || source >= rb->n_joints || joint == source)
+    return fail(PK_ERR_INVALID_ARG, "joint and source must be distinct joints of the robot");
+  if (rb->type[joint] == PK_JOINT_FIXED || rb->type[source] == PK_JOINT_FIXED)
+    return fail(PK_ERR_INVALID_ARG, "mimic and source joints must be movable");
+  if (rb->mimic[source] >= 0) return fail(PK_ERR_INVALID_ARG, "the source joint is itself a mimic joint");
+  if (rb->mimic[joint] >= 0) return fail(PK_ERR_INVALID_ARG, "the joint is already a mimic joint");
+  for (int j = 0; j < rb->n_joints; ++j)
+    if (rb->mimic[j] == joint) return fail(PK_ERR_INVALID_ARG, "another joint mimics this joint");
+  if (!isfinite(multiplier) || !isfinite(offset))
+    return fail(PK_ERR_INVALID_ARG, "multiplier and offset must be finite");
+  rb->mimic[joint] = source;
+  rb->mult[joint] = multiplier;
+  rb->offs[joint] = offset;
+  rb->has_mimic = true;
+  // renumber: variables belong to the movable joints that are not mimics
+  int nd = 0;
+  for (int j = 0; j < rb->n_joints; ++j)
+    rb->var[j] = (rb->type[j] != PK_JOINT_FIXED && rb->mimic[j] < 0) ? nd++ : -1;
+  for (int j = 0; j < rb->n_joints; ++j)
+    if (rb->mimic[j] >= 0) rb->var[j] = rb->var[rb->mimic[j]];
+  rb->n_dof = nd;
+  cudaError_t e = upload_robot(rb);
+  return e == cudaSuccess ? PK_OK : cuda_fail(e, "pk_robot_set_mimic");
 }
 
 void pk_robot_destroy(pk_robot* rb) {

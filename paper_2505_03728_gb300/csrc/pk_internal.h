@@ -12,6 +12,9 @@ struct pk_robot {
   int32_t n_joints = 0, n_dof = 0;
   std::vector<int32_t> parent, type, var;  // var[j]: variable index or -1
   std::vector<float> axis, origin, lower, upper;
+  std::vector<int32_t> mimic;     // source joint of a mimic joint, else -1
+  std::vector<float> mult, offs;  // joint value = mult * q[var] + offs
+  bool has_mimic = false;
   // Device copy for the generic (tree) kernels, see RobotDev.
   void* d_blob = nullptr;
   int device = 0;
@@ -32,6 +35,8 @@ struct RobotDev {
   float axis[kMaxJoints][3];
   float origin[kMaxJoints][12];
   float lower[kMaxJoints], upper[kMaxJoints];
+  float mult[kMaxJoints], offs[kMaxJoints];  // joint value = mult * q[var] + offs (mimic joints)
+  int32_t own[kMaxJoints];                   // 1: the joint owns its variable (not a mimic)
 };
 
 // Serial chain folded so that every fixed joint is merged into the next

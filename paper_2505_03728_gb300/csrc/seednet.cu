@@ -196,7 +196,7 @@ __device__ void tree_fk_link(const pk::RobotDev* __restrict__ rb, const float* q
     pk::rt_identity(X);
     const int t = rb->type[j];
     if (t != PK_JOINT_FIXED) {
-      const float qv = q[rb->var[j]];
+      const float qv = fmaf(rb->mult[j], q[rb->var[j]], rb->offs[j]);
       const float* a = rb->axis[j];
       if (t == PK_JOINT_REVOLUTE) {
         float u[3] = {a[0], a[1], a[2]}, s, c;
@@ -677,7 +677,7 @@ pk_status pk_seednet_create(const pk_robot* rb, int32_t k, const int32_t* target
   }
   s->n_master = off;
   for (int j = 0; j < rb->n_joints; ++j)
-    if (rb->var[j] >= 0) {
+    if (rb->var[j] >= 0 && rb->mimic[j] < 0) {  // the variables' own joints
       s->lo.push_back(rb->lower[j]);
       s->hi.push_back(rb->upper[j]);
     }

@@ -85,6 +85,7 @@ _SIGNATURES = {
     "pk_robot_destroy": (None, [_vp]),
     "pk_robot_n_joints": (_i32, [_vp]),
     "pk_robot_n_dof": (_i32, [_vp]),
+    "pk_robot_set_mimic": (_i32, [_vp, _i32, _i32, C.c_float, C.c_float]),
     "pk_fk": (_i32, [_vp, _i32, _vp, _vp, _vp]),
     "pk_ik_residual": (_i32, [_vp, C.POINTER(pk_ik_params), _i32, _i32p, _i32p, _i32, _vp, _vp, _vp,
                               _vp, _vp]),
@@ -210,10 +211,21 @@ class Robot:
         self.n_joints = lib().pk_robot_n_joints(h)
         self.n_dof = lib().pk_robot_n_dof(h)
 
+    def set_mimic(self, joint: int, source: int, multiplier: float = 1.0, offset: float = 0.0):
+        """Make `joint` follow `source`'s variable: value = multiplier * q_source + offset."""
+        _check(lib().pk_robot_set_mimic(self.handle, int(joint), int(source), C.c_float(multiplier),
+                                        C.c_float(offset)))
+        self.n_dof = lib().pk_robot_n_dof(self.handle)
+
     @classmethod
     def from_spec(cls, spec):
-        return cls(spec["parent"], spec["type"], spec["axis"], spec["origin"], spec["lower"],
-                   spec["upper"])
+        r = cls(spec["parent"], spec["type"], spec["axis"], spec["origin"], spec["lower"], spec["upper"])
+        mimic = spec.get("mimic")
+        if mimic is not None:
+            for j, s in enumerate(np.asarray(mimic)):
+                if s >= 0:
+                    r.set_mimic(j, int(s), float(spec["mimic_mult"][j]), float(spec["mimic_off"][j]))
+        return r
 
     def __del__(self):
         h = getattr(self, "handle", None)
