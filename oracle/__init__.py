@@ -54,14 +54,16 @@ _f64p = C.POINTER(C.c_double)
 class _Robot(C.Structure):
     _fields_ = [("n_joints", C.c_int32), ("parent", _i32p), ("type", _i32p), ("axis", _f64p),
                 ("origin", _f64p), ("lower", _f64p), ("upper", _f64p), ("mimic", _i32p),
-                ("mimic_mult", _f64p), ("mimic_off", _f64p)]
+                ("mimic_mult", _f64p), ("mimic_off", _f64p), ("n_spheres", C.c_int32), ("sph_joint", _i32p),
+                ("sph_centre", _f64p), ("sph_radius", _f64p), ("n_pairs", C.c_int32), ("pairs", _i32p)]
 
 
 class _IkParams(C.Structure):
     _fields_ = [("w_pos", C.c_double), ("w_rot", C.c_double), ("w_limit", C.c_double),
                 ("w_rest", C.c_double), ("lambda0", C.c_double), ("lambda_min", C.c_double),
                 ("lambda_max", C.c_double), ("nu", C.c_double), ("tol_pos", C.c_double),
-                ("tol_rot", C.c_double), ("max_iters", C.c_int32), ("early_exit", C.c_int32)]
+                ("tol_rot", C.c_double), ("max_iters", C.c_int32), ("early_exit", C.c_int32),
+                ("w_self", C.c_double), ("eta_self", C.c_double)]
 
 
 class _TargetSpec(C.Structure):
@@ -109,7 +111,8 @@ def _p(a):
 class Robot:
     """A kinematic tree: parent[j] < j, joint types 0/1/2, axes, origins, limits."""
 
-    def __init__(self, parent, type, axis, origin, lower, upper, mimic=None, mimic_mult=None, mimic_off=None):
+    def __init__(self, parent, type, axis, origin, lower, upper, mimic=None, mimic_mult=None, mimic_off=None,
+                 spheres=None):
         self.parent = _i32(parent)
         self.type = _i32(type)
         self.axis = _f64(axis).reshape(-1, 3)
@@ -120,15 +123,26 @@ class Robot:
         self.mimic = None if mimic is None else _i32(mimic)
         self.mimic_mult = None if mimic is None else _f64(mimic_mult)
         self.mimic_off = None if mimic is None else _f64(mimic_off)
+        # spheres: dict(joint [S], centre [S][3], radius [S], pairs [P][2]) or None
+        self.sph_joint = self.sph_centre = self.sph_radius = self.pairs = None
+        n_s = n_p = 0
+        if spheres is not None:
+            self.sph_joint = _i32(spheres["joint"])
+            self.sph_centre = _f64(spheres["centre"]).reshape(-1, 3)
+            self.sph_radius = _f64(spheres["radius"])
+            self.pairs = _i32(spheres["pairs"]).reshape(-1, 2)
+            n_s, n_p = int(self.sph_joint.shape[0]), int(self.pairs.shape[0])
+        self.n_pairs = n_p
         self._c = _Robot(self.n_joints, _p(self.parent), _p(self.type), _p(self.axis),
                          _p(self.origin), _p(self.lower), _p(self.upper), _p(self.mimic), _p(self.mimic_mult),
-                         _p(self.mimic_off))
+                         _p(self.mimic_off), n_s, _p(self.sph_joint), _p(self.sph_centre), _p(self.sph_radius),
+                         n_p, _p(self.pairs))
         self.n_dof = int(lib().or_n_dof(C.byref(self._c)))
 
     @classmethod
     def from_dict(cls, d):
         return cls(d["parent"], d["type"], d["axis"], d["origin"], d["lower"], d["upper"], d.get("mimic"),
-                   d.get("mimic_mult"), d.get("mimic_off"))
+                   d.get("mimic_mult"), d.get("mimic_off"), d.get("spheres"))
 
     def _own_var(self):
         own = self.type != JOINT_FIXED
@@ -148,9 +162,9 @@ class Robot:
 class IkParams:
     def __init__(self, w_pos=1.0, w_rot=0.5, w_limit=10.0, w_rest=1e-3, lambda0=1e-2,
                  lambda_min=1e-10, lambda_max=1e10, nu=2.0, tol_pos=1e-3,
-                 tol_rot=np.deg2rad(0.5), max_iters=30, early_exit=0):
+                 tol_rot=np.deg2rad(0.5), max_iters=30, early_exit=0, w_self=0.0, eta_self=0.02):
         self._c = _IkParams(w_pos, w_rot, w_limit, w_rest, lambda0, lambda_min, lambda_max, nu,
-                            tol_pos, tol_rot, max_iters, early_exit)
+                            tol_pos, tol_rot, max_iters, early_exit, w_self, eta_self)
 
     def __getattr__(self, k):
         return getattr(self.__dict__["_c"], k)

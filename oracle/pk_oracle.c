@@ -134,8 +134,11 @@ int32_t or_n_residuals(const or_robot* rb, const or_target_spec* ts) {
   int32_t m = 0;
   for (int k = 0; k < ts->n_targets; ++k)
     m += (ts->kinds && ts->kinds[k] == OR_TARGET_POSITION) ? 3 : 6;
-  return m + 2 * or_n_dof(rb);
+  return m + 2 * or_n_dof(rb) + rb->n_pairs;
 }
+
+/* Eq. 1 activation (trajopt_oracle.c). */
+double or_coll_activation(double d, double eta, double* df);
 
 /* T_j = T_parent(j) * origin_j * X_j(q_j) for j in index order. */
 void or_fk(const or_robot* rb, const double* q, double* T_out) {
@@ -388,6 +391,50 @@ void or_ik_residual(const or_robot* rb, const or_ik_params* p, const or_target_s
         }
       }
       row += 3;
+    }
+  }
+  /* self collision (Sec. III-C, Eq. 1): per sphere pair, w_self f(d, eta)
+   * with d = |c_a - c_b| - r_a - r_b and the sphere centres moving with
+   * their frames */
+  const int prow = m - rb->n_pairs;
+  for (int pidx = 0; pidx < rb->n_pairs; ++pidx) {
+    const int sa = rb->pairs[2 * pidx], sb = rb->pairs[2 * pidx + 1];
+    const int ja = rb->sph_joint[sa], jb = rb->sph_joint[sb];
+    double ca[3], cb[3], R[9], t[3];
+    tf_rot(T + 12 * ja, R); tf_trans(T + 12 * ja, t);
+    m3_vec(R, rb->sph_centre + 3 * sa, ca);
+    for (int i = 0; i < 3; ++i) ca[i] += t[i];
+    tf_rot(T + 12 * jb, R); tf_trans(T + 12 * jb, t);
+    m3_vec(R, rb->sph_centre + 3 * sb, cb);
+    for (int i = 0; i < 3; ++i) cb[i] += t[i];
+    double diff[3] = {ca[0] - cb[0], ca[1] - cb[1], ca[2] - cb[2]};
+    const double dist = v3_norm(diff);
+    const double d = dist - rb->sph_radius[sa] - rb->sph_radius[sb];
+    double df = 0;
+    const double f = or_coll_activation(d, p->eta_self, &df);
+    r[prow + pidx] = p->w_self * f;
+    if (J && dist > 1e-12) {
+      double nh[3] = {diff[0] / dist, diff[1] / dist, diff[2] / dist};
+      for (int j = 0; j < n; ++j) {
+        if (var[j] < 0) continue;
+        const int ina = is_ancestor_or_self(rb, j, ja), inb = is_ancestor_or_self(rb, j, jb);
+        if (!ina && !inb) continue;
+        double Rj[9], pj[3], ax[3], va[3] = {0, 0, 0}, vb[3] = {0, 0, 0};
+        tf_rot(T + 12 * j, Rj); tf_trans(T + 12 * j, pj);
+        m3_vec(Rj, rb->axis + 3 * j, ax);
+        /* velocity of a point x moved by joint j: revolute w x (x - p_j), prismatic w */
+        if (rb->type[j] == OR_JOINT_REVOLUTE) {
+          double da[3] = {ca[0] - pj[0], ca[1] - pj[1], ca[2] - pj[2]};
+          double db[3] = {cb[0] - pj[0], cb[1] - pj[1], cb[2] - pj[2]};
+          if (ina) v3_cross(ax, da, va);
+          if (inb) v3_cross(ax, db, vb);
+        } else {
+          if (ina) { va[0] = ax[0]; va[1] = ax[1]; va[2] = ax[2]; }
+          if (inb) { vb[0] = ax[0]; vb[1] = ax[1]; vb[2] = ax[2]; }
+        }
+        const double dd = nh[0] * (va[0] - vb[0]) + nh[1] * (va[1] - vb[1]) + nh[2] * (va[2] - vb[2]);
+        J[(prow + pidx) * nd + var[j]] += mult[j] * p->w_self * df * dd;
+      }
     }
   }
   /* joint limit hinge and rest pose (middle of the limits) of every variable,

@@ -18,6 +18,8 @@
  *     each, numbered in joint order ("dof index"), except mimic joints, which
  *     follow another joint's variable.
  *   - Target kinds: 0 full pose (6 residual rows), 1 position only (3 rows).
+ *   - Residual rows: the targets' rows, then one limit-hinge and one rest row per
+ *     variable, then one self-collision row per sphere pair.
  */
 #ifndef PK_ORACLE_H
 #define PK_ORACLE_H
@@ -48,6 +50,14 @@ typedef struct {
   const int32_t* mimic;      /* [n_joints] source joint or -1 */
   const double* mimic_mult;  /* [n_joints] */
   const double* mimic_off;   /* [n_joints] */
+  /* Self-collision model (Sec. III-C): spheres riding on joint frames and the
+   * sphere pairs whose signed distance enters the self-collision cost. */
+  int32_t n_spheres;
+  const int32_t* sph_joint;   /* [n_spheres] frame each sphere rides on */
+  const double* sph_centre;   /* [n_spheres][3] in that frame */
+  const double* sph_radius;   /* [n_spheres] */
+  int32_t n_pairs;
+  const int32_t* pairs;       /* [n_pairs][2] sphere indices */
 } or_robot;
 
 typedef struct {
@@ -57,6 +67,7 @@ typedef struct {
   double tol_pos, tol_rot; /* success thresholds: metres, radians */
   int32_t max_iters;
   int32_t early_exit;      /* 1: stop once the tolerances are met */
+  double w_self, eta_self; /* self-collision weight and buffer distance (Eq. 1) */
 } or_ik_params;
 
 typedef struct {

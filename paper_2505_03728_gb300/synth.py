@@ -168,6 +168,46 @@ def hand_mimic_robot(seed: int = 102, mult: float = 0.8, off: float = 0.05) -> t
     return spec, tips
 
 
+def hand_collision_spheres(spec: RobotSpec, tips, radius: float = 0.012) -> dict:
+    """Self-collision model of a hand: one sphere per finger link, on the
+    link's joint frame at the midpoint towards the next joint, and the pairs of
+    same-depth links of neighbouring fingers.  Returns dict(joint, centre,
+    radius, pairs)."""
+    parent = np.asarray(spec["parent"])
+    origin = np.asarray(spec["origin"]).reshape(-1, 12)
+    types = np.asarray(spec["type"])
+    fingers = []
+    for tip in tips:
+        chain = []
+        j = int(tip)
+        while parent[j] >= 0 and not _branch_point(parent, int(parent[j])):
+            chain.append(j)
+            j = int(parent[j])
+        chain.append(j)
+        fingers.append(chain[::-1])  # proximal first, ending at the tip frame
+    joint, centre, rad, index = [], [], [], []
+    for chain in fingers:
+        ids = []
+        for a, b in zip(chain[:-1], chain[1:]):
+            if types[a] == JOINT_FIXED:
+                continue
+            ids.append(len(joint))
+            joint.append(a)
+            centre.append(0.5 * origin[b, [3, 7, 11]])
+            rad.append(radius)
+        index.append(ids)
+    pairs = []
+    for f in range(len(index) - 1):
+        for l in range(min(len(index[f]), len(index[f + 1]))):
+            pairs.append((index[f][l], index[f + 1][l]))
+    return dict(joint=np.asarray(joint, np.int32), centre=np.asarray(centre), radius=np.asarray(rad),
+                pairs=np.asarray(pairs, np.int32))
+
+
+def _branch_point(parent, j):
+    return int(np.sum(parent == j)) > 1
+
+
 def humanoid_robot(seed: int = 103) -> tuple[RobotSpec, np.ndarray]:
     """30-joint humanoid-like tree; returns (robot, end frames [6]:
     left hand, right hand, left foot, right foot, head, torso)."""
