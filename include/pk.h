@@ -81,6 +81,8 @@ typedef struct {
   int32_t early_exit;    /* 1: a seed stops as soon as it meets the tolerances  */
   int32_t cancel_siblings; /* 1: all seeds of a target stop once one converged  */
   int32_t reserved;      /* must be 0                                           */
+  float w_self;          /* self-collision weight (Sec. III-C; 0 = off, default)  */
+  float eta_self;        /* its buffer distance eta of Eq. 1, metres (0.02)      */
 } pk_ik_params;
 
 /* Fills *p with the defaults listed above (max_iters 50, early_exit 1,
@@ -123,6 +125,19 @@ void pk_robot_destroy(pk_robot* robot);
  * before any solve that uses the robot.
  */
 pk_status pk_robot_set_mimic(pk_robot* robot, int32_t joint, int32_t source, float multiplier, float offset);
+/*
+ * Self-collision model (Sec. III-C): spheres riding on joint frames and the
+ * sphere pairs that must stay apart.  With params->w_self > 0, every pair adds
+ * the residual w_self f(d, eta_self) of Eq. 1, d = |c_a - c_b| - r_a - r_b
+ * (rows after the limit and rest rows), and the solve runs on the
+ * warp-per-problem path.
+ *   n_spheres 0..64: joint [n] (frame each sphere rides on), centre [n][3]
+ *   (in that frame), radius [n] (>= 0); n_pairs 0..64: pairs [n_pairs][2]
+ *   (distinct sphere indices).  Host pointers, copied; replaces any earlier
+ *   model; synchronous.
+ */
+pk_status pk_robot_set_spheres(pk_robot* robot, int32_t n_spheres, const int32_t* joint, const float* centre,
+                               const float* radius, int32_t n_pairs, const int32_t* pairs);
 int32_t pk_robot_n_joints(const pk_robot* robot);
 int32_t pk_robot_n_dof(const pk_robot* robot);
 

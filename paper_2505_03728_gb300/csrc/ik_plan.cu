@@ -101,6 +101,8 @@ pk::LmParams plan_lm(const pk_ik_params* p) {
   l.tol_pos = p->tol_pos; l.tol_rot = p->tol_rot;
   l.max_iters = p->max_iters; l.early_exit = p->early_exit != 0; l.cancel = p->cancel_siblings != 0;
   l.pos_only = 0;
+  l.w_self = p->w_self;
+  l.eta_self = p->eta_self;
   return l;
 }
 
@@ -269,7 +271,7 @@ pk_status pk_ik_plan_create(const pk_ik_params* params, int32_t n_sets, const pk
     ps.err_out = s.d_err_out;
     ps.iters_out = s.d_iters_out;
     ps.status_out = s.d_status_out;
-    ps.chain_ok = chain_like(s.robot, s.k, s.target_links);
+    ps.chain_ok = chain_like(s.robot, s.k, s.target_links) && !(params->w_self > 0.f && s.robot->n_pairs > 0);
     ps.pos_only = ps.chain_ok && ps.kinds[0] == PK_TARGET_POSITION;
     if (ps.chain_ok) ps.chain_ok = pk::fold_chain_quiet(s.robot, s.target_links[0], &ps.ch);
     if (!pk::build_tree_info(s.robot, s.k, ps.links.data(), ps.kinds.data(), &ps.ti)) {

@@ -51,6 +51,10 @@ struct TreeWarpSmem {
   float q[kTreeMaxDof];           // configuration being evaluated
   float L[kTreeMaxDof][kTreeMaxDof + 1];  // Cholesky factor, row i by lane i (padded rows)
   float dinv[kTreeMaxDof];        // reciprocal diagonal of L
+  // self-collision pairs of the candidate: residual w f(d), slope w f'(d),
+  // unit direction c_a - c_b and the two sphere centres (world)
+  float pr[kMaxPairs], ps[kMaxPairs];
+  float pn[kMaxPairs][3], pca[kMaxPairs][3], pcb[kMaxPairs][3];
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -134,6 +138,44 @@ __device__ __forceinline__ float tree_eval(const RobotDev* __restrict__ rb, cons
     const float h = fmaxf(0.f, q - ti.hi[lane]) + fmaxf(0.f, ti.lo[lane] - q);
     const float d = q - 0.5f * (ti.lo[lane] + ti.hi[lane]);
     acc = fmaf(lp.w_limit * lp.w_limit, h * h, fmaf(lp.w_rest * lp.w_rest, d * d, acc));
+  }
+  if (lp.w_self > 0.f) {
+    // self collision (Sec. III-C, Eq. 1): one row per sphere pair
+    for (int p = lane; p < rb->n_pairs; p += 32) {
+      const int sa = rb->pair[p][0], sb = rb->pair[p][1];
+      float ca[3], cb[3];
+      Rt Ta, Tb;
+      rt_load(sm.frames[rb->sph_joint[sa]], Ta);
+      rt_load(sm.frames[rb->sph_joint[sb]], Tb);
+      mat_vec(Ta.r, rb->sph[sa], ca);
+      mat_vec(Tb.r, rb->sph[sb], cb);
+      float diff[3], dist2 = 0.f;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        ca[i] += Ta.t[i];
+        cb[i] += Tb.t[i];
+        diff[i] = ca[i] - cb[i];
+        dist2 = fmaf(diff[i], diff[i], dist2);
+      }
+      const float dist = sqrtf(dist2);
+      const float d = dist - rb->sph[sa][3] - rb->sph[sb][3];
+      const float eta = lp.eta_self;
+      float f, df;
+      if (d <= 0.f) { f = 0.5f * eta - d; df = -1.f; }
+      else if (d < eta) { f = 0.5f / eta * (eta - d) * (eta - d); df = -(eta - d) / eta; }
+      else { f = 0.f; df = 0.f; }
+      const float r = lp.w_self * f;
+      sm.pr[p] = r;
+      sm.ps[p] = dist > 1e-12f ? lp.w_self * df : 0.f;
+      const float inv = dist > 1e-12f ? 1.f / dist : 0.f;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        sm.pn[p][i] = diff[i] * inv;
+        sm.pca[p][i] = ca[i];
+        sm.pcb[p][i] = cb[i];
+      }
+      acc = fmaf(r, r, acc);
+    }
   }
   pe = warp_max(mpe);
   re = warp_max(mre);
@@ -219,6 +261,59 @@ __device__ __forceinline__ void tree_normal(const RobotDev* __restrict__ rb, con
       for (int j = 0; j < N; ++j) Arow[j] = fmaf(col[r], sm.Jk[r][j], Arow[j]);
     }
     __syncwarp();
+  }
+  if (lp.w_self > 0.f) {
+    // self-collision rows, six at a time through sm.Jk
+    for (int p0 = 0; p0 < rb->n_pairs; p0 += 6) {
+      const int rows = min(6, rb->n_pairs - p0);
+      float col[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (mine) {
+        for (int r = 0; r < rows; ++r) {
+          const int p = p0 + r;
+          if (sm.ps[p] == 0.f) continue;
+          const int ja = rb->sph_joint[rb->pair[p][0]], jb = rb->sph_joint[rb->pair[p][1]];
+          float v = 0.f;
+          for (int m = -1; m < ti.n_mim[lane]; ++m) {  // the variable's own joint, then its mimics
+            const int jj = m < 0 ? ti.dof_joint[lane] : ti.mim_joint[lane][m];
+            const float scale = m < 0 ? 1.f : ti.mim_mult[lane][m];
+            const bool ina = rb->subtree[jj] >> ja & 1ull, inb = rb->subtree[jj] >> jb & 1ull;
+            if (!ina && !inb) continue;
+            Rt Tj;
+            rt_load(sm.frames[jj], Tj);
+            float w[3];
+            mat_vec(Tj.r, rb->axis[jj], w);
+            // velocity of a point x moved by joint jj: revolute w x (x - p_j), prismatic w
+            float va[3] = {0.f, 0.f, 0.f}, vb[3] = {0.f, 0.f, 0.f};
+            if (rb->type[jj] == PK_JOINT_REVOLUTE) {
+              if (ina) {
+                const float da[3] = {sm.pca[p][0] - Tj.t[0], sm.pca[p][1] - Tj.t[1], sm.pca[p][2] - Tj.t[2]};
+                cross3(w, da, va);
+              }
+              if (inb) {
+                const float db[3] = {sm.pcb[p][0] - Tj.t[0], sm.pcb[p][1] - Tj.t[1], sm.pcb[p][2] - Tj.t[2]};
+                cross3(w, db, vb);
+              }
+            } else {
+              if (ina) { va[0] = w[0]; va[1] = w[1]; va[2] = w[2]; }
+              if (inb) { vb[0] = w[0]; vb[1] = w[1]; vb[2] = w[2]; }
+            }
+            const float dd = sm.pn[p][0] * (va[0] - vb[0]) + sm.pn[p][1] * (va[1] - vb[1]) +
+                             sm.pn[p][2] * (va[2] - vb[2]);
+            v = fmaf(scale, dd, v);
+          }
+          col[r] = sm.ps[p] * v;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 6; ++r) sm.Jk[r][lane] = col[r];
+      __syncwarp();
+      for (int r = 0; r < rows; ++r) {
+        g = fmaf(col[r], sm.pr[p0 + r], g);
+#pragma unroll
+        for (int j = 0; j < N; ++j) Arow[j] = fmaf(col[r], sm.Jk[r][j], Arow[j]);
+      }
+      __syncwarp();
+    }
   }
   if (mine) {
     const float q = sm.q[lane];

@@ -80,8 +80,13 @@ pk_status check_params(const pk_ik_params* p) {
   if (!(p->tol_pos >= 0.f) || !(p->tol_rot >= 0.f))
     return fail(PK_ERR_INVALID_ARG, "tolerances must be >= 0");
   if (p->reserved != 0) return fail(PK_ERR_INVALID_ARG, "reserved must be 0");
+  if (!(p->w_self >= 0.f) || !isfinite(p->w_self) || (p->w_self > 0.f && !(p->eta_self > 0.f)))
+    return fail(PK_ERR_INVALID_ARG, "w_self must be >= 0 (and eta_self > 0 when it is used)");
   return PK_OK;
 }
+
+// The self-collision rows are in play (tree path only).
+bool self_collision(const pk_robot* rb, const pk_ik_params* p) { return p->w_self > 0.f && rb->n_pairs > 0; }
 
 pk::LmParams lm_params(const pk_ik_params* p, bool pos_only) {
   pk::LmParams l;
@@ -90,6 +95,8 @@ pk::LmParams lm_params(const pk_ik_params* p, bool pos_only) {
   l.tol_pos = p->tol_pos; l.tol_rot = pos_only ? INFINITY : p->tol_rot;
   l.max_iters = p->max_iters; l.early_exit = p->early_exit != 0; l.cancel = p->cancel_siblings != 0;
   l.pos_only = pos_only;
+  l.w_self = p->w_self;
+  l.eta_self = p->eta_self;
   return l;
 }
 
@@ -365,6 +372,8 @@ void pk_ik_params_default(pk_ik_params* p) {
   p->early_exit = 1;
   p->cancel_siblings = 0;
   p->reserved = 0;
+  p->w_self = 0.f;
+  p->eta_self = 0.02f;
 }
 
 const char* pk_last_error(void) { return g_last_error.c_str(); }
@@ -386,6 +395,18 @@ static cudaError_t upload_robot(const pk_robot* rb) {
     h.mult[j] = rb->mult[j];
     h.offs[j] = rb->offs[j];
     h.own[j] = rb->type[j] != PK_JOINT_FIXED && rb->mimic[j] < 0;
+  }
+  for (int l = 0; l < rb->n_joints; ++l)  // l lies in the subtree of each of its ancestors
+    for (int j = l; j >= 0; j = rb->parent[j]) h.subtree[j] |= 1ull << l;
+  h.n_spheres = rb->n_spheres;
+  h.n_pairs = rb->n_pairs;
+  for (int i = 0; i < rb->n_spheres; ++i) {
+    h.sph_joint[i] = rb->sph_joint[i];
+    for (int c = 0; c < 4; ++c) h.sph[i][c] = rb->sph[4 * i + c];
+  }
+  for (int i = 0; i < rb->n_pairs; ++i) {
+    h.pair[i][0] = rb->pairs[2 * i];
+    h.pair[i][1] = rb->pairs[2 * i + 1];
   }
   return cudaMemcpy(rb->d_blob, &h, sizeof h, cudaMemcpyHostToDevice);
 }
@@ -479,6 +500,34 @@ pk_status pk_robot_create(int32_t n_joints, const int32_t* parent, const int32_t
   return PK_OK;
 }
 
+pk_status pk_robot_set_spheres(pk_robot* rb, int32_t n_spheres, const int32_t* joint, const float* centre,
+                               const float* radius, int32_t n_pairs, const int32_t* pairs) {
+  if (!rb) return fail(PK_ERR_INVALID_ARG, "robot is NULL");
+  if (n_spheres < 0 || n_spheres > pk::kMaxSpheres || n_pairs < 0 || n_pairs > pk::kMaxPairs)
+    return fail(PK_ERR_INVALID_ARG, "need 0..%d spheres and 0..%d pairs", pk::kMaxSpheres, pk::kMaxPairs);
+  if ((n_spheres > 0 && (!joint || !centre || !radius)) || (n_pairs > 0 && !pairs))
+    return fail(PK_ERR_INVALID_ARG, "NULL sphere array");
+  for (int i = 0; i < n_spheres; ++i)
+    if (joint[i] < 0 || joint[i] >= rb->n_joints || !finite_all(centre + 3 * i, 3) || !(radius[i] >= 0.f) ||
+        !isfinite(radius[i]))
+      return fail(PK_ERR_INVALID_ARG, "sphere %d: bad joint, centre or radius", i);
+  for (int i = 0; i < n_pairs; ++i)
+    if (pairs[2 * i] < 0 || pairs[2 * i] >= n_spheres || pairs[2 * i + 1] < 0 || pairs[2 * i + 1] >= n_spheres ||
+        pairs[2 * i] == pairs[2 * i + 1])
+      return fail(PK_ERR_INVALID_ARG, "pair %d: sphere indices must be distinct and in range", i);
+  rb->n_spheres = n_spheres;
+  rb->n_pairs = n_pairs;
+  rb->sph_joint.assign(joint, joint + n_spheres);
+  rb->sph.resize(4 * (size_t)n_spheres);
+  for (int i = 0; i < n_spheres; ++i) {
+    for (int c = 0; c < 3; ++c) rb->sph[4 * i + c] = centre[3 * i + c];
+    rb->sph[4 * i + 3] = radius[i];
+  }
+  rb->pairs.assign(pairs, pairs + 2 * (size_t)n_pairs);
+  cudaError_t e = upload_robot(rb);
+  return e == cudaSuccess ? PK_OK : cuda_fail(e, "pk_robot_set_spheres");
+}
+
 pk_status pk_robot_set_mimic(pk_robot* rb, int32_t joint, int32_t source, float multiplier, float offset) {
   if (!rb) return fail(PK_ERR_INVALID_ARG, "robot is NULL");
   if (joint < 0 || joint >= rb->n_joints || source < 0 || source >= rb->n_joints || joint == source)
@@ -566,7 +615,7 @@ pk_status pk_ik_solve(const pk_robot* rb, const pk_ik_params* params, int32_t k,
   if (n_seeds < 1) return fail(PK_ERR_INVALID_ARG, "n_seeds must be >= 1");
   if ((long long)batch * n_seeds > 0x7fffff00LL)
     return fail(PK_ERR_INVALID_ARG, "batch * n_seeds exceeds 2^31");
-  const bool chain = chain_eligible(rb, k, target_links);
+  const bool chain = chain_eligible(rb, k, target_links) && !self_collision(rb, params);
   pk::ChainHost ch;
   pk::TreeInfo ti;
   if (chain) {
@@ -646,8 +695,8 @@ pk_status pk_ik_beam_solve(const pk_robot* rb, const pk_ik_params* params, const
     return fail(PK_ERR_INVALID_ARG, "beam: need 1 <= keep <= 32, keep <= n_seeds <= 1024, steps >= 0");
   bool pos_only = false;
   if ((s = check_targets(rb, k, target_links, target_kinds, &pos_only)) != PK_OK) return s;
-  if (!chain_eligible(rb, k, target_links))
-    return fail(PK_ERR_UNSUPPORTED, "IK-Beam runs on serial chains with one target");
+  if (!chain_eligible(rb, k, target_links) || self_collision(rb, params))
+    return fail(PK_ERR_UNSUPPORTED, "IK-Beam runs on serial chains with one target and no self-collision rows");
   pk::ChainHost ch;
   if ((s = fold_chain(rb, target_links[0], &ch)) != PK_OK) return s;
   if (batch < 0) return fail(PK_ERR_INVALID_ARG, "batch must be >= 0");

@@ -15,6 +15,9 @@ struct pk_robot {
   std::vector<int32_t> mimic;     // source joint of a mimic joint, else -1
   std::vector<float> mult, offs;  // joint value = mult * q[var] + offs
   bool has_mimic = false;
+  std::vector<int32_t> sph_joint, pairs;  // self-collision spheres and pairs
+  std::vector<float> sph;                 // [n_spheres][4]: centre, radius
+  int n_spheres = 0, n_pairs = 0;
   // Device copy for the generic (tree) kernels, see RobotDev.
   void* d_blob = nullptr;
   int device = 0;
@@ -23,6 +26,8 @@ struct pk_robot {
 namespace pk {
 
 constexpr int kMaxJoints = 64;
+constexpr int kMaxSpheres = 64;
+constexpr int kMaxPairs = 64;
 constexpr int kMaxDevices = 64;
 constexpr int kMaxChainDof = 8;
 
@@ -37,6 +42,11 @@ struct RobotDev {
   float lower[kMaxJoints], upper[kMaxJoints];
   float mult[kMaxJoints], offs[kMaxJoints];  // joint value = mult * q[var] + offs (mimic joints)
   int32_t own[kMaxJoints];                   // 1: the joint owns its variable (not a mimic)
+  uint64_t subtree[kMaxJoints];              // bit l: joint l is joint j or one of its descendants
+  int32_t n_spheres, n_pairs;                // self-collision model
+  int32_t sph_joint[kMaxSpheres];
+  float sph[kMaxSpheres][4];                 // centre in the joint frame, radius
+  int32_t pair[kMaxPairs][2];
 };
 
 // Serial chain folded so that every fixed joint is merged into the next
@@ -55,6 +65,7 @@ struct ChainHost {
 // Device-ready LM settings.
 struct LmParams {
   float w_pos, w_rot, w_limit, w_rest;
+  float w_self = 0.f, eta_self = 0.02f;  // self-collision (tree path)
   float lambda0, lambda_min, lambda_max, nu;
   float tol_pos, tol_rot;
   int32_t max_iters, early_exit, cancel, pos_only;

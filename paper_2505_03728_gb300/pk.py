@@ -43,7 +43,8 @@ class pk_ik_params(C.Structure):
                 ("w_rest", C.c_float), ("lambda0", C.c_float), ("lambda_min", C.c_float),
                 ("lambda_max", C.c_float), ("nu", C.c_float), ("tol_pos", C.c_float),
                 ("tol_rot", C.c_float), ("max_iters", C.c_int32), ("early_exit", C.c_int32),
-                ("cancel_siblings", C.c_int32), ("reserved", C.c_int32)]
+                ("cancel_siblings", C.c_int32), ("reserved", C.c_int32), ("w_self", C.c_float),
+                ("eta_self", C.c_float)]
 
 
 class pk_ik_beam_params(C.Structure):
@@ -86,6 +87,7 @@ _SIGNATURES = {
     "pk_robot_n_joints": (_i32, [_vp]),
     "pk_robot_n_dof": (_i32, [_vp]),
     "pk_robot_set_mimic": (_i32, [_vp, _i32, _i32, C.c_float, C.c_float]),
+    "pk_robot_set_spheres": (_i32, [_vp, _i32, _i32p, _f32p, _f32p, _i32, _i32p]),
     "pk_fk": (_i32, [_vp, _i32, _vp, _vp, _vp]),
     "pk_ik_residual": (_i32, [_vp, C.POINTER(pk_ik_params), _i32, _i32p, _i32p, _i32, _vp, _vp, _vp,
                               _vp, _vp]),
@@ -217,6 +219,16 @@ class Robot:
                                         C.c_float(offset)))
         self.n_dof = lib().pk_robot_n_dof(self.handle)
 
+    def set_spheres(self, joint, centre, radius, pairs):
+        """Self-collision model: spheres (frame, centre in it, radius) and the pairs that must stay apart."""
+        joint = np.ascontiguousarray(joint, np.int32).reshape(-1)
+        centre = np.ascontiguousarray(centre, np.float32).reshape(-1)
+        radius = np.ascontiguousarray(radius, np.float32).reshape(-1)
+        pairs = np.ascontiguousarray(pairs, np.int32).reshape(-1)
+        _check(lib().pk_robot_set_spheres(self.handle, len(joint), joint.ctypes.data_as(_i32p),
+                                          centre.ctypes.data_as(_f32p), radius.ctypes.data_as(_f32p),
+                                          len(pairs) // 2, pairs.ctypes.data_as(_i32p)))
+
     @classmethod
     def from_spec(cls, spec):
         r = cls(spec["parent"], spec["type"], spec["axis"], spec["origin"], spec["lower"], spec["upper"])
@@ -225,6 +237,9 @@ class Robot:
             for j, s in enumerate(np.asarray(mimic)):
                 if s >= 0:
                     r.set_mimic(j, int(s), float(spec["mimic_mult"][j]), float(spec["mimic_off"][j]))
+        sp = spec.get("spheres")
+        if sp is not None:
+            r.set_spheres(sp["joint"], sp["centre"], sp["radius"], sp["pairs"])
         return r
 
     def __del__(self):
