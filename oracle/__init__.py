@@ -353,7 +353,8 @@ class _TrajParams(C.Structure):
                 ("w_vel", C.c_double), ("w_acc", C.c_double), ("w_limit", C.c_double),
                 ("w_coll", C.c_double), ("eta", C.c_double), ("lambda0", C.c_double),
                 ("lambda_min", C.c_double), ("lambda_max", C.c_double), ("nu", C.c_double),
-                ("iters", C.c_int32), ("banded", C.c_int32)]
+                ("iters", C.c_int32), ("banded", C.c_int32), ("w_vlimit", C.c_double), ("v_max", C.c_double),
+                ("w_swept", C.c_double)]
 
 
 class _TrajScene(C.Structure):
@@ -364,9 +365,9 @@ class _TrajScene(C.Structure):
 class TrajParams:
     def __init__(self, w_start=100.0, w_goal_pos=100.0, w_goal_rot=50.0, w_vel=1.0, w_acc=1.0, w_limit=10.0,
                  w_coll=10.0, eta=0.02, lambda0=1e-2, lambda_min=1e-10, lambda_max=1e10, nu=2.0, iters=50,
-                 banded=1):
+                 banded=1, w_vlimit=0.0, v_max=0.1, w_swept=0.0):
         self._c = _TrajParams(w_start, w_goal_pos, w_goal_rot, w_vel, w_acc, w_limit, w_coll, eta, lambda0,
-                              lambda_min, lambda_max, nu, iters, banded)
+                              lambda_min, lambda_max, nu, iters, banded, w_vlimit, v_max, w_swept)
 
     def __getattr__(self, k):
         return getattr(self.__dict__["_c"], k)

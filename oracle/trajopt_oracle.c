@@ -32,6 +32,11 @@ typedef struct {
   double lambda0, lambda_min, lambda_max, nu;
   int32_t iters;
   int32_t banded; /* 1: block-banded Cholesky, 0: dense */
+  /* extensions (0 = off): velocity-limit hinge w_vlimit max(0, |q_t - q_{t-1}|
+   * - v_max) (Sec. III-C, dt = 1) and swept-sphere collision between t and
+   * t+1, w_swept f(d, eta) with d the distance from an obstacle sphere to the
+   * capsule swept by a link sphere (Sec. IV-B continuous collision) */
+  double w_vlimit, v_max, w_swept;
 } or_traj_params;
 
 typedef struct {
@@ -58,18 +63,23 @@ double or_coll_activation(double d, double eta, double* df) {
 
 int32_t or_traj_n_residuals(const or_robot* rb, const or_traj_scene* sc, int32_t T) {
   const int n = or_n_dof(rb);
-  return n + 6 + n * (T - 1) + n * (T - 2 > 0 ? T - 2 : 0) + n * T + T * n * sc->S * (sc->n_obs + 1);
+  return n + 6 + n * (T - 1) + n * (T - 2 > 0 ? T - 2 : 0) + n * T + T * n * sc->S * (sc->n_obs + 1) +
+         n * (T - 1) + (T - 1) * n * sc->S * sc->n_obs;
 }
 
-/* Row-sparse Jacobian: every row has at most n nonzeros; row i keeps its
- * column indices in Jc[i][0..n) (-1 = unused) and values in Jv[i][0..n). */
+/* Row width of the row-sparse Jacobian: a swept-sphere row touches two
+ * timesteps. */
+#define KW (2 * n)
+
+/* Row-sparse Jacobian: every row has at most KW = 2n nonzeros; row i keeps
+ * its column indices in Jc[i][0..KW) (-1 = unused) and values in Jv[i][0..KW). */
 #define SETJ(row_, col_, val_)                                     \
   do {                                                             \
     if (Jc) {                                                      \
-      int* c_ = Jc + (size_t)(row_) * n;                           \
-      double* v_ = Jv + (size_t)(row_) * n;                        \
+      int* c_ = Jc + (size_t)(row_) * KW;                          \
+      double* v_ = Jv + (size_t)(row_) * KW;                       \
       int k_ = 0;                                                  \
-      while (k_ < n && c_[k_] >= 0 && c_[k_] != (col_)) ++k_;      \
+      while (k_ < KW && c_[k_] >= 0 && c_[k_] != (col_)) ++k_;     \
       c_[k_] = (col_);                                             \
       v_[k_] = (val_);                                             \
     }                                                              \
@@ -84,7 +94,7 @@ void or_traj_residual_sparse(const or_robot* rb, const or_traj_params* p, const 
   const int n = or_n_dof(rb), nj = rb->n_joints;
   const int m = or_traj_n_residuals(rb, sc, T);
   if (Jc)
-    for (size_t i = 0; i < (size_t)m * n; ++i) Jc[i] = -1;
+    for (size_t i = 0; i < (size_t)m * KW; ++i) Jc[i] = -1;
   int row = 0;
   /* start */
   for (int i = 0; i < n; ++i, ++row) {
@@ -202,6 +212,86 @@ void or_traj_residual_sparse(const or_robot* rb, const or_traj_params* p, const 
       }
     }
   }
+  /* velocity-limit hinge per (t >= 1, joint): w_vlimit max(0, |q_t - q_{t-1}| - v_max) */
+  for (int t = 1; t < T; ++t)
+    for (int i = 0; i < n; ++i, ++row) {
+      const double v = x[t * n + i] - x[(t - 1) * n + i];
+      const double h = fabs(v) - p->v_max;
+      if (h > 0 && p->w_vlimit > 0) {
+        const double sg = v > 0 ? 1.0 : -1.0;
+        r[row] = p->w_vlimit * h;
+        SETJ(row, t * n + i, p->w_vlimit * sg);
+        SETJ(row, (t - 1) * n + i, -p->w_vlimit * sg);
+      } else {
+        r[row] = 0;
+      }
+    }
+  /* swept spheres: the capsule from c(t) to c(t+1) of every link sphere
+   * against every obstacle sphere; d = |o - p| - r - r_o with p the capsule
+   * axis point closest to the obstacle centre o (parameter u in [0, 1]);
+   * dd/dc(t) = (1 - u) n and dd/dc(t+1) = u n, n = (p - o) / |p - o| */
+  double* Tf2 = (double*)malloc(sizeof(double) * 12 * nj);
+  for (int t = 0; t + 1 < T; ++t) {
+    or_fk(rb, x + (size_t)t * n, Tf);
+    or_fk(rb, x + (size_t)(t + 1) * n, Tf2);
+    for (int l = 0; l < n; ++l) {
+      for (int s = 0; s < sc->S; ++s) {
+        const double al = (s + 0.5) / sc->S;
+        double c0[3], c1[3];
+        {
+          const double* pa = Tf + 12 * jidx[l];
+          const double* pb = Tf + 12 * jidx[l + 1];
+          const double* qa = Tf2 + 12 * jidx[l];
+          const double* qb = Tf2 + 12 * jidx[l + 1];
+          for (int i = 0; i < 3; ++i) {
+            const int k = 4 * i + 3;
+            c0[i] = pa[k] + al * (pb[k] - pa[k]);
+            c1[i] = qa[k] + al * (qb[k] - qa[k]);
+          }
+        }
+        const double rad = sc->radii[l * sc->S + s];
+        for (int o = 0; o < sc->n_obs; ++o, ++row) {
+          const double* ob = sc->obs + 4 * o;
+          double e[3] = {c1[0] - c0[0], c1[1] - c0[1], c1[2] - c0[2]};
+          const double ee = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+          double u = ee > 0 ? ((ob[0] - c0[0]) * e[0] + (ob[1] - c0[1]) * e[1] + (ob[2] - c0[2]) * e[2]) / ee : 0.0;
+          u = u < 0 ? 0 : (u > 1 ? 1 : u);
+          double pnt[3] = {c0[0] + u * e[0], c0[1] + u * e[1], c0[2] + u * e[2]};
+          double v3[3] = {pnt[0] - ob[0], pnt[1] - ob[1], pnt[2] - ob[2]};
+          const double len = sqrt(v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2]);
+          const double d = len - rad - ob[3];
+          double df;
+          const double fa = p->w_swept > 0 ? or_coll_activation(d, p->eta, &df) : 0.0;
+          r[row] = p->w_swept * fa;
+          if (!Jc || p->w_swept <= 0 || df == 0.0 || len <= 0) continue;
+          const double nrm[3] = {v3[0] / len, v3[1] / len, v3[2] / len};
+          for (int side = 0; side < 2; ++side) {
+            const double* TT = side ? Tf2 : Tf;
+            const double* c = side ? c1 : c0;
+            const double sc_ = side ? u : 1.0 - u;
+            const int tt = t + side;
+            for (int i = 0; i <= l; ++i) {
+              const double* Ti = TT + 12 * jidx[i];
+              const double* a = rb->axis + 3 * jidx[i];
+              double w[3] = {Ti[0] * a[0] + Ti[1] * a[1] + Ti[2] * a[2], Ti[4] * a[0] + Ti[5] * a[1] + Ti[6] * a[2],
+                             Ti[8] * a[0] + Ti[9] * a[1] + Ti[10] * a[2]};
+              double dc[3];
+              if (rb->type[jidx[i]] == OR_JOINT_REVOLUTE) {
+                double ev[3] = {c[0] - Ti[3], c[1] - Ti[7], c[2] - Ti[11]};
+                dc[0] = w[1] * ev[2] - w[2] * ev[1];
+                dc[1] = w[2] * ev[0] - w[0] * ev[2];
+                dc[2] = w[0] * ev[1] - w[1] * ev[0];
+              } else {
+                dc[0] = w[0]; dc[1] = w[1]; dc[2] = w[2];
+              }
+              SETJ(row, tt * n + i, p->w_swept * df * sc_ * (nrm[0] * dc[0] + nrm[1] * dc[1] + nrm[2] * dc[2]));
+            }
+          }
+        }
+      }
+    }
+  }
+  free(Tf2);
   free(Tf);
   free(jidx);
 }
@@ -210,13 +300,14 @@ void or_traj_residual_sparse(const or_robot* rb, const or_traj_params* p, const 
 void or_traj_residual(const or_robot* rb, const or_traj_params* p, const or_traj_scene* sc, int32_t T,
                       const double* x, const double* q_start, const double* goal, double* r, double* J) {
   const int n = or_n_dof(rb), N = T * n, m = or_traj_n_residuals(rb, sc, T);
-  int* Jc = J ? (int*)malloc(sizeof(int) * (size_t)m * n) : NULL;
-  double* Jv = J ? (double*)malloc(sizeof(double) * (size_t)m * n) : NULL;
+  int* Jc = J ? (int*)malloc(sizeof(int) * (size_t)m * KW) : NULL;
+  double* Jv = J ? (double*)malloc(sizeof(double) * (size_t)m * KW) : NULL;
   or_traj_residual_sparse(rb, p, sc, T, x, q_start, goal, r, Jc, Jv);
   if (J) {
     memset(J, 0, sizeof(double) * (size_t)m * N);
     for (int i = 0; i < m; ++i)
-      for (int k = 0; k < n && Jc[(size_t)i * n + k] >= 0; ++k) J[(size_t)i * N + Jc[(size_t)i * n + k]] = Jv[(size_t)i * n + k];
+      for (int k = 0; k < KW && Jc[(size_t)i * KW + k] >= 0; ++k)
+        J[(size_t)i * N + Jc[(size_t)i * KW + k]] = Jv[(size_t)i * KW + k];
   }
   free(Jc);
   free(Jv);
@@ -228,8 +319,8 @@ static double traj_normal(const or_robot* rb, const or_traj_params* p, const or_
                           const double* x, const double* qs, const double* goal, double* A, double* g) {
   const int n = or_n_dof(rb), N = T * n, m = or_traj_n_residuals(rb, sc, T);
   double* r = (double*)malloc(sizeof(double) * m);
-  int* Jc = A ? (int*)malloc(sizeof(int) * (size_t)m * n) : NULL;
-  double* Jv = A ? (double*)malloc(sizeof(double) * (size_t)m * n) : NULL;
+  int* Jc = A ? (int*)malloc(sizeof(int) * (size_t)m * KW) : NULL;
+  double* Jv = A ? (double*)malloc(sizeof(double) * (size_t)m * KW) : NULL;
   or_traj_residual_sparse(rb, p, sc, T, x, qs, goal, r, Jc, Jv);
   double f = 0;
   for (int i = 0; i < m; ++i) f += r[i] * r[i];
@@ -238,11 +329,11 @@ static double traj_normal(const or_robot* rb, const or_traj_params* p, const or_
     memset(A, 0, sizeof(double) * (size_t)N * N);
     memset(g, 0, sizeof(double) * N);
     for (int i = 0; i < m; ++i) {
-      const int* c = Jc + (size_t)i * n;
-      const double* v = Jv + (size_t)i * n;
-      for (int u = 0; u < n && c[u] >= 0; ++u) {
+      const int* c = Jc + (size_t)i * KW;
+      const double* v = Jv + (size_t)i * KW;
+      for (int u = 0; u < KW && c[u] >= 0; ++u) {
         g[c[u]] += v[u] * r[i];
-        for (int w = 0; w < n && c[w] >= 0; ++w) A[(size_t)c[u] * N + c[w]] += v[u] * v[w];
+        for (int w = 0; w < KW && c[w] >= 0; ++w) A[(size_t)c[u] * N + c[w]] += v[u] * v[w];
       }
     }
     free(Jc);

@@ -43,7 +43,10 @@ def test_residual_jacobian_matches_central_fd():
     rb, scene, x, qs, goal = _small()
     prm = oracle.TrajParams()
     r, J = oracle.traj_residual(rb, prm, scene, x, qs, goal)
-    assert np.count_nonzero(r[-(5 * 7 * 4 * 4):]) > 5  # some collision rows active
+    ext = 4 * 7 + 4 * 7 * 4 * 3  # velocity-limit and swept-sphere rows (off here) follow the collision rows
+    coll = slice(len(r) - ext - 5 * 7 * 4 * 4, len(r) - ext)
+    assert np.count_nonzero(r[coll]) > 5  # some collision rows active
+    assert np.count_nonzero(r[len(r) - ext:]) == 0
     h = 1e-6
     Jfd = np.zeros_like(J)
     for a in range(x.size):
@@ -55,9 +58,8 @@ def test_residual_jacobian_matches_central_fd():
     # rows next to an activation kink (d = 0 or d = eta) are not differentiable at FD scale
     f = r / prm.w_coll
     near_kink = np.zeros(len(r), bool)
-    coll0 = len(r) - 5 * 7 * 4 * 4
-    fc = f[coll0:]
-    near_kink[coll0:] = (np.abs(fc - 0.5 * prm.eta) < 1e-4) | ((fc > 0) & (fc < 1e-7))
+    fc = f[coll]
+    near_kink[coll] = (np.abs(fc - 0.5 * prm.eta) < 1e-4) | ((fc > 0) & (fc < 1e-7))
     err = np.abs(J - Jfd) / np.maximum(1.0, np.abs(J))
     assert err[~near_kink].max() <= 1e-6
 
