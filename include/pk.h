@@ -376,6 +376,13 @@ typedef struct {
   float tol_pos, tol_rot; /* goal success thresholds (1 mm, 0.5 deg) */
   int32_t iters;      /* LM iterations (default 50) */
   int32_t reserved;   /* must be 0 */
+  /* extensions, off by default: velocity-limit hinge (Sec. III-C, dt = 1)
+   * w_vlimit max(0, |q_t - q_{t-1}| - v_max) per joint, and swept-sphere
+   * collision between t and t+1 (Sec. IV-B): w_swept f(d, eta) with d the
+   * distance from each obstacle sphere to the capsule a link sphere sweeps */
+  float w_vlimit;     /* default 0 */
+  float v_max;        /* rad (or m) per timestep, default 0.1 */
+  float w_swept;      /* default 0 */
 } pk_trajopt_params;
 
 void pk_trajopt_params_default(pk_trajopt_params* p);
@@ -400,14 +407,16 @@ pk_status pk_trajopt_solve(const pk_robot* robot, const pk_trajopt_params* param
 /*
  * pk_trajopt_normal -- the normal equations of the same problem at given
  * trajectories d_q [batch][T][n]: full diagonal blocks of J^T J
- * d_D_out [batch][T][n][n] (smoothness included), J^T r d_g_out [batch][T][n]
- * and the cost d_cost_out [batch].  The off-diagonal blocks are the
- * smoothness terms alone: -(w_vel^2 + 2 w_acc^2 ...) I and w_acc^2 I.
+ * d_D_out [batch][T][n][n] (smoothness included), the first sub-diagonal
+ * blocks (t, t-1) d_E_out [batch][T][n][n] (NULL: not written; block 0 is
+ * zero), J^T r d_g_out [batch][T][n] and the cost d_cost_out [batch].  The
+ * second sub-diagonal blocks are the acceleration term alone, w_acc^2 I.
  */
 pk_status pk_trajopt_normal(const pk_robot* robot, const pk_trajopt_params* params, int32_t batch, int32_t T,
                             const float* d_q_start, const float* d_goal, const float* d_q,
                             int32_t spheres_per_link, const float* d_radii, int32_t n_obs, const float* d_obs,
-                            const float* plane, float* d_D_out, float* d_g_out, float* d_cost_out, void* stream);
+                            const float* plane, float* d_D_out, float* d_E_out, float* d_g_out, float* d_cost_out,
+                            void* stream);
 
 /*
  * Learned seeds.  The paper's solver starts from given seeds; a seed network

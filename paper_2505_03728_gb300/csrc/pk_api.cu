@@ -292,18 +292,23 @@ void pk_trajopt_params_default(pk_trajopt_params* p) {
   p->tol_rot = 0.5f * 3.14159265358979f / 180.f;
   p->iters = 50;
   p->reserved = 0;
+  p->w_vlimit = 0.f;
+  p->v_max = 0.1f;
+  p->w_swept = 0.f;
 }
 
 static pk_status trajopt_common(const pk_robot* rb, const pk_trajopt_params* p, int32_t batch, int32_t T,
                                 const float* d_q_start, const float* d_goal, const float* d_q,
                                 int32_t S, const float* d_radii, int32_t n_obs, const float* d_obs,
                                 const float* plane, float* d_q_out, float* d_cost_out, int32_t* d_status_out,
-                                float* d_D_out, float* d_g_out, void* stream) {
+                                float* d_D_out, float* d_E_out, float* d_g_out, void* stream) {
   if (!rb || !p) return fail(PK_ERR_INVALID_ARG, "robot or params is NULL");
   if (!(p->nu > 1.f) || !(p->lambda0 > 0.f) || !(p->lambda_min > 0.f) || !(p->lambda_max >= p->lambda_min))
     return fail(PK_ERR_INVALID_ARG, "invalid damping parameters");
   if (p->iters < 0 || p->reserved != 0) return fail(PK_ERR_INVALID_ARG, "iters must be >= 0, reserved 0");
   if (!(p->eta > 0.f)) return fail(PK_ERR_INVALID_ARG, "eta must be > 0");
+  if (!(p->w_vlimit >= 0.f) || !(p->v_max >= 0.f) || !(p->w_swept >= 0.f))
+    return fail(PK_ERR_INVALID_ARG, "w_vlimit, v_max and w_swept must be >= 0");
   if (T < 3 || T > pk::kTrajMaxT) return fail(PK_ERR_INVALID_ARG, "T must be in 3..%d", pk::kTrajMaxT);
   if (S < 1 || S > pk::kTrajMaxS) return fail(PK_ERR_INVALID_ARG, "spheres_per_link must be in 1..%d", pk::kTrajMaxS);
   if (n_obs < 0 || n_obs > pk::kTrajMaxObs) return fail(PK_ERR_INVALID_ARG, "n_obs must be in 0..%d", pk::kTrajMaxObs);
@@ -323,8 +328,9 @@ static pk_status trajopt_common(const pk_robot* rb, const pk_trajopt_params* p, 
   tp.tol_pos = p->tol_pos; tp.tol_rot = p->tol_rot;
   tp.iters = p->iters; tp.T = T; tp.S = S; tp.n_obs = n_obs;
   for (int i = 0; i < 4; ++i) tp.plane[i] = plane[i];
+  tp.w_vlimit = p->w_vlimit; tp.v_max = p->v_max; tp.w_swept = p->w_swept;
   cudaError_t e = pk::launch_trajopt(ch, tp, batch, d_q_start, d_goal, d_q, d_radii, d_obs, d_q_out, d_cost_out,
-                                     d_status_out, d_D_out, d_g_out, (cudaStream_t)stream);
+                                     d_status_out, d_D_out, d_E_out, d_g_out, (cudaStream_t)stream);
   return e == cudaSuccess ? PK_OK : cuda_fail(e, "trajectory optimisation launch");
 }
 
@@ -334,16 +340,16 @@ pk_status pk_trajopt_solve(const pk_robot* rb, const pk_trajopt_params* p, int32
                            float* d_q_out, float* d_cost_out, int32_t* d_status_out, void* stream) {
   if (batch > 0 && (!d_q_out || !d_status_out)) return fail(PK_ERR_INVALID_ARG, "NULL device buffer");
   return trajopt_common(rb, p, batch, T, d_q_start, d_goal, d_q_init, S, d_radii, n_obs, d_obs, plane, d_q_out,
-                        d_cost_out, d_status_out, nullptr, nullptr, stream);
+                        d_cost_out, d_status_out, nullptr, nullptr, nullptr, stream);
 }
 
 pk_status pk_trajopt_normal(const pk_robot* rb, const pk_trajopt_params* p, int32_t batch, int32_t T,
                             const float* d_q_start, const float* d_goal, const float* d_q, int32_t S,
                             const float* d_radii, int32_t n_obs, const float* d_obs, const float* plane,
-                            float* d_D_out, float* d_g_out, float* d_cost_out, void* stream) {
+                            float* d_D_out, float* d_E_out, float* d_g_out, float* d_cost_out, void* stream) {
   if (batch > 0 && (!d_D_out || !d_g_out)) return fail(PK_ERR_INVALID_ARG, "NULL device buffer");
   return trajopt_common(rb, p, batch, T, d_q_start, d_goal, d_q, S, d_radii, n_obs, d_obs, plane, nullptr,
-                        d_cost_out, nullptr, d_D_out, d_g_out, stream);
+                        d_cost_out, nullptr, d_D_out, d_E_out, d_g_out, stream);
 }
 
 pk_status pk_ik_workspace_stats(const void* d_workspace, int64_t* stats_out) {

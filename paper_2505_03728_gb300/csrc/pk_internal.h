@@ -157,12 +157,13 @@ struct TrajParamsDev {
   float lambda0, lambda_min, lambda_max, nu, tol_pos, tol_rot;
   int32_t iters, T, S, n_obs;
   float plane[4];
+  float w_vlimit, v_max, w_swept;
 };
 
 cudaError_t launch_trajopt(const ChainHost& ch, const TrajParamsDev& tp, int batch, const float* q_start,
                            const float* goals, const float* q_init, const float* radii, const float* obs,
-                           float* q_out, float* cost_out, int32_t* status_out, float* D_out, float* g_out,
-                           cudaStream_t st);
+                           float* q_out, float* cost_out, int32_t* status_out, float* D_out, float* E_out,
+                           float* g_out, cudaStream_t st);
 
 // Folds a serial chain ending at frame `link` (false if it is not one).
 bool fold_chain_quiet(const pk_robot* rb, int link, ChainHost* ch);

@@ -38,6 +38,8 @@ struct TrajSmem {
   static constexpr int NT = N * (N + 1) / 2;
   float x[2][kTrajMaxT][8];    // current / candidate trajectories
   float D[2][kTrajMaxT][NT];   // diagonal blocks of J^T J without smoothness
+  float E[2][kTrajMaxT][N][N]; // block (t, t-1) of J^T J beyond the smoothness scalar (velocity
+                               // limits, swept spheres)
   float g[2][kTrajMaxT][8];    // J^T r
   float f[2], mind[2], gpe[2], gre[2];
   float p[kTrajMaxT][N + 1][3];  // joint origins and tool point (world), candidate
@@ -180,6 +182,41 @@ __device__ void eval_timestep(const ChainC<N>& rc, const TrajParamsDev& tp, Traj
     if (t + 1 >= 1 && t + 1 <= T - 2) gj = fmaf(a2, xp2 - 2.f * xp + x0, gj);
     g[j] += gj;
   }
+  // velocity-limit hinge (Sec. III-C, dt = 1): the row (t, t-1) is owned by t;
+  // t also takes its part of the row (t+1, t).  E_t is written whole here.
+  float ed[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) ed[j] = 0.f;
+  if (tp.w_vlimit > 0.f) {
+    const float wv2 = tp.w_vlimit * tp.w_vlimit;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      if (t >= 1) {
+        const float v = q[j] - S.x[buf][t - 1][j];
+        const float h = fabsf(v) - tp.v_max;
+        if (h > 0.f) {
+          const float sg = v > 0.f ? 1.f : -1.f;
+          acc = fmaf(wv2, h * h, acc);
+          D[tri(j, j)] += wv2;
+          ed[j] = -wv2;
+          g[j] = fmaf(wv2 * sg, h, g[j]);
+        }
+      }
+      if (t + 1 < T) {
+        const float v = S.x[buf][t + 1][j] - q[j];
+        const float h = fabsf(v) - tp.v_max;
+        if (h > 0.f) {
+          const float sg = v > 0.f ? 1.f : -1.f;
+          D[tri(j, j)] += wv2;
+          g[j] = fmaf(-wv2 * sg, h, g[j]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) S.E[buf][t][i][j] = (i == j) ? ed[i] : 0.f;
   // start configuration
   if (t == 0) {
     const float s2 = tp.w_start * tp.w_start;
@@ -255,6 +292,27 @@ __device__ void eval_timestep(const ChainC<N>& rc, const TrajParamsDev& tp, Traj
   fpart += acc;
 }
 
+// n . dc/dq_i for a point c carried by link l at timestep t (joints 0..l).
+template <int N>
+__device__ __forceinline__ void coll_jrow(const ChainC<N>& rc, const TrajSmem<N>& S, int t, int l, const float* c,
+                                          const float* nrm, float scale, float* jr) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float dc;
+    if (i > l) {
+      dc = 0.f;
+    } else if (rc.prism & (1u << i)) {
+      dc = S.w[t][i][0] * nrm[0] + S.w[t][i][1] * nrm[1] + S.w[t][i][2] * nrm[2];
+    } else {
+      // n . (w_i x (c - p_i)) = w_i . ((c - p_i) x n)
+      const float e0 = c[0] - S.p[t][i][0], e1 = c[1] - S.p[t][i][1], e2 = c[2] - S.p[t][i][2];
+      const float x0 = e1 * nrm[2] - e2 * nrm[1], x1 = e2 * nrm[0] - e0 * nrm[2], x2 = e0 * nrm[1] - e1 * nrm[0];
+      dc = S.w[t][i][0] * x0 + S.w[t][i][1] * x1 + S.w[t][i][2] * x2;
+    }
+    jr[i] = scale * dc;
+  }
+}
+
 // Collision terms of timestep t, one link sphere per lane (lanes >= N*S idle).
 template <int N>
 __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N>& S, int buf, int t,
@@ -297,21 +355,7 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
       const float r = wc * fa;
       fpart = fmaf(r, r, fpart);
       float jr[N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        float dc;
-        if (i > l) {
-          dc = 0.f;
-        } else if (rc.prism & (1u << i)) {
-          dc = S.w[t][i][0] * nrm[0] + S.w[t][i][1] * nrm[1] + S.w[t][i][2] * nrm[2];
-        } else {
-          // n . (w_i x (c - p_i)) = w_i . ((c - p_i) x n)
-          const float e0 = c[0] - S.p[t][i][0], e1 = c[1] - S.p[t][i][1], e2 = c[2] - S.p[t][i][2];
-          const float x0 = e1 * nrm[2] - e2 * nrm[1], x1 = e2 * nrm[0] - e0 * nrm[2], x2 = e0 * nrm[1] - e1 * nrm[0];
-          dc = S.w[t][i][0] * x0 + S.w[t][i][1] * x1 + S.w[t][i][2] * x2;
-        }
-        jr[i] = wc * df * dc;
-      }
+      coll_jrow<N>(rc, S, t, l, c, nrm, wc * df, jr);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         gl[i] = fmaf(jr[i], r, gl[i]);
@@ -329,11 +373,56 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
     for (int j = 0; j < N; ++j)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) gl[j] += __shfl_xor_sync(0xffffffffu, gl[j], o);
-    if (lane == 0) {
+    if (lane == 0) {  // atomic: the swept rows of segment (t-1, t) also land in D_t, g_t
 #pragma unroll
-      for (int i = 0; i < NT; ++i) S.D[buf][t][i] += Dl[i];
+      for (int i = 0; i < NT; ++i) atomicAdd(&S.D[buf][t][i], Dl[i]);
 #pragma unroll
-      for (int j = 0; j < N; ++j) S.g[buf][t][j] += gl[j];
+      for (int j = 0; j < N; ++j) atomicAdd(&S.g[buf][t][j], gl[j]);
+    }
+  }
+  // swept spheres (Sec. IV-B): the capsule of this lane's sphere from t to t+1
+  // against every obstacle sphere; the row couples q_t and q_{t+1}
+  if (tp.w_swept > 0.f && t + 1 < tp.T && lane < nsph) {
+    const int l = lane / tp.S, s = lane % tp.S;
+    const float al = (s + 0.5f) / (float)tp.S;
+    float c0[3], c1[3], e[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      c0[i] = fmaf(al, S.p[t][l + 1][i] - S.p[t][l][i], S.p[t][l][i]);
+      c1[i] = fmaf(al, S.p[t + 1][l + 1][i] - S.p[t + 1][l][i], S.p[t + 1][l][i]);
+      e[i] = c1[i] - c0[i];
+    }
+    const float ee = fmaf(e[0], e[0], fmaf(e[1], e[1], e[2] * e[2]));
+    const float rad = S.rad[l][s];
+    for (int o = 0; o < tp.n_obs; ++o) {
+      const float4 ob = *reinterpret_cast<const float4*>(S.obs[o]);
+      float u = ee > 0.f ? ((ob.x - c0[0]) * e[0] + (ob.y - c0[1]) * e[1] + (ob.z - c0[2]) * e[2]) / ee : 0.f;
+      u = fminf(fmaxf(u, 0.f), 1.f);
+      const float v0 = fmaf(u, e[0], c0[0]) - ob.x, v1 = fmaf(u, e[1], c0[1]) - ob.y, v2 = fmaf(u, e[2], c0[2]) - ob.z;
+      const float len = sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
+      const float d = len - rad - ob.w;
+      float df;
+      const float fa = coll_act(d, tp.eta, &df);
+      if (df == 0.f || !(len > 0.f)) continue;
+      const float r = tp.w_swept * fa;
+      fpart = fmaf(r, r, fpart);
+      const float inv = 1.f / len;
+      const float nrm[3] = {v0 * inv, v1 * inv, v2 * inv};
+      float a[N], bq[N];
+      coll_jrow<N>(rc, S, t, l, c0, nrm, tp.w_swept * df * (1.f - u), a);
+      coll_jrow<N>(rc, S, t + 1, l, c1, nrm, tp.w_swept * df * u, bq);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        atomicAdd(&S.g[buf][t][i], a[i] * r);
+        atomicAdd(&S.g[buf][t + 1][i], bq[i] * r);
+#pragma unroll
+        for (int k = 0; k <= i; ++k) {
+          atomicAdd(&S.D[buf][t][tri(i, k)], a[i] * a[k]);
+          atomicAdd(&S.D[buf][t + 1][tri(i, k)], bq[i] * bq[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k) atomicAdd(&S.E[buf][t + 1][i][k], bq[i] * a[k]);
+      }
     }
   }
 }
@@ -382,7 +471,7 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N>& S, int buf, f
     // (1) L2_t = c_t Linv_{t-2}^T and M = b_t I - L2_t L1_{t-1}^T
     if (tid < N * N && t >= 1) {
       const int i = tid / N, j = tid % N;
-      float m = (i == j) ? bd : 0.f;
+      float m = ((i == j) ? bd : 0.f) + S.E[buf][t][i][j];
       if (t >= 2) {
         S.L2[t][i][j] = (j >= i) ? cd * S.Linv[t - 2][tri(j, i)] : 0.f;
 #pragma unroll
@@ -499,7 +588,8 @@ __global__ void __launch_bounds__(kThreads) trajopt_kernel(
     const __grid_constant__ ChainC<N> rc, const __grid_constant__ TrajParamsDev tp, const float* __restrict__ q_start,
     const float* __restrict__ goals, const float* __restrict__ q_init, const float* __restrict__ radii,
     const float* __restrict__ obs, float* __restrict__ q_out, float* __restrict__ cost_out,
-    int32_t* __restrict__ status_out, float* __restrict__ D_out, float* __restrict__ g_out) {
+    int32_t* __restrict__ status_out, float* __restrict__ D_out, float* __restrict__ E_out,
+    float* __restrict__ g_out) {
   extern __shared__ float4 smem_f4[];
   TrajSmem<N>& S = *reinterpret_cast<TrajSmem<N>*>(smem_f4);
   const int b = blockIdx.x, tid = threadIdx.x, T = tp.T;
@@ -525,6 +615,13 @@ __global__ void __launch_bounds__(kThreads) trajopt_kernel(
       const float v = (r >= c) ? S.D[0][t][tri(r, c)] : S.D[0][t][tri(c, r)];
       D_out[(size_t)b * T * N * N + i] = v + ((r == c) ? sd : 0.f);
     }
+    if (E_out)
+      for (int i = tid; i < T * N * N; i += kThreads) {
+        const int t = i / (N * N), r = (i / N) % N, c = i % N;
+        float sd, bd, cd;
+        smooth_scalars(tp, t, &sd, &bd, &cd);
+        E_out[(size_t)b * T * N * N + i] = t >= 1 ? S.E[0][t][r][c] + ((r == c) ? bd : 0.f) : 0.f;
+      }
     for (int i = tid; i < T * N; i += kThreads) g_out[(size_t)b * T * N + i] = S.g[0][i / N][i % N];
     if (tid == 0) cost_out[b] = S.f[0];
     return;
@@ -562,8 +659,8 @@ __global__ void __launch_bounds__(kThreads) trajopt_kernel(
 template <int N>
 cudaError_t trajopt_launch(const ChainHost& ch, const TrajParamsDev& tp, int batch, const float* q_start,
                            const float* goals, const float* q_init, const float* radii, const float* obs,
-                           float* q_out, float* cost_out, int32_t* status_out, float* D_out, float* g_out,
-                           cudaStream_t st) {
+                           float* q_out, float* cost_out, int32_t* status_out, float* D_out, float* E_out,
+                           float* g_out, cudaStream_t st) {
   const size_t smem = sizeof(TrajSmem<N>);
   static bool attr = false;
   if (!attr) {
@@ -574,7 +671,7 @@ cudaError_t trajopt_launch(const ChainHost& ch, const TrajParamsDev& tp, int bat
   const ChainC<N> rc = chain_const<N>(ch);
   TraceScope tr("trajopt", st);
   trajopt_kernel<N><<<batch, kThreads, smem, st>>>(rc, tp, q_start, goals, q_init, radii, obs, q_out, cost_out,
-                                                   status_out, D_out, g_out);
+                                                   status_out, D_out, E_out, g_out);
   return cudaGetLastError();
 }
 
@@ -582,11 +679,11 @@ cudaError_t trajopt_launch(const ChainHost& ch, const TrajParamsDev& tp, int bat
 
 cudaError_t launch_trajopt(const ChainHost& ch, const TrajParamsDev& tp, int batch, const float* q_start,
                            const float* goals, const float* q_init, const float* radii, const float* obs,
-                           float* q_out, float* cost_out, int32_t* status_out, float* D_out, float* g_out,
-                           cudaStream_t st) {
+                           float* q_out, float* cost_out, int32_t* status_out, float* D_out, float* E_out,
+                           float* g_out, cudaStream_t st) {
   switch (ch.n) {
-    case 6: return trajopt_launch<6>(ch, tp, batch, q_start, goals, q_init, radii, obs, q_out, cost_out, status_out, D_out, g_out, st);
-    case 7: return trajopt_launch<7>(ch, tp, batch, q_start, goals, q_init, radii, obs, q_out, cost_out, status_out, D_out, g_out, st);
+    case 6: return trajopt_launch<6>(ch, tp, batch, q_start, goals, q_init, radii, obs, q_out, cost_out, status_out, D_out, E_out, g_out, st);
+    case 7: return trajopt_launch<7>(ch, tp, batch, q_start, goals, q_init, radii, obs, q_out, cost_out, status_out, D_out, E_out, g_out, st);
     default: return cudaErrorInvalidValue;
   }
 }

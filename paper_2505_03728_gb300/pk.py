@@ -63,7 +63,8 @@ class pk_trajopt_params(C.Structure):
                 ("w_vel", C.c_float), ("w_acc", C.c_float), ("w_limit", C.c_float), ("w_coll", C.c_float),
                 ("eta", C.c_float), ("lambda0", C.c_float), ("lambda_min", C.c_float),
                 ("lambda_max", C.c_float), ("nu", C.c_float), ("tol_pos", C.c_float), ("tol_rot", C.c_float),
-                ("iters", C.c_int32), ("reserved", C.c_int32)]
+                ("iters", C.c_int32), ("reserved", C.c_int32), ("w_vlimit", C.c_float), ("v_max", C.c_float),
+                ("w_swept", C.c_float)]
 
 
 class pk_train_params(C.Structure):
@@ -113,7 +114,7 @@ _SIGNATURES = {
     "pk_trajopt_params_default": (None, [_vp]),
     "pk_trajopt_solve": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _i32, _vp, _f32p, _vp, _vp,
                                 _vp, _vp]),
-    "pk_trajopt_normal": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _i32, _vp, _f32p, _vp, _vp,
+    "pk_trajopt_normal": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _i32, _vp, _f32p, _vp, _vp, _vp,
                                  _vp, _vp]),
     "pk_seednet_create": (_i32, [_vp, _i32, _i32p, _i32, _i32, _i32, C.c_uint64, C.POINTER(_vp)]),
     "pk_seednet_destroy": (None, [_vp]),
@@ -540,19 +541,22 @@ def pk_trajopt_solve(robot: Robot, params: pk_trajopt_params, q_start, goals, q_
 
 
 def pk_trajopt_normal(robot: Robot, params: pk_trajopt_params, q_start, goals, q, radii, obstacles, plane,
-                      stream=None):
-    """Diagonal blocks [B][T][n][n], J^T r [B][T][n] and costs [B] at trajectories q."""
+                      stream=None, with_offdiag=False):
+    """Diagonal blocks [B][T][n][n], J^T r [B][T][n] and costs [B] at trajectories q
+    (and the (t, t-1) blocks [B][T][n][n] last when with_offdiag)."""
     B, T, n = q.shape
     S, n_obs, pl = _scene_args(radii, obstacles, plane)
     D = torch.empty(B, T, n, n, device=q.device)
+    E = torch.empty(B, T, n, n, device=q.device) if with_offdiag else None
     g = torch.empty(B, T, n, device=q.device)
     cost = torch.empty(B, device=q.device)
     _check(lib().pk_trajopt_normal(robot.handle, C.byref(params), B, T, _dev(q_start, name="q_start"),
                                    _dev(goals, name="goals"), _dev(q, name="q"), S, _dev(radii, name="radii"),
                                    n_obs, _dev(obstacles, name="obstacles") if n_obs else None,
-                                   pl.ctypes.data_as(_f32p), _dev(D, name="D"), _dev(g, name="g"),
+                                   pl.ctypes.data_as(_f32p), _dev(D, name="D"),
+                                   _dev(E, name="E") if E is not None else None, _dev(g, name="g"),
                                    _dev(cost, name="cost"), _stream(stream)))
-    return D, g, cost
+    return (D, g, cost, E) if with_offdiag else (D, g, cost)
 
 
 class IkPlan:

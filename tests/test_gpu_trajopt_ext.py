@@ -1,0 +1,73 @@
+"""GPU trajectory extensions against the FP64 oracle: the velocity-limit hinge
+(Sec. III-C) and swept-sphere collision between consecutive timesteps
+(Sec. IV-B), whose rows couple q_t and q_{t+1} and fill the (t, t-1) blocks of
+the normal matrix.  Tolerances as in test_gpu_trajopt.py."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2505_03728_gb300 import pk
+from test_gpu_trajopt import dev, oparams, setup
+
+pytestmark = pytest.mark.gpu
+
+EXT = dict(w_vlimit=3.0, v_max=0.02, w_swept=10.0)
+
+
+@pytest.mark.parametrize("T", [3, 17, 64])
+def test_normal_equations_with_extensions_match_oracle(T):
+    o, g, qs, goals, x0, radii, obs, plane, scene = setup(6, T, perturb=0.1, seed=T)
+    p = pk.pk_trajopt_params_default(**EXT)
+    D, gg, cost, E = [x.cpu().numpy().astype(np.float64) for x in
+                      pk.pk_trajopt_normal(g, p, dev(qs), dev(goals), dev(x0), dev(radii), dev(obs), plane,
+                                           with_offdiag=True)]
+    op = oparams(p)
+    n = 7
+    swept_rows = 0
+    for b in range(6):
+        f, A, gr = oracle.traj_normal(o, op, scene, x0[b], qs[b], goals[b])
+        r, _ = oracle.traj_residual(o, op, scene, x0[b], qs[b], goals[b], jacobian=False), None
+        swept_rows += int(np.count_nonzero(r[-(T - 1) * n * 4 * len(obs):]))
+        scale = np.abs(A).max()
+        for t in range(T):
+            np.testing.assert_allclose(D[b, t], A[t * n:(t + 1) * n, t * n:(t + 1) * n], atol=1e-4 * scale)
+            if t >= 1:
+                np.testing.assert_allclose(E[b, t], A[t * n:(t + 1) * n, (t - 1) * n:t * n], atol=1e-4 * scale)
+            if t >= 2:
+                blk = A[t * n:(t + 1) * n, (t - 2) * n:(t - 1) * n]
+                np.testing.assert_allclose(blk, blk[0, 0] * np.eye(n), atol=1e-12)
+        np.testing.assert_allclose(gg[b].ravel(), gr, atol=1e-4 * max(1.0, np.abs(gr).max()))
+        assert abs(cost[b] - f) <= 1e-4 * max(1.0, f)
+    if T > 3:
+        assert swept_rows > 0  # the case exercises the swept rows
+
+
+def test_one_step_with_extensions_matches_oracle():
+    o, g, qs, goals, x0, radii, obs, plane, scene = setup(16, 64, perturb=0.05, seed=1)
+    for start_iters in (0, 5):
+        start = x0 if start_iters == 0 else oracle.traj_solve(
+            o, oparams(pk.pk_trajopt_params_default(iters=5, **EXT)), scene, x0, qs, goals)["x"]
+        ref = oracle.traj_solve(o, oparams(pk.pk_trajopt_params_default(iters=1, **EXT)), scene, start, qs, goals,
+                                n_trace=True)
+        q = pk.pk_trajopt_solve(g, pk.pk_trajopt_params_default(iters=1, **EXT), dev(qs), dev(goals), dev(start),
+                                dev(radii), dev(obs), plane)[0].cpu().numpy()
+        tie = ref["margin"] <= 1e-5
+        rel = (np.abs(q - ref["x"]) / np.maximum(1.0, np.abs(ref["x"]))).reshape(16, -1).max(axis=1)
+        assert np.all(rel[~tie] <= 5e-3), rel
+        # the velocity hinges (active on most steps of these perturbed
+        # trajectories) stiffen the system: FP32 steps spread more than without
+        assert np.median(rel[~tie]) <= 1e-3, rel
+
+
+def test_velocity_limit_bounds_the_steps():
+    o, g, qs, goals, x0, radii, obs, plane, scene = setup(32, 32)
+    vmax = 0.1
+    out = {}
+    for w in (0.0, 30.0):
+        p = pk.pk_trajopt_params_default(iters=50, w_vlimit=w, v_max=vmax)
+        q = pk.pk_trajopt_solve(g, p, dev(qs), dev(goals), dev(x0), dev(radii), dev(obs), plane)[0].cpu().numpy()
+        out[w] = np.abs(np.diff(q, axis=1)).max(axis=(1, 2))
+    print(f"largest joint step: without the limit {np.median(out[0.0]):.3f}, with it {np.median(out[30.0]):.3f}")
+    assert np.median(out[30.0]) < np.median(out[0.0])
+    assert np.median(out[30.0]) <= vmax * 1.5
