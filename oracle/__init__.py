@@ -81,7 +81,7 @@ def lib():
             L.or_cholesky_solve.restype = C.c_int32
             L.or_ik_solve.restype = C.c_int32
             for name in ("or_traj_solve", "or_mlp_forward", "or_mlp_loss_grad", "or_traj_n_residuals",
-                         "or_banded_cholesky", "or_host_cores", "or_ik_beam"):
+                         "or_banded_cholesky", "or_banded_cholesky_b", "or_host_cores", "or_ik_beam"):
                 if hasattr(L, name):
                     getattr(L, name).restype = C.c_int32
             for name in ("or_coll_activation", "or_traj_normal"):
@@ -354,7 +354,7 @@ class _TrajParams(C.Structure):
                 ("w_coll", C.c_double), ("eta", C.c_double), ("lambda0", C.c_double),
                 ("lambda_min", C.c_double), ("lambda_max", C.c_double), ("nu", C.c_double),
                 ("iters", C.c_int32), ("banded", C.c_int32), ("w_vlimit", C.c_double), ("v_max", C.c_double),
-                ("w_swept", C.c_double)]
+                ("w_swept", C.c_double), ("w_acc5", C.c_double), ("w_jerk", C.c_double)]
 
 
 class _TrajScene(C.Structure):
@@ -365,9 +365,9 @@ class _TrajScene(C.Structure):
 class TrajParams:
     def __init__(self, w_start=100.0, w_goal_pos=100.0, w_goal_rot=50.0, w_vel=1.0, w_acc=1.0, w_limit=10.0,
                  w_coll=10.0, eta=0.02, lambda0=1e-2, lambda_min=1e-10, lambda_max=1e10, nu=2.0, iters=50,
-                 banded=1, w_vlimit=0.0, v_max=0.1, w_swept=0.0):
+                 banded=1, w_vlimit=0.0, v_max=0.1, w_swept=0.0, w_acc5=0.0, w_jerk=0.0):
         self._c = _TrajParams(w_start, w_goal_pos, w_goal_rot, w_vel, w_acc, w_limit, w_coll, eta, lambda0,
-                              lambda_min, lambda_max, nu, iters, banded, w_vlimit, v_max, w_swept)
+                              lambda_min, lambda_max, nu, iters, banded, w_vlimit, v_max, w_swept, w_acc5, w_jerk)
 
     def __getattr__(self, k):
         return getattr(self.__dict__["_c"], k)
@@ -415,10 +415,10 @@ def traj_normal(robot, params, scene, x, q_start, goal):
     return f, A, g
 
 
-def banded_cholesky(A, T, n):
+def banded_cholesky(A, T, n, band=2):
     A = _f64(A)
     L = np.empty_like(A)
-    rc = lib().or_banded_cholesky(T, n, A.ctypes.data_as(_f64p), L.ctypes.data_as(_f64p))
+    rc = lib().or_banded_cholesky_b(T, n, band, A.ctypes.data_as(_f64p), L.ctypes.data_as(_f64p))
     return L if rc == 0 else None
 
 

@@ -37,6 +37,11 @@ typedef struct {
    * t+1, w_swept f(d, eta) with d the distance from an obstacle sphere to the
    * capsule swept by a link sphere (Sec. IV-B continuous collision) */
   double w_vlimit, v_max, w_swept;
+  /* five-point stencils (Sec. III-C smoothness; 0 = off): acceleration
+   * (-q_{t+2} + 16 q_{t+1} - 30 q_t + 16 q_{t-1} - q_{t-2}) / 12 and jerk
+   * (q_{t+2} - 2 q_{t+1} + 2 q_{t-1} - q_{t-2}) / 2 for t = 2..T-3 (dt = 1);
+   * they widen the block band of the normal matrix from 2 to 4 */
+  double w_acc5, w_jerk;
 } or_traj_params;
 
 typedef struct {
@@ -64,7 +69,7 @@ double or_coll_activation(double d, double eta, double* df) {
 int32_t or_traj_n_residuals(const or_robot* rb, const or_traj_scene* sc, int32_t T) {
   const int n = or_n_dof(rb);
   return n + 6 + n * (T - 1) + n * (T - 2 > 0 ? T - 2 : 0) + n * T + T * n * sc->S * (sc->n_obs + 1) +
-         n * (T - 1) + (T - 1) * n * sc->S * sc->n_obs;
+         n * (T - 1) + (T - 1) * n * sc->S * sc->n_obs + 2 * n * (T - 4 > 0 ? T - 4 : 0);
 }
 
 /* Row width of the row-sparse Jacobian: a swept-sphere row touches two
@@ -292,6 +297,24 @@ void or_traj_residual_sparse(const or_robot* rb, const or_traj_params* p, const 
     }
   }
   free(Tf2);
+  /* five-point acceleration and jerk rows, t = 2..T-3 */
+  {
+    static const double ca[5] = {-1.0 / 12, 16.0 / 12, -30.0 / 12, 16.0 / 12, -1.0 / 12}; /* q_{t-2} .. q_{t+2} */
+    static const double cj[5] = {-0.5, 1.0, 0.0, -1.0, 0.5};
+    for (int kind = 0; kind < 2; ++kind) {
+      const double* c = kind ? cj : ca;
+      const double w = kind ? p->w_jerk : p->w_acc5;
+      for (int t = 2; t + 2 < T; ++t)
+        for (int i = 0; i < n; ++i, ++row) {
+          double v = 0;
+          for (int k = 0; k < 5; ++k) v += c[k] * x[(t - 2 + k) * n + i];
+          r[row] = w * v;
+          if (w != 0.0)
+            for (int k = 0; k < 5; ++k)
+              if (c[k] != 0.0) SETJ(row, (t - 2 + k) * n + i, w * c[k]);
+        }
+    }
+  }
   free(Tf);
   free(jidx);
 }
@@ -343,20 +366,20 @@ static double traj_normal(const or_robot* rb, const or_traj_params* p, const or_
   return 0.5 * f;
 }
 
-/* Block-banded Cholesky of an SPD matrix with blocks (t, t'), |t - t'| <= 2,
- * of size n: the three block diagonals are factored step by step in t.
- * L is written into a dense [N][N] array (zero outside the band).  Returns 0
- * on success. */
-int32_t or_banded_cholesky(int32_t T, int32_t n, const double* A, double* L) {
+/* Block-banded Cholesky of an SPD matrix with blocks (t, t'), |t - t'| <= B,
+ * of size n: the block diagonals are factored step by step in t.  L is
+ * written into a dense [N][N] array (zero outside the band).  Returns 0 on
+ * success. */
+int32_t or_banded_cholesky_b(int32_t T, int32_t n, int32_t B, const double* A, double* L) {
   const int N = T * n;
   memset(L, 0, sizeof(double) * (size_t)N * N);
   for (int t = 0; t < T; ++t) {
-    const int c0 = (t >= 2 ? t - 2 : 0) * n; /* first column of the band in block row t */
+    const int c0 = (t >= B ? t - B : 0) * n; /* first column of the band in block row t */
     for (int i = t * n; i < (t + 1) * n; ++i) {
       for (int j = c0; j <= i; ++j) {
         double s = A[(size_t)i * N + j];
         /* L[i][k] and L[j][k] are both inside the band only from column k0 on */
-        const int cj = (j / n >= 2 ? j / n - 2 : 0) * n;
+        const int cj = (j / n >= B ? j / n - B : 0) * n;
         const int k0 = cj > c0 ? cj : c0;
         for (int k = k0; k < j; ++k) s -= L[(size_t)i * N + k] * L[(size_t)j * N + k];
         if (i == j) {
@@ -369,6 +392,11 @@ int32_t or_banded_cholesky(int32_t T, int32_t n, const double* A, double* L) {
     }
   }
   return 0;
+}
+
+/* The band-2 case (the three-point stencils). */
+int32_t or_banded_cholesky(int32_t T, int32_t n, const double* A, double* L) {
+  return or_banded_cholesky_b(T, n, 2, A, L);
 }
 
 static int dense_cholesky(int N, const double* A, double* L) {
@@ -428,7 +456,8 @@ static double traj_lm(const or_robot* rb, const or_traj_params* p, const or_traj
       Al[(size_t)i * N + i] += lambda;
       ng[i] = -g[i];
     }
-    const int rc = p->banded ? or_banded_cholesky(T, n, Al, L) : dense_cholesky(N, Al, L);
+    const int band = (p->w_acc5 != 0.0 || p->w_jerk != 0.0) ? 4 : 2;
+    const int rc = p->banded ? or_banded_cholesky_b(T, n, band, Al, L) : dense_cholesky(N, Al, L);
     int accepted = 0;
     if (rc == 0) {
       chol_solve(N, L, ng, dx);

@@ -43,7 +43,8 @@ def test_residual_jacobian_matches_central_fd():
     rb, scene, x, qs, goal = _small()
     prm = oracle.TrajParams()
     r, J = oracle.traj_residual(rb, prm, scene, x, qs, goal)
-    ext = 4 * 7 + 4 * 7 * 4 * 3  # velocity-limit and swept-sphere rows (off here) follow the collision rows
+    # velocity-limit, swept-sphere and five-point rows (off here) follow the collision rows
+    ext = 4 * 7 + 4 * 7 * 4 * 3 + 2 * 7 * 1
     coll = slice(len(r) - ext - 5 * 7 * 4 * 4, len(r) - ext)
     assert np.count_nonzero(r[coll]) > 5  # some collision rows active
     assert np.count_nonzero(r[len(r) - ext:]) == 0

@@ -43,8 +43,9 @@ def sphere_centres(rb, q):
 
 def rows(rb, prm, scene, x, qs, goal):
     r, J = oracle.traj_residual(rb, prm, scene, x, qs, goal)
-    n_vel, n_sw = (T - 1) * N, (T - 1) * N * S * 3
-    return r, J, slice(len(r) - n_sw - n_vel, len(r) - n_sw), slice(len(r) - n_sw, len(r))
+    n_vel, n_sw, n_5 = (T - 1) * N, (T - 1) * N * S * 3, 2 * N * max(T - 4, 0)  # five-point rows come last
+    end = len(r) - n_5
+    return r, J, slice(end - n_sw - n_vel, end - n_sw), slice(end - n_sw, end)
 
 
 def test_rows_recomputed_in_numpy():
@@ -105,4 +106,35 @@ def test_normal_matrix_stays_block_pentadiagonal_and_banded_equals_dense():
                           scene, x[None], qs[None], goal[None])
     b = oracle.traj_solve(rb, oracle.TrajParams(iters=6, banded=0, w_vlimit=3.0, v_max=0.2, w_swept=7.0, eta=0.03),
                           scene, x[None], qs[None], goal[None])
+    np.testing.assert_allclose(a["x"], b["x"], atol=1e-9)
+
+
+def test_five_point_rows_are_the_stencils_and_widen_the_band_to_four():
+    rb, scene, x, qs, goal, radii, obs = setup(seed=7)
+    Tl = 9
+    rng = np.random.default_rng(7)
+    x = qs + np.cumsum(rng.normal(0, 0.1, (Tl, N)), axis=0)
+    prm = oracle.TrajParams(w_acc5=2.0, w_jerk=3.0)
+    r, J = oracle.traj_residual(rb, prm, scene, x, qs, goal)
+    nr = N * (Tl - 4)
+    acc = (-x[4:] + 16 * x[3:-1] - 30 * x[2:-2] + 16 * x[1:-3] - x[:-4]) / 12
+    jerk = (x[4:] - 2 * x[3:-1] + 2 * x[1:-3] - x[:-4]) / 2
+    np.testing.assert_allclose(r[-2 * nr:-nr], 2.0 * acc.ravel(), atol=1e-12)
+    np.testing.assert_allclose(r[-nr:], 3.0 * jerk.ravel(), atol=1e-12)
+    # a quadratic trajectory has zero jerk and constant acceleration (exact stencils)
+    tt = np.arange(Tl, dtype=float)[:, None]
+    xq = qs + 0.01 * tt + 0.003 * tt ** 2
+    rq, _ = oracle.traj_residual(rb, prm, scene, xq, qs, goal)
+    np.testing.assert_allclose(rq[-nr:], 0.0, atol=1e-12)
+    np.testing.assert_allclose(rq[-2 * nr:-nr], 2.0 * 0.006, atol=1e-12)
+    f, A, g = oracle.traj_normal(rb, prm, scene, x, qs, goal)
+    nz = lambda t, u: np.any(A[t * N:(t + 1) * N, u * N:(u + 1) * N] != 0.0)
+    assert nz(6, 2) and not nz(7, 2)  # blocks at distance 4 are filled, beyond 4 empty
+    A2 = A + 1e-2 * np.eye(A.shape[0])
+    np.testing.assert_allclose(oracle.banded_cholesky(A2, Tl, N, band=4), np.linalg.cholesky(A2), rtol=1e-10,
+                               atol=1e-12)
+    a = oracle.traj_solve(rb, oracle.TrajParams(iters=6, banded=1, w_acc5=2.0, w_jerk=3.0), scene, x[None],
+                          qs[None], goal[None])
+    b = oracle.traj_solve(rb, oracle.TrajParams(iters=6, banded=0, w_acc5=2.0, w_jerk=3.0), scene, x[None],
+                          qs[None], goal[None])
     np.testing.assert_allclose(a["x"], b["x"], atol=1e-9)
