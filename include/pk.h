@@ -383,6 +383,13 @@ typedef struct {
   float w_vlimit;     /* default 0 */
   float v_max;        /* rad (or m) per timestep, default 0.1 */
   float w_swept;      /* default 0 */
+  /* five-point stencils (Sec. III-C smoothness, dt = 1), off by default: for
+   * t = 2..T-3 and every joint, acceleration
+   * w_acc5 (-q_{t+2} + 16 q_{t+1} - 30 q_t + 16 q_{t-1} - q_{t-2}) / 12 and jerk
+   * w_jerk (q_{t+2} - 2 q_{t+1} + 2 q_{t-1} - q_{t-2}) / 2.  Either one nonzero
+   * widens the normal matrix to four block sub-diagonals. */
+  float w_acc5;       /* default 0 */
+  float w_jerk;       /* default 0 */
 } pk_trajopt_params;
 
 void pk_trajopt_params_default(pk_trajopt_params* p);
@@ -410,7 +417,8 @@ pk_status pk_trajopt_solve(const pk_robot* robot, const pk_trajopt_params* param
  * d_D_out [batch][T][n][n] (smoothness included), the first sub-diagonal
  * blocks (t, t-1) d_E_out [batch][T][n][n] (NULL: not written; block 0 is
  * zero), J^T r d_g_out [batch][T][n] and the cost d_cost_out [batch].  The
- * second sub-diagonal blocks are the acceleration term alone, w_acc^2 I.
+ * blocks further from the diagonal come from the smoothness rows alone and are
+ * scalar multiples of I: w_acc^2 I at offset 2 when w_acc5 = w_jerk = 0.
  */
 pk_status pk_trajopt_normal(const pk_robot* robot, const pk_trajopt_params* params, int32_t batch, int32_t T,
                             const float* d_q_start, const float* d_goal, const float* d_q,

@@ -295,6 +295,8 @@ void pk_trajopt_params_default(pk_trajopt_params* p) {
   p->w_vlimit = 0.f;
   p->v_max = 0.1f;
   p->w_swept = 0.f;
+  p->w_acc5 = 0.f;
+  p->w_jerk = 0.f;
 }
 
 static pk_status trajopt_common(const pk_robot* rb, const pk_trajopt_params* p, int32_t batch, int32_t T,
@@ -309,6 +311,7 @@ static pk_status trajopt_common(const pk_robot* rb, const pk_trajopt_params* p, 
   if (!(p->eta > 0.f)) return fail(PK_ERR_INVALID_ARG, "eta must be > 0");
   if (!(p->w_vlimit >= 0.f) || !(p->v_max >= 0.f) || !(p->w_swept >= 0.f))
     return fail(PK_ERR_INVALID_ARG, "w_vlimit, v_max and w_swept must be >= 0");
+  if (!(p->w_acc5 >= 0.f) || !(p->w_jerk >= 0.f)) return fail(PK_ERR_INVALID_ARG, "w_acc5 and w_jerk must be >= 0");
   if (T < 3 || T > pk::kTrajMaxT) return fail(PK_ERR_INVALID_ARG, "T must be in 3..%d", pk::kTrajMaxT);
   if (S < 1 || S > pk::kTrajMaxS) return fail(PK_ERR_INVALID_ARG, "spheres_per_link must be in 1..%d", pk::kTrajMaxS);
   if (n_obs < 0 || n_obs > pk::kTrajMaxObs) return fail(PK_ERR_INVALID_ARG, "n_obs must be in 0..%d", pk::kTrajMaxObs);
@@ -329,6 +332,7 @@ static pk_status trajopt_common(const pk_robot* rb, const pk_trajopt_params* p, 
   tp.iters = p->iters; tp.T = T; tp.S = S; tp.n_obs = n_obs;
   for (int i = 0; i < 4; ++i) tp.plane[i] = plane[i];
   tp.w_vlimit = p->w_vlimit; tp.v_max = p->v_max; tp.w_swept = p->w_swept;
+  tp.w_acc5 = p->w_acc5; tp.w_jerk = p->w_jerk;
   cudaError_t e = pk::launch_trajopt(ch, tp, batch, d_q_start, d_goal, d_q, d_radii, d_obs, d_q_out, d_cost_out,
                                      d_status_out, d_D_out, d_E_out, d_g_out, (cudaStream_t)stream);
   return e == cudaSuccess ? PK_OK : cuda_fail(e, "trajectory optimisation launch");

@@ -157,7 +157,7 @@ struct TrajParamsDev {
   float lambda0, lambda_min, lambda_max, nu, tol_pos, tol_rot;
   int32_t iters, T, S, n_obs;
   float plane[4];
-  float w_vlimit, v_max, w_swept;
+  float w_vlimit, v_max, w_swept, w_acc5, w_jerk;
 };
 
 cudaError_t launch_trajopt(const ChainHost& ch, const TrajParamsDev& tp, int batch, const float* q_start,

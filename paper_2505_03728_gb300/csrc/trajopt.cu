@@ -9,10 +9,11 @@
 // S spheres centred at p_j + (s + 1/2)/S (p_{j+1} - p_j).  LM (Sec. III-A) with
 // a fixed iteration count.
 //
-// The normal matrix is block pentadiagonal in t: collision, limit, start and
-// goal rows touch one timestep (full N x N diagonal blocks D_t), while the
-// smoothness rows add s_t I on the diagonal and the scalar multiples b_t I and
-// c_t I on the first and second sub-diagonals.  Per LM iteration:
+// The normal matrix is block banded in t with B = 2 block sub-diagonals
+// (B = 4 with the five-point stencils): collision, limit, start and goal rows
+// touch one timestep (full N x N diagonal blocks D_t), velocity-limit and swept
+// rows add full blocks E_t at (t, t-1), and the smoothness rows add scalar
+// multiples of I on the diagonal and every sub-diagonal.  Per LM iteration:
 //   1. timestep threads run FK, limits, smoothness, start and goal terms;
 //      warps then take timesteps and their lanes take link spheres, test them
 //      against every obstacle and the plane, and reduce the active rows' rank-1
@@ -33,7 +34,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-template <int N>
+template <int N, int B>
 struct TrajSmem {
   static constexpr int NT = N * (N + 1) / 2;
   float x[2][kTrajMaxT][8];    // current / candidate trajectories
@@ -45,8 +46,7 @@ struct TrajSmem {
   float p[kTrajMaxT][N + 1][3];  // joint origins and tool point (world), candidate
   float w[kTrajMaxT][N][3];      // joint axes (world), candidate
   float Linv[kTrajMaxT][NT];     // inverse of the diagonal Cholesky factor (lower)
-  float L1[kTrajMaxT][N][N];     // factor block (t, t-1)
-  float L2[kTrajMaxT][N][N];     // factor block (t, t-2)
+  float L[B][kTrajMaxT][N][N];   // L[k-1][t]: factor block (t, t-k)
   float M[N][N];
   float Sch[NT];
   float tmp[8];
@@ -88,9 +88,35 @@ __device__ __forceinline__ void smooth_scalars(const TrajParamsDev& tp, int t, f
   *c = a2 * in(t - 1) * (t >= 2 ? 1.f : 0.f);
 }
 
+// Five-point stencils over q_{u-2} .. q_{u+2}, rows u = 2..T-3: acceleration
+// (-1, 16, -30, 16, -1) / 12 and jerk (-1, 2, 0, -2, 1) / 2.
+__device__ __forceinline__ float acc5_coef(int k) {
+  return k == 2 ? -30.f / 12.f : (k == 1 || k == 3) ? 16.f / 12.f : -1.f / 12.f;
+}
+__device__ __forceinline__ float jerk_coef(int k) { return k == 2 ? 0.f : k == 1 ? 1.f : k == 3 ? -1.f : k == 0 ? -0.5f : 0.5f; }
+
+// All smoothness scalars of block row t: sb[k] multiplies I in block (t, t-k),
+// k = 0..B.
+template <int B>
+__device__ __forceinline__ void smooth_band(const TrajParamsDev& tp, int t, float* sb) {
+  smooth_scalars(tp, t, &sb[0], &sb[1], &sb[2]);
+  if constexpr (B == 4) {
+    sb[3] = sb[4] = 0.f;
+    const float wa2 = tp.w_acc5 * tp.w_acc5, wj2 = tp.w_jerk * tp.w_jerk;
+#pragma unroll
+    for (int du = -2; du <= 2; ++du) {  // row u = t + du holds q_t in slot o = 2 - du
+      const int u = t + du, o = 2 - du;
+      if (u < 2 || u > tp.T - 3) continue;
+#pragma unroll
+      for (int k = 0; k <= o; ++k)  // q_{t-k} sits in slot o - k
+        sb[k] += wa2 * acc5_coef(o) * acc5_coef(o - k) + wj2 * jerk_coef(o) * jerk_coef(o - k);
+    }
+  }
+}
+
 // Per-timestep terms (thread t): FK, limits, smoothness, start and goal.
-template <int N>
-__device__ void eval_timestep(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N>& S, int buf, int t,
+template <int N, int B>
+__device__ void eval_timestep(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N, B>& S, int buf, int t,
                               float& fpart) {
   constexpr int NT = N * (N + 1) / 2;
   const int T = tp.T;
@@ -182,6 +208,27 @@ __device__ void eval_timestep(const ChainC<N>& rc, const TrajParamsDev& tp, Traj
     if (t + 1 >= 1 && t + 1 <= T - 2) gj = fmaf(a2, xp2 - 2.f * xp + x0, gj);
     g[j] += gj;
   }
+  if constexpr (B == 4) {
+    // five-point rows u = t-2 .. t+2 that hold q_t; row t is owned by t
+    const float wa2 = tp.w_acc5 * tp.w_acc5, wj2 = tp.w_jerk * tp.w_jerk;
+#pragma unroll
+    for (int du = -2; du <= 2; ++du) {
+      const int u = t + du, o = 2 - du;
+      if (u < 2 || u > T - 3) continue;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        float ra = 0.f, rj = 0.f;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          const float xv = S.x[buf][u - 2 + k][j];
+          ra = fmaf(acc5_coef(k), xv, ra);
+          rj = fmaf(jerk_coef(k), xv, rj);
+        }
+        g[j] = fmaf(wa2 * acc5_coef(o), ra, fmaf(wj2 * jerk_coef(o), rj, g[j]));
+        if (du == 0) acc = fmaf(wa2, ra * ra, fmaf(wj2, rj * rj, acc));
+      }
+    }
+  }
   // velocity-limit hinge (Sec. III-C, dt = 1): the row (t, t-1) is owned by t;
   // t also takes its part of the row (t+1, t).  E_t is written whole here.
   float ed[N];
@@ -243,8 +290,8 @@ __device__ void eval_timestep(const ChainC<N>& rc, const TrajParamsDev& tp, Traj
     S.gpe[buf] = sqrtf(E.t[0] * E.t[0] + E.t[1] * E.t[1] + E.t[2] * E.t[2]);
     S.gre[buf] = th;
     const float wv[6] = {tp.w_goal_pos, tp.w_goal_pos, tp.w_goal_pos, tp.w_goal_rot, tp.w_goal_rot, tp.w_goal_rot};
-    float A[9], B[9];
-    se3_jlinv_blocks(xi, xi + 3, th, A, B);
+    float Ja[9], Jb[9];
+    se3_jlinv_blocks(xi, xi + 3, th, Ja, Jb);
     float J[6][N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
@@ -257,14 +304,14 @@ __device__ void eval_timestep(const ChainC<N>& rc, const TrajParamsDev& tp, Traj
       mat_vec(Gi.r, ww, wg);
       float top[3], bot[3];
       if (rc.prism & (1u << j)) {
-        mat_vec(A, wg, top);
+        mat_vec(Ja, wg, top);
         bot[0] = bot[1] = bot[2] = 0.f;
       } else {
         float v[3], t1[3], t2[3];
         cross3(pg, wg, v);
-        mat_vec(A, v, t1);
-        mat_vec(B, wg, t2);
-        mat_vec(A, wg, bot);
+        mat_vec(Ja, v, t1);
+        mat_vec(Jb, wg, t2);
+        mat_vec(Ja, wg, bot);
         top[0] = t1[0] + t2[0]; top[1] = t1[1] + t2[1]; top[2] = t1[2] + t2[2];
       }
 #pragma unroll
@@ -293,8 +340,8 @@ __device__ void eval_timestep(const ChainC<N>& rc, const TrajParamsDev& tp, Traj
 }
 
 // n . dc/dq_i for a point c carried by link l at timestep t (joints 0..l).
-template <int N>
-__device__ __forceinline__ void coll_jrow(const ChainC<N>& rc, const TrajSmem<N>& S, int t, int l, const float* c,
+template <int N, int B>
+__device__ __forceinline__ void coll_jrow(const ChainC<N>& rc, const TrajSmem<N, B>& S, int t, int l, const float* c,
                                           const float* nrm, float scale, float* jr) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -314,8 +361,8 @@ __device__ __forceinline__ void coll_jrow(const ChainC<N>& rc, const TrajSmem<N>
 }
 
 // Collision terms of timestep t, one link sphere per lane (lanes >= N*S idle).
-template <int N>
-__device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N>& S, int buf, int t,
+template <int N, int B>
+__device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N, B>& S, int buf, int t,
                                 int lane, float& fpart, float& mind) {
   constexpr int NT = N * (N + 1) / 2;
   const int nsph = N * tp.S;
@@ -355,7 +402,7 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
       const float r = wc * fa;
       fpart = fmaf(r, r, fpart);
       float jr[N];
-      coll_jrow<N>(rc, S, t, l, c, nrm, wc * df, jr);
+      coll_jrow<N, B>(rc, S, t, l, c, nrm, wc * df, jr);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         gl[i] = fmaf(jr[i], r, gl[i]);
@@ -409,8 +456,8 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
       const float inv = 1.f / len;
       const float nrm[3] = {v0 * inv, v1 * inv, v2 * inv};
       float a[N], bq[N];
-      coll_jrow<N>(rc, S, t, l, c0, nrm, tp.w_swept * df * (1.f - u), a);
-      coll_jrow<N>(rc, S, t + 1, l, c1, nrm, tp.w_swept * df * u, bq);
+      coll_jrow<N, B>(rc, S, t, l, c0, nrm, tp.w_swept * df * (1.f - u), a);
+      coll_jrow<N, B>(rc, S, t + 1, l, c1, nrm, tp.w_swept * df * u, bq);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         atomicAdd(&S.g[buf][t][i], a[i] * r);
@@ -428,13 +475,13 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
 }
 
 // Cost, J^T J diagonal blocks and J^T r of trajectory buffer `buf`.
-template <int N>
-__device__ void evaluate(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N>& S, int buf) {
+template <int N, int B>
+__device__ void evaluate(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N, B>& S, int buf) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float fpart = 0.f, mind = INFINITY;
-  for (int t = tid; t < tp.T; t += kThreads) eval_timestep<N>(rc, tp, S, buf, t, fpart);
+  for (int t = tid; t < tp.T; t += kThreads) eval_timestep<N, B>(rc, tp, S, buf, t, fpart);
   __syncthreads();
-  for (int t = warp; t < tp.T; t += kWarps) eval_collisions<N>(rc, tp, S, buf, t, lane, fpart, mind);
+  for (int t = warp; t < tp.T; t += kWarps) eval_collisions<N, B>(rc, tp, S, buf, t, lane, fpart, mind);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     fpart += __shfl_xor_sync(0xffffffffu, fpart, o);
@@ -457,57 +504,82 @@ __device__ void evaluate(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<
   __syncthreads();
 }
 
-// Block-banded Cholesky of D[buf] + smoothness + lambda I, then the two block
-// substitutions for dq = -(A)^-1 g; the step lands in S.y.  Returns false if a
-// diagonal block was not positive definite.
-template <int N>
-__device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N>& S, int buf, float lam) {
+// Block-banded Cholesky of D[buf] + smoothness + lambda I (B block
+// sub-diagonals), then the two block substitutions for dq = -(A)^-1 g; the
+// step lands in S.y.  Block row t of the factor:
+//   L_{t,t-k} = (A_{t,t-k} - sum_{m=k+1..B} L_{t,t-m} L_{t-k,t-m}^T) Linv_{t-k}^T,
+// k = B down to 1 (A_{t,t-B} is a scalar multiple of I, so the top block is a
+// scaled transposed inverse), then the Schur complement
+//   A_tt - sum_k L_{t,t-k} L_{t,t-k}^T
+// is factored densely.  Returns false if a diagonal block was not positive
+// definite.
+template <int N, int B>
+__device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B>& S, int buf, float lam) {
   constexpr int NT = N * (N + 1) / 2;
   const int tid = threadIdx.x, T = tp.T;
   if (tid == 0) S.chol_fail = 0;
   for (int t = 0; t < T; ++t) {
-    float sd, bd, cd;
-    smooth_scalars(tp, t, &sd, &bd, &cd);
-    // (1) L2_t = c_t Linv_{t-2}^T and M = b_t I - L2_t L1_{t-1}^T
-    if (tid < N * N && t >= 1) {
+    float sb[B + 1];
+    smooth_band<B>(tp, t, sb);
+    // (1) L_{t,t-B} = sb[B] Linv_{t-B}^T (kept inline) and M = A_{t,t-B+1} - L_{t,t-B} L_{t-B+1,t-B}^T
+    if (tid < N * N && t >= B - 1) {
       const int i = tid / N, j = tid % N;
-      float m = ((i == j) ? bd : 0.f) + S.E[buf][t][i][j];
-      if (t >= 2) {
-        S.L2[t][i][j] = (j >= i) ? cd * S.Linv[t - 2][tri(j, i)] : 0.f;
+      const float cb = sb[B];
+      float m = ((i == j) ? sb[B - 1] : 0.f);
+      if constexpr (B == 2) m += S.E[buf][t][i][j];
+      if (t >= B) {
+        S.L[B - 1][t][i][j] = (j >= i) ? cb * S.Linv[t - B][tri(j, i)] : 0.f;
 #pragma unroll
         for (int k = 0; k < N; ++k)
-          if (k >= i) m = fmaf(-cd * S.Linv[t - 2][tri(k, i)], S.L1[t - 1][j][k], m);
+          if (k >= i) m = fmaf(-cb * S.Linv[t - B][tri(k, i)], S.L[0][t - B + 1][j][k], m);
       }
       S.M[i][j] = m;
     }
     __syncthreads();
-    // (2) L1_t = M Linv_{t-1}^T
-    if (tid < N * N && t >= 1) {
-      const int i = tid / N, j = tid % N;
-      float v = 0.f;
 #pragma unroll
-      for (int k = 0; k < N; ++k)
-        if (k <= j) v = fmaf(S.M[i][k], S.Linv[t - 1][tri(j, k)], v);
-      S.L1[t][i][j] = v;
+    for (int k = B - 1; k >= 1; --k) {
+      if (k < B - 1) {
+        // M = A_{t,t-k} - sum_{m > k} L_{t,t-m} L_{t-k,t-m}^T
+        if (tid < N * N && t >= k) {
+          const int i = tid / N, j = tid % N;
+          float m = ((i == j) ? sb[k] : 0.f);
+          if (k == 1) m += S.E[buf][t][i][j];
+#pragma unroll
+          for (int mm = k + 1; mm <= B; ++mm)
+            if (t >= mm)
+#pragma unroll
+              for (int l = 0; l < N; ++l) m = fmaf(-S.L[mm - 1][t][i][l], S.L[mm - k - 1][t - k][j][l], m);
+          S.M[i][j] = m;
+        }
+        __syncthreads();
+      }
+      // L_{t,t-k} = M Linv_{t-k}^T
+      if (tid < N * N && t >= k) {
+        const int i = tid / N, j = tid % N;
+        float v = 0.f;
+#pragma unroll
+        for (int l = 0; l < N; ++l)
+          if (l <= j) v = fmaf(S.M[i][l], S.Linv[t - k][tri(j, l)], v);
+        S.L[k - 1][t][i][j] = v;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    // (3) Schur complement S = D_t + (s_t + lambda) I - L1 L1^T - L2 L2^T (lower)
+    // Schur complement A_tt + lambda I - sum_k L_{t,t-k} L_{t,t-k}^T (lower)
     if (tid < NT) {
       int i = 0;
       while ((i + 1) * (i + 2) / 2 <= tid) ++i;
       const int j = tid - i * (i + 1) / 2;
-      float v = S.D[buf][t][tid] + ((i == j) ? sd + lam : 0.f);
-      if (t >= 1)
+      float v = S.D[buf][t][tid] + ((i == j) ? sb[0] + lam : 0.f);
 #pragma unroll
-        for (int k = 0; k < N; ++k) v = fmaf(-S.L1[t][i][k], S.L1[t][j][k], v);
-      if (t >= 2)
+      for (int k = 1; k <= B; ++k)
+        if (t >= k)
 #pragma unroll
-        for (int k = 0; k < N; ++k) v = fmaf(-S.L2[t][i][k], S.L2[t][j][k], v);
+          for (int l = 0; l < N; ++l) v = fmaf(-S.L[k - 1][t][i][l], S.L[k - 1][t][j][l], v);
       S.Sch[tid] = v;
     }
     __syncthreads();
-    // (4) dense Cholesky of the Schur complement (lane 0), then its inverse
-    //     (lane j computes column j)
+    // dense Cholesky of the Schur complement (lane 0), then its inverse
+    // (lane j computes column j)
     if (tid == 0) {
       float L[NT];
 #pragma unroll
@@ -536,16 +608,15 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N>& S, int buf, f
     __syncthreads();
   }
   const bool ok = S.chol_fail == 0;
-  // forward substitution: y_t = Linv_t (-g_t - L1_t y_{t-1} - L2_t y_{t-2})
+  // forward substitution: y_t = Linv_t (-g_t - sum_k L_{t,t-k} y_{t-k})
   for (int t = 0; t < T; ++t) {
     if (tid < N) {
       float v = -S.g[buf][t][tid];
-      if (t >= 1)
 #pragma unroll
-        for (int k = 0; k < N; ++k) v = fmaf(-S.L1[t][tid][k], S.y[t - 1][k], v);
-      if (t >= 2)
+      for (int k = 1; k <= B; ++k)
+        if (t >= k)
 #pragma unroll
-        for (int k = 0; k < N; ++k) v = fmaf(-S.L2[t][tid][k], S.y[t - 2][k], v);
+          for (int l = 0; l < N; ++l) v = fmaf(-S.L[k - 1][t][tid][l], S.y[t - k][l], v);
       S.tmp[tid] = v;
     }
     __syncthreads();
@@ -558,16 +629,15 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N>& S, int buf, f
     }
     __syncthreads();
   }
-  // backward substitution: dq_t = Linv_t^T (y_t - L1_{t+1}^T dq_{t+1} - L2_{t+2}^T dq_{t+2})
+  // backward substitution: dq_t = Linv_t^T (y_t - sum_k L_{t+k,t}^T dq_{t+k})
   for (int t = T - 1; t >= 0; --t) {
     if (tid < N) {
       float v = S.y[t][tid];
-      if (t + 1 < T)
 #pragma unroll
-        for (int k = 0; k < N; ++k) v = fmaf(-S.L1[t + 1][k][tid], S.y[t + 1][k], v);
-      if (t + 2 < T)
+      for (int k = 1; k <= B; ++k)
+        if (t + k < T)
 #pragma unroll
-        for (int k = 0; k < N; ++k) v = fmaf(-S.L2[t + 2][k][tid], S.y[t + 2][k], v);
+          for (int l = 0; l < N; ++l) v = fmaf(-S.L[k - 1][t + k][l][tid], S.y[t + k][l], v);
       S.tmp[tid] = v;
     }
     __syncthreads();
@@ -583,7 +653,7 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N>& S, int buf, f
   return ok;
 }
 
-template <int N>
+template <int N, int B>
 __global__ void __launch_bounds__(kThreads) trajopt_kernel(
     const __grid_constant__ ChainC<N> rc, const __grid_constant__ TrajParamsDev tp, const float* __restrict__ q_start,
     const float* __restrict__ goals, const float* __restrict__ q_init, const float* __restrict__ radii,
@@ -591,7 +661,7 @@ __global__ void __launch_bounds__(kThreads) trajopt_kernel(
     int32_t* __restrict__ status_out, float* __restrict__ D_out, float* __restrict__ E_out,
     float* __restrict__ g_out) {
   extern __shared__ float4 smem_f4[];
-  TrajSmem<N>& S = *reinterpret_cast<TrajSmem<N>*>(smem_f4);
+  TrajSmem<N, B>& S = *reinterpret_cast<TrajSmem<N, B>*>(smem_f4);
   const int b = blockIdx.x, tid = threadIdx.x, T = tp.T;
   // inputs
   for (int i = tid; i < T * N; i += kThreads) S.x[0][i / N][i % N] = q_init[(size_t)b * T * N + i];
@@ -605,22 +675,22 @@ __global__ void __launch_bounds__(kThreads) trajopt_kernel(
     rt_store(S.Tgi, Gi);
   }
   __syncthreads();
-  evaluate<N>(rc, tp, S, 0);
+  evaluate<N, B>(rc, tp, S, 0);
   if (D_out) {
     // normal equations only: full diagonal blocks (smoothness included) and J^T r
     for (int i = tid; i < T * N * N; i += kThreads) {
       const int t = i / (N * N), r = (i / N) % N, c = i % N;
-      float sd, bd, cd;
-      smooth_scalars(tp, t, &sd, &bd, &cd);
+      float sb[B + 1];
+      smooth_band<B>(tp, t, sb);
       const float v = (r >= c) ? S.D[0][t][tri(r, c)] : S.D[0][t][tri(c, r)];
-      D_out[(size_t)b * T * N * N + i] = v + ((r == c) ? sd : 0.f);
+      D_out[(size_t)b * T * N * N + i] = v + ((r == c) ? sb[0] : 0.f);
     }
     if (E_out)
       for (int i = tid; i < T * N * N; i += kThreads) {
         const int t = i / (N * N), r = (i / N) % N, c = i % N;
-        float sd, bd, cd;
-        smooth_scalars(tp, t, &sd, &bd, &cd);
-        E_out[(size_t)b * T * N * N + i] = t >= 1 ? S.E[0][t][r][c] + ((r == c) ? bd : 0.f) : 0.f;
+        float sb[B + 1];
+        smooth_band<B>(tp, t, sb);
+        E_out[(size_t)b * T * N * N + i] = t >= 1 ? S.E[0][t][r][c] + ((r == c) ? sb[1] : 0.f) : 0.f;
       }
     for (int i = tid; i < T * N; i += kThreads) g_out[(size_t)b * T * N + i] = S.g[0][i / N][i % N];
     if (tid == 0) cost_out[b] = S.f[0];
@@ -629,12 +699,12 @@ __global__ void __launch_bounds__(kThreads) trajopt_kernel(
   int u = 0;  // buffer of the accepted trajectory
   float lam = tp.lambda0;
   for (int it = 0; it < tp.iters; ++it) {
-    const bool ok = banded_solve<N>(tp, S, u, lam);
+    const bool ok = banded_solve<N, B>(tp, S, u, lam);
     if (ok) {
       const int c = u ^ 1;
       for (int i = tid; i < T * N; i += kThreads) S.x[c][i / N][i % N] = S.x[u][i / N][i % N] + S.y[i / N][i % N];
       __syncthreads();
-      evaluate<N>(rc, tp, S, c);
+      evaluate<N, B>(rc, tp, S, c);
       if (S.f[c] < S.f[u]) {
         u = c;
         lam = fmaxf(lam / tp.nu, tp.lambda_min);
@@ -656,21 +726,21 @@ __global__ void __launch_bounds__(kThreads) trajopt_kernel(
   }
 }
 
-template <int N>
+template <int N, int B>
 cudaError_t trajopt_launch(const ChainHost& ch, const TrajParamsDev& tp, int batch, const float* q_start,
                            const float* goals, const float* q_init, const float* radii, const float* obs,
                            float* q_out, float* cost_out, int32_t* status_out, float* D_out, float* E_out,
                            float* g_out, cudaStream_t st) {
-  const size_t smem = sizeof(TrajSmem<N>);
+  const size_t smem = sizeof(TrajSmem<N, B>);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(trajopt_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(trajopt_kernel<N, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const ChainC<N> rc = chain_const<N>(ch);
   TraceScope tr("trajopt", st);
-  trajopt_kernel<N><<<batch, kThreads, smem, st>>>(rc, tp, q_start, goals, q_init, radii, obs, q_out, cost_out,
+  trajopt_kernel<N, B><<<batch, kThreads, smem, st>>>(rc, tp, q_start, goals, q_init, radii, obs, q_out, cost_out,
                                                    status_out, D_out, E_out, g_out);
   return cudaGetLastError();
 }
@@ -681,11 +751,19 @@ cudaError_t launch_trajopt(const ChainHost& ch, const TrajParamsDev& tp, int bat
                            const float* goals, const float* q_init, const float* radii, const float* obs,
                            float* q_out, float* cost_out, int32_t* status_out, float* D_out, float* E_out,
                            float* g_out, cudaStream_t st) {
-  switch (ch.n) {
-    case 6: return trajopt_launch<6>(ch, tp, batch, q_start, goals, q_init, radii, obs, q_out, cost_out, status_out, D_out, E_out, g_out, st);
-    case 7: return trajopt_launch<7>(ch, tp, batch, q_start, goals, q_init, radii, obs, q_out, cost_out, status_out, D_out, E_out, g_out, st);
+  // four block sub-diagonals only when a five-point stencil is on (the
+  // band-2 layout keeps two CTAs per SM)
+  const bool b4 = tp.w_acc5 != 0.f || tp.w_jerk != 0.f;
+#define PK_TRAJ_ARGS ch, tp, batch, q_start, goals, q_init, radii, obs, q_out, cost_out, status_out, D_out, E_out, g_out, st
+  switch (ch.n * 8 + (b4 ? 4 : 2)) {
+    case 6 * 8 + 2: return trajopt_launch<6, 2>(PK_TRAJ_ARGS);
+    case 6 * 8 + 4: return trajopt_launch<6, 4>(PK_TRAJ_ARGS);
+    case 7 * 8 + 2: return trajopt_launch<7, 2>(PK_TRAJ_ARGS);
+    case 7 * 8 + 4: return trajopt_launch<7, 4>(PK_TRAJ_ARGS);
     default: return cudaErrorInvalidValue;
   }
 }
+
+#undef PK_TRAJ_ARGS
 
 }  // namespace pk

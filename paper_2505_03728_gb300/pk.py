@@ -64,7 +64,7 @@ class pk_trajopt_params(C.Structure):
                 ("eta", C.c_float), ("lambda0", C.c_float), ("lambda_min", C.c_float),
                 ("lambda_max", C.c_float), ("nu", C.c_float), ("tol_pos", C.c_float), ("tol_rot", C.c_float),
                 ("iters", C.c_int32), ("reserved", C.c_int32), ("w_vlimit", C.c_float), ("v_max", C.c_float),
-                ("w_swept", C.c_float)]
+                ("w_swept", C.c_float), ("w_acc5", C.c_float), ("w_jerk", C.c_float)]
 
 
 class pk_train_params(C.Structure):

@@ -55,7 +55,8 @@ def setup(B, T=64, perturb=0.0, seed=0):
 def oparams(p, banded=1):
     return oracle.TrajParams(p.w_start, p.w_goal_pos, p.w_goal_rot, p.w_vel, p.w_acc, p.w_limit, p.w_coll,
                              p.eta, p.lambda0, p.lambda_min, p.lambda_max, p.nu, p.iters, banded,
-                             w_vlimit=p.w_vlimit, v_max=p.v_max, w_swept=p.w_swept)
+                             w_vlimit=p.w_vlimit, v_max=p.v_max, w_swept=p.w_swept,
+                             w_acc5=p.w_acc5, w_jerk=p.w_jerk)
 
 
 @pytest.mark.parametrize("T", [3, 17, 64])

@@ -1,7 +1,9 @@
 """GPU trajectory extensions against the FP64 oracle: the velocity-limit hinge
 (Sec. III-C) and swept-sphere collision between consecutive timesteps
 (Sec. IV-B), whose rows couple q_t and q_{t+1} and fill the (t, t-1) blocks of
-the normal matrix.  Tolerances as in test_gpu_trajopt.py."""
+the normal matrix, and the five-point acceleration and jerk stencils
+(Sec. III-C smoothness), which widen the normal matrix to four block
+sub-diagonals.  Tolerances as in test_gpu_trajopt.py."""
 import numpy as np
 import pytest
 import torch
@@ -72,3 +74,66 @@ def test_velocity_limit_bounds_the_steps():
     print(f"largest joint step: without the limit {np.median(out[0.0]):.3f}, with it {np.median(out[30.0]):.3f}")
     assert np.median(out[30.0]) < np.median(out[0.0])
     assert np.median(out[30.0]) <= vmax * 1.5
+
+
+FIVE = dict(w_acc5=2.0, w_jerk=3.0)
+
+
+@pytest.mark.parametrize("T", [3, 5, 17, 64])
+def test_normal_equations_with_five_point_stencils_match_oracle(T):
+    o, g, qs, goals, x0, radii, obs, plane, scene = setup(6, T, perturb=0.1, seed=40 + T)
+    p = pk.pk_trajopt_params_default(**FIVE, **EXT)
+    D, gg, cost, E = [x.cpu().numpy().astype(np.float64) for x in
+                      pk.pk_trajopt_normal(g, p, dev(qs), dev(goals), dev(x0), dev(radii), dev(obs), plane,
+                                           with_offdiag=True)]
+    op = oparams(p)
+    n = 7
+    for b in range(6):
+        f, A, gr = oracle.traj_normal(o, op, scene, x0[b], qs[b], goals[b])
+        scale = np.abs(A).max()
+        for t in range(T):
+            np.testing.assert_allclose(D[b, t], A[t * n:(t + 1) * n, t * n:(t + 1) * n], atol=1e-4 * scale)
+            if t >= 1:
+                np.testing.assert_allclose(E[b, t], A[t * n:(t + 1) * n, (t - 1) * n:t * n], atol=1e-4 * scale)
+        np.testing.assert_allclose(gg[b].ravel(), gr, atol=1e-4 * max(1.0, np.abs(gr).max()))
+        assert abs(cost[b] - f) <= 1e-4 * max(1.0, f)
+    if T >= 7:  # the oracle's band reaches four blocks, as the kernel's factorisation assumes
+        assert np.abs(A[6 * n:7 * n, 2 * n:3 * n]).max() > 0 and np.abs(A[6 * n:7 * n, :2 * n]).max() == 0
+
+
+@pytest.mark.parametrize("ext", [False, True], ids=["five_point", "five_point_vlimit_swept"])
+def test_one_step_with_five_point_stencils_matches_oracle(ext):
+    o, g, qs, goals, x0, radii, obs, plane, scene = setup(16, 64, perturb=0.05, seed=2)
+    kw = dict(FIVE, **(EXT if ext else {}))
+    for start_iters in (0, 5):
+        start = x0 if start_iters == 0 else oracle.traj_solve(
+            o, oparams(pk.pk_trajopt_params_default(iters=5, **kw)), scene, x0, qs, goals)["x"]
+        ref = oracle.traj_solve(o, oparams(pk.pk_trajopt_params_default(iters=1, **kw)), scene, start, qs, goals,
+                                n_trace=True)
+        q = pk.pk_trajopt_solve(g, pk.pk_trajopt_params_default(iters=1, **kw), dev(qs), dev(goals), dev(start),
+                                dev(radii), dev(obs), plane)[0].cpu().numpy()
+        tie = ref["margin"] <= 1e-5
+        rel = (np.abs(q - ref["x"]) / np.maximum(1.0, np.abs(ref["x"]))).reshape(16, -1).max(axis=1)
+        assert np.all(rel[~tie] <= 5e-3), (ext, start_iters, rel)
+        assert np.median(rel[~tie]) <= 1e-3, (ext, start_iters, rel)
+        assert tie.sum() <= 2
+
+
+def jerk(q):
+    return 0.5 * (q[:, 4:] - 2 * q[:, 3:-1] + 2 * q[:, 1:-3] - q[:, :-4])
+
+
+def test_jerk_stencil_smooths_the_solution():
+    o, g, qs, goals, x0, radii, obs, plane, scene = setup(32, 32)
+    out = {}
+    for w in (0.0, 20.0):
+        p = pk.pk_trajopt_params_default(iters=50, w_jerk=w)
+        q, cost, st = [x.cpu().numpy() for x in
+                       pk.pk_trajopt_solve(g, p, dev(qs), dev(goals), dev(x0), dev(radii), dev(obs), plane)]
+        out[w] = (np.sqrt((jerk(q.astype(np.float64)) ** 2).sum(axis=(1, 2))), st)
+    j0, j1 = np.median(out[0.0][0]), np.median(out[20.0][0])
+    print(f"jerk norm: without the stencil {j0:.4f}, with it {j1:.4f}")
+    assert j1 < 0.5 * j0  # the FP64 oracle on the same problems: 1.03e-2 -> 1.9e-3
+    # the goal is held as well as without the stencil
+    hit = {w: ((st & pk.PK_T_GOAL_MISSED) == 0).mean() for w, (_, st) in out.items()}
+    assert hit[20.0] >= hit[0.0] - 0.1, hit
