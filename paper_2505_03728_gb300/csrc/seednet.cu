@@ -22,6 +22,7 @@
 
 #include "pk_internal.h"
 #include "pk_math.cuh"
+#include "mlp_fused.cuh"
 #include "tc_gemm.cuh"
 
 using pk::tc::Epilogue;
@@ -802,6 +803,66 @@ pk_status pk_seednet_forward(pk_seednet* s, int32_t batch, const float* d_target
   return sn_cuda(e, "pk_seednet_forward");
 }
 
+namespace {
+
+// The whole-network kernel takes widths 256 and 512 (the accumulator fits
+// TMEM's 512 columns), inputs up to 256 and head outputs up to 256 wide.
+// PK_SEEDNET_FUSED=0 selects the layer-by-layer GEMMs instead.
+bool fused_ok(const pk_seednet* s) {
+  const char* env = getenv("PK_SEEDNET_FUSED");
+  if (env && env[0] == '0') return false;
+  return (s->width == 256 || s->width == 512) && s->in_pad <= 256 && s->out_pad <= 256 &&
+         s->L <= pk::tc::kMlpMaxLayers;
+}
+
+cudaError_t infer_fused(pk_seednet* s, int batch, const float* d_targets, float* d_seeds_out, cudaStream_t st) {
+  using namespace pk::tc;
+  static int sms = 0, max_smem = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaError_t e = cudaFuncSetAttribute(mlp_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess) return e;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  MlpParams p{};
+  p.n_layers = s->L;
+  p.width = s->width;
+  p.in_pad = s->in_pad;
+  p.out_pad = s->out_pad;
+  p.out_dim = s->out_dim;
+  p.n_dof = s->n_dof;
+  p.k = s->k;
+  p.batch = batch;
+  p.tiles = (batch + kBM - 1) / kBM;
+  // weight ring: as deep as shared memory allows (PK_MLP_STAGES caps it, for tuning sweeps)
+  const int room = max_smem - MlpSmem::bytes(s->width, 0);
+  int cap = kMlpMaxStages;
+  if (const char* env = getenv("PK_MLP_STAGES")) cap = atoi(env) > 1 ? atoi(env) : 2;
+  if (cap > kMlpMaxStages) cap = kMlpMaxStages;
+  p.stages = room / kMlpStageBytes < cap ? room / kMlpStageBytes : cap;
+  if (p.stages < 2) return cudaErrorInvalidConfiguration;
+  MlpMaps maps;
+  for (int l = 0; l < s->L; ++l) {
+    const int box = s->dout[l] < kMlpChunk ? s->dout[l] : kMlpChunk;
+    if (!make_map(&maps.w[l], s->W[l], s->dout[l], s->din[l], box)) return cudaErrorInvalidValue;
+    p.bias[l] = s->master + s->b_off[l];
+  }
+  p.lohi = s->d_lohi;
+  p.targets = d_targets;
+  p.seeds = d_seeds_out;
+  int grid = p.tiles < sms ? p.tiles : sms;
+  if (const char* env = getenv("PK_MLP_GRID"))  // persistent grid size, for tuning sweeps
+    if (atoi(env) > 0 && atoi(env) < grid) grid = atoi(env);
+  pk::TraceScope tr("seednet_mlp", st);
+  mlp_fused_kernel<<<grid, kMlpThreads, MlpSmem::bytes(s->width, p.stages), st>>>(maps, p, s->d_err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 pk_status pk_seednet_infer(pk_seednet* s, int32_t batch, const float* d_targets, float* d_seeds_out,
                            void* stream) {
   if (!s) return sn_fail(PK_ERR_INVALID_ARG, "net is NULL");
@@ -809,6 +870,7 @@ pk_status pk_seednet_infer(pk_seednet* s, int32_t batch, const float* d_targets,
   if (batch == 0) return PK_OK;
   if (!d_targets || !d_seeds_out) return sn_fail(PK_ERR_INVALID_ARG, "NULL device buffer");
   cudaStream_t st = (cudaStream_t)stream;
+  if (fused_ok(s)) return sn_cuda(infer_fused(s, batch, d_targets, d_seeds_out, st), "pk_seednet_infer");
   const int m_pad = round_up(batch, 128);
   pk_status ps = ensure_acts(s, m_pad);
   if (ps != PK_OK) return ps;
