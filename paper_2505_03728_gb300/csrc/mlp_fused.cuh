@@ -2,31 +2,35 @@
 // the joint-limit head) in one persistent tcgen05 kernel.
 //
 // The layer-by-layer GEMMs write each 128 x width activation tile to global
-// memory and read it back for the next layer; at the inference batch that
-// round trip costs as much as the MMAs.  Here a CTA keeps its 128-row tile's
-// activations in shared memory for the whole network:
+// memory and read it back for the next layer.  Here a CTA keeps its 128-row
+// tile's activations in tensor memory for the whole network and feeds them
+// to the MMA as the A operand straight from TMEM:
 //
-//   ACT (shared)  [width / 64 K-blocks][128 rows][64 BF16], 128B-swizzled,
-//                 exactly the K-major layout the MMA descriptor reads;
-//   TMEM          the layer's FP32 accumulator, 128 lanes x width columns
-//                 (two 256-column chunks at width 512);
-//   ring          weight tiles [256 outputs][64 K] streamed by TMA from L2.
+//   TMEM columns [256, 512)  ACT: row r in lane r, inputs 2c, 2c+1 packed in
+//                            column 256 + c (BF16 pairs; up to 512 inputs);
+//   TMEM columns [0, 256)    two FP32 accumulators of 128 columns, used by
+//                            the output chunks (128 features) in turn;
+//   shared memory            a ring of weight tiles [128 outputs][256 K]
+//                            (64 KB, one 3-D TMA box of four 128B-swizzled
+//                            K-blocks), and the head's output staging.
 //
-// Warp 0 / lane 0 streams the weights of every (tile, layer, chunk, K-block)
-// in MMA order; warp 1 / lane 0 issues tcgen05.mma (M = 128, N = 256 or the
-// head width, K = 16) chunk by chunk; eight epilogue warps read a finished
-// chunk from TMEM, add the bias and apply SiLU, and write the BF16 result
-// back into ACT as the next layer's A operand.  A chunk's results can only be
-// written once every MMA of the layer has finished reading ACT, so the first
-// chunk's results wait in registers while the MMAs of the second chunk run,
-// and the next layer's MMAs over the first 256 inputs start while the
-// epilogue still works on the second chunk.  The head writes
-// q = mid + half tanh(y) straight to global memory; the next tile's features
-// are computed in the same warps.
+// Large weight boxes matter: a TMA request costs a roughly fixed few hundred
+// cycles up to 32 KB, so 64 KB requests keep the ring ahead of the MMAs.
 //
-// Arithmetic per element is the layer-by-layer path's (same MMA shapes and
-// K order, same SiLU and head formulas), so both give the same seeds.  Every
-// mbarrier wait is bounded as in tc_gemm.cuh.
+// Warp 0 / lane 0 streams the weights of every (tile, layer, chunk, stage) in
+// MMA order; warp 1 / lane 0 issues tcgen05.mma (M = 128, N = 128, K = 16, A
+// from TMEM, B from shared memory); eight epilogue warps (two per TMEM lane
+// quarter, 64 columns each) read a finished accumulator, add the bias and
+// apply SiLU.  A layer's outputs can only replace ACT once every MMA of the
+// layer has read it, so the first chunks wait in registers (BF16) and are
+// stored to TMEM when the last chunk is done; the next layer's first stage
+// (inputs 0..255) starts as soon as those are written.  The head writes
+// q = mid + half tanh(y) through a shared-memory staging tile; the next
+// tile's features are written into ACT right after the head's last MMA.
+//
+// Arithmetic per element is the layer-by-layer path's (same MMA K order,
+// same SiLU and head formulas).  Every mbarrier wait is bounded as in
+// tc_gemm.cuh.
 #pragma once
 #include "tc_gemm.cuh"
 
@@ -34,22 +38,24 @@ namespace pk {
 namespace tc {
 
 constexpr int kMlpMaxLayers = 9;
-constexpr int kMlpChunk = 256;                        // accumulator chunk = MMA N of hidden layers
-constexpr int kMlpStageBytes = kMlpChunk * kBK * 2;   // one weight tile, 32 KB
-constexpr int kMlpBlockBytes = kBM * kBK * 2;         // one ACT K-block, 16 KB
+constexpr int kMlpChunk = 128;                    // output features per accumulator chunk (MMA N)
+constexpr int kMlpStageK = 4;                     // K-blocks of 64 per weight stage
+constexpr int kMlpStageBytes = kMlpChunk * kMlpStageK * kBK * 2;  // 64 KB
 constexpr int kMlpEpiWarps = 8;
 constexpr int kMlpThreads = 64 + 32 * kMlpEpiWarps;
-constexpr int kMlpMaxStages = 6;
+constexpr int kMlpMaxStages = 3;
 constexpr uint32_t kMlpTmemCols = 512;
+constexpr uint32_t kMlpActCol = 256;              // first TMEM column of ACT
 
 struct MlpMaps {
-  CUtensorMap w[kMlpMaxLayers];  // W_l [dout_l][din_l] BF16, boxes of 64 K x min(256, dout_l) rows
+  // W_l viewed as [din_l / 64][dout_l][64] BF16: 3-D boxes of 64 x rows x K-blocks
+  CUtensorMap w[kMlpMaxLayers];
 };
 
 struct MlpParams {
   int n_layers;    // hidden layers + head
   int width;       // 256 or 512
-  int in_pad;      // input features padded to a multiple of 64, <= width
+  int in_pad;      // input features padded to a multiple of 64, <= 256
   int out_pad;     // head outputs padded to a multiple of 64, <= 256
   int out_dim;     // K * n_dof real head outputs
   int n_dof;
@@ -57,6 +63,9 @@ struct MlpParams {
   int batch;
   int tiles;       // ceil(batch / 128)
   int stages;      // weight ring depth
+  int stage_bytes; // ring slot size
+  int head_rows;   // output features per head chunk (64 or 128)
+  int staged;      // head outputs through the shared-memory staging tile
   const float* bias[kMlpMaxLayers];
   const float* lohi;     // joint limits [2][n_dof]
   const float* targets;  // [batch][k][12]
@@ -64,13 +73,50 @@ struct MlpParams {
 };
 
 struct MlpSmem {
-  static constexpr int act_bytes(int width) { return width / kBK * kMlpBlockBytes; }
-  static constexpr int bar_offset(int width, int stages) { return act_bytes(width) + stages * kMlpStageBytes; }
-  static constexpr int bytes(int width, int stages) { return bar_offset(width, stages) + 256 + 1024; }
+  static constexpr int staging_bytes(int out_dim) { return kBM * out_dim * 4; }
+  static constexpr int bar_offset(int stages, int stage_bytes, int staging) {
+    return stages * stage_bytes + ((staging + 1023) & ~1023);
+  }
+  static constexpr int bytes(int stages, int stage_bytes, int staging) {
+    return bar_offset(stages, stage_bytes, staging) + 256 + 1024;
+  }
 };
 
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+          "r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// D (TMEM) (+)= A (TMEM) * B (shared memory descriptor)^T
+__device__ __forceinline__ void mma_bf16_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                                uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// 32 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // BF16 SiLU of 32 accumulator columns; the arithmetic of epilogue_silu32.
-__device__ __forceinline__ void silu_pack32(const float* bias, const uint32_t (&r)[32], uint32_t* packed) {
+__device__ __forceinline__ void silu_pack32(const float* bias, const uint32_t (&r)[32], uint32_t (&packed)[16]) {
   const uint64_t half2 = f32x2(0.5f, 0.5f);
   const float2* b2 = reinterpret_cast<const float2*>(bias);
 #pragma unroll
@@ -86,21 +132,26 @@ __device__ __forceinline__ void silu_pack32(const float* bias, const uint32_t (&
   }
 }
 
-// 32 BF16 values (inputs n0 .. n0 + 31, n0 a multiple of 32) of tile row r
-// into ACT: K-block n0 / 64, 16-byte chunks (n0 % 64) / 8 .. + 3, each at its
-// 128B-swizzled position (chunk index XOR row % 8).
-__device__ __forceinline__ void act_store32(uint8_t* act, int r, int n0, const uint32_t* packed) {
-  uint8_t* row = act + (n0 >> 6) * kMlpBlockBytes + r * 128;
-  const int c0 = (n0 & 63) >> 3;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-    *reinterpret_cast<uint4*>(row + (((c0 + i) ^ (r & 7)) << 4)) =
-        make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2], packed[4 * i + 3]);
+// This warp's 64 columns (col, col + 32) of an accumulator -> registers, then
+// `release` (the MMA may reuse the buffer) -> SiLU with bias -> 32 BF16 pairs.
+template <class F>
+__device__ __forceinline__ void chunk_silu(uint32_t taddr, const float* bias, uint32_t (&out)[32], F&& release) {
+  uint32_t ra[32];
+  uint32_t (&lo)[16] = *reinterpret_cast<uint32_t(*)[16]>(&out[0]);
+  uint32_t (&hi)[16] = *reinterpret_cast<uint32_t(*)[16]>(&out[16]);
+  tmem_ld32_issue(taddr, ra);
+  tmem_ld_wait(ra);
+  silu_pack32(bias, ra, lo);
+  tmem_ld32_issue(taddr + 32, ra);
+  tmem_ld_wait(ra);
+  release();
+  silu_pack32(bias + 32, ra, hi);
 }
 
-// Pose features of one row (position, first two rotation columns per target;
-// zero past 9 k and for rows past the batch) into ACT K-blocks 0 .. in_pad/64.
-__device__ __forceinline__ void act_features(uint8_t* act, const MlpParams& p, int tile, int r) {
+// Pose features of tile row r (position, first two rotation columns per
+// target; zero past 9 k and for rows past the batch), packed BF16 pairs,
+// into ACT columns 0 .. in_pad / 2 of this thread's lane.
+__device__ __forceinline__ void act_features(uint32_t act_lane, const MlpParams& p, int tile, int r) {
   const int row = tile * kBM + r;
   const bool ok = row < p.batch;
   const float* T = p.targets + (size_t)(ok ? row : 0) * p.k * 12;
@@ -108,10 +159,10 @@ __device__ __forceinline__ void act_features(uint8_t* act, const MlpParams& p, i
   // feature j of a target reads its 3 x 4 row-major pose at 3, 7, 11 (position),
   // 0, 4, 8 (rotation column 0), 1, 5, 9 (rotation column 1)
   auto off = [](int j) { return j < 3 ? 3 + 4 * j : j < 6 ? 4 * (j - 3) : 1 + 4 * (j - 6); };
-  for (int n0 = 0; n0 < p.in_pad; n0 += 32) {
-    uint32_t packed[16];
+  for (int n0 = 0; n0 < p.in_pad; n0 += 64) {
+    uint32_t packed[32];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < 32; ++i) {
       float v[2];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
@@ -121,7 +172,7 @@ __device__ __forceinline__ void act_features(uint8_t* act, const MlpParams& p, i
       __nv_bfloat162 h = __floats2bfloat162_rn(v[0], v[1]);
       packed[i] = *reinterpret_cast<uint32_t*>(&h);
     }
-    act_store32(act, r, n0, packed);
+    tmem_st32(act_lane + (uint32_t)(n0 >> 1), packed);
   }
 }
 
@@ -129,19 +180,23 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     mlp_fused_kernel(const __grid_constant__ MlpMaps maps, const __grid_constant__ MlpParams p, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* act = smem;
-  uint8_t* ring = smem + MlpSmem::act_bytes(p.width);
-  uint64_t* full = (uint64_t*)(smem + MlpSmem::bar_offset(p.width, p.stages));
-  uint64_t* empty = full + p.stages;
-  uint64_t* tfull = empty + p.stages;  // [2] accumulator chunk ready (MMA -> epilogue)
-  uint64_t* tfree = tfull + 2;         // [2] accumulator chunk read out (epilogue -> MMA)
-  uint64_t* actb = tfree + 2;          // [4] ACT inputs 128 b .. 128 b + 127 written (epilogue -> MMA)
-  uint64_t* stg = actb + 4;            // [2] head staging written / read out (epilogue warps)
+  const int S = p.stages;
+  uint8_t* ring = smem;
+  float* stage = reinterpret_cast<float*>(smem + S * p.stage_bytes);
+  uint64_t* full = (uint64_t*)(smem + MlpSmem::bar_offset(S, p.stage_bytes,
+                                                          p.staged ? MlpSmem::staging_bytes(p.out_dim) : 0));
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;   // [2] accumulator buffer ready (MMA -> epilogue)
+  uint64_t* tfree = tfull + 2;   // [2] accumulator buffer read out (epilogue -> MMA)
+  uint64_t* actb = tfree + 2;    // [4] ACT inputs 128 b .. 128 b + 127 written (epilogue -> MMA)
+  uint64_t* stg = actb + 4;      // [2] head staging written / read out (epilogue warps)
   uint64_t* drain = stg + 2;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int L = p.n_layers, nch = p.width / kMlpChunk, S = p.stages;
+  const int L = p.n_layers;
+  const int hidden_chunks = p.width / kMlpChunk;  // 2 or 4
+  const int head_chunks = p.out_pad / p.head_rows;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -164,6 +219,11 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  // per layer: K-blocks of 64 inputs, output chunks and rows per chunk
+  auto kblocks = [&](int l) { return (l == 0 ? p.in_pad : p.width) / kBK; };
+  auto chunks = [&](int l) { return l == L - 1 ? head_chunks : hidden_chunks; };
+  auto rows = [&](int l) { return l == L - 1 ? p.head_rows : kMlpChunk; };
+
   if (warp == 0) {
     if (lane == 0) {
       // ---- weight producer, in the MMA's order
@@ -171,19 +231,18 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
       bool ok = true;
       for (int t = blockIdx.x; t < p.tiles && ok; t += gridDim.x)
         for (int l = 0; l < L && ok; ++l) {
-          const bool head = l == L - 1;
-          const int nc_n = head ? 1 : nch, kb_n = (l == 0 ? p.in_pad : p.width) / kBK;
-          const uint32_t bytes = (uint32_t)(head ? p.out_pad : kMlpChunk) * kBK * 2;
-          for (int nc = 0; nc < nc_n && ok; ++nc)
-            for (int kb = 0; kb < kb_n; ++kb, ++it) {
+          const int nkb = kblocks(l), nc = chunks(l), nr = rows(l);
+          for (int c = 0; c < nc && ok; ++c)
+            for (int kb0 = 0; kb0 < nkb; kb0 += kMlpStageK, ++it) {
               const int s = it % S;
               const uint32_t round = it / S;
               if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1, err, 11)) {
                 ok = false;
                 break;
               }
-              mbar_arrive_expect_tx(&full[s], bytes);
-              tma_load_2d(ring + s * kMlpStageBytes, &maps.w[l], &full[s], kb * kBK, nc * kMlpChunk);
+              const int kbs = min(kMlpStageK, nkb - kb0);
+              mbar_arrive_expect_tx(&full[s], (uint32_t)(nr * kbs * kBK * 2));
+              tma_load_3d(ring + s * p.stage_bytes, &maps.w[l], &full[s], 0, c * nr, kb0);
               ++issued;
             }
         }
@@ -195,48 +254,47 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer
-      uint32_t it = 0, uses0 = 0, uses1 = 0, acts = 0;  // completions consumed per barrier (acts: 8 bits each)
+      uint32_t it = 0, gc = 0, used0 = 0, used1 = 0, acts = 0;  // acts: parity bit 8 b of ACT barrier b
       bool ok = true;
       for (int t = blockIdx.x; t < p.tiles && ok; t += gridDim.x)
         for (int l = 0; l < L && ok; ++l) {
-          const bool head = l == L - 1;
-          // the head accumulates in chunk 1's columns, so that the next tile's
-          // first chunk can start while the head is read out
-          const int nc0 = head ? 1 : 0, nc1 = head ? 2 : nch, kb_n = (l == 0 ? p.in_pad : p.width) / kBK;
-          const uint32_t idesc = idesc_bf16(head ? p.out_pad : kMlpChunk);
-          for (int nc = nc0; nc < nc1 && ok; ++nc) {
-            const uint32_t used = nc ? uses1 : uses0;
-            if (used > 0 && !mbar_wait(&tfree[nc], (used - 1) & 1, err, 14)) {
+          const int nkb = kblocks(l), nc = chunks(l), nr = rows(l);
+          const uint32_t idesc = idesc_bf16(nr);
+          for (int c = 0; c < nc && ok; ++c, ++gc) {
+            const int b = gc & 1;
+            const uint32_t u = b ? used1 : used0;
+            if (u > 0 && !mbar_wait(&tfree[b], (u - 1) & 1, err, 14)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t d = tmem + (uint32_t)(nc * kMlpChunk);
-            for (int kb = 0; kb < kb_n; ++kb, ++it) {
-              if (nc == nc0 && (kb & 1) == 0) {  // first read of ACT inputs 64 kb .. 64 kb + 127 in this layer
-                const int b = kb >> 1;
-                if (!mbar_wait(&actb[b], (acts >> (8 * b)) & 1, err, 15)) {
-                  ok = false;
-                  break;
+            const uint32_t d = tmem + (uint32_t)(b * kMlpChunk);
+            for (int kb0 = 0; kb0 < nkb && ok; kb0 += kMlpStageK, ++it) {
+              const int kbs = min(kMlpStageK, nkb - kb0);
+              if (c == 0)  // first read of ACT inputs 64 kb0 .. 64 (kb0 + kbs) in this layer
+                for (int pc = kb0 >> 1; pc < (kb0 + kbs + 1) >> 1 && ok; ++pc) {
+                  ok = mbar_wait(&actb[pc], (acts >> (8 * pc)) & 1, err, 15);
+                  acts ^= 1u << (8 * pc);
                 }
-                acts ^= 1u << (8 * b);
-                tc_fence_after();
-              }
               const int s = it % S;
-              if (!mbar_wait(&full[s], (it / S) & 1, err, 12)) {
+              if (!ok || !mbar_wait(&full[s], (it / S) & 1, err, 12)) {
                 ok = false;
                 break;
               }
               tc_fence_after();
-              const uint64_t ad = smem_desc(smem_u32(act + kb * kMlpBlockBytes));
-              const uint64_t bd = smem_desc(smem_u32(ring + s * kMlpStageBytes));
+              const uint32_t sb = smem_u32(ring + s * p.stage_bytes);
+              for (int j = 0; j < kbs; ++j) {
+                const uint64_t bd = smem_desc(sb + (uint32_t)(j * nr * 128));
+                const uint32_t a = tmem + kMlpActCol + (uint32_t)((kb0 + j) * (kBK / 2));
 #pragma unroll
-              for (int k = 0; k < kBK / 16; ++k) mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                for (int k = 0; k < kBK / 16; ++k)
+                  mma_bf16_tmem_a(d, a + (uint32_t)(k * 8), bd + 2 * k, idesc, (kb0 + j > 0 || k > 0) ? 1u : 0u);
+              }
               mma_commit(&empty[s]);
             }
             if (!ok) break;
-            mma_commit(&tfull[nc]);
-            if (nc) ++uses1; else ++uses0;
+            mma_commit(&tfull[b]);
+            if (b) ++used1; else ++used0;
           }
         }
       mma_commit(drain);  // completes once every MMA issued above has finished
@@ -249,77 +307,59 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     const int q = warp & 3, h = (warp - 2) >> 2;
     const int r = q * 32 + lane, te = threadIdx.x - 64;  // te: 0 .. 255 over the epilogue warps
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-    const int in_blocks = p.in_pad / kBK;
-    // the head's outputs are staged in ACT blocks past the inputs (free once
-    // the head's MMAs are done) and written out row-contiguously; pitch odd
-    // for conflict-free column writes
-    const bool staged = (p.out_dim & 3) == 0 && ((uintptr_t)p.seeds & 15) == 0 &&
-                        (p.width / kBK - in_blocks) * kMlpBlockBytes >= kBM * p.out_dim * 4;
-    float* stage = reinterpret_cast<float*>(act + in_blocks * kMlpBlockBytes);
-    uint32_t tf[2] = {0, 0};
+    const uint32_t act_lane = lane_base + kMlpActCol;
+    uint32_t gc = 0, tf0 = 0, tf1 = 0, sg0 = 0, sg1 = 0;
     bool ok = true;
-    auto wait_chunk = [&](int c) -> bool {
-      uint32_t ready = 0;
-      if (lane == 0) ready = mbar_wait(&tfull[c], tf[c] & 1, err, 13) ? 1u : 0u;
-      ready = __shfl_sync(0xffffffffu, ready, 0);
-      ++tf[c];
-      if (ready) tc_fence_after();
-      return ready != 0;
-    };
     auto signal = [&](uint64_t* bar) {
       __syncwarp();
       if (lane == 0) mbar_arrive(bar);
     };
-    // bounded rendezvous of the epilogue warps on stg[i] (one phase per tile)
-    uint32_t sg[2] = {0, 0};
-    auto epi_sync = [&](int i) -> bool {
-      signal(&stg[i]);
+    // wait for the accumulator buffer b of the next chunk in sequence
+    auto wait_acc = [&](int b) -> bool {
+      uint32_t& n = b ? tf1 : tf0;
       uint32_t ready = 0;
-      if (lane == 0) ready = mbar_wait(&stg[i], sg[i] & 1, err, 16) ? 1u : 0u;
-      ++sg[i];
-      return __shfl_sync(0xffffffffu, ready, 0) != 0;
+      if (lane == 0) ready = mbar_wait(&tfull[b], n & 1, err, 13) ? 1u : 0u;
+      ready = __shfl_sync(0xffffffffu, ready, 0);
+      ++n;
+      if (ready) tc_fence_after();
+      return ready != 0;
     };
-    // column of piece i (0..3) of chunk c for this warp: both warps of a lane
-    // quarter finish the chunk's lower 128 columns (pieces 0, 1) before the
-    // upper ones, so that the next layer's MMAs can read them early
-    auto pcol = [&](int c, int i) { return c * kMlpChunk + (i >> 1) * 128 + h * 64 + (i & 1) * 32; };
-    // the warp's four pieces of chunk c, TMEM loads one piece ahead of the
-    // SiLU; `sink(i, packed)` takes piece i's 16 BF16 pairs
-    auto chunk_silu = [&](int c, const float* bias, auto&& sink) {
-      uint32_t ra[32], rb[32], pk[16];
-      tmem_ld32_issue(lane_base + (uint32_t)pcol(c, 0), ra);
-      tmem_ld_wait(ra);
-      tmem_ld32_issue(lane_base + (uint32_t)pcol(c, 1), rb);
-      silu_pack32(bias + pcol(c, 0), ra, pk);
-      sink(0, pk);
-      tmem_ld_wait(rb);
-      tmem_ld32_issue(lane_base + (uint32_t)pcol(c, 2), ra);
-      silu_pack32(bias + pcol(c, 1), rb, pk);
-      sink(1, pk);
-      tmem_ld_wait(ra);
-      tmem_ld32_issue(lane_base + (uint32_t)pcol(c, 3), rb);
-      silu_pack32(bias + pcol(c, 2), ra, pk);
-      sink(2, pk);
-      tmem_ld_wait(rb);
-      silu_pack32(bias + pcol(c, 3), rb, pk);
-      sink(3, pk);
-    };
-    // ACT pieces written to shared memory -> visible to the MMA, then signal
+    // this warp's TMEM stores into ACT are complete and ordered before the
+    // MMA's reads; then signal
     auto publish = [&](uint64_t* bar) {
-      fence_proxy_async_smem();
+      tmem_st_wait();
+      tc_fence_before();
       signal(bar);
     };
+    auto epi_sync = [&](int i) -> bool {  // bounded rendezvous of the epilogue warps
+      uint32_t& n = i ? sg1 : sg0;
+      signal(&stg[i]);
+      uint32_t ready = 0;
+      if (lane == 0) ready = mbar_wait(&stg[i], n & 1, err, 16) ? 1u : 0u;
+      ++n;
+      return __shfl_sync(0xffffffffu, ready, 0) != 0;
+    };
+    // chunk c of the current layer, in accumulator buffer b, through SiLU
+    auto silu_chunk = [&](int b, const float* bias, int c, uint32_t (&out)[32]) {
+      chunk_silu(lane_base + (uint32_t)(b * kMlpChunk + h * 64), bias + c * kMlpChunk + h * 64, out, [&] {
+        tc_fence_before();
+        signal(&tfree[b]);
+      });
+    };
+    auto to_act = [&](int c, const uint32_t (&v)[32]) {
+      tmem_st32(act_lane + (uint32_t)(c * (kMlpChunk / 2) + h * 32), v);
+      publish(&actb[c]);
+    };
     auto features = [&](int t) {
-      if (h == 0) act_features(act, p, t, r);
-      fence_proxy_async_smem();
-      for (int b = 0; b < (in_blocks + 1) / 2; ++b) signal(&actb[b]);
+      if (h == 0) act_features(act_lane, p, t, r);
+      for (int b = 0; b < (p.in_pad + 127) / 128; ++b) publish(&actb[b]);
     };
     auto prefetch_targets = [&](int t) {  // next tile's target poses into L2
       if (te != 0 || t >= p.tiles) return;
-      const int rows = min(kBM, p.batch - t * kBM);
+      const int nrow = min(kBM, p.batch - t * kBM);
       const float* src = p.targets + (size_t)t * kBM * p.k * 12;
       if (((uintptr_t)src & 15) == 0)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"((uint32_t)(rows * p.k * 48))
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"((uint32_t)(nrow * p.k * 48))
                      : "memory");
     };
     if (blockIdx.x < p.tiles) features(blockIdx.x);
@@ -328,82 +368,80 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
       prefetch_targets(tn);
       for (int l = 0; l + 1 < L && ok; ++l) {
         const float* bias = p.bias[l];
-        // ACT inputs 128 b .. 128 b + 127 are published on actb[b] once both
-        // warps of every lane quarter have written their pieces
-        auto to_act = [&](int c) {
-          return [&, c](int i, const uint32_t* pk) {
-            act_store32(act, r, pcol(c, i), pk);
-            if (i & 1) publish(&actb[2 * c + (i >> 1)]);
-          };
-        };
-        if (nch == 2) {
-          // chunk 0 waits in registers until the layer's last MMA has read ACT
-          uint32_t keep[64];
-          if (!(ok = wait_chunk(0))) break;
-          chunk_silu(0, bias, [&](int i, const uint32_t* pk) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) keep[16 * i + j] = pk[j];
-          });
-          tc_fence_before();
-          signal(&tfree[0]);
-          if (!(ok = wait_chunk(1))) break;
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            act_store32(act, r, pcol(0, i), keep + 16 * i);
-            if (i & 1) publish(&actb[i >> 1]);
-          }
-          chunk_silu(1, bias, to_act(1));
-          tc_fence_before();
-          signal(&tfree[1]);
+        // chunks 0 .. n-2 wait in registers until the layer's last MMA has read
+        // ACT; then ACT is rewritten chunk by chunk, each 128 inputs published
+        // as soon as they are in place
+        const int b0 = gc & 1, b1 = b0 ^ 1;
+        uint32_t k0[32], k1[32], k2[32];
+        if (!(ok = wait_acc(b0))) break;
+        silu_chunk(b0, bias, 0, k0);
+        if (hidden_chunks == 4) {
+          if (!(ok = wait_acc(b1))) break;
+          silu_chunk(b1, bias, 1, k1);
+          if (!(ok = wait_acc(b0))) break;
+          silu_chunk(b0, bias, 2, k2);
+          if (!(ok = wait_acc(b1))) break;
+          to_act(0, k0);
+          to_act(1, k1);
+          to_act(2, k2);
+          silu_chunk(b1, bias, 3, k0);
+          to_act(3, k0);
         } else {
-          if (!(ok = wait_chunk(0))) break;
-          chunk_silu(0, bias, to_act(0));
-          tc_fence_before();
-          signal(&tfree[0]);
+          if (!(ok = wait_acc(b1))) break;
+          to_act(0, k0);
+          silu_chunk(b1, bias, 1, k1);
+          to_act(1, k1);
         }
+        gc += hidden_chunks;
       }
       if (!ok) break;
-      // head (chunk 1's columns): its last MMA has read ACT, so the next
-      // tile's features go in first and its first chunk starts at once
-      if (!(ok = wait_chunk(1))) break;
-      if (tn < p.tiles) features(tn);
+      // head: q = mid + half tanh(y + b), chunk by chunk
       const int row0 = t * kBM, row = row0 + r;
       const bool row_ok = row < p.batch;
       const float* bias = p.bias[L - 1];
-      const int half = p.out_pad >> 1;
-#pragma unroll 1
-      for (int c0 = h * half; c0 < (h + 1) * half; c0 += 32) {
-        uint32_t rr[32];
-        tmem_ld32_issue(lane_base + (uint32_t)(kMlpChunk + c0), rr);
-        tmem_ld_wait(rr);
-        if (c0 >= p.out_dim) continue;
-        float v[32];
-        int j = c0 % p.n_dof;  // joint of column c0 + i, advanced incrementally
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int c = c0 + i;
-          v[i] = 0.f;
-          if (c < p.out_dim) {
-            const float lo = __ldg(p.lohi + j), hi = __ldg(p.lohi + p.n_dof + j);
-            v[i] = 0.5f * (lo + hi) + 0.5f * (hi - lo) * tanhf(__uint_as_float(rr[i]) + __ldg(bias + c));
-            if (!staged && row_ok) p.seeds[(size_t)row * p.out_dim + c] = v[i];
-          }
-          if (++j == p.n_dof) j = 0;
+      const int wcols = p.head_rows / 2;  // this warp's columns of a head chunk (32 or 64)
+      for (int hc = 0; hc < head_chunks && ok; ++hc, ++gc) {
+        const int b = gc & 1;
+        if (!(ok = wait_acc(b))) break;
+        if (hc == head_chunks - 1 && tn < p.tiles) features(tn);  // ACT is free: the next tile's inputs
+        uint32_t rr[2][32];
+        tmem_ld32_issue(lane_base + (uint32_t)(b * kMlpChunk + h * wcols), rr[0]);
+        tmem_ld_wait(rr[0]);
+        if (wcols > 32) {
+          tmem_ld32_issue(lane_base + (uint32_t)(b * kMlpChunk + h * wcols + 32), rr[1]);
+          tmem_ld_wait(rr[1]);
         }
-        if (staged)  // out_dim % 4 == 0: a group of four is all in or all out
+        tc_fence_before();
+        signal(&tfree[b]);
 #pragma unroll
-          for (int g = 0; g < 8; ++g)
-            if (c0 + 4 * g < p.out_dim)
-              *reinterpret_cast<float4*>(stage + r * p.out_dim + c0 + 4 * g) =
-                  make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+        for (int i = 0; i < 2; ++i) {
+          const int c0 = hc * p.head_rows + h * wcols + i * 32;
+          if (i * 32 >= wcols || c0 >= p.out_dim) continue;
+          float v[32];
+          int j = c0 % p.n_dof;  // joint of column c0 + e, advanced incrementally
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int c = c0 + e;
+            v[e] = 0.f;
+            if (c < p.out_dim) {
+              const float lo = __ldg(p.lohi + j), hi = __ldg(p.lohi + p.n_dof + j);
+              v[e] = 0.5f * (lo + hi) + 0.5f * (hi - lo) * tanhf(__uint_as_float(rr[i][e]) + __ldg(bias + c));
+              if (!p.staged && row_ok) p.seeds[(size_t)row * p.out_dim + c] = v[e];
+            }
+            if (++j == p.n_dof) j = 0;
+          }
+          if (p.staged)  // out_dim % 4 == 0: a group of four is all in or all out
+#pragma unroll
+            for (int g = 0; g < 8; ++g)
+              if (c0 + 4 * g < p.out_dim)
+                *reinterpret_cast<float4*>(stage + r * p.out_dim + c0 + 4 * g) =
+                    make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+        }
       }
-      tc_fence_before();
-      signal(&tfree[1]);
-      if (staged) {
-        // every epilogue warp's head columns are staged; copy the tile's rows
-        // out contiguously, then release the staging area
+      if (!ok) break;
+      if (p.staged) {
+        // the staging tile holds the tile's rows in their global layout: a flat copy
         if (!(ok = epi_sync(0))) break;
-        // staging holds the tile's rows in their global layout: a flat copy
         const int n4 = min(kBM, p.batch - row0) * p.out_dim / 4;
         float4* dst = reinterpret_cast<float4*>(p.seeds + (size_t)row0 * p.out_dim);
         const float4* src = reinterpret_cast<const float4*>(stage);

@@ -815,6 +815,22 @@ bool fused_ok(const pk_seednet* s) {
          s->L <= pk::tc::kMlpMaxLayers;
 }
 
+// 3-D view [din / 64][dout][64] of a BF16 weight matrix W[dout][din], boxes of
+// 64 x box_rows x box_kb, 128-byte swizzle: one box is box_kb K-major tiles
+// of box_rows x 64, 1024-byte aligned one after the other.
+bool make_map_kblocks(CUtensorMap* m, const void* base, uint64_t dout, uint64_t din, uint32_t box_rows,
+                      uint32_t box_kb) {
+  cuuint64_t dims[3] = {64, dout, din / 64};
+  cuuint64_t strides[2] = {din * 2, 128};
+  cuuint32_t box[3] = {64, box_rows, box_kb};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// cudaErrorNotSupported: this network or batch does not fit the kernel's
+// layout (the caller falls back to the layer-by-layer GEMMs).
 cudaError_t infer_fused(pk_seednet* s, int batch, const float* d_targets, float* d_seeds_out, cudaStream_t st) {
   using namespace pk::tc;
   static int sms = 0, max_smem = 0;
@@ -837,17 +853,27 @@ cudaError_t infer_fused(pk_seednet* s, int batch, const float* d_targets, float*
   p.k = s->k;
   p.batch = batch;
   p.tiles = (batch + kBM - 1) / kBM;
-  // weight ring: as deep as shared memory allows (PK_MLP_STAGES caps it, for tuning sweeps)
-  const int room = max_smem - MlpSmem::bytes(s->width, 0);
+  p.stage_bytes = kMlpStageBytes;
+  p.head_rows = s->out_pad % kMlpChunk == 0 ? kMlpChunk : 64;
+  // weight ring as deep as shared memory allows next to the head staging
+  // tile (PK_MLP_STAGES caps it, for tuning sweeps); without room for both,
+  // the head stores straight to global memory
   int cap = kMlpMaxStages;
   if (const char* env = getenv("PK_MLP_STAGES")) cap = atoi(env) > 1 ? atoi(env) : 2;
   if (cap > kMlpMaxStages) cap = kMlpMaxStages;
-  p.stages = room / kMlpStageBytes < cap ? room / kMlpStageBytes : cap;
-  if (p.stages < 2) return cudaErrorInvalidConfiguration;
+  auto fit = [&](int staging) {
+    const int room = max_smem - MlpSmem::bytes(0, 0, staging);
+    return room / kMlpStageBytes < cap ? room / kMlpStageBytes : cap;
+  };
+  const int staging = MlpSmem::staging_bytes(s->out_dim);
+  p.staged = (s->out_dim % 4 == 0 && ((uintptr_t)d_seeds_out & 15) == 0 && fit(staging) >= 2) ? 1 : 0;
+  p.stages = fit(p.staged ? staging : 0);
+  if (p.stages < 2) return cudaErrorNotSupported;
   MlpMaps maps;
   for (int l = 0; l < s->L; ++l) {
-    const int box = s->dout[l] < kMlpChunk ? s->dout[l] : kMlpChunk;
-    if (!make_map(&maps.w[l], s->W[l], s->dout[l], s->din[l], box)) return cudaErrorInvalidValue;
+    const int rows = l == s->L - 1 ? p.head_rows : kMlpChunk;
+    const int kb = s->din[l] / 64 < kMlpStageK ? s->din[l] / 64 : kMlpStageK;
+    if (!make_map_kblocks(&maps.w[l], s->W[l], s->dout[l], s->din[l], rows, kb)) return cudaErrorNotSupported;
     p.bias[l] = s->master + s->b_off[l];
   }
   p.lohi = s->d_lohi;
@@ -856,8 +882,9 @@ cudaError_t infer_fused(pk_seednet* s, int batch, const float* d_targets, float*
   int grid = p.tiles < sms ? p.tiles : sms;
   if (const char* env = getenv("PK_MLP_GRID"))  // persistent grid size, for tuning sweeps
     if (atoi(env) > 0 && atoi(env) < grid) grid = atoi(env);
+  const int smem = MlpSmem::bytes(p.stages, p.stage_bytes, p.staged ? staging : 0);
   pk::TraceScope tr("seednet_mlp", st);
-  mlp_fused_kernel<<<grid, kMlpThreads, MlpSmem::bytes(s->width, p.stages), st>>>(maps, p, s->d_err);
+  mlp_fused_kernel<<<grid, kMlpThreads, smem, st>>>(maps, p, s->d_err);
   return cudaGetLastError();
 }
 
@@ -870,7 +897,10 @@ pk_status pk_seednet_infer(pk_seednet* s, int32_t batch, const float* d_targets,
   if (batch == 0) return PK_OK;
   if (!d_targets || !d_seeds_out) return sn_fail(PK_ERR_INVALID_ARG, "NULL device buffer");
   cudaStream_t st = (cudaStream_t)stream;
-  if (fused_ok(s)) return sn_cuda(infer_fused(s, batch, d_targets, d_seeds_out, st), "pk_seednet_infer");
+  if (fused_ok(s)) {
+    const cudaError_t e = infer_fused(s, batch, d_targets, d_seeds_out, st);
+    if (e != cudaErrorNotSupported) return sn_cuda(e, "pk_seednet_infer");
+  }
   const int m_pad = round_up(batch, 128);
   pk_status ps = ensure_acts(s, m_pad);
   if (ps != PK_OK) return ps;
