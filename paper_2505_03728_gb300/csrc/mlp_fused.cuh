@@ -8,25 +8,29 @@
 //
 //   TMEM columns [256, 512)  ACT: row r in lane r, inputs 2c, 2c+1 packed in
 //                            column 256 + c (BF16 pairs; up to 512 inputs);
-//   TMEM columns [0, 256)    two FP32 accumulators of 128 columns, used by
-//                            the output chunks (128 features) in turn;
-//   shared memory            a ring of weight tiles [128 outputs][256 K]
-//                            (64 KB, one 3-D TMA box of four 128B-swizzled
-//                            K-blocks), and the head's output staging.
+//   TMEM columns [0, 256)    the FP32 accumulator of one output chunk (256
+//                            features, or the head);
+//   shared memory            a ring of 64 KB weight stages (one 3-D TMA box:
+//                            [K-blocks][256 outputs][64 K], 128B-swizzled),
+//                            the first chunk's BF16 results while the second
+//                            is computed, and the head's output staging.
 //
-// Large weight boxes matter: a TMA request costs a roughly fixed few hundred
-// cycles up to 32 KB, so 64 KB requests keep the ring ahead of the MMAs.
+// Measured on this part (M = 128, K = 16, BF16): an MMA instruction costs a
+// fixed ~116 cycles up to N = 128; at N = 256 it takes ~138 cycles with A in
+// TMEM and ~171 with A in shared memory, so N = 256 with A in TMEM is the
+// only shape near the tensor peak.  A TMA request likewise costs a roughly
+// fixed few hundred cycles, hence the large boxes.
 //
 // Warp 0 / lane 0 streams the weights of every (tile, layer, chunk, stage) in
-// MMA order; warp 1 / lane 0 issues tcgen05.mma (M = 128, N = 128, K = 16, A
-// from TMEM, B from shared memory); eight epilogue warps (two per TMEM lane
-// quarter, 64 columns each) read a finished accumulator, add the bias and
-// apply SiLU.  A layer's outputs can only replace ACT once every MMA of the
-// layer has read it, so the first chunks wait in registers (BF16) and are
-// stored to TMEM when the last chunk is done; the next layer's first stage
-// (inputs 0..255) starts as soon as those are written.  The head writes
-// q = mid + half tanh(y) through a shared-memory staging tile; the next
-// tile's features are written into ACT right after the head's last MMA.
+// MMA order; warp 1 / lane 0 issues tcgen05.mma; sixteen epilogue warps (four
+// per TMEM lane quarter, 64 columns each) drain the accumulator into registers
+// (after which the MMA may overwrite it), add the bias and apply SiLU.  A
+// layer's outputs can only replace ACT once every MMA of the layer has read
+// it, so the first chunk's results wait in shared memory; when the second
+// chunk is drained they are stored to ACT and published per 128 inputs, and
+// the next layer's MMAs start on them while the second chunk is finished.
+// The head writes q = mid + half tanh(y) through a staging tile; the next
+// tile's features go into ACT right after the head's last MMA.
 //
 // Arithmetic per element is the layer-by-layer path's (same MMA K order,
 // same SiLU and head formulas).  Every mbarrier wait is bounded as in
@@ -38,17 +42,17 @@ namespace pk {
 namespace tc {
 
 constexpr int kMlpMaxLayers = 9;
-constexpr int kMlpChunk = 128;                    // output features per accumulator chunk (MMA N)
-constexpr int kMlpStageK = 4;                     // K-blocks of 64 per weight stage
-constexpr int kMlpStageBytes = kMlpChunk * kMlpStageK * kBK * 2;  // 64 KB
-constexpr int kMlpEpiWarps = 8;
+constexpr int kMlpChunk = 256;                    // output features per accumulator chunk (MMA N)
+constexpr int kMlpStageBytes = 65536;             // largest weight stage
+constexpr int kMlpKeepBytes = kBM * kMlpChunk * 2;  // one chunk of BF16 results
+constexpr int kMlpEpiWarps = 16;
 constexpr int kMlpThreads = 64 + 32 * kMlpEpiWarps;
 constexpr int kMlpMaxStages = 3;
 constexpr uint32_t kMlpTmemCols = 512;
 constexpr uint32_t kMlpActCol = 256;              // first TMEM column of ACT
 
 struct MlpMaps {
-  // W_l viewed as [din_l / 64][dout_l][64] BF16: 3-D boxes of 64 x rows x K-blocks
+  // W_l viewed as [din_l / 64][dout_l][64] BF16: 3-D boxes of 64 x rows x stage_kb[l]
   CUtensorMap w[kMlpMaxLayers];
 };
 
@@ -62,10 +66,10 @@ struct MlpParams {
   int k;           // target poses per row (9 features each)
   int batch;
   int tiles;       // ceil(batch / 128)
-  int stages;      // weight ring depth
-  int stage_bytes; // ring slot size
-  int head_rows;   // output features per head chunk (64 or 128)
-  int staged;      // head outputs through the shared-memory staging tile
+  int stages;      // weight ring depth (slots of kMlpStageBytes)
+  int area_bytes;  // keep / staging area after the ring
+  int staged;      // head outputs through the staging tile (in the keep area)
+  int stage_kb[kMlpMaxLayers];  // K-blocks of 64 per weight stage of layer l
   const float* bias[kMlpMaxLayers];
   const float* lohi;     // joint limits [2][n_dof]
   const float* targets;  // [batch][k][12]
@@ -74,12 +78,8 @@ struct MlpParams {
 
 struct MlpSmem {
   static constexpr int staging_bytes(int out_dim) { return kBM * out_dim * 4; }
-  static constexpr int bar_offset(int stages, int stage_bytes, int staging) {
-    return stages * stage_bytes + ((staging + 1023) & ~1023);
-  }
-  static constexpr int bytes(int stages, int stage_bytes, int staging) {
-    return bar_offset(stages, stage_bytes, staging) + 256 + 1024;
-  }
+  static constexpr int bar_offset(int stages, int area) { return stages * kMlpStageBytes + ((area + 1023) & ~1023); }
+  static constexpr int bytes(int stages, int area) { return bar_offset(stages, area) + 256 + 1024; }
 };
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
@@ -115,6 +115,17 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
 }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// 16 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint4& a, const uint4& b, const uint4& c,
+                                          const uint4& d) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w), "r"(c.x), "r"(c.y),
+      "r"(c.z), "r"(c.w), "r"(d.x), "r"(d.y), "r"(d.z), "r"(d.w)
+      : "memory");
+}
+
 // BF16 SiLU of 32 accumulator columns; the arithmetic of epilogue_silu32.
 __device__ __forceinline__ void silu_pack32(const float* bias, const uint32_t (&r)[32], uint32_t (&packed)[16]) {
   const uint64_t half2 = f32x2(0.5f, 0.5f);
@@ -130,22 +141,6 @@ __device__ __forceinline__ void silu_pack32(const float* bias, const uint32_t (&
     __nv_bfloat162 o = __floats2bfloat162_rn(sv.x, sv.y);
     packed[i] = *reinterpret_cast<uint32_t*>(&o);
   }
-}
-
-// This warp's 64 columns (col, col + 32) of an accumulator -> registers, then
-// `release` (the MMA may reuse the buffer) -> SiLU with bias -> 32 BF16 pairs.
-template <class F>
-__device__ __forceinline__ void chunk_silu(uint32_t taddr, const float* bias, uint32_t (&out)[32], F&& release) {
-  uint32_t ra[32];
-  uint32_t (&lo)[16] = *reinterpret_cast<uint32_t(*)[16]>(&out[0]);
-  uint32_t (&hi)[16] = *reinterpret_cast<uint32_t(*)[16]>(&out[16]);
-  tmem_ld32_issue(taddr, ra);
-  tmem_ld_wait(ra);
-  silu_pack32(bias, ra, lo);
-  tmem_ld32_issue(taddr + 32, ra);
-  tmem_ld_wait(ra);
-  release();
-  silu_pack32(bias + 32, ra, hi);
 }
 
 // Pose features of tile row r (position, first two rotation columns per
@@ -182,33 +177,30 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int S = p.stages;
   uint8_t* ring = smem;
-  float* stage = reinterpret_cast<float*>(smem + S * p.stage_bytes);
-  uint64_t* full = (uint64_t*)(smem + MlpSmem::bar_offset(S, p.stage_bytes,
-                                                          p.staged ? MlpSmem::staging_bytes(p.out_dim) : 0));
+  uint8_t* area = smem + S * kMlpStageBytes;  // first chunk's results, then the head's staging
+  float* stage = reinterpret_cast<float*>(area);
+  uint64_t* full = (uint64_t*)(smem + MlpSmem::bar_offset(S, p.area_bytes));
   uint64_t* empty = full + S;
-  uint64_t* tfull = empty + S;   // [2] accumulator buffer ready (MMA -> epilogue)
-  uint64_t* tfree = tfull + 2;   // [2] accumulator buffer read out (epilogue -> MMA)
-  uint64_t* actb = tfree + 2;    // [4] ACT inputs 128 b .. 128 b + 127 written (epilogue -> MMA)
+  uint64_t* tfull = empty + S;   // accumulator ready (MMA -> epilogue)
+  uint64_t* tfree = tfull + 1;   // accumulator drained (epilogue -> MMA)
+  uint64_t* actb = tfree + 1;    // [4] ACT inputs 128 b .. 128 b + 127 written (epilogue -> MMA)
   uint64_t* stg = actb + 4;      // [2] head staging written / read out (epilogue warps)
   uint64_t* drain = stg + 2;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int L = p.n_layers;
-  const int hidden_chunks = p.width / kMlpChunk;  // 2 or 4
-  const int head_chunks = p.out_pad / p.head_rows;
+  const int hidden_chunks = p.width / kMlpChunk;  // 1 or 2
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int c = 0; c < 2; ++c) {
-      mbar_init(&tfull[c], 1);
-      mbar_init(&tfree[c], kMlpEpiWarps);
-      mbar_init(&stg[c], kMlpEpiWarps);
-    }
-    for (int b = 0; b < 4; ++b) mbar_init(&actb[b], kMlpEpiWarps);
+    mbar_init(tfull, 1);
+    mbar_init(tfree, kMlpEpiWarps);
+    for (int b = 0; b < 4; ++b) mbar_init(&actb[b], kMlpEpiWarps / 2);  // the eight warps that write it
+    for (int c = 0; c < 2; ++c) mbar_init(&stg[c], kMlpEpiWarps);
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -219,10 +211,10 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // per layer: K-blocks of 64 inputs, output chunks and rows per chunk
+  // per layer: K-blocks of 64 inputs, output chunks and rows (outputs) per chunk
   auto kblocks = [&](int l) { return (l == 0 ? p.in_pad : p.width) / kBK; };
-  auto chunks = [&](int l) { return l == L - 1 ? head_chunks : hidden_chunks; };
-  auto rows = [&](int l) { return l == L - 1 ? p.head_rows : kMlpChunk; };
+  auto chunks = [&](int l) { return l == L - 1 ? 1 : hidden_chunks; };
+  auto rows = [&](int l) { return l == L - 1 ? p.out_pad : kMlpChunk; };
 
   if (warp == 0) {
     if (lane == 0) {
@@ -231,18 +223,17 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
       bool ok = true;
       for (int t = blockIdx.x; t < p.tiles && ok; t += gridDim.x)
         for (int l = 0; l < L && ok; ++l) {
-          const int nkb = kblocks(l), nc = chunks(l), nr = rows(l);
+          const int nkb = kblocks(l), nc = chunks(l), nr = rows(l), kbs = p.stage_kb[l];
           for (int c = 0; c < nc && ok; ++c)
-            for (int kb0 = 0; kb0 < nkb; kb0 += kMlpStageK, ++it) {
+            for (int kb0 = 0; kb0 < nkb; kb0 += kbs, ++it) {
               const int s = it % S;
               const uint32_t round = it / S;
               if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1, err, 11)) {
                 ok = false;
                 break;
               }
-              const int kbs = min(kMlpStageK, nkb - kb0);
               mbar_arrive_expect_tx(&full[s], (uint32_t)(nr * kbs * kBK * 2));
-              tma_load_3d(ring + s * p.stage_bytes, &maps.w[l], &full[s], 0, c * nr, kb0);
+              tma_load_3d(ring + s * kMlpStageBytes, &maps.w[l], &full[s], 0, c * nr, kb0);
               ++issued;
             }
         }
@@ -253,24 +244,20 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      // ---- MMA issuer
-      uint32_t it = 0, gc = 0, used0 = 0, used1 = 0, acts = 0;  // acts: parity bit 8 b of ACT barrier b
+      // ---- MMA issuer: one accumulator, chunks in turn
+      uint32_t it = 0, used = 0, acts = 0;  // acts: parity bit 8 b of ACT barrier b
       bool ok = true;
       for (int t = blockIdx.x; t < p.tiles && ok; t += gridDim.x)
         for (int l = 0; l < L && ok; ++l) {
-          const int nkb = kblocks(l), nc = chunks(l), nr = rows(l);
+          const int nkb = kblocks(l), nc = chunks(l), nr = rows(l), kbs = p.stage_kb[l];
           const uint32_t idesc = idesc_bf16(nr);
-          for (int c = 0; c < nc && ok; ++c, ++gc) {
-            const int b = gc & 1;
-            const uint32_t u = b ? used1 : used0;
-            if (u > 0 && !mbar_wait(&tfree[b], (u - 1) & 1, err, 14)) {
+          for (int c = 0; c < nc && ok; ++c) {
+            if (used > 0 && !mbar_wait(tfree, (used - 1) & 1, err, 14)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t d = tmem + (uint32_t)(b * kMlpChunk);
-            for (int kb0 = 0; kb0 < nkb && ok; kb0 += kMlpStageK, ++it) {
-              const int kbs = min(kMlpStageK, nkb - kb0);
+            for (int kb0 = 0; kb0 < nkb && ok; kb0 += kbs, ++it) {
               if (c == 0)  // first read of ACT inputs 64 kb0 .. 64 (kb0 + kbs) in this layer
                 for (int pc = kb0 >> 1; pc < (kb0 + kbs + 1) >> 1 && ok; ++pc) {
                   ok = mbar_wait(&actb[pc], (acts >> (8 * pc)) & 1, err, 15);
@@ -282,19 +269,19 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                 break;
               }
               tc_fence_after();
-              const uint32_t sb = smem_u32(ring + s * p.stage_bytes);
+              const uint32_t sb = smem_u32(ring + s * kMlpStageBytes);
               for (int j = 0; j < kbs; ++j) {
                 const uint64_t bd = smem_desc(sb + (uint32_t)(j * nr * 128));
                 const uint32_t a = tmem + kMlpActCol + (uint32_t)((kb0 + j) * (kBK / 2));
 #pragma unroll
                 for (int k = 0; k < kBK / 16; ++k)
-                  mma_bf16_tmem_a(d, a + (uint32_t)(k * 8), bd + 2 * k, idesc, (kb0 + j > 0 || k > 0) ? 1u : 0u);
+                  mma_bf16_tmem_a(tmem, a + (uint32_t)(k * 8), bd + 2 * k, idesc, (kb0 + j > 0 || k > 0) ? 1u : 0u);
               }
               mma_commit(&empty[s]);
             }
             if (!ok) break;
-            mma_commit(&tfull[b]);
-            if (b) ++used1; else ++used0;
+            mma_commit(tfull);
+            ++used;
           }
         }
       mma_commit(drain);  // completes once every MMA issued above has finished
@@ -303,24 +290,27 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     __syncwarp();
   } else {
     // ---- epilogue warps: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile
-    //      rows) and half h = (w - 2) / 4 of each chunk's columns
+    //      rows) and columns 64 h .. 64 h + 63 of a chunk, h = (w - 2) / 4
     const int q = warp & 3, h = (warp - 2) >> 2;
-    const int r = q * 32 + lane, te = threadIdx.x - 64;  // te: 0 .. 255 over the epilogue warps
+    const int r = q * 32 + lane, te = threadIdx.x - 64;  // te: 0 .. 511 over the epilogue warps
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     const uint32_t act_lane = lane_base + kMlpActCol;
-    uint32_t gc = 0, tf0 = 0, tf1 = 0, sg0 = 0, sg1 = 0;
+    uint32_t tf = 0, sg0 = 0, sg1 = 0;
     bool ok = true;
+    // this thread's 32 words of a kept chunk (its row, its 64 features), in
+    // 16-byte pieces rotated by the row so that a warp's accesses spread over
+    // all banks
+    uint8_t* keep_row = area + (size_t)(r * 4 + h) * 128;
+    auto keep_at = [&](int i) { return reinterpret_cast<uint4*>(keep_row + ((i ^ (r & 7)) << 4)); };
     auto signal = [&](uint64_t* bar) {
       __syncwarp();
       if (lane == 0) mbar_arrive(bar);
     };
-    // wait for the accumulator buffer b of the next chunk in sequence
-    auto wait_acc = [&](int b) -> bool {
-      uint32_t& n = b ? tf1 : tf0;
+    auto wait_acc = [&]() -> bool {
       uint32_t ready = 0;
-      if (lane == 0) ready = mbar_wait(&tfull[b], n & 1, err, 13) ? 1u : 0u;
+      if (lane == 0) ready = mbar_wait(tfull, tf & 1, err, 13) ? 1u : 0u;
       ready = __shfl_sync(0xffffffffu, ready, 0);
-      ++n;
+      ++tf;
       if (ready) tc_fence_after();
       return ready != 0;
     };
@@ -339,18 +329,26 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
       ++n;
       return __shfl_sync(0xffffffffu, ready, 0) != 0;
     };
-    // chunk c of the current layer, in accumulator buffer b, through SiLU
-    auto silu_chunk = [&](int b, const float* bias, int c, uint32_t (&out)[32]) {
-      chunk_silu(lane_base + (uint32_t)(b * kMlpChunk + h * 64), bias + c * kMlpChunk + h * 64, out, [&] {
-        tc_fence_before();
-        signal(&tfree[b]);
-      });
+    // this warp's 64 accumulator columns into registers (one wait for both
+    // loads), then release the accumulator to the MMA
+    auto drain = [&](uint32_t (&v0)[32], uint32_t (&v1)[32]) {
+      tmem_ld32_issue(lane_base + (uint32_t)(h * 64), v0);
+      tmem_ld32_issue(lane_base + (uint32_t)(h * 64 + 32), v1);
+      tmem_ld_wait(v0);
+      tmem_ld_wait(v1);
+      tc_fence_before();
+      signal(tfree);
     };
-    auto to_act = [&](int c, const uint32_t (&v)[32]) {
-      tmem_st32(act_lane + (uint32_t)(c * (kMlpChunk / 2) + h * 32), v);
-      publish(&actb[c]);
+    // SiLU of 32 accumulator columns (features f ..) into ACT columns f / 2 ..
+    auto silu_to_act = [&](const float* bias, int f, const uint32_t (&v)[32]) {
+      uint32_t pk[16];
+      silu_pack32(bias + f, v, pk);
+      tmem_st16(act_lane + (uint32_t)(f >> 1), make_uint4(pk[0], pk[1], pk[2], pk[3]),
+                make_uint4(pk[4], pk[5], pk[6], pk[7]), make_uint4(pk[8], pk[9], pk[10], pk[11]),
+                make_uint4(pk[12], pk[13], pk[14], pk[15]));
     };
-    auto features = [&](int t) {
+    auto features = [&](int t) {  // written by the h = 0 warps, published with the h = 1 warps
+      if (h >= 2) return;
       if (h == 0) act_features(act_lane, p, t, r);
       for (int b = 0; b < (p.in_pad + 127) / 128; ++b) publish(&actb[b]);
     };
@@ -368,77 +366,74 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
       prefetch_targets(tn);
       for (int l = 0; l + 1 < L && ok; ++l) {
         const float* bias = p.bias[l];
-        // chunks 0 .. n-2 wait in registers until the layer's last MMA has read
-        // ACT; then ACT is rewritten chunk by chunk, each 128 inputs published
-        // as soon as they are in place
-        const int b0 = gc & 1, b1 = b0 ^ 1;
-        uint32_t k0[32], k1[32], k2[32];
-        if (!(ok = wait_acc(b0))) break;
-        silu_chunk(b0, bias, 0, k0);
-        if (hidden_chunks == 4) {
-          if (!(ok = wait_acc(b1))) break;
-          silu_chunk(b1, bias, 1, k1);
-          if (!(ok = wait_acc(b0))) break;
-          silu_chunk(b0, bias, 2, k2);
-          if (!(ok = wait_acc(b1))) break;
-          to_act(0, k0);
-          to_act(1, k1);
-          to_act(2, k2);
-          silu_chunk(b1, bias, 3, k0);
-          to_act(3, k0);
+        uint32_t v0[32], v1[32];
+        const int f0 = h * 64;  // this warp's features of chunk 0; piece 2 c + h / 2 of ACT
+        if (!(ok = wait_acc())) break;
+        drain(v0, v1);
+        if (hidden_chunks == 2) {
+          // chunk 0 waits in shared memory until the layer's last MMA has read ACT
+          {
+            uint32_t pk[16];
+            silu_pack32(bias + f0, v0, pk);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) *keep_at(j) = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+            silu_pack32(bias + f0 + 32, v1, pk);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) *keep_at(4 + j) = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+          }
+          if (!(ok = wait_acc())) break;
+          drain(v0, v1);
+          // every MMA of the layer is done: chunk 0 into ACT (published at once,
+          // the next layer starts on it), then chunk 1
+          tmem_st16(act_lane + (uint32_t)(f0 >> 1), *keep_at(0), *keep_at(1), *keep_at(2), *keep_at(3));
+          tmem_st16(act_lane + (uint32_t)((f0 >> 1) + 16), *keep_at(4), *keep_at(5), *keep_at(6), *keep_at(7));
+          publish(&actb[h >> 1]);
+          silu_to_act(bias, kMlpChunk + f0, v0);
+          silu_to_act(bias, kMlpChunk + f0 + 32, v1);
+          publish(&actb[2 + (h >> 1)]);
         } else {
-          if (!(ok = wait_acc(b1))) break;
-          to_act(0, k0);
-          silu_chunk(b1, bias, 1, k1);
-          to_act(1, k1);
+          silu_to_act(bias, f0, v0);
+          silu_to_act(bias, f0 + 32, v1);
+          publish(&actb[h >> 1]);
         }
-        gc += hidden_chunks;
       }
       if (!ok) break;
-      // head: q = mid + half tanh(y + b), chunk by chunk
+      // head: q = mid + half tanh(y + b); its last MMA has read ACT, so the next
+      // tile's features go in first
+      if (!(ok = wait_acc())) break;
+      if (tn < p.tiles) features(tn);
       const int row0 = t * kBM, row = row0 + r;
       const bool row_ok = row < p.batch;
       const float* bias = p.bias[L - 1];
-      const int wcols = p.head_rows / 2;  // this warp's columns of a head chunk (32 or 64)
-      for (int hc = 0; hc < head_chunks && ok; ++hc, ++gc) {
-        const int b = gc & 1;
-        if (!(ok = wait_acc(b))) break;
-        if (hc == head_chunks - 1 && tn < p.tiles) features(tn);  // ACT is free: the next tile's inputs
-        uint32_t rr[2][32];
-        tmem_ld32_issue(lane_base + (uint32_t)(b * kMlpChunk + h * wcols), rr[0]);
-        tmem_ld_wait(rr[0]);
-        if (wcols > 32) {
-          tmem_ld32_issue(lane_base + (uint32_t)(b * kMlpChunk + h * wcols + 32), rr[1]);
-          tmem_ld_wait(rr[1]);
-        }
-        tc_fence_before();
-        signal(&tfree[b]);
+      const int wc = p.out_pad / 4;  // this warp's columns of the head: 16 .. 64
+      // 16 columns at a time (few registers; the accumulator is released at
+      // the end), in groups of four (out_dim % 4 == 0 when staged)
+#pragma unroll 1
+      for (int c0 = h * wc; c0 < (h + 1) * wc; c0 += 16) {
+        float v[16];
+        tmem_ld16(lane_base + (uint32_t)c0, v);
+        if (c0 >= p.out_dim) continue;
+        int j = c0 % p.n_dof;  // joint of the current column, advanced incrementally
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          const int c0 = hc * p.head_rows + h * wcols + i * 32;
-          if (i * 32 >= wcols || c0 >= p.out_dim) continue;
-          float v[32];
-          int j = c0 % p.n_dof;  // joint of column c0 + e, advanced incrementally
+        for (int g = 0; g < 4; ++g) {
+          float o[4];
 #pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const int c = c0 + e;
-            v[e] = 0.f;
+          for (int e = 0; e < 4; ++e) {
+            const int c = c0 + 4 * g + e;
+            o[e] = 0.f;
             if (c < p.out_dim) {
               const float lo = __ldg(p.lohi + j), hi = __ldg(p.lohi + p.n_dof + j);
-              v[e] = 0.5f * (lo + hi) + 0.5f * (hi - lo) * tanhf(__uint_as_float(rr[i][e]) + __ldg(bias + c));
-              if (!p.staged && row_ok) p.seeds[(size_t)row * p.out_dim + c] = v[e];
+              o[e] = 0.5f * (lo + hi) + 0.5f * (hi - lo) * tanhf(v[4 * g + e] + __ldg(bias + c));
+              if (!p.staged && row_ok) p.seeds[(size_t)row * p.out_dim + c] = o[e];
             }
             if (++j == p.n_dof) j = 0;
           }
-          if (p.staged)  // out_dim % 4 == 0: a group of four is all in or all out
-#pragma unroll
-            for (int g = 0; g < 8; ++g)
-              if (c0 + 4 * g < p.out_dim)
-                *reinterpret_cast<float4*>(stage + r * p.out_dim + c0 + 4 * g) =
-                    make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+          if (p.staged && c0 + 4 * g < p.out_dim)
+            *reinterpret_cast<float4*>(stage + r * p.out_dim + c0 + 4 * g) = make_float4(o[0], o[1], o[2], o[3]);
         }
       }
-      if (!ok) break;
+      tc_fence_before();
+      signal(tfree);
       if (p.staged) {
         // the staging tile holds the tile's rows in their global layout: a flat copy
         if (!(ok = epi_sync(0))) break;

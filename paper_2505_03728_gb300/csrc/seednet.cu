@@ -853,27 +853,37 @@ cudaError_t infer_fused(pk_seednet* s, int batch, const float* d_targets, float*
   p.k = s->k;
   p.batch = batch;
   p.tiles = (batch + kBM - 1) / kBM;
-  p.stage_bytes = kMlpStageBytes;
-  p.head_rows = s->out_pad % kMlpChunk == 0 ? kMlpChunk : 64;
-  // weight ring as deep as shared memory allows next to the head staging
-  // tile (PK_MLP_STAGES caps it, for tuning sweeps); without room for both,
-  // the head stores straight to global memory
+  // weight stages: the largest divisor of the layer's K-blocks that keeps a
+  // stage within kMlpStageBytes
+  for (int l = 0; l < s->L; ++l) {
+    const int rows = l == s->L - 1 ? s->out_pad : kMlpChunk, nkb = s->din[l] / 64;
+    int kb = kMlpStageBytes / (rows * 128);
+    if (kb > nkb) kb = nkb;
+    while (nkb % kb) --kb;
+    p.stage_kb[l] = kb;
+  }
+  // ring as deep as shared memory allows next to the keep area (one chunk of
+  // BF16 results at width 512) that also stages the head's outputs
+  // (PK_MLP_STAGES caps the ring, for tuning sweeps); without room for the
+  // staging tile the head stores straight to global memory
   int cap = kMlpMaxStages;
   if (const char* env = getenv("PK_MLP_STAGES")) cap = atoi(env) > 1 ? atoi(env) : 2;
   if (cap > kMlpMaxStages) cap = kMlpMaxStages;
-  auto fit = [&](int staging) {
-    const int room = max_smem - MlpSmem::bytes(0, 0, staging);
+  const int keep = s->width == 2 * kMlpChunk ? kMlpKeepBytes : 0;
+  const int staging = MlpSmem::staging_bytes(s->out_dim);
+  auto fit = [&](int area) {
+    const int room = max_smem - MlpSmem::bytes(0, area);
     return room / kMlpStageBytes < cap ? room / kMlpStageBytes : cap;
   };
-  const int staging = MlpSmem::staging_bytes(s->out_dim);
-  p.staged = (s->out_dim % 4 == 0 && ((uintptr_t)d_seeds_out & 15) == 0 && fit(staging) >= 2) ? 1 : 0;
-  p.stages = fit(p.staged ? staging : 0);
+  const int area_staged = staging > keep ? staging : keep;
+  p.staged = (s->out_dim % 4 == 0 && ((uintptr_t)d_seeds_out & 15) == 0 && fit(area_staged) >= 2) ? 1 : 0;
+  p.area_bytes = p.staged ? area_staged : keep;
+  p.stages = fit(p.area_bytes);
   if (p.stages < 2) return cudaErrorNotSupported;
   MlpMaps maps;
   for (int l = 0; l < s->L; ++l) {
-    const int rows = l == s->L - 1 ? p.head_rows : kMlpChunk;
-    const int kb = s->din[l] / 64 < kMlpStageK ? s->din[l] / 64 : kMlpStageK;
-    if (!make_map_kblocks(&maps.w[l], s->W[l], s->dout[l], s->din[l], rows, kb)) return cudaErrorNotSupported;
+    const int rows = l == s->L - 1 ? s->out_pad : kMlpChunk;
+    if (!make_map_kblocks(&maps.w[l], s->W[l], s->dout[l], s->din[l], rows, p.stage_kb[l])) return cudaErrorNotSupported;
     p.bias[l] = s->master + s->b_off[l];
   }
   p.lohi = s->d_lohi;
@@ -882,7 +892,7 @@ cudaError_t infer_fused(pk_seednet* s, int batch, const float* d_targets, float*
   int grid = p.tiles < sms ? p.tiles : sms;
   if (const char* env = getenv("PK_MLP_GRID"))  // persistent grid size, for tuning sweeps
     if (atoi(env) > 0 && atoi(env) < grid) grid = atoi(env);
-  const int smem = MlpSmem::bytes(p.stages, p.stage_bytes, p.staged ? staging : 0);
+  const int smem = MlpSmem::bytes(p.stages, p.area_bytes);
   pk::TraceScope tr("seednet_mlp", st);
   mlp_fused_kernel<<<grid, kMlpThreads, smem, st>>>(maps, p, s->d_err);
   return cudaGetLastError();
