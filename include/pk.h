@@ -480,7 +480,11 @@ pk_status pk_seednet_forward(pk_seednet* net, int32_t batch, const float* d_targ
                              void* stream);
 
 /* Seeds d_seeds_out [batch][K][n_dof] for d_targets [batch][k][12]: the layout
- * pk_ik_solve takes. */
+ * pk_ik_solve takes.  Widths 256 and 512 with K * n_dof <= 256 run as one
+ * kernel (features, every layer and the head, activations kept on chip);
+ * other shapes, or the environment variable PK_SEEDNET_FUSED=0, use the
+ * layer-by-layer GEMMs.  Both give the same seeds.  PK_MLP_STAGES (2..3) and
+ * PK_MLP_GRID (CTAs) cap the fused kernel's weight ring and grid, for tuning. */
 pk_status pk_seednet_infer(pk_seednet* net, int32_t batch, const float* d_targets, float* d_seeds_out,
                            void* stream);
 
