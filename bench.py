@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-cancel", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--train-epochs", type=int, default=8)
+    ap.add_argument("--train-epochs", type=int, default=32)
     ap.add_argument("--no-extra", action="store_true", help="skip the uneven-batch and trajectory lines")
     ap.add_argument("--case", choices=CASES, default=None,
                     help="profiling case: run one small kernel workload (a few launches, --batch sized) and exit; "
@@ -191,8 +191,9 @@ def run_reference(args, cfg):
 
 
 def config_dict(cfg, args, head="plain"):
-    seeding = ("learned: seed network (9 -> 4 x 512 SiLU -> 8 x 7, BF16 tcgen05, trained on the GPU "
-               "before timing, LM-refined labels every 2 epochs) inferred inside every step"
+    seeding = (f"learned: seed network (9 -> 4 x 512 SiLU -> 8 x 7, BF16 tcgen05, trained on the GPU "
+               f"before timing for {args.train_epochs} epochs of 10M fresh samples, LM-refined labels every 2 "
+               f"epochs) inferred inside every step"
                if head == "learned" else "uniform random")
     return {"workload": cfg["name"], "robot": "synthetic 7-DoF revolute chain (seed 100)",
             "targets": args.batch, "seeds_per_target": cfg["n_seeds"], "max_iters": cfg["max_iters"],
