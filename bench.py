@@ -46,6 +46,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max 
 # DRAM bytes (read + write) per target of the LM kernel: ncu capture of the
 # 16,384-target learned-seed launch (4.586 MB), inputs read once (see profiles/).
 LM_DRAM_BYTES_PER_TARGET = 4586240 / 16384
+MLP_DRAM_BYTES_65536 = 4962048.0  # mlp_fused_kernel, dram__bytes_read.sum + write.sum per launch
 # FP32 operations per trajectory-iteration of the trajectory kernel (ncu count
 # over 64 trajectories x 50 iterations, see profiles/).
 TRAJ_FLOPS_PER_ITER = 1.995e6
@@ -625,8 +626,10 @@ def main():
         g_tf = fl / (r["gemm_ms"] / 1e3) / 1e12
         kname = ("mlp_fused_kernel (whole network, 1 launch per inference)" if r["fused_mlp"] else
                  f"gemm_bf16_tc_kernel ({r['gemm_launches']} launches per inference, aggregate)")
+        # DRAM bytes per launch of the fused kernel at 65,536 targets (ncu, profiles/)
+        mlp_traffic = MLP_DRAM_BYTES_65536 if (r["fused_mlp"] and B == 65536) else None
         roofs.append({"bound": "tensor", "kernel": kname,
-                      "achieved": g_tf, "peak": peak, "unit": "TFLOP/s", "frac": g_tf / peak, "traffic": None,
+                      "achieved": g_tf, "peak": peak, "unit": "TFLOP/s", "frac": g_tf / peak, "traffic": mlp_traffic,
                       "peak_source": f"bf16 dense GEMM burst ({src}, MEASURED_PEAKS.json)",
                       "ms_per_step": r["gemm_ms"], "flops_per_step": fl})
     dominant = max(roofs, key=lambda x: x.get("ms_per_launch", x.get("ms_per_step", 0)))
