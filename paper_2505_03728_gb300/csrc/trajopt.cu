@@ -34,13 +34,13 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-template <int N, int B>
+template <int N, int B, bool X>
 struct TrajSmem {
   static constexpr int NT = N * (N + 1) / 2;
   float x[2][kTrajMaxT][8];    // current / candidate trajectories
   float D[2][kTrajMaxT][NT];   // diagonal blocks of J^T J without smoothness
-  float E[2][kTrajMaxT][N][N]; // block (t, t-1) of J^T J beyond the smoothness scalar (velocity
-                               // limits, swept spheres)
+  float E[X ? 2 : 1][X ? kTrajMaxT : 1][N][N];  // block (t, t-1) of J^T J beyond the smoothness
+                                                // scalar (velocity limits, swept spheres; X only)
   float g[2][kTrajMaxT][8];    // J^T r
   float f[2], mind[2], gpe[2], gre[2];
   float p[kTrajMaxT][N + 1][3];  // joint origins and tool point (world), candidate
@@ -115,8 +115,8 @@ __device__ __forceinline__ void smooth_band(const TrajParamsDev& tp, int t, floa
 }
 
 // Per-timestep terms (thread t): FK, limits, smoothness, start and goal.
-template <int N, int B>
-__device__ void eval_timestep(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N, B>& S, int buf, int t,
+template <int N, int B, bool X>
+__device__ void eval_timestep(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int buf, int t,
                               float& fpart) {
   constexpr int NT = N * (N + 1) / 2;
   const int T = tp.T;
@@ -231,6 +231,7 @@ __device__ void eval_timestep(const ChainC<N>& rc, const TrajParamsDev& tp, Traj
   }
   // velocity-limit hinge (Sec. III-C, dt = 1): the row (t, t-1) is owned by t;
   // t also takes its part of the row (t+1, t).  E_t is written whole here.
+  if constexpr (X) {
   float ed[N];
 #pragma unroll
   for (int j = 0; j < N; ++j) ed[j] = 0.f;
@@ -264,6 +265,7 @@ __device__ void eval_timestep(const ChainC<N>& rc, const TrajParamsDev& tp, Traj
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = 0; j < N; ++j) S.E[buf][t][i][j] = (i == j) ? ed[i] : 0.f;
+  }
   // start configuration
   if (t == 0) {
     const float s2 = tp.w_start * tp.w_start;
@@ -340,8 +342,8 @@ __device__ void eval_timestep(const ChainC<N>& rc, const TrajParamsDev& tp, Traj
 }
 
 // n . dc/dq_i for a point c carried by link l at timestep t (joints 0..l).
-template <int N, int B>
-__device__ __forceinline__ void coll_jrow(const ChainC<N>& rc, const TrajSmem<N, B>& S, int t, int l, const float* c,
+template <int N, int B, bool X>
+__device__ __forceinline__ void coll_jrow(const ChainC<N>& rc, const TrajSmem<N, B, X>& S, int t, int l, const float* c,
                                           const float* nrm, float scale, float* jr) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -361,8 +363,8 @@ __device__ __forceinline__ void coll_jrow(const ChainC<N>& rc, const TrajSmem<N,
 }
 
 // Collision terms of timestep t, one link sphere per lane (lanes >= N*S idle).
-template <int N, int B>
-__device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N, B>& S, int buf, int t,
+template <int N, int B, bool X>
+__device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int buf, int t,
                                 int lane, float& fpart, float& mind) {
   constexpr int NT = N * (N + 1) / 2;
   const int nsph = N * tp.S;
@@ -402,7 +404,7 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
       const float r = wc * fa;
       fpart = fmaf(r, r, fpart);
       float jr[N];
-      coll_jrow<N, B>(rc, S, t, l, c, nrm, wc * df, jr);
+      coll_jrow<N, B, X>(rc, S, t, l, c, nrm, wc * df, jr);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         gl[i] = fmaf(jr[i], r, gl[i]);
@@ -429,7 +431,7 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
   }
   // swept spheres (Sec. IV-B): the capsule of this lane's sphere from t to t+1
   // against every obstacle sphere; the row couples q_t and q_{t+1}
-  if (tp.w_swept > 0.f && t + 1 < tp.T && lane < nsph) {
+  if (X && tp.w_swept > 0.f && t + 1 < tp.T && lane < nsph) {
     const int l = lane / tp.S, s = lane % tp.S;
     const float al = (s + 0.5f) / (float)tp.S;
     float c0[3], c1[3], e[3];
@@ -456,8 +458,8 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
       const float inv = 1.f / len;
       const float nrm[3] = {v0 * inv, v1 * inv, v2 * inv};
       float a[N], bq[N];
-      coll_jrow<N, B>(rc, S, t, l, c0, nrm, tp.w_swept * df * (1.f - u), a);
-      coll_jrow<N, B>(rc, S, t + 1, l, c1, nrm, tp.w_swept * df * u, bq);
+      coll_jrow<N, B, X>(rc, S, t, l, c0, nrm, tp.w_swept * df * (1.f - u), a);
+      coll_jrow<N, B, X>(rc, S, t + 1, l, c1, nrm, tp.w_swept * df * u, bq);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         atomicAdd(&S.g[buf][t][i], a[i] * r);
@@ -475,13 +477,13 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
 }
 
 // Cost, J^T J diagonal blocks and J^T r of trajectory buffer `buf`.
-template <int N, int B>
-__device__ void evaluate(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N, B>& S, int buf) {
+template <int N, int B, bool X>
+__device__ void evaluate(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int buf) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float fpart = 0.f, mind = INFINITY;
-  for (int t = tid; t < tp.T; t += kThreads) eval_timestep<N, B>(rc, tp, S, buf, t, fpart);
+  for (int t = tid; t < tp.T; t += kThreads) eval_timestep<N, B, X>(rc, tp, S, buf, t, fpart);
   __syncthreads();
-  for (int t = warp; t < tp.T; t += kWarps) eval_collisions<N, B>(rc, tp, S, buf, t, lane, fpart, mind);
+  for (int t = warp; t < tp.T; t += kWarps) eval_collisions<N, B, X>(rc, tp, S, buf, t, lane, fpart, mind);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     fpart += __shfl_xor_sync(0xffffffffu, fpart, o);
@@ -513,8 +515,8 @@ __device__ void evaluate(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<
 //   A_tt - sum_k L_{t,t-k} L_{t,t-k}^T
 // is factored densely.  Returns false if a diagonal block was not positive
 // definite.
-template <int N, int B>
-__device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B>& S, int buf, float lam) {
+template <int N, int B, bool X>
+__device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int buf, float lam) {
   constexpr int NT = N * (N + 1) / 2;
   const int tid = threadIdx.x, T = tp.T;
   if (tid == 0) S.chol_fail = 0;
@@ -526,7 +528,7 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B>& S, int buf
       const int i = tid / N, j = tid % N;
       const float cb = sb[B];
       float m = ((i == j) ? sb[B - 1] : 0.f);
-      if constexpr (B == 2) m += S.E[buf][t][i][j];
+      if constexpr (B == 2 && X) m += S.E[buf][t][i][j];
       if (t >= B) {
         S.L[B - 1][t][i][j] = (j >= i) ? cb * S.Linv[t - B][tri(j, i)] : 0.f;
 #pragma unroll
@@ -543,7 +545,8 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B>& S, int buf
         if (tid < N * N && t >= k) {
           const int i = tid / N, j = tid % N;
           float m = ((i == j) ? sb[k] : 0.f);
-          if (k == 1) m += S.E[buf][t][i][j];
+          if constexpr (X)
+            if (k == 1) m += S.E[buf][t][i][j];
 #pragma unroll
           for (int mm = k + 1; mm <= B; ++mm)
             if (t >= mm)
@@ -653,7 +656,7 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B>& S, int buf
   return ok;
 }
 
-template <int N, int B>
+template <int N, int B, bool X>
 __global__ void __launch_bounds__(kThreads) trajopt_kernel(
     const __grid_constant__ ChainC<N> rc, const __grid_constant__ TrajParamsDev tp, const float* __restrict__ q_start,
     const float* __restrict__ goals, const float* __restrict__ q_init, const float* __restrict__ radii,
@@ -661,7 +664,7 @@ __global__ void __launch_bounds__(kThreads) trajopt_kernel(
     int32_t* __restrict__ status_out, float* __restrict__ D_out, float* __restrict__ E_out,
     float* __restrict__ g_out) {
   extern __shared__ float4 smem_f4[];
-  TrajSmem<N, B>& S = *reinterpret_cast<TrajSmem<N, B>*>(smem_f4);
+  TrajSmem<N, B, X>& S = *reinterpret_cast<TrajSmem<N, B, X>*>(smem_f4);
   const int b = blockIdx.x, tid = threadIdx.x, T = tp.T;
   // inputs
   for (int i = tid; i < T * N; i += kThreads) S.x[0][i / N][i % N] = q_init[(size_t)b * T * N + i];
@@ -675,7 +678,7 @@ __global__ void __launch_bounds__(kThreads) trajopt_kernel(
     rt_store(S.Tgi, Gi);
   }
   __syncthreads();
-  evaluate<N, B>(rc, tp, S, 0);
+  evaluate<N, B, X>(rc, tp, S, 0);
   if (D_out) {
     // normal equations only: full diagonal blocks (smoothness included) and J^T r
     for (int i = tid; i < T * N * N; i += kThreads) {
@@ -690,7 +693,9 @@ __global__ void __launch_bounds__(kThreads) trajopt_kernel(
         const int t = i / (N * N), r = (i / N) % N, c = i % N;
         float sb[B + 1];
         smooth_band<B>(tp, t, sb);
-        E_out[(size_t)b * T * N * N + i] = t >= 1 ? S.E[0][t][r][c] + ((r == c) ? sb[1] : 0.f) : 0.f;
+        float e = 0.f;
+        if constexpr (X) e = S.E[0][t][r][c];
+        E_out[(size_t)b * T * N * N + i] = t >= 1 ? e + ((r == c) ? sb[1] : 0.f) : 0.f;
       }
     for (int i = tid; i < T * N; i += kThreads) g_out[(size_t)b * T * N + i] = S.g[0][i / N][i % N];
     if (tid == 0) cost_out[b] = S.f[0];
@@ -699,12 +704,12 @@ __global__ void __launch_bounds__(kThreads) trajopt_kernel(
   int u = 0;  // buffer of the accepted trajectory
   float lam = tp.lambda0;
   for (int it = 0; it < tp.iters; ++it) {
-    const bool ok = banded_solve<N, B>(tp, S, u, lam);
+    const bool ok = banded_solve<N, B, X>(tp, S, u, lam);
     if (ok) {
       const int c = u ^ 1;
       for (int i = tid; i < T * N; i += kThreads) S.x[c][i / N][i % N] = S.x[u][i / N][i % N] + S.y[i / N][i % N];
       __syncthreads();
-      evaluate<N, B>(rc, tp, S, c);
+      evaluate<N, B, X>(rc, tp, S, c);
       if (S.f[c] < S.f[u]) {
         u = c;
         lam = fmaxf(lam / tp.nu, tp.lambda_min);
@@ -726,21 +731,21 @@ __global__ void __launch_bounds__(kThreads) trajopt_kernel(
   }
 }
 
-template <int N, int B>
+template <int N, int B, bool X>
 cudaError_t trajopt_launch(const ChainHost& ch, const TrajParamsDev& tp, int batch, const float* q_start,
                            const float* goals, const float* q_init, const float* radii, const float* obs,
                            float* q_out, float* cost_out, int32_t* status_out, float* D_out, float* E_out,
                            float* g_out, cudaStream_t st) {
-  const size_t smem = sizeof(TrajSmem<N, B>);
+  const size_t smem = sizeof(TrajSmem<N, B, X>);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(trajopt_kernel<N, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(trajopt_kernel<N, B, X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const ChainC<N> rc = chain_const<N>(ch);
   TraceScope tr("trajopt", st);
-  trajopt_kernel<N, B><<<batch, kThreads, smem, st>>>(rc, tp, q_start, goals, q_init, radii, obs, q_out, cost_out,
+  trajopt_kernel<N, B, X><<<batch, kThreads, smem, st>>>(rc, tp, q_start, goals, q_init, radii, obs, q_out, cost_out,
                                                    status_out, D_out, E_out, g_out);
   return cudaGetLastError();
 }
@@ -751,15 +756,21 @@ cudaError_t launch_trajopt(const ChainHost& ch, const TrajParamsDev& tp, int bat
                            const float* goals, const float* q_init, const float* radii, const float* obs,
                            float* q_out, float* cost_out, int32_t* status_out, float* D_out, float* E_out,
                            float* g_out, cudaStream_t st) {
-  // four block sub-diagonals only when a five-point stencil is on (the
-  // band-2 layout keeps two CTAs per SM)
+  // four block sub-diagonals only when a five-point stencil is on, full
+  // (t, t-1) blocks only with velocity-limit or swept rows: the smallest
+  // shared-memory layout runs (three CTAs per SM without either)
   const bool b4 = tp.w_acc5 != 0.f || tp.w_jerk != 0.f;
+  const bool x = tp.w_vlimit > 0.f || tp.w_swept > 0.f;
 #define PK_TRAJ_ARGS ch, tp, batch, q_start, goals, q_init, radii, obs, q_out, cost_out, status_out, D_out, E_out, g_out, st
-  switch (ch.n * 8 + (b4 ? 4 : 2)) {
-    case 6 * 8 + 2: return trajopt_launch<6, 2>(PK_TRAJ_ARGS);
-    case 6 * 8 + 4: return trajopt_launch<6, 4>(PK_TRAJ_ARGS);
-    case 7 * 8 + 2: return trajopt_launch<7, 2>(PK_TRAJ_ARGS);
-    case 7 * 8 + 4: return trajopt_launch<7, 4>(PK_TRAJ_ARGS);
+  switch ((ch.n == 7 ? 4 : 0) + (b4 ? 2 : 0) + (x ? 1 : 0) + (ch.n == 6 || ch.n == 7 ? 0 : 8)) {
+    case 0: return trajopt_launch<6, 2, false>(PK_TRAJ_ARGS);
+    case 1: return trajopt_launch<6, 2, true>(PK_TRAJ_ARGS);
+    case 2: return trajopt_launch<6, 4, false>(PK_TRAJ_ARGS);
+    case 3: return trajopt_launch<6, 4, true>(PK_TRAJ_ARGS);
+    case 4: return trajopt_launch<7, 2, false>(PK_TRAJ_ARGS);
+    case 5: return trajopt_launch<7, 2, true>(PK_TRAJ_ARGS);
+    case 6: return trajopt_launch<7, 4, false>(PK_TRAJ_ARGS);
+    case 7: return trajopt_launch<7, 4, true>(PK_TRAJ_ARGS);
     default: return cudaErrorInvalidValue;
   }
 }
