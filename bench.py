@@ -404,7 +404,7 @@ def extra_workloads(torch, pk, synth, args, flush, stream):
     t_tf = cfg["batch"] * cfg["iters"] * TRAJ_FLOPS_PER_ITER / (k_ms / 1e3) / 1e12
     out["trajopt"] = {"workload": cfg["name"], "value": cfg["batch"] * tsteps / (tms / 1e3), "unit": "trajectories/s",
                       "ms_per_step": tms / tsteps, "kernel_ms": k_ms,
-                      "roofline": {"bound": "alu", "kernel": "trajopt_kernel<7, 2>", "achieved": t_tf,
+                      "roofline": {"bound": "alu", "kernel": "trajopt_kernel<7, 2, false>", "achieved": t_tf,
                                    "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": t_tf / FP32_PEAK_TFLOPS},
                       "goal_reached": float(np.mean((st & pk.PK_T_GOAL_MISSED) == 0)),
                       "collision_free": float(np.mean((st & pk.PK_T_COLLISION) == 0)),
