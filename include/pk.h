@@ -488,6 +488,12 @@ pk_status pk_seednet_forward(pk_seednet* net, int32_t batch, const float* d_targ
 pk_status pk_seednet_infer(pk_seednet* net, int32_t batch, const float* d_targets, float* d_seeds_out,
                            void* stream);
 
+/* Synchronises `stream` and reports a device-side failure recorded by earlier
+ * asynchronous calls on this network (pk_seednet_infer, pk_seednet_forward):
+ * a tensor-core pipeline wait that ran out its bound returns PK_ERR_TIMEOUT
+ * (the record is cleared).  PK_OK otherwise. */
+pk_status pk_seednet_check(pk_seednet* net, void* stream);
+
 /* Mean loss and gradient (host, parameter layout above) of one batch with
  * labels d_qstar [batch][n_dof], mu = 0.01.  Synchronous. */
 pk_status pk_seednet_loss_grad(pk_seednet* net, int32_t batch, const float* d_targets,

@@ -924,6 +924,11 @@ pk_status pk_seednet_infer(pk_seednet* s, int32_t batch, const float* d_targets,
   return sn_cuda(e, "pk_seednet_infer");
 }
 
+pk_status pk_seednet_check(pk_seednet* s, void* stream) {
+  if (!s) return sn_fail(PK_ERR_INVALID_ARG, "net is NULL");
+  return check_err(s, (cudaStream_t)stream);
+}
+
 pk_status pk_seednet_loss_grad(pk_seednet* s, int32_t batch, const float* d_targets, const float* d_qstar,
                                float* host_loss, float* host_grad, void* stream) {
   if (!s) return sn_fail(PK_ERR_INVALID_ARG, "net is NULL");

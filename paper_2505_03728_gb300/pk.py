@@ -111,6 +111,7 @@ _SIGNATURES = {
     "pk_ik_plan_schedule": (_i32, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p]),
     "pk_ik_plan_set_schedule": (_i32, [_vp, _i32, _i32, _i32, _i32]),
     "pk_ik_plan_stats": (_i32, [_vp, C.POINTER(C.c_int64)]),
+    "pk_seednet_check": (_i32, [_vp, _vp]),
     "pk_trajopt_params_default": (None, [_vp]),
     "pk_trajopt_solve": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _i32, _vp, _f32p, _vp, _vp,
                                 _vp, _vp]),
@@ -462,6 +463,11 @@ def pk_seednet_infer(net: SeedNet, targets: torch.Tensor, out: torch.Tensor | No
     _check(lib().pk_seednet_infer(net.handle, B, _dev(targets, name="targets"), _dev(out, name="seeds"),
                                   _stream(stream)))
     return out
+
+
+def pk_seednet_check(net: SeedNet, stream=None):
+    """Synchronise and raise PkError (PK_ERR_TIMEOUT) for a device-side pipeline failure of earlier calls."""
+    _check(lib().pk_seednet_check(net.handle, _stream(stream)))
 
 
 def pk_seednet_loss_grad(net: SeedNet, targets: torch.Tensor, qstar: torch.Tensor, stream=None):

@@ -1,6 +1,7 @@
 """Whole-network seed inference (one persistent tcgen05 kernel: features,
-hidden layers with activations kept in shared memory, joint-limit head)
-against the layer-by-layer GEMM path and the FP64 oracle.
+hidden layers with the activations kept in tensor memory as the MMA's A
+operand, joint-limit head) against the layer-by-layer GEMM path and the FP64
+oracle.
 
 Both GPU paths run the same MMA shapes in the same K order and the same
 epilogue arithmetic, so their seeds agree to FP32 rounding of the head
@@ -135,3 +136,11 @@ def test_fused_inference_graph_replay_and_stream():
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
+
+
+def test_check_reports_no_device_failure_after_inference():
+    net, o, dims, params, T = make("chain7", 8, 512, 4, 3000)
+    infer(net, T, True)
+    pk.pk_seednet_check(net)  # raises PkError on a recorded pipeline timeout
+    infer(net, T, False)
+    pk.pk_seednet_check(net)
