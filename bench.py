@@ -238,13 +238,14 @@ class Timed:
         return float(sum(a.elapsed_time(b) for a, b in zip(self.s, self.e)))
 
 
-def reduce_over_ranks(torch, world, ms, count):
+def reduce_over_ranks(torch, world, ms, count, device="cuda"):
+    """Job time = the slowest rank's (MAX), converged count = the sum over ranks."""
     if world == 1:
         return ms, count
     import torch.distributed as dist
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    c = torch.tensor([count], dtype=torch.int64, device="cuda")
+    c = torch.tensor([count], dtype=torch.int64, device=device)
     dist.all_reduce(c, op=dist.ReduceOp.SUM)
     return float(t.item()), int(c.item())
 
