@@ -127,6 +127,19 @@ def test_five_point_rows_are_the_stencils_and_widen_the_band_to_four():
     rq, _ = oracle.traj_residual(rb, prm, scene, xq, qs, goal)
     np.testing.assert_allclose(rq[-nr:], 0.0, atol=1e-12)
     np.testing.assert_allclose(rq[-2 * nr:-nr], 2.0 * 0.006, atol=1e-12)
+    # closed forms: the fourth-order acceleration stencil is exact up to degree 5,
+    # the second-order jerk stencil up to degree 4 (dt = 1): rows equal the
+    # analytic derivatives of a quintic / quartic at the interior steps
+    cq = rng.normal(0, 1e-3, (6, N))  # x(t) = sum_k c_k t^k
+    xp = qs + sum(cq[k] * tt ** k for k in range(1, 6))
+    rp, _ = oracle.traj_residual(rb, prm, scene, xp, qs, goal)
+    ti = tt[2:-2]
+    d2 = sum(k * (k - 1) * cq[k] * ti ** (k - 2) for k in range(2, 6))
+    np.testing.assert_allclose(rp[-2 * nr:-nr], 2.0 * d2.ravel(), rtol=1e-9, atol=1e-12)
+    xp4 = qs + sum(cq[k] * tt ** k for k in range(1, 5))
+    rp4, _ = oracle.traj_residual(rb, prm, scene, xp4, qs, goal)
+    d3 = sum(k * (k - 1) * (k - 2) * cq[k] * ti ** (k - 3) for k in range(3, 5))
+    np.testing.assert_allclose(rp4[-nr:], 3.0 * d3.ravel(), rtol=1e-9, atol=1e-12)
     f, A, g = oracle.traj_normal(rb, prm, scene, x, qs, goal)
     nz = lambda t, u: np.any(A[t * N:(t + 1) * N, u * N:(u + 1) * N] != 0.0)
     assert nz(6, 2) and not nz(7, 2)  # blocks at distance 4 are filled, beyond 4 empty
