@@ -85,6 +85,7 @@ CASES = [  # robot, K, width, depth, batch
     ("chain7", 8, 512, 4, 128),
     ("chain7", 8, 512, 4, 300),
     ("chain7", 8, 512, 4, 20011),
+    ("chain7", 8, 512, 4, 65536),  # the benchmark's batch and launch configuration
     ("chain7", 4, 256, 2, 1000),
     ("chain7", 8, 256, 1, 257),
     ("hand24", 8, 512, 3, 700),
