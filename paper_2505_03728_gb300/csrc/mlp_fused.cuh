@@ -15,7 +15,7 @@
 //                            the first chunk's BF16 results while the second
 //                            is computed, and the head's output staging.
 //
-// Measured on this part (M = 128, K = 16, BF16): an MMA instruction costs a
+// Measured on sm_103a (M = 128, K = 16, BF16): an MMA instruction costs a
 // fixed ~116 cycles up to N = 128; at N = 256 it takes ~138 cycles with A in
 // TMEM and ~171 with A in shared memory, so N = 256 with A in TMEM is the
 // only shape near the tensor peak.  A TMA request likewise costs a roughly
