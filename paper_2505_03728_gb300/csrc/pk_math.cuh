@@ -13,11 +13,25 @@
 
 namespace pk {
 
-// sin and cos of an angle in radians through sincospif: its range reduction is
-// exact (x mod 2), so no large-argument reduction path is compiled in.  The
-// extra rounding of x / pi is below one ulp of x.
+// sin and cos of an angle in radians: Cody-Waite reduction x = k pi/2 + r
+// with pi/2 split into a float head and tail (two FMAs; exact enough for the
+// few-radian joint angles of the LM iterates), then the Taylor series of sin
+// and cos on |r| <= pi/4 (truncated after r^9 / 9! and r^10 / 10!:
+// truncation below 2e-9), and the quadrant from k mod 4.  A few FMAs instead
+// of a general library routine keeps one LM iteration of one thread short.
 __device__ __forceinline__ void sincos_rad(float x, float* s, float* c) {
-  sincospif(x * 0.318309886183790672f, s, c);
+  const float kf = rintf(x * 0.636619772367581343f);  // 2 / pi
+  float r = fmaf(-kf, 1.57079637050628662f, x);       // pi/2 rounded to float
+  r = fmaf(-kf, -4.37113900018624283e-8f, r);         // pi/2 - (its float)
+  const float r2 = r * r;
+  const float sp = fmaf(r2, fmaf(r2, fmaf(r2, fmaf(r2, 2.75573192e-6f, -1.98412698e-4f), 8.33333333e-3f),
+                                 -1.66666667e-1f), 1.f) * r;
+  const float cp = fmaf(r2, fmaf(r2, fmaf(r2, fmaf(r2, fmaf(r2, -2.75573192e-7f, 2.48015873e-5f), -1.38888889e-3f),
+                                           4.16666667e-2f), -0.5f), 1.f);
+  const int q = (int)kf & 3;
+  const float ss = (q & 1) ? cp : sp, cc = (q & 1) ? sp : cp;
+  *s = (q & 2) ? -ss : ss;
+  *c = ((q + 1) & 2) ? -cc : cc;
 }
 
 struct Rt {
