@@ -39,20 +39,20 @@ UNIT = "solves/s"
 # FP32 operations (add, mul = 1; fma = 2) per unit of work of the fused LM
 # kernel for the 7-DoF chain, from ncu's per-thread executed FADD/FMUL/FFMA
 # counts over launches with known work counters (see profiles/).
-FLOPS_PER_EVAL = 1207.4
-FLOPS_PER_BUILD = 1362.0
-FLOPS_PER_SOLVE = 172.4
+FLOPS_PER_EVAL = 1216.6
+FLOPS_PER_BUILD = 1320.5
+FLOPS_PER_SOLVE = 193.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
 # DRAM bytes (read + write) per target of the LM kernel: ncu capture of the
 # 16,384-target learned-seed launch (4.586 MB), inputs read once (see profiles/).
-LM_DRAM_BYTES_PER_TARGET = 4586240 / 16384
+LM_DRAM_BYTES_PER_TARGET = 4584192 / 16384
 MLP_DRAM_BYTES_65536 = 4962048.0  # mlp_fused_kernel, dram__bytes_read.sum + write.sum per launch
 # FP32 operations per trajectory-iteration of the trajectory kernel (ncu count
 # over 64 trajectories x 50 iterations, see profiles/).
 TRAJ_FLOPS_PER_ITER = 1.995e6
 
 
-CASES = ("lm", "lm-learned", "seednet", "tree", "trajopt")
+CASES = ("lm", "lm-learned", "lm-flops", "seednet", "tree", "trajopt")
 
 
 def parse():
@@ -418,6 +418,9 @@ def run_case(args):
     """Small single-kernel workloads for ncu captures (the commands in profiles/):
     lm          pk_ik_solve, 7-DoF chain, uniform seeds, --batch targets x 8, 2 solves
     lm-learned  the same with seeds from a briefly trained seed network
+    lm-flops    three pk_ik_solve launches of --batch targets x 8 uniform seeds without early exit
+                (max_iters 0, 1, 10), printing their work counters: with ncu's FP32 instruction
+                counters they give the per-unit flops of an evaluation, a build and a solve
     seednet     pk_seednet_infer of an untrained network over --batch targets, 3 calls
     tree        pk_ik_solve on the 30-joint humanoid (6 pose targets), --batch targets x 8, 2 solves
     trajopt     pk_trajopt_solve, --batch trajectories of the trajectory workload, 2 solves"""
@@ -426,6 +429,17 @@ def run_case(args):
     build.build()
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
     B = args.batch
+    if args.case == "lm-flops":
+        spec, qt, sd = synth.ik_workload(synth.IK_THROUGHPUT, B)
+        g = pk.Robot.from_spec(spec)
+        ee = g.n_joints - 1
+        T = pk.pk_fk(g, dev(qt))[:, ee:ee + 1].contiguous()
+        ws = torch.empty(pk.pk_ik_workspace_bytes(g, B, 8), dtype=torch.uint8, device="cuda")
+        for mi in (0, 1, 10):
+            pk.pk_ik_solve(g, pk.pk_ik_params_default(max_iters=mi, early_exit=0), [ee], None, T, dev(sd), ws)
+            torch.cuda.synchronize()
+            print("ok lm-flops max_iters", mi, pk.pk_ik_workspace_stats(ws))
+        return
     if args.case in ("lm", "lm-learned", "seednet"):
         spec, qt, sd = synth.ik_workload(synth.IK_THROUGHPUT, B)
         g = pk.Robot.from_spec(spec)
