@@ -146,3 +146,15 @@ def test_check_reports_no_device_failure_after_inference():
     pk.pk_seednet_check(net)  # raises PkError on a recorded pipeline timeout
     infer(net, T, False)
     pk.pk_seednet_check(net)
+
+
+def test_shapes_outside_the_fused_kernel_use_the_gemms():
+    # 16 seeds x 30 joints = 480 head outputs (> 256) and width 1024: the
+    # layer-by-layer GEMMs serve both, with or without PK_SEEDNET_FUSED
+    for robot, K, width, depth in (("humanoid30", 16, 512, 2), ("chain7", 8, 1024, 2)):
+        net, o, dims, params, T = make(robot, K, width, depth, 300)
+        a = infer(net, T, True)
+        b = infer(net, T, False)
+        assert a.shape == (300, K, o.n_dof)
+        np.testing.assert_array_equal(a, b)
+        pk.pk_seednet_check(net)
