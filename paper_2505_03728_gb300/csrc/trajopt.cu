@@ -382,7 +382,38 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
     for (int i = 0; i < 3; ++i) c[i] = fmaf(al, S.p[t][l + 1][i] - S.p[t][l][i], S.p[t][l][i]);
     const float rad = S.rad[l][s];
     const float wc = tp.w_coll;
-    for (int o = 0; o <= tp.n_obs; ++o) {
+    // screening: the signed distance to every obstacle, four independent
+    // tests at a time (few pairs come within eta); the contributions below
+    // run only for a sphere with an active pair, with the same distances
+    bool act = false;
+    int o0 = 0;
+    for (; o0 + 4 <= tp.n_obs; o0 += 4) {
+      float dd[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 ob = *reinterpret_cast<const float4*>(S.obs[o0 + u]);
+        const float v0 = c[0] - ob.x, v1 = c[1] - ob.y, v2 = c[2] - ob.z;
+        dd[u] = sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2))) - rad - ob.w;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        mind = fminf(mind, dd[u]);
+        act = act || dd[u] < tp.eta;
+      }
+    }
+    for (; o0 < tp.n_obs; ++o0) {
+      const float4 ob = *reinterpret_cast<const float4*>(S.obs[o0]);
+      const float v0 = c[0] - ob.x, v1 = c[1] - ob.y, v2 = c[2] - ob.z;
+      const float d = sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2))) - rad - ob.w;
+      mind = fminf(mind, d);
+      act = act || d < tp.eta;
+    }
+    if (l != 0) {  // the first link is not tested against the plane
+      const float d = tp.plane[0] * c[0] + tp.plane[1] * c[1] + tp.plane[2] * c[2] - tp.plane[3] - rad;
+      mind = fminf(mind, d);
+      act = act || d < tp.eta;
+    }
+    for (int o = act ? 0 : tp.n_obs + 1; o <= tp.n_obs; ++o) {
       float d, nrm[3];
       if (o < tp.n_obs) {
         const float4 ob = *reinterpret_cast<const float4*>(S.obs[o]);
@@ -396,7 +427,6 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
         nrm[0] = tp.plane[0]; nrm[1] = tp.plane[1]; nrm[2] = tp.plane[2];
         d = nrm[0] * c[0] + nrm[1] * c[1] + nrm[2] * c[2] - tp.plane[3] - rad;
       }
-      mind = fminf(mind, d);
       float df;
       const float fa = coll_act(d, tp.eta, &df);
       if (df == 0.f) continue;
