@@ -49,7 +49,7 @@ LM_DRAM_BYTES_PER_TARGET = 4584192 / 16384
 MLP_DRAM_BYTES_65536 = 4962048.0  # mlp_fused_kernel, dram__bytes_read.sum + write.sum per launch
 # FP32 operations per trajectory-iteration of the trajectory kernel (ncu count
 # over 64 trajectories x 50 iterations, see profiles/).
-TRAJ_FLOPS_PER_ITER = 1.995e6
+TRAJ_FLOPS_PER_ITER = 1.553e6
 
 
 CASES = ("lm", "lm-learned", "lm-flops", "seednet", "tree", "trajopt")
