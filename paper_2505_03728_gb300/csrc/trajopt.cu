@@ -51,6 +51,14 @@ struct TrajSmem {
   float Sch[NT];
   float tmp[8];
   float y[kTrajMaxT][8];
+  // two-ended factorisation (B = 2): per-chain scratch and the four-row junction
+  float cM[2][N][N];
+  float cSch[2][NT];
+  float ctmp[2][8];
+  float JD[4][NT];      // junction diagonal blocks after both chains' updates
+  float JE[2][N][N];    // blocks (m-1, m-2) and (m, m+1) after the chains' updates
+  float JL1[4][N][N];   // junction factor blocks (j, j-1)
+  float JL2[4][N][N];   // junction factor blocks (j, j-2)
   alignas(16) float obs[kTrajMaxObs][4];
   float rad[N][kTrajMaxS];
   float qs[8];
@@ -686,6 +694,283 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int 
   return ok;
 }
 
+// Two-ended factorisation of the band-2 system (T >= 8): rows 0 .. m-3 are
+// eliminated top-down by threads 0-63 while rows T-1 .. m+2 are eliminated
+// bottom-up by threads 64-127 (the same recurrence on the reversed order, the
+// (t, t+1) blocks being transposes of the stored (t+1, t) ones); the four rows
+// m-2 .. m+1 between them (m = T / 2) take both sides' updates and are
+// factored last.  The serial chain is half as long as banded_solve's and the
+// solve is the same up to rounding order.  Factor blocks: L[0][t], L[1][t] are
+// row t against its first and second predecessor in its chain's order.
+template <int N, bool X>
+__device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int buf, float lam) {
+  constexpr int NT = N * (N + 1) / 2, NN = N * N;
+  const int tid = threadIdx.x, T = tp.T, m = T / 2;
+  const int grp = (tid >> 6) & 1, gt = tid & 63;  // chain (0 top, 1 bottom) and thread within it
+  auto gsync = [&] { asm volatile("bar.sync %0, 64;" ::"r"(1 + grp) : "memory"); };
+  if (tid == 0) S.chol_fail = 0;
+  __syncthreads();
+  // smoothness scalar of block (t, u), 0 <= t - u <= 2
+  auto sc = [&](int t, int u) {
+    float sb[3];
+    smooth_band<2>(tp, t, sb);
+    return sb[t - u];
+  };
+  // element (i, j) of the off-diagonal block (t, u) of A, |t - u| = 1
+  auto a1 = [&](int t, int u, int i, int j) {
+    const int hi = t > u ? t : u;
+    const float sv = sc(hi, hi - 1);
+    float v = (i == j) ? sv : 0.f;
+    if constexpr (X) v += (t > u) ? S.E[buf][t][i][j] : S.E[buf][u][j][i];
+    return v;
+  };
+  // dense factor of a Schur complement (one thread), its inverse into Linv[t]
+  // (N threads); `sync` is the barrier of the threads taking part
+  auto factor_diag = [&](float* sch, int t, int lt, auto&& sync) {
+    if (lt == 0) {
+      float L[NT];
+#pragma unroll
+      for (int i = 0; i < NT; ++i) L[i] = sch[i];
+      if (!chol_packed<N>(L)) S.chol_fail = 1;
+#pragma unroll
+      for (int i = 0; i < NT; ++i) sch[i] = L[i];
+    }
+    sync();
+    if (lt < N) {
+      const int j = lt;
+      float col[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float v = (i == j) ? 1.f : 0.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          if (k >= j && k < i) v = fmaf(-sch[tri(i, k)], col[k], v);
+        col[i] = (i >= j) ? v * sch[tri(i, i)] : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i >= j) S.Linv[t][tri(i, j)] = col[i];
+    }
+    sync();
+  };
+  // row t of a chain (direction d: +1 top-down, -1 bottom-up; k = its position
+  // in the chain).  mode 0: full; 1: up to the Schur complement, kept in
+  // JD[jd]; 2: the last row: its block against the previous row goes to
+  // JE[grp] (not divided by that row's factor, which the junction computes)
+  // and the Schur complement without it to JD[jd]
+  auto chain_row = [&](int t, int d, int k, int mode, int jd) {
+    const int p1 = t - d, p2 = t - 2 * d;
+    const float c2 = k >= 2 ? (d > 0 ? sc(t, p2) : sc(p2, t)) : 0.f;
+    float* Mc = mode == 2 ? &S.JE[grp][0][0] : &S.cM[grp][0][0];
+    if (k >= 1)
+      for (int e = gt; e < NN; e += 64) {
+        const int i = e / N, j = e % N;
+        float mm = a1(t, p1, i, j);
+        if (k >= 2) {
+          S.L[1][t][i][j] = (j >= i) ? c2 * S.Linv[p2][tri(j, i)] : 0.f;
+#pragma unroll
+          for (int q = 0; q < N; ++q)
+            if (q >= i) mm = fmaf(-c2 * S.Linv[p2][tri(q, i)], S.L[0][p1][j][q], mm);
+        }
+        Mc[e] = mm;
+      }
+    gsync();
+    if (mode != 2 && k >= 1) {
+      for (int e = gt; e < NN; e += 64) {
+        const int i = e / N, j = e % N;
+        float v = 0.f;
+#pragma unroll
+        for (int q = 0; q < N; ++q)
+          if (q <= j) v = fmaf(Mc[i * N + q], S.Linv[p1][tri(j, q)], v);
+        S.L[0][t][i][j] = v;
+      }
+      gsync();
+    }
+    if (gt < NT) {
+      int i = 0;
+      while ((i + 1) * (i + 2) / 2 <= gt) ++i;
+      const int j = gt - i * (i + 1) / 2;
+      float v = S.D[buf][t][gt] + ((i == j) ? sc(t, t) + lam : 0.f);
+      if (mode != 2 && k >= 1)
+#pragma unroll
+        for (int q = 0; q < N; ++q) v = fmaf(-S.L[0][t][i][q], S.L[0][t][j][q], v);
+      if (k >= 2)
+#pragma unroll
+        for (int q = 0; q < N; ++q) v = fmaf(-S.L[1][t][i][q], S.L[1][t][j][q], v);
+      if (mode == 0) S.cSch[grp][gt] = v;
+      else S.JD[jd][gt] = v;
+    }
+    gsync();
+    if (mode == 0) factor_diag(S.cSch[grp], t, gt, gsync);
+  };
+  if (tid < 128) {
+    if (grp == 0) {
+      for (int t = 0; t <= m - 3; ++t) chain_row(t, 1, t, 0, 0);
+      chain_row(m - 2, 1, m - 2, 1, 0);
+      chain_row(m - 1, 1, m - 1, 2, 1);
+    } else {
+      for (int t = T - 1; t >= m + 2; --t) chain_row(t, -1, T - 1 - t, 0, 0);
+      chain_row(m + 1, -1, T - 2 - m, 1, 3);
+      chain_row(m, -1, T - 1 - m, 2, 2);
+    }
+  }
+  __syncthreads();
+  // junction rows m-2 .. m+1 (j = 0 .. 3) by threads 0-63
+  if (tid < 64) {
+    for (int j = 0; j < 4; ++j) {
+      const int t = m - 2 + j;
+      if (j >= 1) {
+        const float c2 = j >= 2 ? sc(t, t - 2) : 0.f;
+        for (int e = gt; e < NN; e += 64) {
+          const int r = e / N, c = e % N;
+          float mm = j == 1 ? S.JE[0][r][c] : j == 2 ? a1(m, m - 1, r, c) : S.JE[1][c][r];
+          if (j >= 2) {
+            S.JL2[j][r][c] = (c >= r) ? c2 * S.Linv[t - 2][tri(c, r)] : 0.f;
+#pragma unroll
+            for (int q = 0; q < N; ++q)
+              if (q >= r) mm = fmaf(-c2 * S.Linv[t - 2][tri(q, r)], S.JL1[j - 1][c][q], mm);
+          }
+          S.cM[0][r][c] = mm;
+        }
+        gsync();
+        for (int e = gt; e < NN; e += 64) {
+          const int r = e / N, c = e % N;
+          float v = 0.f;
+#pragma unroll
+          for (int q = 0; q < N; ++q)
+            if (q <= c) v = fmaf(S.cM[0][r][q], S.Linv[t - 1][tri(c, q)], v);
+          S.JL1[j][r][c] = v;
+        }
+        gsync();
+      }
+      if (gt < NT) {
+        int r = 0;
+        while ((r + 1) * (r + 2) / 2 <= gt) ++r;
+        const int c = gt - r * (r + 1) / 2;
+        float v = S.JD[j][gt];
+        if (j >= 1)
+#pragma unroll
+          for (int q = 0; q < N; ++q) v = fmaf(-S.JL1[j][r][q], S.JL1[j][c][q], v);
+        if (j >= 2)
+#pragma unroll
+          for (int q = 0; q < N; ++q) v = fmaf(-S.JL2[j][r][q], S.JL2[j][c][q], v);
+        S.cSch[0][gt] = v;
+      }
+      gsync();
+      factor_diag(S.cSch[0], t, gt, gsync);
+    }
+  }
+  __syncthreads();
+  const bool ok = S.chol_fail == 0;
+  // forward substitution in each chain: y_t = Linv_t (-g_t - L[0][t] y_p1 - L[1][t] y_p2)
+  auto fwd_row = [&](int t, int d, int k) {
+    if (gt < N) {
+      float v = -S.g[buf][t][gt];
+      if (k >= 1)
+#pragma unroll
+        for (int q = 0; q < N; ++q) v = fmaf(-S.L[0][t][gt][q], S.y[t - d][q], v);
+      if (k >= 2)
+#pragma unroll
+        for (int q = 0; q < N; ++q) v = fmaf(-S.L[1][t][gt][q], S.y[t - 2 * d][q], v);
+      S.ctmp[grp][gt] = v;
+    }
+    gsync();
+    if (gt < N) {
+      float v = 0.f;
+#pragma unroll
+      for (int q = 0; q < N; ++q)
+        if (q <= gt) v = fmaf(S.Linv[t][tri(gt, q)], S.ctmp[grp][q], v);
+      S.y[t][gt] = v;
+    }
+    gsync();
+  };
+  if (tid < 128) {
+    if (grp == 0)
+      for (int t = 0; t <= m - 3; ++t) fwd_row(t, 1, t);
+    else
+      for (int t = T - 1; t >= m + 2; --t) fwd_row(t, -1, T - 1 - t);
+  }
+  __syncthreads();
+  // junction: right-hand sides from both chains, forward, then backward
+  if (tid < 64) {
+    for (int j = 0; j < 4; ++j) {
+      const int t = m - 2 + j;
+      if (gt < N) {
+        float v = -S.g[buf][t][gt];
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+          if (j == 0) v = fmaf(-S.L[0][t][gt][q], S.y[m - 3][q], fmaf(-S.L[1][t][gt][q], S.y[m - 4][q], v));
+          if (j == 1) v = fmaf(-S.L[1][t][gt][q], S.y[m - 3][q], v);
+          if (j == 2) v = fmaf(-S.L[1][t][gt][q], S.y[m + 2][q], v);
+          if (j == 3) v = fmaf(-S.L[0][t][gt][q], S.y[m + 2][q], fmaf(-S.L[1][t][gt][q], S.y[m + 3][q], v));
+          if (j >= 1) v = fmaf(-S.JL1[j][gt][q], S.y[t - 1][q], v);
+          if (j >= 2) v = fmaf(-S.JL2[j][gt][q], S.y[t - 2][q], v);
+        }
+        S.ctmp[0][gt] = v;
+      }
+      gsync();
+      if (gt < N) {
+        float v = 0.f;
+#pragma unroll
+        for (int q = 0; q < N; ++q)
+          if (q <= gt) v = fmaf(S.Linv[t][tri(gt, q)], S.ctmp[0][q], v);
+        S.y[t][gt] = v;
+      }
+      gsync();
+    }
+    for (int j = 3; j >= 0; --j) {
+      const int t = m - 2 + j;
+      if (gt < N) {
+        float v = S.y[t][gt];
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+          if (j + 1 <= 3) v = fmaf(-S.JL1[j + 1][q][gt], S.y[t + 1][q], v);
+          if (j + 2 <= 3) v = fmaf(-S.JL2[j + 2][q][gt], S.y[t + 2][q], v);
+        }
+        S.ctmp[0][gt] = v;
+      }
+      gsync();
+      if (gt < N) {
+        float v = 0.f;
+#pragma unroll
+        for (int q = 0; q < N; ++q)
+          if (q >= gt) v = fmaf(S.Linv[t][tri(q, gt)], S.ctmp[0][q], v);
+        S.y[t][gt] = v;
+      }
+      gsync();
+    }
+  }
+  __syncthreads();
+  // backward substitution in each chain, from the junction outwards:
+  // x_t = Linv_t^T (y_t - L[0][t+d]^T x_{t+d} - L[1][t+2d]^T x_{t+2d})
+  auto bwd_row = [&](int t, int d) {
+    if (gt < N) {
+      float v = S.y[t][gt];
+#pragma unroll
+      for (int q = 0; q < N; ++q)
+        v = fmaf(-S.L[0][t + d][q][gt], S.y[t + d][q], fmaf(-S.L[1][t + 2 * d][q][gt], S.y[t + 2 * d][q], v));
+      S.ctmp[grp][gt] = v;
+    }
+    gsync();
+    if (gt < N) {
+      float v = 0.f;
+#pragma unroll
+      for (int q = 0; q < N; ++q)
+        if (q >= gt) v = fmaf(S.Linv[t][tri(q, gt)], S.ctmp[grp][q], v);
+      S.y[t][gt] = v;
+    }
+    gsync();
+  };
+  if (tid < 128) {
+    if (grp == 0)
+      for (int t = m - 3; t >= 0; --t) bwd_row(t, 1);
+    else
+      for (int t = m + 2; t <= T - 1; ++t) bwd_row(t, -1);
+  }
+  __syncthreads();
+  return ok;
+}
+
 template <int N, int B, bool X>
 __global__ void __launch_bounds__(kThreads) trajopt_kernel(
     const __grid_constant__ ChainC<N> rc, const __grid_constant__ TrajParamsDev tp, const float* __restrict__ q_start,
@@ -734,7 +1019,12 @@ __global__ void __launch_bounds__(kThreads) trajopt_kernel(
   int u = 0;  // buffer of the accepted trajectory
   float lam = tp.lambda0;
   for (int it = 0; it < tp.iters; ++it) {
-    const bool ok = banded_solve<N, B, X>(tp, S, u, lam);
+    bool ok;
+    if constexpr (B == 2) {
+      ok = T >= 8 ? twisted_solve<N, X>(tp, S, u, lam) : banded_solve<N, B, X>(tp, S, u, lam);
+    } else {
+      ok = banded_solve<N, B, X>(tp, S, u, lam);
+    }
     if (ok) {
       const int c = u ^ 1;
       for (int i = tid; i < T * N; i += kThreads) S.x[c][i / N][i % N] = S.x[u][i / N][i % N] + S.y[i / N][i % N];
