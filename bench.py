@@ -5,13 +5,18 @@ chain, 65,536 reachable target poses (FK of uniform in-limit configurations),
 8 seeds per target (524,288 LM problems), up to 50 LM iterations with early
 exit at 1 mm / 0.5 deg, and sibling cancellation (a target stops once one of
 its seeds converged).  Two arms, both timed the same way:
-  * plain:   8 uniform random seeds per target -> pk_ik_solve;
+  * plain:   8 uniform random seeds per target -> pk_ik_solve_split;
   * learned: the seed network (trained on the GPU before timing, untimed)
-             proposes the 8 seeds inside every step -> pk_ik_solve.
-One step = one pass of the arm over the whole batch with inputs resident in
-HBM; every timed step is preceded by an L2 flush (a 256 MiB device write
-outside the timed events).  value = converged targets / device time of the
-learned arm (the plain arm is reported beside it).
+             proposes the 8 seeds inside every step -> pk_ik_solve_split.
+One step = one pass of the arm over one batch of 65,536 targets with inputs
+resident in HBM.  Every step reads its own batch (rotating through batches
+that together hold more than twice the L2); consecutive steps overlap on two
+streams: the LM runs as a first launch over every problem up to a split
+iteration and a narrow continuation of the few problems still running, which
+finishes beside the next step's seed inference.  value = converged targets /
+device time of K learned steps (one pair of CUDA events around the run); the
+plain arm, and both arms one batch at a time with a single LM launch
+("serial", L2 flushed before every step), are reported beside it.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pk|reference]
 Multi-GPU: launched by torchrun, one rank per GPU; every rank solves its own
@@ -50,6 +55,16 @@ MLP_DRAM_BYTES_65536 = 4962048.0  # mlp_fused_kernel, dram__bytes_read.sum + wri
 # FP32 operations per trajectory-iteration of the trajectory kernel (ncu count
 # over 64 trajectories x 50 iterations, see profiles/).
 TRAJ_FLOPS_PER_ITER = 1.553e6
+# Every timed step reads its own input batch; an arm rotates through enough
+# batches to hold at least this many bytes (twice the 129 MB L2).
+ROTATE_BYTES = 256 << 20
+# Split solve (pk_ik_solve_split): the first LM launch carries every problem
+# up to SPLIT iterations; the problems still running continue in a second
+# launch of TAIL_CTAS blocks (0: full grid) beside the next step.  Learned
+# seeds: ~0.6% of the problems are left after 6 iterations, and 16 blocks
+# leave the 128 CTAs of the next step's seed inference their SMs.
+LEARNED_SPLIT, LEARNED_TAIL_CTAS = 6, 16
+PLAIN_SPLIT, PLAIN_TAIL_CTAS = 20, 0
 
 
 CASES = ("lm", "lm-learned", "lm-flops", "seednet", "tree", "trajopt")
@@ -199,7 +214,11 @@ def config_dict(cfg, args, head="plain"):
     return {"workload": cfg["name"], "robot": "synthetic 7-DoF revolute chain (seed 100)",
             "targets": args.batch, "seeds_per_target": cfg["n_seeds"], "max_iters": cfg["max_iters"],
             "early_exit": True, "cancel_siblings": not args.no_cancel, "seeding": seeding,
-            "l2": "flushed by a 256 MiB device write before every timed step"}
+            "l2": ("inputs larger than L2: every step reads its own batch, rotating through batches of at least "
+                   "256 MiB together; L2 flushed once before each timed run"),
+            "pipeline": ("steps overlap on two streams: seed inference and the first LM launch (all problems, "
+                         f"up to {LEARNED_SPLIT if head == 'learned' else PLAIN_SPLIT} iterations) on one, the "
+                         "continuation of the problems still running and the best-seed selection on the other")}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -236,6 +255,35 @@ class Timed:
                 after(k)
         self.torch.cuda.synchronize()
         return float(sum(a.elapsed_time(b) for a, b in zip(self.s, self.e)))
+
+
+class Pipelined:
+    """K steps enqueued back to back on two streams: a step's seed inference
+    and first LM launch on `main`, its LM continuation and best-seed
+    selection on `tail`, so that step k+1 starts while step k's slow problems
+    finish.  Step k reuses step k-2's workspace and waits for its end.  One
+    pair of CUDA events on `main` brackets the whole run (main joins tail
+    before the end event); L2 is flushed once before it."""
+
+    def __init__(self, torch, steps, flush):
+        self.torch, self.steps, self.flush = torch, steps, flush
+        self.start = torch.cuda.Event(enable_timing=True)
+        self.end = torch.cuda.Event(enable_timing=True)
+        self.done = [torch.cuda.Event() for _ in range(steps)]
+
+    def run(self, step_fn, main, tail):
+        self.flush.zero_()
+        self.torch.cuda.synchronize()
+        self.start.record(main)
+        for k in range(self.steps):
+            if k >= 2:
+                main.wait_event(self.done[k - 2])
+            step_fn(k)
+            self.done[k].record(tail)
+        main.wait_stream(tail)
+        self.end.record(main)
+        self.torch.cuda.synchronize()
+        return float(self.start.elapsed_time(self.end))
 
 
 def reduce_over_ranks(torch, world, ms, count, device="cuda"):
@@ -527,13 +575,49 @@ def main():
             torch.empty(B, dtype=torch.int32, device="cuda"), torch.empty(B, dtype=torch.int32, device="cuda"))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    tail = torch.cuda.Stream()
+
+    # ---- rotating input batches: step k reads batch k % R, and an arm's R
+    # batches together exceed twice the 129 MB L2, so no timed step finds its
+    # inputs in L2 from an earlier step.  Batch 0 is the workload's own; the
+    # others are drawn the same way on the device (configurations uniform in
+    # the limits -> FK targets; seeds uniform in the limits).
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(cfg_r["target_seed"] * 7919 + 17)
+    lo = torch.tensor(np.asarray(spec.dof_lower), dtype=torch.float32, device="cuda")
+    hi = torch.tensor(np.asarray(spec.dof_upper), dtype=torch.float32, device="cuda")
+
+    def uniform_q_dev(*shape):
+        return lo + (hi - lo) * torch.rand(*shape, n, generator=gen, device="cuda")
+
+    def n_batches(bytes_per_batch):
+        return max(2, -(-ROTATE_BYTES // bytes_per_batch))
+
+    R_t = n_batches(B * 12 * 4)
+    T_rot = torch.empty(R_t, B, 1, 12, device="cuda")
+    T_rot[0] = targets
+    for r in range(1, R_t):
+        T_rot[r] = pk.pk_fk(robot, uniform_q_dev(B))[:, ee:ee + 1]
+    R_s = n_batches(B * 12 * 4 + B * S * n * 4)
+    S_rot = torch.empty(R_s, B, S, n, device="cuda")
+    S_rot[0] = seeds
+    for r in range(1, R_s):
+        S_rot[r] = uniform_q_dev(B, S)
 
     # each timed step writes its own status row; converged targets are counted
     # after the timed region
     status_steps = torch.empty(max(args.steps, 1), B, dtype=torch.int32, device="cuda")
+    wss = [torch.empty(pk.pk_ik_split_workspace_bytes(robot, B, S), dtype=torch.uint8, device="cuda")
+           for _ in range(2)]
 
-    def plain_step(status):
-        pk.pk_ik_solve(robot, params, [ee], None, targets, seeds, ws, out=outs[:3] + (status,))
+    def plain_step(k, status):
+        r = k % R_s
+        pk.pk_ik_solve_split(robot, params, [ee], None, T_rot[r], S_rot[r], wss[k % 2], PLAIN_SPLIT, PLAIN_TAIL_CTAS,
+                             out=outs[:3] + (status,), stream=stream, tail_stream=tail)
+
+    def plain_serial(k, status):
+        r = k % R_s
+        pk.pk_ik_solve(robot, params, [ee], None, T_rot[r], S_rot[r], ws, out=outs[:3] + (status,))
 
     # ---- learned seeds: train once (untimed), then infer + solve per step
     net = None
@@ -547,74 +631,124 @@ def main():
         train_s = time.perf_counter() - t0
         lseeds = torch.empty(B, S, n, device="cuda")
 
-    def learned_step(status):
-        pk.pk_seednet_infer(net, targets, lseeds)
-        pk.pk_ik_solve(robot, params, [ee], None, targets, lseeds, ws, out=outs[:3] + (status,))
+    def learned_step(k, status):
+        tk = T_rot[k % R_t]
+        pk.pk_seednet_infer(net, tk, lseeds, stream=stream)
+        pk.pk_ik_solve_split(robot, params, [ee], None, tk, lseeds, wss[k % 2], LEARNED_SPLIT, LEARNED_TAIL_CTAS,
+                             out=outs[:3] + (status,), stream=stream, tail_stream=tail)
+
+    def learned_serial(k, status):
+        tk = T_rot[k % R_t]
+        pk.pk_seednet_infer(net, tk, lseeds)
+        pk.pk_ik_solve(robot, params, [ee], None, tk, lseeds, ws, out=outs[:3] + (status,))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
 
     props = torch.cuda.get_device_properties(local)
     gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
     results = {}
-    arms = [("plain", plain_step)] + ([("learned", learned_step)] if net is not None else [])
+    arms = [("plain", plain_step, plain_serial)]
+    if net is not None:
+        arms.append(("learned", learned_step, learned_serial))
+    traced = ("ik_lm", "ik_lm_tail", "ik_reduce", "gemm", "seednet_mlp", "features")
     with ClockSampler(gpu_id) as clocks:
-        for name, fn in arms:
-            for _ in range(args.warmup):  # the same kernels the timed steps launch
-                fn(outs[3])
-            torch.cuda.synchronize()
-            if world > 1:
-                import torch.distributed as dist
-                dist.barrier()
+        for name, fn, serial_fn in arms:
+            # the same kernels the timed steps launch
+            Pipelined(torch, args.warmup, flush).run(lambda k: fn(k, outs[3]), stream, tail)
+            barrier()
             pk.pk_trace_enable(True)
-            timed = Timed(torch, args.steps, flush)
             torch.cuda.nvtx.range_push(f"timed_{name}")
-            total_ms = timed.run(lambda k: fn(status_steps[k]), stream)
+            total_ms = Pipelined(torch, args.steps, flush).run(lambda k: fn(k, status_steps[k]), stream, tail)
             torch.cuda.nvtx.range_pop()
-            lm_ms, lm_n = pk.pk_trace_summary("ik_lm")
-            gemm_ms, gemm_n = pk.pk_trace_summary("gemm")
-            mlp_ms, mlp_n = pk.pk_trace_summary("seednet_mlp")  # whole-network inference kernel
-            gemm_ms, gemm_n = gemm_ms + mlp_ms, gemm_n + mlp_n
-            launches = lm_n + gemm_n + sum(pk.pk_trace_summary(k)[1] for k in ("ik_reduce", "features"))
+            tr = {kname: pk.pk_trace_summary(kname) for kname in traced}
             pk.pk_trace_enable(False)
-            stats = pk.pk_ik_workspace_stats(ws)
+            first, second = pk.pk_ik_split_workspace_stats(wss[(args.steps - 1) % 2])
             n_conv = int((status_steps[:args.steps] == pk.PK_P_CONVERGED).sum().item())
-            if world > 1:
-                import torch.distributed as dist
-                dist.barrier()
+            barrier()
             total_ms, n_conv = reduce_over_ranks(torch, world, total_ms, n_conv)
+            # latency view: one batch at a time, single LM launch, L2 flushed
+            # before every step (per-step CUDA events)
+            for _ in range(args.warmup):
+                serial_fn(0, outs[3])
+            torch.cuda.synchronize()
+            barrier()
+            ser_ms = Timed(torch, args.steps, flush).run(lambda k: serial_fn(k, status_steps[k]), stream)
+            ser_conv = int((status_steps[:args.steps] == pk.PK_P_CONVERGED).sum().item())
+            barrier()
+            ser_ms, ser_conv = reduce_over_ranks(torch, world, ser_ms, ser_conv)
+            gemm_ms = tr["gemm"][0] + tr["seednet_mlp"][0]  # layer-wise GEMMs or the whole-network kernel
+            gemm_n = tr["gemm"][1] + tr["seednet_mlp"][1]
             results[name] = dict(value=n_conv / (total_ms / 1e3), ms_per_step=total_ms / args.steps,
-                                 success_rate=n_conv / (B * args.steps * world), lm_ms=lm_ms / max(1, lm_n),
+                                 success_rate=n_conv / (B * args.steps * world),
+                                 lm_ms=tr["ik_lm"][0] / max(1, tr["ik_lm"][1]),
+                                 lm_tail_ms=tr["ik_lm_tail"][0] / max(1, tr["ik_lm_tail"][1]),
                                  gemm_ms=gemm_ms / max(1, args.steps), gemm_launches=gemm_n // max(1, args.steps),
-                                 fused_mlp=mlp_n > 0,
-                                 launches=launches, stats=stats)
+                                 fused_mlp=tr["seednet_mlp"][1] > 0,
+                                 launches=sum(v[1] for v in tr.values()), stats=first, stats_tail=second,
+                                 serial={"value": ser_conv / (ser_ms / 1e3), "ms_per_step": ser_ms / args.steps,
+                                         "success_rate": ser_conv / (B * args.steps * world)})
 
-    # ---- end to end through the public API with host buffers (headline path)
+    # ---- end to end through the public API with host buffers (headline
+    # path): every step copies its inputs from pinned host memory on a copy
+    # stream and reads all of its results back on the tail stream behind the
+    # best-seed selection; steps overlap as in the device-resident run
     head = "learned" if net is not None else "plain"
-    h_t = torch.empty(targets.shape, dtype=torch.float32, pin_memory=True)
-    h_t.copy_(targets)
-    h_s = torch.empty(seeds.shape, dtype=torch.float32, pin_memory=True)
-    h_s.copy_(seeds)
-    h_out = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
-    d_t, d_s = torch.empty_like(targets), torch.empty_like(seeds)
-    e2e_conv, e2e_ms = 0, 0.0
-    for k in range(max(2, args.steps // 2) + 1):
-        flush.zero_()
+    split, tail_ctas = (LEARNED_SPLIT, LEARNED_TAIL_CTAS) if head == "learned" else (PLAIN_SPLIT, PLAIN_TAIL_CTAS)
+    copy = torch.cuda.Stream()
+    Rh = 4
+    h_t = [torch.empty(T_rot.shape[1:], dtype=torch.float32, pin_memory=True) for _ in range(Rh)]
+    h_s = [torch.empty(S_rot.shape[1:], dtype=torch.float32, pin_memory=True) for _ in range(Rh)]
+    for r in range(Rh):
+        h_t[r].copy_(T_rot[r % R_t])
+        if head == "plain":
+            h_s[r].copy_(S_rot[r % R_s])
+    d_t = [torch.empty_like(targets) for _ in range(2)]
+    d_s = [torch.empty_like(seeds) for _ in range(2)]
+    eo = tuple(torch.empty_like(o) for o in outs)
+    h_o = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs[:3]]
+    K_e = max(args.steps, 2)
+    h_status = torch.empty((K_e, B), dtype=torch.int32, pin_memory=True)
+
+    def e2e_run(K):
+        copied = [torch.cuda.Event() for _ in range(K)]
+        done = [torch.cuda.Event() for _ in range(K)]
+        for k in range(K):
+            b = k % 2
+            with torch.cuda.stream(copy):
+                if k >= 2:
+                    copy.wait_event(done[k - 2])  # step k-2's continuation read these buffers
+                d_t[b].copy_(h_t[k % Rh], non_blocking=True)
+                if head == "plain":
+                    d_s[b].copy_(h_s[k % Rh], non_blocking=True)
+                copied[k].record(copy)
+            stream.wait_event(copied[k])
+            if k >= 2:
+                stream.wait_event(done[k - 2])
+            if head == "learned":
+                pk.pk_seednet_infer(net, d_t[b], lseeds, stream=stream)
+                sds = lseeds
+            else:
+                sds = d_s[b]
+            pk.pk_ik_solve_split(robot, params, [ee], None, d_t[b], sds, wss[b], split, tail_ctas, out=eo,
+                                 stream=stream, tail_stream=tail)
+            with torch.cuda.stream(tail):
+                for ho, o in zip(h_o, eo[:3]):
+                    ho.copy_(o, non_blocking=True)
+                h_status[k].copy_(eo[3], non_blocking=True)
+                done[k].record(tail)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        d_t.copy_(h_t, non_blocking=True)
-        if head == "learned":
-            pk.pk_seednet_infer(net, d_t, lseeds)
-            pk.pk_ik_solve(robot, params, [ee], None, d_t, lseeds, ws, out=outs)
-        else:
-            d_s.copy_(h_s, non_blocking=True)
-            pk.pk_ik_solve(robot, params, [ee], None, d_t, d_s, ws, out=outs)
-        for ho, o in zip(h_out, outs):
-            ho.copy_(o, non_blocking=True)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if k > 0:
-            e2e_ms += dt * 1e3
-            e2e_conv += int((h_out[3] == pk.PK_P_CONVERGED).sum())
+
+    e2e_run(max(args.warmup, 2))
+    barrier()
+    t0 = time.perf_counter()
+    e2e_run(K_e)
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    e2e_conv = int((h_status == pk.PK_P_CONVERGED).sum())
     e2e_ms, e2e_conv = reduce_over_ranks(torch, world, e2e_ms, e2e_conv)
-    h2d = h_t.numel() * 4 + (0 if head == "learned" else h_s.numel() * 4)
+    h2d = h_t[0].numel() * 4 + (0 if head == "learned" else h_s[0].numel() * 4)
     d2h = sum(o.numel() * o.element_size() for o in outs)
 
     extra = {} if args.no_extra else extra_workloads(torch, pk, synth, args, flush, stream)
@@ -628,7 +762,8 @@ def main():
         st = r["stats"]
         fl = st["evals"] * FLOPS_PER_EVAL + st["builds"] * FLOPS_PER_BUILD + st["solves"] * FLOPS_PER_SOLVE
         tf = fl / (r["lm_ms"] / 1e3) / 1e12
-        return {"bound": "alu", "kernel": "chain_lm_kernel<7>", "achieved": tf, "peak": FP32_PEAK_TFLOPS,
+        return {"bound": "alu", "kernel": "chain_lm_kernel<7, 1> (first launch of the split solve)",
+                "achieved": tf, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": tf / FP32_PEAK_TFLOPS, "traffic": LM_DRAM_BYTES_PER_TARGET * B,
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (unit counts x max clock)",
                 "ms_per_launch": r["lm_ms"], "work_per_launch": st}
@@ -654,7 +789,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_dict(cfg, args, head),
         "success_rate": r["success_rate"],
-        "plain": dict({k: results["plain"][k] for k in ("value", "ms_per_step", "success_rate", "lm_ms")},
+        "plain": dict({k: results["plain"][k] for k in ("value", "ms_per_step", "success_rate", "lm_ms",
+                                                         "lm_tail_ms", "serial")},
                       roofline=lm_roofline(results["plain"])),
         "roofline": dominant,
         "roofline_other": [x for x in roofs if x is not dominant],
@@ -665,7 +801,8 @@ def main():
     }
     if "learned" in results:
         line["learned"] = {k: results["learned"][k] for k in ("value", "ms_per_step", "success_rate", "lm_ms",
-                                                               "gemm_ms")}
+                                                               "lm_tail_ms", "gemm_ms", "serial")}
+        line["learned"]["tail_work"] = results["learned"]["stats_tail"]
         line["learned"]["train_s"] = train_s
         line["learned"]["train_loss"] = [float(x) for x in train_loss]
         line["learned_over_plain"] = results["learned"]["value"] / results["plain"]["value"]

@@ -226,6 +226,49 @@ pk_status pk_ik_solve_noalloc(const pk_robot* robot, const pk_ik_params* params,
                               int32_t* d_iters_out, int32_t* d_status_out, void* stream);
 
 /*
+ * Scratch that pk_ik_solve_split needs for (batch, n_seeds): the
+ * pk_ik_workspace_bytes() layout plus one index and one damping value per
+ * (target, seed) problem.
+ */
+size_t pk_ik_split_workspace_bytes(const pk_robot* robot, int32_t batch, int32_t n_seeds);
+
+/*
+ * pk_ik_solve_split -- pk_ik_solve (Sec. III-A, Sec. IV-A) in two launches, so
+ * that the iterations of the few slow problems can overlap other work.  Same
+ * arguments, outputs and results as pk_ik_solve, plus:
+ *   split_iters   >= 1: the first launch, on `stream`, carries every problem
+ *                 up to this many LM iterations; a problem still running then
+ *                 (not converged, not cancelled by a converged sibling) is
+ *                 suspended: its configuration, iteration count and damping
+ *                 stay in the workspace.
+ *   tail_ctas     >= 0: 128-thread blocks of the second launch, which resumes
+ *                 the suspended problems and runs them to the end (0: the full
+ *                 persistent grid).  A few blocks leave the rest of the GPU to
+ *                 work queued on `stream` behind the first launch (e.g. the
+ *                 next batch's seed inference).
+ *   tail_stream   the second launch and the best-seed selection run here,
+ *                 ordered after the first launch by an event; the outputs are
+ *                 complete in tail_stream's order.  tail_stream == stream runs
+ *                 everything on one stream.
+ *   d_workspace   required (not NULL), pk_ik_split_workspace_bytes() bytes,
+ *                 256-byte aligned; it is in use until tail_stream passes the
+ *                 call, so a call that overlaps it needs another workspace.
+ * A resumed problem re-evaluates its cost, Jacobian and normal matrix at its
+ * saved configuration and continues with its saved damping, which is what the
+ * single launch holds at that point: without sibling cancellation the results
+ * equal pk_ik_solve's bit for bit.  Robots served by the one-problem-per-warp
+ * tree kernel run in one launch on `stream`, and tail_stream waits for it.
+ * Under CUDA graph capture, join tail_stream back into the capturing stream
+ * before the capture ends.
+ */
+pk_status pk_ik_solve_split(const pk_robot* robot, const pk_ik_params* params, int32_t k,
+                            const int32_t* target_links, const int32_t* target_kinds, int32_t batch,
+                            int32_t n_seeds, const float* d_targets, const float* d_seeds, float* d_q_out,
+                            float* d_err_out, int32_t* d_iters_out, int32_t* d_status_out, void* d_workspace,
+                            size_t workspace_bytes, int32_t split_iters, int32_t tail_ctas, void* stream,
+                            void* tail_stream);
+
+/*
  * IK-Beam (Sec. V-C) -- the paper's benchmark IK schedule: every target starts
  * from n_seeds seeds, all of which take steps1 LM iterations; the `keep` seeds
  * with the lowest cost (ties: lower seed index; a non-finite cost ranks last)
@@ -336,6 +379,10 @@ pk_status pk_ik_plan_stats(const pk_ik_plan* plan, int64_t* stats_out);
  *   [3] problems finished
  */
 pk_status pk_ik_workspace_stats(const void* d_workspace, int64_t* stats_out);
+/* The same for a pk_ik_solve_split workspace, stats_out [8]: [0..4) the first
+ * launch (problems finished there, suspended ones not counted), [4..8) the
+ * second launch (the resumed problems). */
+pk_status pk_ik_split_workspace_stats(const void* d_workspace, int64_t* stats_out);
 
 /*
  * Kernel timing trace.  While enabled, every solver kernel launch is bracketed

@@ -223,7 +223,7 @@ template <int N, int F = 0>
 __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams& lp,
                                              const float* __restrict__ targets, const float* __restrict__ seeds,
                                              int n_seeds, int P, int32_t* head, int32_t* flags, float* rec,
-                                             WorkCount& wc, ChainQueue<N>& qq) {
+                                             WorkCount& wc, ChainQueue<N>& qq, int batch_in = 0) {
   constexpr int NT = N * (N + 1) / 2;
   constexpr int NP = ((N + 3) & ~3);
   constexpr int STRIDE = NP + 4;
@@ -240,12 +240,12 @@ __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams
 
   // Problems come from the warp's double-buffered queue (claim order: see
   // claim_order); a seed whose target is already solved is skipped.
-  const int batch = P / n_seeds;
+  const int batch = batch_in > 0 ? batch_in : P / n_seeds;
   const bool cancel = lp.cancel != 0;
   int tgt = 0, pid = 0;  // target and record index of the lane's problem
   int qcur = 0, qpos = 0;
-  chain_chunk_claim<N>(qq, 0, head, P, batch, n_seeds, cancel, targets, seeds, flags, lp, lane);
-  chain_chunk_claim<N>(qq, 1, head, P, batch, n_seeds, cancel, targets, seeds, flags, lp, lane);
+  chain_chunk_claim<N>(qq, 0, head, P, batch, n_seeds, cancel, targets, seeds, flags, lp, lane, rec);
+  chain_chunk_claim<N>(qq, 1, head, P, batch, n_seeds, cancel, targets, seeds, flags, lp, lane, rec);
   cp_async_wait_one_pending();
   __syncwarp();
   for (;;) {
@@ -259,7 +259,7 @@ __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams
         __syncwarp();
         qcur ^= 1;
         qpos = 0;
-        chain_chunk_claim<N>(qq, qcur ^ 1, head, P, batch, n_seeds, cancel, targets, seeds, flags, lp, lane);
+        chain_chunk_claim<N>(qq, qcur ^ 1, head, P, batch, n_seeds, cancel, targets, seeds, flags, lp, lane, rec);
       }
       const int rank = __popc(nm & ((1u << lane) - 1u));
       const int avail = kQ - qpos;
@@ -293,7 +293,7 @@ __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams
 #pragma unroll
             for (int j = 0; j < N; ++j) qc[j] = qq.seed[qcur][e][j];
             fresh = true;
-            it = 0;
+            it = qq.it0[qcur][e] & 0xffffff;  // 0, or the iterations a resumed problem has done
             lam = qq.lam[qcur][e];
             need = false;
           }
@@ -339,6 +339,7 @@ __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams
       if (lp.early_exit && conv) { done = true; status = PK_P_CONVERGED; }
       else if (it >= lp.max_iters) { done = true; status = conv ? PK_P_CONVERGED : PK_P_MAX_ITERS; }
       else if (cancelled) { done = true; status = PK_P_CANCELLED; }
+      else if (lp.suspend_at > 0 && it >= lp.suspend_at) { done = true; status = kStatusSuspended; }
     }
     fresh = false;
 
@@ -366,9 +367,16 @@ __device__ __forceinline__ void chain_lm_run(const ChainC<N>& rc, const LmParams
       r[NP + 1] = pe_a;
       r[NP + 2] = re_a;
       r[NP + 3] = __int_as_float((status << 24) | it);
-      if (lp.lam_out) lp.lam_out[pid] = lam;
-      if (lp.cancel && status == PK_P_CONVERGED) __stcg(flags + tgt, 1);
-      ++wc.done;
+      if (status == kStatusSuspended) {
+        // the state a later launch continues from: q and the iteration count
+        // (record), the damping, and the problem's place in the resume list
+        lp.lam_sus[pid] = lam;
+        lp.resume_ids[atomicAdd(lp.resume_n, 1)] = pid;
+      } else {
+        if (lp.lam_out) lp.lam_out[pid] = lam;
+        if (lp.cancel && status == PK_P_CONVERGED) __stcg(flags + tgt, 1);
+        ++wc.done;
+      }
       need = true;
     }
   }
@@ -405,8 +413,15 @@ __global__ void __launch_bounds__(kLmThreads, PK_LM_MINB) chain_lm_kernel(
     IkWorkspace ws) {
   __shared__ ChainQueue<N> qq[kLmThreads / 32];
   WorkCount wc;
-  chain_lm_run<N, F>(rc, lp, targets, seeds, n_seeds, P, ws.head, ws.flags, ws.rec, wc, qq[threadIdx.x >> 5]);
-  flush_counts(wc, ws.stats);
+  if (lp.resume_in) {
+    // the continuation of a split solve: the suspended problems, from their own queue head
+    const int n = __ldcg(lp.resume_n);
+    chain_lm_run<N, F>(rc, lp, targets, seeds, n_seeds, n, ws.head2, ws.flags, ws.rec, wc, qq[threadIdx.x >> 5],
+                       P / n_seeds);
+  } else {
+    chain_lm_run<N, F>(rc, lp, targets, seeds, n_seeds, P, ws.head, ws.flags, ws.rec, wc, qq[threadIdx.x >> 5]);
+  }
+  flush_counts(wc, lp.resume_in ? ws.stats + 4 : ws.stats);  // a continuation counts apart
 }
 
 // Best seed per target: converged first, then lowest cost, then lowest index.
@@ -533,7 +548,7 @@ template <int N>
 static cudaError_t chain_lm_launch(const ChainHost& ch, const LmParams& lp, const float* d_targets,
                                    const float* d_seeds, int batch, int n_seeds, IkWorkspace ws,
                                    float* d_q, float* d_err, int32_t* d_iters, int32_t* d_status,
-                                   cudaStream_t stream) {
+                                   cudaStream_t stream, int max_grid = 0) {
   // the fast variant when the chain has only revolute joints, translation-only
   // origins and tool, and a pose target (the common arm)
   const bool fast = PK_CHAIN_FAST && ch.prism == 0 && ch.orot == 0 && !ch.toolrot && !lp.pos_only;
@@ -550,9 +565,10 @@ static cudaError_t chain_lm_launch(const ChainHost& ch, const LmParams& lp, cons
   long grid = (long)blocks_per_sm[fast] * sm_count();
   const long need = (P + kLmThreads - 1) / kLmThreads;
   if (grid > need) grid = need;
+  if (max_grid > 0 && grid > max_grid) grid = max_grid;
   const ChainC<N> rc = chain_const<N>(ch);
   {
-    TraceScope tr("ik_lm", stream);
+    TraceScope tr(lp.resume_in ? "ik_lm_tail" : "ik_lm", stream);
     if (fast)
       chain_lm_kernel<N, kChainFast><<<(unsigned)grid, kLmThreads, 0, stream>>>(rc, lp, d_targets, d_seeds,
                                                                                 n_seeds, (int)P, ws);
@@ -563,6 +579,41 @@ static cudaError_t chain_lm_launch(const ChainHost& ch, const LmParams& lp, cons
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !d_q) return e;
   return launch_ik_reduce(ws.rec, N, batch, n_seeds, d_q, d_err, d_iters, d_status, stream);
+}
+
+// Split solve: launch 1 (every problem, suspended after split_iters
+// iterations) on `stream`, launch 2 (the suspended problems, resumed from
+// their records) and the reduction on `tail`.  The problem count of launch 2
+// is only known on the device, so its grid is fixed: tail_ctas blocks, or the
+// full persistent grid.
+template <int N>
+static cudaError_t chain_lm_split_launch(const ChainHost& ch, const LmParams& lp, const float* d_targets,
+                                         const float* d_seeds, int batch, int n_seeds, IkWorkspace ws,
+                                         int split_iters, int tail_ctas, float* d_q, float* d_err,
+                                         int32_t* d_iters, int32_t* d_status, cudaStream_t stream,
+                                         cudaStream_t tail, cudaEvent_t ev) {
+  LmParams l1 = lp;
+  l1.suspend_at = split_iters;
+  l1.resume_n = ws.resume_n;
+  l1.resume_ids = ws.resume_ids;
+  l1.lam_sus = ws.lam_sus;
+  l1.lam_in = nullptr;
+  l1.lam_out = nullptr;
+  cudaError_t e = chain_lm_launch<N>(ch, l1, d_targets, d_seeds, batch, n_seeds, ws, nullptr, nullptr, nullptr,
+                                     nullptr, stream);
+  if (e != cudaSuccess) return e;
+  if (tail != stream) {
+    if ((e = cudaEventRecord(ev, stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(tail, ev, 0)) != cudaSuccess) return e;
+  }
+  LmParams l2 = l1;
+  l2.suspend_at = 0;
+  l2.resume_ids = nullptr;
+  l2.resume_in = ws.resume_ids;
+  e = chain_lm_launch<N>(ch, l2, d_targets, d_seeds, batch, n_seeds, ws, nullptr, nullptr, nullptr, nullptr, tail,
+                         tail_ctas);
+  if (e != cudaSuccess) return e;
+  return launch_ik_reduce(ws.rec, N, batch, n_seeds, d_q, d_err, d_iters, d_status, tail);
 }
 
 template <int N>
@@ -601,6 +652,14 @@ cudaError_t launch_chain_lm(const ChainHost& ch, const LmParams& lp, const float
                             cudaStream_t stream) {
   PK_CHAIN_DISPATCH(chain_lm_launch, ch, lp, d_targets, d_seeds, batch, n_seeds, ws, d_q, d_err,
                     d_iters, d_status, stream)
+}
+
+cudaError_t launch_chain_lm_split(const ChainHost& ch, const LmParams& lp, const float* d_targets,
+                                  const float* d_seeds, int batch, int n_seeds, IkWorkspace ws, int split_iters,
+                                  int tail_ctas, float* d_q, float* d_err, int32_t* d_iters, int32_t* d_status,
+                                  cudaStream_t stream, cudaStream_t tail, cudaEvent_t ev) {
+  PK_CHAIN_DISPATCH(chain_lm_split_launch, ch, lp, d_targets, d_seeds, batch, n_seeds, ws, split_iters, tail_ctas,
+                    d_q, d_err, d_iters, d_status, stream, tail, ev)
 }
 
 cudaError_t launch_chain_residual(const ChainHost& ch, const LmParams& lp, const float* d_targets,

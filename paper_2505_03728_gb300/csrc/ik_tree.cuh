@@ -544,6 +544,7 @@ struct ChainQueue {
   float lam[2][kQ];    // initial damping
   int32_t pid[2][kQ];  // record index, or -1 past the end
   int32_t tid[2][kQ];  // target index
+  int32_t it0[2][kQ];  // resumed problems: their record's status word (iterations done in the low 24 bits)
 };
 
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
@@ -565,15 +566,21 @@ template <int N>
 __device__ __forceinline__ void chain_chunk_claim(ChainQueue<N>& q, int buf, int32_t* head, int P, int batch,
                                                   int n_seeds, bool cancel, const float* __restrict__ targets,
                                                   const float* __restrict__ seeds, const int32_t* flags,
-                                                  const LmParams& lp, int lane) {
+                                                  const LmParams& lp, int lane, const float* rec = nullptr) {
   int base = 0;
   if (lane == 0) base = atomicAdd(head, kQ);
   base = __shfl_sync(kTreeFull, base, 0);
   const int p = base + lane;
   if (p < P) {
-    int tgt, sd;
-    claim_order(p, batch, n_seeds, cancel, &tgt, &sd);
-    const int pid = tgt * n_seeds + sd;
+    int tgt, pid;
+    if (lp.resume_in) {  // a suspended problem: its record holds the configuration and iteration count
+      pid = __ldcg(lp.resume_in + p);
+      tgt = pid / n_seeds;
+    } else {
+      int sd;
+      claim_order(p, batch, n_seeds, cancel, &tgt, &sd);
+      pid = tgt * n_seeds + sd;
+    }
     q.pid[buf][lane] = pid;
     q.tid[buf][lane] = tgt;
     const float* tp = targets + (size_t)tgt * 12;
@@ -585,17 +592,27 @@ __device__ __forceinline__ void chain_chunk_claim(ChainQueue<N>& q, int buf, int
 #pragma unroll
       for (int j = 0; j < 12; ++j) cp_async4(&q.tgt[buf][lane][j], tp + j);
     }
-    const float* sp = seeds + (size_t)pid * N;
+    if (lp.resume_in) {
+      constexpr int STRIDE = ((N + 3) & ~3) + 4;
+      const float* r = rec + (size_t)pid * STRIDE;
 #pragma unroll
-    for (int j = 0; j < N; ++j) cp_async4(&q.seed[buf][lane][j], sp + j);
+      for (int j = 0; j < N; ++j) cp_async4(&q.seed[buf][lane][j], r + j);
+      cp_async4(&q.it0[buf][lane], r + STRIDE - 1);
+      cp_async4(&q.lam[buf][lane], lp.lam_sus + pid);
+    } else {
+      const float* sp = seeds + (size_t)pid * N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) cp_async4(&q.seed[buf][lane][j], sp + j);
+      q.it0[buf][lane] = 0;
+      if (lp.lam_in)
+        cp_async4(&q.lam[buf][lane], lp.lam_in + pid);
+      else
+        q.lam[buf][lane] = lp.lambda0;
+    }
     if (cancel)
       cp_async4(&q.flag[buf][lane], flags + tgt);
     else
       q.flag[buf][lane] = 0;
-    if (lp.lam_in)
-      cp_async4(&q.lam[buf][lane], lp.lam_in + pid);
-    else
-      q.lam[buf][lane] = lp.lambda0;
   } else {
     q.pid[buf][lane] = -1;
   }

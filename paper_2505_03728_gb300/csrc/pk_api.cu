@@ -201,6 +201,26 @@ void ik_workspace_carve(void* base, int n_dof, long batch, long n_seeds, IkWorks
   (void)n_seeds;
 }
 
+// The split solve's workspace: the plain one, then the suspended problems'
+// indices and damping (one int and one float per problem); its second queue
+// head and suspended count sit in the zeroed head area.
+size_t ik_split_workspace_bytes(int n_dof, long batch, long n_seeds) {
+  const size_t P = (size_t)batch * n_seeds;
+  return ik_workspace_bytes(n_dof, batch, n_seeds) + 2 * (((P * 4) + 255) & ~(size_t)255);
+}
+
+void ik_split_workspace_carve(void* base, int n_dof, long batch, long n_seeds, IkWorkspace* ws,
+                              size_t* zero_bytes) {
+  ik_workspace_carve(base, n_dof, batch, n_seeds, ws, zero_bytes);
+  char* p = (char*)base;
+  const size_t P = (size_t)batch * n_seeds;
+  const size_t ids = ik_workspace_bytes(n_dof, batch, n_seeds);
+  ws->resume_n = (int32_t*)(p + 128);
+  ws->head2 = (int32_t*)(p + 192);
+  ws->resume_ids = (int32_t*)(p + ids);
+  ws->lam_sus = (float*)(p + ids + (((P * 4) + 255) & ~(size_t)255));
+}
+
 // ---------------------------------------------------------------------------
 // Kernel timing trace: a pool of event pairs, one per traced launch.
 
@@ -362,6 +382,15 @@ pk_status pk_ik_workspace_stats(const void* d_workspace, int64_t* stats_out) {
   cudaError_t e = cudaMemcpy(h, d_workspace, sizeof h, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "pk_ik_workspace_stats");
   for (int i = 0; i < 4; ++i) stats_out[i] = (int64_t)h[i];
+  return PK_OK;
+}
+
+pk_status pk_ik_split_workspace_stats(const void* d_workspace, int64_t* stats_out) {
+  if (!d_workspace || !stats_out) return fail(PK_ERR_INVALID_ARG, "NULL argument");
+  unsigned long long h[8];
+  cudaError_t e = cudaMemcpy(h, d_workspace, sizeof h, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "pk_ik_split_workspace_stats");
+  for (int i = 0; i < 8; ++i) stats_out[i] = (int64_t)h[i];
   return PK_OK;
 }
 
@@ -610,34 +639,48 @@ size_t pk_ik_workspace_bytes(const pk_robot* rb, int32_t batch, int32_t n_seeds)
   return pk::ik_workspace_bytes(rb->n_dof, batch, n_seeds);
 }
 
+// Argument checks shared by the IK entry points; picks the chain or tree
+// kernel.  *empty: batch == 0 (nothing to launch).
+static pk_status ik_prepare(const pk_robot* rb, const pk_ik_params* params, int32_t k,
+                            const int32_t* target_links, const int32_t* target_kinds, int32_t batch,
+                            int32_t n_seeds, const float* d_targets, const float* d_seeds, float* d_q_out,
+                            float* d_err_out, int32_t* d_iters_out, int32_t* d_status_out, bool* chain,
+                            pk::ChainHost* ch, pk::TreeInfo* ti, bool* pos_only, bool* empty) {
+  if (!rb) return fail(PK_ERR_INVALID_ARG, "robot is NULL");
+  pk_status s = check_params(params);
+  if (s != PK_OK) return s;
+  if ((s = check_targets(rb, k, target_links, target_kinds, pos_only)) != PK_OK) return s;
+  if (batch < 0) return fail(PK_ERR_INVALID_ARG, "batch must be >= 0");
+  if (n_seeds < 1) return fail(PK_ERR_INVALID_ARG, "n_seeds must be >= 1");
+  if ((long long)batch * n_seeds > 0x7fffff00LL)
+    return fail(PK_ERR_INVALID_ARG, "batch * n_seeds exceeds 2^31");
+  *chain = chain_eligible(rb, k, target_links) && !self_collision(rb, params);
+  if (*chain) {
+    if ((s = fold_chain(rb, target_links[0], ch)) != PK_OK) return s;
+  } else if (!pk::build_tree_info(rb, k, target_links, target_kinds, ti)) {
+    return fail(PK_ERR_UNSUPPORTED, "IK supports up to %d movable joints, %d targets and %d joints",
+                pk::kTreeMaxDof, pk::kTreeMaxTargets, pk::kMaxJoints);
+  }
+  *empty = batch == 0;
+  if (*empty) return PK_OK;
+  if (!d_targets || !d_seeds || !d_q_out || !d_err_out || !d_iters_out || !d_status_out)
+    return fail(PK_ERR_INVALID_ARG, "NULL device buffer");
+  if (((uintptr_t)d_targets & 15) != 0) return fail(PK_ERR_INVALID_ARG, "d_targets must be 16-byte aligned");
+  return PK_OK;
+}
+
 pk_status pk_ik_solve(const pk_robot* rb, const pk_ik_params* params, int32_t k,
                       const int32_t* target_links, const int32_t* target_kinds, int32_t batch,
                       int32_t n_seeds, const float* d_targets, const float* d_seeds,
                       float* d_q_out, float* d_err_out, int32_t* d_iters_out,
                       int32_t* d_status_out, void* d_workspace, size_t workspace_bytes,
                       void* stream) {
-  if (!rb) return fail(PK_ERR_INVALID_ARG, "robot is NULL");
-  pk_status s = check_params(params);
-  if (s != PK_OK) return s;
-  bool pos_only = false;
-  if ((s = check_targets(rb, k, target_links, target_kinds, &pos_only)) != PK_OK) return s;
-  if (batch < 0) return fail(PK_ERR_INVALID_ARG, "batch must be >= 0");
-  if (n_seeds < 1) return fail(PK_ERR_INVALID_ARG, "n_seeds must be >= 1");
-  if ((long long)batch * n_seeds > 0x7fffff00LL)
-    return fail(PK_ERR_INVALID_ARG, "batch * n_seeds exceeds 2^31");
-  const bool chain = chain_eligible(rb, k, target_links) && !self_collision(rb, params);
+  bool chain = false, pos_only = false, empty = false;
   pk::ChainHost ch;
   pk::TreeInfo ti;
-  if (chain) {
-    if ((s = fold_chain(rb, target_links[0], &ch)) != PK_OK) return s;
-  } else if (!pk::build_tree_info(rb, k, target_links, target_kinds, &ti)) {
-    return fail(PK_ERR_UNSUPPORTED, "IK supports up to %d movable joints, %d targets and %d joints",
-                pk::kTreeMaxDof, pk::kTreeMaxTargets, pk::kMaxJoints);
-  }
-  if (batch == 0) return PK_OK;
-  if (!d_targets || !d_seeds || !d_q_out || !d_err_out || !d_iters_out || !d_status_out)
-    return fail(PK_ERR_INVALID_ARG, "NULL device buffer");
-  if (((uintptr_t)d_targets & 15) != 0) return fail(PK_ERR_INVALID_ARG, "d_targets must be 16-byte aligned");
+  pk_status s = ik_prepare(rb, params, k, target_links, target_kinds, batch, n_seeds, d_targets, d_seeds, d_q_out,
+                           d_err_out, d_iters_out, d_status_out, &chain, &ch, &ti, &pos_only, &empty);
+  if (s != PK_OK || empty) return s;
   const size_t need = pk::ik_workspace_bytes(rb->n_dof, batch, n_seeds);
   cudaStream_t st = (cudaStream_t)stream;
   void* ws_base = d_workspace;
@@ -671,6 +714,71 @@ pk_status pk_ik_solve(const pk_robot* rb, const pk_ik_params* params, int32_t k,
     if (e == cudaSuccess) e = e2;
   }
   return e == cudaSuccess ? PK_OK : cuda_fail(e, "pk_ik_solve launch");
+}
+
+size_t pk_ik_split_workspace_bytes(const pk_robot* rb, int32_t batch, int32_t n_seeds) {
+  if (!rb || batch < 0 || n_seeds < 1) return 0;
+  return pk::ik_split_workspace_bytes(rb->n_dof, batch, n_seeds);
+}
+
+// One event per device and host thread orders the tail stream behind the
+// first launch (recorded and waited on in the same call, so reuse is safe).
+static cudaError_t split_event(cudaEvent_t* ev) {
+  thread_local cudaEvent_t evs[pk::kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= pk::kMaxDevices) return cudaErrorInvalidDevice;
+  if (!evs[dev] && (e = cudaEventCreateWithFlags(&evs[dev], cudaEventDisableTiming)) != cudaSuccess) return e;
+  *ev = evs[dev];
+  return cudaSuccess;
+}
+
+pk_status pk_ik_solve_split(const pk_robot* rb, const pk_ik_params* params, int32_t k,
+                            const int32_t* target_links, const int32_t* target_kinds, int32_t batch,
+                            int32_t n_seeds, const float* d_targets, const float* d_seeds, float* d_q_out,
+                            float* d_err_out, int32_t* d_iters_out, int32_t* d_status_out, void* d_workspace,
+                            size_t workspace_bytes, int32_t split_iters, int32_t tail_ctas, void* stream,
+                            void* tail_stream) {
+  bool chain = false, pos_only = false, empty = false;
+  pk::ChainHost ch;
+  pk::TreeInfo ti;
+  pk_status s = ik_prepare(rb, params, k, target_links, target_kinds, batch, n_seeds, d_targets, d_seeds, d_q_out,
+                           d_err_out, d_iters_out, d_status_out, &chain, &ch, &ti, &pos_only, &empty);
+  if (s != PK_OK) return s;
+  if (split_iters < 1) return fail(PK_ERR_INVALID_ARG, "split_iters must be >= 1");
+  if (tail_ctas < 0) return fail(PK_ERR_INVALID_ARG, "tail_ctas must be >= 0");
+  if (empty) return PK_OK;
+  if (!d_workspace) return fail(PK_ERR_INVALID_ARG, "pk_ik_solve_split needs a caller workspace");
+  const size_t need = pk::ik_split_workspace_bytes(rb->n_dof, batch, n_seeds);
+  if (workspace_bytes < need)
+    return fail(PK_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
+  if (((uintptr_t)d_workspace & 255) != 0) return fail(PK_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream, tail = (cudaStream_t)tail_stream;
+  cudaEvent_t ev = nullptr;
+  cudaError_t e = split_event(&ev);
+  if (e != cudaSuccess) return cuda_fail(e, "pk_ik_solve_split event");
+  pk::IkWorkspace ws;
+  size_t zero_bytes = 0;
+  pk::ik_split_workspace_carve(d_workspace, rb->n_dof, batch, n_seeds, &ws, &zero_bytes);
+  e = cudaMemsetAsync(d_workspace, 0, zero_bytes, st);
+  if (e == cudaSuccess) {
+    if (chain) {
+      e = pk::launch_chain_lm_split(ch, lm_params(params, pos_only), d_targets, d_seeds, batch, n_seeds, ws,
+                                    split_iters, tail_ctas, d_q_out, d_err_out, d_iters_out, d_status_out, st, tail,
+                                    ev);
+    } else {  // trees: one launch on `stream`, the tail stream waits for it
+      pk::LmParams lp = lm_params(params, false);
+      lp.tol_rot = params->tol_rot;
+      e = pk::launch_tree_lm(rb, ti, lp, d_targets, d_seeds, batch, n_seeds, ws, d_q_out, d_err_out, d_iters_out,
+                             d_status_out, st);
+      if (e == cudaSuccess && tail != st) {
+        e = cudaEventRecord(ev, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(tail, ev, 0);
+      }
+    }
+  }
+  return e == cudaSuccess ? PK_OK : cuda_fail(e, "pk_ik_solve_split launch");
 }
 
 void pk_ik_beam_params_default(pk_ik_beam_params* b) {

@@ -74,19 +74,44 @@ struct LmParams {
   // records; used to continue an LM run in a later launch (IK-Beam).
   const float* lam_in = nullptr;
   float* lam_out = nullptr;
+  // Chain path only, two-launch solve.  suspend_at > 0: a problem still
+  // running after that many iterations (not converged, not cancelled) writes
+  // its record with status kStatusSuspended and its iteration count, its
+  // damping to lam_sus[pid], and appends pid to resume_ids (*resume_n counts).
+  // resume_in != NULL: the launch takes its problems from resume_in[0 ..
+  // *resume_n) and continues each one from its record and lam_sus.
+  int32_t suspend_at = 0;
+  int32_t* resume_n = nullptr;
+  int32_t* resume_ids = nullptr;
+  const int32_t* resume_in = nullptr;
+  float* lam_sus = nullptr;
 };
+
+// Record status of a problem suspended between the two launches of a split
+// solve (never returned: the second launch rewrites every such record).
+constexpr int kStatusSuspended = 15;
 
 // Scratch layout of the IK solve.
 struct IkWorkspace {
-  unsigned long long* stats;  // [4] work counters (zeroed per call)
+  unsigned long long* stats;  // [4] work counters, [4..8) the split solve's second launch (zeroed per call)
   int32_t* head;   // work-queue head (1 int, zeroed per call)
   int32_t* flags;  // [batch] converged-sibling flags (zeroed per call)
   float* rec;      // [batch * n_seeds][rec_stride] per-seed results
+  // split solve only (ik_split_workspace_bytes): second queue head and the
+  // suspended-problem count (zeroed per call), suspended problem indices and
+  // their damping
+  int32_t* head2 = nullptr;
+  int32_t* resume_n = nullptr;
+  int32_t* resume_ids = nullptr;
+  float* lam_sus = nullptr;
 };
 
 size_t ik_workspace_bytes(int n_dof, long batch, long n_seeds);
 void ik_workspace_carve(void* base, int n_dof, long batch, long n_seeds, IkWorkspace* ws,
                         size_t* zero_bytes);
+size_t ik_split_workspace_bytes(int n_dof, long batch, long n_seeds);
+void ik_split_workspace_carve(void* base, int n_dof, long batch, long n_seeds, IkWorkspace* ws,
+                              size_t* zero_bytes);
 int ik_rec_stride(int n_dof);
 
 // Launchers (ik_chain.cu).  Return a cudaError_t from the launch.
@@ -97,6 +122,14 @@ cudaError_t launch_chain_lm(const ChainHost& ch, const LmParams& lp, const float
                             cudaStream_t stream);
 cudaError_t launch_ik_reduce(const float* rec, int n_dof, int batch, int n_seeds, float* d_q, float* d_err,
                              int32_t* d_iters, int32_t* d_status, cudaStream_t stream);
+// Two-launch chain solve: every problem runs up to split_iters iterations on
+// `stream`; the ones still running are finished on `tail` (tail_ctas blocks,
+// 0: a full grid) after `ev`, recorded on `stream` behind the first launch,
+// then the best-seed reduction runs on `tail`.
+cudaError_t launch_chain_lm_split(const ChainHost& ch, const LmParams& lp, const float* d_targets,
+                                  const float* d_seeds, int batch, int n_seeds, IkWorkspace ws, int split_iters,
+                                  int tail_ctas, float* d_q, float* d_err, int32_t* d_iters, int32_t* d_status,
+                                  cudaStream_t stream, cudaStream_t tail, cudaEvent_t ev);
 struct TreeInfo;
 bool build_tree_info(const pk_robot* rb, int k, const int32_t* links, const int32_t* kinds, TreeInfo* ti);
 cudaError_t launch_tree_lm(const pk_robot* rb, const TreeInfo& ti, const LmParams& lp, const float* d_targets,

@@ -889,7 +889,10 @@ cudaError_t infer_fused(pk_seednet* s, int batch, const float* d_targets, float*
   p.lohi = s->d_lohi;
   p.targets = d_targets;
   p.seeds = d_seeds_out;
-  int grid = p.tiles < sms ? p.tiles : sms;
+  // the fewest CTAs that keep the number of tile rounds (the busiest CTA sets
+  // the launch time), so that the other SMs stay free for concurrent work
+  const int rounds = (p.tiles + sms - 1) / sms;
+  int grid = (p.tiles + rounds - 1) / rounds;
   if (const char* env = getenv("PK_MLP_GRID"))  // persistent grid size, for tuning sweeps
     if (atoi(env) > 0 && atoi(env) < grid) grid = atoi(env);
   const int smem = MlpSmem::bytes(p.stages, p.area_bytes);

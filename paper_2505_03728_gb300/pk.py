@@ -99,9 +99,13 @@ _SIGNATURES = {
                                 _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "pk_ik_solve": (_i32, [_vp, C.POINTER(pk_ik_params), _i32, _i32p, _i32p, _i32, _i32, _vp, _vp,
                            _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "pk_ik_split_workspace_bytes": (C.c_size_t, [_vp, _i32, _i32]),
+    "pk_ik_solve_split": (_i32, [_vp, C.POINTER(pk_ik_params), _i32, _i32p, _i32p, _i32, _i32, _vp, _vp,
+                                 _vp, _vp, _vp, _vp, _vp, C.c_size_t, _i32, _i32, _vp, _vp]),
     "pk_ik_solve_noalloc": (_i32, [_vp, C.POINTER(pk_ik_params), _i32, _i32p, _i32p, _i32, _i32, _vp,
                                    _vp, _vp, _vp, _vp, _vp, _vp]),
     "pk_ik_workspace_stats": (_i32, [_vp, C.POINTER(C.c_int64)]),
+    "pk_ik_split_workspace_stats": (_i32, [_vp, C.POINTER(C.c_int64)]),
     "pk_train_params_default": (None, [_vp]),
     "pk_ik_plan_create": (_i32, [C.POINTER(pk_ik_params), _i32, _vp, C.POINTER(_vp)]),
     "pk_ik_plan_destroy": (None, [_vp]),
@@ -316,6 +320,39 @@ def pk_ik_solve(robot: Robot, params: pk_ik_params, links, kinds, targets: torch
     return q, err, iters, status
 
 
+def pk_ik_split_workspace_bytes(robot: Robot, batch: int, n_seeds: int) -> int:
+    return int(lib().pk_ik_split_workspace_bytes(robot.handle, batch, n_seeds))
+
+
+def pk_ik_solve_split(robot: Robot, params: pk_ik_params, links, kinds, targets: torch.Tensor,
+                      seeds: torch.Tensor, workspace: torch.Tensor, split_iters: int, tail_ctas: int = 0,
+                      out=None, stream=None, tail_stream=None):
+    """pk_ik_solve in two launches: every problem up to ``split_iters``
+    iterations on ``stream``, the problems still running then resumed on
+    ``tail_stream`` (``tail_ctas`` blocks, 0: full grid), where the outputs
+    are complete.  ``workspace``: pk_ik_split_workspace_bytes() bytes."""
+    links, kinds_a, kinds_p = _links(links, kinds)
+    B, S = seeds.shape[0], seeds.shape[1]
+    if seeds.shape != (B, S, robot.n_dof):
+        raise ValueError("seeds must be [batch][n_seeds][n_dof]")
+    if targets.shape != (B, len(links), 12):
+        raise ValueError("targets must be [batch][k][12]")
+    dev = seeds.device
+    if out is None:
+        out = (torch.empty(B, robot.n_dof, device=dev), torch.empty(B, 2, device=dev),
+               torch.empty(B, device=dev, dtype=torch.int32), torch.empty(B, device=dev, dtype=torch.int32))
+    q, err, iters, status = out
+    st = _stream(stream)
+    tst = st if tail_stream is None else _stream(tail_stream)
+    _check(lib().pk_ik_solve_split(robot.handle, C.byref(params), len(links), links.ctypes.data_as(_i32p),
+                                   kinds_p, B, S, _dev(targets, name="targets"), _dev(seeds, name="seeds"),
+                                   _dev(q, name="q"), _dev(err, name="err"),
+                                   _dev(iters, torch.int32, "iters"), _dev(status, torch.int32, "status"),
+                                   _dev(workspace, torch.uint8, "workspace"), workspace.numel(), split_iters,
+                                   tail_ctas, st, tst))
+    return q, err, iters, status
+
+
 def pk_ik_beam_params_default(**overrides) -> pk_ik_beam_params:
     b = pk_ik_beam_params()
     lib().pk_ik_beam_params_default(C.byref(b))
@@ -364,6 +401,14 @@ def pk_ik_workspace_stats(workspace: torch.Tensor) -> dict:
     out = (C.c_int64 * 4)()
     _check(lib().pk_ik_workspace_stats(_dev(workspace, torch.uint8, "workspace"), out))
     return dict(evals=out[0], builds=out[1], solves=out[2], problems=out[3])
+
+
+def pk_ik_split_workspace_stats(workspace: torch.Tensor) -> tuple:
+    """Work counters of the two launches of the last pk_ik_solve_split that
+    used ``workspace`` (synchronises): (first launch, second launch)."""
+    out = (C.c_int64 * 8)()
+    _check(lib().pk_ik_split_workspace_stats(_dev(workspace, torch.uint8, "workspace"), out))
+    return tuple(dict(evals=out[i], builds=out[i + 1], solves=out[i + 2], problems=out[i + 3]) for i in (0, 4))
 
 
 def pk_trace_enable(enable: bool = True):
