@@ -49,12 +49,12 @@ FLOPS_PER_BUILD = 1320.5
 FLOPS_PER_SOLVE = 193.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
 # DRAM bytes (read + write) per target of the LM kernel: ncu capture of the
-# 16,384-target learned-seed launch (4.586 MB), inputs read once (see profiles/).
-LM_DRAM_BYTES_PER_TARGET = 4584192 / 16384
+# 16,384-target learned-seed launch (4.626 MB), inputs read once (see profiles/).
+LM_DRAM_BYTES_PER_TARGET = 4625664 / 16384
 MLP_DRAM_BYTES_65536 = 4962048.0  # mlp_fused_kernel, dram__bytes_read.sum + write.sum per launch
 # FP32 operations per trajectory-iteration of the trajectory kernel (ncu count
 # over 64 trajectories x 50 iterations, see profiles/).
-TRAJ_FLOPS_PER_ITER = 1.553e6
+TRAJ_FLOPS_PER_ITER = 1.376e6
 # Every timed step reads its own input batch; an arm rotates through enough
 # batches to hold at least this many bytes (twice the 129 MB L2).
 ROTATE_BYTES = 256 << 20
@@ -710,7 +710,7 @@ def main():
     eo = tuple(torch.empty_like(o) for o in outs)
     h_o = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs[:3]]
     K_e = max(args.steps, 2)
-    h_status = torch.empty((K_e, B), dtype=torch.int32, pin_memory=True)
+    h_status = torch.empty((max(K_e, args.warmup, 2), B), dtype=torch.int32, pin_memory=True)
 
     def e2e_run(K):
         copied = [torch.cuda.Event() for _ in range(K)]
@@ -746,7 +746,7 @@ def main():
     t0 = time.perf_counter()
     e2e_run(K_e)
     e2e_ms = (time.perf_counter() - t0) * 1e3
-    e2e_conv = int((h_status == pk.PK_P_CONVERGED).sum())
+    e2e_conv = int((h_status[:K_e] == pk.PK_P_CONVERGED).sum())
     e2e_ms, e2e_conv = reduce_over_ranks(torch, world, e2e_ms, e2e_conv)
     h2d = h_t[0].numel() * 4 + (0 if head == "learned" else h_s[0].numel() * 4)
     d2h = sum(o.numel() * o.element_size() for o in outs)
