@@ -11,9 +11,9 @@
 //   TMEM columns [0, 256)    the FP32 accumulator of one output chunk (256
 //                            features, or the head);
 //   shared memory            a ring of 64 KB weight stages (one 3-D TMA box:
-//                            [K-blocks][256 outputs][64 K], 128B-swizzled),
-//                            the first chunk's BF16 results while the second
-//                            is computed, and the head's output staging.
+//                            [K-blocks][256 outputs][64 K], 128B-swizzled)
+//                            and the first chunk's BF16 results while the
+//                            second is computed.
 //
 // Measured on sm_103a (M = 128, K = 16, BF16): an MMA instruction costs a
 // fixed ~116 cycles up to N = 128; at N = 256 it takes ~138 cycles with A in
@@ -23,14 +23,18 @@
 //
 // Warp 0 / lane 0 streams the weights of every (tile, layer, chunk, stage) in
 // MMA order; warp 1 / lane 0 issues tcgen05.mma; sixteen epilogue warps (four
-// per TMEM lane quarter, 64 columns each) drain the accumulator into registers
-// (after which the MMA may overwrite it), add the bias and apply SiLU.  A
-// layer's outputs can only replace ACT once every MMA of the layer has read
-// it, so the first chunk's results wait in shared memory; when the second
-// chunk is drained they are stored to ACT and published per 128 inputs, and
-// the next layer's MMAs start on them while the second chunk is finished.
-// The head writes q = mid + half tanh(y) through a staging tile; the next
-// tile's features go into ACT right after the head's last MMA.
+// per TMEM lane quarter) drain the accumulator into registers (after which
+// the MMA may overwrite it), add the bias and apply SiLU.  Each warp owns 16
+// columns of every 64-column quarter of a chunk, so all sixteen warps finish
+// each 128 ACT inputs together (the MUFU tanh throughput bounds this work).
+// A layer's outputs can only replace ACT once every MMA of the layer has
+// read it, so the first chunk's results wait in shared memory; when the
+// second chunk is drained they are stored to ACT and published per 128
+// inputs, and the next layer's MMAs start on them while the second chunk is
+// finished, again 128 inputs at a time.  The head releases the accumulator
+// as soon as it is in registers and stores q = mid + half tanh(y) straight to
+// global memory; the next tile's features go into ACT right after the head's
+// last MMA.
 //
 // Arithmetic per element is the layer-by-layer path's (same MMA K order,
 // same SiLU and head formulas).  Every mbarrier wait is bounded as in
@@ -68,7 +72,7 @@ struct MlpParams {
   int tiles;       // ceil(batch / 128)
   int stages;      // weight ring depth (slots of kMlpStageBytes)
   int area_bytes;  // keep / staging area after the ring
-  int staged;      // head outputs through the staging tile (in the keep area)
+  int vec4;        // head outputs as float4 stores (out_dim % 4 == 0, 16-byte aligned output)
   int stage_kb[kMlpMaxLayers];  // K-blocks of 64 per weight stage of layer l
   const float* bias[kMlpMaxLayers];
   const float* lohi;     // joint limits [2][n_dof]
@@ -77,7 +81,6 @@ struct MlpParams {
 };
 
 struct MlpSmem {
-  static constexpr int staging_bytes(int out_dim) { return kBM * out_dim * 4; }
   static constexpr int bar_offset(int stages, int area) { return stages * kMlpStageBytes + ((area + 1023) & ~1023); }
   static constexpr int bytes(int stages, int area) { return bar_offset(stages, area) + 256 + 1024; }
 };
@@ -126,6 +129,46 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint4& a, const 
       : "memory");
 }
 
+// 16 consecutive 32-bit columns of this thread's TMEM lane into r[O .. O + 15]
+// (completed by tmem_ld_wait on r).
+template <int O>
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[O + 0]), "=r"(r[O + 1]), "=r"(r[O + 2]), "=r"(r[O + 3]), "=r"(r[O + 4]), "=r"(r[O + 5]),
+        "=r"(r[O + 6]), "=r"(r[O + 7]), "=r"(r[O + 8]), "=r"(r[O + 9]), "=r"(r[O + 10]), "=r"(r[O + 11]),
+        "=r"(r[O + 12]), "=r"(r[O + 13]), "=r"(r[O + 14]), "=r"(r[O + 15])
+      : "r"(taddr));
+}
+
+// 8 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint4& a, const uint4& b) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+               : "memory");
+}
+
+// BF16 SiLU of the 16 accumulator columns r[O .. O + 15] (bias of their
+// first feature at `bias`); per element the arithmetic of silu_pack32.
+template <int O>
+__device__ __forceinline__ void silu_pack16(const float* bias, const uint32_t (&r)[32], uint32_t (&packed)[8]) {
+  const uint64_t half2 = f32x2(0.5f, 0.5f);
+  const float2* b2 = reinterpret_cast<const float2*>(bias);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float2 b = __ldg(b2 + i);
+    const uint64_t hb = fma_f32x2(f32x2(b.x, b.y), half2, f32x2(0.f, 0.f));
+    const uint64_t h2 =
+        fma_f32x2(f32x2(__uint_as_float(r[O + 2 * i]), __uint_as_float(r[O + 2 * i + 1])), half2, hb);
+    const float2 h = f32x2_split(h2);
+    const uint64_t s2 = fma_f32x2(h2, f32x2(tanh_fast(h.x), tanh_fast(h.y)), h2);
+    const float2 sv = f32x2_split(s2);
+    __nv_bfloat162 o = __floats2bfloat162_rn(sv.x, sv.y);
+    packed[i] = *reinterpret_cast<uint32_t*>(&o);
+  }
+}
+
 // BF16 SiLU of 32 accumulator columns; the arithmetic of epilogue_silu32.
 __device__ __forceinline__ void silu_pack32(const float* bias, const uint32_t (&r)[32], uint32_t (&packed)[16]) {
   const uint64_t half2 = f32x2(0.5f, 0.5f);
@@ -151,6 +194,25 @@ __device__ __forceinline__ void act_features(uint32_t act_lane, const MlpParams&
   const bool ok = row < p.batch;
   const float* T = p.targets + (size_t)(ok ? row : 0) * p.k * 12;
   const int in_dim = 9 * p.k;
+  if (p.k == 1 && p.in_pad == 64 && ((uintptr_t)p.targets & 15) == 0) {
+    // one pose per row: three 16-byte loads instead of nine scattered ones
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a;
+    if (ok) {
+      const float4* T4 = reinterpret_cast<const float4*>(T);
+      a = __ldg(T4);
+      b = __ldg(T4 + 1);
+      c = __ldg(T4 + 2);
+    }
+    const float f[10] = {a.w, b.w, c.w, a.x, b.x, c.x, a.y, b.y, c.y, 0.f};
+    uint32_t packed[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      __nv_bfloat162 hv = __floats2bfloat162_rn(i < 5 ? f[2 * i] : 0.f, i < 5 ? f[2 * i + 1] : 0.f);
+      packed[i] = *reinterpret_cast<uint32_t*>(&hv);
+    }
+    tmem_st32(act_lane, packed);
+    return;
+  }
   // feature j of a target reads its 3 x 4 row-major pose at 3, 7, 11 (position),
   // 0, 4, 8 (rotation column 0), 1, 5, 9 (rotation column 1)
   auto off = [](int j) { return j < 3 ? 3 + 4 * j : j < 6 ? 4 * (j - 3) : 1 + 4 * (j - 6); };
@@ -184,8 +246,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
   uint64_t* tfull = empty + S;   // accumulator ready (MMA -> epilogue)
   uint64_t* tfree = tfull + 1;   // accumulator drained (epilogue -> MMA)
   uint64_t* actb = tfree + 1;    // [4] ACT inputs 128 b .. 128 b + 127 written (epilogue -> MMA)
-  uint64_t* stg = actb + 4;      // [2] head staging written / read out (epilogue warps)
-  uint64_t* drain = stg + 2;
+  uint64_t* drain = actb + 4;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -199,8 +260,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     }
     mbar_init(tfull, 1);
     mbar_init(tfree, kMlpEpiWarps);
-    for (int b = 0; b < 4; ++b) mbar_init(&actb[b], kMlpEpiWarps / 2);  // the eight warps that write it
-    for (int c = 0; c < 2; ++c) mbar_init(&stg[c], kMlpEpiWarps);
+    for (int b = 0; b < 4; ++b) mbar_init(&actb[b], kMlpEpiWarps);  // every epilogue warp writes a part
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -290,12 +350,13 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     __syncwarp();
   } else {
     // ---- epilogue warps: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile
-    //      rows) and columns 64 h .. 64 h + 63 of a chunk, h = (w - 2) / 4
+    //      rows) and, of every 64-column quarter m of a chunk, the columns
+    //      64 m + 16 h .. 64 m + 16 h + 15, h = (w - 2) / 4
     const int q = warp & 3, h = (warp - 2) >> 2;
     const int r = q * 32 + lane, te = threadIdx.x - 64;  // te: 0 .. 511 over the epilogue warps
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     const uint32_t act_lane = lane_base + kMlpActCol;
-    uint32_t tf = 0, sg0 = 0, sg1 = 0;
+    uint32_t tf = 0;
     bool ok = true;
     // this thread's 32 words of a kept chunk (its row, its 64 features), in
     // 16-byte pieces rotated by the row so that a warp's accesses spread over
@@ -321,34 +382,33 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
       tc_fence_before();
       signal(bar);
     };
-    auto epi_sync = [&](int i) -> bool {  // bounded rendezvous of the epilogue warps
-      uint32_t& n = i ? sg1 : sg0;
-      signal(&stg[i]);
-      uint32_t ready = 0;
-      if (lane == 0) ready = mbar_wait(&stg[i], n & 1, err, 16) ? 1u : 0u;
-      ++n;
-      return __shfl_sync(0xffffffffu, ready, 0) != 0;
-    };
-    // this warp's 64 accumulator columns into registers (one wait for both
-    // loads), then release the accumulator to the MMA
+    // this warp's 64 accumulator columns into registers (quarters 0, 1 in v0,
+    // 2, 3 in v1; one wait for all four loads), then release the accumulator
     auto drain = [&](uint32_t (&v0)[32], uint32_t (&v1)[32]) {
-      tmem_ld32_issue(lane_base + (uint32_t)(h * 64), v0);
-      tmem_ld32_issue(lane_base + (uint32_t)(h * 64 + 32), v1);
+      tmem_ld16_issue<0>(lane_base + (uint32_t)(16 * h), v0);
+      tmem_ld16_issue<16>(lane_base + (uint32_t)(64 + 16 * h), v0);
+      tmem_ld16_issue<0>(lane_base + (uint32_t)(128 + 16 * h), v1);
+      tmem_ld16_issue<16>(lane_base + (uint32_t)(192 + 16 * h), v1);
       tmem_ld_wait(v0);
       tmem_ld_wait(v1);
       tc_fence_before();
       signal(tfree);
     };
-    // SiLU of 32 accumulator columns (features f ..) into ACT columns f / 2 ..
-    auto silu_to_act = [&](const float* bias, int f, const uint32_t (&v)[32]) {
-      uint32_t pk[16];
-      silu_pack32(bias + f, v, pk);
-      tmem_st16(act_lane + (uint32_t)(f >> 1), make_uint4(pk[0], pk[1], pk[2], pk[3]),
-                make_uint4(pk[4], pk[5], pk[6], pk[7]), make_uint4(pk[8], pk[9], pk[10], pk[11]),
-                make_uint4(pk[12], pk[13], pk[14], pk[15]));
+    // SiLU of this warp's 16 columns of quarter m of a chunk whose first
+    // feature is f0: 8 packed BF16 pairs (ACT columns f0 / 2 + 32 m + 8 h ..)
+    auto silu_q = [&](const float* bias, int f0, int m, const uint32_t (&v0)[32], const uint32_t (&v1)[32],
+                      uint32_t (&pk)[8]) {
+      const float* b = bias + f0 + 64 * m + 16 * h;
+      if (m == 0)
+        silu_pack16<0>(b, v0, pk);
+      else if (m == 1)
+        silu_pack16<16>(b, v0, pk);
+      else if (m == 2)
+        silu_pack16<0>(b, v1, pk);
+      else
+        silu_pack16<16>(b, v1, pk);
     };
-    auto features = [&](int t) {  // written by the h = 0 warps, published with the h = 1 warps
-      if (h >= 2) return;
+    auto features = [&](int t) {  // written by the h = 0 warps, published by all
       if (h == 0) act_features(act_lane, p, t, r);
       for (int b = 0; b < (p.in_pad + 127) / 128; ++b) publish(&actb[b]);
     };
@@ -367,34 +427,43 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
       for (int l = 0; l + 1 < L && ok; ++l) {
         const float* bias = p.bias[l];
         uint32_t v0[32], v1[32];
-        const int f0 = h * 64;  // this warp's features of chunk 0; piece 2 c + h / 2 of ACT
         if (!(ok = wait_acc())) break;
         drain(v0, v1);
         if (hidden_chunks == 2) {
           // chunk 0 waits in shared memory until the layer's last MMA has read ACT
-          {
-            uint32_t pk[16];
-            silu_pack32(bias + f0, v0, pk);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) *keep_at(j) = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
-            silu_pack32(bias + f0 + 32, v1, pk);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) *keep_at(4 + j) = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+          for (int m = 0; m < 4; ++m) {
+            uint32_t pk[8];
+            silu_q(bias, 0, m, v0, v1, pk);
+            *keep_at(2 * m) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *keep_at(2 * m + 1) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
           }
           if (!(ok = wait_acc())) break;
           drain(v0, v1);
-          // every MMA of the layer is done: chunk 0 into ACT (published at once,
-          // the next layer starts on it), then chunk 1
-          tmem_st16(act_lane + (uint32_t)(f0 >> 1), *keep_at(0), *keep_at(1), *keep_at(2), *keep_at(3));
-          tmem_st16(act_lane + (uint32_t)((f0 >> 1) + 16), *keep_at(4), *keep_at(5), *keep_at(6), *keep_at(7));
-          publish(&actb[h >> 1]);
-          silu_to_act(bias, kMlpChunk + f0, v0);
-          silu_to_act(bias, kMlpChunk + f0 + 32, v1);
-          publish(&actb[2 + (h >> 1)]);
+          // every MMA of the layer is done: chunk 0 into ACT, each 128 inputs
+          // published at once (the next layer starts on them), then chunk 1
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            tmem_st8(act_lane + (uint32_t)(32 * m + 8 * h), *keep_at(2 * m), *keep_at(2 * m + 1));
+            if (m & 1) publish(&actb[m >> 1]);
+          }
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            uint32_t pk[8];
+            silu_q(bias, kMlpChunk, m, v0, v1, pk);
+            tmem_st8(act_lane + (uint32_t)(kMlpChunk / 2 + 32 * m + 8 * h), make_uint4(pk[0], pk[1], pk[2], pk[3]),
+                     make_uint4(pk[4], pk[5], pk[6], pk[7]));
+            if (m & 1) publish(&actb[2 + (m >> 1)]);
+          }
         } else {
-          silu_to_act(bias, f0, v0);
-          silu_to_act(bias, f0 + 32, v1);
-          publish(&actb[h >> 1]);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            uint32_t pk[8];
+            silu_q(bias, 0, m, v0, v1, pk);
+            tmem_st8(act_lane + (uint32_t)(32 * m + 8 * h), make_uint4(pk[0], pk[1], pk[2], pk[3]),
+                     make_uint4(pk[4], pk[5], pk[6], pk[7]));
+            if (m & 1) publish(&actb[m >> 1]);
+          }
         }
       }
       if (!ok) break;
@@ -402,17 +471,14 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
       // tile's features go in first
       if (!(ok = wait_acc())) break;
       if (tn < p.tiles) features(tn);
-      const int row0 = t * kBM, row = row0 + r;
+      const int row = t * kBM + r;
       const bool row_ok = row < p.batch;
       const float* bias = p.bias[L - 1];
       const int wc = p.out_pad / 4;  // this warp's columns of the head: 16 .. 64
-      // 16 columns at a time (few registers; the accumulator is released at
-      // the end), in groups of four (out_dim % 4 == 0 when staged)
-#pragma unroll 1
-      for (int c0 = h * wc; c0 < (h + 1) * wc; c0 += 16) {
-        float v[16];
-        tmem_ld16(lane_base + (uint32_t)c0, v);
-        if (c0 >= p.out_dim) continue;
+      // 16 columns c0 .. c0 + 15 of this row, in groups of four
+      auto head16 = [&](int c0, const float (&v)[16]) {
+        if (c0 >= p.out_dim || !row_ok) return;
+        float* dst = p.seeds + (size_t)row * p.out_dim + c0;
         int j = c0 % p.n_dof;  // joint of the current column, advanced incrementally
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
@@ -424,24 +490,32 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
             if (c < p.out_dim) {
               const float lo = __ldg(p.lohi + j), hi = __ldg(p.lohi + p.n_dof + j);
               o[e] = 0.5f * (lo + hi) + 0.5f * (hi - lo) * tanhf(v[4 * g + e] + __ldg(bias + c));
-              if (!p.staged && row_ok) p.seeds[(size_t)row * p.out_dim + c] = o[e];
+              if (!p.vec4) dst[4 * g + e] = o[e];
             }
             if (++j == p.n_dof) j = 0;
           }
-          if (p.staged && c0 + 4 * g < p.out_dim)
-            *reinterpret_cast<float4*>(stage + r * p.out_dim + c0 + 4 * g) = make_float4(o[0], o[1], o[2], o[3]);
+          if (p.vec4 && c0 + 4 * g < p.out_dim)
+            *reinterpret_cast<float4*>(dst + 4 * g) = make_float4(o[0], o[1], o[2], o[3]);
         }
-      }
-      tc_fence_before();
-      signal(tfree);
-      if (p.staged) {
-        // the staging tile holds the tile's rows in their global layout: a flat copy
-        if (!(ok = epi_sync(0))) break;
-        const int n4 = min(kBM, p.batch - row0) * p.out_dim / 4;
-        float4* dst = reinterpret_cast<float4*>(p.seeds + (size_t)row0 * p.out_dim);
-        const float4* src = reinterpret_cast<const float4*>(stage);
-        for (int i = te; i < n4; i += 32 * kMlpEpiWarps) dst[i] = src[i];
-        if (!(ok = epi_sync(1))) break;
+      };
+      float v[16];
+      if (wc == 16) {
+        // one 16-column piece per warp: release the accumulator before the
+        // arithmetic, so the next tile's first MMAs overlap it
+        tmem_ld16(lane_base + (uint32_t)(h * 16), v);
+        tc_fence_before();
+        signal(tfree);
+        head16(h * 16, v);
+      } else {
+        // wider heads 16 columns at a time (few registers; the accumulator
+        // is released at the end)
+#pragma unroll 1
+        for (int c0 = h * wc; c0 < (h + 1) * wc; c0 += 16) {
+          tmem_ld16(lane_base + (uint32_t)c0, v);
+          head16(c0, v);
+        }
+        tc_fence_before();
+        signal(tfree);
       }
     }
   }

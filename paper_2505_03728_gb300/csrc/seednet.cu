@@ -863,22 +863,15 @@ cudaError_t infer_fused(pk_seednet* s, int batch, const float* d_targets, float*
     p.stage_kb[l] = kb;
   }
   // ring as deep as shared memory allows next to the keep area (one chunk of
-  // BF16 results at width 512) that also stages the head's outputs
-  // (PK_MLP_STAGES caps the ring, for tuning sweeps); without room for the
-  // staging tile the head stores straight to global memory
+  // BF16 results at width 512; PK_MLP_STAGES caps the ring, for tuning sweeps)
   int cap = kMlpMaxStages;
   if (const char* env = getenv("PK_MLP_STAGES")) cap = atoi(env) > 1 ? atoi(env) : 2;
   if (cap > kMlpMaxStages) cap = kMlpMaxStages;
   const int keep = s->width == 2 * kMlpChunk ? kMlpKeepBytes : 0;
-  const int staging = MlpSmem::staging_bytes(s->out_dim);
-  auto fit = [&](int area) {
-    const int room = max_smem - MlpSmem::bytes(0, area);
-    return room / kMlpStageBytes < cap ? room / kMlpStageBytes : cap;
-  };
-  const int area_staged = staging > keep ? staging : keep;
-  p.staged = (s->out_dim % 4 == 0 && ((uintptr_t)d_seeds_out & 15) == 0 && fit(area_staged) >= 2) ? 1 : 0;
-  p.area_bytes = p.staged ? area_staged : keep;
-  p.stages = fit(p.area_bytes);
+  const int room = max_smem - MlpSmem::bytes(0, keep);
+  p.vec4 = (s->out_dim % 4 == 0 && ((uintptr_t)d_seeds_out & 15) == 0) ? 1 : 0;
+  p.area_bytes = keep;
+  p.stages = room / kMlpStageBytes < cap ? room / kMlpStageBytes : cap;
   if (p.stages < 2) return cudaErrorNotSupported;
   MlpMaps maps;
   for (int l = 0; l < s->L; ++l) {
