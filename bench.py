@@ -61,9 +61,10 @@ ROTATE_BYTES = 256 << 20
 # Split solve (pk_ik_solve_split): the first LM launch carries every problem
 # up to SPLIT iterations; the problems still running continue in a second
 # launch of TAIL_CTAS blocks (0: full grid) beside the next step.  Learned
-# seeds: ~0.6% of the problems are left after 6 iterations, and 16 blocks
-# leave the 128 CTAs of the next step's seed inference their SMs.
-LEARNED_SPLIT, LEARNED_TAIL_CTAS = 6, 16
+# seeds: ~5% of the problems are still running after 8 iterations (most of
+# them are cancelled once a sibling seed converges), and 24 blocks fit on
+# the SMs that the next step's seed inference (128 CTAs) leaves free.
+LEARNED_SPLIT, LEARNED_TAIL_CTAS = 8, 24
 PLAIN_SPLIT, PLAIN_TAIL_CTAS = 20, 0
 
 
