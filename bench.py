@@ -51,7 +51,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max 
 # DRAM bytes (read + write) per target of the LM kernel: ncu capture of the
 # 16,384-target learned-seed launch (4.626 MB), inputs read once (see profiles/).
 LM_DRAM_BYTES_PER_TARGET = 4625664 / 16384
-MLP_DRAM_BYTES_65536 = 4962048.0  # mlp_fused_kernel, dram__bytes_read.sum + write.sum per launch
+MLP_DRAM_BYTES_65536 = 4952832.0  # mlp_fused_kernel, dram__bytes_read.sum + write.sum per launch
 # FP32 operations per trajectory-iteration of the trajectory kernel (ncu count
 # over 64 trajectories x 50 iterations, see profiles/).
 TRAJ_FLOPS_PER_ITER = 1.376e6
