@@ -522,6 +522,16 @@ int64_t pk_seednet_n_params(const pk_seednet* net);
 pk_status pk_seednet_get_params(const pk_seednet* net, float* host_params, int64_t n);
 pk_status pk_seednet_set_params(pk_seednet* net, const float* host_params, int64_t n);
 
+/* Write the parameters to a file at `path` (host path; a small header with
+ * the network's shape, then the FP32 parameters in the get_params layout,
+ * host byte order), or read such a file into a network of the same shape
+ * (which also resets the AdamW state, as set_params).  Synchronous.
+ * PK_ERR_INVALID_ARG if the file cannot be opened, written or fully read, is
+ * not such a file, or holds a network of another shape (the network is then
+ * unchanged). */
+pk_status pk_seednet_save(const pk_seednet* net, const char* path);
+pk_status pk_seednet_load(pk_seednet* net, const char* path);
+
 /* Pre-head outputs d_y_out [batch][K * n_dof] (FP32) for d_targets [batch][k][12]. */
 pk_status pk_seednet_forward(pk_seednet* net, int32_t batch, const float* d_targets, float* d_y_out,
                              void* stream);

@@ -784,6 +784,64 @@ pk_status pk_seednet_set_params(pk_seednet* s, const float* host, int64_t n) {
   return sn_cuda(e, "pk_seednet_set_params");
 }
 
+// File layout of pk_seednet_save / pk_seednet_load (host byte order): the
+// header below, then the FP32 parameters in the pk_seednet_get_params order.
+namespace {
+struct SeednetFileHeader {
+  char magic[4];     // "PKSN"
+  uint32_t version;  // 1
+  int32_t k, K, n_dof, in_dim, out_dim, width, depth, reserved;
+  int64_t n_params;
+};
+}  // namespace
+
+pk_status pk_seednet_save(const pk_seednet* s, const char* path) {
+  if (!s || !path) return sn_fail(PK_ERR_INVALID_ARG, "NULL argument");
+  const int64_t n = (int64_t)oracle_count(s);
+  std::vector<float> h((size_t)n);
+  pk_status st = pk_seednet_get_params(s, h.data(), n);
+  if (st != PK_OK) return st;
+  SeednetFileHeader hd{};
+  memcpy(hd.magic, "PKSN", 4);
+  hd.version = 1;
+  hd.k = s->k;
+  hd.K = s->K;
+  hd.n_dof = s->n_dof;
+  hd.in_dim = s->in_dim;
+  hd.out_dim = s->out_dim;
+  hd.width = s->width;
+  hd.depth = s->depth;
+  hd.n_params = n;
+  FILE* f = fopen(path, "wb");
+  if (!f) return sn_fail(PK_ERR_INVALID_ARG, "pk_seednet_save: cannot open the file for writing");
+  const bool ok = fwrite(&hd, sizeof hd, 1, f) == 1 && fwrite(h.data(), sizeof(float), (size_t)n, f) == (size_t)n;
+  const bool closed = fclose(f) == 0;
+  if (!ok || !closed) return sn_fail(PK_ERR_INVALID_ARG, "pk_seednet_save: write failed");
+  return PK_OK;
+}
+
+pk_status pk_seednet_load(pk_seednet* s, const char* path) {
+  if (!s || !path) return sn_fail(PK_ERR_INVALID_ARG, "NULL argument");
+  FILE* f = fopen(path, "rb");
+  if (!f) return sn_fail(PK_ERR_INVALID_ARG, "pk_seednet_load: cannot open the file");
+  SeednetFileHeader hd{};
+  if (fread(&hd, sizeof hd, 1, f) != 1 || memcmp(hd.magic, "PKSN", 4) != 0 || hd.version != 1) {
+    fclose(f);
+    return sn_fail(PK_ERR_INVALID_ARG, "pk_seednet_load: not a seed-network file");
+  }
+  const int64_t n = (int64_t)oracle_count(s);
+  if (hd.k != s->k || hd.K != s->K || hd.n_dof != s->n_dof || hd.in_dim != s->in_dim || hd.out_dim != s->out_dim ||
+      hd.width != s->width || hd.depth != s->depth || hd.n_params != n) {
+    fclose(f);
+    return sn_fail(PK_ERR_INVALID_ARG, "pk_seednet_load: the file holds a network of another shape");
+  }
+  std::vector<float> h((size_t)n);
+  const bool ok = fread(h.data(), sizeof(float), (size_t)n, f) == (size_t)n;
+  fclose(f);
+  if (!ok) return sn_fail(PK_ERR_INVALID_ARG, "pk_seednet_load: the file is truncated");
+  return pk_seednet_set_params(s, h.data(), n);
+}
+
 pk_status pk_seednet_forward(pk_seednet* s, int32_t batch, const float* d_targets, float* d_y_out,
                              void* stream) {
   if (!s) return sn_fail(PK_ERR_INVALID_ARG, "net is NULL");

@@ -116,6 +116,8 @@ _SIGNATURES = {
     "pk_ik_plan_set_schedule": (_i32, [_vp, _i32, _i32, _i32, _i32]),
     "pk_ik_plan_stats": (_i32, [_vp, C.POINTER(C.c_int64)]),
     "pk_seednet_check": (_i32, [_vp, _vp]),
+    "pk_seednet_save": (_i32, [_vp, C.c_char_p]),
+    "pk_seednet_load": (_i32, [_vp, C.c_char_p]),
     "pk_trajopt_params_default": (None, [_vp]),
     "pk_trajopt_solve": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _i32, _vp, _f32p, _vp, _vp,
                                 _vp, _vp]),
@@ -513,6 +515,16 @@ def pk_seednet_infer(net: SeedNet, targets: torch.Tensor, out: torch.Tensor | No
 def pk_seednet_check(net: SeedNet, stream=None):
     """Synchronise and raise PkError (PK_ERR_TIMEOUT) for a device-side pipeline failure of earlier calls."""
     _check(lib().pk_seednet_check(net.handle, _stream(stream)))
+
+
+def pk_seednet_save(net: SeedNet, path: str):
+    """Write the network's parameters to ``path`` (shape header + FP32 parameters)."""
+    _check(lib().pk_seednet_save(net.handle, os.fsencode(path)))
+
+
+def pk_seednet_load(net: SeedNet, path: str):
+    """Read parameters written by pk_seednet_save into a network of the same shape."""
+    _check(lib().pk_seednet_load(net.handle, os.fsencode(path)))
 
 
 def pk_seednet_loss_grad(net: SeedNet, targets: torch.Tensor, qstar: torch.Tensor, stream=None):
