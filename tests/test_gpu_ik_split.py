@@ -192,3 +192,71 @@ def test_split_argument_checks():
     with pytest.raises(pk.PkError):
         pk.pk_ik_solve_split(g, p, links, kinds, targets, seeds, small, 3)
     assert pk.pk_ik_split_workspace_bytes(g, B, S) > pk.pk_ik_workspace_bytes(g, B, S)
+
+
+def test_full_size_split_equals_single_launch_without_cancellation():
+    """The throughput workload at full size (65,536 targets x 8 seeds, up to 50
+    iterations) through the split solve in the bench's launch configuration
+    (first launch up to 8 iterations, 24-block continuation on a second
+    stream): bit-identical to the single launch when siblings do not cancel."""
+    cfg = synth.IK_THROUGHPUT
+    spec, qt, sd = synth.ik_workload(cfg)
+    g = pk.Robot.from_spec(spec)
+    ee = g.n_joints - 1
+    targets = pk.pk_fk(g, dev(qt))[:, ee:ee + 1].contiguous()
+    seeds = dev(sd)
+    B, S = sd.shape[0], sd.shape[1]
+    p = pk.pk_ik_params_default(max_iters=50, early_exit=1, cancel_siblings=0)
+    ref = pk.pk_ik_solve(g, p, [ee], None, targets, seeds)
+    side = torch.cuda.Stream()
+    got = pk.pk_ik_solve_split(g, p, [ee], None, targets, seeds, split_ws(g, B, S), 8, 24, tail_stream=side)
+    side.synchronize()
+    same(got, ref)
+
+
+def test_full_size_pipelined_learned_steps_are_valid():
+    """Consecutive learned-seed steps overlapped as the bench runs them (seed
+    inference and first launch on one stream, continuation and selection on a
+    second, two workspaces, a different target batch per step, sibling
+    cancellation on): every step's converged answers meet the tolerance when
+    re-checked in FP64, and the success rate matches one batch at a time."""
+    cfg = synth.IK_THROUGHPUT
+    spec, qt, sd = synth.ik_workload(cfg)
+    g, o = pk.Robot.from_spec(spec), oracle.Robot.from_dict(spec)
+    ee = g.n_joints - 1
+    B, S, n = sd.shape
+    net = pk.SeedNet(g, [ee], K=S, width=512, depth=4, seed=11)
+    pk.pk_seednet_train(net, pk.pk_train_params_default(epochs=2, steps_per_epoch=600, batch=8192, seed=500))
+    steps = 3
+    qts = [qt] + [synth.uniform_q(77 + k, B, o.dof_lower, o.dof_upper) for k in range(1, steps)]
+    T = [pk.pk_fk(g, dev(q))[:, ee:ee + 1].contiguous() for q in qts]
+    p = pk.pk_ik_params_default(max_iters=50, early_exit=1, cancel_siblings=1)
+    wss = [split_ws(g, B, S) for _ in range(2)]
+    lseeds = torch.empty(B, S, n, device="cuda")
+    outs = [tuple(torch.empty(B, *shape, device="cuda", dtype=dt) for shape, dt in
+                  (((n,), torch.float32), ((2,), torch.float32), ((), torch.int32), ((), torch.int32)))
+            for _ in range(steps)]
+    main, side = torch.cuda.current_stream(), torch.cuda.Stream()
+    done = [torch.cuda.Event() for _ in range(steps)]
+    for k in range(steps):
+        if k >= 2:
+            main.wait_event(done[k - 2])
+        pk.pk_seednet_infer(net, T[k], lseeds, stream=main)
+        pk.pk_ik_solve_split(g, p, [ee], None, T[k], lseeds, wss[k % 2], 8, 24, out=outs[k], stream=main,
+                             tail_stream=side)
+        done[k].record(side)
+    torch.cuda.synchronize()
+    tg = oracle.Targets([ee])
+    for k in range(steps):
+        q, err, iters, status = [x.cpu().numpy() for x in outs[k]]
+        conv = status == pk.PK_P_CONVERGED
+        # one batch at a time, single launch
+        ref_status = pk.pk_ik_solve(g, p, [ee], None, T[k], pk.pk_seednet_infer(net, T[k]))[3].cpu().numpy()
+        assert abs(conv.mean() - (ref_status == 0).mean()) <= 0.002, (k, conv.mean(), (ref_status == 0).mean())
+        assert conv.mean() >= 0.9
+        targets = T[k].cpu().numpy().astype(np.float64)
+        idx = np.nonzero(conv)[0]
+        for b in np.random.default_rng(k).choice(idx, 500, replace=False):
+            pe, re = oracle.ik_errors(o, tg, targets[b], q[b].astype(np.float64))
+            assert pe <= p.tol_pos * (1 + 1e-3) and re <= p.tol_rot * (1 + 1e-3)
+        assert np.all(iters <= 50)
