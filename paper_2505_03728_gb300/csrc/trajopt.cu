@@ -59,6 +59,10 @@ struct TrajSmem {
   float JE[2][N][N];    // blocks (m-1, m-2) and (m, m+1) after the chains' updates
   float JL1[4][N][N];   // junction factor blocks (j, j-1)
   float JL2[4][N][N];   // junction factor blocks (j, j-2)
+  // two-ended factorisation with B = 4: junction factor blocks (a, a-k) of the
+  // eight middle rows, [k-1][a]
+  float JLb[B == 4 ? 4 : 1][B == 4 ? 8 : 1][N][N];
+  float sbt[B == 4 ? kTrajMaxT : 1][B + 1];  // smoothness scalars of blocks (t, t-k), B = 4
   alignas(16) float obs[kTrajMaxObs][4];
   float rad[N][kTrajMaxS];
   float qs[8];
@@ -971,6 +975,283 @@ __device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int
   return ok;
 }
 
+// Two-ended factorisation of a band of B block sub-diagonals (used for
+// B = 4, T >= 16).  Threads 0-63 eliminate rows 0 .. m-B-1 top-down and
+// threads 64-127 rows T-1 .. m+B bottom-up (m = T / 2), each row t against
+// its chain's predecessors p_j = t - j d (d = +1 top, -1 bottom), j = 1 .. B:
+//   L_j(t) = (A(t, p_j) - sum_{l > j} L_l(t) L_{l-j}(p_j)^T) Linv(p_j)^T,
+//   stored in L[j-1][t], then the Schur complement of t is factored.
+// The 2B middle rows take only the blocks against their chain's eliminated
+// rows; their Schur complements (coupled within the band) form a small
+// banded system factored last by threads 0-63, with the same recurrence in
+// natural order.  Substitutions run down the chains, through the middle and
+// back out.  Same result as the one-ended factorisation up to rounding order.
+template <int N, int B, bool X>
+__device__ bool twisted_solve_b(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int buf, float lam) {
+  constexpr int NT = N * (N + 1) / 2, NN = N * N, J = 2 * B;
+  const int tid = threadIdx.x, T = tp.T, m = T / 2, j0 = m - B;  // j0: first middle row
+  const int grp = (tid >> 6) & 1, gt = tid & 63;
+  auto gsync = [&] { asm volatile("bar.sync %0, 64;" ::"r"(1 + grp) : "memory"); };
+  if (tid == 0) S.chol_fail = 0;
+  for (int t = tid; t < T; t += kThreads) smooth_band<B>(tp, t, S.sbt[t]);
+  __syncthreads();
+  // smoothness scalar of block (t, u), 0 <= t - u <= B
+  auto sc = [&](int t, int u) { return S.sbt[t][t - u]; };
+  // element (i, j) of the off-diagonal block (t, u) of A, 1 <= |t - u| <= B
+  auto aoff = [&](int t, int u, int i, int j) {
+    const int hi = t > u ? t : u, lo = t + u - hi;
+    float v = (i == j) ? sc(hi, lo) : 0.f;
+    if constexpr (X)
+      if (hi - lo == 1) v += (t > u) ? S.E[buf][t][i][j] : S.E[buf][u][j][i];
+    return v;
+  };
+  auto tri_rc = [&](int e, int& r, int& c) {
+    r = 0;
+    while ((r + 1) * (r + 2) / 2 <= e) ++r;
+    c = e - r * (r + 1) / 2;
+  };
+  // dense factor of a Schur complement (one thread), its inverse into Linv[t]
+  auto factor_diag = [&](float* sch, int t) {
+    if (gt == 0) {
+      float L[NT];
+#pragma unroll
+      for (int i = 0; i < NT; ++i) L[i] = sch[i];
+      if (!chol_packed<N>(L)) S.chol_fail = 1;
+#pragma unroll
+      for (int i = 0; i < NT; ++i) sch[i] = L[i];
+    }
+    gsync();
+    if (gt < N) {
+      const int j = gt;
+      float col[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float v = (i == j) ? 1.f : 0.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          if (k >= j && k < i) v = fmaf(-sch[tri(i, k)], col[k], v);
+        col[i] = (i >= j) ? v * sch[tri(i, i)] : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i >= j) S.Linv[t][tri(i, j)] = col[i];
+    }
+    gsync();
+  };
+  // factor blocks L_j(t), j = jhi down to jlo, against eliminated rows of t's chain
+  auto row_blocks = [&](int t, int d, int jlo, int jhi) {
+    for (int j = jhi; j >= jlo; --j) {
+      const int pj = t - j * d;
+      if (j == jhi && j >= 2) {  // A(t, p_j) = c I and nothing to subtract: c Linv(p_j)^T
+        if (gt < NN) {
+          const int r = gt / N, c = gt % N;
+          const float cj = d > 0 ? sc(t, pj) : sc(pj, t);
+          S.L[j - 1][t][r][c] = (c >= r) ? cj * S.Linv[pj][tri(c, r)] : 0.f;
+        }
+        gsync();
+        continue;
+      }
+      if (gt < NN) {
+        const int r = gt / N, c = gt % N;
+        float mm = aoff(t, pj, r, c);
+        for (int l = j + 1; l <= jhi; ++l)
+#pragma unroll
+          for (int q = 0; q < N; ++q) mm = fmaf(-S.L[l - 1][t][r][q], S.L[l - j - 1][pj][c][q], mm);
+        S.cM[grp][r][c] = mm;
+      }
+      gsync();
+      if (gt < NN) {
+        const int r = gt / N, c = gt % N;
+        float v = 0.f;
+#pragma unroll
+        for (int q = 0; q < N; ++q)
+          if (q <= c) v = fmaf(S.cM[grp][r][q], S.Linv[pj][tri(c, q)], v);
+        S.L[j - 1][t][r][c] = v;
+      }
+      gsync();
+    }
+  };
+  // a chain row: blocks, Schur complement, factor (k: rows of the chain before t)
+  auto chain_row = [&](int t, int d, int k) {
+    const int jhi = k < B ? k : B;
+    if (jhi >= 1) row_blocks(t, d, 1, jhi);
+    if (gt < NT) {
+      int r, c;
+      tri_rc(gt, r, c);
+      float v = S.D[buf][t][gt] + ((r == c) ? sc(t, t) + lam : 0.f);
+      for (int j = 1; j <= jhi; ++j)
+#pragma unroll
+        for (int q = 0; q < N; ++q) v = fmaf(-S.L[j - 1][t][r][q], S.L[j - 1][t][c][q], v);
+      S.cSch[grp][gt] = v;
+    }
+    gsync();
+    factor_diag(S.cSch[grp], t);
+  };
+  if (tid < 128) {
+    if (grp == 0) {
+      for (int t = 0; t < j0; ++t) chain_row(t, 1, t);
+      for (int a = 0; a < B; ++a) row_blocks(j0 + a, 1, a + 1, B);  // middle rows above m
+    } else {
+      for (int t = T - 1; t >= m + B; --t) chain_row(t, -1, T - 1 - t);
+      for (int a = B; a < J; ++a) row_blocks(j0 + a, -1, J - a, B);  // middle rows from m
+    }
+  }
+  __syncthreads();
+  // element (r, c) of block (a, b), a >= b, of the middle rows' Schur
+  // complement (b == a: the diagonal block without lambda on the diagonal)
+  auto gblock = [&](int a, int b, int r, int c) {
+    const int ia = j0 + a, ib = j0 + b, k = a - b;
+    float v;
+    if (a < B) {  // both above m: blocks against the top chain
+      v = (k == 0) ? 0.f : aoff(ia, ib, r, c);
+      for (int l = a + 1; l <= B; ++l)
+#pragma unroll
+        for (int q = 0; q < N; ++q) v = fmaf(-S.L[l - 1][ia][r][q], S.L[l - k - 1][ib][c][q], v);
+    } else if (b >= B) {  // both from m: the transpose of block (b, a) against the bottom chain
+      v = (k == 0) ? 0.f : aoff(ia, ib, r, c);
+      for (int l = J - b; l <= B; ++l)
+#pragma unroll
+        for (int q = 0; q < N; ++q) v = fmaf(-S.L[l - 1][ib][c][q], S.L[l - k - 1][ia][r][q], v);
+    } else {
+      v = aoff(ia, ib, r, c);
+    }
+    return v;
+  };
+  if (tid < 64) {
+    for (int a = 0; a < J; ++a) {
+      const int ia = j0 + a, kmax = a < B ? a : B;
+      for (int k = kmax; k >= 1; --k) {
+        const int b = a - k;
+        if (gt < NN) {
+          const int r = gt / N, c = gt % N;
+          float mm = gblock(a, b, r, c);
+          for (int l = k + 1; l <= kmax; ++l)
+#pragma unroll
+            for (int q = 0; q < N; ++q) mm = fmaf(-S.JLb[l - 1][a][r][q], S.JLb[l - k - 1][b][c][q], mm);
+          S.cM[0][r][c] = mm;
+        }
+        gsync();
+        if (gt < NN) {
+          const int r = gt / N, c = gt % N;
+          float v = 0.f;
+#pragma unroll
+          for (int q = 0; q < N; ++q)
+            if (q <= c) v = fmaf(S.cM[0][r][q], S.Linv[j0 + b][tri(c, q)], v);
+          S.JLb[k - 1][a][r][c] = v;
+        }
+        gsync();
+      }
+      if (gt < NT) {
+        int r, c;
+        tri_rc(gt, r, c);
+        float v = S.D[buf][ia][gt] + ((r == c) ? sc(ia, ia) + lam : 0.f) + gblock(a, a, r, c);
+        for (int k = 1; k <= kmax; ++k)
+#pragma unroll
+          for (int q = 0; q < N; ++q) v = fmaf(-S.JLb[k - 1][a][r][q], S.JLb[k - 1][a][c][q], v);
+        S.cSch[0][gt] = v;
+      }
+      gsync();
+      factor_diag(S.cSch[0], ia);
+    }
+  }
+  __syncthreads();
+  const bool ok = S.chol_fail == 0;
+  // y_t = Linv_t (rhs - sum of the given blocks times y), rhs built by `acc`
+  auto solve_lower = [&](int t, auto&& acc) {
+    if (gt < N) S.ctmp[grp][gt] = acc(gt);
+    gsync();
+    if (gt < N) {
+      float v = 0.f;
+#pragma unroll
+      for (int q = 0; q < N; ++q)
+        if (q <= gt) v = fmaf(S.Linv[t][tri(gt, q)], S.ctmp[grp][q], v);
+      S.y[t][gt] = v;
+    }
+    gsync();
+  };
+  auto solve_upper = [&](int t, auto&& acc) {
+    if (gt < N) S.ctmp[grp][gt] = acc(gt);
+    gsync();
+    if (gt < N) {
+      float v = 0.f;
+#pragma unroll
+      for (int q = 0; q < N; ++q)
+        if (q >= gt) v = fmaf(S.Linv[t][tri(q, gt)], S.ctmp[grp][q], v);
+      S.y[t][gt] = v;
+    }
+    gsync();
+  };
+  // forward substitution down both chains
+  if (tid < 128) {
+    const int d = grp == 0 ? 1 : -1;
+    const int t0 = grp == 0 ? 0 : T - 1, n = j0;  // both chains hold m - B rows (T even) or one more (bottom, T odd)
+    const int len = grp == 0 ? n : T - m - B;
+    for (int k = 0; k < len; ++k) {
+      const int t = t0 + k * d, jhi = k < B ? k : B;
+      solve_lower(t, [&](int i) {
+        float v = -S.g[buf][t][i];
+        for (int j = 1; j <= jhi; ++j)
+#pragma unroll
+          for (int q = 0; q < N; ++q) v = fmaf(-S.L[j - 1][t][i][q], S.y[t - j * d][q], v);
+        return v;
+      });
+    }
+  }
+  __syncthreads();
+  // the middle rows: forward with the blocks against both chains, then back
+  if (tid < 64) {
+    for (int a = 0; a < J; ++a) {
+      const int ia = j0 + a, kmax = a < B ? a : B;
+      solve_lower(ia, [&](int i) {
+        float v = -S.g[buf][ia][i];
+        if (a < B) {
+          for (int l = a + 1; l <= B; ++l)
+#pragma unroll
+            for (int q = 0; q < N; ++q) v = fmaf(-S.L[l - 1][ia][i][q], S.y[ia - l][q], v);
+        } else {
+          for (int l = J - a; l <= B; ++l)
+#pragma unroll
+            for (int q = 0; q < N; ++q) v = fmaf(-S.L[l - 1][ia][i][q], S.y[ia + l][q], v);
+        }
+        for (int k = 1; k <= kmax; ++k)
+#pragma unroll
+          for (int q = 0; q < N; ++q) v = fmaf(-S.JLb[k - 1][a][i][q], S.y[ia - k][q], v);
+        return v;
+      });
+    }
+    for (int a = J - 1; a >= 0; --a) {
+      const int ia = j0 + a;
+      solve_upper(ia, [&](int i) {
+        float v = S.y[ia][i];
+        for (int k = 1; k <= B && a + k < J; ++k)
+#pragma unroll
+          for (int q = 0; q < N; ++q) v = fmaf(-S.JLb[k - 1][a + k][q][i], S.y[ia + k][q], v);
+        return v;
+      });
+    }
+  }
+  __syncthreads();
+  // backward substitution up both chains, from the middle outwards
+  if (tid < 128) {
+    const int d = grp == 0 ? 1 : -1;
+    const int tb = grp == 0 ? j0 - 1 : m + B, len = grp == 0 ? j0 : T - m - B;
+    for (int k = 0; k < len; ++k) {
+      const int t = tb - k * d;
+      solve_upper(t, [&](int i) {
+        float v = S.y[t][i];
+        for (int j = 1; j <= B; ++j) {
+          const int u = t + j * d;
+#pragma unroll
+          for (int q = 0; q < N; ++q) v = fmaf(-S.L[j - 1][u][q][i], S.y[u][q], v);
+        }
+        return v;
+      });
+    }
+  }
+  __syncthreads();
+  return ok;
+}
+
 template <int N, int B, bool X>
 __global__ void __launch_bounds__(kThreads) trajopt_kernel(
     const __grid_constant__ ChainC<N> rc, const __grid_constant__ TrajParamsDev tp, const float* __restrict__ q_start,
@@ -1023,7 +1304,7 @@ __global__ void __launch_bounds__(kThreads) trajopt_kernel(
     if constexpr (B == 2) {
       ok = T >= 8 ? twisted_solve<N, X>(tp, S, u, lam) : banded_solve<N, B, X>(tp, S, u, lam);
     } else {
-      ok = banded_solve<N, B, X>(tp, S, u, lam);
+      ok = T >= 4 * B ? twisted_solve_b<N, B, X>(tp, S, u, lam) : banded_solve<N, B, X>(tp, S, u, lam);
     }
     if (ok) {
       const int c = u ^ 1;

@@ -98,11 +98,16 @@ def test_one_step_from_several_points_matches_oracle():
         assert np.median(rel[~tie]) <= 1e-4, rel
 
 
-@pytest.mark.parametrize("T", [5, 7, 8, 9, 12, 33])
-@pytest.mark.parametrize("ext", [{}, dict(w_vlimit=3.0, v_max=0.02, w_swept=10.0)])
+FIVE = dict(w_acc5=2.0, w_jerk=3.0)
+LIMITS = dict(w_vlimit=3.0, v_max=0.02, w_swept=10.0)
+
+
+@pytest.mark.parametrize("T", [5, 7, 8, 9, 12, 15, 16, 17, 33])
+@pytest.mark.parametrize("ext", [{}, LIMITS, FIVE, dict(FIVE, **LIMITS)], ids=["plain", "limits", "five", "both"])
 def test_one_step_short_horizons_match_oracle(T, ext):
     """One LM step at horizons on both sides of the shortest the two-ended
-    block factorisation takes (8), odd and even, with and without the
+    block factorisations take (8 with two block sub-diagonals, 16 with the
+    four of the five-point stencils), odd and even, with and without the
     off-diagonal blocks of the velocity-limit and swept terms."""
     o, g, qs, goals, x0, radii, obs, plane, scene = setup(8, T, perturb=0.1, seed=T)
     p = pk.pk_trajopt_params_default(iters=1, **ext)
@@ -110,12 +115,24 @@ def test_one_step_short_horizons_match_oracle(T, ext):
     q = pk.pk_trajopt_solve(g, p, dev(qs), dev(goals), dev(x0), dev(radii), dev(obs), plane)[0].cpu().numpy()
     tie = ref["margin"] <= 1e-5
     rel = (np.abs(q - ref["x"]) / np.maximum(1.0, np.abs(ref["x"]))).reshape(8, -1).max(axis=1)
-    # a wrong block anywhere in the factorisation moves the step by O(1); the
-    # FP32 factor of these short, perturbed, less well conditioned systems
-    # lands within ~1e-3 of the FP64 step (the banded path measured 4e-8 to
-    # 1.5e-3 at T = 5)
-    assert np.all(rel[~tie] <= 5e-3), rel
-    assert np.median(rel[~tie]) <= 1e-3, rel
+    # these short, perturbed systems have condition numbers of 1e5 - 3e5, so
+    # the FP32 step may differ from the FP64 one by several 1e-3 (measured:
+    # up to 5.3e-3); the backward error below is the sharp check
+    assert np.all(rel[~tie] <= 2e-2), rel
+    assert np.median(rel[~tie]) <= 5e-3, rel
+    # whatever the conditioning, an accepted GPU step solves the oracle's
+    # damped normal equations to FP32 accuracy (backward error); a wrong block
+    # in the factorisation or the substitutions leaves an O(1) residual
+    op = oparams(p)
+    for b in np.nonzero(~tie)[0]:
+        # the GPU started from x0 rounded to FP32: a rejected step leaves it exactly there
+        dx = (q[b].astype(np.float64) - x0[b].astype(np.float32).astype(np.float64)).ravel()
+        if not np.any(dx):
+            continue  # rejected step
+        f, A, gr = oracle.traj_normal(o, op, scene, x0[b], qs[b], goals[b])
+        M = A + p.lambda0 * np.eye(len(A))
+        be = np.linalg.norm(M @ dx + gr) / (np.linalg.norm(M, 2) * np.linalg.norm(dx) + np.linalg.norm(gr))
+        assert be <= 1e-4, (b, be)
 
 
 def test_first_iterates_match_oracle():
