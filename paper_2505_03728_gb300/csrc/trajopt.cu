@@ -62,7 +62,7 @@ struct TrajSmem {
   // two-ended factorisation with B = 4: junction factor blocks (a, a-k) of the
   // eight middle rows, [k-1][a]
   float JLb[B == 4 ? 4 : 1][B == 4 ? 8 : 1][N][N];
-  float sbt[B == 4 ? kTrajMaxT : 1][B + 1];  // smoothness scalars of blocks (t, t-k), B = 4
+  float sbt[kTrajMaxT][B + 1];  // smoothness scalars of blocks (t, t-k) (two-ended solves)
   alignas(16) float obs[kTrajMaxObs][4];
   float rad[N][kTrajMaxS];
   float qs[8];
@@ -713,13 +713,10 @@ __device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int
   const int grp = (tid >> 6) & 1, gt = tid & 63;  // chain (0 top, 1 bottom) and thread within it
   auto gsync = [&] { asm volatile("bar.sync %0, 64;" ::"r"(1 + grp) : "memory"); };
   if (tid == 0) S.chol_fail = 0;
+  for (int t = tid; t < T; t += kThreads) smooth_band<2>(tp, t, S.sbt[t]);
   __syncthreads();
   // smoothness scalar of block (t, u), 0 <= t - u <= 2
-  auto sc = [&](int t, int u) {
-    float sb[3];
-    smooth_band<2>(tp, t, sb);
-    return sb[t - u];
-  };
+  auto sc = [&](int t, int u) { return S.sbt[t][t - u]; };
   // element (i, j) of the off-diagonal block (t, u) of A, |t - u| = 1
   auto a1 = [&](int t, int u, int i, int j) {
     const int hi = t > u ? t : u;
