@@ -54,7 +54,7 @@ LM_DRAM_BYTES_PER_TARGET = 4625664 / 16384
 MLP_DRAM_BYTES_65536 = 4952832.0  # mlp_fused_kernel, dram__bytes_read.sum + write.sum per launch
 # FP32 operations per trajectory-iteration of the trajectory kernel (ncu count
 # over 64 trajectories x 50 iterations, see profiles/).
-TRAJ_FLOPS_PER_ITER = 1.376e6
+TRAJ_FLOPS_PER_ITER = 1.355e6
 # Every timed step reads its own input batch; an arm rotates through enough
 # batches to hold at least this many bytes (twice the 129 MB L2).
 ROTATE_BYTES = 256 << 20
