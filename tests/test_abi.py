@@ -77,3 +77,10 @@ def test_null_arguments(L):
     assert L.pk_ik_solve(None, None, 1, None, None, 1, 1, None, None, None, None, None, None, None, 0,
                          None) == pk.PK_ERR_INVALID_ARG
     assert L.pk_ik_workspace_bytes(None, 1, 1) == 0
+    assert L.pk_ik_solve_split(None, None, 1, None, None, 1, 1, None, None, None, None, None, None, None, 0, 8, 0,
+                               None, None) == pk.PK_ERR_INVALID_ARG
+    assert L.pk_ik_split_workspace_bytes(None, 1, 1) == 0
+    stats = (C.c_int64 * 8)()
+    assert L.pk_ik_split_workspace_stats(None, stats) == pk.PK_ERR_INVALID_ARG
+    assert L.pk_seednet_save(None, b"x.pksn") == pk.PK_ERR_INVALID_ARG
+    assert L.pk_seednet_load(None, b"x.pksn") == pk.PK_ERR_INVALID_ARG
