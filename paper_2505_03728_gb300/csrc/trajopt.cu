@@ -1181,8 +1181,9 @@ __device__ bool twisted_solve_b(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, i
   // forward substitution down both chains
   if (tid < 128) {
     const int d = grp == 0 ? 1 : -1;
-    const int t0 = grp == 0 ? 0 : T - 1, n = j0;  // both chains hold m - B rows (T even) or one more (bottom, T odd)
-    const int len = grp == 0 ? n : T - m - B;
+    // the top chain holds rows 0 .. m-B-1, the bottom one T-1 .. m+B (one
+    // more row than the top for odd T)
+    const int t0 = grp == 0 ? 0 : T - 1, len = grp == 0 ? j0 : T - m - B;
     for (int k = 0; k < len; ++k) {
       const int t = t0 + k * d, jhi = k < B ? k : B;
       solve_lower(t, [&](int i) {
