@@ -68,7 +68,7 @@ LEARNED_SPLIT, LEARNED_TAIL_CTAS = 8, 24
 PLAIN_SPLIT, PLAIN_TAIL_CTAS = 20, 0
 
 
-CASES = ("lm", "lm-learned", "lm-flops", "seednet", "tree", "trajopt")
+CASES = ("lm", "lm-learned", "lm-learned-split", "lm-flops", "seednet", "tree", "trajopt")
 
 
 def parse():
@@ -467,6 +467,8 @@ def run_case(args):
     """Small single-kernel workloads for ncu captures (the commands in profiles/):
     lm          pk_ik_solve, 7-DoF chain, uniform seeds, --batch targets x 8, 2 solves
     lm-learned  the same with seeds from a briefly trained seed network
+    lm-learned-split  the same through pk_ik_solve_split as the bench runs it (first launch up to
+                LEARNED_SPLIT iterations, LEARNED_TAIL_CTAS-block continuation on a second stream)
     lm-flops    three pk_ik_solve launches of --batch targets x 8 uniform seeds without early exit
                 (max_iters 0, 1, 10), printing their work counters: with ncu's FP32 instruction
                 counters they give the per-unit flops of an evaluation, a build and a solve
@@ -489,7 +491,7 @@ def run_case(args):
             torch.cuda.synchronize()
             print("ok lm-flops max_iters", mi, pk.pk_ik_workspace_stats(ws))
         return
-    if args.case in ("lm", "lm-learned", "seednet"):
+    if args.case in ("lm", "lm-learned", "lm-learned-split", "seednet"):
         spec, qt, sd = synth.ik_workload(synth.IK_THROUGHPUT, B)
         g = pk.Robot.from_spec(spec)
         ee = g.n_joints - 1
@@ -506,6 +508,15 @@ def run_case(args):
             pk.pk_seednet_train(net, pk.pk_train_params_default(epochs=2, steps_per_epoch=600))
             seeds = pk.pk_seednet_infer(net, T)
         p = pk.pk_ik_params_default(cancel_siblings=1)
+        if args.case == "lm-learned-split":
+            ws = torch.empty(pk.pk_ik_split_workspace_bytes(g, B, 8), dtype=torch.uint8, device="cuda")
+            tail = torch.cuda.Stream()
+            for _ in range(2):
+                out = pk.pk_ik_solve_split(g, p, [ee], None, T, seeds, ws, LEARNED_SPLIT, LEARNED_TAIL_CTAS,
+                                           tail_stream=tail)
+            torch.cuda.synchronize()
+            print("ok", args.case, B, pk.pk_ik_split_workspace_stats(ws), float((out[3] == 0).float().mean()))
+            return
         ws = torch.empty(pk.pk_ik_workspace_bytes(g, B, 8), dtype=torch.uint8, device="cuda")
         for _ in range(2):
             out = pk.pk_ik_solve(g, p, [ee], None, T, seeds, ws)
