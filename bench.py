@@ -185,14 +185,19 @@ def run_reference(args, cfg):
     from paper_2505_03728_gb300 import synth
     spec, qt, sd = synth.ik_workload(cfg)
     # calibrate a per-step sample of ~3 s
-    conv, dt, thr = oracle_sample(spec, qt, sd, 32)
-    n = int(min(len(qt), max(32, 32 * 3.0 / max(dt, 1e-3))))
+    n0 = min(32, len(qt))
+    conv, dt, thr = oracle_sample(spec, qt, sd, n0)
+    n = int(min(len(qt), max(n0, n0 * 3.0 / max(dt, 1e-3))))
+    # step k (warm-ups first) takes the n targets from offset(k); the window
+    # always lies inside the workload, also when n covers all of it
+    offset = lambda k: (k * n) % max(1, len(qt) - n + 1)
     for w in range(args.warmup):
-        oracle_sample(spec, qt[w * n:], sd[w * n:], n)
+        off = offset(w)
+        oracle_sample(spec, qt[off:off + n], sd[off:off + n], n)
     tot_c, tot_t = 0, 0.0
     for k in range(args.steps):
-        off = (k * n) % max(1, len(qt) - n)
-        c, t, thr = oracle_sample(spec, qt[off:], sd[off:], n)
+        off = offset(args.warmup + k)
+        c, t, thr = oracle_sample(spec, qt[off:off + n], sd[off:off + n], n)
         tot_c += c
         tot_t += t
     value = tot_c / tot_t
@@ -363,7 +368,7 @@ def extra_workloads(torch, pk, synth, args, flush, stream):
         nconv = int((hst == pk.PK_P_CONVERGED).sum().item())
         hum[name] = {"value": nconv / (hms / 1e3), "ms_per_step": hms / 3, "success_rate": nconv / (3 * Bh)}
     out["learned_humanoid"] = hum
-    # mobile-base IK (Sec. IV-D): shifted reachable poses, fixed vs SE(2)-base arm, 5 mm / 0.05 rad
+    # mobile-base IK (Sec. V-B): shifted reachable poses, fixed vs SE(2)-base arm, 5 mm / 0.05 rad
     mcfg = synth.MOBILE
     arm, mob, qt, shift, sdm = synth.mobile_workload(mcfg)
     ga, gm = pk.Robot.from_spec(arm), pk.Robot.from_spec(mob)

@@ -425,7 +425,7 @@ typedef struct {
   int32_t reserved;   /* must be 0 */
   /* extensions, off by default: velocity-limit hinge (Sec. III-C, dt = 1)
    * w_vlimit max(0, |q_t - q_{t-1}| - v_max) per joint, and swept-sphere
-   * collision between t and t+1 (Sec. IV-B): w_swept f(d, eta) with d the
+   * collision between t and t+1 (Sec. IV-A): w_swept f(d, eta) with d the
    * distance from each obstacle sphere to the capsule a link sphere sweeps */
   float w_vlimit;     /* default 0 */
   float v_max;        /* rad (or m) per timestep, default 0.1 */

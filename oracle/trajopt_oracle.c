@@ -35,7 +35,7 @@ typedef struct {
   /* extensions (0 = off): velocity-limit hinge w_vlimit max(0, |q_t - q_{t-1}|
    * - v_max) (Sec. III-C, dt = 1) and swept-sphere collision between t and
    * t+1, w_swept f(d, eta) with d the distance from an obstacle sphere to the
-   * capsule swept by a link sphere (Sec. IV-B continuous collision) */
+   * capsule swept by a link sphere (Sec. IV-A continuous collision) */
   double w_vlimit, v_max, w_swept;
   /* five-point stencils (Sec. III-C smoothness; 0 = off): acceleration
    * (-q_{t+2} + 16 q_{t+1} - 30 q_t + 16 q_{t-1} - q_{t-2}) / 12 and jerk

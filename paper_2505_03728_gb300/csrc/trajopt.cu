@@ -471,7 +471,7 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
       for (int j = 0; j < N; ++j) atomicAdd(&S.g[buf][t][j], gl[j]);
     }
   }
-  // swept spheres (Sec. IV-B): the capsule of this lane's sphere from t to t+1
+  // swept spheres (Sec. IV-A): the capsule of this lane's sphere from t to t+1
   // against every obstacle sphere; the row couples q_t and q_{t+1}
   if (X && tp.w_swept > 0.f && t + 1 < tp.T && lane < nsph) {
     const int l = lane / tp.S, s = lane % tp.S;

@@ -68,3 +68,16 @@ def test_reference_arm_prints_once_on_rank_zero():
     line = json.loads(outs[0][0].strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_warmups_when_the_sample_covers_the_workload():
+    """With a 64-target workload the calibrated per-step sample covers every
+    target, so every warm-up and timed step must take the whole workload
+    rather than slice past its end."""
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    p = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--batch", "64", "--steps", "2",
+                        "--warmup", "3"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    line = json.loads(p.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["warmup"] == 3 and line["steps"] == 2
+    assert line["value"] > 0 and "64 targets" in line["cpu_baseline"]["sample"]

@@ -1,4 +1,4 @@
-"""Mobile-base IK on the GPU (Sec. IV-D): the 7-DoF chain on an SE(2) base
+"""Mobile-base IK on the GPU (Sec. V-B): the 7-DoF chain on an SE(2) base
 (prismatic x, prismatic y, revolute z ahead of the arm; ten variables, the
 warp-per-problem path) against the FP64 oracle, and the paper's experiment:
 reachable poses shifted in the plane, solved with a fixed and with a mobile

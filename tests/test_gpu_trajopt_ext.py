@@ -1,6 +1,6 @@
 """GPU trajectory extensions against the FP64 oracle: the velocity-limit hinge
 (Sec. III-C) and swept-sphere collision between consecutive timesteps
-(Sec. IV-B), whose rows couple q_t and q_{t+1} and fill the (t, t-1) blocks of
+(Sec. IV-A), whose rows couple q_t and q_{t+1} and fill the (t, t-1) blocks of
 the normal matrix, and the five-point acceleration and jerk stencils
 (Sec. III-C smoothness), which widen the normal matrix to four block
 sub-diagonals.  Tolerances as in test_gpu_trajopt.py."""

@@ -1,4 +1,4 @@
-"""Mobile-base IK (Sec. IV-D): the SE(2) base as prismatic x, prismatic y and
+"""Mobile-base IK (Sec. V-B): the SE(2) base as prismatic x, prismatic y and
 revolute z joints ahead of the arm.  Pinned against the closed form
 T_world<-base(x, y, theta) T_base<-i of the arm's own FK."""
 import numpy as np

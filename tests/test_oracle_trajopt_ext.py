@@ -1,6 +1,6 @@
 """Trajectory-optimisation extensions of the oracle: the velocity-limit hinge
 (Sec. III-C, dt = 1) and swept-sphere collision between consecutive timesteps
-(Sec. IV-B).  Pinned by recomputing the rows in numpy from the oracle's FK
+(Sec. IV-A).  Pinned by recomputing the rows in numpy from the oracle's FK
 frames -- the capsule distance by a dense brute-force search along the segment
 instead of the closed-form closest point --, by central differences of the
 new rows, and by the normal matrix's block structure (still pentadiagonal:
