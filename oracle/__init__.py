@@ -84,7 +84,8 @@ def lib():
                          "or_banded_cholesky", "or_banded_cholesky_b", "or_host_cores", "or_ik_beam"):
                 if hasattr(L, name):
                     getattr(L, name).restype = C.c_int32
-            for name in ("or_coll_activation", "or_traj_normal"):
+            L.or_lm_run.restype = C.c_int32
+            for name in ("or_coll_activation", "or_traj_normal", "or_traj_lm_run"):
                 getattr(L, name).restype = C.c_double
             _lib = L
     return _lib
@@ -282,6 +283,25 @@ def ik_solve(robot: Robot, params: IkParams, tg: Targets, targets, seeds, n_trac
     return out
 
 
+def lm_run(robot: Robot, params: IkParams, tg: Targets, targets, seed, n_trace, lambda_init=-1.0):
+    """One LM run of a single problem (targets [k][12], seed [n_dof]) with its
+    configuration and damping after iterations 1..n_trace.
+
+    Returns a dict with q [n], q_trace [n_trace][n], lam_trace [n_trace], cost,
+    pos_err, rot_err, iters, status and lam (the final damping)."""
+    targets = _f64(targets).reshape(tg.k, 12)
+    seed = _f64(seed).reshape(robot.n_dof)
+    n = robot.n_dof
+    qtr = np.zeros((max(n_trace, 1), n))
+    ltr = np.zeros(max(n_trace, 1))
+    q = np.zeros(n)
+    res = np.zeros(6)
+    lib().or_lm_run(C.byref(robot._c), C.byref(params._c), C.byref(tg._c), _p(targets), _p(seed),
+                    C.c_double(lambda_init), int(n_trace), _p(qtr), _p(ltr), _p(q), _p(res))
+    return dict(q=q, q_trace=qtr[:n_trace], lam_trace=ltr[:n_trace], cost=res[0], pos_err=res[1],
+                rot_err=res[2], iters=int(res[3]), status=int(res[4]), lam=res[5])
+
+
 def ik_beam(robot: Robot, params: IkParams, tg: Targets, targets, seeds, steps1=6, keep=4, steps2=10,
             n_threads=0):
     """IK-Beam (Sec. V-C).  targets [B][k][12], seeds [B][S][n_dof]; steps1 LM
@@ -420,6 +440,18 @@ def banded_cholesky(A, T, n, band=2):
     L = np.empty_like(A)
     rc = lib().or_banded_cholesky_b(T, n, band, A.ctypes.data_as(_f64p), L.ctypes.data_as(_f64p))
     return L if rc == 0 else None
+
+
+def traj_lm_run(robot, params, scene, x0, q_start, goal):
+    """One trajectory's LM run (x0 [T][n]).  Returns dict(x, cost, trace
+    [iters][T][n], lam_trace [iters]): x and the damping after every iteration."""
+    x = _f64(x0).copy()
+    T, n = x.shape
+    tr = np.empty((params.iters, T, n))
+    lt = np.empty(params.iters)
+    f = lib().or_traj_lm_run(C.byref(robot._c), C.byref(params._c), C.byref(scene._c), T, _p(x),
+                             _p(_f64(q_start)), _p(_f64(goal)), tr.ctypes.data_as(_f64p), _p(lt))
+    return dict(x=x, cost=f, trace=tr, lam_trace=lt)
 
 
 def traj_solve(robot, params, scene, x0, q_start, goals, n_trace=False, n_threads=0):

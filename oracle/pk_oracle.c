@@ -542,10 +542,13 @@ static int converged(const or_ik_params* p, double pe, double re) {
 
 /* One LM run (Sec. III-A) from `seed` with damping lambda_init (the LM state
  * of an earlier run, or p->lambda0 when negative); the damping after the last
- * iteration goes to *lambda_out when given. */
+ * iteration goes to *lambda_out when given.  trace / lam_trace (optional,
+ * n_trace entries each) receive q and the damping after iterations
+ * 1..n_trace; entries past the last iteration repeat the final state. */
 static void lm_problem(const or_robot* rb, const or_ik_params* p, const or_target_spec* ts,
                        const double* targets, const double* seed, double* q, lm_result* res,
-                       int n_trace, double* trace, double lambda_init, double* lambda_out) {
+                       int n_trace, double* trace, double* lam_trace, double lambda_init,
+                       double* lambda_out) {
   const int nd = or_n_dof(rb), m = or_n_residuals(rb, ts);
   double* r = (double*)malloc(sizeof(double) * m);
   double* rt = (double*)malloc(sizeof(double) * m);
@@ -563,7 +566,10 @@ static void lm_problem(const or_robot* rb, const or_ik_params* p, const or_targe
   if (!isfinite(f)) {
     res->cost = f; res->pos_err = NAN; res->rot_err = NAN;
     res->iters = 0; res->status = OR_P_NONFINITE;
-    for (int t = 0; t < n_trace; ++t) memcpy(trace + t * nd, q, sizeof(double) * nd);
+    for (int t = 0; t < n_trace; ++t) {
+      if (trace) memcpy(trace + t * nd, q, sizeof(double) * nd);
+      if (lam_trace) lam_trace[t] = lambda_init >= 0 ? lambda_init : p->lambda0;
+    }
     goto done;
   }
   or_ik_errors(rb, ts, targets, q, &pe, &re);
@@ -609,11 +615,15 @@ static void lm_problem(const or_robot* rb, const or_ik_params* p, const or_targe
         lambda = lambda * p->nu;
         if (lambda > p->lambda_max) lambda = p->lambda_max;
       }
-      if (it <= n_trace) memcpy(trace + (it - 1) * nd, q, sizeof(double) * nd);
+      if (it <= n_trace && trace) memcpy(trace + (it - 1) * nd, q, sizeof(double) * nd);
+      if (it <= n_trace && lam_trace) lam_trace[it - 1] = lambda;
       if (p->early_exit && conv) break;
     }
   }
-  for (int t = it; t < n_trace; ++t) memcpy(trace + t * nd, q, sizeof(double) * nd);
+  for (int t = it; t < n_trace; ++t) {
+    if (trace) memcpy(trace + t * nd, q, sizeof(double) * nd);
+    if (lam_trace) lam_trace[t] = lambda;
+  }
   or_ik_errors(rb, ts, targets, q, &pe, &re);
   res->cost = f; res->pos_err = pe; res->rot_err = re; res->iters = it;
   res->status = converged(p, pe, re) ? OR_P_CONVERGED : OR_P_MAX_ITERS;
@@ -648,7 +658,7 @@ static void* pool_worker(void* arg) {
     long b = i / c->n_seeds;
     lm_problem(c->rb, c->p, c->ts, c->targets + b * 12 * k, c->seeds + i * c->nd,
                c->q_all + i * c->nd, &c->res[i], c->n_trace,
-               c->trace ? c->trace + i * (long)c->n_trace * c->nd : NULL, -1.0, NULL);
+               c->trace ? c->trace + i * (long)c->n_trace * c->nd : NULL, NULL, -1.0, NULL);
   }
   return NULL;
 }
@@ -711,6 +721,17 @@ int32_t or_ik_solve(const or_robot* rb, const or_ik_params* p, const or_target_s
   return n_threads;
 }
 
+int32_t or_lm_run(const or_robot* rb, const or_ik_params* p, const or_target_spec* ts, const double* targets,
+                  const double* seed, double lambda_init, int32_t n_trace, double* q_trace, double* lam_trace,
+                  double* q_out, double* res_out) {
+  lm_result res;
+  double lam = 0;
+  lm_problem(rb, p, ts, targets, seed, q_out, &res, n_trace, q_trace, lam_trace, lambda_init, &lam);
+  res_out[0] = res.cost; res_out[1] = res.pos_err; res_out[2] = res.rot_err;
+  res_out[3] = res.iters; res_out[4] = res.status; res_out[5] = lam;
+  return res.status;
+}
+
 /* ------------------------------------------------------------------ */
 /* IK-Beam (Sec. V-C): every target starts from n_seeds seeds; all of them
  * take steps1 LM iterations; the `keep` seeds with the lowest cost (ties: the
@@ -748,7 +769,8 @@ static void beam_target(beam_ctx* c, long b) {
   double* q2 = (double*)malloc(sizeof(double) * nd);
   /* phase 1: every seed */
   for (int s = 0; s < S; ++s)
-    lm_problem(c->rb, &p1, c->ts, tg, c->seeds + (b * S + s) * nd, q1 + s * nd, &r1[s], 0, NULL, -1.0, &lam1[s]);
+    lm_problem(c->rb, &p1, c->ts, tg, c->seeds + (b * S + s) * nd, q1 + s * nd, &r1[s], 0, NULL, NULL, -1.0,
+               &lam1[s]);
   /* selection and phase 2 */
   int best_s = -1, best_conv = 0, best_it = 0, best_status = 0;
   double best_f = INFINITY, best_pe = NAN, best_re = NAN;
@@ -767,7 +789,7 @@ static void beam_target(beam_ctx* c, long b) {
       r2 = r1[sel];
       r2.iters = 0;
     } else {
-      lm_problem(c->rb, &p2, c->ts, tg, q1 + sel * nd, q2, &r2, 0, NULL, lam1[sel], NULL);
+      lm_problem(c->rb, &p2, c->ts, tg, q1 + sel * nd, q2, &r2, 0, NULL, NULL, lam1[sel], NULL);
     }
     const int conv = r2.status == OR_P_CONVERGED;
     const double f = rank_cost(r2.cost);

@@ -118,6 +118,20 @@ int32_t or_ik_solve(const or_robot* rb, const or_ik_params* p, const or_target_s
                     int32_t n_threads);
 
 /*
+ * One LM run (Sec. III-A) of a single (target set, seed) problem, for the pins
+ * of the damping schedule.  lambda_init < 0 starts from p->lambda0.
+ *   q_trace [n_trace][n_dof], lam_trace [n_trace] (either may be NULL): q and
+ *     the damping after iterations 1..n_trace (the final state repeated past
+ *     the last iteration);
+ *   q_out [n_dof]; res_out [6] = cost, pos_err, rot_err, iterations, status,
+ *     final damping.
+ * Returns the status.
+ */
+int32_t or_lm_run(const or_robot* rb, const or_ik_params* p, const or_target_spec* ts, const double* targets,
+                  const double* seed, double lambda_init, int32_t n_trace, double* q_trace, double* lam_trace,
+                  double* q_out, double* res_out);
+
+/*
  * IK-Beam (Sec. V-C) over batch targets with n_seeds seeds each: steps1 LM
  * iterations on every seed, then the `keep` lowest-cost seeds (ties: lower
  * seed index; non-finite costs last) continue from their configuration and

@@ -436,9 +436,11 @@ double or_traj_normal(const or_robot* rb, const or_traj_params* p, const or_traj
   return traj_normal(rb, p, sc, T, x, qs, goal, A, g);
 }
 
-/* LM on one trajectory: x [T][n] in/out; trace (optional) [iters][T][n]. */
+/* LM on one trajectory: x [T][n] in/out; trace (optional) [iters][T][n] and
+ * lam_trace (optional) [iters]: x and the damping after every iteration. */
 static double traj_lm(const or_robot* rb, const or_traj_params* p, const or_traj_scene* sc, int32_t T,
-                      double* x, const double* qs, const double* goal, double* trace, double* margin) {
+                      double* x, const double* qs, const double* goal, double* trace, double* margin,
+                      double* lam_trace) {
   const int n = or_n_dof(rb), N = T * n;
   double* A = (double*)malloc(sizeof(double) * (size_t)N * N);
   double* Al = (double*)malloc(sizeof(double) * (size_t)N * N);
@@ -478,6 +480,7 @@ static double traj_lm(const or_robot* rb, const or_traj_params* p, const or_traj
       if (lambda > p->lambda_max) lambda = p->lambda_max;
     }
     if (trace) memcpy(trace + (size_t)it * N, x, sizeof(double) * N);
+    if (lam_trace) lam_trace[it] = lambda;
   }
   free(A); free(Al); free(L); free(g); free(ng); free(dx); free(xt);
   return f;
@@ -505,7 +508,7 @@ static void* traj_worker(void* arg) {
     const size_t N = (size_t)c->T * c->n;
     c->cost[b] = traj_lm(c->rb, c->p, c->sc, c->T, c->x + b * N, c->qs + b * c->n, c->goals + b * 12,
                          c->trace ? c->trace + b * (size_t)c->p->iters * N : NULL,
-                         c->margin ? c->margin + b : NULL);
+                         c->margin ? c->margin + b : NULL, NULL);
   }
   return NULL;
 }
@@ -523,4 +526,11 @@ int32_t or_traj_solve(const or_robot* rb, const or_traj_params* p, const or_traj
   for (int i = 0; i < n_threads; ++i) pthread_join(th[i], NULL);
   free(th);
   return n_threads;
+}
+
+/* One trajectory's LM run with its x and damping after every iteration, for
+ * the pins of the damping schedule; returns the final cost. */
+double or_traj_lm_run(const or_robot* rb, const or_traj_params* p, const or_traj_scene* sc, int32_t T, double* x,
+                      const double* q_start, const double* goal, double* trace, double* lam_trace) {
+  return traj_lm(rb, p, sc, T, x, q_start, goal, trace, NULL, lam_trace);
 }
