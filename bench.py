@@ -41,20 +41,27 @@ sys.path.insert(0, ROOT)
 METRIC = "converged IK solves/s at ≤1mm/0.5° (learned-seed vs plain LM, 1 GB300)"
 UNIT = "solves/s"
 
-# FP32 operations (add, mul = 1; fma = 2) per unit of work of the fused LM
-# kernel for the 7-DoF chain, from ncu's per-thread executed FADD/FMUL/FFMA
-# counts over launches with known work counters (see profiles/).
-FLOPS_PER_EVAL = 1216.6
-FLOPS_PER_BUILD = 1320.5
-FLOPS_PER_SOLVE = 193.0
+# Algorithmic FLOPs per unit of LM work on the 7-DoF chain, counted on the
+# oracle's own arithmetic by its FLOP census (`python -m oracle.census`:
+# +, -, *, /, sqrt one FLOP each, structural zeros free; averaged over the
+# states the oracle's LM runs visit): a candidate evaluation (FK, residuals,
+# cost), a normal-equation build at an accepted point (Jacobian, J^T J, J^T r,
+# convergence errors) and a damped solve (Cholesky, both substitutions).
+# The roofline multiplies them by the GPU's live work counters.
+FLOPS_PER_EVAL = 975.1
+FLOPS_PER_BUILD = 1818.9
+FLOPS_PER_SOLVE = 252.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
 # DRAM bytes (read + write) per target of the LM kernel: ncu capture of the
 # 16,384-target learned-seed launch (4.626 MB), inputs read once (see profiles/).
 LM_DRAM_BYTES_PER_TARGET = 4625664 / 16384
 MLP_DRAM_BYTES_65536 = 4952832.0  # mlp_fused_kernel, dram__bytes_read.sum + write.sum per launch
-# FP32 operations per trajectory-iteration of the trajectory kernel (ncu count
-# over 64 trajectories x 50 iterations, see profiles/).
-TRAJ_FLOPS_PER_ITER = 1.355e6
+# Algorithmic FLOPs of the trajectory workload (T = 64, 32 obstacles + plane),
+# same census: per trajectory-iteration one candidate evaluation, one damped
+# block-banded solve and, at the oracle's accept rate, one normal-equation
+# build; per trajectory the initial evaluation and build.
+TRAJ_FLOPS_PER_ITER = 1.0631e6
+TRAJ_FLOPS_PER_INIT = 0.8959e6
 # Every timed step reads its own input batch; an arm rotates through enough
 # batches to hold at least this many bytes (twice the 129 MB L2).
 ROTATE_BYTES = 256 << 20
@@ -236,8 +243,9 @@ def measured_bf16_peak():
         return 1900.0, "fallback"
 
 
-def seednet_flops(n_in_pad, width, depth, n_out_pad, rows):
-    macs = n_in_pad * width + (depth - 1) * width * width + width * n_out_pad
+def seednet_flops(n_in, width, depth, n_out, rows):
+    """Multiply-adds x 2 of the seed network's layers, unpadded shapes."""
+    macs = n_in * width + (depth - 1) * width * width + width * n_out
     return 2.0 * rows * macs
 
 
@@ -456,7 +464,7 @@ def extra_workloads(torch, pk, synth, args, flush, stream):
     pk.pk_trace_enable(False)
     st = holder["r"][2].cpu().numpy()
     k_ms = t_ms / max(1, t_n)
-    t_tf = cfg["batch"] * cfg["iters"] * TRAJ_FLOPS_PER_ITER / (k_ms / 1e3) / 1e12
+    t_tf = cfg["batch"] * (cfg["iters"] * TRAJ_FLOPS_PER_ITER + TRAJ_FLOPS_PER_INIT) / (k_ms / 1e3) / 1e12
     out["trajopt"] = {"workload": cfg["name"], "value": cfg["batch"] * tsteps / (tms / 1e3), "unit": "trajectories/s",
                       "ms_per_step": tms / tsteps, "kernel_ms": k_ms,
                       "roofline": {"bound": "alu", "kernel": "trajopt_kernel<7, 2, false>", "achieved": t_tf,
@@ -789,7 +797,7 @@ def main():
     roofs = [lm_roofline(r)]
     if head == "learned":
         peak, src = measured_bf16_peak()
-        fl = seednet_flops(64, 512, 4, 64, ((B + 127) // 128) * 128)
+        fl = seednet_flops(9, 512, 4, 8 * 7, B)
         g_tf = fl / (r["gemm_ms"] / 1e3) / 1e12
         kname = ("mlp_fused_kernel (whole network, 1 launch per inference)" if r["fused_mlp"] else
                  f"gemm_bf16_tc_kernel ({r['gemm_launches']} launches per inference, aggregate)")

@@ -9,7 +9,8 @@ The arithmetic lives in plain C (``pk_oracle.c``, ``trajopt_oracle.c``,
 ``mlp_oracle.c``), compiled with gcc into ``oracle/_build/libpk_oracle.so``;
 this module is the ctypes marshalling around it.  Each C function cites the
 paper passage it follows (Sec. III-A solver, Sec. III-B variables, Sec. III-C
-costs and Eq. 1).
+costs and Eq. 1).  The same C sources compiled as C++ with a counting double
+(``flopcount.hpp``, ``flops_*.cpp``) give the FLOP census of ``census.py``.
 """
 from __future__ import annotations
 
@@ -24,8 +25,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libpk_oracle.so")
 _SOURCES = ["pk_oracle.c", "trajopt_oracle.c", "mlp_oracle.c"]
+# the same sources compiled as C++ with the counting double of flopcount.hpp
+_FLOPS_PATH = os.path.join(_BUILD, "libpk_oracle_flops.so")
+_FLOPS_SOURCES = ["flops_pk.cpp", "flops_traj.cpp"]
 _lock = threading.Lock()
 _lib = None
+_flib = None
 
 JOINT_FIXED, JOINT_REVOLUTE, JOINT_PRISMATIC = 0, 1, 2
 TARGET_POSE, TARGET_POSITION = 0, 1
@@ -44,7 +49,36 @@ def build(force: bool = False) -> str:
         "-lpthread", "-lm"]
     subprocess.run(cmd, check=True, cwd=_HERE)
     os.replace(tmp, _LIB_PATH)
+    try:
+        build_flops(force)
+    except (OSError, subprocess.CalledProcessError) as e:  # the census alone needs g++
+        print(f"oracle: FLOP census not built ({e})")
     return _LIB_PATH
+
+
+def build_flops(force: bool = False) -> str:
+    """Compile the FLOP census: the oracle's C sources again, as C++, with
+    every double replaced by the counting type of flopcount.hpp."""
+    deps = [os.path.join(_HERE, s) for s in _FLOPS_SOURCES + ["flopcount.hpp", "pk_oracle.h"] + _SOURCES[:2]]
+    newest = max(os.path.getmtime(s) for s in deps)
+    if not force and os.path.exists(_FLOPS_PATH) and os.path.getmtime(_FLOPS_PATH) >= newest:
+        return _FLOPS_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _FLOPS_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-std=c++17", "-O1", "-ffp-contract=off", "-fPIC", "-shared", "-Wl,-Bsymbolic",
+           "-Wno-class-memaccess", "-o", tmp] + [os.path.join(_HERE, s) for s in _FLOPS_SOURCES] + ["-lpthread"]
+    subprocess.run(cmd, check=True, cwd=_HERE)
+    os.replace(tmp, _FLOPS_PATH)
+    return _FLOPS_PATH
+
+
+def flops_lib():
+    global _flib
+    with _lock:
+        if _flib is None:
+            build_flops()
+            _flib = C.CDLL(_FLOPS_PATH)
+    return _flib
 
 
 _i32p = C.POINTER(C.c_int32)
@@ -325,6 +359,19 @@ def ik_beam(robot: Robot, params: IkParams, tg: Targets, targets, seeds, steps1=
     return dict(q=q, err=err, iters=iters, status=status, kept=kept, threads=int(threads))
 
 
+# ---------------------------------------------------------------- FLOP census
+def ik_flop_units(robot: Robot, params: IkParams, tg: Targets, targets, q, lam=1e-2):
+    """Algorithmic work of the three LM units at configuration q, counted on
+    the oracle's own arithmetic (flopcount.hpp): dict(eval, build, solve) of
+    (FLOPs, special-function calls)."""
+    targets = _f64(targets).reshape(tg.k, 12)
+    q = _f64(q)
+    out = np.zeros(6, np.int64)
+    flops_lib().orf_ik_units(C.byref(robot._c), C.byref(params._c), C.byref(tg._c), _p(targets), _p(q),
+                             C.c_double(lam), out.ctypes.data_as(C.POINTER(C.c_int64)))
+    return dict(eval=(int(out[0]), int(out[1])), build=(int(out[2]), int(out[3])), solve=(int(out[4]), int(out[5])))
+
+
 # ---------------------------------------------------------------- seed network
 def mlp_n_params(dims):
     return int(sum(dims[l + 1] * dims[l] + dims[l + 1] for l in range(len(dims) - 1)))
@@ -452,6 +499,18 @@ def traj_lm_run(robot, params, scene, x0, q_start, goal):
     f = lib().or_traj_lm_run(C.byref(robot._c), C.byref(params._c), C.byref(scene._c), T, _p(x),
                              _p(_f64(q_start)), _p(_f64(goal)), tr.ctypes.data_as(_f64p), _p(lt))
     return dict(x=x, cost=f, trace=tr, lam_trace=lt)
+
+
+def traj_flop_units(robot, params, scene, x, q_start, goal, lam=1e-2):
+    """Algorithmic work of one trajectory's LM units at x [T][n], counted on
+    the oracle's own arithmetic: dict(eval, build, solve) of (FLOPs, special
+    calls)."""
+    x = _f64(x)
+    out = np.zeros(6, np.int64)
+    flops_lib().orf_traj_units(C.byref(robot._c), C.byref(params._c), C.byref(scene._c), x.shape[0], _p(x),
+                               _p(_f64(q_start)), _p(_f64(goal)), C.c_double(lam),
+                               out.ctypes.data_as(C.POINTER(C.c_int64)))
+    return dict(eval=(int(out[0]), int(out[1])), build=(int(out[2]), int(out[3])), solve=(int(out[4]), int(out[5])))
 
 
 def traj_solve(robot, params, scene, x0, q_start, goals, n_trace=False, n_threads=0):

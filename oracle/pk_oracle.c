@@ -15,7 +15,9 @@
  * damping D = I, nu = 2, strict-decrease acceptance, rest pose = middle of the
  * limits) are the ones listed in the design notes.
  */
+#ifndef _GNU_SOURCE
 #define _GNU_SOURCE
+#endif
 #include "pk_oracle.h"
 
 #include <math.h>
@@ -525,6 +527,22 @@ int32_t or_cholesky_solve(int32_t n, const double* A, const double* b, double* x
 /* ------------------------------------------------------------------ */
 /* Levenberg-Marquardt on one (target, seed) problem (Sec. III-A)       */
 
+/* Gauss-Newton normal equations A = J^T J, g = J^T r of an m x nd Jacobian
+ * (row-major).  A is symmetric: its lower triangle is summed and mirrored. */
+void or_normal_equations(int32_t m, int32_t nd, const double* J, const double* r, double* A, double* g) {
+  for (int a = 0; a < nd; ++a) {
+    double s = 0;
+    for (int i = 0; i < m; ++i) s += J[i * nd + a] * r[i];
+    g[a] = s;
+    for (int b = 0; b <= a; ++b) {
+      double t = 0;
+      for (int i = 0; i < m; ++i) t += J[i * nd + a] * J[i * nd + b];
+      A[a * nd + b] = t;
+      A[b * nd + a] = t;
+    }
+  }
+}
+
 typedef struct {
   double cost, pos_err, rot_err, margin;
   int32_t iters, status;
@@ -562,34 +580,28 @@ static void lm_problem(const or_robot* rb, const or_ik_params* p, const or_targe
   res->margin = INFINITY;
   or_ik_residual(rb, p, ts, targets, q, r, NULL);
   double f = half_sq(r, m), pe, re;
-  int it = 0;
+  double lambda = lambda_init >= 0 ? lambda_init : p->lambda0;
+  int it = 0, conv = 0;
   if (!isfinite(f)) {
     res->cost = f; res->pos_err = NAN; res->rot_err = NAN;
     res->iters = 0; res->status = OR_P_NONFINITE;
     for (int t = 0; t < n_trace; ++t) {
       if (trace) memcpy(trace + t * nd, q, sizeof(double) * nd);
-      if (lam_trace) lam_trace[t] = lambda_init >= 0 ? lambda_init : p->lambda0;
+      if (lam_trace) lam_trace[t] = lambda;
     }
     goto done;
   }
   or_ik_errors(rb, ts, targets, q, &pe, &re);
-  double lambda = lambda_init >= 0 ? lambda_init : p->lambda0;
-  int conv = converged(p, pe, re);
+  conv = converged(p, pe, re);
   if (!(p->early_exit && conv)) {
     while (it < p->max_iters) {
       ++it;
       /* normal equations (J^T J + lambda I) dq = -J^T r */
       or_ik_residual(rb, p, ts, targets, q, r, J);
+      or_normal_equations(m, nd, J, r, A, g);
       for (int a = 0; a < nd; ++a) {
-        double s = 0;
-        for (int i = 0; i < m; ++i) s += J[i * nd + a] * r[i];
-        g[a] = s;
-        ng[a] = -s;
-        for (int b = 0; b < nd; ++b) {
-          double t = 0;
-          for (int i = 0; i < m; ++i) t += J[i * nd + a] * J[i * nd + b];
-          A[a * nd + b] = t + (a == b ? lambda : 0.0);
-        }
+        A[a * nd + a] += lambda;
+        ng[a] = -g[a];
       }
       int accepted = 0;
       if (or_cholesky_solve(nd, A, ng, dq) == 0) {

@@ -96,6 +96,10 @@ void or_ik_residual(const or_robot* rb, const or_ik_params* p, const or_target_s
 void or_ik_errors(const or_robot* rb, const or_target_spec* ts, const double* targets,
                   const double* q, double* pos_err, double* rot_err);
 
+/* Gauss-Newton normal equations A = J^T J [nd][nd], g = J^T r [nd] of the
+ * m x nd row-major Jacobian J. */
+void or_normal_equations(int32_t m, int32_t nd, const double* J, const double* r, double* A, double* g);
+
 /* Cholesky solve of the SPD system A x = b (n x n row-major). Returns 0 on success. */
 int32_t or_cholesky_solve(int32_t n, const double* A, const double* b, double* x);
 

@@ -220,9 +220,10 @@ void or_traj_residual_sparse(const or_robot* rb, const or_traj_params* p, const 
   /* velocity-limit hinge per (t >= 1, joint): w_vlimit max(0, |q_t - q_{t-1}| - v_max) */
   for (int t = 1; t < T; ++t)
     for (int i = 0; i < n; ++i, ++row) {
+      if (!(p->w_vlimit > 0)) { r[row] = 0; continue; } /* hinge off */
       const double v = x[t * n + i] - x[(t - 1) * n + i];
       const double h = fabs(v) - p->v_max;
-      if (h > 0 && p->w_vlimit > 0) {
+      if (h > 0) {
         const double sg = v > 0 ? 1.0 : -1.0;
         r[row] = p->w_vlimit * h;
         SETJ(row, t * n + i, p->w_vlimit * sg);
@@ -236,7 +237,11 @@ void or_traj_residual_sparse(const or_robot* rb, const or_traj_params* p, const 
    * axis point closest to the obstacle centre o (parameter u in [0, 1]);
    * dd/dc(t) = (1 - u) n and dd/dc(t+1) = u n, n = (p - o) / |p - o| */
   double* Tf2 = (double*)malloc(sizeof(double) * 12 * nj);
-  for (int t = 0; t + 1 < T; ++t) {
+  if (!(p->w_swept > 0)) {
+    /* swept rows off: every row is w_swept * f = 0 */
+    for (int i = 0; i < (T - 1) * n * sc->S * sc->n_obs; ++i, ++row) r[row] = 0;
+  }
+  for (int t = 0; t + 1 < T && p->w_swept > 0; ++t) {
     or_fk(rb, x + (size_t)t * n, Tf);
     or_fk(rb, x + (size_t)(t + 1) * n, Tf2);
     for (int l = 0; l < n; ++l) {
@@ -306,6 +311,7 @@ void or_traj_residual_sparse(const or_robot* rb, const or_traj_params* p, const 
       const double w = kind ? p->w_jerk : p->w_acc5;
       for (int t = 2; t + 2 < T; ++t)
         for (int i = 0; i < n; ++i, ++row) {
+          if (w == 0.0) { r[row] = 0; continue; } /* stencil off */
           double v = 0;
           for (int k = 0; k < 5; ++k) v += c[k] * x[(t - 2 + k) * n + i];
           r[row] = w * v;
@@ -348,7 +354,8 @@ static double traj_normal(const or_robot* rb, const or_traj_params* p, const or_
   double f = 0;
   for (int i = 0; i < m; ++i) f += r[i] * r[i];
   if (A) {
-    /* J^T J and J^T r, one row's outer product at a time */
+    /* J^T J and J^T r, one row's outer product at a time; J^T J is
+     * symmetric, so its lower triangle is summed and mirrored at the end */
     memset(A, 0, sizeof(double) * (size_t)N * N);
     memset(g, 0, sizeof(double) * N);
     for (int i = 0; i < m; ++i) {
@@ -356,9 +363,12 @@ static double traj_normal(const or_robot* rb, const or_traj_params* p, const or_
       const double* v = Jv + (size_t)i * KW;
       for (int u = 0; u < KW && c[u] >= 0; ++u) {
         g[c[u]] += v[u] * r[i];
-        for (int w = 0; w < KW && c[w] >= 0; ++w) A[(size_t)c[u] * N + c[w]] += v[u] * v[w];
+        for (int w = 0; w < KW && c[w] >= 0; ++w)
+          if (c[w] <= c[u]) A[(size_t)c[u] * N + c[w]] += v[u] * v[w];
       }
     }
+    for (int a = 0; a < N; ++a)
+      for (int b = 0; b < a; ++b) A[(size_t)b * N + a] = A[(size_t)a * N + b];
     free(Jc);
     free(Jv);
   }
@@ -430,6 +440,25 @@ static void chol_solve(int N, const double* L, const double* b, double* x) {
   free(y);
 }
 
+/* The same substitutions with a block-banded factor (blocks of n, B block
+ * sub-diagonals): only the band of L enters the sums. */
+static void chol_solve_band(int N, int n, int B, const double* L, const double* b, double* x) {
+  double* y = (double*)malloc(sizeof(double) * N);
+  for (int i = 0; i < N; ++i) {
+    const int k0 = (i / n >= B ? i / n - B : 0) * n;
+    double s = b[i];
+    for (int k = k0; k < i; ++k) s -= L[(size_t)i * N + k] * y[k];
+    y[i] = s / L[(size_t)i * N + i];
+  }
+  for (int i = N - 1; i >= 0; --i) {
+    const int k1 = (i / n + B + 1) * n < N ? (i / n + B + 1) * n : N;
+    double s = y[i];
+    for (int k = i + 1; k < k1; ++k) s -= L[(size_t)k * N + i] * x[k];
+    x[i] = s / L[(size_t)i * N + i];
+  }
+  free(y);
+}
+
 /* Exported for the pins: normal matrix, gradient and cost at x. */
 double or_traj_normal(const or_robot* rb, const or_traj_params* p, const or_traj_scene* sc, int32_t T,
                       const double* x, const double* qs, const double* goal, double* A, double* g) {
@@ -462,7 +491,10 @@ static double traj_lm(const or_robot* rb, const or_traj_params* p, const or_traj
     const int rc = p->banded ? or_banded_cholesky_b(T, n, band, Al, L) : dense_cholesky(N, Al, L);
     int accepted = 0;
     if (rc == 0) {
-      chol_solve(N, L, ng, dx);
+      if (p->banded)
+        chol_solve_band(N, n, band, L, ng, dx);
+      else
+        chol_solve(N, L, ng, dx);
       for (int i = 0; i < N; ++i) xt[i] = x[i] + dx[i];
       const double ft = traj_normal(rb, p, sc, T, xt, qs, goal, NULL, NULL);
       if (margin && it < 5 && f > 0 && fabs(ft - f) / f < *margin) *margin = fabs(ft - f) / f;
