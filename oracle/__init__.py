@@ -387,6 +387,27 @@ def mlp_forward(dims, params, x):
     return y
 
 
+def round_bf16(x):
+    """x rounded to BF16 (8 significant bits, ties to even), as float64."""
+    x = _f64(x)
+    y = np.empty_like(x)
+    lib().or_round_bf16(C.c_int64(x.size), _p(x), _p(y))
+    return y
+
+
+def mlp_forward_bf16(dims, params, x):
+    """Pre-head outputs [M][dims[-1]] at the network's own precision (BF16
+    operands into every layer: hidden SiLU outputs rounded to BF16; FP64 sums)
+    and the output layer's magnitude scale sum |W||a| + |b| [M][dims[-1]]."""
+    dims_a = _i32(dims)
+    params = _f64(params)
+    x = _f64(x).reshape(-1, dims[0])
+    y = np.empty((x.shape[0], dims[-1]))
+    sc = np.empty((x.shape[0], dims[-1]))
+    lib().or_mlp_forward_bf16(len(dims) - 1, _p(dims_a), _p(params), x.shape[0], _p(x), _p(y), _p(sc))
+    return y, sc
+
+
 def mlp_loss_grad(dims, params, x, q_star, K, lo, hi, mu=0.01):
     """(mean loss, gradient [n_params], proposals [M][K][n]) of the min-over-K loss."""
     dims_a = _i32(dims)

@@ -63,6 +63,60 @@ int32_t or_mlp_forward(int32_t n_layers, const int32_t* dims, const double* para
   return 0;
 }
 
+/* x rounded to BF16 (8 significant bits, round to nearest, ties to even):
+ * x = m 2^e with 1/2 <= |m| < 1, and m 2^8 rounded to an integer. */
+static double round_bf16(double x) {
+  if (x == 0.0 || !isfinite(x)) return x;
+  int e;
+  const double m = frexp(x, &e);
+  return ldexp(nearbyint(ldexp(m, 8)), e - 8);
+}
+
+/* Exported for the pins. */
+void or_round_bf16(int64_t n, const double* x, double* y) {
+  for (int64_t i = 0; i < n; ++i) y[i] = round_bf16(x[i]);
+}
+
+/* The forward pass at the precision the seed network runs in: every layer's
+ * operands are BF16 (the weights and the inputs are given BF16-rounded; each
+ * hidden layer's SiLU output is rounded to BF16 before it enters the next
+ * layer), sums and SiLU in FP64.  y_out [M][d_L] pre-head outputs; scale_out
+ * (optional) [M][d_L]: sum_i |W_oi| |a_i| + |b_o| of the output layer, the
+ * magnitude that rounding differences in its inputs are relative to. */
+int32_t or_mlp_forward_bf16(int32_t n_layers, const int32_t* dims, const double* params, int32_t M,
+                            const double* x, double* y_out, double* scale_out) {
+  int maxd = 0;
+  for (int l = 0; l <= n_layers; ++l)
+    if (dims[l] > maxd) maxd = dims[l];
+  double* a = (double*)malloc(sizeof(double) * maxd);
+  double* z = (double*)malloc(sizeof(double) * maxd);
+  for (int m = 0; m < M; ++m) {
+    memcpy(a, x + (long)m * dims[0], sizeof(double) * dims[0]);
+    const double* P = params;
+    for (int l = 0; l < n_layers; ++l) {
+      const int di = dims[l], dout = dims[l + 1];
+      const double* W = P;
+      const double* b = P + (long)dout * di;
+      const int last = l + 1 == n_layers;
+      for (int o = 0; o < dout; ++o) {
+        double s = b[o], mag = fabs(b[o]);
+        for (int i = 0; i < di; ++i) {
+          s += W[(long)o * di + i] * a[i];
+          mag += fabs(W[(long)o * di + i]) * fabs(a[i]);
+        }
+        z[o] = s;
+        if (last && scale_out) scale_out[(long)m * dout + o] = mag;
+      }
+      P += (long)dout * di + dout;
+      for (int o = 0; o < dout; ++o) a[o] = last ? z[o] : round_bf16(silu(z[o]));
+    }
+    memcpy(y_out + (long)m * dims[n_layers], a, sizeof(double) * dims[n_layers]);
+  }
+  free(a);
+  free(z);
+  return 0;
+}
+
 /*
  * Loss and gradient over M samples.  The last layer has K * n outputs; the
  * head maps output (k, i) to q = mid_i + half_i tanh(y), mid/half from the

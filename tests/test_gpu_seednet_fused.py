@@ -158,3 +158,63 @@ def test_shapes_outside_the_fused_kernel_use_the_gemms():
         assert a.shape == (300, K, o.n_dof)
         np.testing.assert_array_equal(a, b)
         pk.pk_seednet_check(net)
+
+
+def seed_violations(q, y_ref, scale, lo, hi, c=2.0 ** -7):
+    """Elements of seeds q [R][K][n] outside their per-element bound around the
+    oracle's forward pass at the network's precision (y_ref, scale: pre-head
+    outputs and the output layer's sum |W||a| + |b|, both [R][K][n]).
+
+    Both sides round every hidden activation to BF16 and sum its inputs
+    exactly enough (FP32 accumulation here, FP64 there) for the sums to agree
+    to ~1e-7; the GPU's SiLU runs through the hardware tanh approximation
+    (relative error ~2^-11), so an activation near a rounding boundary can
+    land one BF16 ulp (at most 2^-7 of its value) away from the oracle's.
+    Such flips in the last hidden layer move output o by at most 2^-7
+    sum_i |W_oi||a_i| <= 2^-7 scale_o; earlier flips reach the output damped
+    by the same sums, so |y - y_ref| <= 2^-7 scale is the pre-head bound.
+    The head q = mid + half tanh(y) maps it through tanh's slope on the
+    interval, plus FP32 rounding of the head."""
+    half, mid = (hi - lo) / 2, (lo + hi) / 2
+    tol_y = c * scale + 1e-6
+    slope = 1.0 / np.cosh(np.maximum(np.abs(y_ref) - tol_y, 0.0)) ** 2
+    tol_q = half * slope * tol_y + 4e-6 * half + 1e-6
+    return np.abs(q - (mid + half * np.tanh(y_ref))) > tol_q
+
+
+@pytest.mark.parametrize("robot,B", [("chain7", 1), ("chain7", 300), ("chain7", 65536), ("hand24", 300),
+                                     ("humanoid30", 300)])
+def test_fused_seeds_elementwise_against_oracle(robot, B):
+    """Every seed of the fused kernel, element by element, against the FP64
+    oracle at the network's precision: the 7-DoF, hand and humanoid heads, a
+    single target, a ragged batch and the benchmark's 65,536-target launch
+    (there on the first and last 128-row tiles and 1,792 random rows).  A
+    swapped pair of output columns, or seeds shifted by one row, fails the
+    same bound."""
+    K, width, depth = 8, 512, 4
+    net, o, dims, params, T = make(robot, K, width, depth, B)
+    n = o.n_dof
+    q = infer(net, T, True).astype(np.float64)
+    if B <= 4096:
+        rows = np.arange(B)
+    else:
+        rng = np.random.default_rng(5)
+        rows = np.unique(np.concatenate([np.arange(128), np.arange(B - 128, B), rng.choice(B, 1792, replace=False)]))
+    y, scale = oracle.mlp_forward_bf16(dims, params, bf16(features(T[rows])))
+    y = y[:, :K * n].reshape(-1, K, n)
+    scale = scale[:, :K * n].reshape(-1, K, n)
+    lo, hi = o.dof_lower, o.dof_upper
+    qr = q[rows]
+    bad = seed_violations(qr, y, scale, lo, hi)
+    worst = np.abs(qr - ((lo + hi) / 2 + (hi - lo) / 2 * np.tanh(y))).max()
+    print(f"{robot} B={B}: {bad.sum()} of {bad.size} outside the bound, max |dq| {worst:.2e}")
+    assert not bad.any()
+    # sensitivity: two swapped output columns are caught in most rows (seeds
+    # saturated at a joint limit can coincide), a row holding another
+    # target's seeds is caught in every row
+    qs = qr.copy()
+    qs[:, 0, [0, 1]] = qs[:, 0, [1, 0]]
+    assert seed_violations(qs, y, scale, lo, hi)[:, 0, :2].any(axis=1).mean() >= 0.5
+    if len(rows) > 1:
+        shifted = seed_violations(np.roll(qr, 1, axis=0), y, scale, lo, hi)
+        assert shifted.reshape(len(rows), -1).any(axis=1).all()

@@ -91,3 +91,38 @@ def test_adamw_matches_torch():
         tparam.grad = torch.tensor(g)
         opt.step()
     np.testing.assert_allclose(p, tparam.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_round_bf16_matches_torch_bfloat16():
+    """BF16 rounding (8 significant bits, ties to even) against PyTorch's
+    bfloat16 cast, on float32 values (the cast rounds from float32) including
+    exact ties."""
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(20000).astype(np.float32).astype(np.float64) * 10.0 ** rng.integers(-6, 6, 20000)
+    x = x.astype(np.float32).astype(np.float64)
+    ties = np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8, -(1 + 2 ** -8), 2 ** -3 * (1 + 5 * 2 ** -8), 0.0, -0.0])
+    for v in (x, ties):
+        ref = torch.tensor(v, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+        np.testing.assert_array_equal(oracle.round_bf16(v), ref)
+    np.testing.assert_array_equal(oracle.round_bf16(ties[:4]), [1.0, 1 + 2 ** -6, -1.0, 2 ** -3 * (1 + 4 * 2 ** -8)])
+
+
+def test_forward_bf16_matches_torch_with_bf16_activations():
+    """The forward pass at the network's precision: the same layers with every
+    hidden SiLU output cast to bfloat16 by PyTorch, and the output layer's
+    magnitude scale sum |W||a| + |b|."""
+    params, x, q_star, lo, hi = _setup(seed=4)
+    y, scale = oracle.mlp_forward_bf16(DIMS, params, x)
+    tp = _torch_model(params)
+    a = torch.tensor(x)
+    L = len(DIMS) - 1
+    for l in range(L):
+        z = torch.nn.functional.linear(a, tp[2 * l], tp[2 * l + 1])
+        if l + 1 < L:
+            a = torch.nn.functional.silu(z).to(torch.float32).to(torch.bfloat16).to(torch.float64)
+        else:
+            mag = torch.nn.functional.linear(a.abs(), tp[2 * l].abs(), tp[2 * l + 1].abs())
+            a = z
+    np.testing.assert_allclose(y, a.detach().numpy(), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(scale, mag.detach().numpy(), rtol=1e-12)
+    assert np.abs(y - oracle.mlp_forward(DIMS, params, x)).max() > 0  # the rounding does act
