@@ -211,9 +211,14 @@ pk_status pk_ik_solve(const pk_robot* robot, const pk_ik_params* params, int32_t
  *   exits); a (batch, n_seeds) whose pk_ik_workspace_bytes() exceeds it is
  *   rejected with PK_ERR_INVALID_ARG and nothing is enqueued (about 690,000
  *   seeds in total for a 7-DoF chain).
- *   No cudaMalloc, cudaFree or other allocating call is made.  The first call
- *   on each device looks up the array's device address (set-up), so make that
- *   first call before any stream capture.
+ *   No cudaMalloc, cudaFree or other allocating call is made.  The argument
+ *   checks of pk_ik_solve run first (a bad argument is reported as such, and
+ *   batch == 0 returns PK_OK before anything else); the size limit comes
+ *   next.  Every call outside stream capture looks up the array's device
+ *   address on the current device (set-up; a lookup allocates nothing and
+ *   stays valid after a device or context reset); a call made while `stream`
+ *   is being captured uses the address of the last call outside capture, so
+ *   make the first call on each device before any stream capture.
  *   All calls on a device share the one array, and it keeps the last call's
  *   contents; each call clears what must start at zero.  Calls that can
  *   overlap on the GPU (different streams, or threads) race on the array and

@@ -22,6 +22,33 @@ static __device__ __align__(256) unsigned char g_ik_scratch[kNoallocScratchBytes
 std::mutex g_setup_mu;
 void* g_scratch_ptr[pk::kMaxDevices] = {};
 
+// Device address of g_ik_scratch on the current device.  The host-side name
+// is only a stand-in, so the address is looked up with the device current:
+// on every call outside stream capture (the lookup allocates nothing, and a
+// fresh lookup stays valid after a device or context reset), and from the
+// copy kept by the last such call while `st` is being captured.
+pk_status scratch_address(cudaStream_t st, void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return pk::set_error(PK_ERR_CUDA, cudaGetErrorString(e));
+  if (dev < 0 || dev >= pk::kMaxDevices)
+    return pk::set_error(PK_ERR_UNSUPPORTED, "device ordinal beyond the supported range");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const bool capturing = cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+  std::lock_guard<std::mutex> lk(g_setup_mu);
+  if (!capturing) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_ik_scratch);
+    if (e != cudaSuccess) return pk::set_error(PK_ERR_CUDA, cudaGetErrorString(e));
+    g_scratch_ptr[dev] = p;
+  } else if (!g_scratch_ptr[dev]) {
+    return pk::set_error(PK_ERR_INVALID_ARG,
+                         "pk_ik_solve_noalloc: the first call on a device must come before any stream capture");
+  }
+  *out = g_scratch_ptr[dev];
+  return PK_OK;
+}
+
 }  // namespace
 
 extern "C" pk_status pk_ik_solve_noalloc(const pk_robot* robot, const pk_ik_params* params,
@@ -31,9 +58,12 @@ extern "C" pk_status pk_ik_solve_noalloc(const pk_robot* robot, const pk_ik_para
                                          const float* d_seeds, float* d_q_out, float* d_err_out,
                                          int32_t* d_iters_out, int32_t* d_status_out,
                                          void* stream) {
-  if (!robot) return pk::set_error(PK_ERR_INVALID_ARG, "robot is NULL");
-  if (batch < 0 || n_seeds < 1)
-    return pk::set_error(PK_ERR_INVALID_ARG, "batch must be >= 0 and n_seeds >= 1");
+  // the argument checks of pk_ik_solve first, so that a bad argument is
+  // reported as such; an empty batch returns before any set-up
+  bool empty = false;
+  pk_status s = pk::ik_check_args(robot, params, k, target_links, target_kinds, batch, n_seeds, d_targets, d_seeds,
+                                  d_q_out, d_err_out, d_iters_out, d_status_out, &empty);
+  if (s != PK_OK || empty) return s;
   const size_t need = pk_ik_workspace_bytes(robot, batch, n_seeds);
   if (need > kNoallocScratchBytes) {
     char msg[256];
@@ -43,26 +73,10 @@ extern "C" pk_status pk_ik_solve_noalloc(const pk_robot* robot, const pk_ik_para
              batch, n_seeds, need, kNoallocScratchBytes);
     return pk::set_error(PK_ERR_INVALID_ARG, msg);
   }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return pk::set_error(PK_ERR_CUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= pk::kMaxDevices)
-    return pk::set_error(PK_ERR_UNSUPPORTED, "device ordinal beyond the supported range");
   void* ptr = nullptr;
-  {
-    // One-time set-up per device, with that device current: the host-side
-    // name g_ik_scratch is only a stand-in, so its device address is looked up.
-    std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_ptr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_ik_scratch);
-      if (e != cudaSuccess) return pk::set_error(PK_ERR_CUDA, cudaGetErrorString(e));
-      g_scratch_ptr[dev] = p;
-    }
-    ptr = g_scratch_ptr[dev];
-  }
-  // pk_ik_solve zeroes the queue head, counters and flags in the scratch
-  // before its kernel runs; the result records are fully rewritten.
+  if ((s = scratch_address((cudaStream_t)stream, &ptr)) != PK_OK) return s;
+  // pk_ik_solve zeroes the queue head, counters and cancellation flags in the
+  // scratch before its kernel runs; the result records are fully rewritten.
   return pk_ik_solve(robot, params, k, target_links, target_kinds, batch, n_seeds, d_targets,
                      d_seeds, d_q_out, d_err_out, d_iters_out, d_status_out, ptr,
                      kNoallocScratchBytes, stream);

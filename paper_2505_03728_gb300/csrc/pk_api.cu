@@ -669,6 +669,23 @@ static pk_status ik_prepare(const pk_robot* rb, const pk_ik_params* params, int3
   return PK_OK;
 }
 
+}  // extern "C"
+
+namespace pk {
+pk_status ik_check_args(const pk_robot* rb, const pk_ik_params* params, int32_t k, const int32_t* target_links,
+                        const int32_t* target_kinds, int32_t batch, int32_t n_seeds, const float* d_targets,
+                        const float* d_seeds, float* d_q_out, float* d_err_out, int32_t* d_iters_out,
+                        int32_t* d_status_out, bool* empty) {
+  bool chain = false, pos_only = false;
+  pk::ChainHost ch;
+  pk::TreeInfo ti;
+  return ik_prepare(rb, params, k, target_links, target_kinds, batch, n_seeds, d_targets, d_seeds, d_q_out,
+                    d_err_out, d_iters_out, d_status_out, &chain, &ch, &ti, &pos_only, empty);
+}
+}  // namespace pk
+
+extern "C" {
+
 pk_status pk_ik_solve(const pk_robot* rb, const pk_ik_params* params, int32_t k,
                       const int32_t* target_links, const int32_t* target_kinds, int32_t batch,
                       int32_t n_seeds, const float* d_targets, const float* d_seeds,

@@ -204,6 +204,13 @@ bool fold_chain_quiet(const pk_robot* rb, int link, ChainHost* ch);
 // Records a thread-local error message (pk_last_error) and returns s.
 pk_status set_error(pk_status s, const char* msg);
 
+// The argument checks of pk_ik_solve (everything but the workspace); *empty
+// is set when batch == 0 (nothing to do).
+pk_status ik_check_args(const pk_robot* rb, const pk_ik_params* params, int32_t k, const int32_t* target_links,
+                        const int32_t* target_kinds, int32_t batch, int32_t n_seeds, const float* d_targets,
+                        const float* d_seeds, float* d_q_out, float* d_err_out, int32_t* d_iters_out,
+                        int32_t* d_status_out, bool* empty);
+
 // Kernel timing trace (pk_api.cu): brackets a launch with events when enabled.
 struct TraceScope {
   TraceScope(const char* name, cudaStream_t s);

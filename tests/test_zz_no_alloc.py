@@ -64,3 +64,62 @@ def test_noalloc_rejects_batches_beyond_the_static_scratch():
         pk.pk_ik_solve_noalloc(g, p, [ee], None, t, s)
     assert e.value.status == pk.PK_ERR_INVALID_ARG
     assert "static scratch" in pk.pk_last_error()
+
+
+def _tree_inputs(batch, seed_offset=0):
+    spec, tips = synth.hand_robot(102)
+    g = pk.Robot.from_spec(spec)
+    qt = synth.uniform_q(640 + seed_offset, batch, spec.dof_lower, spec.dof_upper)
+    sd = synth.uniform_q(650 + seed_offset, (batch, 4), spec.dof_lower, spec.dof_upper)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    targets = pk.pk_fk(g, dev(qt))[:, list(tips)].contiguous()
+    kinds = [pk.PK_TARGET_POSITION] * len(tips)
+    return g, list(tips), kinds, targets, dev(sd)
+
+
+def test_noalloc_tree_robot_twice():
+    """The warp-per-problem tree kernel (24-DoF hand, five fingertip position
+    targets) has a larger per-seed record than the chain kernel; two calls in
+    a row through the shared array equal pk_ik_solve with a caller workspace."""
+    p = pk.pk_ik_params_default(max_iters=30, early_exit=1, cancel_siblings=0)
+    for batch, off in ((700, 0), (333, 3)):
+        g, tips, kinds, targets, seeds = _tree_inputs(batch, off)
+        ws = torch.empty(pk.pk_ik_workspace_bytes(g, batch, 4), dtype=torch.uint8, device="cuda")
+        ref = pk.pk_ik_solve(g, p, tips, kinds, targets, seeds, ws)
+        got = pk.pk_ik_solve_noalloc(g, p, tips, kinds, targets, seeds)
+        torch.cuda.synchronize()
+        _compare(ref, got)
+
+
+def test_noalloc_sibling_cancellation_flags_start_clear():
+    """With sibling cancellation the per-target flags live in the shared
+    array: a flag left set by the previous call would stop that target's
+    seeds.  A target is solved iff one of its seeds converges, whichever
+    seeds were cancelled, so the solved set of each call must equal
+    pk_ik_solve's, and every converged answer must meet the tolerances."""
+    p = pk.pk_ik_params_default(max_iters=50, early_exit=1, cancel_siblings=1)
+    for batch, off in ((3000, 11), (3000, 12)):
+        g, ee, targets, seeds = _inputs(batch, off)
+        ws = torch.empty(pk.pk_ik_workspace_bytes(g, batch, 8), dtype=torch.uint8, device="cuda")
+        ref = pk.pk_ik_solve(g, p, [ee], None, targets, seeds, ws)
+        got = pk.pk_ik_solve_noalloc(g, p, [ee], None, targets, seeds)
+        torch.cuda.synchronize()
+        s_ref, s_got = ref[3].cpu().numpy(), got[3].cpu().numpy()
+        np.testing.assert_array_equal(s_got == pk.PK_P_CONVERGED, s_ref == pk.PK_P_CONVERGED)
+        err = got[1].cpu().numpy()[s_got == pk.PK_P_CONVERGED]
+        assert np.all(err[:, 0] <= p.tol_pos) and np.all(err[:, 1] <= p.tol_rot)
+
+
+def test_noalloc_empty_batch_and_argument_errors_come_first():
+    g, ee, targets, seeds = _inputs(8)
+    p = pk.pk_ik_params_default()
+    t0, s0 = torch.zeros(0, 1, 12, device="cuda"), torch.zeros(0, 8, 7, device="cuda")
+    q, err, iters, status = pk.pk_ik_solve_noalloc(g, p, [ee], None, t0, s0)
+    assert q.shape == (0, 7)
+    # an unsupported target frame beside an oversized batch reports the target
+    big = 200_000
+    t = torch.zeros(big, 1, 12, device="cuda")
+    s = torch.zeros(big, 8, 7, device="cuda")
+    with pytest.raises(pk.PkError):
+        pk.pk_ik_solve_noalloc(g, p, [g.n_joints + 5], None, t, s)
+    assert "static scratch" not in pk.pk_last_error()
