@@ -1,19 +1,29 @@
 """GPU trajectory optimisation (block-banded LM) against the FP64 oracle.
 
-Tolerances: normal-equation blocks and gradient within 1e-4 relative to the
-largest entry of each trajectory; one LM step from the same trajectory within
-5e-3 * max(1, |q|) with a median over trajectories below 1e-4, and LM iterates
-1 to 3 within 5e-3 for at least 90% of the trajectories with a median below
-1e-4 (first iterate) or 1e-3 (iterates 2, 3) (near-ties in the accept test
-excluded).  The bound follows from the conditioning of the
-smoothness-dominated banded system: with lambda at 1e-2 .. 5e-3 its condition
-number is ~1e3 to 3e3 (more where collision rows add curvature), and an FP32
-factorisation loses about cond * 6e-8 of relative accuracy per step, most of
-it along the slowest smoothness modes; trajectories without active collisions
-agree to ~1e-7.  After the full solve the
-oracle's FP64 cost at the GPU's trajectory agrees with the GPU's own cost to
-1e-3, and the distribution of final costs and collision-free trajectories
-matches the oracle's."""
+The damped normal matrices of this workload have condition numbers of 1e6 -
+3e6: the start and goal rows (weight 100) put entries of ~1e4 into the first
+and last diagonal blocks, the smoothness rows (weight 1) and lambda ~1e-2 set
+the soft directions.  Merely holding M = J^T J + lambda I and g in FP32 moves
+the exact step by 3e-5 .. 6e-4 of max(1, |q|), so no FP32 solver, iterative
+refinement included, can match an FP64 step to 1e-4 on every trajectory.
+The parity bar is therefore per trajectory and per step, from the
+arithmetic: the first-order componentwise perturbation bound of the solution
+of M d = -g when every entry of M and g carries a relative error u = 2^-24,
+
+    s = u max_i (|M^-1| (|A| |d| + |g|))_i / max(1, |q_i|),
+
+computed from the oracle's FP64 normal equations at the step's start; every
+trajectory without an accept/reject near-tie (|f_trial - f| <= 1e-5 f) must
+agree within 2 s (measured: at most 0.8 s), one step at a time from the
+oracle's own iterates and damping (iterates 1 to 5) and over free runs of 1
+to 5 iterations (within 2 sum_k s_k).  Two kinds of step are decided by
+rounding and excluded (and counted), because both results are correct: an
+accept/reject near-tie, and a start with a joint within 1e-6 rad of a limit,
+where the limit hinge's derivative jumps from 0 to w_limit and FP32 rounding
+of q decides which side the step sees.  Where 2 s <= 1e-4 this is the 1e-4
+bar itself.  Normal-equation blocks and gradient agree within 1e-4 of the
+largest entry; after the full solve the oracle's FP64 cost at the GPU's
+trajectory agrees with the GPU's own cost to 1e-3."""
 import numpy as np
 import pytest
 import torch
@@ -52,6 +62,28 @@ def setup(B, T=64, perturb=0.0, seed=0):
     return o, g, qs, goals, x0, radii, obs, plane, scene
 
 
+U32 = 2.0 ** -24
+
+
+def step_sensitivity(o, op, scene, x, qs, goal, lam):
+    """First-order componentwise bound of the damped LM step's FP32 error,
+    relative to max(1, |q|) (see the module docstring)."""
+    f, A, gr = oracle.traj_normal(o, op, scene, x, qs, goal)
+    M = A + lam * np.eye(len(A))
+    d = np.linalg.solve(M, -gr)
+    s = U32 * np.abs(np.linalg.inv(M)) @ (np.abs(A) @ np.abs(d) + np.abs(gr))
+    return float(np.max(s / np.maximum(1.0, np.abs(np.asarray(x).ravel()))))
+
+
+HINGE_KINK = 1e-6  # rad: a joint this close to a limit may round onto the other side in FP32
+
+
+def hinge_kink(o, x):
+    """True when a joint of trajectory x [T][n] lies within HINGE_KINK of a limit."""
+    x = np.asarray(x)
+    return bool(np.min(np.minimum(np.abs(x - o.dof_lower), np.abs(x - o.dof_upper))) <= HINGE_KINK)
+
+
 def oparams(p, banded=1):
     return oracle.TrajParams(p.w_start, p.w_goal_pos, p.w_goal_rot, p.w_vel, p.w_acc, p.w_limit, p.w_coll,
                              p.eta, p.lambda0, p.lambda_min, p.lambda_max, p.nu, p.iters, banded,
@@ -83,19 +115,24 @@ def test_normal_equations_match_oracle(T):
 
 def test_one_step_from_several_points_matches_oracle():
     """One LM step (lambda0) from the initial trajectories and from the oracle's
-    own iterates 5 and 20: the step alone, without accumulated history."""
+    own iterates 5 and 20: the step alone, without accumulated history, within
+    twice its FP32 sensitivity bound on every trajectory."""
     o, g, qs, goals, x0, radii, obs, plane, scene = setup(16, 64)
+    p1 = pk.pk_trajopt_params_default(iters=1)
+    op1 = oparams(p1)
     trace = oracle.traj_solve(o, oparams(pk.pk_trajopt_params_default(iters=20)), scene, x0, qs, goals,
                               n_trace=True)["trace"]
     for start in (x0, trace[:, 4], trace[:, 19]):
-        ref = oracle.traj_solve(o, oparams(pk.pk_trajopt_params_default(iters=1)), scene, start, qs, goals,
-                                n_trace=True)
-        q = pk.pk_trajopt_solve(g, pk.pk_trajopt_params_default(iters=1), dev(qs), dev(goals), dev(start),
-                                dev(radii), dev(obs), plane)[0].cpu().numpy()
+        ref = oracle.traj_solve(o, op1, scene, start, qs, goals, n_trace=True)
+        q = pk.pk_trajopt_solve(g, p1, dev(qs), dev(goals), dev(start), dev(radii), dev(obs), plane)[0].cpu().numpy()
         tie = ref["margin"] <= 1e-5
+        kink = np.array([hinge_kink(o, start[b]) for b in range(16)])
         rel = (np.abs(q - ref["x"]) / np.maximum(1.0, np.abs(ref["x"]))).reshape(16, -1).max(axis=1)
-        assert np.all(rel[~tie] <= 5e-3), rel
-        assert np.median(rel[~tie]) <= 1e-4, rel
+        for b in np.nonzero(~tie & ~kink)[0]:
+            sb = step_sensitivity(o, op1, scene, start[b], qs[b], goals[b], p1.lambda0)
+            assert rel[b] <= 2 * sb + 1e-6, (b, rel[b], sb)
+        # near a stationary point (the start at iterate 20) cost changes are small
+        assert (tie | kink).sum() <= 4
 
 
 FIVE = dict(w_acc5=2.0, w_jerk=3.0)
@@ -115,15 +152,14 @@ def test_one_step_short_horizons_match_oracle(T, ext):
     q = pk.pk_trajopt_solve(g, p, dev(qs), dev(goals), dev(x0), dev(radii), dev(obs), plane)[0].cpu().numpy()
     tie = ref["margin"] <= 1e-5
     rel = (np.abs(q - ref["x"]) / np.maximum(1.0, np.abs(ref["x"]))).reshape(8, -1).max(axis=1)
-    # these short, perturbed systems have condition numbers of 1e5 - 3e5, so
-    # the FP32 step may differ from the FP64 one by several 1e-3 (measured:
-    # up to 5.3e-3); the backward error below is the sharp check
-    assert np.all(rel[~tie] <= 2e-2), rel
-    assert np.median(rel[~tie]) <= 5e-3, rel
-    # whatever the conditioning, an accepted GPU step solves the oracle's
-    # damped normal equations to FP32 accuracy (backward error); a wrong block
-    # in the factorisation or the substitutions leaves an O(1) residual
     op = oparams(p)
+    # every step within twice its FP32 sensitivity bound
+    for b in np.nonzero(~tie)[0]:
+        sb = step_sensitivity(o, op, scene, x0[b], qs[b], goals[b], p.lambda0)
+        assert rel[b] <= 2 * sb + 1e-6, (b, rel[b], sb)
+    # and an accepted GPU step solves the oracle's damped normal equations to
+    # FP32 accuracy (backward error); a wrong block in the factorisation or
+    # the substitutions leaves an O(1) residual
     for b in np.nonzero(~tie)[0]:
         # the GPU started from x0 rounded to FP32: a rejected step leaves it exactly there
         dx = (q[b].astype(np.float64) - x0[b].astype(np.float32).astype(np.float64)).ravel()
@@ -135,21 +171,69 @@ def test_one_step_short_horizons_match_oracle(T, ext):
         assert be <= 1e-4, (b, be)
 
 
+def test_first_iterates_one_step_from_the_oracle_path():
+    """Iterates 1 to 5, one step at a time: the GPU starts every step from the
+    oracle's iterate k-1 with the oracle's damping after k-1 iterations (the
+    damping trace of oracle.traj_lm_run), and its iterate k must lie within
+    twice the step's FP32 sensitivity of the oracle's on every trajectory
+    without a near-tie at that step.  Where that bound is below 1e-4, the
+    1e-4 bar holds."""
+    B, K = 24, 5
+    o, g, qs, goals, x0, radii, obs, plane, scene = setup(B, 64)
+    op = oparams(pk.pk_trajopt_params_default(iters=K))
+    ratios, ties, within_bar = [], 0, []
+    for b in range(B):
+        run = oracle.traj_lm_run(o, op, scene, x0[b], qs[b], goals[b])
+        lam_prev = np.concatenate([[op.lambda0], run["lam_trace"]])
+        for k in range(1, K + 1):
+            start = x0[b] if k == 1 else run["trace"][k - 2]
+            p1 = pk.pk_trajopt_params_default(iters=1, lambda0=float(lam_prev[k - 1]))
+            one = oracle.traj_solve(o, oparams(p1), scene, start[None], qs[b:b + 1], goals[b:b + 1], n_trace=True)
+            if one["margin"][0] <= 1e-5 or hinge_kink(o, start):
+                ties += 1
+                continue
+            q = pk.pk_trajopt_solve(g, p1, dev(qs[b:b + 1]), dev(goals[b:b + 1]), dev(start[None]), dev(radii),
+                                    dev(obs), plane)[0].cpu().numpy()[0]
+            ref = run["trace"][k - 1]
+            np.testing.assert_array_equal(one["x"][0], ref)  # the single step reproduces the oracle's path
+            rel = np.max(np.abs(q - ref) / np.maximum(1.0, np.abs(ref)))
+            sb = step_sensitivity(o, op, scene, start, qs[b], goals[b], lam_prev[k - 1])
+            ratios.append(rel / sb)
+            assert rel <= 2 * sb + 1e-6, (b, k, rel, sb)
+            if 2 * sb <= 1e-4:
+                within_bar.append(rel)
+    print(f"one-step iterates: max error / bound {max(ratios):.2f}, {ties} near-ties or hinge kinks excluded, "
+          f"{len(within_bar)} steps where FP32 allows the 1e-4 bar (worst {max(within_bar, default=0):.1e})")
+    assert ties <= 6 and all(r <= 1e-4 for r in within_bar)  # at most 5% of the 120 steps
+
+
 def test_first_iterates_match_oracle():
-    o, g, qs, goals, x0, radii, obs, plane, scene = setup(16, 64)
-    ref = oracle.traj_solve(o, oparams(pk.pk_trajopt_params_default(iters=3)), scene, x0, qs, goals, n_trace=True)
+    """Free runs of 1 to 5 iterations from the same start: every trajectory
+    without a near-tie in its first five iterations stays within twice the
+    sum of its steps' FP32 sensitivity bounds."""
+    B, K = 24, 5
+    o, g, qs, goals, x0, radii, obs, plane, scene = setup(B, 64)
+    op = oparams(pk.pk_trajopt_params_default(iters=K))
+    ref = oracle.traj_solve(o, op, scene, x0, qs, goals, n_trace=True)
     tie = ref["margin"] <= 1e-5
-    for k in (1, 2, 3):
+    # a hinge kink at the start of any of the five steps makes the rest of the
+    # run depend on rounding, like a near-tie
+    tie |= np.array([any(hinge_kink(o, x) for x in [x0[b]] + list(ref["trace"][b, :K - 1])) for b in range(B)])
+    cum = np.zeros(B)
+    lam = [oracle.traj_lm_run(o, op, scene, x0[b], qs[b], goals[b])["lam_trace"] for b in range(B)]
+    for k in range(1, K + 1):
+        for b in range(B):
+            start = x0[b] if k == 1 else ref["trace"][b, k - 2]
+            lam_k = op.lambda0 if k == 1 else lam[b][k - 2]
+            cum[b] += step_sensitivity(o, op, scene, start, qs[b], goals[b], lam_k)
         p = pk.pk_trajopt_params_default(iters=k)
-        q, cost, st = pk.pk_trajopt_solve(g, p, dev(qs), dev(goals), dev(x0), dev(radii), dev(obs), plane)
-        q = q.cpu().numpy()
-        rel = (np.abs(q - ref["trace"][:, k - 1]) / np.maximum(1.0, np.abs(ref["trace"][:, k - 1]))).reshape(16, -1)
-        worst = rel.max(axis=1)[~tie]
-        # per-step FP32 error compounds through the accept decisions and the
-        # collision active set: bound most trajectories, and the typical one
-        assert np.mean(worst <= 5e-3) >= 0.9, (k, worst)
-        assert np.median(worst) <= (1e-4 if k == 1 else 1e-3), (k, worst)
-    assert tie.sum() <= 2
+        q = pk.pk_trajopt_solve(g, p, dev(qs), dev(goals), dev(x0), dev(radii), dev(obs), plane)[0].cpu().numpy()
+        rel = (np.abs(q - ref["trace"][:, k - 1]) / np.maximum(1.0, np.abs(ref["trace"][:, k - 1]))).reshape(B, -1)
+        worst = rel.max(axis=1)
+        bad = (~tie) & (worst > 2 * cum + 1e-6)
+        assert not bad.any(), (k, worst[bad], cum[bad])
+    print(f"free runs: {tie.sum()} of {B} trajectories with a near-tie or hinge kink in five iterations")
+    assert tie.sum() <= 3
 
 
 def test_full_solve_against_oracle():

@@ -3,14 +3,15 @@
 (Sec. IV-A), whose rows couple q_t and q_{t+1} and fill the (t, t-1) blocks of
 the normal matrix, and the five-point acceleration and jerk stencils
 (Sec. III-C smoothness), which widen the normal matrix to four block
-sub-diagonals.  Tolerances as in test_gpu_trajopt.py."""
+sub-diagonals.  Tolerances as in test_gpu_trajopt.py: every step within twice
+its first-order FP32 sensitivity bound (step_sensitivity)."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 from paper_2505_03728_gb300 import pk
-from test_gpu_trajopt import dev, oparams, setup
+from test_gpu_trajopt import dev, hinge_kink, oparams, setup, step_sensitivity
 
 pytestmark = pytest.mark.gpu
 
@@ -57,10 +58,13 @@ def test_one_step_with_extensions_matches_oracle():
                                 dev(radii), dev(obs), plane)[0].cpu().numpy()
         tie = ref["margin"] <= 1e-5
         rel = (np.abs(q - ref["x"]) / np.maximum(1.0, np.abs(ref["x"]))).reshape(16, -1).max(axis=1)
-        assert np.all(rel[~tie] <= 5e-3), rel
-        # the velocity hinges (active on most steps of these perturbed
-        # trajectories) stiffen the system: FP32 steps spread more than without
-        assert np.median(rel[~tie]) <= 1e-3, rel
+        op = oparams(pk.pk_trajopt_params_default(iters=1, **EXT))
+        for b in np.nonzero(~tie)[0]:
+            if hinge_kink(o, start[b]):
+                continue
+            sb = step_sensitivity(o, op, scene, start[b], qs[b], goals[b], op.lambda0)
+            assert rel[b] <= 2 * sb + 1e-6, (b, rel[b], sb)
+        assert tie.sum() <= 2
 
 
 def test_velocity_limit_bounds_the_steps():
@@ -114,8 +118,12 @@ def test_one_step_with_five_point_stencils_matches_oracle(ext):
                                 dev(radii), dev(obs), plane)[0].cpu().numpy()
         tie = ref["margin"] <= 1e-5
         rel = (np.abs(q - ref["x"]) / np.maximum(1.0, np.abs(ref["x"]))).reshape(16, -1).max(axis=1)
-        assert np.all(rel[~tie] <= 5e-3), (ext, start_iters, rel)
-        assert np.median(rel[~tie]) <= 1e-3, (ext, start_iters, rel)
+        op = oparams(pk.pk_trajopt_params_default(iters=1, **kw))
+        for b in np.nonzero(~tie)[0]:
+            if hinge_kink(o, start[b]):
+                continue
+            sb = step_sensitivity(o, op, scene, start[b], qs[b], goals[b], op.lambda0)
+            assert rel[b] <= 2 * sb + 1e-6, (ext, start_iters, b, rel[b], sb)
         assert tie.sum() <= 2
 
 
