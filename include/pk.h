@@ -464,6 +464,44 @@ pk_status pk_trajopt_solve(const pk_robot* robot, const pk_trajopt_params* param
                            void* stream);
 
 /*
+ * pk_ik_select_clear -- collision-free goal configurations by IK (Sec. IV-A:
+ * the start and goal configurations of a trajectory are found by IK and must
+ * be collision-free).  Runs after pk_ik_solve on the same workspace and
+ * (batch, n_seeds), on the same stream, and re-chooses each target's answer
+ * from that solve's per-seed results: among the converged seeds, the lowest
+ * cost whose link spheres clear every obstacle sphere and the plane by
+ * `margin` (sphere model and plane rule of pk_trajopt_solve); if none is
+ * clear, the lowest-cost converged seed; if none converged, the lowest cost.
+ * Ties go to the lower seed index.  Run the solve with cancel_siblings = 0 so
+ * that every seed runs to its end (a cancelled seed is not a candidate).
+ *   robot              serial chain with 6 or 7 movable joints
+ *   d_workspace        the workspace the preceding pk_ik_solve used
+ *   spheres_per_link   1..4;  d_radii [n][spheres_per_link]
+ *   n_obs 0..64;  d_obs [n_obs][4] centre, radius (16-byte aligned)
+ *   plane              host [4]: unit normal and offset h
+ *   margin             metres (the clearance a sphere must keep)
+ *   outputs as pk_ik_solve: d_q_out [batch][n], d_err_out [batch][2],
+ *   d_iters_out [batch], d_status_out [batch] (caller-owned device buffers).
+ * Argument errors return synchronously with nothing enqueued.
+ */
+pk_status pk_ik_select_clear(const pk_robot* robot, int32_t batch, int32_t n_seeds, const void* d_workspace,
+                             int32_t spheres_per_link, const float* d_radii, int32_t n_obs, const float* d_obs,
+                             const float* plane, float margin, float* d_q_out, float* d_err_out,
+                             int32_t* d_iters_out, int32_t* d_status_out, void* stream);
+
+/*
+ * pk_trajopt_interpolate -- the initial trajectory of Sec. IV-A: start and
+ * goal configurations (the goal found by IK) joined by linear interpolation
+ * in joint space, q_t = (1 - s_t) q_start + s_t q_goal, s_t = t / (T - 1)
+ * (s_0 = 0 when T = 1).
+ *   d_q_start, d_q_goal [batch][n]; d_q_out [batch][T][n] (caller-owned
+ *   device buffers).  batch >= 0, T >= 1, n >= 1, batch * T * n < 2^31;
+ *   argument errors return PK_ERR_INVALID_ARG with nothing enqueued.
+ */
+pk_status pk_trajopt_interpolate(int32_t batch, int32_t T, int32_t n, const float* d_q_start,
+                                 const float* d_q_goal, float* d_q_out, void* stream);
+
+/*
  * pk_trajopt_normal -- the normal equations of the same problem at given
  * trajectories d_q [batch][T][n]: full diagonal blocks of J^T J
  * d_D_out [batch][T][n][n] (smoothness included), the first sub-diagonal

@@ -8,6 +8,8 @@
 #include <mutex>
 #include <new>
 
+#include <cmath>
+
 #include "pk_internal.h"
 #include "ik_tree.cuh"
 
@@ -365,6 +367,42 @@ pk_status pk_trajopt_solve(const pk_robot* rb, const pk_trajopt_params* p, int32
   if (batch > 0 && (!d_q_out || !d_status_out)) return fail(PK_ERR_INVALID_ARG, "NULL device buffer");
   return trajopt_common(rb, p, batch, T, d_q_start, d_goal, d_q_init, S, d_radii, n_obs, d_obs, plane, d_q_out,
                         d_cost_out, d_status_out, nullptr, nullptr, nullptr, stream);
+}
+
+pk_status pk_ik_select_clear(const pk_robot* rb, int32_t batch, int32_t n_seeds, const void* d_workspace,
+                             int32_t S, const float* d_radii, int32_t n_obs, const float* d_obs, const float* plane,
+                             float margin, float* d_q_out, float* d_err_out, int32_t* d_iters_out,
+                             int32_t* d_status_out, void* stream) {
+  if (!rb) return fail(PK_ERR_INVALID_ARG, "robot is NULL");
+  if (batch < 0 || n_seeds < 1) return fail(PK_ERR_INVALID_ARG, "batch must be >= 0 and n_seeds >= 1");
+  if (S < 1 || S > pk::kTrajMaxS) return fail(PK_ERR_INVALID_ARG, "spheres_per_link must be in 1..%d", pk::kTrajMaxS);
+  if (n_obs < 0 || n_obs > pk::kTrajMaxObs) return fail(PK_ERR_INVALID_ARG, "n_obs must be in 0..%d", pk::kTrajMaxObs);
+  if (!plane || !finite_all(plane, 4) || !std::isfinite(margin))
+    return fail(PK_ERR_INVALID_ARG, "plane must be 4 finite floats and margin finite");
+  pk::ChainHost ch;
+  pk_status s = fold_chain(rb, rb->n_joints - 1, &ch);
+  if (s != PK_OK) return s;
+  if (ch.n != 6 && ch.n != 7) return fail(PK_ERR_UNSUPPORTED, "clearance selection supports 6 or 7 movable joints");
+  if (batch == 0) return PK_OK;
+  if (!d_workspace || !d_radii || (n_obs > 0 && !d_obs) || !d_q_out || !d_err_out || !d_iters_out || !d_status_out)
+    return fail(PK_ERR_INVALID_ARG, "NULL device buffer");
+  if (((uintptr_t)d_obs & 15) != 0) return fail(PK_ERR_INVALID_ARG, "d_obs must be 16-byte aligned");
+  pk::IkWorkspace ws;
+  size_t zero_bytes = 0;
+  pk::ik_workspace_carve(const_cast<void*>(d_workspace), rb->n_dof, batch, n_seeds, &ws, &zero_bytes);
+  cudaError_t e = pk::launch_select_clear(ch, ws.rec, batch, n_seeds, S, d_radii, n_obs, d_obs, plane, margin, d_q_out,
+                                          d_err_out, d_iters_out, d_status_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? PK_OK : cuda_fail(e, "pk_ik_select_clear launch");
+}
+
+pk_status pk_trajopt_interpolate(int32_t batch, int32_t T, int32_t n, const float* d_q_start,
+                                 const float* d_q_goal, float* d_q_out, void* stream) {
+  if (batch < 0 || T < 1 || n < 1) return fail(PK_ERR_INVALID_ARG, "batch must be >= 0, T and n >= 1");
+  if ((long long)batch * T * n > 0x7fffffffLL) return fail(PK_ERR_INVALID_ARG, "batch * T * n exceeds 2^31");
+  if (batch == 0) return PK_OK;
+  if (!d_q_start || !d_q_goal || !d_q_out) return fail(PK_ERR_INVALID_ARG, "NULL device buffer");
+  cudaError_t e = pk::launch_interpolate(batch, T, n, d_q_start, d_q_goal, d_q_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? PK_OK : cuda_fail(e, "pk_trajopt_interpolate launch");
 }
 
 pk_status pk_trajopt_normal(const pk_robot* rb, const pk_trajopt_params* p, int32_t batch, int32_t T,

@@ -198,6 +198,18 @@ cudaError_t launch_trajopt(const ChainHost& ch, const TrajParamsDev& tp, int bat
                            float* q_out, float* cost_out, int32_t* status_out, float* D_out, float* E_out,
                            float* g_out, cudaStream_t st);
 
+// Linear interpolation of trajectories [batch][T][n] between q_start and
+// q_goal [batch][n] (trajopt.cu).
+cudaError_t launch_interpolate(int batch, int T, int n, const float* q_start, const float* q_goal, float* q_out,
+                               cudaStream_t st);
+
+// Best seed per target preferring converged seeds whose link spheres clear a
+// scene by `margin` (trajopt.cu); rec: the per-seed records of a chain solve.
+cudaError_t launch_select_clear(const ChainHost& ch, const float* rec, int batch, int n_seeds, int S,
+                                const float* radii, int n_obs, const float* obs, const float* plane, float margin,
+                                float* q_out, float* err_out, int32_t* iters_out, int32_t* status_out,
+                                cudaStream_t st);
+
 // Folds a serial chain ending at frame `link` (false if it is not one).
 bool fold_chain_quiet(const pk_robot* rb, int link, ChainHost* ch);
 

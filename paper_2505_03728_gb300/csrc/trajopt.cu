@@ -23,6 +23,8 @@
 //      products spread over N*N threads (the inverse of each diagonal factor is
 //      kept so that the off-diagonal factors are plain products);
 //   4. block forward and backward substitution, then the next candidate.
+#include <algorithm>
+
 #include "pk_chain.cuh"
 #include "pk_internal.h"
 #include "pk_math.cuh"
@@ -1375,5 +1377,176 @@ cudaError_t launch_trajopt(const ChainHost& ch, const TrajParamsDev& tp, int bat
 }
 
 #undef PK_TRAJ_ARGS
+
+namespace {
+
+// Initial trajectory (Sec. IV-A): q_t = (1 - s_t) q_start + s_t q_goal with
+// s_t = t / (T - 1), one thread per (trajectory, timestep, joint).
+__global__ void interpolate_kernel(int batch, int T, int n, const float* __restrict__ q_start,
+                                   const float* __restrict__ q_goal, float* __restrict__ q_out) {
+  const long total = (long)batch * T * n;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(i % n);
+    const int t = (int)((i / n) % T);
+    const long b = i / ((long)n * T);
+    const float s = T > 1 ? (float)t / (float)(T - 1) : 0.f;
+    q_out[i] = (1.f - s) * q_start[b * n + j] + s * q_goal[b * n + j];
+  }
+}
+
+}  // namespace
+
+namespace {
+
+// Joint origins p_0 .. p_{N-1} and the tool point p_N of a serial chain at q
+// (the world-frame points the link spheres of the trajectory cost lie on).
+template <int N>
+__device__ void chain_points(const ChainC<N>& rc, const float* q, float (*p)[3]) {
+  Rt Tw;
+  rt_identity(Tw);
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if (rc.orot & (1u << j)) {
+      Rt O;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) O.r[i] = rc.o_r[j][i];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) O.t[i] = rc.o_t[j][i];
+      rt_mul(Tw, O, Tw);
+    } else {
+      rt_translate(Tw, rc.o_t[j]);
+    }
+    float u[3];
+    mat_vec(Tw.r, rc.a[j], u);
+    if (rc.prism & (1u << j)) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Tw.t[i] = fmaf(u[i], q[j], Tw.t[i]);
+    } else {
+      float sn, cs;
+      sincos_rad(q[j], &sn, &cs);
+      rot_joint(Tw.r, u, rc.a[j], sn, cs);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) p[j][i] = Tw.t[i];
+  }
+  if (rc.toolrot) {
+    Rt O;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) O.r[i] = rc.tool_r[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) O.t[i] = rc.tool_t[i];
+    rt_mul(Tw, O, Tw);
+  } else {
+    rt_translate(Tw, rc.tool_t);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) p[N][i] = Tw.t[i];
+}
+
+// Per target (one warp; lanes take the seeds): the seed of the multi-start
+// solve whose records are in `rec` that is converged and whose link spheres
+// clear every obstacle and the plane by `margin`, else converged, else any;
+// within a class the lowest cost, then the lowest seed index.
+template <int N>
+__global__ void __launch_bounds__(128) select_clear_kernel(
+    const __grid_constant__ ChainC<N> rc, const float* __restrict__ rec, int stride, int batch, int n_seeds, int S,
+    const float* __restrict__ radii, int n_obs, const float* __restrict__ obs, float4 plane, float margin,
+    float* __restrict__ q_out, float* __restrict__ err_out, int32_t* __restrict__ iters_out,
+    int32_t* __restrict__ status_out) {
+  const int b = (int)((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (b >= batch) return;  // uniform across the warp
+  const int np = stride - 4;
+  int bc = -1, bs = 0x7fffffff;
+  float bf = INFINITY;
+  for (int s = lane; s < n_seeds; s += 32) {
+    const float* r = rec + ((size_t)b * n_seeds + s) * stride;
+    const int meta = __float_as_int(r[np + 3]);
+    const bool conv = (meta >> 24) == PK_P_CONVERGED;
+    float fv = r[np];
+    if (!isfinite(fv)) fv = INFINITY;
+    int cls = conv ? 1 : 0;
+    if (conv) {
+      float q[N], p[N + 1][3];
+#pragma unroll
+      for (int j = 0; j < N; ++j) q[j] = r[j];
+      chain_points<N>(rc, q, p);
+      bool clear = true;
+      for (int l = 0; l < N && clear; ++l) {
+        for (int k = 0; k < S && clear; ++k) {
+          const float al = (k + 0.5f) / (float)S, rad = __ldg(radii + l * S + k);
+          float c[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) c[i] = fmaf(al, p[l + 1][i] - p[l][i], p[l][i]);
+          for (int o = 0; o < n_obs; ++o) {
+            const float4 ob = __ldg(reinterpret_cast<const float4*>(obs) + o);
+            const float v0 = c[0] - ob.x, v1 = c[1] - ob.y, v2 = c[2] - ob.z;
+            if (sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2))) - rad - ob.w < margin) {
+              clear = false;
+              break;
+            }
+          }
+          // the first link's spheres are not tested against the plane
+          if (clear && l >= 1 && fmaf(plane.x, c[0], fmaf(plane.y, c[1], plane.z * c[2])) - plane.w - rad < margin)
+            clear = false;
+        }
+      }
+      if (clear) cls = 2;
+    }
+    if (cls > bc || (cls == bc && (fv < bf || (fv == bf && s < bs)))) {
+      bc = cls;
+      bf = fv;
+      bs = s;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    const int oc = __shfl_xor_sync(0xffffffffu, bc, off), os = __shfl_xor_sync(0xffffffffu, bs, off);
+    const float of = __shfl_xor_sync(0xffffffffu, bf, off);
+    if (oc > bc || (oc == bc && (of < bf || (of == bf && os < bs)))) {
+      bc = oc;
+      bf = of;
+      bs = os;
+    }
+  }
+  if (lane == 0) {
+    const float* r = rec + ((size_t)b * n_seeds + bs) * stride;
+#pragma unroll
+    for (int j = 0; j < N; ++j) q_out[(size_t)b * N + j] = r[j];
+    err_out[2 * (size_t)b] = r[np + 1];
+    err_out[2 * (size_t)b + 1] = r[np + 2];
+    const int meta = __float_as_int(r[np + 3]);
+    iters_out[b] = meta & 0xffffff;
+    status_out[b] = meta >> 24;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_select_clear(const ChainHost& ch, const float* rec, int batch, int n_seeds, int S,
+                                const float* radii, int n_obs, const float* obs, const float* plane, float margin,
+                                float* q_out, float* err_out, int32_t* iters_out, int32_t* status_out,
+                                cudaStream_t st) {
+  const float4 pl = make_float4(plane[0], plane[1], plane[2], plane[3]);
+  const int grid = (int)(((long)batch * 32 + 127) / 128);
+  if (ch.n == 7) {
+    select_clear_kernel<7><<<grid, 128, 0, st>>>(chain_const<7>(ch), rec, ik_rec_stride(7), batch, n_seeds, S, radii,
+                                                 n_obs, obs, pl, margin, q_out, err_out, iters_out, status_out);
+  } else if (ch.n == 6) {
+    select_clear_kernel<6><<<grid, 128, 0, st>>>(chain_const<6>(ch), rec, ik_rec_stride(6), batch, n_seeds, S, radii,
+                                                 n_obs, obs, pl, margin, q_out, err_out, iters_out, status_out);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interpolate(int batch, int T, int n, const float* q_start, const float* q_goal, float* q_out,
+                               cudaStream_t st) {
+  const long total = (long)batch * T * n;
+  const int block = 256;
+  const int grid = (int)std::min<long>((total + block - 1) / block, 152L * 8);
+  interpolate_kernel<<<grid, block, 0, st>>>(batch, T, n, q_start, q_goal, q_out);
+  return cudaGetLastError();
+}
 
 }  // namespace pk

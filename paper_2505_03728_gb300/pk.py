@@ -123,6 +123,9 @@ _SIGNATURES = {
                                 _vp, _vp]),
     "pk_trajopt_normal": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _i32, _vp, _f32p, _vp, _vp, _vp,
                                  _vp, _vp]),
+    "pk_trajopt_interpolate": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp]),
+    "pk_ik_select_clear": (_i32, [_vp, _i32, _i32, _vp, _i32, _vp, _i32, _vp, _f32p, C.c_float, _vp, _vp, _vp, _vp,
+                                  _vp]),
     "pk_seednet_create": (_i32, [_vp, _i32, _i32p, _i32, _i32, _i32, C.c_uint64, C.POINTER(_vp)]),
     "pk_seednet_destroy": (None, [_vp]),
     "pk_seednet_n_params": (C.c_int64, [_vp]),
@@ -601,6 +604,34 @@ def pk_trajopt_solve(robot: Robot, params: pk_trajopt_params, q_start, goals, q_
                                   pl.ctypes.data_as(_f32p), _dev(q_out, name="q_out"), _dev(cost, name="cost"),
                                   _dev(status, torch.int32, "status"), _stream(stream)))
     return q_out, cost, status
+
+
+def pk_ik_select_clear(robot: Robot, workspace: torch.Tensor, n_seeds: int, radii, obstacles, plane, margin: float,
+                       out, stream=None):
+    """Re-choose the answers of the preceding pk_ik_solve (same workspace) preferring converged seeds whose
+    link spheres clear the scene by `margin`.  out = (q, err, iters, status) as pk_ik_solve's."""
+    q, err, iters, status = out
+    B = q.shape[0]
+    S, n_obs, pl = _scene_args(radii, obstacles, plane)
+    _check(lib().pk_ik_select_clear(robot.handle, B, int(n_seeds), _dev(workspace, torch.uint8, "workspace"), S,
+                                    _dev(radii, name="radii"), n_obs,
+                                    _dev(obstacles, name="obstacles") if n_obs else None, pl.ctypes.data_as(_f32p),
+                                    float(margin), _dev(q, name="q"), _dev(err, name="err"),
+                                    _dev(iters, torch.int32, "iters"), _dev(status, torch.int32, "status"),
+                                    _stream(stream)))
+    return out
+
+
+def pk_trajopt_interpolate(q_start: torch.Tensor, q_goal: torch.Tensor, T: int, out=None, stream=None):
+    """Initial trajectories [B][T][n]: q_start and q_goal [B][n] joined linearly in joint space."""
+    B, n = q_start.shape
+    if q_goal.shape != (B, n):
+        raise ValueError("q_goal must match q_start [batch][n]")
+    if out is None:
+        out = torch.empty(B, T, n, device=q_start.device)
+    _check(lib().pk_trajopt_interpolate(B, int(T), n, _dev(q_start, name="q_start"), _dev(q_goal, name="q_goal"),
+                                        _dev(out, name="out"), _stream(stream)))
+    return out
 
 
 def pk_trajopt_normal(robot: Robot, params: pk_trajopt_params, q_start, goals, q, radii, obstacles, plane,

@@ -84,3 +84,10 @@ def test_null_arguments(L):
     assert L.pk_ik_split_workspace_stats(None, stats) == pk.PK_ERR_INVALID_ARG
     assert L.pk_seednet_save(None, b"x.pksn") == pk.PK_ERR_INVALID_ARG
     assert L.pk_seednet_load(None, b"x.pksn") == pk.PK_ERR_INVALID_ARG
+
+
+def test_trajopt_interpolate_rejects_bad_sizes_on_the_host(L):
+    assert L.pk_trajopt_interpolate(-1, 4, 7, None, None, None, None) == pk.PK_ERR_INVALID_ARG
+    assert L.pk_trajopt_interpolate(2, 0, 7, None, None, None, None) == pk.PK_ERR_INVALID_ARG
+    assert L.pk_trajopt_interpolate(2, 4, 7, None, None, None, None) == pk.PK_ERR_INVALID_ARG  # NULL buffers
+    assert L.pk_trajopt_interpolate(0, 4, 7, None, None, None, None) == pk.PK_OK  # nothing to do
