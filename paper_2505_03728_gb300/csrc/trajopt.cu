@@ -377,100 +377,116 @@ __device__ __forceinline__ void coll_jrow(const ChainC<N>& rc, const TrajSmem<N,
 }
 
 // Collision terms of timestep t, one link sphere per lane (lanes >= N*S idle).
+// Screening tests every (sphere, obstacle) pair on squared distances (no
+// square root): |c - o|^2 < (r + r_o + eta)^2 marks the pair active in a bit
+// mask, and mind keeps a quantity with the sign of the smallest signed
+// distance (|c - o|^2 - (r + r_o)^2; the plane's distance itself), all the
+// collision status needs.  Then the active pairs, lane by lane in lane order
+// (a fixed summation order), are processed by the whole warp, which adds each
+// row's cost, J^T r and J^T J contributions straight into timestep t's
+// blocks.
 template <int N, int B, bool X>
 __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int buf, int t,
                                 int lane, float& fpart, float& mind) {
-  constexpr int NT = N * (N + 1) / 2;
   const int nsph = N * tp.S;
-  float Dl[NT], gl[N];
-#pragma unroll
-  for (int i = 0; i < NT; ++i) Dl[i] = 0.f;
-#pragma unroll
-  for (int j = 0; j < N; ++j) gl[j] = 0.f;
-  bool any = false;
+  unsigned long long amask = 0ull;
+  bool aplane = false;
+  float c[3] = {0.f, 0.f, 0.f}, rad = 0.f;
+  int l = 0;
   if (lane < nsph) {
-    const int l = lane / tp.S, s = lane % tp.S;
+    l = lane / tp.S;
+    const int s = lane % tp.S;
     const float al = (s + 0.5f) / (float)tp.S;
-    float c[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) c[i] = fmaf(al, S.p[t][l + 1][i] - S.p[t][l][i], S.p[t][l][i]);
-    const float rad = S.rad[l][s];
-    const float wc = tp.w_coll;
-    // screening: the signed distance to every obstacle, four independent
-    // tests at a time (few pairs come within eta); the contributions below
-    // run only for a sphere with an active pair, with the same distances
-    bool act = false;
-    int o0 = 0;
-    for (; o0 + 4 <= tp.n_obs; o0 += 4) {
-      float dd[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float4 ob = *reinterpret_cast<const float4*>(S.obs[o0 + u]);
-        const float v0 = c[0] - ob.x, v1 = c[1] - ob.y, v2 = c[2] - ob.z;
-        dd[u] = sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2))) - rad - ob.w;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        mind = fminf(mind, dd[u]);
-        act = act || dd[u] < tp.eta;
-      }
-    }
-    for (; o0 < tp.n_obs; ++o0) {
-      const float4 ob = *reinterpret_cast<const float4*>(S.obs[o0]);
+    rad = S.rad[l][s];
+#pragma unroll 4
+    for (int o = 0; o < tp.n_obs; ++o) {
+      const float4 ob = *reinterpret_cast<const float4*>(S.obs[o]);
       const float v0 = c[0] - ob.x, v1 = c[1] - ob.y, v2 = c[2] - ob.z;
-      const float d = sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2))) - rad - ob.w;
-      mind = fminf(mind, d);
-      act = act || d < tp.eta;
+      const float dd = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+      const float R = rad + ob.w, Re = R + tp.eta;
+      mind = fminf(mind, fmaf(-R, R, dd));
+      if (dd < Re * Re) amask |= 1ull << o;
     }
     if (l != 0) {  // the first link is not tested against the plane
       const float d = tp.plane[0] * c[0] + tp.plane[1] * c[1] + tp.plane[2] * c[2] - tp.plane[3] - rad;
       mind = fminf(mind, d);
-      act = act || d < tp.eta;
+      aplane = d < tp.eta;
     }
-    for (int o = act ? 0 : tp.n_obs + 1; o <= tp.n_obs; ++o) {
+  }
+  // active pairs, lane by lane in lane order; every pair is processed by the
+  // whole warp: lane i < N forms Jacobian entry i, lane e < N(N+1)/2 adds
+  // J^T J entry e, lane i < N adds J^T r entry i
+  constexpr int NT = N * (N + 1) / 2;
+  int ei = 0;
+  while ((ei + 1) * (ei + 2) / 2 <= lane) ++ei;
+  const int ek = lane - ei * (ei + 1) / 2;  // (ei, ek): this lane's J^T J entry when lane < NT
+  unsigned lanes = __ballot_sync(0xffffffffu, amask != 0ull || aplane);
+  while (lanes) {
+    const int src = __ffs(lanes) - 1;
+    lanes &= lanes - 1;
+    unsigned long long m = ((unsigned long long)__shfl_sync(0xffffffffu, (unsigned)(amask >> 32), src) << 32) |
+                           __shfl_sync(0xffffffffu, (unsigned)amask, src);
+    bool pl = __shfl_sync(0xffffffffu, aplane ? 1 : 0, src) != 0;
+    const float cs[3] = {__shfl_sync(0xffffffffu, c[0], src), __shfl_sync(0xffffffffu, c[1], src),
+                         __shfl_sync(0xffffffffu, c[2], src)};
+    const float rs = __shfl_sync(0xffffffffu, rad, src);
+    const int ls = __shfl_sync(0xffffffffu, l, src);
+    for (;;) {
+      int o;
+      if (m) {
+        o = __ffsll(m) - 1;
+        m &= m - 1;
+      } else if (pl) {
+        o = tp.n_obs;
+        pl = false;
+      } else {
+        break;
+      }
+      // the pair's distance, normal and activation, the same on every lane
       float d, nrm[3];
       if (o < tp.n_obs) {
         const float4 ob = *reinterpret_cast<const float4*>(S.obs[o]);
-        const float v0 = c[0] - ob.x, v1 = c[1] - ob.y, v2 = c[2] - ob.z;
+        const float v0 = cs[0] - ob.x, v1 = cs[1] - ob.y, v2 = cs[2] - ob.z;
         const float len = sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
-        d = len - rad - ob.w;
+        d = len - rs - ob.w;
         const float inv = 1.f / len;
         nrm[0] = v0 * inv; nrm[1] = v1 * inv; nrm[2] = v2 * inv;
       } else {
-        if (l == 0) continue;  // the first link is not tested against the plane
         nrm[0] = tp.plane[0]; nrm[1] = tp.plane[1]; nrm[2] = tp.plane[2];
-        d = nrm[0] * c[0] + nrm[1] * c[1] + nrm[2] * c[2] - tp.plane[3] - rad;
+        d = nrm[0] * cs[0] + nrm[1] * cs[1] + nrm[2] * cs[2] - tp.plane[3] - rs;
       }
       float df;
       const float fa = coll_act(d, tp.eta, &df);
       if (df == 0.f) continue;
-      any = true;
-      const float r = wc * fa;
-      fpart = fmaf(r, r, fpart);
-      float jr[N];
-      coll_jrow<N, B, X>(rc, S, t, l, c, nrm, wc * df, jr);
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        gl[i] = fmaf(jr[i], r, gl[i]);
-#pragma unroll
-        for (int k = 0; k <= i; ++k) Dl[tri(i, k)] = fmaf(jr[i], jr[k], Dl[tri(i, k)]);
+      const float r = tp.w_coll * fa;
+      if (lane == 0) fpart = fmaf(r, r, fpart);
+      // Jacobian entry i = lane: d(c)/d(q_i) = w_i x (c - p_i) for the joints of links 0..ls
+      float ji = 0.f;
+      if (lane < N && lane <= ls) {
+        const int i = lane;
+        float dc;
+        if (rc.prism & (1u << i)) {
+          dc = S.w[t][i][0] * nrm[0] + S.w[t][i][1] * nrm[1] + S.w[t][i][2] * nrm[2];
+        } else {
+          const float e0 = cs[0] - S.p[t][i][0], e1 = cs[1] - S.p[t][i][1], e2 = cs[2] - S.p[t][i][2];
+          const float x0 = e1 * nrm[2] - e2 * nrm[1], x1 = e2 * nrm[0] - e0 * nrm[2], x2 = e0 * nrm[1] - e1 * nrm[0];
+          dc = S.w[t][i][0] * x0 + S.w[t][i][1] * x1 + S.w[t][i][2] * x2;
+        }
+        ji = tp.w_coll * df * dc;
       }
-    }
-  }
-  if (__any_sync(0xffffffffu, any)) {
-#pragma unroll
-    for (int i = 0; i < NT; ++i)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) Dl[i] += __shfl_xor_sync(0xffffffffu, Dl[i], o);
-#pragma unroll
-    for (int j = 0; j < N; ++j)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) gl[j] += __shfl_xor_sync(0xffffffffu, gl[j], o);
-    if (lane == 0) {  // atomic: the swept rows of segment (t-1, t) also land in D_t, g_t
-#pragma unroll
-      for (int i = 0; i < NT; ++i) atomicAdd(&S.D[buf][t][i], Dl[i]);
-#pragma unroll
-      for (int j = 0; j < N; ++j) atomicAdd(&S.g[buf][t][j], gl[j]);
+      const float jei = __shfl_sync(0xffffffffu, ji, ei < N ? ei : 0);
+      const float jek = __shfl_sync(0xffffffffu, ji, ek < N ? ek : 0);
+      // with swept rows other warps add into D_t and g_t too: atomics then
+      if (lane < NT) {
+        if constexpr (X) atomicAdd(&S.D[buf][t][lane], jei * jek);
+        else S.D[buf][t][lane] = fmaf(jei, jek, S.D[buf][t][lane]);
+      }
+      if (lane < N) {
+        if constexpr (X) atomicAdd(&S.g[buf][t][lane], ji * r);
+        else S.g[buf][t][lane] = fmaf(ji, r, S.g[buf][t][lane]);
+      }
     }
   }
   // swept spheres (Sec. IV-A): the capsule of this lane's sphere from t to t+1
@@ -1253,7 +1269,7 @@ __device__ bool twisted_solve_b(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, i
 }
 
 template <int N, int B, bool X>
-__global__ void __launch_bounds__(kThreads) trajopt_kernel(
+__global__ void __launch_bounds__(kThreads, (B == 2 && !X) ? 3 : 2) trajopt_kernel(
     const __grid_constant__ ChainC<N> rc, const __grid_constant__ TrajParamsDev tp, const float* __restrict__ q_start,
     const float* __restrict__ goals, const float* __restrict__ q_init, const float* __restrict__ radii,
     const float* __restrict__ obs, float* __restrict__ q_out, float* __restrict__ cost_out,
