@@ -548,7 +548,11 @@ typedef struct {
   int32_t refine_iters;    /* LM iterations of a round (default 20) */
   float pool_frac;         /* share of every batch drawn from the label pool once it
                               holds a round (0..1, default 0.5) */
-  int32_t reserved;        /* must be 0 */
+  int32_t first_epoch;     /* a call runs epochs first_epoch .. last_epoch - 1 of the
+                              `epochs`-long schedule (learning rate, refinement rounds):
+                              stop with last_epoch, save, load, resume with first_epoch
+                              (default 0) */
+  int32_t last_epoch;      /* 0: epochs (default 0) */
 } pk_train_params;
 
 void pk_train_params_default(pk_train_params* p);
@@ -565,10 +569,15 @@ int64_t pk_seednet_n_params(const pk_seednet* net);
 pk_status pk_seednet_get_params(const pk_seednet* net, float* host_params, int64_t n);
 pk_status pk_seednet_set_params(pk_seednet* net, const float* host_params, int64_t n);
 
-/* Write the parameters to a file at `path` (host path; a small header with
- * the network's shape, then the FP32 parameters in the get_params layout,
- * host byte order), or read such a file into a network of the same shape
- * (which also resets the AdamW state, as set_params).  Synchronous.
+/* Training checkpoint.  pk_seednet_save writes the network and its whole
+ * training state to a file at `path` (host path, host byte order): a small
+ * header with the network's shape, the FP32 parameters in the get_params
+ * layout, the AdamW step count (also the training-data generator's counter),
+ * the AdamW first and second moments, and the LM-refined label pool.
+ * pk_seednet_load reads such a file into a network of the same shape and
+ * restores all of it, so that pk_seednet_train continues (first_epoch) where
+ * the saved run stopped; files of the earlier parameters-only format load
+ * their parameters and reset the AdamW state, as set_params.  Synchronous.
  * PK_ERR_INVALID_ARG if the file cannot be opened, written or fully read, is
  * not such a file, or holds a network of another shape (the network is then
  * unchanged). */

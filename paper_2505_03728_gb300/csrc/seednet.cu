@@ -610,6 +610,37 @@ size_t oracle_count(const pk_seednet* s) {
   return n;
 }
 
+// A padded FP32 device buffer of the parameter layout (master weights, AdamW
+// moments) to and from the unpadded host order of pk_seednet_get_params: per
+// layer W [out][in] row-major, then b [out].
+pk_status device_to_layout(const pk_seednet* s, const float* dev, float* host, const char* what) {
+  std::vector<float> h(s->n_master);
+  cudaError_t e = cudaMemcpy(h.data(), dev, s->n_master * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return sn_cuda(e, what);
+  size_t o = 0;
+  for (int l = 0; l < s->L; ++l) {
+    const int fi = l == 0 ? s->in_dim : s->width;
+    const int fo = l == s->L - 1 ? s->out_dim : s->width;
+    for (int r = 0; r < fo; ++r)
+      for (int c = 0; c < fi; ++c) host[o++] = h[s->w_off[l] + (size_t)r * s->din[l] + c];
+    for (int r = 0; r < fo; ++r) host[o++] = h[s->b_off[l] + r];
+  }
+  return PK_OK;
+}
+
+cudaError_t layout_to_device(const pk_seednet* s, const float* host, float* dev) {
+  std::vector<float> h(s->n_master, 0.f);
+  size_t o = 0;
+  for (int l = 0; l < s->L; ++l) {
+    const int fi = l == 0 ? s->in_dim : s->width;
+    const int fo = l == s->L - 1 ? s->out_dim : s->width;
+    for (int r = 0; r < fo; ++r)
+      for (int c = 0; c < fi; ++c) h[s->w_off[l] + (size_t)r * s->din[l] + c] = host[o++];
+    for (int r = 0; r < fo; ++r) h[s->b_off[l] + r] = host[o++];
+  }
+  return cudaMemcpy(dev, h.data(), s->n_master * 4, cudaMemcpyHostToDevice);
+}
+
 }  // namespace
 
 extern "C" {
@@ -626,11 +657,12 @@ void pk_train_params_default(pk_train_params* p) {
   p->eps = 1e-8f;
   p->mu = 0.01f;
   p->refine_every = 0;
+  p->first_epoch = 0;
+  p->last_epoch = 0;
   p->seed = 500;
   p->refine_n = 65536;
   p->refine_iters = 20;
   p->pool_frac = 0.5f;
-  p->reserved = 0;
 }
 
 pk_status pk_seednet_create(const pk_robot* rb, int32_t k, const int32_t* target_links, int32_t K,
@@ -749,33 +781,13 @@ int64_t pk_seednet_n_params(const pk_seednet* s) { return s ? (int64_t)oracle_co
 pk_status pk_seednet_get_params(const pk_seednet* s, float* host, int64_t n) {
   if (!s || !host) return sn_fail(PK_ERR_INVALID_ARG, "NULL argument");
   if ((size_t)n != oracle_count(s)) return sn_fail(PK_ERR_INVALID_ARG, "parameter count mismatch");
-  std::vector<float> h(s->n_master);
-  cudaError_t e = cudaMemcpy(h.data(), s->master, s->n_master * 4, cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return sn_cuda(e, "pk_seednet_get_params");
-  size_t o = 0;
-  for (int l = 0; l < s->L; ++l) {
-    const int fi = l == 0 ? s->in_dim : s->width;
-    const int fo = l == s->L - 1 ? s->out_dim : s->width;
-    for (int r = 0; r < fo; ++r)
-      for (int c = 0; c < fi; ++c) host[o++] = h[s->w_off[l] + (size_t)r * s->din[l] + c];
-    for (int r = 0; r < fo; ++r) host[o++] = h[s->b_off[l] + r];
-  }
-  return PK_OK;
+  return device_to_layout(s, s->master, host, "pk_seednet_get_params");
 }
 
 pk_status pk_seednet_set_params(pk_seednet* s, const float* host, int64_t n) {
   if (!s || !host) return sn_fail(PK_ERR_INVALID_ARG, "NULL argument");
   if ((size_t)n != oracle_count(s)) return sn_fail(PK_ERR_INVALID_ARG, "parameter count mismatch");
-  std::vector<float> h(s->n_master, 0.f);
-  size_t o = 0;
-  for (int l = 0; l < s->L; ++l) {
-    const int fi = l == 0 ? s->in_dim : s->width;
-    const int fo = l == s->L - 1 ? s->out_dim : s->width;
-    for (int r = 0; r < fo; ++r)
-      for (int c = 0; c < fi; ++c) h[s->w_off[l] + (size_t)r * s->din[l] + c] = host[o++];
-    for (int r = 0; r < fo; ++r) h[s->b_off[l] + r] = host[o++];
-  }
-  cudaError_t e = cudaMemcpy(s->master, h.data(), s->n_master * 4, cudaMemcpyHostToDevice);
+  cudaError_t e = layout_to_device(s, host, s->master);
   if (e == cudaSuccess) e = cudaMemset(s->adam_m, 0, s->n_master * 4);
   if (e == cudaSuccess) e = cudaMemset(s->adam_v, 0, s->n_master * 4);
   if (e == cudaSuccess) e = cast_all(s, 0);
@@ -785,25 +797,48 @@ pk_status pk_seednet_set_params(pk_seednet* s, const float* host, int64_t n) {
 }
 
 // File layout of pk_seednet_save / pk_seednet_load (host byte order): the
-// header below, then the FP32 parameters in the pk_seednet_get_params order.
+// header below, the FP32 parameters (pk_seednet_get_params order), and from
+// version 2 on the training state: step and refinement-round counters, the
+// AdamW first and second moments (parameter order), the label pool's target
+// poses [pool_n][k][12] and labels [pool_n][n_dof].
+// Version 1 files (parameters only) still load.
 namespace {
 struct SeednetFileHeader {
   char magic[4];     // "PKSN"
-  uint32_t version;  // 1
+  uint32_t version;  // 1 or 2
   int32_t k, K, n_dof, in_dim, out_dim, width, depth, reserved;
   int64_t n_params;
 };
+struct SeednetFileState {  // version 2, after the parameters
+  int64_t step;            // AdamW step count, also the training data generator's counter
+  int64_t refine_round;    // refinement rounds so far (keys the next round's targets)
+  int32_t pool_n;          // label-pool rows
+  int32_t reserved;
+};
+
+bool write_all(FILE* f, const void* p, size_t bytes) { return bytes == 0 || fwrite(p, bytes, 1, f) == 1; }
+bool read_all(FILE* f, void* p, size_t bytes) { return bytes == 0 || fread(p, bytes, 1, f) == 1; }
 }  // namespace
 
 pk_status pk_seednet_save(const pk_seednet* s, const char* path) {
   if (!s || !path) return sn_fail(PK_ERR_INVALID_ARG, "NULL argument");
   const int64_t n = (int64_t)oracle_count(s);
-  std::vector<float> h((size_t)n);
-  pk_status st = pk_seednet_get_params(s, h.data(), n);
+  std::vector<float> h((size_t)n), m((size_t)n), v((size_t)n);
+  pk_status st = device_to_layout(s, s->master, h.data(), "pk_seednet_save");
+  if (st == PK_OK) st = device_to_layout(s, s->adam_m, m.data(), "pk_seednet_save");
+  if (st == PK_OK) st = device_to_layout(s, s->adam_v, v.data(), "pk_seednet_save");
   if (st != PK_OK) return st;
+  const size_t pT = (size_t)s->pool_n * s->k * 12, pq = (size_t)s->pool_n * s->n_dof;
+  std::vector<float> poolT(pT), poolq(pq);
+  cudaError_t e = cudaSuccess;
+  if (s->pool_n > 0) {
+    e = cudaMemcpy(poolT.data(), s->pool_T, pT * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(poolq.data(), s->pool_q, pq * 4, cudaMemcpyDeviceToHost);
+  }
+  if (e != cudaSuccess) return sn_cuda(e, "pk_seednet_save");
   SeednetFileHeader hd{};
   memcpy(hd.magic, "PKSN", 4);
-  hd.version = 1;
+  hd.version = 2;
   hd.k = s->k;
   hd.K = s->K;
   hd.n_dof = s->n_dof;
@@ -812,9 +847,16 @@ pk_status pk_seednet_save(const pk_seednet* s, const char* path) {
   hd.width = s->width;
   hd.depth = s->depth;
   hd.n_params = n;
+  SeednetFileState fs{};
+  fs.step = s->step;
+  fs.refine_round = s->refine_round;
+  fs.pool_n = s->pool_n;
   FILE* f = fopen(path, "wb");
   if (!f) return sn_fail(PK_ERR_INVALID_ARG, "pk_seednet_save: cannot open the file for writing");
-  const bool ok = fwrite(&hd, sizeof hd, 1, f) == 1 && fwrite(h.data(), sizeof(float), (size_t)n, f) == (size_t)n;
+  const size_t nb = (size_t)n * 4;
+  const bool ok = write_all(f, &hd, sizeof hd) && write_all(f, h.data(), nb) && write_all(f, &fs, sizeof fs) &&
+                  write_all(f, m.data(), nb) && write_all(f, v.data(), nb) && write_all(f, poolT.data(), pT * 4) &&
+                  write_all(f, poolq.data(), pq * 4);
   const bool closed = fclose(f) == 0;
   if (!ok || !closed) return sn_fail(PK_ERR_INVALID_ARG, "pk_seednet_save: write failed");
   return PK_OK;
@@ -825,7 +867,7 @@ pk_status pk_seednet_load(pk_seednet* s, const char* path) {
   FILE* f = fopen(path, "rb");
   if (!f) return sn_fail(PK_ERR_INVALID_ARG, "pk_seednet_load: cannot open the file");
   SeednetFileHeader hd{};
-  if (fread(&hd, sizeof hd, 1, f) != 1 || memcmp(hd.magic, "PKSN", 4) != 0 || hd.version != 1) {
+  if (!read_all(f, &hd, sizeof hd) || memcmp(hd.magic, "PKSN", 4) != 0 || (hd.version != 1 && hd.version != 2)) {
     fclose(f);
     return sn_fail(PK_ERR_INVALID_ARG, "pk_seednet_load: not a seed-network file");
   }
@@ -835,11 +877,46 @@ pk_status pk_seednet_load(pk_seednet* s, const char* path) {
     fclose(f);
     return sn_fail(PK_ERR_INVALID_ARG, "pk_seednet_load: the file holds a network of another shape");
   }
-  std::vector<float> h((size_t)n);
-  const bool ok = fread(h.data(), sizeof(float), (size_t)n, f) == (size_t)n;
+  const size_t nb = (size_t)n * 4;
+  std::vector<float> h((size_t)n), m, v, poolT, poolq;
+  SeednetFileState fs{};
+  bool ok = read_all(f, h.data(), nb);
+  if (ok && hd.version == 2) {
+    ok = read_all(f, &fs, sizeof fs) && fs.pool_n >= 0 && fs.step >= 0 && fs.refine_round >= 0;
+    if (ok) {
+      m.resize((size_t)n);
+      v.resize((size_t)n);
+      poolT.resize((size_t)fs.pool_n * s->k * 12);
+      poolq.resize((size_t)fs.pool_n * s->n_dof);
+      ok = read_all(f, m.data(), nb) && read_all(f, v.data(), nb) && read_all(f, poolT.data(), poolT.size() * 4) &&
+           read_all(f, poolq.data(), poolq.size() * 4);
+    }
+  }
   fclose(f);
   if (!ok) return sn_fail(PK_ERR_INVALID_ARG, "pk_seednet_load: the file is truncated");
-  return pk_seednet_set_params(s, h.data(), n);
+  pk_status st = pk_seednet_set_params(s, h.data(), n);  // weights (and their BF16 copies); AdamW state cleared
+  if (st != PK_OK || hd.version == 1) return st;
+  // the training state: moments, step (and generator position), label pool
+  cudaError_t e = layout_to_device(s, m.data(), s->adam_m);
+  if (e == cudaSuccess) e = layout_to_device(s, v.data(), s->adam_v);
+  if (e == cudaSuccess && fs.pool_n > s->pool_cap) {
+    if (s->pool_T) cudaFree(s->pool_T);
+    if (s->pool_q) cudaFree(s->pool_q);
+    s->pool_T = s->pool_q = nullptr;
+    s->pool_cap = s->pool_n = 0;
+    e = cudaMalloc(&s->pool_T, poolT.size() * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->pool_q, poolq.size() * 4);
+    if (e == cudaSuccess) s->pool_cap = fs.pool_n;
+  }
+  if (e == cudaSuccess && fs.pool_n > 0) {
+    e = cudaMemcpy(s->pool_T, poolT.data(), poolT.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->pool_q, poolq.data(), poolq.size() * 4, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) return sn_cuda(e, "pk_seednet_load");
+  s->pool_n = fs.pool_n;
+  s->step = fs.step;
+  s->refine_round = fs.refine_round;
+  return PK_OK;
 }
 
 pk_status pk_seednet_forward(pk_seednet* s, int32_t batch, const float* d_targets, float* d_y_out,
@@ -1093,15 +1170,18 @@ pk_status pk_seednet_train(pk_seednet* s, const pk_train_params* tp, float* host
   if (tp->epochs < 0 || tp->batch < 128 || tp->steps_per_epoch < 1 || !(tp->lr > 0.f))
     return sn_fail(PK_ERR_INVALID_ARG, "invalid training parameters");
   if (tp->refine_every < 0 || (tp->refine_every > 0 && (tp->refine_n < 1 || tp->refine_iters < 0)) ||
-      !(tp->pool_frac >= 0.f && tp->pool_frac <= 1.f) || tp->reserved != 0)
+      !(tp->pool_frac >= 0.f && tp->pool_frac <= 1.f))
     return sn_fail(PK_ERR_INVALID_ARG, "invalid refinement parameters");
+  const int last = tp->last_epoch > 0 ? tp->last_epoch : tp->epochs;
+  if (tp->first_epoch < 0 || tp->last_epoch < 0 || last > tp->epochs || tp->first_epoch > last)
+    return sn_fail(PK_ERR_INVALID_ARG, "need 0 <= first_epoch <= last_epoch <= epochs");
   cudaStream_t st = (cudaStream_t)stream;
   const int M = tp->batch, m_pad = round_up(M, 128);
   pk_status ps = ensure_acts(s, m_pad);
   if (ps != PK_OK) return ps;
   const int64_t total = (int64_t)tp->epochs * tp->steps_per_epoch;
-  int64_t t = 0;
-  for (int ep = 0; ep < tp->epochs; ++ep) {
+  int64_t t = (int64_t)tp->first_epoch * tp->steps_per_epoch;  // position in the cosine schedule
+  for (int ep = tp->first_epoch; ep < last; ++ep) {
     cudaError_t e = cudaMemsetAsync(s->d_loss, 0, 4, st);
     for (int it = 0; it < tp->steps_per_epoch && e == cudaSuccess; ++it, ++t) {
       datagen_kernel<<<(m_pad + 127) / 128, 128, 0, st>>>(s->d_robot, s->d_links, s->k, s->d_lohi, s->n_dof,
@@ -1123,7 +1203,7 @@ pk_status pk_seednet_train(pk_seednet* s, const pk_train_params* tp, float* host
       float l = 0.f;
       e = cudaMemcpy(&l, s->d_loss, 4, cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) return sn_cuda(e, "pk_seednet_train");
-      host_loss[ep] = l / ((float)M * tp->steps_per_epoch);
+      host_loss[ep - tp->first_epoch] = l / ((float)M * tp->steps_per_epoch);
     }
     if (tp->refine_every > 0 && (ep + 1) % tp->refine_every == 0 && ep + 1 < tp->epochs) {
       ps = pk_seednet_refine(s, tp->refine_n, tp->refine_iters, tp->seed, nullptr, stream);

@@ -72,7 +72,7 @@ class pk_train_params(C.Structure):
                 ("lr", C.c_float), ("weight_decay", C.c_float), ("beta1", C.c_float),
                 ("beta2", C.c_float), ("eps", C.c_float), ("mu", C.c_float), ("refine_every", C.c_int32),
                 ("seed", C.c_uint64), ("refine_n", C.c_int32), ("refine_iters", C.c_int32),
-                ("pool_frac", C.c_float), ("reserved", C.c_int32)]
+                ("pool_frac", C.c_float), ("first_epoch", C.c_int32), ("last_epoch", C.c_int32)]
 
 
 _vp = C.c_void_p
@@ -546,10 +546,13 @@ def pk_seednet_train_step(net: SeedNet, params: pk_train_params, targets, qstar,
 
 
 def pk_seednet_train(net: SeedNet, params: pk_train_params, stream=None) -> np.ndarray:
-    losses = np.zeros(max(1, params.epochs), np.float32)
+    """Mean loss of every epoch the call runs (first_epoch .. last_epoch - 1 of the schedule)."""
+    last = params.last_epoch if params.last_epoch > 0 else params.epochs
+    n = max(0, last - params.first_epoch)
+    losses = np.zeros(max(1, n), np.float32)
     _check(lib().pk_seednet_train(net.handle, C.byref(params), losses.ctypes.data_as(_f32p),
                                   _stream(stream)))
-    return losses[:params.epochs]
+    return losses[:n]
 
 
 def pk_seednet_refine(net: SeedNet, n: int, max_iters: int = 20, seed: int = 500, stream=None) -> int:
