@@ -743,19 +743,17 @@ __device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int
     if constexpr (X) v += (t > u) ? S.E[buf][t][i][j] : S.E[buf][u][j][i];
     return v;
   };
-  // dense factor of a Schur complement (one thread), its inverse into Linv[t]
-  // (N threads); `sync` is the barrier of the threads taking part
-  auto factor_diag = [&](float* sch, int t, int lt, auto&& sync) {
-    if (lt == 0) {
+  // dense factor of a Schur complement and its inverse into Linv[t]: each of
+  // N threads factors the 7 x 7 block in its registers (the same arithmetic,
+  // so no exchange or barrier is needed in between) and writes column lt of
+  // the inverse; `sync` is the barrier of the threads taking part
+  auto factor_diag = [&](const float* sch, int t, int lt, auto&& sync) {
+    if (lt < N) {
       float L[NT];
 #pragma unroll
       for (int i = 0; i < NT; ++i) L[i] = sch[i];
-      if (!chol_packed<N>(L)) S.chol_fail = 1;
-#pragma unroll
-      for (int i = 0; i < NT; ++i) sch[i] = L[i];
-    }
-    sync();
-    if (lt < N) {
+      const bool okf = chol_packed<N>(L);
+      if (lt == 0 && !okf) S.chol_fail = 1;
       const int j = lt;
       float col[N];
 #pragma unroll
@@ -763,8 +761,8 @@ __device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int
         float v = (i == j) ? 1.f : 0.f;
 #pragma unroll
         for (int k = 0; k < N; ++k)
-          if (k >= j && k < i) v = fmaf(-sch[tri(i, k)], col[k], v);
-        col[i] = (i >= j) ? v * sch[tri(i, i)] : 0.f;
+          if (k >= j && k < i) v = fmaf(-L[tri(i, k)], col[k], v);
+        col[i] = (i >= j) ? v * L[tri(i, i)] : 0.f;
       }
 #pragma unroll
       for (int i = 0; i < N; ++i)
@@ -881,33 +879,35 @@ __device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int
   }
   __syncthreads();
   const bool ok = S.chol_fail == 0;
-  // forward substitution in each chain: y_t = Linv_t (-g_t - L[0][t] y_p1 - L[1][t] y_p2)
-  auto fwd_row = [&](int t, int d, int k) {
-    if (gt < N) {
-      float v = -S.g[buf][t][gt];
-      if (k >= 1)
+  // forward substitution in each chain, y_t = Linv_t (-g_t - L[0][t] y_p1 - L[1][t] y_p2),
+  // by the chain's first warp alone: lane i < N holds component i of y_t and
+  // of the two rows before it in registers and the other components come by
+  // shuffle, so the rows need no barrier
+  const unsigned fullm = 0xffffffffu;
+  if (tid < 128 && gt < 32) {
+    const int d = grp == 0 ? 1 : -1;
+    const int t0 = grp == 0 ? 0 : T - 1, len = grp == 0 ? m - 2 : T - m - 2;
+    const int li = gt < N ? gt : 0;
+    float y1 = 0.f, y2 = 0.f;  // this lane's components of y_{t-d}, y_{t-2d}
+    for (int k = 0; k < len; ++k) {
+      const int t = t0 + k * d;
+      float v = gt < N ? -S.g[buf][t][li] : 0.f;
 #pragma unroll
-        for (int q = 0; q < N; ++q) v = fmaf(-S.L[0][t][gt][q], S.y[t - d][q], v);
-      if (k >= 2)
+      for (int q = 0; q < N; ++q) {
+        const float a1v = __shfl_sync(fullm, y1, q), a2v = __shfl_sync(fullm, y2, q);
+        if (k >= 1) v = fmaf(-S.L[0][t][li][q], a1v, v);
+        if (k >= 2) v = fmaf(-S.L[1][t][li][q], a2v, v);
+      }
+      float yv = 0.f;
 #pragma unroll
-        for (int q = 0; q < N; ++q) v = fmaf(-S.L[1][t][gt][q], S.y[t - 2 * d][q], v);
-      S.ctmp[grp][gt] = v;
+      for (int q = 0; q < N; ++q) {
+        const float vq = __shfl_sync(fullm, v, q);
+        if (q <= li) yv = fmaf(S.Linv[t][tri(li, q)], vq, yv);
+      }
+      if (gt < N) S.y[t][gt] = yv;
+      y2 = y1;
+      y1 = yv;
     }
-    gsync();
-    if (gt < N) {
-      float v = 0.f;
-#pragma unroll
-      for (int q = 0; q < N; ++q)
-        if (q <= gt) v = fmaf(S.Linv[t][tri(gt, q)], S.ctmp[grp][q], v);
-      S.y[t][gt] = v;
-    }
-    gsync();
-  };
-  if (tid < 128) {
-    if (grp == 0)
-      for (int t = 0; t <= m - 3; ++t) fwd_row(t, 1, t);
-    else
-      for (int t = T - 1; t >= m + 2; --t) fwd_row(t, -1, T - 1 - t);
   }
   __syncthreads();
   // junction: right-hand sides from both chains, forward, then backward
@@ -960,31 +960,32 @@ __device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int
     }
   }
   __syncthreads();
-  // backward substitution in each chain, from the junction outwards:
-  // x_t = Linv_t^T (y_t - L[0][t+d]^T x_{t+d} - L[1][t+2d]^T x_{t+2d})
-  auto bwd_row = [&](int t, int d) {
-    if (gt < N) {
-      float v = S.y[t][gt];
+  // backward substitution in each chain, from the junction outwards,
+  // x_t = Linv_t^T (y_t - L[0][t+d]^T x_{t+d} - L[1][t+2d]^T x_{t+2d}), by the
+  // chain's first warp with the two later rows' x in registers (as above)
+  if (tid < 128 && gt < 32) {
+    const int d = grp == 0 ? 1 : -1;
+    const int tb = grp == 0 ? m - 3 : m + 2, len = grp == 0 ? m - 2 : T - m - 2;
+    const int li = gt < N ? gt : 0;
+    float x1 = gt < N ? S.y[tb + d][li] : 0.f, x2 = gt < N ? S.y[tb + 2 * d][li] : 0.f;
+    for (int k = 0; k < len; ++k) {
+      const int t = tb - k * d;
+      float v = gt < N ? S.y[t][li] : 0.f;
 #pragma unroll
-      for (int q = 0; q < N; ++q)
-        v = fmaf(-S.L[0][t + d][q][gt], S.y[t + d][q], fmaf(-S.L[1][t + 2 * d][q][gt], S.y[t + 2 * d][q], v));
-      S.ctmp[grp][gt] = v;
-    }
-    gsync();
-    if (gt < N) {
-      float v = 0.f;
+      for (int q = 0; q < N; ++q) {
+        const float a1v = __shfl_sync(fullm, x1, q), a2v = __shfl_sync(fullm, x2, q);
+        v = fmaf(-S.L[0][t + d][q][li], a1v, fmaf(-S.L[1][t + 2 * d][q][li], a2v, v));
+      }
+      float xv = 0.f;
 #pragma unroll
-      for (int q = 0; q < N; ++q)
-        if (q >= gt) v = fmaf(S.Linv[t][tri(q, gt)], S.ctmp[grp][q], v);
-      S.y[t][gt] = v;
+      for (int q = 0; q < N; ++q) {
+        const float vq = __shfl_sync(fullm, v, q);
+        if (q >= li) xv = fmaf(S.Linv[t][tri(q, li)], vq, xv);
+      }
+      if (gt < N) S.y[t][gt] = xv;
+      x2 = x1;
+      x1 = xv;
     }
-    gsync();
-  };
-  if (tid < 128) {
-    if (grp == 0)
-      for (int t = m - 3; t >= 0; --t) bwd_row(t, 1);
-    else
-      for (int t = m + 2; t <= T - 1; ++t) bwd_row(t, -1);
   }
   __syncthreads();
   return ok;
