@@ -56,6 +56,7 @@ struct TrajSmem {
   // two-ended factorisation (B = 2): per-chain scratch and the four-row junction
   float cM[2][N][N];
   float cSch[2][NT];
+  float cP[2][NT];     // the next row's A_tt + lambda I - L2 L2^T
   float ctmp[2][8];
   float JD[4][NT];      // junction diagonal blocks after both chains' updates
   float JE[2][N][N];    // blocks (m-1, m-2) and (m, m+1) after the chains' updates
@@ -76,6 +77,26 @@ struct TrajSmem {
 struct Acc {
   float f, mind;
 };
+
+// Row and column (i >= j) of the packed lower-triangle index e: i counts the
+// row starts at or below e (no data-dependent loop, so the lanes of a warp,
+// each with its own e, stay together).  e < N(N+1)/2 for a valid pair.
+template <int N>
+__device__ __forceinline__ void tri_rc(int e, int& i, int& j) {
+  i = 0;
+#pragma unroll
+  for (int r = 1; r < N; ++r) i += (e >= tri(r, 0)) ? 1 : 0;
+  j = e - tri(i, 0);
+}
+
+// Element (a, b) of a packed lower-triangular N x N block, 0 above the
+// diagonal.  tri(a, b) < N(N+1)/2 for every a, b < N, so the load is made
+// unconditionally and lanes with different (a, b) do not branch apart.
+template <int N>
+__device__ __forceinline__ float ltri(const float* L, int a, int b) {
+  const float v = L[tri(a, b)];
+  return a >= b ? v : 0.f;
+}
 
 __device__ __forceinline__ float coll_act(float d, float eta, float* df) {
   if (d <= 0.f) {
@@ -419,10 +440,27 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
   // whole warp: lane i < N forms Jacobian entry i, lane e < N(N+1)/2 adds
   // J^T J entry e, lane i < N adds J^T r entry i
   constexpr int NT = N * (N + 1) / 2;
-  int ei = 0;
-  while ((ei + 1) * (ei + 2) / 2 <= lane) ++ei;
-  const int ek = lane - ei * (ei + 1) / 2;  // (ei, ek): this lane's J^T J entry when lane < NT
+  int ei, ek;
+  tri_rc<N>(lane, ei, ek);  // (ei, ek): this lane's J^T J entry when lane < NT
   unsigned lanes = __ballot_sync(0xffffffffu, amask != 0ull || aplane);
+  // lane i < N keeps joint i's world origin and axis; without swept rows
+  // (which other warps add into D_t and g_t) the timestep's J^T J entry and
+  // J^T r entry stay in registers across the pairs (the same summation order
+  // as adding each pair into shared memory)
+  float pj[3] = {0.f, 0.f, 0.f}, wj[3] = {0.f, 0.f, 0.f};
+  float dacc = 0.f, gacc = 0.f;
+  if (lanes) {
+    if (lane < N)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        pj[i] = S.p[t][lane][i];
+        wj[i] = S.w[t][lane][i];
+      }
+    if constexpr (!X) {
+      if (lane < NT) dacc = S.D[buf][t][lane];
+      if (lane < N) gacc = S.g[buf][t][lane];
+    }
+  }
   while (lanes) {
     const int src = __ffs(lanes) - 1;
     lanes &= lanes - 1;
@@ -465,28 +503,31 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
       // Jacobian entry i = lane: d(c)/d(q_i) = w_i x (c - p_i) for the joints of links 0..ls
       float ji = 0.f;
       if (lane < N && lane <= ls) {
-        const int i = lane;
         float dc;
-        if (rc.prism & (1u << i)) {
-          dc = S.w[t][i][0] * nrm[0] + S.w[t][i][1] * nrm[1] + S.w[t][i][2] * nrm[2];
+        if (rc.prism & (1u << lane)) {
+          dc = wj[0] * nrm[0] + wj[1] * nrm[1] + wj[2] * nrm[2];
         } else {
-          const float e0 = cs[0] - S.p[t][i][0], e1 = cs[1] - S.p[t][i][1], e2 = cs[2] - S.p[t][i][2];
+          const float e0 = cs[0] - pj[0], e1 = cs[1] - pj[1], e2 = cs[2] - pj[2];
           const float x0 = e1 * nrm[2] - e2 * nrm[1], x1 = e2 * nrm[0] - e0 * nrm[2], x2 = e0 * nrm[1] - e1 * nrm[0];
-          dc = S.w[t][i][0] * x0 + S.w[t][i][1] * x1 + S.w[t][i][2] * x2;
+          dc = wj[0] * x0 + wj[1] * x1 + wj[2] * x2;
         }
         ji = tp.w_coll * df * dc;
       }
       const float jei = __shfl_sync(0xffffffffu, ji, ei < N ? ei : 0);
       const float jek = __shfl_sync(0xffffffffu, ji, ek < N ? ek : 0);
-      // with swept rows other warps add into D_t and g_t too: atomics then
-      if (lane < NT) {
-        if constexpr (X) atomicAdd(&S.D[buf][t][lane], jei * jek);
-        else S.D[buf][t][lane] = fmaf(jei, jek, S.D[buf][t][lane]);
+      if constexpr (X) {
+        if (lane < NT) atomicAdd(&S.D[buf][t][lane], jei * jek);
+        if (lane < N) atomicAdd(&S.g[buf][t][lane], ji * r);
+      } else {
+        dacc = fmaf(jei, jek, dacc);
+        gacc = fmaf(ji, r, gacc);
       }
-      if (lane < N) {
-        if constexpr (X) atomicAdd(&S.g[buf][t][lane], ji * r);
-        else S.g[buf][t][lane] = fmaf(ji, r, S.g[buf][t][lane]);
-      }
+    }
+  }
+  if constexpr (!X) {
+    if (__any_sync(0xffffffffu, amask != 0ull || aplane)) {
+      if (lane < NT) S.D[buf][t][lane] = dacc;
+      if (lane < N) S.g[buf][t][lane] = gacc;
     }
   }
   // swept spheres (Sec. IV-A): the capsule of this lane's sphere from t to t+1
@@ -622,16 +663,15 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int 
         float v = 0.f;
 #pragma unroll
         for (int l = 0; l < N; ++l)
-          if (l <= j) v = fmaf(S.M[i][l], S.Linv[t - k][tri(j, l)], v);
+          v = fmaf(S.M[i][l], ltri<N>(S.Linv[t - k], j, l), v);
         S.L[k - 1][t][i][j] = v;
       }
       __syncthreads();
     }
     // Schur complement A_tt + lambda I - sum_k L_{t,t-k} L_{t,t-k}^T (lower)
     if (tid < NT) {
-      int i = 0;
-      while ((i + 1) * (i + 2) / 2 <= tid) ++i;
-      const int j = tid - i * (i + 1) / 2;
+      int i, j;
+      tri_rc<N>(tid, i, j);
       float v = S.D[buf][t][tid] + ((i == j) ? sb[0] + lam : 0.f);
 #pragma unroll
       for (int k = 1; k <= B; ++k)
@@ -661,7 +701,7 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int 
         float v = (i == j) ? 1.f : 0.f;
 #pragma unroll
         for (int k = 0; k < N; ++k)
-          if (k >= j && k < i) v = fmaf(-S.Sch[tri(i, k)], col[k], v);
+          if (k < i) v = fmaf(-S.Sch[tri(i, k)], col[k], v);
         col[i] = (i >= j) ? v * S.Sch[tri(i, i)] : 0.f;
       }
 #pragma unroll
@@ -687,7 +727,7 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int 
       float v = 0.f;
 #pragma unroll
       for (int k = 0; k < N; ++k)
-        if (k <= tid) v = fmaf(S.Linv[t][tri(tid, k)], S.tmp[k], v);
+        v = fmaf(ltri<N>(S.Linv[t], tid, k), S.tmp[k], v);
       S.y[t][tid] = v;
     }
     __syncthreads();
@@ -708,7 +748,7 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int 
       float v = 0.f;
 #pragma unroll
       for (int k = 0; k < N; ++k)
-        if (k >= tid) v = fmaf(S.Linv[t][tri(k, tid)], S.tmp[k], v);
+        v = fmaf(ltri<N>(S.Linv[t], k, tid), S.tmp[k], v);
       S.y[t][tid] = v;
     }
     __syncthreads();
@@ -722,8 +762,10 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int 
 // (t, t+1) blocks being transposes of the stored (t+1, t) ones); the four rows
 // m-2 .. m+1 between them (m = T / 2) take both sides' updates and are
 // factored last.  The serial chain is half as long as banded_solve's and the
-// solve is the same up to rounding order.  Factor blocks: L[0][t], L[1][t] are
-// row t against its first and second predecessor in its chain's order.
+// solve is the same up to rounding order.  Factor blocks: L[0][t] is row t
+// against its first predecessor in its chain's order; the block against the
+// second is a scalar times the transposed inverse factor of that row and is
+// never stored.
 template <int N, bool X>
 __device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int buf, float lam) {
   constexpr int NT = N * (N + 1) / 2, NN = N * N;
@@ -746,89 +788,158 @@ __device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int
   // dense factor of a Schur complement and its inverse into Linv[t]: each of
   // N threads factors the 7 x 7 block in its registers (the same arithmetic,
   // so no exchange or barrier is needed in between) and writes column lt of
-  // the inverse; `sync` is the barrier of the threads taking part
-  auto factor_diag = [&](const float* sch, int t, int lt, auto&& sync) {
-    if (lt < N) {
-      float L[NT];
+  // the inverse
+  auto factor_lane = [&](const float* sch, int t, int lt) {
+    float L[NT];
 #pragma unroll
-      for (int i = 0; i < NT; ++i) L[i] = sch[i];
-      const bool okf = chol_packed<N>(L);
-      if (lt == 0 && !okf) S.chol_fail = 1;
-      const int j = lt;
-      float col[N];
+    for (int i = 0; i < NT; ++i) L[i] = sch[i];
+    const bool okf = chol_packed<N>(L);
+    if (lt == 0 && !okf) S.chol_fail = 1;
+    float col[N];
 #pragma unroll
-      for (int i = 0; i < N; ++i) {
-        float v = (i == j) ? 1.f : 0.f;
+    for (int i = 0; i < N; ++i) {
+      float v = (i == lt) ? 1.f : 0.f;
 #pragma unroll
-        for (int k = 0; k < N; ++k)
-          if (k >= j && k < i) v = fmaf(-L[tri(i, k)], col[k], v);
-        col[i] = (i >= j) ? v * L[tri(i, i)] : 0.f;
-      }
-#pragma unroll
-      for (int i = 0; i < N; ++i)
-        if (i >= j) S.Linv[t][tri(i, j)] = col[i];
+      for (int k = 0; k < N; ++k)
+        if (k < i) v = fmaf(-L[tri(i, k)], col[k], v);
+      col[i] = (i >= lt) ? v * L[tri(i, i)] : 0.f;
     }
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i >= lt) S.Linv[t][tri(i, lt)] = col[i];
+  };
+  auto factor_diag = [&](const float* sch, int t, int lt, auto&& sync) {
+    if (lt < N) factor_lane(sch, t, lt);
     sync();
   };
-  // row t of a chain (direction d: +1 top-down, -1 bottom-up; k = its position
-  // in the chain).  mode 0: full; 1: up to the Schur complement, kept in
-  // JD[jd]; 2: the last row: its block against the previous row goes to
-  // JE[grp] (not divided by that row's factor, which the junction computes)
-  // and the Schur complement without it to JD[jd]
-  auto chain_row = [&](int t, int d, int k, int mode, int jd) {
+  // Chains.  Row t of a chain (direction d: +1 top-down, -1 bottom-up; k its
+  // position; predecessors p1 = t - d, p2 = t - 2d):
+  //   M_t  = A(t, p1) - L2_t L1_{p1}^T         (k >= 1)
+  //   P_t  = A_tt + lambda I - L2_t L2_t^T     (lower, packed)
+  //   L1_t = M_t Linv_{p1}^T,  Sch_t = P_t - L1_t L1_t^T,  factor Sch_t -> Linv_t
+  // with L1 the stored block against p1 (S.L[0][t]) and L2_t = c2 Linv_{p2}^T
+  // the block against p2 (A(t, p2) = c2 I, so it is formed where it is used).
+  // M and P need nothing of row p1's factor, so they are prepared one row
+  // ahead: each row takes two group barriers.  Phase 1: threads e < N(N+1)/2
+  // form Sch_t entry e from rows i, j of L1_t (the diagonal threads store
+  // them).  Phase 2: the group's first warp factors Sch_t while its second
+  // warp prepares M, P of the next row and the forward-substitution row of
+  // the previous one,
+  //   y_p1 = Linv_p1 (-g_p1 - L1_p1 y_{p1-d} - L2_p1 y_{p1-2d}).
+  // The chain's last two rows are not factored: the one before the last keeps
+  // its Schur complement in JD, the last its M in JE and its P in JD (the
+  // junction divides by their factors).
+  const unsigned fullm = 0xffffffffu;
+  auto c2_of = [&](int t, int d) { return d > 0 ? sc(t, t - 2) : sc(t + 2, t); };
+  // entry e < N*N of M_t and entry e < N(N+1)/2 of P_t
+  auto prep_m = [&](int t, int d, int k, int e, float* Mo) {
     const int p1 = t - d, p2 = t - 2 * d;
-    const float c2 = k >= 2 ? (d > 0 ? sc(t, p2) : sc(p2, t)) : 0.f;
-    float* Mc = mode == 2 ? &S.JE[grp][0][0] : &S.cM[grp][0][0];
-    if (k >= 1)
-      for (int e = gt; e < NN; e += 64) {
-        const int i = e / N, j = e % N;
-        float mm = a1(t, p1, i, j);
-        if (k >= 2) {
-          S.L[1][t][i][j] = (j >= i) ? c2 * S.Linv[p2][tri(j, i)] : 0.f;
+    const int i = e / N, j = e % N;
+    float mm = a1(t, p1, i, j);
+    if (k >= 2) {
+      float acc = 0.f;
 #pragma unroll
-          for (int q = 0; q < N; ++q)
-            if (q >= i) mm = fmaf(-c2 * S.Linv[p2][tri(q, i)], S.L[0][p1][j][q], mm);
-        }
-        Mc[e] = mm;
-      }
-    gsync();
-    if (mode != 2 && k >= 1) {
-      for (int e = gt; e < NN; e += 64) {
-        const int i = e / N, j = e % N;
-        float v = 0.f;
-#pragma unroll
-        for (int q = 0; q < N; ++q)
-          if (q <= j) v = fmaf(Mc[i * N + q], S.Linv[p1][tri(j, q)], v);
-        S.L[0][t][i][j] = v;
-      }
-      gsync();
+      for (int q = 0; q < N; ++q) acc = fmaf(ltri<N>(S.Linv[p2], q, i), S.L[0][p1][j][q], acc);
+      mm = fmaf(-c2_of(t, d), acc, mm);
     }
-    if (gt < NT) {
-      int i = 0;
-      while ((i + 1) * (i + 2) / 2 <= gt) ++i;
-      const int j = gt - i * (i + 1) / 2;
-      float v = S.D[buf][t][gt] + ((i == j) ? sc(t, t) + lam : 0.f);
-      if (mode != 2 && k >= 1)
-#pragma unroll
-        for (int q = 0; q < N; ++q) v = fmaf(-S.L[0][t][i][q], S.L[0][t][j][q], v);
-      if (k >= 2)
-#pragma unroll
-        for (int q = 0; q < N; ++q) v = fmaf(-S.L[1][t][i][q], S.L[1][t][j][q], v);
-      if (mode == 0) S.cSch[grp][gt] = v;
-      else S.JD[jd][gt] = v;
-    }
-    gsync();
-    if (mode == 0) factor_diag(S.cSch[grp], t, gt, gsync);
+    Mo[e] = mm;
   };
-  if (tid < 128) {
-    if (grp == 0) {
-      for (int t = 0; t <= m - 3; ++t) chain_row(t, 1, t, 0, 0);
-      chain_row(m - 2, 1, m - 2, 1, 0);
-      chain_row(m - 1, 1, m - 1, 2, 1);
-    } else {
-      for (int t = T - 1; t >= m + 2; --t) chain_row(t, -1, T - 1 - t, 0, 0);
-      chain_row(m + 1, -1, T - 2 - m, 1, 3);
-      chain_row(m, -1, T - 1 - m, 2, 2);
+  auto prep_p = [&](int t, int d, int k, int e, float* Po) {
+    const int p2 = t - 2 * d;
+    int i, j;
+    tri_rc<N>(e, i, j);
+    float v = S.D[buf][t][e] + ((i == j) ? sc(t, t) + lam : 0.f);
+    if (k >= 2) {
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < N; ++q) acc = fmaf(ltri<N>(S.Linv[p2], q, i), ltri<N>(S.Linv[p2], q, j), acc);
+      const float c2 = c2_of(t, d);
+      v = fmaf(-c2 * c2, acc, v);
+    }
+    Po[e] = v;
+  };
+  auto schur = [&](int t, int d, int k, float* out) {
+    int i, j;
+    tri_rc<N>(gt, i, j);
+    float v = S.cP[grp][gt];
+    if (k >= 1) {
+      const float* Mi = &S.cM[grp][i][0];
+      const float* Mj = &S.cM[grp][j][0];
+      const float* Li = S.Linv[t - d];
+      float ri[N], rj[N];
+#pragma unroll
+      for (int c = 0; c < N; ++c) {
+        float a = 0.f, b = 0.f;
+#pragma unroll
+        for (int q = 0; q <= c; ++q) {
+          const float l = Li[tri(c, q)];
+          a = fmaf(Mi[q], l, a);
+          b = fmaf(Mj[q], l, b);
+        }
+        ri[c] = a;
+        rj[c] = b;
+      }
+#pragma unroll
+      for (int c = 0; c < N; ++c) v = fmaf(-ri[c], rj[c], v);
+      if (i == j)
+#pragma unroll
+        for (int c = 0; c < N; ++c) S.L[0][t][i][c] = ri[c];
+    }
+    out[gt] = v;
+  };
+  // (L2_t y)_i for row t's block against p2: c2 sum_{q >= i} Linv_p2[q][i] y_q
+  auto l2y = [&](int p2, float c2, int i, const float* y) {
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+      acc = fmaf(ltri<N>(S.Linv[p2], q, i), y[q], acc);
+    return c2 * acc;
+  };
+  auto fwd_row = [&](int s, int d, int ks, int lane) {
+    const int li = lane < N ? lane : 0;
+    float v = -S.g[buf][s][li];
+    if (ks >= 1)
+#pragma unroll
+      for (int q = 0; q < N; ++q) v = fmaf(-S.L[0][s][li][q], S.y[s - d][q], v);
+    if (ks >= 2) v -= l2y(s - 2 * d, c2_of(s, d), li, S.y[s - 2 * d]);
+    float yv = 0.f;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      const float vq = __shfl_sync(fullm, v, q);
+      yv = fmaf(ltri<N>(S.Linv[s], li, q), vq, yv);
+    }
+    if (lane < N) S.y[s][lane] = yv;
+  };
+  {
+    // four warps per chain: the group's two warps (A: threads 0-31 of the
+    // group, B: 32-63) and two of threads 128-255 (C, D); barrier 3 + grp
+    // spans the 128 threads of a chain
+    const int d = grp == 0 ? 1 : -1, t0 = grp == 0 ? 0 : T - 1;
+    const int nf = grp == 0 ? m - 2 : T - m - 2;  // rows factored in the chain
+    const int jd1 = grp == 0 ? 0 : 3, jd2 = grp == 0 ? 1 : 2;
+    static_assert(kThreads == 256, "the two-ended solve runs each chain on four warps");
+    const int lane = tid & 31, wsub = ((tid >> 7) << 1) | ((tid >> 5) & 1);
+    auto csync = [&] { asm volatile("bar.sync %0, 128;" ::"r"(3 + grp) : "memory"); };
+    if (wsub == 2 && lane < NT) prep_p(t0, d, 0, lane, S.cP[grp]);
+    csync();
+    for (int k = 0; k <= nf; ++k) {
+      const int t = t0 + k * d;
+      if (wsub == 0 && lane < NT) schur(t, d, k, k < nf ? S.cSch[grp] : S.JD[jd1]);
+      csync();
+      // A: factor row t; B, C: M and P of row t + d; D: forward row t - d
+      float* Mo = k + 1 <= nf ? &S.cM[grp][0][0] : &S.JE[grp][0][0];
+      float* Po = k + 1 <= nf ? S.cP[grp] : S.JD[jd2];
+      if (wsub == 0) {
+        if (k < nf && lane < N) factor_lane(S.cSch[grp], t, lane);
+      } else if (wsub == 1) {
+        prep_m(t + d, d, k + 1, lane, Mo);
+      } else if (wsub == 2) {
+        if (lane < NN - 32) prep_m(t + d, d, k + 1, 32 + lane, Mo);
+        if (lane < NT) prep_p(t + d, d, k + 1, lane, Po);
+      } else {
+        if (k >= 1) fwd_row(t - d, d, k - 1, lane);
+      }
+      csync();
     }
   }
   __syncthreads();
@@ -845,7 +956,7 @@ __device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int
             S.JL2[j][r][c] = (c >= r) ? c2 * S.Linv[t - 2][tri(c, r)] : 0.f;
 #pragma unroll
             for (int q = 0; q < N; ++q)
-              if (q >= r) mm = fmaf(-c2 * S.Linv[t - 2][tri(q, r)], S.JL1[j - 1][c][q], mm);
+              mm = fmaf(-c2 * ltri<N>(S.Linv[t - 2], q, r), S.JL1[j - 1][c][q], mm);
           }
           S.cM[0][r][c] = mm;
         }
@@ -855,15 +966,14 @@ __device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int
           float v = 0.f;
 #pragma unroll
           for (int q = 0; q < N; ++q)
-            if (q <= c) v = fmaf(S.cM[0][r][q], S.Linv[t - 1][tri(c, q)], v);
+            v = fmaf(S.cM[0][r][q], ltri<N>(S.Linv[t - 1], c, q), v);
           S.JL1[j][r][c] = v;
         }
         gsync();
       }
       if (gt < NT) {
-        int r = 0;
-        while ((r + 1) * (r + 2) / 2 <= gt) ++r;
-        const int c = gt - r * (r + 1) / 2;
+        int r, c;
+        tri_rc<N>(gt, r, c);
         float v = S.JD[j][gt];
         if (j >= 1)
 #pragma unroll
@@ -879,49 +989,22 @@ __device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int
   }
   __syncthreads();
   const bool ok = S.chol_fail == 0;
-  // forward substitution in each chain, y_t = Linv_t (-g_t - L[0][t] y_p1 - L[1][t] y_p2),
-  // by the chain's first warp alone: lane i < N holds component i of y_t and
-  // of the two rows before it in registers and the other components come by
-  // shuffle, so the rows need no barrier
-  const unsigned fullm = 0xffffffffu;
-  if (tid < 128 && gt < 32) {
-    const int d = grp == 0 ? 1 : -1;
-    const int t0 = grp == 0 ? 0 : T - 1, len = grp == 0 ? m - 2 : T - m - 2;
-    const int li = gt < N ? gt : 0;
-    float y1 = 0.f, y2 = 0.f;  // this lane's components of y_{t-d}, y_{t-2d}
-    for (int k = 0; k < len; ++k) {
-      const int t = t0 + k * d;
-      float v = gt < N ? -S.g[buf][t][li] : 0.f;
-#pragma unroll
-      for (int q = 0; q < N; ++q) {
-        const float a1v = __shfl_sync(fullm, y1, q), a2v = __shfl_sync(fullm, y2, q);
-        if (k >= 1) v = fmaf(-S.L[0][t][li][q], a1v, v);
-        if (k >= 2) v = fmaf(-S.L[1][t][li][q], a2v, v);
-      }
-      float yv = 0.f;
-#pragma unroll
-      for (int q = 0; q < N; ++q) {
-        const float vq = __shfl_sync(fullm, v, q);
-        if (q <= li) yv = fmaf(S.Linv[t][tri(li, q)], vq, yv);
-      }
-      if (gt < N) S.y[t][gt] = yv;
-      y2 = y1;
-      y1 = yv;
-    }
-  }
-  __syncthreads();
   // junction: right-hand sides from both chains, forward, then backward
   if (tid < 64) {
     for (int j = 0; j < 4; ++j) {
       const int t = m - 2 + j;
       if (gt < N) {
         float v = -S.g[buf][t][gt];
+        // blocks against the chains' rows: the stored (t, t -+ 1) ones of the
+        // outer junction rows, and (t, t -+ 2) formed from the chains' Linv
+        if (j == 0) v -= l2y(m - 4, c2_of(m - 2, 1), gt, S.y[m - 4]);
+        if (j == 1) v -= l2y(m - 3, c2_of(m - 1, 1), gt, S.y[m - 3]);
+        if (j == 2) v -= l2y(m + 2, c2_of(m, -1), gt, S.y[m + 2]);
+        if (j == 3) v -= l2y(m + 3, c2_of(m + 1, -1), gt, S.y[m + 3]);
 #pragma unroll
         for (int q = 0; q < N; ++q) {
-          if (j == 0) v = fmaf(-S.L[0][t][gt][q], S.y[m - 3][q], fmaf(-S.L[1][t][gt][q], S.y[m - 4][q], v));
-          if (j == 1) v = fmaf(-S.L[1][t][gt][q], S.y[m - 3][q], v);
-          if (j == 2) v = fmaf(-S.L[1][t][gt][q], S.y[m + 2][q], v);
-          if (j == 3) v = fmaf(-S.L[0][t][gt][q], S.y[m + 2][q], fmaf(-S.L[1][t][gt][q], S.y[m + 3][q], v));
+          if (j == 0) v = fmaf(-S.L[0][t][gt][q], S.y[m - 3][q], v);
+          if (j == 3) v = fmaf(-S.L[0][t][gt][q], S.y[m + 2][q], v);
           if (j >= 1) v = fmaf(-S.JL1[j][gt][q], S.y[t - 1][q], v);
           if (j >= 2) v = fmaf(-S.JL2[j][gt][q], S.y[t - 2][q], v);
         }
@@ -932,7 +1015,7 @@ __device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int
         float v = 0.f;
 #pragma unroll
         for (int q = 0; q < N; ++q)
-          if (q <= gt) v = fmaf(S.Linv[t][tri(gt, q)], S.ctmp[0][q], v);
+          v = fmaf(ltri<N>(S.Linv[t], gt, q), S.ctmp[0][q], v);
         S.y[t][gt] = v;
       }
       gsync();
@@ -953,7 +1036,7 @@ __device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int
         float v = 0.f;
 #pragma unroll
         for (int q = 0; q < N; ++q)
-          if (q >= gt) v = fmaf(S.Linv[t][tri(q, gt)], S.ctmp[0][q], v);
+          v = fmaf(ltri<N>(S.Linv[t], q, gt), S.ctmp[0][q], v);
         S.y[t][gt] = v;
       }
       gsync();
@@ -961,8 +1044,10 @@ __device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int
   }
   __syncthreads();
   // backward substitution in each chain, from the junction outwards,
-  // x_t = Linv_t^T (y_t - L[0][t+d]^T x_{t+d} - L[1][t+2d]^T x_{t+2d}), by the
-  // chain's first warp with the two later rows' x in registers (as above)
+  // x_t = Linv_t^T (y_t - L1_{t+d}^T x_{t+d} - L2_{t+2d}^T x_{t+2d}), by the
+  // chain's first warp: lane i < N holds component i of the two later rows'
+  // x in registers and the other components come by shuffle, so the rows
+  // need no barrier
   if (tid < 128 && gt < 32) {
     const int d = grp == 0 ? 1 : -1;
     const int tb = grp == 0 ? m - 3 : m + 2, len = grp == 0 ? m - 2 : T - m - 2;
@@ -971,16 +1056,20 @@ __device__ bool twisted_solve(const TrajParamsDev& tp, TrajSmem<N, 2, X>& S, int
     for (int k = 0; k < len; ++k) {
       const int t = tb - k * d;
       float v = gt < N ? S.y[t][li] : 0.f;
+      // L2_{t+2d}^T x_{t+2d} = c2 Linv_t x_{t+2d}
+      float w2 = 0.f;
 #pragma unroll
       for (int q = 0; q < N; ++q) {
         const float a1v = __shfl_sync(fullm, x1, q), a2v = __shfl_sync(fullm, x2, q);
-        v = fmaf(-S.L[0][t + d][q][li], a1v, fmaf(-S.L[1][t + 2 * d][q][li], a2v, v));
+        v = fmaf(-S.L[0][t + d][q][li], a1v, v);
+        w2 = fmaf(ltri<N>(S.Linv[t], li, q), a2v, w2);
       }
+      v = fmaf(-c2_of(t + 2 * d, d), w2, v);
       float xv = 0.f;
 #pragma unroll
       for (int q = 0; q < N; ++q) {
         const float vq = __shfl_sync(fullm, v, q);
-        if (q >= li) xv = fmaf(S.Linv[t][tri(q, li)], vq, xv);
+        xv = fmaf(ltri<N>(S.Linv[t], q, li), vq, xv);
       }
       if (gt < N) S.y[t][gt] = xv;
       x2 = x1;
@@ -1021,11 +1110,6 @@ __device__ bool twisted_solve_b(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, i
       if (hi - lo == 1) v += (t > u) ? S.E[buf][t][i][j] : S.E[buf][u][j][i];
     return v;
   };
-  auto tri_rc = [&](int e, int& r, int& c) {
-    r = 0;
-    while ((r + 1) * (r + 2) / 2 <= e) ++r;
-    c = e - r * (r + 1) / 2;
-  };
   // dense factor of a Schur complement (one thread), its inverse into Linv[t]
   auto factor_diag = [&](float* sch, int t) {
     if (gt == 0) {
@@ -1045,7 +1129,7 @@ __device__ bool twisted_solve_b(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, i
         float v = (i == j) ? 1.f : 0.f;
 #pragma unroll
         for (int k = 0; k < N; ++k)
-          if (k >= j && k < i) v = fmaf(-sch[tri(i, k)], col[k], v);
+          if (k < i) v = fmaf(-sch[tri(i, k)], col[k], v);
         col[i] = (i >= j) ? v * sch[tri(i, i)] : 0.f;
       }
 #pragma unroll
@@ -1081,7 +1165,7 @@ __device__ bool twisted_solve_b(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, i
         float v = 0.f;
 #pragma unroll
         for (int q = 0; q < N; ++q)
-          if (q <= c) v = fmaf(S.cM[grp][r][q], S.Linv[pj][tri(c, q)], v);
+          v = fmaf(S.cM[grp][r][q], ltri<N>(S.Linv[pj], c, q), v);
         S.L[j - 1][t][r][c] = v;
       }
       gsync();
@@ -1093,7 +1177,7 @@ __device__ bool twisted_solve_b(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, i
     if (jhi >= 1) row_blocks(t, d, 1, jhi);
     if (gt < NT) {
       int r, c;
-      tri_rc(gt, r, c);
+      tri_rc<N>(gt, r, c);
       float v = S.D[buf][t][gt] + ((r == c) ? sc(t, t) + lam : 0.f);
       for (int j = 1; j <= jhi; ++j)
 #pragma unroll
@@ -1152,14 +1236,14 @@ __device__ bool twisted_solve_b(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, i
           float v = 0.f;
 #pragma unroll
           for (int q = 0; q < N; ++q)
-            if (q <= c) v = fmaf(S.cM[0][r][q], S.Linv[j0 + b][tri(c, q)], v);
+            v = fmaf(S.cM[0][r][q], ltri<N>(S.Linv[j0 + b], c, q), v);
           S.JLb[k - 1][a][r][c] = v;
         }
         gsync();
       }
       if (gt < NT) {
         int r, c;
-        tri_rc(gt, r, c);
+        tri_rc<N>(gt, r, c);
         float v = S.D[buf][ia][gt] + ((r == c) ? sc(ia, ia) + lam : 0.f) + gblock(a, a, r, c);
         for (int k = 1; k <= kmax; ++k)
 #pragma unroll
@@ -1180,7 +1264,7 @@ __device__ bool twisted_solve_b(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, i
       float v = 0.f;
 #pragma unroll
       for (int q = 0; q < N; ++q)
-        if (q <= gt) v = fmaf(S.Linv[t][tri(gt, q)], S.ctmp[grp][q], v);
+        v = fmaf(ltri<N>(S.Linv[t], gt, q), S.ctmp[grp][q], v);
       S.y[t][gt] = v;
     }
     gsync();
@@ -1192,7 +1276,7 @@ __device__ bool twisted_solve_b(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, i
       float v = 0.f;
 #pragma unroll
       for (int q = 0; q < N; ++q)
-        if (q >= gt) v = fmaf(S.Linv[t][tri(q, gt)], S.ctmp[grp][q], v);
+        v = fmaf(ltri<N>(S.Linv[t], q, gt), S.ctmp[grp][q], v);
       S.y[t][gt] = v;
     }
     gsync();
