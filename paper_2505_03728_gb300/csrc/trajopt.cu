@@ -68,6 +68,7 @@ struct TrajSmem {
   float sbt[kTrajMaxT][B + 1];  // smoothness scalars of blocks (t, t-k) (two-ended solves)
   alignas(16) float obs[kTrajMaxObs][4];
   float rad[N][kTrajMaxS];
+  float rmax[N];  // largest sphere radius of each link
   float qs[8];
   float Tgi[12];
   float red_f[kWarps], red_d[kWarps];
@@ -398,11 +399,12 @@ __device__ __forceinline__ void coll_jrow(const ChainC<N>& rc, const TrajSmem<N,
 }
 
 // Collision terms of timestep t, one link sphere per lane (lanes >= N*S idle).
-// Screening tests every (sphere, obstacle) pair on squared distances (no
-// square root): |c - o|^2 < (r + r_o + eta)^2 marks the pair active in a bit
-// mask, and mind keeps a quantity with the sign of the smallest signed
-// distance (|c - o|^2 - (r + r_o)^2; the plane's distance itself), all the
-// collision status needs.  Then the active pairs, lane by lane in lane order
+// Screening tests the (sphere, obstacle) pairs that pass a per-link broad
+// phase on squared distances (no square root): |c - o|^2 < (r + r_o + eta)^2
+// marks the pair active in a bit mask, and mind keeps a quantity with the
+// sign of the smallest signed distance (|c - o|^2 - (r + r_o)^2 over the
+// tested pairs, all others being farther than eta; the plane's distance
+// itself), all the collision status needs.  Then the active pairs, lane by lane in lane order
 // (a fixed summation order), are processed by the whole warp, which adds each
 // row's cost, J^T r and J^T J contributions straight into timestep t's
 // blocks.
@@ -414,15 +416,55 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
   bool aplane = false;
   float c[3] = {0.f, 0.f, 0.f}, rad = 0.f;
   int l = 0;
+  if (lane < nsph) l = lane / tp.S;
+  // broad phase: lane l < N forms link l's bounding sphere (its spheres'
+  // centres lie on the segment p_l -> p_{l+1}: centre at the midpoint, radius
+  // half the length plus the largest sphere radius), then lane o tests
+  // obstacle o (and o + 32) against every link's bound.  A sphere can only
+  // come within r + r_o + eta of an obstacle its link's bound comes within
+  // r_o + eta of; the bound is widened by a relative 1e-5 so that rounding
+  // cannot drop such a pair, and the exact test below decides every pair that
+  // passes, so the active pairs are those of testing all of them.
+  float bm[3] = {0.f, 0.f, 0.f}, bh = 0.f;
+  if (lane < N) {
+    float e2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float a = S.p[t][lane][i], b = S.p[t][lane + 1][i];
+      bm[i] = 0.5f * (a + b);
+      e2 = fmaf(b - a, b - a, e2);
+    }
+    bh = 0.5f * sqrtf(e2) + S.rmax[lane] + tp.eta;
+  }
+  const bool two = tp.n_obs > 32;
+  float4 ob0 = make_float4(0.f, 0.f, 0.f, 0.f), ob1 = ob0;
+  if (lane < tp.n_obs) ob0 = *reinterpret_cast<const float4*>(S.obs[lane]);
+  if (two && lane + 32 < tp.n_obs) ob1 = *reinterpret_cast<const float4*>(S.obs[lane + 32]);
+  unsigned long long cand = 0ull;  // candidate obstacles of this lane's link
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const float mx = __shfl_sync(0xffffffffu, bm[0], k), my = __shfl_sync(0xffffffffu, bm[1], k),
+                mz = __shfl_sync(0xffffffffu, bm[2], k), h = __shfl_sync(0xffffffffu, bh, k);
+    float v0 = ob0.x - mx, v1 = ob0.y - my, v2 = ob0.z - mz;
+    float th = fmaf(h + ob0.w, 1.00001f, 1e-6f);
+    const unsigned lo = __ballot_sync(0xffffffffu, lane < tp.n_obs && fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) < th * th);
+    unsigned hi = 0u;
+    if (two) {
+      v0 = ob1.x - mx; v1 = ob1.y - my; v2 = ob1.z - mz;
+      th = fmaf(h + ob1.w, 1.00001f, 1e-6f);
+      hi = __ballot_sync(0xffffffffu, lane + 32 < tp.n_obs && fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) < th * th);
+    }
+    if (l == k) cand = ((unsigned long long)hi << 32) | lo;
+  }
   if (lane < nsph) {
-    l = lane / tp.S;
     const int s = lane % tp.S;
     const float al = (s + 0.5f) / (float)tp.S;
 #pragma unroll
     for (int i = 0; i < 3; ++i) c[i] = fmaf(al, S.p[t][l + 1][i] - S.p[t][l][i], S.p[t][l][i]);
     rad = S.rad[l][s];
-#pragma unroll 4
-    for (int o = 0; o < tp.n_obs; ++o) {
+    while (cand) {
+      const int o = __ffsll(cand) - 1;
+      cand &= cand - 1;
       const float4 ob = *reinterpret_cast<const float4*>(S.obs[o]);
       const float v0 = c[0] - ob.x, v1 = c[1] - ob.y, v2 = c[2] - ob.z;
       const float dd = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
@@ -1367,6 +1409,11 @@ __global__ void __launch_bounds__(kThreads, (B == 2 && !X) ? 3 : 2) trajopt_kern
   for (int i = tid; i < T * N; i += kThreads) S.x[0][i / N][i % N] = q_init[(size_t)b * T * N + i];
   for (int i = tid; i < tp.n_obs * 4; i += kThreads) S.obs[i / 4][i % 4] = obs[i];
   for (int i = tid; i < N * tp.S; i += kThreads) S.rad[i / tp.S][i % tp.S] = radii[i];
+  if (tid < N) {
+    float r = 0.f;
+    for (int k = 0; k < tp.S; ++k) r = fmaxf(r, radii[tid * tp.S + k]);
+    S.rmax[tid] = r;
+  }
   if (tid < N) S.qs[tid] = q_start[(size_t)b * N + tid];
   if (tid == 0) {
     Rt G, Gi;
