@@ -52,16 +52,24 @@ FLOPS_PER_EVAL = 975.1
 FLOPS_PER_BUILD = 1818.9
 FLOPS_PER_SOLVE = 252.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
-# DRAM bytes (read + write) per target of the LM kernel: ncu capture of the
-# 16,384-target learned-seed launch (4.626 MB), inputs read once (see profiles/).
-LM_DRAM_BYTES_PER_TARGET = 4625664 / 16384
-MLP_DRAM_BYTES_65536 = 4952832.0  # mlp_fused_kernel, dram__bytes_read.sum + write.sum per launch
+# DRAM bytes (read + write) per target of the first LM launch: ncu capture of
+# this benchmark's own learned steps at 65,536 targets x 8 seeds (36.3 MB per
+# launch, the mean of the two timed steps; profiles/ has the launch list).
+LM_DRAM_BYTES_PER_TARGET = (27434240 + 9253888 + 27069184 + 8891648) / 2 / 65536
+# mlp_fused_kernel, dram__bytes_read.sum + write.sum per launch at 65,536
+# targets: mean of the two timed steps of the same capture
+MLP_DRAM_BYTES_65536 = (4965120 + 256 + 4954880 + 256) / 2
 # Algorithmic FLOPs of the trajectory workload (T = 64, 32 obstacles + plane),
 # same census: per trajectory-iteration one candidate evaluation, one damped
 # block-banded solve and, at the oracle's accept rate, one normal-equation
 # build; per trajectory the initial evaluation and build.
 TRAJ_FLOPS_PER_ITER = 1.0631e6
 TRAJ_FLOPS_PER_INIT = 0.8959e6
+# DRAM bytes (read + write) per trajectory of trajopt_kernel<7, 2, false>: ncu
+# capture of the first 64 trajectories (0.301 MB per launch); each
+# trajectory's inputs and outputs are read and written once, so the launch's
+# traffic scales with the trajectories it solves.
+TRAJ_DRAM_BYTES_PER_TRAJ = (300032 + 1280) / 64
 # Every timed step reads its own input batch; an arm rotates through enough
 # batches to hold at least this many bytes (twice the 129 MB L2).
 ROTATE_BYTES = 256 << 20
@@ -518,7 +526,8 @@ def extra_workloads(torch, pk, synth, args, flush, stream, chain_net=None):
                                 "all of it timed"),
                       "ik_converged": ik_conv,
                       "roofline": {"bound": "alu", "kernel": "trajopt_kernel<7, 2, false>", "achieved": t_tf,
-                                   "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": t_tf / FP32_PEAK_TFLOPS},
+                                   "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": t_tf / FP32_PEAK_TFLOPS,
+                                   "traffic": TRAJ_DRAM_BYTES_PER_TRAJ * Bt},
                       "goal_reached": float(np.mean((st & pk.PK_T_GOAL_MISSED) == 0)),
                       "collision_free": float(np.mean((st & pk.PK_T_COLLISION) == 0)),
                       "config": {"T": Tt, "iters": cfg["iters"], "obstacles": cfg["n_obstacles"],
@@ -848,18 +857,18 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    def lm_roofline(r):
+    def lm_roofline(r, learned=True):
         st = r["stats"]
         fl = st["evals"] * FLOPS_PER_EVAL + st["builds"] * FLOPS_PER_BUILD + st["solves"] * FLOPS_PER_SOLVE
         tf = fl / (r["lm_ms"] / 1e3) / 1e12
         return {"bound": "alu", "kernel": "chain_lm_kernel<7, 1> (first launch of the split solve)",
                 "achieved": tf, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": tf / FP32_PEAK_TFLOPS, "traffic": LM_DRAM_BYTES_PER_TARGET * B,
+                "unit": "TFLOP/s", "frac": tf / FP32_PEAK_TFLOPS, "traffic": LM_DRAM_BYTES_PER_TARGET * B if (learned and B == 65536) else None,
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (unit counts x max clock)",
                 "ms_per_launch": r["lm_ms"], "work_per_launch": st}
 
     r = results[head]
-    roofs = [lm_roofline(r)]
+    roofs = [lm_roofline(r, learned=head == "learned")]
     if head == "learned":
         peak, src = measured_bf16_peak()
         fl = seednet_flops(9, 512, 4, 8 * 7, B)
@@ -881,7 +890,7 @@ def main():
         "success_rate": r["success_rate"],
         "plain": dict({k: results["plain"][k] for k in ("value", "ms_per_step", "success_rate", "lm_ms",
                                                          "lm_tail_ms", "serial")},
-                      roofline=lm_roofline(results["plain"])),
+                      roofline=lm_roofline(results["plain"], learned=False)),
         "roofline": dominant,
         "roofline_other": [x for x in roofs if x is not dominant],
         "e2e": {"value": e2e_conv / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
