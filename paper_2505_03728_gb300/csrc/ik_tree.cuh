@@ -50,7 +50,6 @@ struct TreeWarpSmem {
   float th[kTreeMaxTargets];
   float q[kTreeMaxDof];           // configuration being evaluated
   float L[kTreeMaxDof][kTreeMaxDof + 1];  // Cholesky factor, row i by lane i (padded rows)
-  float dinv[kTreeMaxDof];        // reciprocal diagonal of L
   // self-collision pairs of the candidate: residual w f(d), slope w f'(d),
   // unit direction c_a - c_b and the two sphere centres (world)
   float pr[kMaxPairs], ps[kMaxPairs];
@@ -330,50 +329,49 @@ __device__ __forceinline__ void tree_normal(const RobotDev* __restrict__ rb, con
 
 // Solve (A + lam I) x = -g for the n x n system held row-per-lane (Arow on
 // lane i is row i); returns false on a non-positive pivot.  The factor lives
-// in shared memory so that every loop below stays rolled (small code): step k
-// of the right-looking Cholesky scales column k and lane i updates its row
-// with column k broadcast from shared memory; the substitutions broadcast one
-// unknown per step.  x comes back on lane i.
+// in shared memory so that every loop below stays rolled (small code).  The
+// Cholesky runs left-looking (Crout order): step k forms column k, lane i its
+// entry A_ik - sum_{j<k} L_ij L_kj from its own row and row k (broadcast),
+// both already final, so the loop only loads and accumulates in a register
+// (the same products in the same order as updating the trailing matrix after
+// every column), and every lane runs the same k terms.  The substitutions
+// broadcast one unknown per step.  x comes back on lane i.
 template <int N>
 __device__ __forceinline__ bool tree_solve(const float (&Arow)[N], float g, float lam, int n, int lane, float& x,
                                            TreeWarpSmem& sm) {
 #pragma unroll
   for (int j = 0; j < N; ++j) sm.L[lane][j] = Arow[j] + ((j == lane) ? lam : 0.f);
   __syncwarp();
+  // The forward substitution L y = -g runs inside the same loop: once column
+  // k is formed, lane k's right-hand side is final, y_k is broadcast and the
+  // lanes below take their term of it.
   bool ok = true;
+  float b = -g, y = 0.f, dinv = 0.f;  // dinv: lane k's 1 / L_kk
 #pragma unroll 1
   for (int k = 0; k < n; ++k) {
-    const float d = sm.L[k][k];
+    float v = sm.L[lane][k];  // A_ik: entries k.. of row i are untouched so far
+#pragma unroll 4
+    for (int j = 0; j < k; ++j) v = fmaf(-sm.L[lane][j], sm.L[k][j], v);
+    const float d = __shfl_sync(kTreeFull, v, k);
     ok = ok && (d > 0.f) && (d < INFINITY);
     const float inv = rsqrtf(d);
-    __syncwarp();
+    const float lik = v * inv;
     if (lane == k) {
       sm.L[k][k] = d * inv;
-      sm.dinv[k] = inv;
+      dinv = inv;
     } else if (lane > k && lane < n) {
-      sm.L[lane][k] *= inv;
+      sm.L[lane][k] = lik;
     }
-    __syncwarp();
-    if (lane > k && lane < n) {
-      const float lik = sm.L[lane][k];
-#pragma unroll 1
-      for (int j = k + 1; j <= lane; ++j) sm.L[lane][j] = fmaf(-lik, sm.L[j][k], sm.L[lane][j]);
-    }
-    __syncwarp();
-  }
-  // forward: L y = -g
-  float b = -g, y = 0.f;
-#pragma unroll 1
-  for (int k = 0; k < n; ++k) {
-    const float yk = __shfl_sync(kTreeFull, b * sm.dinv[k], k);
+    const float yk = __shfl_sync(kTreeFull, b * inv, k);
     if (lane == k) y = yk;
-    if (lane > k && lane < n) b = fmaf(-sm.L[lane][k], yk, b);
+    if (lane > k && lane < n) b = fmaf(-lik, yk, b);
+    __syncwarp();
   }
   // backward: L^T x = y (row k of L, read by column, holds L[k][i] for lane i)
   float yr = y, xv = 0.f;
 #pragma unroll 1
   for (int k = n - 1; k >= 0; --k) {
-    const float xk = __shfl_sync(kTreeFull, yr * sm.dinv[k], k);
+    const float xk = __shfl_sync(kTreeFull, yr * dinv, k);
     if (lane == k) xv = xk;
     if (lane < k) yr = fmaf(-sm.L[k][lane], xk, yr);
   }
