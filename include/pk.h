@@ -635,6 +635,36 @@ pk_status pk_seednet_refine(pk_seednet* net, int32_t n, int32_t max_iters, uint6
 pk_status pk_seednet_pool(const pk_seednet* net, float* d_targets_out, float* d_labels_out, int32_t* n_out,
                           void* stream);
 
+/*
+ * Index checks.  The paper has no counterpart: these serve testing.  The
+ * library built with -DPK_DEBUG_BOUNDS (libpk_debug.so, from
+ * paper_2505_03728_gb300/build.py with debug_bounds=True) checks the indices
+ * its kernels derive from run-time data (queue claims and resumed records,
+ * tree joint, parent and target lists, kept and chosen seeds, obstacle
+ * indices) and skips an access whose index is out of range, recording the
+ * first such failure; nothing traps.  The default build compiles the checks
+ * out.
+ *
+ * pk_debug_bounds_enabled: 1 in the checked build, 0 otherwise.
+ * pk_debug_bounds_take: synchronizes the device; *code receives the first
+ *   failed check since the last call, (site << 48) | (bound << 24) | index
+ *   (bound clipped to 2^24 - 1, index to 2^24 - 2, a negative index as
+ *   2^24 - 1), 0 if none, and the record is cleared.  Sites: 1 chain queue
+ *   record index, 2 chain queue target index, 3 tree record index, 4 tree
+ *   joint, parent or variable index, 5 tree target link or variable joint,
+ *   6 best-seed record,
+ *   7 IK-Beam kept seed, 8 trajectory obstacle, 9 collision-free seed
+ *   record, 15 the self-test.
+ *   PK_ERR_UNSUPPORTED (and *code = 0) in the default build.
+ * pk_debug_bounds_selftest: enqueues on `stream` one check that fails at site
+ *   15 with index n against bound n, in a kernel that addresses nothing with
+ *   it, so that the status path itself can be tested.  PK_ERR_UNSUPPORTED in
+ *   the default build.
+ */
+int32_t pk_debug_bounds_enabled(void);
+pk_status pk_debug_bounds_take(uint64_t* code);
+pk_status pk_debug_bounds_selftest(int32_t n, void* stream);
+
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char* pk_last_error(void);
 

@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(128) beam_select_kernel(const float* __restric
       }
     }
     const int sel = bi;  // S1 >= keep, so some seed is always left
+    if (!PK_IN_BOUNDS(sel, S1, kSiteBeamKeep)) continue;  // the same on every lane
     if ((sel & 31) == lane) taken |= 1u << (sel >> 5);
     const size_t dst = (size_t)b * keep + r;
     const float* src = rb + (size_t)sel * stride;

@@ -445,6 +445,7 @@ __global__ void ik_reduce_kernel(const float* __restrict__ rec, int n, int strid
       best_f = fv;
     }
   }
+  if (!PK_IN_BOUNDS(best, n_seeds, kSiteReduceRec)) return;
   const float* r = rec + ((size_t)b * n_seeds + best) * stride;
   for (int j = 0; j < n; ++j) q_out[(size_t)b * n + j] = r[j];
   err_out[2 * (size_t)b] = r[np + 1];

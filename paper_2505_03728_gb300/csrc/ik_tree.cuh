@@ -73,12 +73,14 @@ __device__ __forceinline__ void tree_fk(const RobotDev* __restrict__ rb, const T
   for (int l = 0; l < ti.n_levels; ++l) {
     for (int idx = ti.level_start[l] + lane; idx < ti.level_start[l + 1]; idx += 32) {
       const int j = ti.order[idx];
+      if (!PK_IN_BOUNDS(j, kMaxJoints, kSiteTreeParent)) continue;
       Rt O, X, Lm;
       rt_load(rb->origin[j], O);
       rt_identity(X);
       const int t = rb->type[j];
       if (t != PK_JOINT_FIXED) {
-        const float qv = fmaf(rb->mult[j], sm.q[rb->var[j]], rb->offs[j]);
+        const int v = rb->var[j];
+        const float qv = PK_IN_BOUNDS(v, kTreeMaxDof, kSiteTreeParent) ? fmaf(rb->mult[j], sm.q[v], rb->offs[j]) : 0.f;
         const float* a = rb->axis[j];
         if (t == PK_JOINT_REVOLUTE) {
           float u[3] = {a[0], a[1], a[2]}, s, c;
@@ -90,7 +92,7 @@ __device__ __forceinline__ void tree_fk(const RobotDev* __restrict__ rb, const T
       }
       rt_mul(O, X, Lm);
       const int p = rb->parent[j];
-      if (p >= 0) {
+      if (p >= 0 && PK_IN_BOUNDS(p, kMaxJoints, kSiteTreeParent)) {
         Rt Tp;
         rt_load(sm.frames[p], Tp);
         rt_mul(Tp, Lm, Lm);
@@ -107,7 +109,7 @@ __device__ __forceinline__ float tree_eval(const RobotDev* __restrict__ rb, cons
                                            const LmParams& lp, TreeWarpSmem& sm, int lane, float& pe, float& re) {
   tree_fk(rb, ti, sm, lane);
   float acc = 0.f, mpe = 0.f, mre = 0.f;
-  if (lane < ti.k) {
+  if (lane < ti.k && PK_IN_BOUNDS(ti.links[lane], kMaxJoints, kSiteTreeLink)) {
     Rt Tl, Ti, E;
     rt_load(sm.frames[ti.links[lane]], Tl);
     rt_load(sm.Ti[lane], Ti);
@@ -244,9 +246,10 @@ __device__ __forceinline__ void tree_normal(const RobotDev* __restrict__ rb, con
     const bool pose = ti.kinds[k] == PK_TARGET_POSE;
     float col[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (mine && (ti.dof_targets[lane] >> k & 1u)) {
-      if (ti.own_targets[lane] >> k & 1u) tree_joint_col(rb, sm, k, pose, lp, ti.dof_joint[lane], 1.f, col);
+      if ((ti.own_targets[lane] >> k & 1u) && PK_IN_BOUNDS(ti.dof_joint[lane], kMaxJoints, kSiteTreeLink))
+        tree_joint_col(rb, sm, k, pose, lp, ti.dof_joint[lane], 1.f, col);
       for (int m = 0; m < ti.n_mim[lane]; ++m)  // a mimic joint adds to its source's column
-        if (ti.mim_targets[lane][m] >> k & 1u)
+        if ((ti.mim_targets[lane][m] >> k & 1u) && PK_IN_BOUNDS(ti.mim_joint[lane][m], kMaxJoints, kSiteTreeLink))
           tree_joint_col(rb, sm, k, pose, lp, ti.mim_joint[lane][m], ti.mim_mult[lane][m], col);
     }
 #pragma unroll
@@ -425,6 +428,7 @@ __device__ void tree_lm_run(const RobotDev* __restrict__ rb, const TreeInfo& ti,
     int sd, tgt;
     claim_order(prob, batch, n_seeds, lp.cancel != 0, &tgt, &sd);
     const int pid = tgt * n_seeds + sd;
+    if (!PK_IN_BOUNDS(pid, P, kSiteTreeClaimPid)) continue;
     if (lp.cancel) {
       int c = 0;
       if (lane == 0) c = __ldcg(flags + tgt);
@@ -569,8 +573,8 @@ __device__ __forceinline__ void chain_chunk_claim(ChainQueue<N>& q, int buf, int
   if (lane == 0) base = atomicAdd(head, kQ);
   base = __shfl_sync(kTreeFull, base, 0);
   const int p = base + lane;
+  int tgt = 0, pid = -1;
   if (p < P) {
-    int tgt, pid;
     if (lp.resume_in) {  // a suspended problem: its record holds the configuration and iteration count
       pid = __ldcg(lp.resume_in + p);
       tgt = pid / n_seeds;
@@ -579,6 +583,11 @@ __device__ __forceinline__ void chain_chunk_claim(ChainQueue<N>& q, int buf, int
       claim_order(p, batch, n_seeds, cancel, &tgt, &sd);
       pid = tgt * n_seeds + sd;
     }
+    if (!PK_IN_BOUNDS(pid, (long long)batch * n_seeds, kSiteChainClaimPid) ||
+        !PK_IN_BOUNDS(tgt, batch, kSiteChainClaimTgt))
+      pid = -1;  // skipped like a claim past the end
+  }
+  if (pid >= 0) {
     q.pid[buf][lane] = pid;
     q.tid[buf][lane] = tgt;
     const float* tp = targets + (size_t)tgt * 12;

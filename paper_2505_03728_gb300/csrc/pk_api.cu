@@ -267,6 +267,35 @@ TraceScope::~TraceScope() {
 
 }  // namespace pk
 
+namespace pk {
+
+static std::vector<BoundsReader>& bounds_readers() {
+  static std::vector<BoundsReader> readers;
+  return readers;
+}
+// Called from each translation unit's static initialisation (library load).
+bool bounds_register(BoundsReader reader) {
+  bounds_readers().push_back(reader);
+  return true;
+}
+// The first recorded failure over the translation units (each record cleared).
+unsigned long long bounds_take_all() {
+  unsigned long long first = 0;
+  for (BoundsReader r : bounds_readers()) {
+    const unsigned long long v = r();
+    if (v && !first) first = v;
+  }
+  return first;
+}
+
+#ifdef PK_DEBUG_BOUNDS
+// One check that fails (i = n against the bound n) so that the status path can
+// be exercised; the index addresses nothing.
+__global__ void bounds_selftest_kernel(int n) { (void)PK_IN_BOUNDS(n, n, kSiteSelfTest); }
+#endif
+
+}  // namespace pk
+
 extern "C" {
 
 pk_status pk_trace_enable(int32_t enable) {
@@ -294,6 +323,40 @@ pk_status pk_trace_summary(const char* kernel, double* total_ms, int64_t* launch
   *total_ms = ms;
   *launches = n;
   return PK_OK;
+}
+
+int32_t pk_debug_bounds_enabled(void) {
+#ifdef PK_DEBUG_BOUNDS
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+pk_status pk_debug_bounds_take(uint64_t* code) {
+  if (!code) return fail(PK_ERR_INVALID_ARG, "code is NULL");
+  *code = 0;
+#ifdef PK_DEBUG_BOUNDS
+  const cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "pk_debug_bounds_take");
+  *code = pk::bounds_take_all();
+  return PK_OK;
+#else
+  return fail(PK_ERR_UNSUPPORTED, "this library was built without PK_DEBUG_BOUNDS");
+#endif
+}
+
+pk_status pk_debug_bounds_selftest(int32_t n, void* stream) {
+#ifdef PK_DEBUG_BOUNDS
+  if (n < 0) return fail(PK_ERR_INVALID_ARG, "n must be >= 0");
+  pk::bounds_selftest_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(n);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PK_OK : cuda_fail(e, "pk_debug_bounds_selftest");
+#else
+  (void)n;
+  (void)stream;
+  return fail(PK_ERR_UNSUPPORTED, "this library was built without PK_DEBUG_BOUNDS");
+#endif
 }
 
 void pk_trajopt_params_default(pk_trajopt_params* p) {

@@ -231,4 +231,55 @@ struct TraceScope {
   cudaStream_t stream;
 };
 
+
+// ---------------------------------------------------------------------------
+// Index checks (PK_DEBUG_BOUNDS builds).  PK_IN_BOUNDS(i, n, site) is true
+// when 0 <= i < n.  In a build compiled with -DPK_DEBUG_BOUNDS a failed check
+// also records the first failure since the last read as
+//   (site << 48) | (min(n, 2^24 - 1) << 24) | min(i, 2^24 - 2)   (i < 0: 2^24 - 1)
+// in a status word, and the caller skips the access that the index was for;
+// nothing traps.  Without device-code linking every translation unit has its
+// own word, so each registers a reader that pk_debug_bounds_take() calls.  In
+// other builds the macro is the constant `true`.
+using BoundsReader = unsigned long long (*)();
+bool bounds_register(BoundsReader reader);
+unsigned long long bounds_take_all();
+
+// Check sites (the `site` field of a recorded failure).
+enum BoundsSite : int {
+  kSiteChainClaimPid = 1,    // chain queue: record index of a claimed or resumed problem
+  kSiteChainClaimTgt = 2,    // chain queue: target index
+  kSiteTreeClaimPid = 3,     // tree kernel: record index of a claimed problem
+  kSiteTreeParent = 4,       // tree FK: joint, parent or variable index
+  kSiteTreeLink = 5,         // tree targets: target link / variable joint
+  kSiteReduceRec = 6,        // best-seed selection: record index
+  kSiteBeamKeep = 7,         // IK-Beam: kept seed index
+  kSiteTrajSphere = 8,       // trajectory collisions: obstacle index of a screened pair
+  kSiteSelectClear = 9,      // collision-free seed choice: record index
+  kSiteSelfTest = 15,        // pk_debug_bounds_selftest
+};
+
 }  // namespace pk
+
+#if defined(__CUDACC__) && defined(PK_DEBUG_BOUNDS)
+static __device__ unsigned long long g_pk_bounds;
+static unsigned long long pk_bounds_take_local() {
+  unsigned long long v = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, g_pk_bounds, sizeof(v)) != cudaSuccess) return 0;
+  if (v) cudaMemcpyToSymbol(g_pk_bounds, &z, sizeof(z));
+  return v;
+}
+static const bool pk_bounds_registered = pk::bounds_register(&pk_bounds_take_local);
+namespace pk {
+__device__ __forceinline__ bool in_bounds_check(long long i, long long n, int site) {
+  if (i >= 0 && i < n) return true;
+  const unsigned long long nb = n < 0 ? 0ull : (n > 0xffffffll ? 0xffffffull : (unsigned long long)n);
+  const unsigned long long ib = i < 0 ? 0xffffffull : (i > 0xfffffell ? 0xfffffeull : (unsigned long long)i);
+  atomicCAS(&g_pk_bounds, 0ull, ((unsigned long long)(site & 0x7fff) << 48) | (nb << 24) | ib);
+  return false;
+}
+}  // namespace pk
+#define PK_IN_BOUNDS(i, n, site) (::pk::in_bounds_check((long long)(i), (long long)(n), (site)))
+#else
+#define PK_IN_BOUNDS(i, n, site) true
+#endif

@@ -465,6 +465,7 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
     while (cand) {
       const int o = __ffsll(cand) - 1;
       cand &= cand - 1;
+      if (!PK_IN_BOUNDS(o, tp.n_obs, kSiteTrajSphere)) continue;
       const float4 ob = *reinterpret_cast<const float4*>(S.obs[o]);
       const float v0 = c[0] - ob.x, v1 = c[1] - ob.y, v2 = c[2] - ob.z;
       const float dd = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
@@ -1656,7 +1657,7 @@ __global__ void __launch_bounds__(128) select_clear_kernel(
       bs = os;
     }
   }
-  if (lane == 0) {
+  if (lane == 0 && PK_IN_BOUNDS(bs, n_seeds, kSiteSelectClear)) {
     const float* r = rec + ((size_t)b * n_seeds + bs) * stride;
 #pragma unroll
     for (int j = 0; j < N; ++j) q_out[(size_t)b * N + j] = r[j];

@@ -20,7 +20,9 @@ import numpy as np
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpk.so")
+# PK_DEBUG_BOUNDS=1 in the environment selects the index-checked build
+# (libpk_debug.so, build(debug_bounds=True)); tests only.
+LIB_PATH = os.path.join(HERE, "libpk_debug.so" if os.environ.get("PK_DEBUG_BOUNDS") == "1" else "libpk.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pk.h")
 
 PK_OK, PK_ERR_INVALID_ARG, PK_ERR_CUDA, PK_ERR_OOM, PK_ERR_TIMEOUT, PK_ERR_UNSUPPORTED = range(6)
@@ -139,6 +141,9 @@ _SIGNATURES = {
     "pk_seednet_refine": (_i32, [_vp, _i32, _i32, C.c_uint64, _i32p, _vp]),
     "pk_seednet_pool": (_i32, [_vp, _vp, _vp, _i32p, _vp]),
     "pk_trace_enable": (_i32, [_i32]),
+    "pk_debug_bounds_enabled": (_i32, []),
+    "pk_debug_bounds_take": (_i32, [C.POINTER(C.c_uint64)]),
+    "pk_debug_bounds_selftest": (_i32, [_i32, _vp]),
     "pk_trace_summary": (_i32, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
 
@@ -414,6 +419,27 @@ def pk_ik_split_workspace_stats(workspace: torch.Tensor) -> tuple:
     out = (C.c_int64 * 8)()
     _check(lib().pk_ik_split_workspace_stats(_dev(workspace, torch.uint8, "workspace"), out))
     return tuple(dict(evals=out[i], builds=out[i + 1], solves=out[i + 2], problems=out[i + 3]) for i in (0, 4))
+
+
+def pk_debug_bounds_enabled() -> bool:
+    return bool(lib().pk_debug_bounds_enabled())
+
+
+def pk_debug_bounds_take() -> int:
+    """First failed index check since the last call (0: none), cleared on read."""
+    code = C.c_uint64(0)
+    _check(lib().pk_debug_bounds_take(C.byref(code)))
+    return int(code.value)
+
+
+def pk_debug_bounds_decode(code: int) -> tuple[int, int, int]:
+    """(site, bound, index) of a code from pk_debug_bounds_take; index -1 if negative."""
+    site, bound, index = (code >> 48) & 0x7FFF, (code >> 24) & 0xFFFFFF, code & 0xFFFFFF
+    return site, bound, (-1 if index == 0xFFFFFF else index)
+
+
+def pk_debug_bounds_selftest(n: int, stream=None):
+    _check(lib().pk_debug_bounds_selftest(int(n), _stream(stream)))
 
 
 def pk_trace_enable(enable: bool = True):
