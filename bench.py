@@ -96,7 +96,7 @@ def parse():
     ap.add_argument("--no-cancel", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--train-epochs", type=int, default=32)
+    ap.add_argument("--train-epochs", type=int, default=128)
     ap.add_argument("--no-extra", action="store_true", help="skip the uneven-batch and trajectory lines")
     ap.add_argument("--case", choices=CASES, default=None,
                     help="profiling case: run one small kernel workload (a few launches, --batch sized) and exit; "
