@@ -45,10 +45,27 @@ struct TrajSmem {
                                                 // scalar (velocity limits, swept spheres; X only)
   float g[2][kTrajMaxT][8];    // J^T r
   float f[2], mind[2], gpe[2], gre[2];
-  float p[kTrajMaxT][N + 1][3];  // joint origins and tool point (world), candidate
-  float w[kTrajMaxT][N][3];      // joint axes (world), candidate
-  float Linv[kTrajMaxT][NT];     // inverse of the diagonal Cholesky factor (lower)
-  float L[B][kTrajMaxT][N][N];   // L[k-1][t]: factor block (t, t-k)
+  // The candidate's world frames live only through an evaluation and the
+  // factor only through a solve, so they share space.
+  union {
+    struct {
+      float p[kTrajMaxT][N + 1][3];  // joint origins and tool point (world), candidate
+      float w[kTrajMaxT][N][3];      // joint axes (world), candidate
+    };
+    struct {
+      float Linv[kTrajMaxT][NT];     // inverse of the diagonal Cholesky factor (lower)
+      // L[k-1][t]: factor block (t, t-k).  Band 2 keeps only k = 1: the
+      // two-ended solve forms the (t, t-2) block from Linv where it is used,
+      // and the one-ended solve (T < 8) keeps it in L2s.
+      float L[B == 2 ? 1 : B][kTrajMaxT][N][N];
+    };
+  };
+  float L2s[B == 2 ? 8 : 1][N][N];
+  // factor block (t, t-k) of the one-ended solve
+  __device__ float (&Lb(int k, int t))[N][N] {
+    if constexpr (B == 2) return k == 1 ? L[0][t] : L2s[t];
+    else return L[k - 1][t];
+  }
   float M[N][N];
   float Sch[NT];
   float tmp[8];
@@ -674,10 +691,10 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int 
       float m = ((i == j) ? sb[B - 1] : 0.f);
       if constexpr (B == 2 && X) m += S.E[buf][t][i][j];
       if (t >= B) {
-        S.L[B - 1][t][i][j] = (j >= i) ? cb * S.Linv[t - B][tri(j, i)] : 0.f;
+        S.Lb(B, t)[i][j] = (j >= i) ? cb * S.Linv[t - B][tri(j, i)] : 0.f;
 #pragma unroll
         for (int k = 0; k < N; ++k)
-          if (k >= i) m = fmaf(-cb * S.Linv[t - B][tri(k, i)], S.L[0][t - B + 1][j][k], m);
+          if (k >= i) m = fmaf(-cb * S.Linv[t - B][tri(k, i)], S.Lb(1, t - B + 1)[j][k], m);
       }
       S.M[i][j] = m;
     }
@@ -695,7 +712,7 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int 
           for (int mm = k + 1; mm <= B; ++mm)
             if (t >= mm)
 #pragma unroll
-              for (int l = 0; l < N; ++l) m = fmaf(-S.L[mm - 1][t][i][l], S.L[mm - k - 1][t - k][j][l], m);
+              for (int l = 0; l < N; ++l) m = fmaf(-S.Lb(mm, t)[i][l], S.Lb(mm - k, t - k)[j][l], m);
           S.M[i][j] = m;
         }
         __syncthreads();
@@ -707,7 +724,7 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int 
 #pragma unroll
         for (int l = 0; l < N; ++l)
           v = fmaf(S.M[i][l], ltri<N>(S.Linv[t - k], j, l), v);
-        S.L[k - 1][t][i][j] = v;
+        S.Lb(k, t)[i][j] = v;
       }
       __syncthreads();
     }
@@ -720,7 +737,7 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int 
       for (int k = 1; k <= B; ++k)
         if (t >= k)
 #pragma unroll
-          for (int l = 0; l < N; ++l) v = fmaf(-S.L[k - 1][t][i][l], S.L[k - 1][t][j][l], v);
+          for (int l = 0; l < N; ++l) v = fmaf(-S.Lb(k, t)[i][l], S.Lb(k, t)[j][l], v);
       S.Sch[tid] = v;
     }
     __syncthreads();
@@ -762,7 +779,7 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int 
       for (int k = 1; k <= B; ++k)
         if (t >= k)
 #pragma unroll
-          for (int l = 0; l < N; ++l) v = fmaf(-S.L[k - 1][t][tid][l], S.y[t - k][l], v);
+          for (int l = 0; l < N; ++l) v = fmaf(-S.Lb(k, t)[tid][l], S.y[t - k][l], v);
       S.tmp[tid] = v;
     }
     __syncthreads();
@@ -783,7 +800,7 @@ __device__ bool banded_solve(const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int 
       for (int k = 1; k <= B; ++k)
         if (t + k < T)
 #pragma unroll
-          for (int l = 0; l < N; ++l) v = fmaf(-S.L[k - 1][t + k][l][tid], S.y[t + k][l], v);
+          for (int l = 0; l < N; ++l) v = fmaf(-S.Lb(k, t + k)[l][tid], S.y[t + k][l], v);
       S.tmp[tid] = v;
     }
     __syncthreads();
