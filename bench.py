@@ -53,12 +53,12 @@ FLOPS_PER_BUILD = 1818.9
 FLOPS_PER_SOLVE = 252.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
 # DRAM bytes (read + write) per target of the first LM launch: ncu capture of
-# this benchmark's own learned steps at 65,536 targets x 8 seeds (36.3 MB per
+# this benchmark's own learned steps at 65,536 targets x 8 seeds (36.0 MB per
 # launch, the mean of the two timed steps; profiles/ has the launch list).
-LM_DRAM_BYTES_PER_TARGET = (27434240 + 9253888 + 27069184 + 8891648) / 2 / 65536
+LM_DRAM_BYTES_PER_TARGET = (27203328 + 9022720 + 26937088 + 8760832) / 2 / 65536
 # mlp_fused_kernel, dram__bytes_read.sum + write.sum per launch at 65,536
 # targets: mean of the two timed steps of the same capture
-MLP_DRAM_BYTES_65536 = (4965120 + 256 + 4954880 + 256) / 2
+MLP_DRAM_BYTES_65536 = (4964864 + 1536 + 4953344 + 1536) / 2
 # Algorithmic FLOPs of the trajectory workload (T = 64, 32 obstacles + plane),
 # same census: per trajectory-iteration one candidate evaluation, one damped
 # block-banded solve and, at the oracle's accept rate, one normal-equation
