@@ -429,7 +429,10 @@ template <int N, int B, bool X>
 __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, TrajSmem<N, B, X>& S, int buf, int t,
                                 int lane, float& fpart, float& mind) {
   const int nsph = N * tp.S;
-  unsigned long long amask = 0ull;
+  // active obstacles of this lane's sphere as two 32-bit halves (obstacles
+  // 0-31 and 32-63): 32-bit mask arithmetic, and the upper half is empty for
+  // scenes of up to 32 obstacles
+  uint32_t am_lo = 0u, am_hi = 0u;
   bool aplane = false;
   float c[3] = {0.f, 0.f, 0.f}, rad = 0.f;
   int l = 0;
@@ -457,7 +460,7 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
   float4 ob0 = make_float4(0.f, 0.f, 0.f, 0.f), ob1 = ob0;
   if (lane < tp.n_obs) ob0 = *reinterpret_cast<const float4*>(S.obs[lane]);
   if (two && lane + 32 < tp.n_obs) ob1 = *reinterpret_cast<const float4*>(S.obs[lane + 32]);
-  unsigned long long cand = 0ull;  // candidate obstacles of this lane's link
+  uint32_t cand_lo = 0u, cand_hi = 0u;  // candidate obstacles of this lane's link
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     const float mx = __shfl_sync(0xffffffffu, bm[0], k), my = __shfl_sync(0xffffffffu, bm[1], k),
@@ -471,7 +474,10 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
       th = fmaf(h + ob1.w, 1.00001f, 1e-6f);
       hi = __ballot_sync(0xffffffffu, lane + 32 < tp.n_obs && fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) < th * th);
     }
-    if (l == k) cand = ((unsigned long long)hi << 32) | lo;
+    if (l == k) {
+      cand_lo = lo;
+      cand_hi = hi;
+    }
   }
   if (lane < nsph) {
     const int s = lane % tp.S;
@@ -479,16 +485,24 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
 #pragma unroll
     for (int i = 0; i < 3; ++i) c[i] = fmaf(al, S.p[t][l + 1][i] - S.p[t][l][i], S.p[t][l][i]);
     rad = S.rad[l][s];
-    while (cand) {
-      const int o = __ffsll(cand) - 1;
-      cand &= cand - 1;
-      if (!PK_IN_BOUNDS(o, tp.n_obs, kSiteTrajSphere)) continue;
-      const float4 ob = *reinterpret_cast<const float4*>(S.obs[o]);
-      const float v0 = c[0] - ob.x, v1 = c[1] - ob.y, v2 = c[2] - ob.z;
-      const float dd = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
-      const float R = rad + ob.w, Re = R + tp.eta;
-      mind = fminf(mind, fmaf(-R, R, dd));
-      if (dd < Re * Re) amask |= 1ull << o;
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      uint32_t cm = hf ? cand_hi : cand_lo;
+      uint32_t am = 0u;
+      while (cm) {
+        const int ob_i = __ffs(cm) - 1;
+        cm &= cm - 1;
+        const int o = ob_i + 32 * hf;
+        if (!PK_IN_BOUNDS(o, tp.n_obs, kSiteTrajSphere)) continue;
+        const float4 ob = *reinterpret_cast<const float4*>(S.obs[o]);
+        const float v0 = c[0] - ob.x, v1 = c[1] - ob.y, v2 = c[2] - ob.z;
+        const float dd = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+        const float R = rad + ob.w, Re = R + tp.eta;
+        mind = fminf(mind, fmaf(-R, R, dd));
+        if (dd < Re * Re) am |= 1u << ob_i;
+      }
+      if (hf) am_hi = am;
+      else am_lo = am;
     }
     if (l != 0) {  // the first link is not tested against the plane
       const float d = tp.plane[0] * c[0] + tp.plane[1] * c[1] + tp.plane[2] * c[2] - tp.plane[3] - rad;
@@ -502,7 +516,7 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
   constexpr int NT = N * (N + 1) / 2;
   int ei, ek;
   tri_rc<N>(lane, ei, ek);  // (ei, ek): this lane's J^T J entry when lane < NT
-  unsigned lanes = __ballot_sync(0xffffffffu, amask != 0ull || aplane);
+  unsigned lanes = __ballot_sync(0xffffffffu, (am_lo | am_hi) != 0u || aplane);
   // lane i < N keeps joint i's world origin and axis; without swept rows
   // (which other warps add into D_t and g_t) the timestep's J^T J entry and
   // J^T r entry stay in registers across the pairs (the same summation order
@@ -524,8 +538,7 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
   while (lanes) {
     const int src = __ffs(lanes) - 1;
     lanes &= lanes - 1;
-    unsigned long long m = ((unsigned long long)__shfl_sync(0xffffffffu, (unsigned)(amask >> 32), src) << 32) |
-                           __shfl_sync(0xffffffffu, (unsigned)amask, src);
+    uint32_t m_lo = __shfl_sync(0xffffffffu, am_lo, src), m_hi = __shfl_sync(0xffffffffu, am_hi, src);
     bool pl = __shfl_sync(0xffffffffu, aplane ? 1 : 0, src) != 0;
     const float cs[3] = {__shfl_sync(0xffffffffu, c[0], src), __shfl_sync(0xffffffffu, c[1], src),
                          __shfl_sync(0xffffffffu, c[2], src)};
@@ -533,9 +546,12 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
     const int ls = __shfl_sync(0xffffffffu, l, src);
     for (;;) {
       int o;
-      if (m) {
-        o = __ffsll(m) - 1;
-        m &= m - 1;
+      if (m_lo) {  // obstacles in increasing index, then the plane
+        o = __ffs(m_lo) - 1;
+        m_lo &= m_lo - 1;
+      } else if (m_hi) {
+        o = __ffs(m_hi) + 31;
+        m_hi &= m_hi - 1;
       } else if (pl) {
         o = tp.n_obs;
         pl = false;
@@ -585,7 +601,7 @@ __device__ void eval_collisions(const ChainC<N>& rc, const TrajParamsDev& tp, Tr
     }
   }
   if constexpr (!X) {
-    if (__any_sync(0xffffffffu, amask != 0ull || aplane)) {
+    if (__any_sync(0xffffffffu, (am_lo | am_hi) != 0u || aplane)) {
       if (lane < NT) S.D[buf][t][lane] = dacc;
       if (lane < N) S.g[buf][t][lane] = gacc;
     }
