@@ -41,6 +41,32 @@ struct TreeInfo {
   float lo[kTreeMaxDof], hi[kTreeMaxDof];
 };
 
+// The per-variable and per-target fields of TreeInfo that one lane reads,
+// loaded into registers once: indexed by lane in the parameter (constant)
+// space, the lanes' distinct addresses would be served one after another at
+// every use.
+struct TreeLane {
+  int32_t dof_joint = 0, n_mim = 0, link = 0, kind = 0;
+  uint32_t dof_targets = 0u, own_targets = 0u;
+  float lo = 0.f, hi = 0.f;
+};
+__device__ __forceinline__ TreeLane tree_lane(const TreeInfo& ti, int lane) {
+  TreeLane t;
+  if (lane < ti.n_dof) {
+    t.dof_joint = ti.dof_joint[lane];
+    t.n_mim = ti.n_mim[lane];
+    t.dof_targets = ti.dof_targets[lane];
+    t.own_targets = ti.own_targets[lane];
+    t.lo = ti.lo[lane];
+    t.hi = ti.hi[lane];
+  }
+  if (lane < ti.k) {
+    t.link = ti.links[lane];
+    t.kind = ti.kinds[lane];
+  }
+  return t;
+}
+
 // Shared memory of one warp.
 struct TreeWarpSmem {
   float frames[kMaxJoints][12];
@@ -105,17 +131,17 @@ __device__ __forceinline__ void tree_fk(const RobotDev* __restrict__ rb, const T
 
 // Evaluate sm.q: residual data into sm.xi / sm.th, returns the cost; the
 // largest position and rotation errors over targets come back in pe / re.
-__device__ __forceinline__ float tree_eval(const RobotDev* __restrict__ rb, const TreeInfo& ti,
+__device__ __forceinline__ float tree_eval(const RobotDev* __restrict__ rb, const TreeInfo& ti, const TreeLane& tl,
                                            const LmParams& lp, TreeWarpSmem& sm, int lane, float& pe, float& re) {
   tree_fk(rb, ti, sm, lane);
   float acc = 0.f, mpe = 0.f, mre = 0.f;
-  if (lane < ti.k && PK_IN_BOUNDS(ti.links[lane], kMaxJoints, kSiteTreeLink)) {
+  if (lane < ti.k && PK_IN_BOUNDS(tl.link, kMaxJoints, kSiteTreeLink)) {
     Rt Tl, Ti, E;
-    rt_load(sm.frames[ti.links[lane]], Tl);
+    rt_load(sm.frames[tl.link], Tl);
     rt_load(sm.Ti[lane], Ti);
     rt_mul(Ti, Tl, E);
     mpe = sqrtf(E.t[0] * E.t[0] + E.t[1] * E.t[1] + E.t[2] * E.t[2]);
-    if (ti.kinds[lane] == PK_TARGET_POSE) {
+    if (tl.kind == PK_TARGET_POSE) {
       float xi[6];
       const float th = se3_log(E, xi);
       mre = th;
@@ -136,8 +162,8 @@ __device__ __forceinline__ float tree_eval(const RobotDev* __restrict__ rb, cons
   }
   if (lane < ti.n_dof) {
     const float q = sm.q[lane];
-    const float h = fmaxf(0.f, q - ti.hi[lane]) + fmaxf(0.f, ti.lo[lane] - q);
-    const float d = q - 0.5f * (ti.lo[lane] + ti.hi[lane]);
+    const float h = fmaxf(0.f, q - tl.hi) + fmaxf(0.f, tl.lo - q);
+    const float d = q - 0.5f * (tl.lo + tl.hi);
     acc = fmaf(lp.w_limit * lp.w_limit, h * h, fmaf(lp.w_rest * lp.w_rest, d * d, acc));
   }
   if (lp.w_self > 0.f) {
@@ -235,7 +261,7 @@ __device__ __forceinline__ void tree_joint_col(const RobotDev* __restrict__ rb, 
 // Row `lane` of J^T J (in Arow[0..N)) and entry g of J^T r at the configuration
 // whose frames and residuals sm holds.
 template <int N>
-__device__ __forceinline__ void tree_normal(const RobotDev* __restrict__ rb, const TreeInfo& ti,
+__device__ __forceinline__ void tree_normal(const RobotDev* __restrict__ rb, const TreeInfo& ti, const TreeLane& tl,
                                             const LmParams& lp, TreeWarpSmem& sm, int lane, float (&Arow)[N],
                                             float& g) {
 #pragma unroll
@@ -245,10 +271,10 @@ __device__ __forceinline__ void tree_normal(const RobotDev* __restrict__ rb, con
   for (int k = 0; k < ti.k; ++k) {
     const bool pose = ti.kinds[k] == PK_TARGET_POSE;
     float col[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (mine && (ti.dof_targets[lane] >> k & 1u)) {
-      if ((ti.own_targets[lane] >> k & 1u) && PK_IN_BOUNDS(ti.dof_joint[lane], kMaxJoints, kSiteTreeLink))
-        tree_joint_col(rb, sm, k, pose, lp, ti.dof_joint[lane], 1.f, col);
-      for (int m = 0; m < ti.n_mim[lane]; ++m)  // a mimic joint adds to its source's column
+    if (mine && (tl.dof_targets >> k & 1u)) {
+      if ((tl.own_targets >> k & 1u) && PK_IN_BOUNDS(tl.dof_joint, kMaxJoints, kSiteTreeLink))
+        tree_joint_col(rb, sm, k, pose, lp, tl.dof_joint, 1.f, col);
+      for (int m = 0; m < tl.n_mim; ++m)  // a mimic joint adds to its source's column
         if ((ti.mim_targets[lane][m] >> k & 1u) && PK_IN_BOUNDS(ti.mim_joint[lane][m], kMaxJoints, kSiteTreeLink))
           tree_joint_col(rb, sm, k, pose, lp, ti.mim_joint[lane][m], ti.mim_mult[lane][m], col);
     }
@@ -275,8 +301,8 @@ __device__ __forceinline__ void tree_normal(const RobotDev* __restrict__ rb, con
           if (sm.ps[p] == 0.f) continue;
           const int ja = rb->sph_joint[rb->pair[p][0]], jb = rb->sph_joint[rb->pair[p][1]];
           float v = 0.f;
-          for (int m = -1; m < ti.n_mim[lane]; ++m) {  // the variable's own joint, then its mimics
-            const int jj = m < 0 ? ti.dof_joint[lane] : ti.mim_joint[lane][m];
+          for (int m = -1; m < tl.n_mim; ++m) {  // the variable's own joint, then its mimics
+            const int jj = m < 0 ? tl.dof_joint : ti.mim_joint[lane][m];
             const float scale = m < 0 ? 1.f : ti.mim_mult[lane][m];
             const bool ina = rb->subtree[jj] >> ja & 1ull, inb = rb->subtree[jj] >> jb & 1ull;
             if (!ina && !inb) continue;
@@ -320,13 +346,13 @@ __device__ __forceinline__ void tree_normal(const RobotDev* __restrict__ rb, con
   if (mine) {
     const float q = sm.q[lane];
     float h = 0.f, d = 0.f;
-    if (q > ti.hi[lane]) { h = q - ti.hi[lane]; d = 1.f; }
-    if (q < ti.lo[lane]) { h = ti.lo[lane] - q; d = -1.f; }
+    if (q > tl.hi) { h = q - tl.hi; d = 1.f; }
+    if (q < tl.lo) { h = tl.lo - q; d = -1.f; }
     const float wl2 = lp.w_limit * lp.w_limit, wr2 = lp.w_rest * lp.w_rest;
 #pragma unroll
     for (int j = 0; j < N; ++j)
       if (j == lane) Arow[j] += wl2 * d * d + wr2;
-    g = fmaf(wl2 * d, h, fmaf(wr2, q - 0.5f * (ti.lo[lane] + ti.hi[lane]), g));
+    g = fmaf(wl2 * d, h, fmaf(wr2, q - 0.5f * (tl.lo + tl.hi), g));
   }
 }
 
@@ -419,6 +445,7 @@ __device__ void tree_lm_run(const RobotDev* __restrict__ rb, const TreeInfo& ti,
   const int n = ti.n_dof, k = ti.k;
   const int np = (n + 3) & ~3, stride = np + 4;
   const int batch = P / n_seeds;
+  const TreeLane tl = tree_lane(ti, lane);
   for (;;) {
     int prob = 0;
     if (lane == 0) prob = atomicAdd(head, 1);
@@ -445,7 +472,7 @@ __device__ void tree_lm_run(const RobotDev* __restrict__ rb, const TreeInfo& ti,
     if (lane < k) {
       Rt T, Ti;
       rt_load(targets + ((size_t)tgt * k + lane) * 12, T);
-      if (ti.kinds[lane] == PK_TARGET_POSE) {
+      if (tl.kind == PK_TARGET_POSE) {
         rt_inv(T, Ti);
       } else {
         rt_identity(Ti);
@@ -457,7 +484,7 @@ __device__ void tree_lm_run(const RobotDev* __restrict__ rb, const TreeInfo& ti,
     sm.q[lane] = q;
     __syncwarp();
     float pe, re;
-    float f = tree_eval(rb, ti, lp, sm, lane, pe, re);
+    float f = tree_eval(rb, ti, tl, lp, sm, lane, pe, re);
     const unsigned one = lane == 0 ? 1u : 0u;  // warp-level work counted once
     wc.eval += one;
     float Arow[N], g = 0.f;
@@ -468,7 +495,7 @@ __device__ void tree_lm_run(const RobotDev* __restrict__ rb, const TreeInfo& ti,
     if (!isfinite(f)) { done = true; status = PK_P_NONFINITE; }
     else if (lp.early_exit && conv) { done = true; status = PK_P_CONVERGED; }
     else if (lp.max_iters <= 0) { done = true; status = conv ? PK_P_CONVERGED : PK_P_MAX_ITERS; }
-    else { tree_normal<N>(rb, ti, lp, sm, lane, Arow, g); wc.build += one; }
+    else { tree_normal<N>(rb, ti, tl, lp, sm, lane, Arow, g); wc.build += one; }
     while (!done) {
       ++it;
       float dx;
@@ -478,7 +505,7 @@ __device__ void tree_lm_run(const RobotDev* __restrict__ rb, const TreeInfo& ti,
       sm.q[lane] = qc;
       __syncwarp();
       float pe_c, re_c;
-      const float fc = tree_eval(rb, ti, lp, sm, lane, pe_c, re_c);
+      const float fc = tree_eval(rb, ti, tl, lp, sm, lane, pe_c, re_c);
       wc.eval += one;
       if (fc < f) {
         q = qc;
@@ -491,7 +518,7 @@ __device__ void tree_lm_run(const RobotDev* __restrict__ rb, const TreeInfo& ti,
           done = true;
           status = PK_P_CONVERGED;
         } else if (it < lp.max_iters) {
-          tree_normal<N>(rb, ti, lp, sm, lane, Arow, g);
+          tree_normal<N>(rb, ti, tl, lp, sm, lane, Arow, g);
           wc.build += one;
         }
       } else {
