@@ -253,27 +253,37 @@ __device__ __forceinline__ float se3_log(const Rt& E, float* xi) {
 // Packed lower-triangular storage: element (i, j), j <= i, at i(i+1)/2 + j.
 __host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
-// In-place Cholesky of a packed SPD matrix, row by row (Cholesky-Banachiewicz).
-// The diagonal slots receive the RECIPROCAL of L's diagonal so that the
-// triangular solves multiply instead of divide.  Returns false on a
-// non-positive or non-finite pivot.
+// In-place Cholesky of a packed SPD matrix.  The diagonal slots receive the
+// RECIPROCAL of L's diagonal so that the triangular solves multiply instead
+// of divide.  Returns false on a non-positive or non-finite pivot.
+//
+// Column by column (right-looking) with one column of lookahead: once column
+// j is scaled, pivot j+1 takes its last update and its rsqrt is issued before
+// the rest of the trailing update, whose independent FMAs then cover the
+// rsqrt's latency (a warp issues in order, so the order of the code is the
+// order of the waits).  Every entry still sees the row-by-row form's FMAs in
+// the same order, a_ij - l_i0 l_j0 - l_i1 l_j1 - ... (k ascending), then one
+// multiply by 1 / l_jj, so the factor is bit for bit the same.
 template <int N>
 __device__ __forceinline__ bool chol_packed(float* L) {
-  bool ok = true;
+  float d = L[0];
+  bool ok = (d > 0.f) & (d < INFINITY);
+  float inv = rsqrtf(d);
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
+  for (int j = 0; j < N; ++j) {
+    L[tri(j, j)] = inv;
 #pragma unroll
-    for (int j = 0; j < i; ++j) {
-      float x = L[tri(i, j)];
+    for (int i = j + 1; i < N; ++i) L[tri(i, j)] *= inv;
+    if (j + 1 < N) {
+      d = fmaf(-L[tri(j + 1, j)], L[tri(j + 1, j)], L[tri(j + 1, j + 1)]);
+      ok = ok & (d > 0.f) & (d < INFINITY);
+      inv = rsqrtf(d);
 #pragma unroll
-      for (int k = 0; k < j; ++k) x = fmaf(-L[tri(i, k)], L[tri(j, k)], x);
-      L[tri(i, j)] = x * L[tri(j, j)];
+      for (int k = j + 1; k < N; ++k)
+#pragma unroll
+        for (int i = k; i < N; ++i)
+          if (i > j + 1 || k > j + 1) L[tri(i, k)] = fmaf(-L[tri(i, j)], L[tri(k, j)], L[tri(i, k)]);
     }
-    float d = L[tri(i, i)];
-#pragma unroll
-    for (int k = 0; k < i; ++k) d = fmaf(-L[tri(i, k)], L[tri(i, k)], d);
-    ok = ok & (d > 0.f) & (d < INFINITY);
-    L[tri(i, i)] = rsqrtf(d);
   }
   return ok;
 }
