@@ -363,13 +363,14 @@ def extra_workloads(torch, pk, synth, args, flush, stream, chain_net=None):
     pers = []
     for variant, blocks in ((0, (64, 128, 256)), (1, (64, 128))):  # variant 1 caps registers for <= 128
         for block in blocks:
-            plan.set_schedule(block=block, chains_as_trees=0, given_order=best["given_order"], variant=variant)
-            plan.run()
-            torch.cuda.synchronize()
-            conv.zero_()
-            pms = Timed(torch, steps, flush).run(lambda k: plan.run(), stream, after=count)
-            pers.append({"variant": variant, "block": block, "ms_per_step": pms / steps,
-                         "value": int(conv.item()) / (pms / 1e3)})
+            for cat in (0, 1):  # chains thread-per-problem, or every set on the warp path
+                plan.set_schedule(block=block, chains_as_trees=cat, given_order=best["given_order"], variant=variant)
+                plan.run()
+                torch.cuda.synchronize()
+                conv.zero_()
+                pms = Timed(torch, steps, flush).run(lambda k: plan.run(), stream, after=count)
+                pers.append({"variant": variant, "block": block, "chains_as_trees": cat, "ms_per_step": pms / steps,
+                             "value": int(conv.item()) / (pms / 1e3)})
     pbest = min(pers, key=lambda x: x["ms_per_step"])
     out["uneven"]["persistent_single_launch"] = dict(pbest, launch=UNEVEN_LAUNCH[pbest["variant"]] + ", CUDA graph replay")
     plan.set_schedule(block=best["block"], chains_as_trees=best["chains_as_trees"], given_order=best["given_order"],

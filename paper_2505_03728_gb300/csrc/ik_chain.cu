@@ -695,17 +695,22 @@ struct MultiParams {
 
 // MINB = 1 lets the compiler keep every path in registers; MINB = 3 caps the
 // registers for three 128-thread blocks per SM (the autotuner picks).
+// CHAINS = false compiles the thread-per-problem chain path out, for plans
+// whose sets all run on the warp path: the kernel then needs only the tree
+// path's registers, and the capped variant takes four 128-thread blocks per
+// SM (128 registers), as the specialised tree kernel does.
 static_assert(sizeof(ChainQueue<7>) <= sizeof(TreeWarpSmem), "chain queue must fit the per-warp scratch");
 static_assert(sizeof(TreeWarpSmem) % 16 == 0, "per-warp scratch must keep 16-byte alignment");
 
-template <int MINB>
-__global__ void __launch_bounds__(MINB == 1 ? 256 : 128, MINB) ik_multi_kernel(const __grid_constant__ MultiParams mp) {
+template <int MINB, bool CHAINS>
+__global__ void __launch_bounds__(MINB == 1 ? 256 : 128, (MINB == 3 && !CHAINS) ? 4 : MINB)
+    ik_multi_kernel(const __grid_constant__ MultiParams mp) {
   extern __shared__ TreeWarpSmem tsm[];
   TreeWarpSmem& sm = tsm[threadIdx.x >> 5];
   WorkCount wc;
   for (int s = 0; s < mp.n_segs; ++s) {
     const MultiSeg& g = mp.seg[s];
-    if (g.kind == 0) {
+    if (CHAINS && g.kind == 0) {
       LmParams lp = mp.lp;
       lp.pos_only = g.pos_only;
       if (g.pos_only) lp.tol_rot = INFINITY;
@@ -745,27 +750,36 @@ void ik_multi_set_common(void* p, int n_segs, const LmParams& lp, unsigned long 
   mp->stats = stats;
 }
 
-int ik_multi_max_blocks_per_sm(int block, int variant) {
+namespace {
+template <int MINB, bool CHAINS>
+int multi_blocks(int block, size_t smem) {
   int b = 0;
-  const size_t smem = (size_t)(block / 32) * sizeof(TreeWarpSmem);
-  if (variant == 1) {
-    if (block > 128) return 0;
-    cudaFuncSetAttribute(ik_multi_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ik_multi_kernel<3>, block, smem) != cudaSuccess) return 1;
-  } else {
-    cudaFuncSetAttribute(ik_multi_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ik_multi_kernel<1>, block, smem) != cudaSuccess) return 1;
-  }
+  cudaFuncSetAttribute(ik_multi_kernel<MINB, CHAINS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ik_multi_kernel<MINB, CHAINS>, block, smem) != cudaSuccess)
+    return 1;
   return b > 0 ? b : 1;
 }
+}  // namespace
 
-cudaError_t launch_ik_multi(const void* host_params, int variant, int block, int grid, cudaStream_t st) {
+int ik_multi_max_blocks_per_sm(int block, int variant, bool chains) {
+  const size_t smem = (size_t)(block / 32) * sizeof(TreeWarpSmem);
+  if (variant == 1 && block > 128) return 0;
+  if (variant == 1) return chains ? multi_blocks<3, true>(block, smem) : multi_blocks<3, false>(block, smem);
+  return chains ? multi_blocks<1, true>(block, smem) : multi_blocks<1, false>(block, smem);
+}
+
+cudaError_t launch_ik_multi(const void* host_params, int variant, bool chains, int block, int grid,
+                            cudaStream_t st) {
   const size_t smem = (size_t)(block / 32) * sizeof(TreeWarpSmem);
   TraceScope tr("ik_multi", st);
-  if (variant == 1)
-    ik_multi_kernel<3><<<grid, block, smem, st>>>(*(const MultiParams*)host_params);
-  else
-    ik_multi_kernel<1><<<grid, block, smem, st>>>(*(const MultiParams*)host_params);
+  const MultiParams& mp = *(const MultiParams*)host_params;
+  if (variant == 1) {
+    if (chains) ik_multi_kernel<3, true><<<grid, block, smem, st>>>(mp);
+    else ik_multi_kernel<3, false><<<grid, block, smem, st>>>(mp);
+  } else {
+    if (chains) ik_multi_kernel<1, true><<<grid, block, smem, st>>>(mp);
+    else ik_multi_kernel<1, false><<<grid, block, smem, st>>>(mp);
+  }
   return cudaGetLastError();
 }
 

@@ -62,6 +62,7 @@ struct pk_ik_plan {
   size_t ws_bytes = 0, zero_bytes = 0;
   PlanConfig cfg;
   int grid = 0;
+  bool chain_path = false;  // some set runs on the thread-per-problem chain path
   std::vector<int> order;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -117,6 +118,7 @@ void configure(pk_ik_plan* pl, const PlanConfig& cfg) {
                      [&](int a, int b) { return pl->sets[a].cost > pl->sets[b].cost; });
   char* ws = (char*)pl->d_ws;
   int c6 = 0, c7 = 0, tr = 0;
+  pl->chain_path = false;
   for (int s = 0; s < n; ++s) {
     const PlanSet& ps = pl->sets[pl->order[s]];
     pk::MultiSeg g{};
@@ -134,6 +136,7 @@ void configure(pk_ik_plan* pl, const PlanConfig& cfg) {
     g.rec = (float*)(ws + ps.rec_off);
     g.rb = (const pk::RobotDev*)ps.robot->d_blob;
     if (chain) {
+      pl->chain_path = true;
       g.slot = g.n == 6 ? c6++ : c7++;
       pk::ik_multi_set_chain(pl->mp, g.slot, ps.ch);
     } else {
@@ -145,7 +148,9 @@ void configure(pk_ik_plan* pl, const PlanConfig& cfg) {
   pk::ik_multi_set_common(pl->mp, n, plan_lm(&pl->params), (unsigned long long*)ws);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device);
-  pl->grid = cfg.variant < 2 ? pk::ik_multi_max_blocks_per_sm(cfg.block, cfg.variant) * (sms > 0 ? sms : 1) : 0;
+  pl->grid = cfg.variant < 2
+                 ? pk::ik_multi_max_blocks_per_sm(cfg.block, cfg.variant, pl->chain_path) * (sms > 0 ? sms : 1)
+                 : 0;
   if (pl->exec) {
     cudaGraphExecDestroy(pl->exec);
     pl->exec = nullptr;
@@ -209,7 +214,7 @@ cudaError_t enqueue(pk_ik_plan* pl, cudaStream_t st) {
       if ((e = cudaStreamWaitEvent(st, pl->join[s], 0)) != cudaSuccess) return e;
     return cudaSuccess;
   }
-  e = pk::launch_ik_multi(pl->mp, v, pl->cfg.block, pl->grid, st);
+  e = pk::launch_ik_multi(pl->mp, v, pl->chain_path, pl->cfg.block, pl->grid, st);
   if (e != cudaSuccess) return e;
   for (const PlanSet& ps : pl->sets) {
     if (ps.batch == 0) continue;

@@ -169,7 +169,10 @@ struct MultiSeg {
   const RobotDev* rb;
 };
 
-cudaError_t launch_ik_multi(const void* host_params, int variant, int block, int grid, cudaStream_t st);
+// chains: some segment runs on the thread-per-problem chain path (false
+// selects the instantiation without it)
+cudaError_t launch_ik_multi(const void* host_params, int variant, bool chains, int block, int grid,
+                            cudaStream_t st);
 size_t ik_multi_params_size();
 void* ik_multi_params_new();
 void ik_multi_params_free(void* p);
@@ -178,7 +181,7 @@ bool ik_multi_set_chain(void* p, int slot, const ChainHost& ch);
 void ik_multi_set_tree(void* p, int slot, const struct TreeInfo& ti);
 void ik_multi_set_seg(void* p, int s, const MultiSeg& seg);
 void ik_multi_set_common(void* p, int n_segs, const LmParams& lp, unsigned long long* stats);
-int ik_multi_max_blocks_per_sm(int block, int variant);  // sets the smem attribute; 0 = not launchable
+int ik_multi_max_blocks_per_sm(int block, int variant, bool chains);  // sets the smem attribute; 0 = not launchable
 
 // Trajectory optimisation (trajopt.cu).
 constexpr int kTrajMaxT = 64;
