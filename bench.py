@@ -55,10 +55,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 x max 
 # DRAM bytes (read + write) per target of the first LM launch: ncu capture of
 # this benchmark's own learned steps at 65,536 targets x 8 seeds (36.0 MB per
 # launch, the mean of the two timed steps; profiles/ has the launch list).
-LM_DRAM_BYTES_PER_TARGET = (27203328 + 9022720 + 26937088 + 8760832) / 2 / 65536
+LM_DRAM_BYTES_PER_TARGET = (27220736 + 9041152 + 26930176 + 8759040) / 2 / 65536
 # mlp_fused_kernel, dram__bytes_read.sum + write.sum per launch at 65,536
 # targets: mean of the two timed steps of the same capture
-MLP_DRAM_BYTES_65536 = (4964864 + 1536 + 4953344 + 1536) / 2
+MLP_DRAM_BYTES_65536 = (4964352 + 1792 + 4954112 + 2048) / 2
 # Algorithmic FLOPs of the trajectory workload (T = 64, 32 obstacles + plane),
 # same census: per trajectory-iteration one candidate evaluation, one damped
 # block-banded solve and, at the oracle's accept rate, one normal-equation
@@ -66,10 +66,10 @@ MLP_DRAM_BYTES_65536 = (4964864 + 1536 + 4953344 + 1536) / 2
 TRAJ_FLOPS_PER_ITER = 1.0631e6
 TRAJ_FLOPS_PER_INIT = 0.8959e6
 # DRAM bytes (read + write) per trajectory of trajopt_kernel<7, 2, false>: ncu
-# capture of the first 64 trajectories (0.301 MB per launch); each
+# capture of the first 64 trajectories (0.303 MB per launch); each
 # trajectory's inputs and outputs are read and written once, so the launch's
 # traffic scales with the trajectories it solves.
-TRAJ_DRAM_BYTES_PER_TRAJ = (300032 + 1280) / 64
+TRAJ_DRAM_BYTES_PER_TRAJ = (300544 + 2304) / 64
 # Every timed step reads its own input batch; an arm rotates through enough
 # batches to hold at least this many bytes (twice the 129 MB L2).
 ROTATE_BYTES = 256 << 20
