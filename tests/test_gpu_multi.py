@@ -86,3 +86,22 @@ def test_autotuned_schedule_keeps_results_valid():
             assert (a[3] == b[3]).mean() >= 0.97, variant
     st = plan.stats()
     assert st["problems"] > 0
+
+
+def test_persistent_launch_without_chain_path_matches_specialised_kernels():
+    """With every set on the warp path (chains_as_trees = 1) the single
+    persistent launch (variants 0 and 1) is the instantiation without the
+    thread-per-problem chain path; without sibling cancellation its results
+    match the specialised tree kernels' on the same path (variant 2)."""
+    sets, meta = make(0.05)
+    p = pk.pk_ik_params_default(max_iters=50, early_exit=1, cancel_siblings=0)
+    plan = pk.IkPlan(p, sets)
+    plan.set_schedule(block=128, chains_as_trees=1, given_order=1, variant=2)
+    ref = host(plan.run())
+    for variant, block in ((0, 64), (0, 256), (1, 128)):
+        plan.set_schedule(block=block, chains_as_trees=1, given_order=1, variant=variant)
+        got = host(plan.run())
+        for (name, *_), (q0, _, _, s0), (q1, _, _, s1) in zip(meta, ref, got):
+            np.testing.assert_array_equal(s1, s0, err_msg=f"{name} variant {variant} block {block}")
+            both = s0 == 0
+            np.testing.assert_allclose(q1[both], q0[both], rtol=1e-5, atol=1e-5)
