@@ -325,7 +325,9 @@ pk_status pk_ik_beam_solve(const pk_robot* robot, const pk_ik_params* params, co
  * chains of 6 or 7 movable joints one problem per thread and other trees one
  * problem per warp, so warps that finish the expensive sets fall through to
  * the cheap ones (variant 1 caps registers for three 128-thread blocks per SM).
- * Variants 2 and 3 run each set's own specialised kernel (the pk_ik_solve
+ * With every set on the warp path (chains_as_trees = 1) the launch uses a
+ * kernel without the per-thread chain path, at the tree kernel's 128
+ * registers (variant 1: four 128-thread blocks per SM).  Variants 2 and 3 run each set's own specialised kernel (the pk_ik_solve
  * kernels), one after another (2) or on forked streams so that their tails
  * overlap (3).  A plan fixes its buffers at creation; its first run captures
  * the whole solve (workspace reset, the LM kernels, one best-seed reduction
