@@ -381,7 +381,7 @@ def extra_workloads(torch, pk, synth, args, flush, stream, chain_net=None):
     g = pk.Robot.from_spec(spec)
     net = pk.SeedNet(g, links, K=8, width=512, depth=4, seed=11)
     t0 = time.perf_counter()
-    pk.pk_seednet_train(net, pk.pk_train_params_default(epochs=8, steps_per_epoch=1220, batch=8192, seed=520,
+    pk.pk_seednet_train(net, pk.pk_train_params_default(epochs=32, steps_per_epoch=1220, batch=8192, seed=520,
                                                          refine_every=2))
     h_train = time.perf_counter() - t0
     Bh = 65536
